@@ -1,0 +1,395 @@
+"""Benchmark: time-tiled acoustic forward sweep (and its untiled baseline) on GB300.
+
+Default workload (one "step" = one wave_fwd call = the whole forward path):
+512^3 grid, space order 8, two-layer velocity with +-2% noise, 40-point
+damping layer, 1000 time steps, one Ricker source and 512 receivers, fused
+injection and interpolation.  Metric: grid-point updates per second (GPts/s)
+= nx*ny*nz*nt / seconds, device-timed with inputs resident in HBM; each field
+(512 MiB) is larger than L2, so no flush is needed between steps.
+
+Also reported: the untiled sweep on the same workload, the end-to-end rate
+through the C ABI with host buffers (pinned H2D copies of m, damp and the
+source trace, D2H of the receiver traces, inside the timed region), the
+roofline of the sweep kernel from CUDA events the library records around its
+launches, the FWI gradient time per shot (256^3, so 8, 2000 steps,
+checkpoints every 50 steps), SM clocks sampled during the timed region, and
+the FP64 CPU oracle timed on a bounded sample of the workload.
+
+`--impl reference` times the oracle itself (the CPU reference of this
+method) on the same workload and metric.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "acoustic stencil GPts/s tiled vs untiled, % roofline; FWI gradient s/shot"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _workload(args):
+    from paper_1806_08299_gb300 import inputs
+    if args.workload == "c1":
+        p = inputs.c1(nt=args.nt or 100)
+        desc = "c1: 64^3 so4 constant 1.5 km/s, no damping, %d steps, Ricker 10 Hz, 32 receivers" % p.nt
+    else:
+        n = (args.size,) * 3
+        p = inputs.c2(nt=args.nt or 1000, n=n)
+        desc = ("c2: %d^3 so8 two-layer 1.5/2.5 km/s +-2%% noise, 40-pt damping, %d steps, "
+                "1 Ricker 15 Hz source, %d receivers, fused inject/interp" % (n[0], p.nt, len(p.rec_xyz)))
+    return p, desc
+
+
+def _cpu_sample(p, target_s=15.0, max_steps=64):
+    """Time the FP64 oracle on the top z-slab of the workload (the part that
+    holds the source and receivers), sized to ~target_s seconds of host work."""
+    import oracle
+    ncores = os.cpu_count() or 1
+    oracle.set_threads(ncores)
+    nzs = min(p.n[2], 64)
+    m = np.ascontiguousarray(p.m[:, :, :nzs], dtype=np.float64)
+    damp = np.ascontiguousarray(p.damp[:, :, :nzs], dtype=np.float64)
+    h = [float(np.float32(v)) for v in p.h]
+    dt = float(np.float32(p.dt))
+    q = p.src_q.astype(np.float64)
+
+    def run(steps):
+        t0 = time.perf_counter()
+        oracle.forward(m, damp, h, dt, steps, p.space_order, p.src_xyz.astype(np.float64),
+                       q[:steps], p.rec_xyz.astype(np.float64))
+        return time.perf_counter() - t0
+
+    t2 = run(2)
+    steps = int(max(2, min(max_steps, target_s / max(t2 / 2, 1e-6))))
+    dt_run = run(steps)
+    pts = m.size * steps
+    return {"value": pts / dt_run / 1e9, "unit": "GPts/s", "cores": oracle.max_threads(),
+            "kind": "oracle", "seconds": dt_run,
+            "sample": "FP64 oracle forward (untiled loop, OpenMP) on the top %d-plane z-slab "
+                      "%dx%dx%d of the workload for %d steps" % (nzs, p.n[0], p.n[1], nzs, steps)}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    p, desc = _workload(args)
+    import oracle
+    ncores = os.cpu_count() or 1
+    oracle.set_threads(ncores)
+    nzs = min(p.n[2], 32)
+    m = np.ascontiguousarray(p.m[:, :, :nzs], dtype=np.float64)
+    damp = np.ascontiguousarray(p.damp[:, :, :nzs], dtype=np.float64)
+    h = [float(np.float32(v)) for v in p.h]
+    dt = float(np.float32(p.dt))
+    q = p.src_q.astype(np.float64)
+    steps = 2
+
+    def one():
+        t0 = time.perf_counter()
+        oracle.forward(m, damp, h, dt, steps, p.space_order, p.src_xyz.astype(np.float64),
+                       q[:steps], p.rec_xyz.astype(np.float64))
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        one()
+    times = [one() for _ in range(args.steps)]
+    tot = sum(times)
+    val = m.size * steps * args.steps / tot / 1e9
+    sample = ("FP64 oracle forward (untiled, OpenMP) on the top %d-plane z-slab %dx%dx%d for %d "
+              "steps per bench step" % (nzs, p.n[0], p.n[1], nzs, steps))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GPts/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc, "sample": sample},
+        "cpu_baseline": {"value": val, "unit": "GPts/s", "cores": oracle.max_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "GPts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def _timed(fn, steps, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    extra = [fn() for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), extra
+
+
+def run_ours(args):
+    import torch
+    from paper_1806_08299_gb300 import inputs, wave
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    p, desc = _workload(args)
+    grid = wave.Grid(p.n, p.h, p.dt, p.nt, p.space_order)
+    tm = torch.from_numpy(p.m).to(dev)
+    td = torch.from_numpy(p.damp).to(dev)
+    tq = torch.from_numpy(p.src_q).to(dev)
+    stream = torch.cuda.current_stream()
+    nsrc, nrec = len(p.src_xyz), len(p.rec_xyz)
+    ws = torch.empty(wave.workspace_bytes(grid, wave.WAVE_OP_FWD, nsrc, nrec), dtype=torch.uint8,
+                     device=dev)
+    pts = float(np.prod(p.n)) * p.nt
+
+    def fwd(tune):
+        d, _, _, _ = wave.fwd(grid, tm, td, p.src_xyz, tq, p.rec_xyz, tuning=tune, workspace=ws)
+        return wave.sweep_stats() if tune.flags & wave.WAVE_TIME_SWEEPS else None
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # autotune once (outside any timed region), then fix the plan
+    if args.time_tile:
+        tiled = wave.Tuning(time_tile=args.time_tile)
+    else:
+        fwd(wave.Tuning(time_tile=0))
+        plan = wave.describe_plan(grid, wave.Tuning(time_tile=0))
+        tiled = wave.Tuning(time_tile=plan["time_tile"], tile_y=plan["tile_y"],
+                            tile_x=plan["tile_x"])
+    plan = wave.describe_plan(grid, tiled)
+    prof = wave.Tuning(tiled.time_tile, tiled.tile_y, tiled.tile_x, wave.WAVE_TIME_SWEEPS)
+    untiled = wave.Tuning(time_tile=1)
+
+    # --- device-timed, inputs resident: tiled sweep (headline) -------------
+    for _ in range(args.warmup):
+        fwd(prof)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    ms, stats = _timed(lambda: fwd(prof), args.steps, stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = max_over_ranks(ms)
+    value = world * pts * args.steps / (ms / 1e3) / 1e9
+    sweep_ms = sum(s[0] for s in stats)
+    launches = sum(s[1] for s in stats)
+
+    # --- untiled sweep, same workload --------------------------------------
+    for _ in range(max(1, args.warmup)):
+        fwd(untiled)
+    barrier()
+    ms_u, _ = _timed(lambda: fwd(untiled), args.steps, stream)
+    ms_u = max_over_ranks(ms_u)
+    untiled_gpts = world * pts * args.steps / (ms_u / 1e3) / 1e9
+
+    # --- end to end through the C ABI with host buffers --------------------
+    hm = torch.from_numpy(p.m).pin_memory()
+    hd = torch.from_numpy(p.damp).pin_memory()
+    hq = torch.from_numpy(p.src_q).pin_memory()
+    hrec = torch.empty((p.nt, nrec), dtype=torch.float32).pin_memory()
+    dm, dd, dq = torch.empty_like(tm), torch.empty_like(td), torch.empty_like(tq)
+
+    def e2e_step():
+        dm.copy_(hm, non_blocking=True)
+        dd.copy_(hd, non_blocking=True)
+        dq.copy_(hq, non_blocking=True)
+        d, _, _, _ = wave.fwd(grid, dm, dd, p.src_xyz, dq, p.rec_xyz, tuning=tiled, workspace=ws)
+        hrec.copy_(d, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    ms_e, _ = _timed(e2e_step, args.steps, stream)
+    ms_e = max_over_ranks(ms_e)
+    h2d = (hm.numel() + hd.numel() + hq.numel()) * 4
+    d2h = hrec.numel() * 4
+
+    # --- FWI gradient per shot (256^3 so 8, 2000 steps, k = 50) -------------
+    fwi = None
+    if args.fwi and world == 1:
+        fwi = _fwi_gradient(dev, inputs, wave, args)
+
+    # --- roofline of the sweep kernel --------------------------------------
+    hbm, peak_kind = _peaks()
+    T = plan["time_tile"]
+    bytes_per_pt = 24 if T >= 2 else 20  # read u^n, u^{n-1}, B, C; write 2 levels (1 if untiled)
+    alg_bytes = float(np.prod(p.n)) * bytes_per_pt
+    avg_launch_ms = sweep_ms / max(launches, 1)
+    achieved = alg_bytes / (avg_launch_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": args.traffic, "peak_kind": peak_kind,
+                "kernel": "sweep_kernel<R=%d,T=%d>" % (p.space_order // 2, T),
+                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_sample(p)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GPts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": desc, "l2": "inputs larger than L2 (512 MiB per field)",
+                       "time_tile": T, "tile_y": plan["tile_y"], "tile_z": plan["tile_z"],
+                       "tile_x": plan["tile_x"], "untiled_gpts": untiled_gpts,
+                       "tiled_over_untiled": value / untiled_gpts,
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "e2e": {"value": world * pts * args.steps / (ms_e / 1e3) / 1e9, "unit": "GPts/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": roofline,
+            "gpu_launches": args.steps * (launches // max(args.steps, 1) + 2),
+            "clocks": clocks,
+        }
+        if fwi is not None:
+            line["fwi_gradient"] = fwi
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _fwi_gradient(dev, inputs, wave, args):
+    """Forward with checkpoints + recompute + adjoint + imaging condition for
+    one 256^3 so-8 shot of 2000 steps, k = 50 (s per shot)."""
+    import torch
+    p = inputs.c4(nt=args.fwi_nt, true_model=False)
+    grid = wave.Grid(p.n, p.h, p.dt, p.nt, p.space_order)
+    tm = torch.from_numpy(p.m).to(dev)
+    td = torch.from_numpy(p.damp).to(dev)
+    tq = torch.from_numpy(p.src_q).to(dev)
+    k = 50
+    tune = wave.Tuning(time_tile=0)
+
+    def shot():
+        d, _, ckpt, _ = wave.fwd(grid, tm, td, p.src_xyz, tq, p.rec_xyz, tuning=tune, ckpt_every=k)
+        g, _ = wave.grad(grid, tm, td, p.src_xyz, tq, p.rec_xyz, d, ckpt, k, tuning=tune)
+        return g
+
+    shot()
+    torch.cuda.synchronize()
+    ms, _ = _timed(shot, 1, torch.cuda.current_stream())
+    plan = wave.describe_plan(grid, tune)
+    return {"s_per_shot": ms / 1e3, "workload": "c4: 256^3 so8, %d steps, checkpoints every %d, "
+            "forward + recompute + adjoint + imaging condition" % (p.nt, k),
+            "time_tile": plan["time_tile"],
+            "gpts_equiv": 3 * float(np.prod(p.n)) * p.nt / (ms / 1e3) / 1e9}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2"])
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--nt", type=int, default=0)
+    ap.add_argument("--time-tile", type=int, default=0)
+    ap.add_argument("--no-fwi", dest="fwi", action="store_false")
+    ap.add_argument("--fwi-nt", type=int, default=2000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per sweep launch, when captured for this kernel")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

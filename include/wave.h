@@ -1,0 +1,198 @@
+/*
+ * wave.h -- C ABI of the GB300 time-tiled acoustic wave library (libwavetile).
+ *
+ * The library solves the isotropic acoustic wave equation
+ *
+ *     m u_tt + damp u_t - lap u = f            (m = 1/v^2, km, s units)
+ *
+ * on a 3D grid with leapfrog time stepping and an order-`space_order` central
+ * Laplacian (radius r = space_order/2), point sources injected and receivers
+ * interpolated every step.  The paper it follows (N. Sim, "Optimising finite-
+ * difference methods for PDEs through parameterised time-tiling in Devito",
+ * 2018) tiles this sweep in time: Sec. 4.1 skews space by the stencil radius
+ * per time step, Sec. 4.2 tiles the skewed space-time, Sec. 5.8 applies it to
+ * the acoustic operator at space orders 4..16.  The paper states no
+ * discretisation; the one implemented here is:
+ *
+ *   u^{n+1} = u^n + B (u^n - u^{n-1}) + C (L u^n + f^n)
+ *     B = (m - eta)/(m + eta),  C = dt^2/(m + eta),  eta = damp dt / 2
+ *   which is the centred-damping leapfrog  m(u^{n+1}-2u^n+u^{n-1})/dt^2
+ *   + damp(u^{n+1}-u^{n-1})/(2 dt) - L u^n = f^n  solved for u^{n+1};
+ *   L u = sum_a h_a^-2 [c_0 u + sum_{k=1..r} c_k (u(+k e_a) + u(-k e_a))],
+ *   u = 0 outside the grid, u^0 = u^{-1} = 0;
+ *   f^n[p] = sum_s w_{s,p} q_s^n (trilinear weights over the 8 corners of the
+ *   cell holding source s, no 1/h^3 factor);
+ *   d^n[r] = sum_p w_{r,p} u^{n+1}[p]   (receivers record the new level).
+ *
+ * Conventions for every entry point
+ *   - Arrays are float32, C order [nx][ny][nz] (z contiguous), as in the
+ *     paper's generated code (Sec. 3.2.1).  Traces are [nt][npts].
+ *   - "device" pointers are CUDA device memory owned by the caller; "host"
+ *     pointers are ordinary host memory, read during the call only.
+ *   - The library never allocates device memory.  The caller passes a device
+ *     workspace of at least wave_workspace_bytes(...) bytes (256-byte aligned)
+ *     that the call may overwrite; it must not be shared by calls that can
+ *     overlap on the GPU.
+ *   - Calls enqueue work on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and return without waiting, except the first call for a new
+ *     problem shape with tuning.time_tile == 0, which times candidate tilings
+ *     on `stream` before it returns.  wave_status() waits for the stream and
+ *     reports device-side errors recorded in the workspace.
+ *   - Return value: WAVE_OK or a negative WAVE_E* code; nothing is enqueued
+ *     when an argument check fails.  No C++ exception crosses the ABI.
+ */
+#ifndef WAVETILE_WAVE_H
+#define WAVETILE_WAVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WAVE_OK 0
+#define WAVE_EINVAL (-1)      /* bad argument: space order, shape, pointer, point outside grid */
+#define WAVE_EUNSTABLE (-2)   /* dt above the von Neumann limit (see wave_cfl_dt)             */
+#define WAVE_ECUDA (-3)       /* a CUDA runtime call failed                                  */
+#define WAVE_ETIMEOUT (-4)    /* a bounded device-side wait gave up                           */
+#define WAVE_ENOSPACE (-5)    /* workspace smaller than wave_workspace_bytes()                */
+#define WAVE_EUNSUPPORTED (-6)/* requested tiling not compiled into this library              */
+
+/* wave_workspace_bytes `op` values */
+#define WAVE_OP_FWD 0
+#define WAVE_OP_ADJ 1
+#define WAVE_OP_GRAD 2
+
+/* wave_tuning.flags */
+#define WAVE_ALLOW_UNSTABLE 1 /* skip the dt <= CFL check                              */
+#define WAVE_TIME_SWEEPS 2    /* record CUDA events around the sweep launches of the call
+                                 (read back with wave_sweep_stats)                       */
+
+typedef struct wave_grid {
+    int32_t n[3];        /* nx, ny, nz >= space_order + 1 each                     */
+    float h[3];          /* grid spacing per axis (km), > 0                          */
+    float dt;            /* time step (s), > 0                                       */
+    int32_t nt;          /* number of time steps, >= 1                               */
+    int32_t space_order; /* even, 2..16 (paper: 4, 6, 8, 12, 16, Sec. 5.8.1)         */
+} wave_grid;
+
+typedef struct wave_points {
+    int32_t npts;        /* number of points, >= 0                                   */
+    const float *xyz;    /* HOST, [npts][3] physical coordinates (km) inside
+                            [0, (n_a - 1) h_a] on every axis                         */
+} wave_points;
+
+/* Sweep configuration.  Zero fields mean "choose automatically".
+ *   time_tile : 0 = autotune, 1 = untiled sweep (one step per launch),
+ *               T >= 2 = T steps per launch (time-tile depth, Sec. 4.2).
+ *   tile_y    : output rows per block (0 = the default of the chosen variant).
+ *   tile_x    : x-chunk length streamed by one block (0 = default).
+ *   flags     : WAVE_ALLOW_UNSTABLE. */
+typedef struct wave_tuning {
+    int32_t time_tile;
+    int32_t tile_y;
+    int32_t tile_x;
+    int32_t flags;
+} wave_tuning;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t wave_version(void);
+
+/* Message for a WAVE_* code; never NULL, static storage. */
+const char *wave_strerror(int32_t code);
+
+/* Stencil coefficients c_0..c_r (unit spacing) of the order-`space_order`
+ * central second derivative, c_k = 2(-1)^(k+1)(r!)^2 / (k^2 (r-k)! (r+k)!),
+ * c_0 = -2 sum_{k>=1} c_k.  The paper derives its stencils from Taylor's
+ * theorem (Sec. 2.1).  c_out (HOST) receives space_order/2 + 1 doubles.
+ * Returns WAVE_OK or WAVE_EINVAL. */
+int32_t wave_fd_coefficients(int32_t space_order, double *c_out);
+
+/* Largest stable dt of the undamped scheme (von Neumann, periodic):
+ *   dt = 2 / (v_max sqrt(sum_a S / h_a^2)),  S = |c_0 + 2 sum_k (-1)^k c_k|.
+ * Returns a negative value on bad arguments. */
+double wave_cfl_dt(int32_t space_order, const float *h /* HOST [3] */, float v_max);
+
+/* Device workspace needed by one call of operation `op` (WAVE_OP_*).
+ * nsrc/nrec are the source and receiver counts of that call; ckpt_every is
+ * the checkpoint interval k for WAVE_OP_GRAD (and ignored otherwise).
+ * tuning may be NULL.  Returns 0 for invalid arguments. */
+size_t wave_workspace_bytes(const wave_grid *g, int32_t op, int32_t nsrc, int32_t nrec,
+                            int32_t ckpt_every, const wave_tuning *tuning);
+
+/* Size in bytes of the checkpoint buffer that wave_fwd fills and wave_grad
+ * reads: ceil(nt / ckpt_every) states of two levels each, in the library's
+ * internal (z-padded) layout.  Returns 0 on invalid arguments. */
+size_t wave_ckpt_bytes(const wave_grid *g, int32_t ckpt_every);
+
+/* Forward modelling (Sec. 5.8: the acoustic operator, with the source and
+ * receiver loops of Sec. 4.5.1 fused into the time-tiled sweep).
+ *   m, damp      device [nx][ny][nz]; m > 0 (s^2/km^2), damp >= 0 (1/s)
+ *   src          host points; src_traces device [nt][nsrc] (q_s^n), may be
+ *                NULL when nsrc == 0
+ *   rec          host points; rec_traces device [nt][nrec] out (d^n), may be
+ *                NULL when nrec == 0
+ *   u_last       device [2][nx][ny][nz] out (u^nt, u^{nt-1}) or NULL
+ *   ckpt         device, wave_ckpt_bytes(g, ckpt_every) bytes out, or NULL;
+ *                state c holds (u^{c k}, u^{c k - 1})
+ *   ckpt_every   k >= 1 when ckpt != NULL
+ *   tuning       NULL = autotune
+ *   ws, ws_bytes device workspace (WAVE_OP_FWD)
+ *   stream       cudaStream_t
+ * The time-tiled and untiled sweeps give bitwise identical results. */
+int32_t wave_fwd(const wave_grid *g, const float *m, const float *damp,
+                 const wave_points *src, const float *src_traces,
+                 const wave_points *rec, float *rec_traces,
+                 float *u_last, float *ckpt, int32_t ckpt_every,
+                 const wave_tuning *tuning, void *ws, size_t ws_bytes, void *stream);
+
+/* Adjoint modelling: the transpose of wave_fwd's source-to-receiver map.
+ * With a residual res = dJ/dd (device [nt][nrec]) it returns
+ *   src_adj  device [nt][nsrc] out: dJ/dq_s^n = sum_p w_{s,p} nu^{n+1}[p]
+ *   v_last   device [2][nx][ny][nz] out (nu^1, nu^2) or NULL,
+ * where nu^k = C lambda^k and lambda^k = dJ/du^k.  nu obeys the forward
+ * scheme run backwards in time with res injected at the receivers, which is
+ * how it is computed (the same time-tiled sweep).  Workspace: WAVE_OP_ADJ. */
+int32_t wave_adj(const wave_grid *g, const float *m, const float *damp,
+                 const wave_points *rec, const float *rec_resid,
+                 const wave_points *src, float *src_adj, float *v_last,
+                 const wave_tuning *tuning, void *ws, size_t ws_bytes, void *stream);
+
+/* Gradient of J with respect to m for a fixed residual res = dJ/dd:
+ *   grad = dJ/dm = -(1/dt^2) sum_{n=0}^{nt-1} nu^{n+1} (u^{n+1} - 2u^n + u^{n-1})
+ * (device [nx][ny][nz] out, overwritten).  u comes from the checkpoints of a
+ * previous wave_fwd call with the same grid, m, damp, sources and ckpt_every:
+ * each segment of ckpt_every steps is recomputed from its checkpoint with the
+ * second difference stored per step, then the adjoint sweep of that segment
+ * accumulates the imaging condition.  Workspace: WAVE_OP_GRAD. */
+int32_t wave_grad(const wave_grid *g, const float *m, const float *damp,
+                  const wave_points *src, const float *src_traces,
+                  const wave_points *rec, const float *rec_resid,
+                  const float *ckpt, int32_t ckpt_every, float *grad,
+                  const wave_tuning *tuning, void *ws, size_t ws_bytes, void *stream);
+
+/* Wait for `stream`, then read the device status word that kernels of the
+ * last call using workspace `ws` may have set.  Returns WAVE_OK,
+ * WAVE_ETIMEOUT or WAVE_ECUDA. */
+int32_t wave_status(const void *ws, void *stream);
+
+/* Timing of the sweep launches of the last wave_fwd / wave_adj / wave_grad
+ * call made on this host thread with WAVE_TIME_SWEEPS set: events recorded on
+ * that call's stream just before its first sweep launch and just after its
+ * last.  Waits for the second event.  ms (HOST) receives the elapsed time,
+ * launches (HOST) the number of sweep kernel launches and steps the number of
+ * time steps they advanced.  Returns WAVE_OK, WAVE_EINVAL (no such call) or
+ * WAVE_ECUDA. */
+int32_t wave_sweep_stats(float *ms, int32_t *launches, int32_t *steps);
+
+/* Sweep variant the library would run for grid g with `tuning`
+ * (after autotuning if tuning->time_tile == 0 and it already ran):
+ * out[0..4] = time_tile, tile_y, tile_x, variant index, vector width.
+ * Returns WAVE_OK or a WAVE_E* code. */
+int32_t wave_describe_plan(const wave_grid *g, const wave_tuning *tuning, int32_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WAVETILE_WAVE_H */

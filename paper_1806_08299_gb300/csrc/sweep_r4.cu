@@ -1,0 +1,5 @@
+// sweep_r4.cu -- sweep variants of stencil radius 4 (space order 8).
+#include "variants.h"
+#include "wave_internal.h"
+
+WAVE_DEFINE_RADIUS(4)

@@ -1,0 +1,5 @@
+// sweep_r7.cu -- sweep variants of stencil radius 7 (space order 14).
+#include "variants.h"
+#include "wave_internal.h"
+
+WAVE_DEFINE_RADIUS(7)

@@ -1,0 +1,971 @@
+// wave_api.cu -- host runtime behind the C ABI in include/wave.h.
+//
+// Argument checks, stencil coefficients, sparse point tables, workspace
+// layout, launch sequencing (time tiles, checkpoints, recompute segments),
+// the autotuner and the device status word.  All device memory comes from
+// the caller's workspace; nothing here allocates on the device.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "wave.h"
+#include "wave_internal.h"
+
+namespace {
+
+using wt::PointTable;
+using wt::Stencil;
+using wt::SweepArgs;
+using wt::SweepVariant;
+
+constexpr size_t kAlign = 256;
+constexpr int kStatusWords = 64;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+#define CK(call)                                         \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return WAVE_ECUDA;        \
+    } while (0)
+
+struct Dims {
+    int nx, ny, nz, nzp;
+    long long npad;  // nx * ny * nzp
+    long long n;     // nx * ny * nz
+};
+
+int check_grid(const wave_grid *g, Dims *d)
+{
+    if (g == nullptr) return WAVE_EINVAL;
+    const int so = g->space_order;
+    if (so < 2 || so > 16 || so % 2) return WAVE_EINVAL;
+    for (int a = 0; a < 3; ++a) {
+        if (g->n[a] < so + 1 || g->n[a] > (1 << 20)) return WAVE_EINVAL;
+        if (!(g->h[a] > 0.f) || !std::isfinite(g->h[a])) return WAVE_EINVAL;
+    }
+    if (!(g->dt > 0.f) || !std::isfinite(g->dt) || g->nt < 1) return WAVE_EINVAL;
+    d->nx = g->n[0];
+    d->ny = g->n[1];
+    d->nz = g->n[2];
+    d->nzp = (g->n[2] + 3) / 4 * 4;
+    d->npad = (long long)d->nx * d->ny * d->nzp;
+    d->n = (long long)d->nx * d->ny * d->nz;
+    if (d->npad > (1LL << 36)) return WAVE_EINVAL;
+    return WAVE_OK;
+}
+
+// c_k = 2 (-1)^(k+1) (r!)^2 / (k^2 (r-k)! (r+k)!) by the product form
+// (r!)^2/((r-k)!(r+k)!) = prod_{j=1..k} (r-k+j)/(r+j), exact to double rounding.
+void fd_coeffs(int so, double *c)
+{
+    const int r = so / 2;
+    double sum = 0.0;
+    for (int k = 1; k <= r; ++k) {
+        double ratio = 1.0;
+        for (int j = 1; j <= k; ++j) ratio *= (double)(r - k + j) / (double)(r + j);
+        const double ck = ((k % 2) ? 2.0 : -2.0) * ratio / ((double)k * k);
+        c[k] = ck;
+        sum += ck;
+    }
+    c[0] = -2.0 * sum;
+}
+
+double symbol_at_pi(int so)
+{
+    double c[wt::kMaxR + 1];
+    fd_coeffs(so, c);
+    double s = c[0];
+    for (int k = 1; k <= so / 2; ++k) s += 2.0 * ((k % 2) ? -c[k] : c[k]);
+    return std::fabs(s);
+}
+
+Stencil make_stencil(const wave_grid *g)
+{
+    double c[wt::kMaxR + 1];
+    fd_coeffs(g->space_order, c);
+    Stencil st;
+    std::memset(&st, 0, sizeof(st));
+    const double ih[3] = {1.0 / ((double)g->h[0] * g->h[0]), 1.0 / ((double)g->h[1] * g->h[1]),
+                          1.0 / ((double)g->h[2] * g->h[2])};
+    st.cc = (float)((c[0] * ih[0] + c[0] * ih[1]) + c[0] * ih[2]);
+    for (int k = 1; k <= g->space_order / 2; ++k) {
+        st.cx[k] = (float)(c[k] * ih[0]);
+        st.cy[k] = (float)(c[k] * ih[1]);
+        st.cz[k] = (float)(c[k] * ih[2]);
+    }
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// Sparse point tables
+// ---------------------------------------------------------------------------
+
+struct HostTable {
+    std::vector<int> plane_start;  // nx + 1
+    std::vector<int4> pts;         // sorted (x, y, z) -> (y, z, begin, end)
+    std::vector<int> item;
+    std::vector<float> w;          // injection weights per item
+    std::vector<float> wts;        // record: [npts][8] interpolation weights
+};
+
+// Trilinear corners and weights of one point; corner c = 4 dx + 2 dy + dz,
+// cell = floor(x/h) clamped to [0, n-2].  Returns false if outside the grid.
+bool trilinear(const Dims &d, const float *h, const float *xyz, long long corner[8],
+               float w[8], int cx[8], int cy[8], int cz[8])
+{
+    const int n[3] = {d.nx, d.ny, d.nz};
+    int cell[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        const double s = (double)xyz[a] / (double)h[a];
+        if (!std::isfinite(s) || s < -1e-4 || s > (double)(n[a] - 1) + 1e-4) return false;
+        int i = (int)std::floor(s);
+        if (i < 0) i = 0;
+        if (i > n[a] - 2) i = n[a] - 2;
+        cell[a] = i;
+        f[a] = s - (double)i;
+    }
+    for (int c = 0; c < 8; ++c) {
+        const int dx = (c >> 2) & 1, dy = (c >> 1) & 1, dz = c & 1;
+        const double wx = dx ? f[0] : 1.0 - f[0];
+        const double wy = dy ? f[1] : 1.0 - f[1];
+        const double wz = dz ? f[2] : 1.0 - f[2];
+        cx[c] = cell[0] + dx;
+        cy[c] = cell[1] + dy;
+        cz[c] = cell[2] + dz;
+        corner[c] = ((long long)cx[c] * d.ny + cy[c]) * d.nz + cz[c];
+        w[c] = (float)(wx * wy * wz);
+    }
+    return true;
+}
+
+// Build a table of unique grid points touched by `pts`.  For injection
+// (record == false) each unique point lists (point index, weight) in
+// ascending point order; for recording it lists the corner slots 8 r + c.
+int build_table(const Dims &d, const float *h, const wave_points *p, bool record, HostTable *t)
+{
+    const int np = p ? p->npts : 0;
+    t->plane_start.assign(d.nx + 1, 0);
+    t->pts.clear();
+    t->item.clear();
+    t->w.clear();
+    t->wts.assign((size_t)8 * np, 0.f);
+    if (np == 0) return WAVE_OK;
+    if (p->xyz == nullptr) return WAVE_EINVAL;
+    struct Entry {
+        int x, y, z, idx;
+        float w;
+    };
+    std::vector<Entry> ent;
+    ent.reserve((size_t)8 * np);
+    for (int i = 0; i < np; ++i) {
+        long long corner[8];
+        float w[8];
+        int cx[8], cy[8], cz[8];
+        if (!trilinear(d, h, p->xyz + 3 * i, corner, w, cx, cy, cz)) return WAVE_EINVAL;
+        for (int c = 0; c < 8; ++c) {
+            ent.push_back({cx[c], cy[c], cz[c], record ? 8 * i + c : i, w[c]});
+            t->wts[(size_t)8 * i + c] = w[c];
+        }
+    }
+    // stable sort keeps ascending point index among equal grid points
+    std::stable_sort(ent.begin(), ent.end(), [](const Entry &a, const Entry &b) {
+        return std::tie(a.x, a.y, a.z) < std::tie(b.x, b.y, b.z);
+    });
+    for (size_t i = 0; i < ent.size();) {
+        size_t j = i;
+        const int begin = (int)t->item.size();
+        while (j < ent.size() && ent[j].x == ent[i].x && ent[j].y == ent[i].y && ent[j].z == ent[i].z) {
+            t->item.push_back(ent[j].idx);
+            t->w.push_back(ent[j].w);
+            ++j;
+        }
+        t->pts.push_back(make_int4(ent[i].y, ent[i].z, begin, (int)t->item.size()));
+        t->plane_start[ent[i].x + 1]++;
+        i = j;
+    }
+    for (int x = 0; x < d.nx; ++x) t->plane_start[x + 1] += t->plane_start[x];
+    return WAVE_OK;
+}
+
+// Device copy of a table inside the workspace.
+struct DevTable {
+    int *plane_start = nullptr;
+    int4 *pts = nullptr;
+    int *item = nullptr;
+    float *w = nullptr;
+    float *wts = nullptr;
+    int npts = 0;
+    PointTable view() const { return PointTable{npts ? plane_start : nullptr, pts, item, w}; }
+};
+
+// ---------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------
+
+struct Carver {
+    char *base;
+    size_t off = 0, cap;
+    bool dry;
+    Carver(void *b, size_t c, bool d) : base((char *)b), cap(c), dry(d) {}
+    template <class T>
+    T *take(size_t count)
+    {
+        const size_t bytes = align_up(sizeof(T) * std::max<size_t>(count, 1));
+        T *p = dry ? nullptr : (T *)(base + off);
+        off += bytes;
+        return p;
+    }
+};
+
+size_t table_bytes(const Dims &d, int np)
+{
+    Carver c(nullptr, 0, true);
+    c.take<int>(d.nx + 1);
+    c.take<int4>((size_t)8 * np);
+    c.take<int>((size_t)8 * np);
+    c.take<float>((size_t)8 * np);
+    c.take<float>((size_t)8 * np);
+    return c.off;
+}
+
+void carve_table(Carver &c, const Dims &d, int np, DevTable *t)
+{
+    t->plane_start = c.take<int>(d.nx + 1);
+    t->pts = c.take<int4>((size_t)8 * np);
+    t->item = c.take<int>((size_t)8 * np);
+    t->w = c.take<float>((size_t)8 * np);
+    t->wts = c.take<float>((size_t)8 * np);
+    t->npts = np;
+}
+
+int upload_table(const HostTable &h, const DevTable &t, cudaStream_t s)
+{
+    if (t.npts == 0) return WAVE_OK;
+    CK(cudaMemcpyAsync(t.plane_start, h.plane_start.data(), sizeof(int) * h.plane_start.size(),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(t.pts, h.pts.data(), sizeof(int4) * h.pts.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(t.item, h.item.data(), sizeof(int) * h.item.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(t.w, h.w.data(), sizeof(float) * h.w.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(t.wts, h.wts.data(), sizeof(float) * h.wts.size(), cudaMemcpyHostToDevice, s));
+    return WAVE_OK;
+}
+
+struct Layout {
+    int *status = nullptr;
+    float *cB = nullptr, *cC = nullptr, *cE = nullptr;
+    float *U[4] = {nullptr, nullptr, nullptr, nullptr};
+    float *V[4] = {nullptr, nullptr, nullptr, nullptr};
+    float *G = nullptr;
+    float *store = nullptr;
+    DevTable inj, rec, inj2;
+    float *corner = nullptr;
+    size_t bytes = 0;
+};
+
+// op FWD: inj = sources, rec = receivers, corner [nt][8 nrec]
+// op ADJ: inj = receivers, rec = sources, corner [nt][8 nsrc]
+// op GRAD: inj = sources (recompute), inj2 = receivers (adjoint), V, G, store [k]
+Layout carve(void *ws, size_t cap, bool dry, const Dims &d, int op, int nsrc, int nrec, int nt,
+             int ckpt_every)
+{
+    Carver c(ws, cap, dry);
+    Layout L;
+    L.status = c.take<int>(kStatusWords);
+    L.cB = c.take<float>(d.npad);
+    L.cC = c.take<float>(d.npad);
+    if (op == WAVE_OP_GRAD) L.cE = c.take<float>(d.npad);
+    for (int i = 0; i < 4; ++i) L.U[i] = c.take<float>(d.npad);
+    if (op == WAVE_OP_GRAD) {
+        for (int i = 0; i < 4; ++i) L.V[i] = c.take<float>(d.npad);
+        L.G = c.take<float>(d.npad);
+        L.store = c.take<float>((size_t)d.npad * (size_t)std::max(1, std::min(ckpt_every, nt)));
+        carve_table(c, d, nsrc, &L.inj);
+        carve_table(c, d, nrec, &L.inj2);
+    } else {
+        const int ni = op == WAVE_OP_FWD ? nsrc : nrec;
+        const int nr = op == WAVE_OP_FWD ? nrec : nsrc;
+        carve_table(c, d, ni, &L.inj);
+        carve_table(c, d, nr, &L.rec);
+        L.corner = c.take<float>((size_t)nt * 8 * std::max(nr, 0));
+    }
+    L.bytes = c.off;
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// Variants, plans and the autotuner
+// ---------------------------------------------------------------------------
+
+int variants_for(int R, const SweepVariant **out)
+{
+    switch (R) {
+    case 1: return wt::sweep_variants_r1(out);
+    case 2: return wt::sweep_variants_r2(out);
+    case 3: return wt::sweep_variants_r3(out);
+    case 4: return wt::sweep_variants_r4(out);
+    case 5: return wt::sweep_variants_r5(out);
+    case 6: return wt::sweep_variants_r6(out);
+    case 7: return wt::sweep_variants_r7(out);
+    case 8: return wt::sweep_variants_r8(out);
+    default: *out = nullptr; return 0;
+    }
+}
+
+int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 152;
+    }
+    return n;
+}
+
+struct Plan {
+    const SweepVariant *v = nullptr;
+    int chunk = 0;
+};
+
+int tiles(int n, int b) { return (n + b - 1) / b; }
+
+// Default x-chunk: the split of x that best fills whole waves of resident
+// blocks, discounting the 2RT warm-up planes each chunk streams.
+int default_chunk(const Dims &d, const SweepVariant *v)
+{
+    cudaFuncSetAttribute(v->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->smem);
+    int occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(&occ, v->func, v->threads, v->smem,
+                                                               cudaOccupancyDefault) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    const long long per_wave = (long long)sm_count() * occ;
+    const long long cols = (long long)tiles(d.nzp, v->BZ) * tiles(d.ny, v->BY);
+    const int warm = 2 * v->R * v->T;
+    int best = d.nx;
+    double best_eff = -1.0;
+    for (int nch = 1; nch <= 64; ++nch) {
+        const int chunk = tiles(d.nx, nch);
+        if (nch > 1 && chunk < 2 * warm) break;
+        const long long blocks = cols * tiles(d.nx, chunk);
+        const long long waves = (blocks + per_wave - 1) / per_wave;
+        const double eff = (double)blocks / (double)(waves * per_wave) * chunk / (double)(chunk + warm);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = chunk;
+        }
+    }
+    return best;
+}
+
+// Pick the variant for radius R with time tile T (and tile_y if given).
+const SweepVariant *find_variant(int R, int T, int tile_y)
+{
+    const SweepVariant *vs;
+    const int nv = variants_for(R, &vs);
+    for (int i = 0; i < nv; ++i)
+        if (vs[i].T == T && (tile_y == 0 || vs[i].BY == tile_y)) return &vs[i];
+    return nullptr;
+}
+
+// Largest-T variant of radius R with T <= limit (T = 1 always exists).
+const SweepVariant *fallback_variant(int R, int limit)
+{
+    const SweepVariant *vs;
+    const int nv = variants_for(R, &vs);
+    const SweepVariant *best = nullptr;
+    for (int i = 0; i < nv; ++i)
+        if (vs[i].T <= limit && (best == nullptr || vs[i].T > best->T)) best = &vs[i];
+    return best;
+}
+
+struct TuneKey {
+    int nx, ny, nz, so, dev;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(nx, ny, nz, so, dev) < std::tie(o.nx, o.ny, o.nz, o.so, o.dev);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, Plan> g_tune_cache;
+
+TuneKey tune_key(const Dims &d, int so)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return TuneKey{d.nx, d.ny, d.nz, so, dev};
+}
+
+// ---------------------------------------------------------------------------
+// The sweep driver
+// ---------------------------------------------------------------------------
+
+// What one run of consecutive steps injects, records and stores.  Every row
+// index is "base + dir * j" for local step j of the run (j = 0 first).
+struct Job {
+    Dims d;
+    Stencil st;
+    const float *cB, *cC, *cE;
+    PointTable inj{};
+    const float *q = nullptr;
+    int nq = 0, q_base = 0, q_dir = 1;
+    PointTable rec{};
+    float *corner = nullptr;
+    int nslot = 0, c_base = 0, c_dir = 1;
+    float *dstore = nullptr;
+    long long d_base = 0;
+    int d_dir = 1;
+    const float *dload = nullptr;
+    long long l_base = 0;
+    int l_dir = 1;
+    float *gacc = nullptr;
+};
+
+// Events around the sweep launches of the last timed call on this thread.
+struct SweepProf {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int launches = 0, steps = 0;
+    bool valid = false, active = false;
+};
+thread_local SweepProf g_prof;
+
+int prof_begin(const wave_tuning *t, cudaStream_t s)
+{
+    g_prof.active = t != nullptr && (t->flags & WAVE_TIME_SWEEPS);
+    if (!g_prof.active) return WAVE_OK;
+    if (g_prof.e0 == nullptr) {
+        CK(cudaEventCreate(&g_prof.e0));
+        CK(cudaEventCreate(&g_prof.e1));
+    }
+    g_prof.launches = 0;
+    g_prof.steps = 0;
+    g_prof.valid = false;
+    CK(cudaEventRecord(g_prof.e0, s));
+    return WAVE_OK;
+}
+
+int prof_end(cudaStream_t s)
+{
+    if (!g_prof.active) return WAVE_OK;
+    CK(cudaEventRecord(g_prof.e1, s));
+    g_prof.valid = true;
+    g_prof.active = false;
+    return WAVE_OK;
+}
+
+// Four buffers; (a, b) index levels n and n-1.
+struct State {
+    float *buf[4];
+    int a = 0, b = 1;
+};
+
+// Advance `st` by nsteps.  When ckpt != nullptr, state c = (u^{ck}, u^{ck-1})
+// is copied to ckpt + c * 2 * npad at every step count j0 + j that is a
+// multiple of ckpt_every (j counts from the run start, j0 = global offset).
+int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream_t stream,
+              float *ckpt = nullptr, int ckpt_every = 0, int j0 = 0)
+{
+    const Dims &d = job.d;
+    const int R = plan.v->R;
+    int j = 0;
+    while (j <= nsteps) {
+        if (ckpt != nullptr && (j0 + j) % ckpt_every == 0 && j < nsteps) {
+            float *dst = ckpt + (size_t)((j0 + j) / ckpt_every) * 2 * d.npad;
+            CK(cudaMemcpyAsync(dst, s.buf[s.a], sizeof(float) * d.npad, cudaMemcpyDeviceToDevice, stream));
+            CK(cudaMemcpyAsync(dst + d.npad, s.buf[s.b], sizeof(float) * d.npad,
+                               cudaMemcpyDeviceToDevice, stream));
+        }
+        if (j == nsteps) break;
+        int limit = nsteps - j;
+        if (ckpt != nullptr) limit = std::min(limit, ckpt_every - (j0 + j) % ckpt_every);
+        const SweepVariant *v = plan.v->T <= limit ? plan.v : fallback_variant(R, limit);
+        if (v == nullptr) return WAVE_EUNSUPPORTED;
+        const int chunk = (v == plan.v && plan.chunk > 0) ? plan.chunk : default_chunk(d, v);
+        SweepArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.nx = d.nx;
+        a.ny = d.ny;
+        a.nz = d.nzp;
+        a.sx = (long long)d.ny * d.nzp;
+        a.npad = d.npad;
+        a.u = s.buf[s.a];
+        a.um = s.buf[s.b];
+        int spare[2], ns = 0;
+        for (int i = 0; i < 4; ++i)
+            if (i != s.a && i != s.b) spare[ns++] = i;
+        if (v->T == 1) {
+            a.out_hi = s.buf[s.b];
+        } else {
+            a.out_hi = s.buf[spare[0]];
+            a.out_lo = s.buf[spare[1]];
+        }
+        a.cB = job.cB;
+        a.cC = job.cC;
+        a.cE = job.cE;
+        a.inj = job.inj;
+        a.q = job.q;
+        a.nq = job.nq;
+        a.q_row0 = job.q_base + job.q_dir * j;
+        a.q_dir = job.q_dir;
+        a.rec = job.rec;
+        a.corner = job.corner;
+        a.nslot = job.nslot;
+        a.c_row0 = job.c_base + job.c_dir * j;
+        a.c_dir = job.c_dir;
+        a.dstore = job.dstore;
+        a.d_row0 = job.d_base + (long long)job.d_dir * j;
+        a.d_dir = job.d_dir;
+        a.dload = job.dload;
+        a.l_row0 = job.l_base + (long long)job.l_dir * j;
+        a.l_dir = job.l_dir;
+        a.gacc = job.gacc;
+        a.chunk = chunk;
+        a.tiles_z = tiles(d.nzp, v->BZ);
+        a.tiles_y = tiles(d.ny, v->BY);
+        const long long nblocks = (long long)a.tiles_z * a.tiles_y * tiles(d.nx, chunk);
+        if (nblocks > 0x7fffffffLL) return WAVE_EINVAL;
+        CK(v->launch((int)nblocks, stream, a, job.st));
+        if (g_prof.active) {
+            g_prof.launches++;
+            g_prof.steps += v->T;
+        }
+        if (v->T == 1) {
+            std::swap(s.a, s.b);  // new level n+1 sits where n-1 was
+        } else {
+            s.a = spare[0];
+            s.b = spare[1];
+        }
+        j += v->T;
+    }
+    return WAVE_OK;
+}
+
+// Time candidate plans on the real coefficients (zero wavefield, no sparse
+// points) and cache the fastest: the paper's auto-tuner extended to the time
+// tile (Sec. 4.4, Sec. 5.2.2), here over (T, tile, x-chunk).
+int autotune(const Dims &d, const Stencil &st, const float *cB, const float *cC, float *const U[4],
+             int R, cudaStream_t stream, Plan *out)
+{
+    const SweepVariant *vs;
+    const int nv = variants_for(R, &vs);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    Plan bestp;
+    for (int i = 0; i < nv; ++i) {
+        const SweepVariant *v = &vs[i];
+        std::vector<int> chunks = {default_chunk(d, v)};
+        for (int c : {d.nx, (d.nx + 1) / 2, (d.nx + 3) / 4, 128, 64})
+            if (c >= 4 * v->R * v->T && c <= d.nx &&
+                std::find(chunks.begin(), chunks.end(), c) == chunks.end())
+                chunks.push_back(c);
+        for (int chunk : chunks) {
+            Plan p;
+            p.v = v;
+            p.chunk = chunk;
+            Job job;
+            job.d = d;
+            job.st = st;
+            job.cB = cB;
+            job.cC = cC;
+            job.cE = nullptr;
+            State s;
+            for (int k = 0; k < 4; ++k) s.buf[k] = U[k];
+            const int steps = 4 * v->T > 8 ? 4 * v->T : 8;
+            int rc = run_steps(job, s, v->T, p, stream);  // warm-up
+            if (rc) return rc;
+            CK(cudaEventRecord(e0, stream));
+            rc = run_steps(job, s, steps, p, stream);
+            if (rc) return rc;
+            CK(cudaEventRecord(e1, stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            const float per_step = ms / steps;
+            if (per_step < best) {
+                best = per_step;
+                bestp = p;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (bestp.v == nullptr) return WAVE_EUNSUPPORTED;
+    *out = bestp;
+    return WAVE_OK;
+}
+
+// Plan for this call: explicit tuning, or the cached / freshly tuned one.
+// `may_tune` is false for dry queries (wave_describe_plan).
+int resolve_plan(const Dims &d, const wave_grid *g, const wave_tuning *t, bool may_tune,
+                 const Stencil *st, const float *cB, const float *cC, float *const U[4],
+                 cudaStream_t stream, Plan *out)
+{
+    const int R = g->space_order / 2;
+    const int T = t ? t->time_tile : 0;
+    if (T < 0 || (t && (t->tile_x < 0 || t->tile_y < 0))) return WAVE_EINVAL;
+    if (T > 0) {
+        const SweepVariant *v = find_variant(R, T, t ? t->tile_y : 0);
+        if (v == nullptr) return WAVE_EUNSUPPORTED;
+        out->v = v;
+        out->chunk = (t && t->tile_x > 0) ? std::min(t->tile_x, d.nx) : default_chunk(d, v);
+        return WAVE_OK;
+    }
+    const TuneKey key = tune_key(d, g->space_order);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *out = it->second;
+            return WAVE_OK;
+        }
+    }
+    if (!may_tune) {
+        out->v = fallback_variant(R, 1);
+        out->chunk = default_chunk(d, out->v);
+        return WAVE_OK;
+    }
+    Plan p;
+    const int rc = autotune(d, *st, cB, cC, U, R, stream, &p);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = p;
+    *out = p;
+    return WAVE_OK;
+}
+
+int prep_model(const Dims &d, const wave_grid *g, const wave_tuning *t, const float *m,
+               const float *damp, const Layout &L, cudaStream_t stream)
+{
+    const bool allow = t && (t->flags & WAVE_ALLOW_UNSTABLE);
+    double stot = 0.0;
+    for (int a = 0; a < 3; ++a) stot += symbol_at_pi(g->space_order) / ((double)g->h[a] * g->h[a]);
+    const float stab = allow ? 0.f : (float)((double)g->dt * g->dt * stot);
+    CK(cudaMemsetAsync(L.status, 0, sizeof(int) * kStatusWords, stream));
+    CK(wt::launch_prep(m, damp, d.nx, d.ny, d.nz, d.nzp, g->dt, stab, L.cB, L.cC, L.cE, L.status,
+                       stream));
+    return WAVE_OK;
+}
+
+int check_points(const wave_points *p, bool need_data_ptr, const void *data)
+{
+    if (p == nullptr) return WAVE_OK;
+    if (p->npts < 0) return WAVE_EINVAL;
+    if (p->npts > 0 && (p->xyz == nullptr || (need_data_ptr && data == nullptr))) return WAVE_EINVAL;
+    return WAVE_OK;
+}
+
+int npts_of(const wave_points *p) { return p ? p->npts : 0; }
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+int32_t wave_version(void) { return 100; }
+
+const char *wave_strerror(int32_t code)
+{
+    switch (code) {
+    case WAVE_OK: return "ok";
+    case WAVE_EINVAL: return "invalid argument";
+    case WAVE_EUNSTABLE: return "dt above the stability limit";
+    case WAVE_ECUDA: return "CUDA runtime error";
+    case WAVE_ETIMEOUT: return "device wait timed out";
+    case WAVE_ENOSPACE: return "workspace too small";
+    case WAVE_EUNSUPPORTED: return "tiling not compiled into this library";
+    default: return "unknown error";
+    }
+}
+
+int32_t wave_fd_coefficients(int32_t space_order, double *c_out)
+{
+    if (space_order < 2 || space_order > 16 || space_order % 2 || c_out == nullptr) return WAVE_EINVAL;
+    fd_coeffs(space_order, c_out);
+    return WAVE_OK;
+}
+
+double wave_cfl_dt(int32_t space_order, const float *h, float v_max)
+{
+    if (space_order < 2 || space_order > 16 || space_order % 2 || h == nullptr || !(v_max > 0.f))
+        return -1.0;
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        if (!(h[a] > 0.f)) return -1.0;
+        s += symbol_at_pi(space_order) / ((double)h[a] * h[a]);
+    }
+    return 2.0 / ((double)v_max * std::sqrt(s));
+}
+
+size_t wave_workspace_bytes(const wave_grid *g, int32_t op, int32_t nsrc, int32_t nrec,
+                            int32_t ckpt_every, const wave_tuning *tuning)
+{
+    (void)tuning;
+    Dims d;
+    if (check_grid(g, &d) || nsrc < 0 || nrec < 0 || op < WAVE_OP_FWD || op > WAVE_OP_GRAD) return 0;
+    if (op == WAVE_OP_GRAD && ckpt_every < 1) return 0;
+    return carve(nullptr, 0, true, d, op, nsrc, nrec, g->nt, ckpt_every).bytes;
+}
+
+size_t wave_ckpt_bytes(const wave_grid *g, int32_t ckpt_every)
+{
+    Dims d;
+    if (check_grid(g, &d) || ckpt_every < 1) return 0;
+    const size_t nseg = (size_t)((g->nt + ckpt_every - 1) / ckpt_every);
+    return nseg * 2 * sizeof(float) * (size_t)d.npad;
+}
+
+int32_t wave_fwd(const wave_grid *g, const float *m, const float *damp, const wave_points *src,
+                 const float *src_traces, const wave_points *rec, float *rec_traces, float *u_last,
+                 float *ckpt, int32_t ckpt_every, const wave_tuning *tuning, void *ws,
+                 size_t ws_bytes, void *stream_)
+{
+    try {
+        Dims d;
+        int rc = check_grid(g, &d);
+        if (rc) return rc;
+        if (!m || !damp || !ws) return WAVE_EINVAL;
+        if (check_points(src, true, src_traces) || check_points(rec, false, nullptr)) return WAVE_EINVAL;
+        if (ckpt != nullptr && ckpt_every < 1) return WAVE_EINVAL;
+        if ((uintptr_t)ws % kAlign) return WAVE_EINVAL;
+        const int nsrc = npts_of(src), nrec = npts_of(rec);
+        const Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_FWD, nsrc, nrec, g->nt, ckpt_every);
+        if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
+        HostTable ti, tr;
+        if (build_table(d, g->h, src, false, &ti) || build_table(d, g->h, rec, true, &tr))
+            return WAVE_EINVAL;
+        cudaStream_t stream = (cudaStream_t)stream_;
+        const Stencil st = make_stencil(g);
+        if ((rc = prep_model(d, g, tuning, m, damp, L, stream))) return rc;
+        Plan plan;
+        for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.U[i], 0, sizeof(float) * d.npad, stream));
+        if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, stream, &plan))) return rc;
+        for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.U[i], 0, sizeof(float) * d.npad, stream));
+        if ((rc = upload_table(ti, L.inj, stream)) || (rc = upload_table(tr, L.rec, stream))) return rc;
+        Job job;
+        job.d = d;
+        job.st = st;
+        job.cB = L.cB;
+        job.cC = L.cC;
+        job.cE = nullptr;
+        job.inj = L.inj.view();
+        job.q = src_traces;
+        job.nq = nsrc;
+        job.rec = L.rec.view();
+        job.corner = L.corner;
+        job.nslot = 8 * nrec;
+        State s;
+        for (int i = 0; i < 4; ++i) s.buf[i] = L.U[i];
+        if ((rc = prof_begin(tuning, stream))) return rc;
+        if ((rc = run_steps(job, s, g->nt, plan, stream, ckpt, ckpt_every, 0))) return rc;
+        if ((rc = prof_end(stream))) return rc;
+        if (nrec > 0 && rec_traces != nullptr)
+            CK(wt::launch_gather(L.corner, L.rec.wts, g->nt, nrec, 1, rec_traces, stream));
+        if (u_last != nullptr) {
+            CK(wt::launch_unpad(s.buf[s.a], d.nx, d.ny, d.nz, d.nzp, 1.f, u_last, stream));
+            CK(wt::launch_unpad(s.buf[s.b], d.nx, d.ny, d.nz, d.nzp, 1.f, u_last + d.n, stream));
+        }
+        return WAVE_OK;
+    } catch (const std::bad_alloc &) {
+        return WAVE_EINVAL;
+    } catch (...) {
+        return WAVE_EINVAL;
+    }
+}
+
+int32_t wave_adj(const wave_grid *g, const float *m, const float *damp, const wave_points *rec,
+                 const float *rec_resid, const wave_points *src, float *src_adj, float *v_last,
+                 const wave_tuning *tuning, void *ws, size_t ws_bytes, void *stream_)
+{
+    try {
+        Dims d;
+        int rc = check_grid(g, &d);
+        if (rc) return rc;
+        if (!m || !damp || !ws) return WAVE_EINVAL;
+        if (check_points(rec, true, rec_resid) || check_points(src, false, nullptr)) return WAVE_EINVAL;
+        if ((uintptr_t)ws % kAlign) return WAVE_EINVAL;
+        const int nsrc = npts_of(src), nrec = npts_of(rec);
+        const Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_ADJ, nsrc, nrec, g->nt, 0);
+        if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
+        HostTable ti, tr;
+        if (build_table(d, g->h, rec, false, &ti) || build_table(d, g->h, src, true, &tr))
+            return WAVE_EINVAL;
+        cudaStream_t stream = (cudaStream_t)stream_;
+        const Stencil st = make_stencil(g);
+        if ((rc = prep_model(d, g, tuning, m, damp, L, stream))) return rc;
+        Plan plan;
+        for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.U[i], 0, sizeof(float) * d.npad, stream));
+        if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, stream, &plan))) return rc;
+        for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.U[i], 0, sizeof(float) * d.npad, stream));
+        if ((rc = upload_table(ti, L.inj, stream)) || (rc = upload_table(tr, L.rec, stream))) return rc;
+        // reversed step j produces nu^{nt-j}: it injects res^{nt-1-j} and records
+        // dJ/dq^{nt-1-j}
+        Job job;
+        job.d = d;
+        job.st = st;
+        job.cB = L.cB;
+        job.cC = L.cC;
+        job.inj = L.inj.view();
+        job.q = rec_resid;
+        job.nq = nrec;
+        job.q_base = g->nt - 1;
+        job.q_dir = -1;
+        job.rec = L.rec.view();
+        job.corner = L.corner;
+        job.nslot = 8 * nsrc;
+        job.c_base = g->nt - 1;
+        job.c_dir = -1;
+        State s;
+        for (int i = 0; i < 4; ++i) s.buf[i] = L.U[i];
+        if ((rc = prof_begin(tuning, stream))) return rc;
+        if ((rc = run_steps(job, s, g->nt, plan, stream))) return rc;
+        if ((rc = prof_end(stream))) return rc;
+        if (nsrc > 0 && src_adj != nullptr)
+            CK(wt::launch_gather(L.corner, L.rec.wts, g->nt, nsrc, 1, src_adj, stream));
+        if (v_last != nullptr) {
+            CK(wt::launch_unpad(s.buf[s.a], d.nx, d.ny, d.nz, d.nzp, 1.f, v_last, stream));
+            CK(wt::launch_unpad(s.buf[s.b], d.nx, d.ny, d.nz, d.nzp, 1.f, v_last + d.n, stream));
+        }
+        return WAVE_OK;
+    } catch (...) {
+        return WAVE_EINVAL;
+    }
+}
+
+int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const wave_points *src,
+                  const float *src_traces, const wave_points *rec, const float *rec_resid,
+                  const float *ckpt, int32_t ckpt_every, float *grad, const wave_tuning *tuning,
+                  void *ws, size_t ws_bytes, void *stream_)
+{
+    try {
+        Dims d;
+        int rc = check_grid(g, &d);
+        if (rc) return rc;
+        if (!m || !damp || !ws || !ckpt || !grad || ckpt_every < 1) return WAVE_EINVAL;
+        if (check_points(src, true, src_traces) || check_points(rec, true, rec_resid)) return WAVE_EINVAL;
+        if ((uintptr_t)ws % kAlign) return WAVE_EINVAL;
+        const int nsrc = npts_of(src), nrec = npts_of(rec);
+        const int nt = g->nt;
+        const Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_GRAD, nsrc, nrec, nt, ckpt_every);
+        if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
+        HostTable ts, tr;
+        if (build_table(d, g->h, src, false, &ts) || build_table(d, g->h, rec, false, &tr))
+            return WAVE_EINVAL;
+        cudaStream_t stream = (cudaStream_t)stream_;
+        const Stencil st = make_stencil(g);
+        if ((rc = prep_model(d, g, tuning, m, damp, L, stream))) return rc;
+        Plan plan;
+        if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, stream, &plan))) return rc;
+        if ((rc = upload_table(ts, L.inj, stream)) || (rc = upload_table(tr, L.inj2, stream))) return rc;
+        CK(cudaMemsetAsync(L.G, 0, sizeof(float) * d.npad, stream));
+        for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.V[i], 0, sizeof(float) * d.npad, stream));
+        State adj;
+        for (int i = 0; i < 4; ++i) adj.buf[i] = L.V[i];
+        const int nseg = (nt + ckpt_every - 1) / ckpt_every;
+        if ((rc = prof_begin(tuning, stream))) return rc;
+        for (int c = nseg - 1; c >= 0; --c) {
+            const int s0 = c * ckpt_every;
+            const int len = std::min(ckpt_every, nt - s0);
+            // 1) recompute u over [s0, s0+len) from checkpoint c, storing
+            //    D^n = u^{n+1} - 2u^n + u^{n-1} in store[n - s0]
+            State fw;
+            for (int i = 0; i < 4; ++i) fw.buf[i] = L.U[i];
+            const float *cp = ckpt + (size_t)c * 2 * d.npad;
+            CK(cudaMemcpyAsync(fw.buf[0], cp, sizeof(float) * d.npad, cudaMemcpyDeviceToDevice, stream));
+            CK(cudaMemcpyAsync(fw.buf[1], cp + d.npad, sizeof(float) * d.npad, cudaMemcpyDeviceToDevice,
+                               stream));
+            fw.a = 0;
+            fw.b = 1;
+            Job rj;
+            rj.d = d;
+            rj.st = st;
+            rj.cB = L.cB;
+            rj.cC = L.cC;
+            rj.cE = L.cE;
+            rj.inj = L.inj.view();
+            rj.q = src_traces;
+            rj.nq = nsrc;
+            rj.q_base = s0;
+            rj.q_dir = 1;
+            rj.dstore = L.store;
+            rj.d_base = 0;
+            rj.d_dir = 1;
+            if ((rc = run_steps(rj, fw, len, plan, stream))) return rc;
+            // 2) adjoint over the segment, newest step first: reversed step
+            //    for n = s0+len-1 .. s0 produces nu^{n+1}, injects res^n and
+            //    accumulates G += nu^{n+1} D^n
+            Job aj;
+            aj.d = d;
+            aj.st = st;
+            aj.cB = L.cB;
+            aj.cC = L.cC;
+            aj.inj = L.inj2.view();
+            aj.q = rec_resid;
+            aj.nq = nrec;
+            aj.q_base = s0 + len - 1;
+            aj.q_dir = -1;
+            aj.dload = L.store;
+            aj.l_base = len - 1;
+            aj.l_dir = -1;
+            aj.gacc = L.G;
+            if ((rc = run_steps(aj, adj, len, plan, stream))) return rc;
+        }
+        if ((rc = prof_end(stream))) return rc;
+        const float scale = (float)(-1.0 / ((double)g->dt * (double)g->dt));
+        CK(wt::launch_unpad(L.G, d.nx, d.ny, d.nz, d.nzp, scale, grad, stream));
+        return WAVE_OK;
+    } catch (...) {
+        return WAVE_EINVAL;
+    }
+}
+
+int32_t wave_status(const void *ws, void *stream_)
+{
+    if (ws == nullptr) return WAVE_EINVAL;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return WAVE_ECUDA;
+    int st = 0;
+    if (cudaMemcpy(&st, ws, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return WAVE_ECUDA;
+    return st;
+}
+
+int32_t wave_sweep_stats(float *ms, int32_t *launches, int32_t *steps)
+{
+    if (!g_prof.valid || ms == nullptr) return WAVE_EINVAL;
+    if (cudaEventSynchronize(g_prof.e1) != cudaSuccess) return WAVE_ECUDA;
+    if (cudaEventElapsedTime(ms, g_prof.e0, g_prof.e1) != cudaSuccess) return WAVE_ECUDA;
+    if (launches) *launches = g_prof.launches;
+    if (steps) *steps = g_prof.steps;
+    return WAVE_OK;
+}
+
+int32_t wave_describe_plan(const wave_grid *g, const wave_tuning *tuning, int32_t *out)
+{
+    Dims d;
+    int rc = check_grid(g, &d);
+    if (rc) return rc;
+    if (out == nullptr) return WAVE_EINVAL;
+    Plan p;
+    float *U[4] = {nullptr, nullptr, nullptr, nullptr};
+    if ((rc = resolve_plan(d, g, tuning, false, nullptr, nullptr, nullptr, U, nullptr, &p))) return rc;
+    out[0] = p.v->T;
+    out[1] = p.v->BY;
+    out[2] = p.chunk;
+    out[3] = p.v->BZ;
+    out[4] = p.v->V;
+    return WAVE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// wave_internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "sweep.cuh"
+
+namespace wt {
+
+// One compiled sweep variant and its launcher.
+struct SweepVariant {
+    int R, T, V, BZ, BY, threads;
+    size_t smem;
+    cudaError_t (*launch)(int nblocks, cudaStream_t stream, const SweepArgs &a, const Stencil &st);
+    const void *func;
+};
+
+// Variants of radius r (defined in sweep_r<r>.cu).
+int sweep_variants_r1(const SweepVariant **out);
+int sweep_variants_r2(const SweepVariant **out);
+int sweep_variants_r3(const SweepVariant **out);
+int sweep_variants_r4(const SweepVariant **out);
+int sweep_variants_r5(const SweepVariant **out);
+int sweep_variants_r6(const SweepVariant **out);
+int sweep_variants_r7(const SweepVariant **out);
+int sweep_variants_r8(const SweepVariant **out);
+
+// Auxiliary kernels (aux_kernels.cu).  Status codes are written to status[0]
+// with atomicMin, so the most severe (most negative) error wins.
+cudaError_t launch_prep(const float *m, const float *damp, int nx, int ny, int nz, int nzp,
+                        float dt, float stab_lhs, float *cB, float *cC, float *cE, int *status,
+                        cudaStream_t s);
+cudaError_t launch_pad(const float *src, int nx, int ny, int nz, int nzp, float *dst,
+                       cudaStream_t s);
+cudaError_t launch_unpad(const float *src, int nx, int ny, int nz, int nzp, float scale,
+                         float *dst, cudaStream_t s);
+cudaError_t launch_gather(const float *corner, const float *w, int rows, int npts, int row_dir,
+                          float *out, cudaStream_t s);
+
+template <int R, int T, int V, int BZ, int BY>
+cudaError_t launch_sweep(int nblocks, cudaStream_t stream, const SweepArgs &a, const Stencil &st)
+{
+    using S = SweepShape<R, T, V, BZ, BY>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R, T, V, BZ, BY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)S::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    sweep_kernel<R, T, V, BZ, BY><<<nblocks, S::NT, S::SMEM, stream>>>(a, st);
+    return cudaGetLastError();
+}
+
+}  // namespace wt
+
+#define WAVE_VARIANT_ENTRY(R_, T_, V_, BZ_, BY_)                                                  \
+    {R_, T_, V_, BZ_, BY_, wt::SweepShape<R_, T_, V_, BZ_, BY_>::NT,                              \
+     wt::SweepShape<R_, T_, V_, BZ_, BY_>::SMEM, &wt::launch_sweep<R_, T_, V_, BZ_, BY_>,         \
+     (const void *)&wt::sweep_kernel<R_, T_, V_, BZ_, BY_>},
+
+#define WAVE_DEFINE_RADIUS(r_)                                                                    \
+    namespace wt {                                                                                \
+    static const SweepVariant kVariants_r##r_[] = {WAVE_SWEEP_VARIANTS_R##r_(WAVE_VARIANT_ENTRY)}; \
+    int sweep_variants_r##r_(const SweepVariant **out)                                            \
+    {                                                                                             \
+        *out = kVariants_r##r_;                                                                   \
+        return (int)(sizeof(kVariants_r##r_) / sizeof(kVariants_r##r_[0]));                       \
+    }                                                                                             \
+    }

@@ -1,0 +1,305 @@
+"""Thin ctypes binding of libwavetile (include/wave.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers are torch CUDA tensors (float32, contiguous); point
+coordinates are host arrays.  The library is required: importing the
+functions below on a machine without the built library raises instead of
+falling back to anything else.
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+WAVE_OK = 0
+WAVE_EINVAL = -1
+WAVE_EUNSTABLE = -2
+WAVE_ECUDA = -3
+WAVE_ETIMEOUT = -4
+WAVE_ENOSPACE = -5
+WAVE_EUNSUPPORTED = -6
+WAVE_OP_FWD, WAVE_OP_ADJ, WAVE_OP_GRAD = 0, 1, 2
+WAVE_ALLOW_UNSTABLE = 1
+WAVE_TIME_SWEEPS = 2
+
+EXPORTED = ["wave_version", "wave_strerror", "wave_fd_coefficients", "wave_cfl_dt",
+            "wave_workspace_bytes", "wave_ckpt_bytes", "wave_fwd", "wave_adj", "wave_grad",
+            "wave_status", "wave_describe_plan", "wave_sweep_stats"]
+
+
+class WaveError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, _lib().wave_strerror(code).decode(), code))
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 3), ("h", ctypes.c_float * 3), ("dt", ctypes.c_float),
+                ("nt", ctypes.c_int32), ("space_order", ctypes.c_int32)]
+
+
+class _Points(ctypes.Structure):
+    _fields_ = [("npts", ctypes.c_int32), ("xyz", ctypes.POINTER(ctypes.c_float))]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("time_tile", ctypes.c_int32), ("tile_y", ctypes.c_int32),
+                ("tile_x", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+@dataclass
+class Grid:
+    """Grid shape (nx, ny, nz), spacing h (km), dt (s), nt steps, space order."""
+    n: tuple
+    h: tuple
+    dt: float
+    nt: int
+    space_order: int
+
+    def c(self):
+        g = _Grid()
+        g.n[:] = [int(v) for v in self.n]
+        g.h[:] = [float(v) for v in self.h]
+        g.dt = float(self.dt)
+        g.nt = int(self.nt)
+        g.space_order = int(self.space_order)
+        return g
+
+
+@dataclass
+class Tuning:
+    """time_tile: 0 autotune, 1 untiled, T >= 2 time-tile depth."""
+    time_tile: int = 0
+    tile_y: int = 0
+    tile_x: int = 0
+    flags: int = 0
+
+    def c(self):
+        return _Tuning(int(self.time_tile), int(self.tile_y), int(self.tile_x), int(self.flags))
+
+
+_LIB = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libwavetile is not built (%s); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+        lib = ctypes.CDLL(path)
+        vp = ctypes.c_void_p
+        i32 = ctypes.c_int32
+        gp = ctypes.POINTER(_Grid)
+        pp = ctypes.POINTER(_Points)
+        tp = ctypes.POINTER(_Tuning)
+        lib.wave_version.restype = i32
+        lib.wave_strerror.argtypes = [i32]
+        lib.wave_strerror.restype = ctypes.c_char_p
+        lib.wave_fd_coefficients.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+        lib.wave_fd_coefficients.restype = i32
+        lib.wave_cfl_dt.argtypes = [i32, ctypes.POINTER(ctypes.c_float), ctypes.c_float]
+        lib.wave_cfl_dt.restype = ctypes.c_double
+        lib.wave_workspace_bytes.argtypes = [gp, i32, i32, i32, i32, tp]
+        lib.wave_workspace_bytes.restype = ctypes.c_size_t
+        lib.wave_ckpt_bytes.argtypes = [gp, i32]
+        lib.wave_ckpt_bytes.restype = ctypes.c_size_t
+        lib.wave_fwd.argtypes = [gp, vp, vp, pp, vp, pp, vp, vp, vp, i32, tp, vp, ctypes.c_size_t, vp]
+        lib.wave_fwd.restype = i32
+        lib.wave_adj.argtypes = [gp, vp, vp, pp, vp, pp, vp, vp, tp, vp, ctypes.c_size_t, vp]
+        lib.wave_adj.restype = i32
+        lib.wave_grad.argtypes = [gp, vp, vp, pp, vp, pp, vp, vp, i32, vp, tp, vp, ctypes.c_size_t, vp]
+        lib.wave_grad.restype = i32
+        lib.wave_status.argtypes = [vp, vp]
+        lib.wave_status.restype = i32
+        lib.wave_describe_plan.argtypes = [gp, tp, ctypes.POINTER(i32)]
+        lib.wave_describe_plan.restype = i32
+        lib.wave_sweep_stats.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32),
+                                         ctypes.POINTER(i32)]
+        lib.wave_sweep_stats.restype = i32
+        _LIB = lib
+    return _LIB
+
+
+def _check(code, what):
+    if code != WAVE_OK:
+        raise WaveError(code, what)
+
+
+def fd_coefficients(space_order):
+    out = (ctypes.c_double * (space_order // 2 + 1))()
+    _check(_lib().wave_fd_coefficients(int(space_order), out), "wave_fd_coefficients")
+    return np.array(list(out))
+
+
+def cfl_dt(space_order, h, v_max):
+    hh = (ctypes.c_float * 3)(*[float(v) for v in h])
+    return float(_lib().wave_cfl_dt(int(space_order), hh, float(v_max)))
+
+
+def workspace_bytes(grid, op, nsrc, nrec, ckpt_every=0):
+    g = grid.c()
+    return int(_lib().wave_workspace_bytes(ctypes.byref(g), int(op), int(nsrc), int(nrec),
+                                           int(ckpt_every), None))
+
+
+def ckpt_bytes(grid, ckpt_every):
+    g = grid.c()
+    return int(_lib().wave_ckpt_bytes(ctypes.byref(g), int(ckpt_every)))
+
+
+def describe_plan(grid, tuning=None):
+    g = grid.c()
+    out = (ctypes.c_int32 * 5)()
+    t = tuning.c() if tuning is not None else None
+    _check(_lib().wave_describe_plan(ctypes.byref(g), ctypes.byref(t) if t else None, out),
+           "wave_describe_plan")
+    return dict(time_tile=out[0], tile_y=out[1], tile_x=out[2], tile_z=out[3], vec=out[4])
+
+
+# --------------------------------------------------------------------------
+# torch marshalling
+# --------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev_ptr(t, name, shape=None):
+    torch = _torch()
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous float32 tensor" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _points(xyz):
+    if xyz is None:
+        return _Points(0, None), np.zeros((0, 3), np.float32)
+    a = np.ascontiguousarray(np.asarray(xyz, dtype=np.float32).reshape(-1, 3))
+    return _Points(a.shape[0], a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), a
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _workspace(nbytes, device, workspace):
+    torch = _torch()
+    if workspace is not None:
+        if workspace.numel() * workspace.element_size() < nbytes:
+            raise ValueError("workspace too small: need %d bytes" % nbytes)
+        return workspace
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def fwd(grid, m, damp, src_xyz=None, src_traces=None, rec_xyz=None, *, tuning=None,
+        want_u_last=False, ckpt_every=0, workspace=None, stream=None):
+    """Forward modelling.  Returns (rec_traces [nt][nrec], u_last [2,...] or None,
+    ckpt (flat float32 tensor) or None)."""
+    torch = _torch()
+    n = tuple(grid.n)
+    sp, sa = _points(src_xyz)
+    rp, ra = _points(rec_xyz)
+    dev = m.device
+    rec = torch.empty((grid.nt, rp.npts), dtype=torch.float32, device=dev)
+    u_last = torch.empty((2,) + n, dtype=torch.float32, device=dev) if want_u_last else None
+    ckpt = None
+    if ckpt_every:
+        ckpt = torch.empty(ckpt_bytes(grid, ckpt_every) // 4, dtype=torch.float32, device=dev)
+    ws = _workspace(workspace_bytes(grid, WAVE_OP_FWD, sp.npts, rp.npts), dev, workspace)
+    g = grid.c()
+    t = tuning.c() if tuning is not None else None
+    code = _lib().wave_fwd(
+        ctypes.byref(g), _dev_ptr(m, "m", n), _dev_ptr(damp, "damp", n), ctypes.byref(sp),
+        _dev_ptr(src_traces, "src_traces", (grid.nt, sp.npts)) if sp.npts else None,
+        ctypes.byref(rp), _dev_ptr(rec, "rec") if rp.npts else None,
+        _dev_ptr(u_last, "u_last") if u_last is not None else None,
+        _dev_ptr(ckpt, "ckpt") if ckpt is not None else None, int(ckpt_every),
+        ctypes.byref(t) if t is not None else None, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+        _stream(stream))
+    del sa, ra
+    _check(code, "wave_fwd")
+    return rec, u_last, ckpt, ws
+
+
+def adj(grid, m, damp, rec_xyz, rec_resid, src_xyz=None, *, tuning=None, want_v_last=False,
+        workspace=None, stream=None):
+    """Adjoint modelling.  Returns (src_adj [nt][nsrc], v_last [2,...] or None)."""
+    torch = _torch()
+    n = tuple(grid.n)
+    rp, ra = _points(rec_xyz)
+    sp, sa = _points(src_xyz)
+    dev = m.device
+    sadj = torch.empty((grid.nt, sp.npts), dtype=torch.float32, device=dev)
+    v_last = torch.empty((2,) + n, dtype=torch.float32, device=dev) if want_v_last else None
+    ws = _workspace(workspace_bytes(grid, WAVE_OP_ADJ, sp.npts, rp.npts), dev, workspace)
+    g = grid.c()
+    t = tuning.c() if tuning is not None else None
+    code = _lib().wave_adj(
+        ctypes.byref(g), _dev_ptr(m, "m", n), _dev_ptr(damp, "damp", n), ctypes.byref(rp),
+        _dev_ptr(rec_resid, "rec_resid", (grid.nt, rp.npts)) if rp.npts else None,
+        ctypes.byref(sp), _dev_ptr(sadj, "src_adj") if sp.npts else None,
+        _dev_ptr(v_last, "v_last") if v_last is not None else None,
+        ctypes.byref(t) if t is not None else None, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+        _stream(stream))
+    del sa, ra
+    _check(code, "wave_adj")
+    return sadj, v_last, ws
+
+
+def grad(grid, m, damp, src_xyz, src_traces, rec_xyz, rec_resid, ckpt, ckpt_every, *,
+         tuning=None, workspace=None, stream=None):
+    """dJ/dm for the residual rec_resid = dJ/dd, from wave_fwd checkpoints."""
+    torch = _torch()
+    n = tuple(grid.n)
+    sp, sa = _points(src_xyz)
+    rp, ra = _points(rec_xyz)
+    dev = m.device
+    g_out = torch.empty(n, dtype=torch.float32, device=dev)
+    ws = _workspace(workspace_bytes(grid, WAVE_OP_GRAD, sp.npts, rp.npts, ckpt_every), dev,
+                    workspace)
+    g = grid.c()
+    t = tuning.c() if tuning is not None else None
+    code = _lib().wave_grad(
+        ctypes.byref(g), _dev_ptr(m, "m", n), _dev_ptr(damp, "damp", n), ctypes.byref(sp),
+        _dev_ptr(src_traces, "src_traces", (grid.nt, sp.npts)) if sp.npts else None,
+        ctypes.byref(rp), _dev_ptr(rec_resid, "rec_resid", (grid.nt, rp.npts)) if rp.npts else None,
+        _dev_ptr(ckpt, "ckpt"), int(ckpt_every), _dev_ptr(g_out, "grad"),
+        ctypes.byref(t) if t is not None else None, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+        _stream(stream))
+    del sa, ra
+    _check(code, "wave_grad")
+    return g_out, ws
+
+
+def sweep_stats():
+    """(ms, launches, steps) of the sweep launches of the last call made with
+    Tuning.flags |= WAVE_TIME_SWEEPS on this thread."""
+    ms = ctypes.c_float()
+    nl = ctypes.c_int32()
+    ns = ctypes.c_int32()
+    _check(_lib().wave_sweep_stats(ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(ns)),
+           "wave_sweep_stats")
+    return float(ms.value), int(nl.value), int(ns.value)
+
+
+def status(ws, stream=None):
+    """Wait for the stream and return the device status word of workspace ws."""
+    return int(_lib().wave_status(ctypes.c_void_p(ws.data_ptr()), _stream(stream)))

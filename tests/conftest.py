@@ -17,3 +17,20 @@ def oracle():
     import oracle as _oracle
     _oracle._load()
     return _oracle
+
+
+@pytest.fixture(scope="session")
+def wavelib():
+    """The built CUDA library's binding (builds it if needed)."""
+    from paper_1806_08299_gb300 import build, wave
+    build.build()
+    wave._lib()
+    return wave
+
+
+@pytest.fixture(scope="session")
+def cuda(wavelib):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test collected without a CUDA device")
+    return torch.device("cuda:0")

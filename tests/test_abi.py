@@ -1,0 +1,73 @@
+"""CPU-side checks of the C ABI: the library loads, exports every function
+include/wave.h declares, and its host-only functions (coefficients, stability
+limit, workspace sizing, argument checks) behave; no kernel is launched."""
+import ctypes
+import os
+import re
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "wave.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(wave_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(wavelib):
+    names = _declared()
+    assert len(names) >= 10
+    lib = ctypes.CDLL(wavelib.library_path())
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(wavelib.EXPORTED) == names
+
+
+def test_coefficients_match_oracle(wavelib, oracle):
+    for so in range(2, 17, 2):
+        want = [float(v) for v in oracle.fd2_central_weights(so)]
+        got = wavelib.fd_coefficients(so)
+        assert np.allclose(got, want, rtol=1e-14, atol=0)
+
+
+def test_cfl_matches_oracle(wavelib, oracle):
+    h32 = [float(np.float32(v)) for v in (0.01, 0.012, 0.02)]
+    for so in (2, 4, 8, 12, 16):
+        assert wavelib.cfl_dt(so, h32, 2.5) == pytest.approx(oracle.cfl_dt(so, h32, 2.5), rel=1e-6)
+
+
+def test_workspace_and_ckpt_sizes(wavelib):
+    g = wavelib.Grid((33, 34, 35), (0.01,) * 3, 1e-3, 40, 8)
+    npad = 33 * 34 * 36
+    fwd = wavelib.workspace_bytes(g, wavelib.WAVE_OP_FWD, 2, 5)
+    assert fwd >= 6 * 4 * npad + 40 * 8 * 5 * 4
+    assert fwd % 256 == 0
+    grad = wavelib.workspace_bytes(g, wavelib.WAVE_OP_GRAD, 2, 5, ckpt_every=7)
+    assert grad >= (3 + 4 + 4 + 1 + 7) * 4 * npad
+    assert wavelib.ckpt_bytes(g, 7) == 6 * 2 * 4 * npad
+    assert wavelib.workspace_bytes(g, wavelib.WAVE_OP_GRAD, 2, 5, ckpt_every=0) == 0
+    bad = wavelib.Grid((33, 34, 35), (0.01,) * 3, 1e-3, 40, 7)
+    assert wavelib.workspace_bytes(bad, wavelib.WAVE_OP_FWD, 0, 0) == 0
+
+
+@pytest.mark.parametrize("field,value", [("space_order", 3), ("space_order", 18), ("nt", 0),
+                                         ("dt", -1.0), ("n", (4, 40, 40))])
+def test_invalid_grid_rejected_without_gpu(wavelib, field, value):
+    lib = wavelib._lib()
+    g = wavelib.Grid((40, 40, 40), (0.01,) * 3, 1e-3, 10, 8)
+    setattr(g, field, value)
+    cg = g.c()
+    dummy = ctypes.c_void_p(256)
+    rc = lib.wave_fwd(ctypes.byref(cg), dummy, dummy, None, None, None, None, None, None, 0,
+                      None, dummy, 1 << 30, None)
+    assert rc == wavelib.WAVE_EINVAL
+
+
+def test_strerror(wavelib):
+    lib = wavelib._lib()
+    for code in (0, -1, -2, -3, -4, -5, -6, -99):
+        assert isinstance(lib.wave_strerror(code), bytes)
