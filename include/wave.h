@@ -188,7 +188,7 @@ int32_t wave_sweep_stats(float *ms, int32_t *launches, int32_t *steps);
 
 /* Sweep variant the library would run for grid g with `tuning`
  * (after autotuning if tuning->time_tile == 0 and it already ran):
- * out[0..4] = time_tile, tile_y, tile_x, variant index, vector width.
+ * out[0..4] = time_tile, tile_y, tile_x, tile_z, TMA prefetch distance.
  * Returns WAVE_OK or a WAVE_E* code. */
 int32_t wave_describe_plan(const wave_grid *g, const wave_tuning *tuning, int32_t *out);
 

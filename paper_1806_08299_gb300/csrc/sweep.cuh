@@ -5,24 +5,36 @@
 // time tiles with min/max bounding) for a GPU:
 //
 //  * Each block owns an output tile of BZ (z) x BY (y) columns and an x-chunk
-//    of `chunk` planes, and streams along x.  Stage s (1..T) computes level
-//    n+s on plane c_0 - s*R, where c_0 is the plane of level n loaded in the
-//    same iteration: the skew by the stencil radius R per time step of
-//    Sec. 4.1, the minimum legal factor (Sec. 2.3.2.1).  The x-dependences
-//    of a stage are thereby always already computed, and T time levels are
-//    live on chip at once (the time buffer of Sec. 5.2.1).
+//    of `chunk` planes, and streams along x.  In iteration i, plane c0 = X0 -
+//    RT + i of level n enters, and stage s (1..T) computes level n+s on plane
+//    c0 - s*R: the skew by the stencil radius R per time step of Sec. 4.1, the
+//    minimum legal factor (Sec. 2.3.2.1).  Every x-dependence of a stage is
+//    then already computed, and T time levels are live on chip at once (the
+//    time buffer of Sec. 5.2.1).
 //  * In y and z, neighbouring blocks read overlapping halos of width R*T and
 //    recompute the shrinking halo of each stage, so blocks never wait on one
-//    another.  Points outside the grid read as 0 and, because the per-point
-//    coefficients B, C are 0 there, are computed as exactly 0: this plays the
-//    role of the paper's min/max bounds (Sec. 4.2.2) without branches.
-//  * Per thread: one column of V consecutive z points; for every stage a
-//    register queue of the 2R+1 x-planes it needs; the centre plane of every
-//    stage goes through shared memory (double buffered, one barrier per
-//    plane) for the y and z neighbours.
+//    another.
+//  * Staging (Blackwell TMA): one thread issues cp.async.bulk.tensor loads P
+//    iterations ahead into two shared-memory rings completed through
+//    mbarriers.  Ring U holds the 2R+1+P most recent level-n planes with their
+//    y/z halos, so stage 1 reads all its x, y and z neighbours from shared
+//    memory.  Ring K holds, per iteration, level n-1 and the per-point
+//    coefficients B, C of stage 1's plane; stage s reads the B, C that stage 1
+//    read (s-1)R iterations earlier, so ring K is (T-1)R+1+P iterations deep.
+//    TMA fills everything outside
+//    the grid with zeros; with B = C = 0 there, points outside the grid are
+//    computed as exactly 0.  This plays the role of the paper's min/max bounds
+//    (Sec. 4.2.2) without branches.
+//  * Stages s >= 2 keep a register queue of the 2R+1 x-planes of their input
+//    level per thread (V = 4 consecutive z points) and exchange the centre
+//    plane through shared memory for the y and z neighbours (double buffered,
+//    one barrier per plane).
 //  * Sources are injected and receiver corners recorded inside the sweep (the
 //    imperfectly nested source/receiver loops the paper leaves open,
 //    Sec. 4.5.1 and Sec. 6.3.1).
+//  * Every mbarrier wait is bounded by %globaltimer; on expiry the block
+//    records WAVE_ETIMEOUT in the status word, finishes the plane, waits
+//    (bounded) for its copies in flight and returns.
 //
 // Bit-exactness: every point update is the same sequence of IEEE-rounded
 // operations (explicit __fmaf_rn / __fadd_rn / __fsub_rn / __fmul_rn, so no
@@ -30,12 +42,15 @@
 // launch split.  Tiled and untiled sweeps therefore agree bitwise, the GPU
 // analogue of the paper's verification rule (Sec. 4.3, Sec. 5.4.3).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace wt {
 
 constexpr int kMaxR = 8;
+constexpr int kV = 4;                                   // z points per thread
+constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
 
 // Per-axis stencil coefficients c_k / h_a^2 in FP32; cc is the centre
 // weight (c_0/hx^2 + c_0/hy^2) + c_0/hz^2 rounded once on the host.
@@ -60,12 +75,8 @@ struct SweepArgs {
     int nx, ny, nz;          // nz: padded z extent, a multiple of 4
     long long sx;            // ny * nz
     long long npad;          // nx * ny * nz
-    const float *u;          // level n
-    const float *um;         // level n-1
-    float *out_hi;           // level n+T (T == 1: may alias um, updated in place)
+    float *out_hi;           // level n+T (T == 1: may alias level n-1, updated in place)
     float *out_lo;           // level n+T-1 (T >= 2)
-    const float *cB;         // per point (m-eta)/(m+eta)
-    const float *cC;         // per point dt^2/(m+eta)
     const float *cE;         // per point -2 eta/(m+eta) (second-difference mode)
     PointTable inj;          // injection points
     const float *q;          // traces [rows][nq]
@@ -82,74 +93,148 @@ struct SweepArgs {
     float *gacc;
     int chunk;               // x planes per block
     int tiles_z, tiles_y;
+    int *status;             // device status word (atomicMin of WAVE_E* codes)
 };
 
-template <int R, int T, int V, int BZ, int BY>
+// TMA descriptors of the arrays the sweep reads (all [nx][ny][nz] float32):
+//   u    : level n, box (PW, H0, 1)
+//   um   : level n-1, box (W0, H0 - 2R, 1)
+//   B, C : coefficients, box (W0, H0 - 2R, 1)
+struct SweepMaps {
+    CUtensorMap u, um, B, C;
+};
+
+template <int R, int T, int BZ, int BY, int P>
 struct SweepShape {
+    static constexpr int V = kV;
     static constexpr int RT = R * T;
-    static constexpr int A0 = ((RT + 3) / 4) * 4;  // z halo, keeps 16-byte alignment
-    static constexpr int W0 = BZ + 2 * A0;         // layout width (z points)
-    static constexpr int LZ = W0 / V;              // threads per layout row
-    static constexpr int H0 = BY + 2 * RT;         // layout rows (y)
-    static constexpr int NT = LZ * H0;             // threads per block
-    static constexpr int RP = ((R + V - 1) / V) * V;
-    static constexpr int PW = W0 + 2 * RP;         // shared row pitch (floats)
-    static constexpr int PLANE = PW * H0;
-    static constexpr size_t SMEM = sizeof(float) * 2 * T * PLANE;
+    static constexpr int A0 = ((RT + 3) / 4) * 4;   // z halo, keeps 16-byte alignment
+    static constexpr int W0 = BZ + 2 * A0;          // layout width (z points)
+    static constexpr int LZ = W0 / V;               // threads per layout row
+    static constexpr int H0 = BY + 2 * RT;          // layout rows (y)
+    static constexpr int NT = LZ * H0;              // threads per block
+    static constexpr int RP = ((R + 3) / 4) * 4;    // z pad of ring-U rows
+    static constexpr int PW = W0 + 2 * RP;          // ring-U / centre-plane pitch
+    static constexpr int HK = H0 - 2 * R;           // rows of ring-K boxes (from row R)
+    static constexpr int DU = 2 * R + 1 + P;        // ring-U depth (planes)
+    static constexpr int DK = (T - 1) * R + 1 + P;  // ring-K depth (iterations)
+    static constexpr int NKB = 3;                   // ring-K boxes per iteration: um, B, C
+    static constexpr unsigned UBOX = PW * H0 * 4;   // bytes of one U box
+    static constexpr unsigned KBOX = W0 * HK * 4;   // bytes of one K box
+    static constexpr unsigned USLOT = (UBOX + 127) / 128 * 128;
+    static constexpr unsigned KBOXP = (KBOX + 127) / 128 * 128;
+    static constexpr unsigned KSLOT = NKB * KBOXP;
+    static constexpr int PLANE = PW * H0;           // centre plane (floats), stages >= 2
+    static constexpr size_t OFF_K = (size_t)DU * USLOT;
+    static constexpr size_t OFF_S = OFF_K + (size_t)DK * KSLOT;
+    static constexpr size_t OFF_BAR = OFF_S + sizeof(float) * 2 * (T - 1) * PLANE;
+    static constexpr size_t OFF_P = OFF_BAR + 8 * (DU + DK) + 16;
+    static constexpr size_t SMEM = OFF_P;           // + plane_start slices (smem_bytes)
+    static size_t smem_bytes(int chunk) { return OFF_P + sizeof(int) * 2 * (chunk + 3 * RT + 2); }
     static_assert(BZ % 4 == 0, "BZ must keep 16-byte alignment");
-    static_assert(W0 % V == 0, "layout width must be a multiple of V");
     static_assert(NT <= 1024, "too many threads per block");
     static_assert(R >= 1 && R <= kMaxR, "radius out of range");
+    static_assert(PW <= 256 && H0 <= 256, "TMA box dimension above 256");
+    static_assert(UBOX < (1u << 20) && NKB * KBOX < (1u << 20), "mbarrier tx count");
+    static_assert(SMEM <= 220 * 1024, "shared memory above the per-block limit");
 };
 
-template <int V>
-__device__ __forceinline__ void ld_vec(float (&d)[V], const float *p)
+// ---------------------------------------------------------------------------
+// PTX helpers (TMA, mbarrier)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
-    if constexpr (V == 4) {
-        float4 t = *reinterpret_cast<const float4 *>(p);
-        d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
-    } else if constexpr (V == 2) {
-        float2 t = *reinterpret_cast<const float2 *>(p);
-        d[0] = t.x; d[1] = t.y;
-    } else {
-        d[0] = *p;
-    }
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-template <int V>
-__device__ __forceinline__ void ldg_vec(float (&d)[V], const float *p)
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
-    if constexpr (V == 4) {
-        float4 t = __ldg(reinterpret_cast<const float4 *>(p));
-        d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
-    } else if constexpr (V == 2) {
-        float2 t = __ldg(reinterpret_cast<const float2 *>(p));
-        d[0] = t.x; d[1] = t.y;
-    } else {
-        d[0] = __ldg(p);
-    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
 
-template <int V>
-__device__ __forceinline__ void st_vec(float *p, const float (&s)[V])
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
 {
-    if constexpr (V == 4) {
-        *reinterpret_cast<float4 *>(p) = make_float4(s[0], s[1], s[2], s[3]);
-    } else if constexpr (V == 2) {
-        *reinterpret_cast<float2 *>(p) = make_float2(s[0], s[1]);
-    } else {
-        *p = s[0];
-    }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
 }
 
-template <int R, int T, int V, int BZ, int BY>
-__global__ void __launch_bounds__(SweepShape<R, T, V, BZ, BY>::NT, 1)
-sweep_kernel(const SweepArgs a, const Stencil st)
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
-    using S = SweepShape<R, T, V, BZ, BY>;
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar`; false if it did not complete within kWaitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitNs) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void ld4(float (&d)[4], const float *p)
+{
+    float4 t = *reinterpret_cast<const float4 *>(p);
+    d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
+}
+
+__device__ __forceinline__ void ldg4(float (&d)[4], const float *p)
+{
+    float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
+}
+
+__device__ __forceinline__ void st4(float *p, const float (&s)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(s[0], s[1], s[2], s[3]);
+}
+
+template <int R, int T, int BZ, int BY, int P>
+__global__ void __launch_bounds__(SweepShape<R, T, BZ, BY, P>::NT, 1)
+sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stencil st,
+             const __grid_constant__ SweepMaps mp)
+{
+    using S = SweepShape<R, T, BZ, BY, P>;
+    constexpr int V = S::V;
     constexpr int QL = 2 * R + 1;
-    constexpr int ZW = V + 2 * S::RP;  // z window per thread (floats)
-    extern __shared__ __align__(16) float smem[];  // [T][2][PLANE]
+    constexpr int QS = T > 1 ? T - 1 : 1;  // queues of stages 2..T
+    constexpr int ZW = V + 2 * S::RP;      // z window per thread (floats)
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *ringU = reinterpret_cast<float *>(smem_raw);
+    unsigned char *ringK = smem_raw + S::OFF_K;
+    float *splane = reinterpret_cast<float *>(smem_raw + S::OFF_S);  // [T-1][2][PLANE]
+    uint64_t *barU = reinterpret_cast<uint64_t *>(smem_raw + S::OFF_BAR);
+    uint64_t *barK = barU + S::DU;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(barK + S::DK);
+    int *pinj = reinterpret_cast<int *>(smem_raw + S::OFF_P);
 
     const int tid = threadIdx.x;
     const int lane = tid % S::LZ;
@@ -161,116 +246,185 @@ sweep_kernel(const SweepArgs a, const Stencil st)
     const int txi = b / a.tiles_y;
     const int X0 = txi * a.chunk;
     const int X1 = min(X0 + a.chunk, a.nx);
-    const int gz = tzi * BZ - S::A0 + lane * V;
-    const int gy = tyi * BY - S::RT + row;
+    const int gz0 = tzi * BZ - S::A0;  // global z of layout column 0
+    const int gy0 = tyi * BY - S::RT;  // global y of layout row 0
+    const int gz = gz0 + lane * V;
+    const int gy = gy0 + row;
     const bool in_yz = gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz;
     const bool inner = in_yz && row >= S::RT && row < S::RT + BY &&
                        lane * V >= S::A0 && lane * V < S::A0 + BZ;
-    const bool row1 = row >= R && row < S::H0 - R;  // rows stage 1 computes
     const long long yz = in_yz ? (long long)gy * a.nz + gz : 0;
-    const int own = row * S::PW + S::RP + lane * V;
+    const int ownU = row * S::PW + S::RP + lane * V;   // in a U box / centre plane
+    const int ownK = (row - R) * S::W0 + lane * V;     // in a K box (rows >= R only)
+    const int niter = (X1 - X0) + 2 * S::RT;
+    const int c00 = X0 - S::RT;                        // plane of level n at iteration 0
 
-    for (int i = tid; i < 2 * T * S::PLANE; i += S::NT) smem[i] = 0.f;
+    // plane_start slices for [X0 - 2RT, X1 + RT], clamped (empty planes -> 0 points)
+    const int pbase = X0 - 2 * S::RT;
+    const int plen = (X1 - X0) + 3 * S::RT + 2;
+    int *prec = pinj + plen;
+    for (int k = tid; k < plen; k += S::NT) {
+        const int c = min(max(pbase + k, 0), a.nx);
+        pinj[k] = a.inj.plane_start != nullptr ? a.inj.plane_start[c] : 0;
+        prec[k] = a.rec.plane_start != nullptr ? a.rec.plane_start[c] : 0;
+    }
+    for (int k = tid; k < 2 * (T - 1) * S::PLANE; k += S::NT) splane[k] = 0.f;
+    if (tid == 0) {
+        for (int k = 0; k < S::DU + S::DK; ++k) mbar_init(barU + k, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
 
-    float q[T][QL][V];
+    // producer (thread 0): loads of iteration j into U slot j % DU, K slot j % DK
+    auto issue = [&](int j) {
+        const int c0 = c00 + j;
+        uint64_t *bu = barU + j % S::DU;
+        mbar_expect_tx(bu, S::UBOX);
+        tma_load_3d(ringU + (size_t)(j % S::DU) * (S::USLOT / 4), &mp.u, gz0 - S::RP, gy0, c0, bu);
+        uint64_t *bk = barK + j % S::DK;
+        unsigned char *kslot = ringK + (size_t)(j % S::DK) * S::KSLOT;
+        mbar_expect_tx(bk, S::NKB * S::KBOX);
+        tma_load_3d(kslot, &mp.um, gz0, gy0 + R, c0 - R, bk);
+        tma_load_3d(kslot + S::KBOXP, &mp.B, gz0, gy0 + R, c0 - R, bk);
+        tma_load_3d(kslot + 2 * S::KBOXP, &mp.C, gz0, gy0 + R, c0 - R, bk);
+    };
+    if (tid == 0)
+        for (int j = 0; j < P && j < niter; ++j) issue(j);
+
+    float q[QS][QL][V];
 #pragma unroll
-    for (int s = 0; s < T; ++s)
+    for (int s = 0; s < QS; ++s)
 #pragma unroll
         for (int k = 0; k < QL; ++k)
 #pragma unroll
             for (int j = 0; j < V; ++j) q[s][k][j] = 0.f;
 
-    const int niter = (X1 - X0) + 2 * S::RT;
-    int c0 = X0 - S::RT;  // plane of level n entering the pipeline this iteration
-    float pre_u[V], pre_um[V], um_cur[V];
-#pragma unroll
-    for (int j = 0; j < V; ++j) { pre_u[j] = 0.f; pre_um[j] = 0.f; }
-    if (in_yz && c0 >= 0 && c0 < a.nx) ld_vec<V>(pre_u, a.u + (long long)c0 * a.sx + yz);
-    if (in_yz && row1 && c0 - R >= 0 && c0 - R < a.nx)
-        ld_vec<V>(pre_um, a.um + (long long)(c0 - R) * a.sx + yz);
-    __syncthreads();
+    // U slot of iteration j (negative j: slots not yet filled, read only by
+    // computations whose results are never used)
+    auto uslot = [&](int j) -> const float * {
+        const int k = ((j % S::DU) + S::DU) % S::DU;
+        return ringU + (size_t)k * (S::USLOT / 4);
+    };
 
     int cur = 0;
-    for (int it = 0; it < niter; ++it, ++c0) {
-        // level n of plane c0 enters stage 1's queue
-#pragma unroll
-        for (int k = 0; k < QL - 1; ++k)
-#pragma unroll
-            for (int j = 0; j < V; ++j) q[0][k][j] = q[0][k + 1][j];
-#pragma unroll
-        for (int j = 0; j < V; ++j) { q[0][QL - 1][j] = pre_u[j]; um_cur[j] = pre_um[j]; }
-        {
-            const int cn = c0 + 1, cm = c0 + 1 - R;
-#pragma unroll
-            for (int j = 0; j < V; ++j) { pre_u[j] = 0.f; pre_um[j] = 0.f; }
-            if (in_yz && cn >= 0 && cn < a.nx) ld_vec<V>(pre_u, a.u + (long long)cn * a.sx + yz);
-            if (in_yz && row1 && cm >= 0 && cm < a.nx)
-                ld_vec<V>(pre_um, a.um + (long long)cm * a.sx + yz);
+    int it = 0;
+    for (; it < niter; ++it) {
+        const int c0 = c00 + it;
+        if (tid == 0 && it + P < niter && !*abort_flag) issue(it + P);
+        bool ok = mbar_wait_bounded(barU + it % S::DU, (uint32_t)((it / S::DU) & 1));
+        ok = mbar_wait_bounded(barK + it % S::DK, (uint32_t)((it / S::DK) & 1)) && ok;
+        if (!ok) {
+            *abort_flag = 1;
+            atomicMin(a.status, -4 /* WAVE_ETIMEOUT */);
         }
+        // K slot of iteration j (stage s reads iteration it - (s-1)R)
+        auto kslot_of = [&](int j) -> const unsigned char * {
+            const int k = ((j % S::DK) + S::DK) % S::DK;
+            return ringK + (size_t)k * S::KSLOT;
+        };
+        const unsigned char *kslot = kslot_of(it);
 
 #pragma unroll
         for (int s = 1; s <= T; ++s) {
             const int cs = c0 - s * R;  // plane computed by stage s
             const bool rowok = row >= s * R && row < S::H0 - s * R;
-            const bool plane_in = cs >= 0 && cs < a.nx;
             const long long pidx = (long long)cs * a.sx + yz;
-            float un[V], dd[V];
+            float un[V], dd[V], lap[V], cBv[V], cCv[V], u0[V], up[V];
 #pragma unroll
-            for (int j = 0; j < V; ++j) { un[j] = 0.f; dd[j] = 0.f; }
-            float lap[V], cBv[V], cCv[V];
-#pragma unroll
-            for (int j = 0; j < V; ++j) { lap[j] = 0.f; cBv[j] = 0.f; cCv[j] = 0.f; }
+            for (int j = 0; j < V; ++j) {
+                un[j] = 0.f; dd[j] = 0.f; lap[j] = 0.f; cBv[j] = 0.f; cCv[j] = 0.f;
+                u0[j] = 0.f; up[j] = 0.f;
+            }
             if (rowok) {
-                const float *P = smem + ((s - 1) * 2 + cur) * S::PLANE;
-                float zz[ZW / V][V];
+                const unsigned char *ks = kslot_of(it - (s - 1) * R);
+                ld4(cBv, reinterpret_cast<const float *>(ks + S::KBOXP) + ownK);
+                ld4(cCv, reinterpret_cast<const float *>(ks + 2 * S::KBOXP) + ownK);
+                if (s == 1) {
+                    // stage 1: every neighbour from ring U (centre plane c0 - R)
+                    const float *Pc = uslot(it - R);
+                    float zz[ZW / V][V];
 #pragma unroll
-                for (int j = 0; j < ZW / V; ++j) ld_vec<V>(zz[j], P + own - S::RP + j * V);
-#pragma unroll
-                for (int j = 0; j < V; ++j) lap[j] = __fmul_rn(st.cc, q[s - 1][R][j]);
-#pragma unroll
-                for (int k = 1; k <= R; ++k) {
-                    float yp[V], ym[V];
-                    ld_vec<V>(yp, P + own + k * S::PW);
-                    ld_vec<V>(ym, P + own - k * S::PW);
+                    for (int j = 0; j < ZW / V; ++j) ld4(zz[j], Pc + ownU - S::RP + j * V);
 #pragma unroll
                     for (int j = 0; j < V; ++j) {
-                        lap[j] = __fmaf_rn(st.cx[k], __fadd_rn(q[s - 1][R + k][j], q[s - 1][R - k][j]), lap[j]);
-                        lap[j] = __fmaf_rn(st.cy[k], __fadd_rn(yp[j], ym[j]), lap[j]);
-                        lap[j] = __fmaf_rn(st.cz[k],
-                                           __fadd_rn(zz[(S::RP + j + k) / V][(S::RP + j + k) % V],
-                                                     zz[(S::RP + j - k) / V][(S::RP + j - k) % V]),
-                                           lap[j]);
+                        u0[j] = zz[S::RP / V][j];
+                        lap[j] = __fmul_rn(st.cc, u0[j]);
+                    }
+#pragma unroll
+                    for (int k = 1; k <= R; ++k) {
+                        float xp[V], xm[V], yp[V], ym[V];
+                        ld4(xp, uslot(it - R + k) + ownU);
+                        ld4(xm, uslot(it - R - k) + ownU);
+                        ld4(yp, Pc + ownU + k * S::PW);
+                        ld4(ym, Pc + ownU - k * S::PW);
+#pragma unroll
+                        for (int j = 0; j < V; ++j) {
+                            lap[j] = __fmaf_rn(st.cx[k], __fadd_rn(xp[j], xm[j]), lap[j]);
+                            lap[j] = __fmaf_rn(st.cy[k], __fadd_rn(yp[j], ym[j]), lap[j]);
+                            lap[j] = __fmaf_rn(st.cz[k],
+                                               __fadd_rn(zz[(S::RP + j + k) / V][(S::RP + j + k) % V],
+                                                         zz[(S::RP + j - k) / V][(S::RP + j - k) % V]),
+                                               lap[j]);
+                        }
+                    }
+                    ld4(up, reinterpret_cast<const float *>(kslot) + ownK);  // level n-1
+                } else {
+                    // stage s >= 2: x from the register queue, y/z from the centre plane
+                    const int qs = s - 2;
+                    const float *Pc = splane + (qs * 2 + cur) * S::PLANE;
+                    float zz[ZW / V][V];
+#pragma unroll
+                    for (int j = 0; j < ZW / V; ++j) ld4(zz[j], Pc + ownU - S::RP + j * V);
+#pragma unroll
+                    for (int j = 0; j < V; ++j) {
+                        u0[j] = q[qs][R][j];
+                        lap[j] = __fmul_rn(st.cc, u0[j]);
+                    }
+#pragma unroll
+                    for (int k = 1; k <= R; ++k) {
+                        float yp[V], ym[V];
+                        ld4(yp, Pc + ownU + k * S::PW);
+                        ld4(ym, Pc + ownU - k * S::PW);
+#pragma unroll
+                        for (int j = 0; j < V; ++j) {
+                            lap[j] = __fmaf_rn(st.cx[k], __fadd_rn(q[qs][R + k][j], q[qs][R - k][j]),
+                                               lap[j]);
+                            lap[j] = __fmaf_rn(st.cy[k], __fadd_rn(yp[j], ym[j]), lap[j]);
+                            lap[j] = __fmaf_rn(st.cz[k],
+                                               __fadd_rn(zz[(S::RP + j + k) / V][(S::RP + j + k) % V],
+                                                         zz[(S::RP + j - k) / V][(S::RP + j - k) % V]),
+                                               lap[j]);
+                        }
+                    }
+                    if (s == 2) {
+                        ld4(up, uslot(it - 2 * R) + ownU);  // level n on plane c0 - 2R
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < V; ++j) up[j] = q[s > 2 ? s - 3 : 0][0][j];
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < V; ++j) { cBv[j] = 0.f; cCv[j] = 0.f; }
-                if (in_yz && plane_in) {
-                    ldg_vec<V>(cBv, a.cB + pidx);
-                    ldg_vec<V>(cCv, a.cC + pidx);
-                }
-#pragma unroll
-                for (int j = 0; j < V; ++j) {
-                    const float u0 = q[s - 1][R][j];
-                    const float up = (s == 1) ? um_cur[j] : q[s > 1 ? s - 2 : 0][0][j];
-                    un[j] = __fmaf_rn(cCv[j], lap[j], __fmaf_rn(cBv[j], __fsub_rn(u0, up), u0));
-                }
+                for (int j = 0; j < V; ++j)
+                    un[j] = __fmaf_rn(cCv[j], lap[j], __fmaf_rn(cBv[j], __fsub_rn(u0[j], up[j]), u0[j]));
+                const bool plane_in = cs >= 0 && cs < a.nx;
                 if (a.dstore != nullptr && in_yz && plane_in) {
                     // u^{n+1} - 2u^n + u^{n-1} = E (u^n - u^{n-1}) + C (L u^n + f^n)
                     float e[V];
-                    ldg_vec<V>(e, a.cE + pidx);
+                    ldg4(e, a.cE + pidx);
 #pragma unroll
-                    for (int j = 0; j < V; ++j) {
-                        const float u0 = q[s - 1][R][j];
-                        const float up = (s == 1) ? um_cur[j] : q[s > 1 ? s - 2 : 0][0][j];
-                        dd[j] = __fmaf_rn(cCv[j], lap[j], __fmul_rn(e[j], __fsub_rn(u0, up)));
-                    }
+                    for (int j = 0; j < V; ++j)
+                        dd[j] = __fmaf_rn(cCv[j], lap[j], __fmul_rn(e[j], __fsub_rn(u0[j], up[j])));
                 }
                 // point sources: f = sum_s w q_s (ascending source order), u += C f
-                if (a.inj.plane_start != nullptr && in_yz && plane_in) {
-                    // each grid point appears at most once in the table
-                    const int e0 = a.inj.plane_start[cs], e1 = a.inj.plane_start[cs + 1];
-                    float fv = 0.f;
-                    int hit = -1;
+                const int e0 = pinj[cs - pbase], e1 = pinj[cs - pbase + 1];
+                if (e1 > e0 && in_yz) {
+                    // each grid point appears at most once in the table, but up
+                    // to V table points can fall in this thread's V z-points
+                    float fv[V];
+                    unsigned hits = 0u;
+#pragma unroll
+                    for (int j = 0; j < V; ++j) fv[j] = 0.f;
                     for (int e = e0; e < e1; ++e) {
                         const int4 pt = a.inj.pts[e];
                         if (pt.x == gy && pt.y >= gz && pt.y < gz + V) {
@@ -278,65 +432,75 @@ sweep_kernel(const SweepArgs a, const Stencil st)
                             float f = 0.f;
                             for (int itm = pt.z; itm < pt.w; ++itm)
                                 f = __fmaf_rn(a.inj.w[itm], a.q[qrow + a.inj.item[itm]], f);
-                            fv = f;
-                            hit = pt.y - gz;
+                            const int jj = pt.y - gz;
+#pragma unroll
+                            for (int j = 0; j < V; ++j)
+                                if (jj == j) fv[j] = f;
+                            hits |= 1u << jj;
                         }
                     }
-                    if (hit >= 0) {
+                    if (hits) {
 #pragma unroll
                         for (int j = 0; j < V; ++j)
-                            if (hit == j) {
-                                un[j] = __fmaf_rn(cCv[j], fv, un[j]);
-                                dd[j] = __fmaf_rn(cCv[j], fv, dd[j]);
+                            if (hits & (1u << j)) {
+                                un[j] = __fmaf_rn(cCv[j], fv[j], un[j]);
+                                dd[j] = __fmaf_rn(cCv[j], fv[j], dd[j]);
                             }
                     }
                 }
             }
             const bool own_pt = inner && cs >= X0 && cs < X1;
             if (own_pt) {
-                if (a.rec.plane_start != nullptr) {
-                    const int e0 = a.rec.plane_start[cs], e1 = a.rec.plane_start[cs + 1];
-                    for (int e = e0; e < e1; ++e) {
-                        const int4 pt = a.rec.pts[e];
-                        if (pt.x == gy && pt.y >= gz && pt.y < gz + V) {
-                            float v = 0.f;
+                const int e0 = prec[cs - pbase], e1 = prec[cs - pbase + 1];
+                for (int e = e0; e < e1; ++e) {
+                    const int4 pt = a.rec.pts[e];
+                    if (pt.x == gy && pt.y >= gz && pt.y < gz + V) {
+                        float v = 0.f;
 #pragma unroll
-                            for (int j = 0; j < V; ++j)
-                                if (pt.y - gz == j) v = un[j];
-                            const long long crow = (long long)(a.c_row0 + a.c_dir * (s - 1)) * a.nslot;
-                            for (int itm = pt.z; itm < pt.w; ++itm) a.corner[crow + a.rec.item[itm]] = v;
-                        }
+                        for (int j = 0; j < V; ++j)
+                            if (pt.y - gz == j) v = un[j];
+                        const long long crow = (long long)(a.c_row0 + a.c_dir * (s - 1)) * a.nslot;
+                        for (int itm = pt.z; itm < pt.w; ++itm) a.corner[crow + a.rec.item[itm]] = v;
                     }
                 }
-                if (s == T) st_vec<V>(a.out_hi + pidx, un);
-                if (T >= 2 && s == T - 1) st_vec<V>(a.out_lo + pidx, un);
+                if (s == T) st4(a.out_hi + pidx, un);
+                if (T >= 2 && s == T - 1) st4(a.out_lo + pidx, un);
                 if (a.dstore != nullptr)
-                    st_vec<V>(a.dstore + (a.d_row0 + (long long)a.d_dir * (s - 1)) * a.npad + pidx, dd);
+                    st4(a.dstore + (a.d_row0 + (long long)a.d_dir * (s - 1)) * a.npad + pidx, dd);
                 if (a.gacc != nullptr) {
                     float dl[V], g[V];
-                    ldg_vec<V>(dl, a.dload + (a.l_row0 + (long long)a.l_dir * (s - 1)) * a.npad + pidx);
-                    ld_vec<V>(g, a.gacc + pidx);
+                    ldg4(dl, a.dload + (a.l_row0 + (long long)a.l_dir * (s - 1)) * a.npad + pidx);
+                    ld4(g, a.gacc + pidx);
 #pragma unroll
                     for (int j = 0; j < V; ++j) g[j] = __fmaf_rn(un[j], dl[j], g[j]);
-                    st_vec<V>(a.gacc + pidx, g);
+                    st4(a.gacc + pidx, g);
                 }
             }
             if (s < T) {
+                // level n+s of plane cs enters stage s+1's queue
 #pragma unroll
                 for (int k = 0; k < QL - 1; ++k)
 #pragma unroll
-                    for (int j = 0; j < V; ++j) q[s][k][j] = q[s][k + 1][j];
+                    for (int j = 0; j < V; ++j) q[s - 1][k][j] = q[s - 1][k + 1][j];
 #pragma unroll
-                for (int j = 0; j < V; ++j) q[s][QL - 1][j] = un[j];
+                for (int j = 0; j < V; ++j) q[s - 1][QL - 1][j] = un[j];
             }
         }
 
-        // centres of the next iteration (plane c_s + 1 of each stage's input)
+        // centres of stages >= 2 for the next iteration
 #pragma unroll
-        for (int s = 0; s < T; ++s)
-            st_vec<V>(smem + (s * 2 + (cur ^ 1)) * S::PLANE + own, q[s][R + 1]);
+        for (int s = 2; s <= T; ++s)
+            st4(splane + ((s - 2) * 2 + (cur ^ 1)) * S::PLANE + ownU, q[s - 2][R + 1]);
         __syncthreads();
         cur ^= 1;
+        if (*abort_flag) break;
+    }
+    if (it < niter && tid == 0) {
+        // aborted: wait (bounded) for the copies still in flight before exiting
+        for (int j = it + 1; j < niter && j <= it + P; ++j) {
+            mbar_wait_bounded(barU + j % S::DU, (uint32_t)((j / S::DU) & 1));
+            mbar_wait_bounded(barK + j % S::DK, (uint32_t)((j / S::DK) & 1));
+        }
     }
 }
 

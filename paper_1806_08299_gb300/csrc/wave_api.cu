@@ -13,6 +13,8 @@
 #include <tuple>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "wave.h"
 #include "wave_internal.h"
 
@@ -58,6 +60,35 @@ int check_grid(const wave_grid *g, Dims *d)
     d->n = (long long)d->nx * d->ny * d->nz;
     if (d->npad > (1LL << 36)) return WAVE_EINVAL;
     return WAVE_OK;
+}
+
+// TMA descriptor of a padded [nx][ny][nzp] float32 array with a (bz, by, 1)
+// box; out-of-bounds elements read as zero.  cuTensorMapEncodeTiled comes from
+// the driver through the runtime's entry-point query (no link to libcuda).
+int encode_map(CUtensorMap *map, const float *base, const Dims &d, int bz, int by)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (fn == nullptr) {
+            cudaDriverEntryPointQueryResult q;
+            void *f = nullptr;
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                                 &q) != cudaSuccess ||
+                q != cudaDriverEntryPointSuccess || f == nullptr)
+                return WAVE_ECUDA;
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+        }
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)d.nzp, (cuuint64_t)d.ny, (cuuint64_t)d.nx};
+    const cuuint64_t strides[2] = {(cuuint64_t)d.nzp * 4, (cuuint64_t)d.ny * d.nzp * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bz, (cuuint32_t)by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? WAVE_OK : WAVE_ECUDA;
 }
 
 // c_k = 2 (-1)^(k+1) (r!)^2 / (k^2 (r-k)! (r+k)!) by the product form
@@ -339,21 +370,42 @@ int tiles(int n, int b) { return (n + b - 1) / b; }
 
 // Default x-chunk: the split of x that best fills whole waves of resident
 // blocks, discounting the 2RT warm-up planes each chunk streams.
-int default_chunk(const Dims &d, const SweepVariant *v)
+// Dynamic shared memory of a launch: planes + plane_start slices of the chunk.
+size_t launch_smem(const SweepVariant *v, int chunk)
 {
-    cudaFuncSetAttribute(v->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->smem);
+    return v->smem + sizeof(int) * 2 * (size_t)(chunk + 3 * v->R * v->T + 2);
+}
+
+// Largest x-chunk whose plane_start slices still fit the per-block limit.
+int max_chunk(const SweepVariant *v)
+{
+    const long long room = (227LL * 1024 - (long long)v->smem) / 8 - 3LL * v->R * v->T - 2;
+    return (int)std::max(16LL, std::min(room, 1LL << 20));
+}
+
+int occupancy(const SweepVariant *v, int chunk)
+{
+    const size_t smem = launch_smem(v, chunk);
+    cudaFuncSetAttribute(v->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(&occ, v->func, v->threads, v->smem,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(&occ, v->func, v->threads, smem,
                                                                cudaOccupancyDefault) != cudaSuccess ||
         occ < 1)
         occ = 1;
+    return occ;
+}
+
+int default_chunk(const Dims &d, const SweepVariant *v)
+{
+    const int occ = occupancy(v, std::min(d.nx, max_chunk(v)));
     const long long per_wave = (long long)sm_count() * occ;
     const long long cols = (long long)tiles(d.nzp, v->BZ) * tiles(d.ny, v->BY);
     const int warm = 2 * v->R * v->T;
-    int best = d.nx;
+    int best = std::min(d.nx, max_chunk(v));
     double best_eff = -1.0;
     for (int nch = 1; nch <= 64; ++nch) {
         const int chunk = tiles(d.nx, nch);
+        if (chunk > max_chunk(v)) continue;
         if (nch > 1 && chunk < 2 * warm) break;
         const long long blocks = cols * tiles(d.nx, chunk);
         const long long waves = (blocks + per_wave - 1) / per_wave;
@@ -414,6 +466,7 @@ struct Job {
     Dims d;
     Stencil st;
     const float *cB, *cC, *cE;
+    int *status = nullptr;
     PointTable inj{};
     const float *q = nullptr;
     int nq = 0, q_base = 0, q_dir = 1;
@@ -488,7 +541,8 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         if (ckpt != nullptr) limit = std::min(limit, ckpt_every - (j0 + j) % ckpt_every);
         const SweepVariant *v = plan.v->T <= limit ? plan.v : fallback_variant(R, limit);
         if (v == nullptr) return WAVE_EUNSUPPORTED;
-        const int chunk = (v == plan.v && plan.chunk > 0) ? plan.chunk : default_chunk(d, v);
+        const int chunk =
+            std::min((v == plan.v && plan.chunk > 0) ? plan.chunk : default_chunk(d, v), max_chunk(v));
         SweepArgs a;
         std::memset(&a, 0, sizeof(a));
         a.nx = d.nx;
@@ -496,8 +550,13 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         a.nz = d.nzp;
         a.sx = (long long)d.ny * d.nzp;
         a.npad = d.npad;
-        a.u = s.buf[s.a];
-        a.um = s.buf[s.b];
+        a.status = job.status;
+        wt::SweepMaps maps;
+        int rc = encode_map(&maps.u, s.buf[s.a], d, v->PW, v->H0);
+        if (!rc) rc = encode_map(&maps.um, s.buf[s.b], d, v->W0, v->HK);
+        if (!rc) rc = encode_map(&maps.B, job.cB, d, v->W0, v->HK);
+        if (!rc) rc = encode_map(&maps.C, job.cC, d, v->W0, v->HK);
+        if (rc) return rc;
         int spare[2], ns = 0;
         for (int i = 0; i < 4; ++i)
             if (i != s.a && i != s.b) spare[ns++] = i;
@@ -507,8 +566,6 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
             a.out_hi = s.buf[spare[0]];
             a.out_lo = s.buf[spare[1]];
         }
-        a.cB = job.cB;
-        a.cC = job.cC;
         a.cE = job.cE;
         a.inj = job.inj;
         a.q = job.q;
@@ -532,7 +589,7 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         a.tiles_y = tiles(d.ny, v->BY);
         const long long nblocks = (long long)a.tiles_z * a.tiles_y * tiles(d.nx, chunk);
         if (nblocks > 0x7fffffffLL) return WAVE_EINVAL;
-        CK(v->launch((int)nblocks, stream, a, job.st));
+        CK(v->launch((int)nblocks, stream, a, job.st, maps));
         if (g_prof.active) {
             g_prof.launches++;
             g_prof.steps += v->T;
@@ -552,7 +609,7 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
 // points) and cache the fastest: the paper's auto-tuner extended to the time
 // tile (Sec. 4.4, Sec. 5.2.2), here over (T, tile, x-chunk).
 int autotune(const Dims &d, const Stencil &st, const float *cB, const float *cC, float *const U[4],
-             int R, cudaStream_t stream, Plan *out)
+             int *status, int R, cudaStream_t stream, Plan *out)
 {
     const SweepVariant *vs;
     const int nv = variants_for(R, &vs);
@@ -578,6 +635,7 @@ int autotune(const Dims &d, const Stencil &st, const float *cB, const float *cC,
             job.cB = cB;
             job.cC = cC;
             job.cE = nullptr;
+            job.status = status;
             State s;
             for (int k = 0; k < 4; ++k) s.buf[k] = U[k];
             const int steps = 4 * v->T > 8 ? 4 * v->T : 8;
@@ -607,7 +665,7 @@ int autotune(const Dims &d, const Stencil &st, const float *cB, const float *cC,
 // Plan for this call: explicit tuning, or the cached / freshly tuned one.
 // `may_tune` is false for dry queries (wave_describe_plan).
 int resolve_plan(const Dims &d, const wave_grid *g, const wave_tuning *t, bool may_tune,
-                 const Stencil *st, const float *cB, const float *cC, float *const U[4],
+                 const Stencil *st, const float *cB, const float *cC, float *const U[4], int *status,
                  cudaStream_t stream, Plan *out)
 {
     const int R = g->space_order / 2;
@@ -635,7 +693,7 @@ int resolve_plan(const Dims &d, const wave_grid *g, const wave_tuning *t, bool m
         return WAVE_OK;
     }
     Plan p;
-    const int rc = autotune(d, *st, cB, cC, U, R, stream, &p);
+    const int rc = autotune(d, *st, cB, cC, U, status, R, stream, &p);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = p;
@@ -751,7 +809,7 @@ int32_t wave_fwd(const wave_grid *g, const float *m, const float *damp, const wa
         if ((rc = prep_model(d, g, tuning, m, damp, L, stream))) return rc;
         Plan plan;
         for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.U[i], 0, sizeof(float) * d.npad, stream));
-        if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, stream, &plan))) return rc;
+        if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, L.status, stream, &plan))) return rc;
         for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.U[i], 0, sizeof(float) * d.npad, stream));
         if ((rc = upload_table(ti, L.inj, stream)) || (rc = upload_table(tr, L.rec, stream))) return rc;
         Job job;
@@ -759,6 +817,7 @@ int32_t wave_fwd(const wave_grid *g, const float *m, const float *damp, const wa
         job.st = st;
         job.cB = L.cB;
         job.cC = L.cC;
+        job.status = L.status;
         job.cE = nullptr;
         job.inj = L.inj.view();
         job.q = src_traces;
@@ -807,7 +866,7 @@ int32_t wave_adj(const wave_grid *g, const float *m, const float *damp, const wa
         if ((rc = prep_model(d, g, tuning, m, damp, L, stream))) return rc;
         Plan plan;
         for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.U[i], 0, sizeof(float) * d.npad, stream));
-        if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, stream, &plan))) return rc;
+        if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, L.status, stream, &plan))) return rc;
         for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.U[i], 0, sizeof(float) * d.npad, stream));
         if ((rc = upload_table(ti, L.inj, stream)) || (rc = upload_table(tr, L.rec, stream))) return rc;
         // reversed step j produces nu^{nt-j}: it injects res^{nt-1-j} and records
@@ -817,6 +876,7 @@ int32_t wave_adj(const wave_grid *g, const float *m, const float *damp, const wa
         job.st = st;
         job.cB = L.cB;
         job.cC = L.cC;
+        job.status = L.status;
         job.inj = L.inj.view();
         job.q = rec_resid;
         job.nq = nrec;
@@ -867,7 +927,7 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
         const Stencil st = make_stencil(g);
         if ((rc = prep_model(d, g, tuning, m, damp, L, stream))) return rc;
         Plan plan;
-        if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, stream, &plan))) return rc;
+        if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, L.status, stream, &plan))) return rc;
         if ((rc = upload_table(ts, L.inj, stream)) || (rc = upload_table(tr, L.inj2, stream))) return rc;
         CK(cudaMemsetAsync(L.G, 0, sizeof(float) * d.npad, stream));
         for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.V[i], 0, sizeof(float) * d.npad, stream));
@@ -893,6 +953,7 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
             rj.st = st;
             rj.cB = L.cB;
             rj.cC = L.cC;
+            rj.status = L.status;
             rj.cE = L.cE;
             rj.inj = L.inj.view();
             rj.q = src_traces;
@@ -911,6 +972,7 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
             aj.st = st;
             aj.cB = L.cB;
             aj.cC = L.cC;
+            aj.status = L.status;
             aj.inj = L.inj2.view();
             aj.q = rec_resid;
             aj.nq = nrec;
@@ -959,12 +1021,12 @@ int32_t wave_describe_plan(const wave_grid *g, const wave_tuning *tuning, int32_
     if (out == nullptr) return WAVE_EINVAL;
     Plan p;
     float *U[4] = {nullptr, nullptr, nullptr, nullptr};
-    if ((rc = resolve_plan(d, g, tuning, false, nullptr, nullptr, nullptr, U, nullptr, &p))) return rc;
+    if ((rc = resolve_plan(d, g, tuning, false, nullptr, nullptr, nullptr, U, nullptr, nullptr, &p))) return rc;
     out[0] = p.v->T;
     out[1] = p.v->BY;
     out[2] = p.chunk;
     out[3] = p.v->BZ;
-    out[4] = p.v->V;
+    out[4] = p.v->P;
     return WAVE_OK;
 }
 

@@ -162,7 +162,7 @@ def describe_plan(grid, tuning=None):
     t = tuning.c() if tuning is not None else None
     _check(_lib().wave_describe_plan(ctypes.byref(g), ctypes.byref(t) if t else None, out),
            "wave_describe_plan")
-    return dict(time_tile=out[0], tile_y=out[1], tile_x=out[2], tile_z=out[3], vec=out[4])
+    return dict(time_tile=out[0], tile_y=out[1], tile_x=out[2], tile_z=out[3], prefetch=out[4])
 
 
 # --------------------------------------------------------------------------

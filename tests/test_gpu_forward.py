@@ -137,7 +137,15 @@ def test_linearity_bitwise(wavelib, cuda):
     grid = wavelib.Grid(n, (inputs.H,) * 3, dt, nt, 8)
     d1, u1 = _run(wavelib, cuda, grid, m, damp, src, q, rec, 2)
     d2, u2 = _run(wavelib, cuda, grid, m, damp, src, 2 * q, rec, 2)
-    assert np.array_equal(u2, 2 * u1) and np.array_equal(d2, 2 * d1)
+    # Scaling by 2 commutes with every rounding except in the subnormal range,
+    # where the rounding step is absolute (2^-149): bitwise there, one ulp below.
+    # Values that passed through the subnormal range at any step carry that
+    # absolute rounding, so compare bitwise only well above it.
+    big = np.abs(2 * u1) >= 1e-30
+    assert np.array_equal(u2[big], 2 * u1[big])
+    assert np.abs(u2 - 2 * u1).max() <= 1e-36
+    db = np.abs(2 * d1) >= 1e-30
+    assert np.array_equal(d2[db], 2 * d1[db])
 
 
 def test_status_flags(wavelib, cuda):
@@ -182,14 +190,15 @@ def test_c2_full_grid_crop_vs_oracle(wavelib, cuda, oracle):
     sl = tuple(slice(lo[a], hi[a]) for a in range(3))
     keep = [i for i in range(len(p.rec_xyz))
             if all(lo[a] * inputs.H <= p.rec_xyz[i, a] <= (hi[a] - 2) * inputs.H for a in range(3))]
-    shift = np.array([lo[a] * inputs.H for a in range(3)], np.float32)
+    # shift the points in float64 so that x/h keeps its fraction exactly (an
+    # FP32 shift moves near-node fractions by ~1e-6 of a cell)
+    shift = np.array([lo[a] * float(np.float32(inputs.H)) for a in range(3)], np.float64)
     cgrid = wavelib.Grid(tuple(hi[a] - lo[a] for a in range(3)), p.h, p.dt, nt, p.space_order)
-    dref, uref, _ = _oracle(oracle, cgrid, p.m[sl], p.damp[sl], p.src_xyz - shift, p.src_q,
-                            p.rec_xyz[keep] - shift)
+    dref, uref, _ = _oracle(oracle, cgrid, p.m[sl], p.damp[sl],
+                            p.src_xyz.astype(np.float64) - shift, p.src_q,
+                            p.rec_xyz[keep].astype(np.float64) - shift)
     u = out[1][1][0]
     assert np.abs(u).sum() == pytest.approx(np.abs(u[sl]).sum(), rel=1e-12)  # support inside the crop
     assert _relerr(u[sl], uref[0]) <= TOL
-    # receiver coordinates shifted into the crop are rounded again in FP32, which
-    # moves their trilinear weights by ~1e-5 of a cell: compare at that level
     d = out[1][0][:, keep]
-    assert np.abs(d - dref).max() <= 1e-4 * np.abs(dref).max()
+    assert np.abs(d - dref).max() <= TOL * np.abs(dref).max()
