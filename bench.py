@@ -240,17 +240,22 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    # autotune once (outside any timed region), then fix the plan
+    # autotune once (outside any timed region), then fix the plans: the
+    # time-tiled sweep over every depth and shape, the untiled baseline over
+    # every T = 1 shape
+    def tuned(tune):
+        fwd(tune)
+        pl = wave.describe_plan(grid, tune)
+        return wave.Tuning(time_tile=pl["time_tile"], tile_y=pl["tile_y"], tile_x=pl["tile_x"],
+                           vec=pl["vec"])
     if args.time_tile:
-        tiled = wave.Tuning(time_tile=args.time_tile)
+        tiled = tuned(wave.Tuning(time_tile=args.time_tile, flags=wave.WAVE_AUTOTUNE_SHAPE))
     else:
-        fwd(wave.Tuning(time_tile=0))
-        plan = wave.describe_plan(grid, wave.Tuning(time_tile=0))
-        tiled = wave.Tuning(time_tile=plan["time_tile"], tile_y=plan["tile_y"],
-                            tile_x=plan["tile_x"])
+        tiled = tuned(wave.Tuning(time_tile=0))
+    untiled = tuned(wave.Tuning(time_tile=1, flags=wave.WAVE_AUTOTUNE_SHAPE))
     plan = wave.describe_plan(grid, tiled)
-    prof = wave.Tuning(tiled.time_tile, tiled.tile_y, tiled.tile_x, wave.WAVE_TIME_SWEEPS)
-    untiled = wave.Tuning(time_tile=1)
+    uplan = wave.describe_plan(grid, untiled)
+    prof = wave.Tuning(tiled.time_tile, tiled.tile_y, tiled.tile_x, wave.WAVE_TIME_SWEEPS, tiled.vec)
 
     # --- device-timed, inputs resident: tiled sweep (headline) -------------
     for _ in range(args.warmup):
@@ -324,7 +329,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": desc, "l2": "inputs larger than L2 (512 MiB per field)",
                        "time_tile": T, "tile_y": plan["tile_y"], "tile_z": plan["tile_z"],
-                       "tile_x": plan["tile_x"], "untiled_gpts": untiled_gpts,
+                       "tile_x": plan["tile_x"], "vec": plan["vec"], "untiled_gpts": untiled_gpts,
+                       "untiled_plan": uplan,
                        "tiled_over_untiled": value / untiled_gpts,
                        "parallelism": "replicas" if world > 1 else "single"},
             "e2e": {"value": world * pts * args.steps / (ms_e / 1e3) / 1e9, "unit": "GPts/s",

@@ -68,6 +68,8 @@ extern "C" {
 #define WAVE_ALLOW_UNSTABLE 1 /* skip the dt <= CFL check                              */
 #define WAVE_TIME_SWEEPS 2    /* record CUDA events around the sweep launches of the call
                                  (read back with wave_sweep_stats)                       */
+#define WAVE_AUTOTUNE_SHAPE 4 /* with time_tile = T >= 1: time the compiled variants of
+                                 depth T (tile, vec, x-chunk) and keep the fastest       */
 
 typedef struct wave_grid {
     int32_t n[3];        /* nx, ny, nz >= space_order + 1 each                     */
@@ -86,13 +88,15 @@ typedef struct wave_points {
 /* Sweep configuration.  Zero fields mean "choose automatically".
  *   time_tile : 0 = autotune, 1 = untiled sweep (one step per launch),
  *               T >= 2 = T steps per launch (time-tile depth, Sec. 4.2).
- *   tile_y    : output rows per block (0 = the default of the chosen variant).
+ *   tile_y    : output rows per block (0 = any compiled variant).
  *   tile_x    : x-chunk length streamed by one block (0 = default).
- *   flags     : WAVE_ALLOW_UNSTABLE. */
+ *   vec       : z points per thread, 2 or 4 (0 = any compiled variant).
+ *   flags     : WAVE_ALLOW_UNSTABLE | WAVE_TIME_SWEEPS. */
 typedef struct wave_tuning {
     int32_t time_tile;
     int32_t tile_y;
     int32_t tile_x;
+    int32_t vec;
     int32_t flags;
 } wave_tuning;
 
@@ -186,10 +190,17 @@ int32_t wave_status(const void *ws, void *stream);
  * WAVE_ECUDA. */
 int32_t wave_sweep_stats(float *ms, int32_t *launches, int32_t *steps);
 
-/* Sweep variant the library would run for grid g with `tuning`
- * (after autotuning if tuning->time_tile == 0 and it already ran):
- * out[0..4] = time_tile, tile_y, tile_x, tile_z, TMA prefetch distance.
- * Returns WAVE_OK or a WAVE_E* code. */
+/* Compiled sweep variants for `space_order`: writes up to `max` records of
+ * six int32 each to out (HOST) -- time_tile, tile_y, tile_z, vec, TMA
+ * prefetch distance, threads per block -- and returns the number of variants
+ * (negative WAVE_EINVAL on bad arguments). */
+int32_t wave_list_variants(int32_t space_order, int32_t *out, int32_t max);
+
+/* Sweep variant the library would run for grid g with `tuning` (the cached
+ * autotuned plan when tuning->time_tile == 0 and the autotuner already ran
+ * for this shape, otherwise the untiled default): out[0..5] = time_tile,
+ * tile_y, tile_x, tile_z, vec, TMA prefetch distance.  Returns WAVE_OK or a
+ * WAVE_E* code. */
 int32_t wave_describe_plan(const wave_grid *g, const wave_tuning *tuning, int32_t *out);
 
 #ifdef __cplusplus

@@ -14,9 +14,12 @@
 //  * In y and z, neighbouring blocks read overlapping halos of width R*T and
 //    recompute the shrinking halo of each stage, so blocks never wait on one
 //    another.
-//  * Staging (Blackwell TMA): one thread issues cp.async.bulk.tensor loads P
-//    iterations ahead into two shared-memory rings completed through
-//    mbarriers.  Ring U holds the 2R+1+P most recent level-n planes with their
+//  * Staging (Blackwell TMA, warp specialised): a producer warp issues
+//    cp.async.bulk.tensor loads up to P iterations ahead into two
+//    shared-memory rings; "full" mbarriers (transaction counts) tell the
+//    consumer threads a slot has landed and "empty" mbarriers (one arrival per
+//    consumer thread) tell the producer a slot may be refilled, so consumer
+//    warps are never held in lock step by the loads.  Ring U holds the 2R+1+P most recent level-n planes with their
 //    y/z halos, so stage 1 reads all its x, y and z neighbours from shared
 //    memory.  Ring K holds, per iteration, level n-1 and the per-point
 //    coefficients B, C of stage 1's plane; stage s reads the B, C that stage 1
@@ -25,16 +28,18 @@
 //    the grid with zeros; with B = C = 0 there, points outside the grid are
 //    computed as exactly 0.  This plays the role of the paper's min/max bounds
 //    (Sec. 4.2.2) without branches.
-//  * Stages s >= 2 keep a register queue of the 2R+1 x-planes of their input
-//    level per thread (V = 4 consecutive z points) and exchange the centre
-//    plane through shared memory for the y and z neighbours (double buffered,
-//    one barrier per plane).
+//  * Every stage keeps a register queue of the 2R+1 x-planes of its input
+//    level per thread (V consecutive z points per thread).  Stages s >= 2
+//    exchange their centre plane through shared memory for the y and z
+//    neighbours (double buffered, one named barrier among the consumer threads
+//    per plane); stage 1 reads them from ring U.
 //  * Sources are injected and receiver corners recorded inside the sweep (the
 //    imperfectly nested source/receiver loops the paper leaves open,
 //    Sec. 4.5.1 and Sec. 6.3.1).
-//  * Every mbarrier wait is bounded by %globaltimer; on expiry the block
-//    records WAVE_ETIMEOUT in the status word, finishes the plane, waits
-//    (bounded) for its copies in flight and returns.
+//  * Every mbarrier wait is bounded by %globaltimer; on expiry the thread
+//    records WAVE_ETIMEOUT in the status word and raises a block-wide abort
+//    flag; every thread leaves its loop at its next check, and the producer
+//    waits (bounded) for its copies in flight before the block exits.
 //
 // Bit-exactness: every point update is the same sequence of IEEE-rounded
 // operations (explicit __fmaf_rn / __fadd_rn / __fsub_rn / __fmul_rn, so no
@@ -49,7 +54,6 @@
 namespace wt {
 
 constexpr int kMaxR = 8;
-constexpr int kV = 4;                                   // z points per thread
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
 
 // Per-axis stencil coefficients c_k / h_a^2 in FP32; cc is the centre
@@ -104,38 +108,51 @@ struct SweepMaps {
     CUtensorMap u, um, B, C;
 };
 
-template <int R, int T, int BZ, int BY, int P>
+template <int R, int T, int V, int BZ, int BY, int P>
 struct SweepShape {
-    static constexpr int V = kV;
     static constexpr int RT = R * T;
     static constexpr int A0 = ((RT + 3) / 4) * 4;   // z halo, keeps 16-byte alignment
     static constexpr int W0 = BZ + 2 * A0;          // layout width (z points)
-    static constexpr int LZ = W0 / V;               // threads per layout row
     static constexpr int H0 = BY + 2 * RT;          // layout rows (y)
-    static constexpr int NT = LZ * H0;              // threads per block
-    static constexpr int RP = ((R + 3) / 4) * 4;    // z pad of ring-U rows
+    // Consumer threads cover only what stage 1 computes: rows [R, H0 - R) and
+    // the columns [ZL, ZR) of stage 1's z-range, V points per thread.
+    static constexpr int ZL = (A0 - (T - 1) * R) / 4 * 4;
+    static constexpr int ZR = (A0 + BZ + (T - 1) * R + 3) / 4 * 4;
+    static constexpr int LZ = (ZR - ZL) / V;        // threads per row
+    static constexpr int HT = H0 - 2 * R;           // thread rows
+    static constexpr int NT = LZ * HT;              // consumer threads per block
+    static constexpr int NTB = NT + 32;             // + one producer warp
+    static constexpr int RP = ((R + 3) / 4) * 4;    // z pad of ring-U rows / centre planes
     static constexpr int PW = W0 + 2 * RP;          // ring-U / centre-plane pitch
     static constexpr int HK = H0 - 2 * R;           // rows of ring-K boxes (from row R)
-    static constexpr int DU = 2 * R + 1 + P;        // ring-U depth (planes)
+    static constexpr int DU = R + 1 + P;            // ring-U depth (planes)
     static constexpr int DK = (T - 1) * R + 1 + P;  // ring-K depth (iterations)
-    static constexpr int NKB = 3;                   // ring-K boxes per iteration: um, B, C
+    static constexpr int DF = P + 1;                // iterations in flight (full barriers)
     static constexpr unsigned UBOX = PW * H0 * 4;   // bytes of one U box
-    static constexpr unsigned KBOX = W0 * HK * 4;   // bytes of one K box
+    static constexpr unsigned KBOX = W0 * HK * 4;   // bytes of one K box (um, B or C)
     static constexpr unsigned USLOT = (UBOX + 127) / 128 * 128;
     static constexpr unsigned KBOXP = (KBOX + 127) / 128 * 128;
-    static constexpr unsigned KSLOT = NKB * KBOXP;
+    static constexpr unsigned KSLOT = 3 * KBOXP;
+    static constexpr unsigned TXB = UBOX + 3 * KBOX; // bytes landing per iteration
     static constexpr int PLANE = PW * H0;           // centre plane (floats), stages >= 2
     static constexpr size_t OFF_K = (size_t)DU * USLOT;
     static constexpr size_t OFF_S = OFF_K + (size_t)DK * KSLOT;
     static constexpr size_t OFF_BAR = OFF_S + sizeof(float) * 2 * (T - 1) * PLANE;
-    static constexpr size_t OFF_P = OFF_BAR + 8 * (DU + DK) + 16;
+    static constexpr size_t OFF_P = OFF_BAR + 8 * (2 * DF + DU + DK) + 16;
     static constexpr size_t SMEM = OFF_P;           // + plane_start slices (smem_bytes)
     static size_t smem_bytes(int chunk) { return OFF_P + sizeof(int) * 2 * (chunk + 3 * RT + 2); }
+    // blocks per SM that shared memory admits (with ~4 KB of plane_start
+    // slices); the register budget per thread follows from it
+    static constexpr int MINB_SMEM = (int)((227 * 1024) / (SMEM + 4096));
+    static constexpr int MINB_THR = 2048 / NTB;
+    static constexpr int MINB = MINB_SMEM < 1 ? 1 : (MINB_SMEM < MINB_THR ? MINB_SMEM : MINB_THR);
+    static_assert(V == 2 || V == 4, "V must be 2 or 4");
     static_assert(BZ % 4 == 0, "BZ must keep 16-byte alignment");
-    static_assert(NT <= 1024, "too many threads per block");
+    static_assert(NT % 32 == 0, "consumer threads must fill whole warps (named barrier)");
+    static_assert(NTB <= 1024, "too many threads per block");
     static_assert(R >= 1 && R <= kMaxR, "radius out of range");
     static_assert(PW <= 256 && H0 <= 256, "TMA box dimension above 256");
-    static_assert(UBOX < (1u << 20) && NKB * KBOX < (1u << 20), "mbarrier tx count");
+    static_assert(TXB < (1u << 20), "mbarrier tx count");
     static_assert(SMEM <= 220 * 1024, "shared memory above the per-block limit");
 };
 
@@ -158,6 +175,28 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
                  "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Barrier 1 over the consumer threads only (the producer warp is not part of
+// it); returns the OR of `flag` over them, so every consumer takes the same
+// decision.
+__device__ __forceinline__ bool consumer_sync_any(int nthreads, bool flag)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)flag), "r"(nthreads)
+        : "memory");
+    return r != 0;
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
@@ -200,45 +239,66 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-__device__ __forceinline__ void ld4(float (&d)[4], const float *p)
+template <int V>
+__device__ __forceinline__ void ldv(float (&d)[V], const float *p)
 {
-    float4 t = *reinterpret_cast<const float4 *>(p);
-    d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
+    if constexpr (V == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
+    } else {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        d[0] = t.x; d[1] = t.y;
+    }
 }
 
-__device__ __forceinline__ void ldg4(float (&d)[4], const float *p)
+template <int V>
+__device__ __forceinline__ void ldgv(float (&d)[V], const float *p)
 {
-    float4 t = __ldg(reinterpret_cast<const float4 *>(p));
-    d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
+    if constexpr (V == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
+    } else {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        d[0] = t.x; d[1] = t.y;
+    }
 }
 
-__device__ __forceinline__ void st4(float *p, const float (&s)[4])
+template <int V>
+__device__ __forceinline__ void stv(float *p, const float (&s)[V])
 {
-    *reinterpret_cast<float4 *>(p) = make_float4(s[0], s[1], s[2], s[3]);
+    if constexpr (V == 4)
+        *reinterpret_cast<float4 *>(p) = make_float4(s[0], s[1], s[2], s[3]);
+    else
+        *reinterpret_cast<float2 *>(p) = make_float2(s[0], s[1]);
 }
 
-template <int R, int T, int BZ, int BY, int P>
-__global__ void __launch_bounds__(SweepShape<R, T, BZ, BY, P>::NT, 1)
+template <int R, int T, int V, int BZ, int BY, int P>
+__global__ void __launch_bounds__(SweepShape<R, T, V, BZ, BY, P>::NTB,
+                                  SweepShape<R, T, V, BZ, BY, P>::MINB)
 sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stencil st,
              const __grid_constant__ SweepMaps mp)
 {
-    using S = SweepShape<R, T, BZ, BY, P>;
-    constexpr int V = S::V;
+    using S = SweepShape<R, T, V, BZ, BY, P>;
     constexpr int QL = 2 * R + 1;
-    constexpr int QS = T > 1 ? T - 1 : 1;  // queues of stages 2..T
-    constexpr int ZW = V + 2 * S::RP;      // z window per thread (floats)
+    constexpr int ZW = V + 2 * S::RP;  // z window per thread (floats)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *ringU = reinterpret_cast<float *>(smem_raw);
     unsigned char *ringK = smem_raw + S::OFF_K;
     float *splane = reinterpret_cast<float *>(smem_raw + S::OFF_S);  // [T-1][2][PLANE]
-    uint64_t *barU = reinterpret_cast<uint64_t *>(smem_raw + S::OFF_BAR);
-    uint64_t *barK = barU + S::DU;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(barK + S::DK);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + S::OFF_BAR);  // per iteration in flight
+    uint64_t *empF = full + S::DF;   // consumers have waited on full[] (one per iteration in flight)
+    uint64_t *empU = empF + S::DF;   // per ring-U slot: released by all consumers
+    uint64_t *empK = empU + S::DU;   // per ring-K slot: released by all consumers
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(empK + S::DK);
     int *pinj = reinterpret_cast<int *>(smem_raw + S::OFF_P);
 
+    if (blockDim.x != S::NTB) {  // launched with the wrong shape: report, do nothing
+        if (threadIdx.x == 0 && blockIdx.x == 0) atomicMin(a.status, -1 /* WAVE_EINVAL */);
+        return;
+    }
     const int tid = threadIdx.x;
-    const int lane = tid % S::LZ;
-    const int row = tid / S::LZ;
+    const int col = S::ZL + (tid % S::LZ) * V;  // layout column of this thread's V points
+    const int row = R + tid / S::LZ;            // layout row
     int b = blockIdx.x;
     const int tzi = b % a.tiles_z;
     b /= a.tiles_z;
@@ -248,14 +308,13 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
     const int X1 = min(X0 + a.chunk, a.nx);
     const int gz0 = tzi * BZ - S::A0;  // global z of layout column 0
     const int gy0 = tyi * BY - S::RT;  // global y of layout row 0
-    const int gz = gz0 + lane * V;
+    const int gz = gz0 + col;
     const int gy = gy0 + row;
     const bool in_yz = gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz;
-    const bool inner = in_yz && row >= S::RT && row < S::RT + BY &&
-                       lane * V >= S::A0 && lane * V < S::A0 + BZ;
+    const bool inner = in_yz && row >= S::RT && row < S::RT + BY && col >= S::A0 && col < S::A0 + BZ;
     const long long yz = in_yz ? (long long)gy * a.nz + gz : 0;
-    const int ownU = row * S::PW + S::RP + lane * V;   // in a U box / centre plane
-    const int ownK = (row - R) * S::W0 + lane * V;     // in a K box (rows >= R only)
+    const int ownU = row * S::PW + S::RP + col;        // in a U box / centre plane
+    const int ownK = (row - R) * S::W0 + col;          // in a K box
     const int niter = (X1 - X0) + 2 * S::RT;
     const int c00 = X0 - S::RT;                        // plane of level n at iteration 0
 
@@ -263,164 +322,159 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
     const int pbase = X0 - 2 * S::RT;
     const int plen = (X1 - X0) + 3 * S::RT + 2;
     int *prec = pinj + plen;
-    for (int k = tid; k < plen; k += S::NT) {
+    for (int k = tid; k < plen; k += S::NTB) {
         const int c = min(max(pbase + k, 0), a.nx);
         pinj[k] = a.inj.plane_start != nullptr ? a.inj.plane_start[c] : 0;
         prec[k] = a.rec.plane_start != nullptr ? a.rec.plane_start[c] : 0;
     }
-    for (int k = tid; k < 2 * (T - 1) * S::PLANE; k += S::NT) splane[k] = 0.f;
+    for (int k = tid; k < 2 * (T - 1) * S::PLANE; k += S::NTB) splane[k] = 0.f;
     if (tid == 0) {
-        for (int k = 0; k < S::DU + S::DK; ++k) mbar_init(barU + k, 1);
+        for (int k = 0; k < S::DF; ++k) mbar_init(full + k, 1);
+        for (int k = 0; k < S::DF + S::DU + S::DK; ++k) mbar_init(empF + k, S::NT);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    // producer (thread 0): loads of iteration j into U slot j % DU, K slot j % DK
-    auto issue = [&](int j) {
-        const int c0 = c00 + j;
-        uint64_t *bu = barU + j % S::DU;
-        mbar_expect_tx(bu, S::UBOX);
-        tma_load_3d(ringU + (size_t)(j % S::DU) * (S::USLOT / 4), &mp.u, gz0 - S::RP, gy0, c0, bu);
-        uint64_t *bk = barK + j % S::DK;
-        unsigned char *kslot = ringK + (size_t)(j % S::DK) * S::KSLOT;
-        mbar_expect_tx(bk, S::NKB * S::KBOX);
-        tma_load_3d(kslot, &mp.um, gz0, gy0 + R, c0 - R, bk);
-        tma_load_3d(kslot + S::KBOXP, &mp.B, gz0, gy0 + R, c0 - R, bk);
-        tma_load_3d(kslot + 2 * S::KBOXP, &mp.C, gz0, gy0 + R, c0 - R, bk);
-    };
-    if (tid == 0)
-        for (int j = 0; j < P && j < niter; ++j) issue(j);
+    if (tid >= S::NT) {
+        // ------------------------------ producer warp ------------------------------
+        if (tid == S::NT) {
+            int ju = 0, jk = 0, jf = 0;  // slot of iteration j in ring U / ring K / full barriers
+            int ru = 0, rk = 0, rf = 0;  // round of the slot: iteration j is its (r+1)-th use
+            int j = 0;
+            for (; j < niter; ++j) {
+                if (*abort_flag) break;
+                // Before its (r+1)-th use a slot must have been released r times:
+                // empF -- every consumer has waited on the phase of full[jf] that
+                // this iteration re-arms, so at most DF iterations are ever in
+                // flight; empU / empK -- every consumer is done reading the slot.
+                bool ok = true;
+                if (rf > 0) ok = mbar_wait_bounded(empF + jf, (uint32_t)((rf - 1) & 1));
+                if (ok && ru > 0) ok = mbar_wait_bounded(empU + ju, (uint32_t)((ru - 1) & 1));
+                if (ok && rk > 0) ok = mbar_wait_bounded(empK + jk, (uint32_t)((rk - 1) & 1));
+                if (!ok) {
+                    *abort_flag = 1;
+                    atomicMin(a.status, -4 /* WAVE_ETIMEOUT */);
+                    break;
+                }
+                const int c0 = c00 + j;
+                uint64_t *bf = full + jf;
+                mbar_expect_tx(bf, S::TXB);
+                tma_load_3d(ringU + (size_t)ju * (S::USLOT / 4), &mp.u, gz0 - S::RP, gy0, c0, bf);
+                unsigned char *kslot = ringK + (size_t)jk * S::KSLOT;
+                tma_load_3d(kslot, &mp.um, gz0, gy0 + R, c0 - R, bf);
+                tma_load_3d(kslot + S::KBOXP, &mp.B, gz0, gy0 + R, c0 - R, bf);
+                tma_load_3d(kslot + 2 * S::KBOXP, &mp.C, gz0, gy0 + R, c0 - R, bf);
+                if (++ju == S::DU) { ju = 0; ++ru; }
+                if (++jk == S::DK) { jk = 0; ++rk; }
+                if (++jf == S::DF) { jf = 0; ++rf; }
+            }
+            // make sure no copy into this block's shared memory is still in
+            // flight (only the last DF issued iterations can be)
+            for (int i = (j > S::DF ? j - S::DF : 0); i < j; ++i)
+                mbar_wait_bounded(full + i % S::DF, (uint32_t)((i / S::DF) & 1));
+        }
+        return;
+    }
 
-    float q[QS][QL][V];
+    // ------------------------------ consumer threads ------------------------------
+    // q[0]: level n (stage 1's input), q[s-1]: level n+s-1 (stage s's input)
+    float q[T][QL][V];
 #pragma unroll
-    for (int s = 0; s < QS; ++s)
+    for (int s = 0; s < T; ++s)
 #pragma unroll
         for (int k = 0; k < QL; ++k)
 #pragma unroll
             for (int j = 0; j < V; ++j) q[s][k][j] = 0.f;
 
-    // U slot of iteration j (negative j: slots not yet filled, read only by
-    // computations whose results are never used)
-    auto uslot = [&](int j) -> const float * {
-        const int k = ((j % S::DU) + S::DU) % S::DU;
-        return ringU + (size_t)k * (S::USLOT / 4);
-    };
-
+    int su = 0, sk = 0, sf = 0;  // ring slots of the current iteration
+    uint32_t pf = 0;             // parity of the current full barrier phase
     int cur = 0;
-    int it = 0;
-    for (; it < niter; ++it) {
+    for (int it = 0; it < niter; ++it) {
         const int c0 = c00 + it;
-        if (tid == 0 && it + P < niter && !*abort_flag) issue(it + P);
-        bool ok = mbar_wait_bounded(barU + it % S::DU, (uint32_t)((it / S::DU) & 1));
-        ok = mbar_wait_bounded(barK + it % S::DK, (uint32_t)((it / S::DK) & 1)) && ok;
-        if (!ok) {
+        if (!mbar_wait_bounded(full + sf, pf)) {
             *abort_flag = 1;
             atomicMin(a.status, -4 /* WAVE_ETIMEOUT */);
+            if (T == 1) break;  // T > 1: decided at the consumer barrier
         }
-        // K slot of iteration j (stage s reads iteration it - (s-1)R)
-        auto kslot_of = [&](int j) -> const unsigned char * {
-            const int k = ((j % S::DK) + S::DK) % S::DK;
-            return ringK + (size_t)k * S::KSLOT;
-        };
-        const unsigned char *kslot = kslot_of(it);
+        mbar_arrive(empF + sf);  // this thread is past this phase of full[sf]
+        {
+            // level n of plane c0 enters stage 1's queue
+            float v[V];
+            ldv<V>(v, ringU + (size_t)su * (S::USLOT / 4) + ownU);
+#pragma unroll
+            for (int k = 0; k < QL - 1; ++k)
+#pragma unroll
+                for (int j = 0; j < V; ++j) q[0][k][j] = q[0][k + 1][j];
+#pragma unroll
+            for (int j = 0; j < V; ++j) q[0][QL - 1][j] = v[j];
+        }
+        const int suc = su - R < 0 ? su - R + S::DU : su - R;  // U slot of plane c0 - R
+        const unsigned char *kslot = ringK + (size_t)sk * S::KSLOT;
 
 #pragma unroll
         for (int s = 1; s <= T; ++s) {
             const int cs = c0 - s * R;  // plane computed by stage s
             const bool rowok = row >= s * R && row < S::H0 - s * R;
             const long long pidx = (long long)cs * a.sx + yz;
-            float un[V], dd[V], lap[V], cBv[V], cCv[V], u0[V], up[V];
+            float un[V], dd[V], lap[V], cBv[V], cCv[V], up[V];
 #pragma unroll
-            for (int j = 0; j < V; ++j) {
-                un[j] = 0.f; dd[j] = 0.f; lap[j] = 0.f; cBv[j] = 0.f; cCv[j] = 0.f;
-                u0[j] = 0.f; up[j] = 0.f;
-            }
+            for (int j = 0; j < V; ++j) { un[j] = 0.f; dd[j] = 0.f; }
             if (rowok) {
-                const unsigned char *ks = kslot_of(it - (s - 1) * R);
-                ld4(cBv, reinterpret_cast<const float *>(ks + S::KBOXP) + ownK);
-                ld4(cCv, reinterpret_cast<const float *>(ks + 2 * S::KBOXP) + ownK);
-                if (s == 1) {
-                    // stage 1: every neighbour from ring U (centre plane c0 - R)
-                    const float *Pc = uslot(it - R);
-                    float zz[ZW / V][V];
+                const int kk = sk - (s - 1) * R;
+                const unsigned char *ks = ringK + (size_t)(kk < 0 ? kk + S::DK : kk) * S::KSLOT;
+                ldv<V>(cBv, reinterpret_cast<const float *>(ks + S::KBOXP) + ownK);
+                ldv<V>(cCv, reinterpret_cast<const float *>(ks + 2 * S::KBOXP) + ownK);
+                // centre plane of stage s: ring U (s = 1) or the exchanged plane
+                const float *Pc = s == 1 ? ringU + (size_t)suc * (S::USLOT / 4)
+                                         : splane + ((s - 2) * 2 + cur) * S::PLANE;
+                float zz[ZW / V][V];
 #pragma unroll
-                    for (int j = 0; j < ZW / V; ++j) ld4(zz[j], Pc + ownU - S::RP + j * V);
+                for (int j = 0; j < ZW / V; ++j) ldv<V>(zz[j], Pc + ownU - S::RP + j * V);
 #pragma unroll
-                    for (int j = 0; j < V; ++j) {
-                        u0[j] = zz[S::RP / V][j];
-                        lap[j] = __fmul_rn(st.cc, u0[j]);
-                    }
+                for (int j = 0; j < V; ++j) lap[j] = __fmul_rn(st.cc, q[s - 1][R][j]);
 #pragma unroll
-                    for (int k = 1; k <= R; ++k) {
-                        float xp[V], xm[V], yp[V], ym[V];
-                        ld4(xp, uslot(it - R + k) + ownU);
-                        ld4(xm, uslot(it - R - k) + ownU);
-                        ld4(yp, Pc + ownU + k * S::PW);
-                        ld4(ym, Pc + ownU - k * S::PW);
-#pragma unroll
-                        for (int j = 0; j < V; ++j) {
-                            lap[j] = __fmaf_rn(st.cx[k], __fadd_rn(xp[j], xm[j]), lap[j]);
-                            lap[j] = __fmaf_rn(st.cy[k], __fadd_rn(yp[j], ym[j]), lap[j]);
-                            lap[j] = __fmaf_rn(st.cz[k],
-                                               __fadd_rn(zz[(S::RP + j + k) / V][(S::RP + j + k) % V],
-                                                         zz[(S::RP + j - k) / V][(S::RP + j - k) % V]),
-                                               lap[j]);
-                        }
-                    }
-                    ld4(up, reinterpret_cast<const float *>(kslot) + ownK);  // level n-1
-                } else {
-                    // stage s >= 2: x from the register queue, y/z from the centre plane
-                    const int qs = s - 2;
-                    const float *Pc = splane + (qs * 2 + cur) * S::PLANE;
-                    float zz[ZW / V][V];
-#pragma unroll
-                    for (int j = 0; j < ZW / V; ++j) ld4(zz[j], Pc + ownU - S::RP + j * V);
+                for (int k = 1; k <= R; ++k) {
+                    float yp[V], ym[V];
+                    ldv<V>(yp, Pc + ownU + k * S::PW);
+                    ldv<V>(ym, Pc + ownU - k * S::PW);
 #pragma unroll
                     for (int j = 0; j < V; ++j) {
-                        u0[j] = q[qs][R][j];
-                        lap[j] = __fmul_rn(st.cc, u0[j]);
-                    }
-#pragma unroll
-                    for (int k = 1; k <= R; ++k) {
-                        float yp[V], ym[V];
-                        ld4(yp, Pc + ownU + k * S::PW);
-                        ld4(ym, Pc + ownU - k * S::PW);
-#pragma unroll
-                        for (int j = 0; j < V; ++j) {
-                            lap[j] = __fmaf_rn(st.cx[k], __fadd_rn(q[qs][R + k][j], q[qs][R - k][j]),
-                                               lap[j]);
-                            lap[j] = __fmaf_rn(st.cy[k], __fadd_rn(yp[j], ym[j]), lap[j]);
-                            lap[j] = __fmaf_rn(st.cz[k],
-                                               __fadd_rn(zz[(S::RP + j + k) / V][(S::RP + j + k) % V],
-                                                         zz[(S::RP + j - k) / V][(S::RP + j - k) % V]),
-                                               lap[j]);
-                        }
-                    }
-                    if (s == 2) {
-                        ld4(up, uslot(it - 2 * R) + ownU);  // level n on plane c0 - 2R
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < V; ++j) up[j] = q[s > 2 ? s - 3 : 0][0][j];
+                        lap[j] = __fmaf_rn(st.cx[k], __fadd_rn(q[s - 1][R + k][j], q[s - 1][R - k][j]),
+                                           lap[j]);
+                        lap[j] = __fmaf_rn(st.cy[k], __fadd_rn(yp[j], ym[j]), lap[j]);
+                        lap[j] = __fmaf_rn(st.cz[k],
+                                           __fadd_rn(zz[(S::RP + j + k) / V][(S::RP + j + k) % V],
+                                                     zz[(S::RP + j - k) / V][(S::RP + j - k) % V]),
+                                           lap[j]);
                     }
                 }
+                if (s == 1) {
+                    ldv<V>(up, reinterpret_cast<const float *>(kslot) + ownK);  // level n-1
+                } else {
 #pragma unroll
-                for (int j = 0; j < V; ++j)
-                    un[j] = __fmaf_rn(cCv[j], lap[j], __fmaf_rn(cBv[j], __fsub_rn(u0[j], up[j]), u0[j]));
+                    for (int j = 0; j < V; ++j) up[j] = q[s - 2][0][j];  // level n+s-2 on plane cs
+                }
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    const float u0 = q[s - 1][R][j];
+                    un[j] = __fmaf_rn(cCv[j], lap[j], __fmaf_rn(cBv[j], __fsub_rn(u0, up[j]), u0));
+                }
                 const bool plane_in = cs >= 0 && cs < a.nx;
                 if (a.dstore != nullptr && in_yz && plane_in) {
                     // u^{n+1} - 2u^n + u^{n-1} = E (u^n - u^{n-1}) + C (L u^n + f^n)
                     float e[V];
-                    ldg4(e, a.cE + pidx);
+                    ldgv<V>(e, a.cE + pidx);
 #pragma unroll
                     for (int j = 0; j < V; ++j)
-                        dd[j] = __fmaf_rn(cCv[j], lap[j], __fmul_rn(e[j], __fsub_rn(u0[j], up[j])));
+                        dd[j] = __fmaf_rn(cCv[j], lap[j], __fmul_rn(e[j], __fsub_rn(q[s - 1][R][j], up[j])));
                 }
                 // point sources: f = sum_s w q_s (ascending source order), u += C f
                 const int e0 = pinj[cs - pbase], e1 = pinj[cs - pbase + 1];
                 if (e1 > e0 && in_yz) {
                     // each grid point appears at most once in the table, but up
-                    // to V table points can fall in this thread's V z-points
+                    // to V table points can fall in this thread's V z-points;
+                    // scalar selects keep fv[] in registers
                     float fv[V];
                     unsigned hits = 0u;
 #pragma unroll
@@ -434,46 +488,48 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                                 f = __fmaf_rn(a.inj.w[itm], a.q[qrow + a.inj.item[itm]], f);
                             const int jj = pt.y - gz;
 #pragma unroll
-                            for (int j = 0; j < V; ++j)
-                                if (jj == j) fv[j] = f;
+                            for (int j = 0; j < V; ++j) fv[j] = jj == j ? f : fv[j];
                             hits |= 1u << jj;
                         }
                     }
-                    if (hits) {
 #pragma unroll
-                        for (int j = 0; j < V; ++j)
-                            if (hits & (1u << j)) {
-                                un[j] = __fmaf_rn(cCv[j], fv[j], un[j]);
-                                dd[j] = __fmaf_rn(cCv[j], fv[j], dd[j]);
-                            }
-                    }
+                    for (int j = 0; j < V; ++j)
+                        if (hits & (1u << j)) {
+                            un[j] = __fmaf_rn(cCv[j], fv[j], un[j]);
+                            dd[j] = __fmaf_rn(cCv[j], fv[j], dd[j]);
+                        }
                 }
             }
             const bool own_pt = inner && cs >= X0 && cs < X1;
             if (own_pt) {
                 const int e0 = prec[cs - pbase], e1 = prec[cs - pbase + 1];
-                for (int e = e0; e < e1; ++e) {
-                    const int4 pt = a.rec.pts[e];
-                    if (pt.x == gy && pt.y >= gz && pt.y < gz + V) {
-                        float v = 0.f;
+                if (e1 > e0) {
+                    float rv[V];
 #pragma unroll
-                        for (int j = 0; j < V; ++j)
-                            if (pt.y - gz == j) v = un[j];
-                        const long long crow = (long long)(a.c_row0 + a.c_dir * (s - 1)) * a.nslot;
-                        for (int itm = pt.z; itm < pt.w; ++itm) a.corner[crow + a.rec.item[itm]] = v;
+                    for (int j = 0; j < V; ++j) rv[j] = un[j];
+                    for (int e = e0; e < e1; ++e) {
+                        const int4 pt = a.rec.pts[e];
+                        if (pt.x == gy && pt.y >= gz && pt.y < gz + V) {
+                            const int jj = pt.y - gz;
+                            float v = rv[0];
+#pragma unroll
+                            for (int j = 1; j < V; ++j) v = jj == j ? rv[j] : v;
+                            const long long crow = (long long)(a.c_row0 + a.c_dir * (s - 1)) * a.nslot;
+                            for (int itm = pt.z; itm < pt.w; ++itm) a.corner[crow + a.rec.item[itm]] = v;
+                        }
                     }
                 }
-                if (s == T) st4(a.out_hi + pidx, un);
-                if (T >= 2 && s == T - 1) st4(a.out_lo + pidx, un);
+                if (s == T) stv<V>(a.out_hi + pidx, un);
+                if (T >= 2 && s == T - 1) stv<V>(a.out_lo + pidx, un);
                 if (a.dstore != nullptr)
-                    st4(a.dstore + (a.d_row0 + (long long)a.d_dir * (s - 1)) * a.npad + pidx, dd);
+                    stv<V>(a.dstore + (a.d_row0 + (long long)a.d_dir * (s - 1)) * a.npad + pidx, dd);
                 if (a.gacc != nullptr) {
                     float dl[V], g[V];
-                    ldg4(dl, a.dload + (a.l_row0 + (long long)a.l_dir * (s - 1)) * a.npad + pidx);
-                    ld4(g, a.gacc + pidx);
+                    ldgv<V>(dl, a.dload + (a.l_row0 + (long long)a.l_dir * (s - 1)) * a.npad + pidx);
+                    ldv<V>(g, a.gacc + pidx);
 #pragma unroll
                     for (int j = 0; j < V; ++j) g[j] = __fmaf_rn(un[j], dl[j], g[j]);
-                    st4(a.gacc + pidx, g);
+                    stv<V>(a.gacc + pidx, g);
                 }
             }
             if (s < T) {
@@ -481,26 +537,32 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
 #pragma unroll
                 for (int k = 0; k < QL - 1; ++k)
 #pragma unroll
-                    for (int j = 0; j < V; ++j) q[s - 1][k][j] = q[s - 1][k + 1][j];
+                    for (int j = 0; j < V; ++j) q[s][k][j] = q[s][k + 1][j];
 #pragma unroll
-                for (int j = 0; j < V; ++j) q[s - 1][QL - 1][j] = un[j];
+                for (int j = 0; j < V; ++j) q[s][QL - 1][j] = un[j];
             }
         }
 
-        // centres of stages >= 2 for the next iteration
-#pragma unroll
-        for (int s = 2; s <= T; ++s)
-            st4(splane + ((s - 2) * 2 + (cur ^ 1)) * S::PLANE + ownU, q[s - 2][R + 1]);
-        __syncthreads();
-        cur ^= 1;
-        if (*abort_flag) break;
-    }
-    if (it < niter && tid == 0) {
-        // aborted: wait (bounded) for the copies still in flight before exiting
-        for (int j = it + 1; j < niter && j <= it + P; ++j) {
-            mbar_wait_bounded(barU + j % S::DU, (uint32_t)((j / S::DU) & 1));
-            mbar_wait_bounded(barK + j % S::DK, (uint32_t)((j / S::DK) & 1));
+        // release the ring slots read for the last time: U slot of plane c0 - R
+        // (iteration it - R), K slot read by stage T (iteration it - (T-1)R).
+        // Slots of iterations before 0 were never filled and are not released.
+        if (it >= R) mbar_arrive(empU + suc);
+        if (it >= (T - 1) * R) {
+            const int kk = sk - (T - 1) * R;
+            mbar_arrive(empK + (kk < 0 ? kk + S::DK : kk));
         }
+        if constexpr (T > 1) {
+            // centres of stages >= 2 for the next iteration
+#pragma unroll
+            for (int s = 2; s <= T; ++s)
+                stv<V>(splane + ((s - 2) * 2 + (cur ^ 1)) * S::PLANE + ownU, q[s - 1][R + 1]);
+            const bool stop = consumer_sync_any(S::NT, *abort_flag != 0);
+            cur ^= 1;
+            if (stop) break;
+        }
+        if (++su == S::DU) su = 0;
+        if (++sk == S::DK) sk = 0;
+        if (++sf == S::DF) { sf = 0; pf ^= 1u; }
     }
 }
 

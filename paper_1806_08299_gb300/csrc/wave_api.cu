@@ -418,13 +418,14 @@ int default_chunk(const Dims &d, const SweepVariant *v)
     return best;
 }
 
-// Pick the variant for radius R with time tile T (and tile_y if given).
-const SweepVariant *find_variant(int R, int T, int tile_y)
+// Pick the variant for radius R with time tile T (and tile_y / vec if given).
+const SweepVariant *find_variant(int R, int T, int tile_y, int vec)
 {
     const SweepVariant *vs;
     const int nv = variants_for(R, &vs);
     for (int i = 0; i < nv; ++i)
-        if (vs[i].T == T && (tile_y == 0 || vs[i].BY == tile_y)) return &vs[i];
+        if (vs[i].T == T && (tile_y == 0 || vs[i].BY == tile_y) && (vec == 0 || vs[i].V == vec))
+            return &vs[i];
     return nullptr;
 }
 
@@ -440,20 +441,20 @@ const SweepVariant *fallback_variant(int R, int limit)
 }
 
 struct TuneKey {
-    int nx, ny, nz, so, dev;
+    int nx, ny, nz, so, dev, T;  // T = 0: any depth
     bool operator<(const TuneKey &o) const
     {
-        return std::tie(nx, ny, nz, so, dev) < std::tie(o.nx, o.ny, o.nz, o.so, o.dev);
+        return std::tie(nx, ny, nz, so, dev, T) < std::tie(o.nx, o.ny, o.nz, o.so, o.dev, o.T);
     }
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, Plan> g_tune_cache;
 
-TuneKey tune_key(const Dims &d, int so)
+TuneKey tune_key(const Dims &d, int so, int T)
 {
     int dev = 0;
     cudaGetDevice(&dev);
-    return TuneKey{d.nx, d.ny, d.nz, so, dev};
+    return TuneKey{d.nx, d.ny, d.nz, so, dev, T};
 }
 
 // ---------------------------------------------------------------------------
@@ -609,7 +610,7 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
 // points) and cache the fastest: the paper's auto-tuner extended to the time
 // tile (Sec. 4.4, Sec. 5.2.2), here over (T, tile, x-chunk).
 int autotune(const Dims &d, const Stencil &st, const float *cB, const float *cC, float *const U[4],
-             int *status, int R, cudaStream_t stream, Plan *out)
+             int *status, int R, int T_only, cudaStream_t stream, Plan *out)
 {
     const SweepVariant *vs;
     const int nv = variants_for(R, &vs);
@@ -620,6 +621,7 @@ int autotune(const Dims &d, const Stencil &st, const float *cB, const float *cC,
     Plan bestp;
     for (int i = 0; i < nv; ++i) {
         const SweepVariant *v = &vs[i];
+        if (T_only > 0 && v->T != T_only) continue;
         std::vector<int> chunks = {default_chunk(d, v)};
         for (int c : {d.nx, (d.nx + 1) / 2, (d.nx + 3) / 4, 128, 64})
             if (c >= 4 * v->R * v->T && c <= d.nx &&
@@ -670,15 +672,17 @@ int resolve_plan(const Dims &d, const wave_grid *g, const wave_tuning *t, bool m
 {
     const int R = g->space_order / 2;
     const int T = t ? t->time_tile : 0;
-    if (T < 0 || (t && (t->tile_x < 0 || t->tile_y < 0))) return WAVE_EINVAL;
-    if (T > 0) {
-        const SweepVariant *v = find_variant(R, T, t ? t->tile_y : 0);
+    if (T < 0 || (t && (t->tile_x < 0 || t->tile_y < 0 || t->vec < 0))) return WAVE_EINVAL;
+    const bool shape_tune = T > 0 && t && (t->flags & WAVE_AUTOTUNE_SHAPE);
+    if (shape_tune && fallback_variant(R, T) == nullptr) return WAVE_EUNSUPPORTED;
+    if (T > 0 && !shape_tune) {
+        const SweepVariant *v = find_variant(R, T, t ? t->tile_y : 0, t ? t->vec : 0);
         if (v == nullptr) return WAVE_EUNSUPPORTED;
         out->v = v;
         out->chunk = (t && t->tile_x > 0) ? std::min(t->tile_x, d.nx) : default_chunk(d, v);
         return WAVE_OK;
     }
-    const TuneKey key = tune_key(d, g->space_order);
+    const TuneKey key = tune_key(d, g->space_order, T);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -688,12 +692,13 @@ int resolve_plan(const Dims &d, const wave_grid *g, const wave_tuning *t, bool m
         }
     }
     if (!may_tune) {
-        out->v = fallback_variant(R, 1);
+        out->v = shape_tune ? find_variant(R, T, 0, 0) : fallback_variant(R, 1);
+        if (out->v == nullptr) return WAVE_EUNSUPPORTED;
         out->chunk = default_chunk(d, out->v);
         return WAVE_OK;
     }
     Plan p;
-    const int rc = autotune(d, *st, cB, cC, U, status, R, stream, &p);
+    const int rc = autotune(d, *st, cB, cC, U, status, R, T, stream, &p);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = p;
@@ -1013,6 +1018,24 @@ int32_t wave_sweep_stats(float *ms, int32_t *launches, int32_t *steps)
     return WAVE_OK;
 }
 
+int32_t wave_list_variants(int32_t space_order, int32_t *out, int32_t max)
+{
+    if (space_order < 2 || space_order > 16 || space_order % 2 || max < 0 || (max > 0 && !out))
+        return WAVE_EINVAL;
+    const SweepVariant *vs;
+    const int nv = variants_for(space_order / 2, &vs);
+    for (int i = 0; i < nv && i < max; ++i) {
+        int32_t *o = out + 6 * i;
+        o[0] = vs[i].T;
+        o[1] = vs[i].BY;
+        o[2] = vs[i].BZ;
+        o[3] = vs[i].V;
+        o[4] = vs[i].P;
+        o[5] = vs[i].threads;
+    }
+    return nv;
+}
+
 int32_t wave_describe_plan(const wave_grid *g, const wave_tuning *tuning, int32_t *out)
 {
     Dims d;
@@ -1026,7 +1049,8 @@ int32_t wave_describe_plan(const wave_grid *g, const wave_tuning *tuning, int32_
     out[1] = p.v->BY;
     out[2] = p.chunk;
     out[3] = p.v->BZ;
-    out[4] = p.v->P;
+    out[4] = p.v->V;
+    out[5] = p.v->P;
     return WAVE_OK;
 }
 

@@ -10,7 +10,7 @@ namespace wt {
 
 // One compiled sweep variant, its layout and its launcher.
 struct SweepVariant {
-    int R, T, BZ, BY, P, threads;
+    int R, T, V, BZ, BY, P, threads;  // threads: consumers + the producer warp
     int W0, H0, PW, HK;  // layout width/rows, ring-U pitch, ring-K rows
     size_t smem;         // shared memory without the plane_start slices
     cudaError_t (*launch)(int nblocks, cudaStream_t stream, const SweepArgs &a, const Stencil &st,
@@ -40,31 +40,32 @@ cudaError_t launch_unpad(const float *src, int nx, int ny, int nz, int nzp, floa
 cudaError_t launch_gather(const float *corner, const float *w, int rows, int npts, int row_dir,
                           float *out, cudaStream_t s);
 
-template <int R, int T, int BZ, int BY, int P>
+template <int R, int T, int V, int BZ, int BY, int P>
 cudaError_t launch_sweep(int nblocks, cudaStream_t stream, const SweepArgs &a, const Stencil &st,
                          const SweepMaps &m)
 {
-    using S = SweepShape<R, T, BZ, BY, P>;
+    using S = SweepShape<R, T, V, BZ, BY, P>;
     const size_t smem = S::smem_bytes(a.chunk);
     static size_t attr_bytes = 0;
     if (smem > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R, T, BZ, BY, P>,
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R, T, V, BZ, BY, P>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_bytes = smem;
     }
-    sweep_kernel<R, T, BZ, BY, P><<<nblocks, S::NT, smem, stream>>>(a, st, m);
+    sweep_kernel<R, T, V, BZ, BY, P><<<nblocks, S::NTB, smem, stream>>>(a, st, m);
     return cudaGetLastError();
 }
 
 }  // namespace wt
 
-#define WAVE_VARIANT_ENTRY(R_, T_, BZ_, BY_, P_)                                                  \
-    {R_, T_, BZ_, BY_, P_, wt::SweepShape<R_, T_, BZ_, BY_, P_>::NT,                              \
-     wt::SweepShape<R_, T_, BZ_, BY_, P_>::W0, wt::SweepShape<R_, T_, BZ_, BY_, P_>::H0,          \
-     wt::SweepShape<R_, T_, BZ_, BY_, P_>::PW, wt::SweepShape<R_, T_, BZ_, BY_, P_>::HK,          \
-     wt::SweepShape<R_, T_, BZ_, BY_, P_>::SMEM, &wt::launch_sweep<R_, T_, BZ_, BY_, P_>,         \
-     (const void *)&wt::sweep_kernel<R_, T_, BZ_, BY_, P_>},
+#define WAVE_VARIANT_ENTRY(R_, T_, V_, BZ_, BY_, P_)                                              \
+    {R_, T_, V_, BZ_, BY_, P_, wt::SweepShape<R_, T_, V_, BZ_, BY_, P_>::NTB,                     \
+     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_>::W0, wt::SweepShape<R_, T_, V_, BZ_, BY_, P_>::H0,  \
+     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_>::PW, wt::SweepShape<R_, T_, V_, BZ_, BY_, P_>::HK,  \
+     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_>::SMEM,                                             \
+     &wt::launch_sweep<R_, T_, V_, BZ_, BY_, P_>,                                                \
+     (const void *)&wt::sweep_kernel<R_, T_, V_, BZ_, BY_, P_>},
 
 #define WAVE_DEFINE_RADIUS(r_)                                                                    \
     namespace wt {                                                                                \

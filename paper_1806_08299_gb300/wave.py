@@ -24,10 +24,11 @@ WAVE_EUNSUPPORTED = -6
 WAVE_OP_FWD, WAVE_OP_ADJ, WAVE_OP_GRAD = 0, 1, 2
 WAVE_ALLOW_UNSTABLE = 1
 WAVE_TIME_SWEEPS = 2
+WAVE_AUTOTUNE_SHAPE = 4
 
 EXPORTED = ["wave_version", "wave_strerror", "wave_fd_coefficients", "wave_cfl_dt",
             "wave_workspace_bytes", "wave_ckpt_bytes", "wave_fwd", "wave_adj", "wave_grad",
-            "wave_status", "wave_describe_plan", "wave_sweep_stats"]
+            "wave_status", "wave_describe_plan", "wave_sweep_stats", "wave_list_variants"]
 
 
 class WaveError(RuntimeError):
@@ -47,7 +48,7 @@ class _Points(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("time_tile", ctypes.c_int32), ("tile_y", ctypes.c_int32),
-                ("tile_x", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("tile_x", ctypes.c_int32), ("vec", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 @dataclass
@@ -71,14 +72,17 @@ class Grid:
 
 @dataclass
 class Tuning:
-    """time_tile: 0 autotune, 1 untiled, T >= 2 time-tile depth."""
+    """time_tile: 0 autotune, 1 untiled, T >= 2 time-tile depth; tile_y, vec
+    (z points per thread) and tile_x pick a compiled variant and x-chunk."""
     time_tile: int = 0
     tile_y: int = 0
     tile_x: int = 0
     flags: int = 0
+    vec: int = 0
 
     def c(self):
-        return _Tuning(int(self.time_tile), int(self.tile_y), int(self.tile_x), int(self.flags))
+        return _Tuning(int(self.time_tile), int(self.tile_y), int(self.tile_x), int(self.vec),
+                       int(self.flags))
 
 
 _LIB = None
@@ -125,6 +129,8 @@ def _lib():
         lib.wave_sweep_stats.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32),
                                          ctypes.POINTER(i32)]
         lib.wave_sweep_stats.restype = i32
+        lib.wave_list_variants.argtypes = [i32, ctypes.POINTER(i32), i32]
+        lib.wave_list_variants.restype = i32
         _LIB = lib
     return _LIB
 
@@ -156,13 +162,26 @@ def ckpt_bytes(grid, ckpt_every):
     return int(_lib().wave_ckpt_bytes(ctypes.byref(g), int(ckpt_every)))
 
 
+def list_variants(space_order):
+    """Compiled sweep variants: dicts with time_tile, tile_y, tile_z, vec,
+    prefetch, threads."""
+    n = _lib().wave_list_variants(int(space_order), None, 0)
+    if n < 0:
+        raise WaveError(n, "wave_list_variants")
+    out = (ctypes.c_int32 * (6 * max(n, 1)))()
+    _lib().wave_list_variants(int(space_order), out, n)
+    keys = ("time_tile", "tile_y", "tile_z", "vec", "prefetch", "threads")
+    return [dict(zip(keys, out[6 * i:6 * i + 6])) for i in range(n)]
+
+
 def describe_plan(grid, tuning=None):
     g = grid.c()
-    out = (ctypes.c_int32 * 5)()
+    out = (ctypes.c_int32 * 6)()
     t = tuning.c() if tuning is not None else None
     _check(_lib().wave_describe_plan(ctypes.byref(g), ctypes.byref(t) if t else None, out),
            "wave_describe_plan")
-    return dict(time_tile=out[0], tile_y=out[1], tile_x=out[2], tile_z=out[3], prefetch=out[4])
+    return dict(time_tile=out[0], tile_y=out[1], tile_x=out[2], tile_z=out[3], vec=out[4],
+                prefetch=out[5])
 
 
 # --------------------------------------------------------------------------

@@ -202,3 +202,29 @@ def test_c2_full_grid_crop_vs_oracle(wavelib, cuda, oracle):
     assert _relerr(u[sl], uref[0]) <= TOL
     d = out[1][0][:, keep]
     assert np.abs(d - dref).max() <= TOL * np.abs(dref).max()
+
+
+@pytest.mark.parametrize("so", [2, 4, 6, 8, 10, 12, 14, 16])
+def test_every_compiled_variant(wavelib, cuda, oracle, so):
+    # every (T, tile, vec, prefetch) variant compiled for this order: bitwise
+    # equal to the untiled default, and at parity with the oracle
+    n = (37, 45, 51)
+    nt = 13
+    m, damp, src, q, rec = inputs.random_problem(n, so, nt, seed=so + 1000, nsrc=2, nrec=5)
+    dt = 0.4 * wavelib.cfl_dt(so, (inputs.H,) * 3, 3.0)
+    grid = wavelib.Grid(n, (inputs.H,) * 3, dt, nt, so)
+    d1, u1 = _run(wavelib, cuda, grid, m, damp, src, q, rec, 1)
+    _, uref, _ = _oracle(oracle, grid, m, damp, src, q, rec)
+    assert _relerr(u1[0], uref[0]) <= TOL
+    variants = wavelib.list_variants(so)
+    assert len(variants) >= 1
+    for v in variants:
+        import torch
+        dv, uv, _, ws = wavelib.fwd(grid, _t(m, cuda), _t(damp, cuda), src, _t(q, cuda), rec,
+                                    tuning=wavelib.Tuning(time_tile=v["time_tile"], tile_y=v["tile_y"],
+                                                          vec=v["vec"]),
+                                    want_u_last=True)
+        assert wavelib.status(ws) == 0
+        torch.cuda.synchronize()
+        assert np.array_equal(uv.cpu().numpy(), u1), v
+        assert np.array_equal(dv.cpu().numpy(), d1), v
