@@ -108,7 +108,7 @@ struct SweepMaps {
     CUtensorMap u, um, B, C;
 };
 
-template <int R, int T, int V, int BZ, int BY, int P>
+template <int R, int T, int V, int BZ, int BY, int P, int MB>
 struct SweepShape {
     static constexpr int RT = R * T;
     static constexpr int A0 = ((RT + 3) / 4) * 4;   // z halo, keeps 16-byte alignment
@@ -139,13 +139,14 @@ struct SweepShape {
     static constexpr size_t OFF_S = OFF_K + (size_t)DK * KSLOT;
     static constexpr size_t OFF_BAR = OFF_S + sizeof(float) * 2 * (T - 1) * PLANE;
     static constexpr size_t OFF_P = OFF_BAR + 8 * (2 * DF + DU + DK) + 16;
-    static constexpr size_t SMEM = OFF_P;           // + plane_start slices (smem_bytes)
-    static size_t smem_bytes(int chunk) { return OFF_P + sizeof(int) * 2 * (chunk + 3 * RT + 2); }
-    // blocks per SM that shared memory admits (with ~4 KB of plane_start
-    // slices); the register budget per thread follows from it
-    static constexpr int MINB_SMEM = (int)((227 * 1024) / (SMEM + 4096));
-    static constexpr int MINB_THR = 2048 / NTB;
-    static constexpr int MINB = MINB_SMEM < 1 ? 1 : (MINB_SMEM < MINB_THR ? MINB_SMEM : MINB_THR);
+    static constexpr size_t SMEM = OFF_P;           // + per-plane sparse slices (smem_bytes)
+    // plane_start slices (2 ints) and relevance flags (2 bytes) per plane visited
+    static size_t smem_bytes(int chunk) { return OFF_P + 10 * (size_t)(chunk + 3 * RT + 2) + 16; }
+    // blocks per SM the variant is compiled for (__launch_bounds__ minimum):
+    // bounds the registers per thread; must also fit shared memory
+    static constexpr int MINB = MB;
+    static_assert(MB >= 1 && (size_t)MB * (SMEM + 4096) <= 228 * 1024 && MB * NTB <= 2048,
+                  "blocks per SM do not fit shared memory or thread slots");
     static_assert(V == 2 || V == 4, "V must be 2 or 4");
     static_assert(BZ % 4 == 0, "BZ must keep 16-byte alignment");
     static_assert(NT % 32 == 0, "consumer threads must fill whole warps (named barrier)");
@@ -272,13 +273,12 @@ __device__ __forceinline__ void stv(float *p, const float (&s)[V])
         *reinterpret_cast<float2 *>(p) = make_float2(s[0], s[1]);
 }
 
-template <int R, int T, int V, int BZ, int BY, int P>
-__global__ void __launch_bounds__(SweepShape<R, T, V, BZ, BY, P>::NTB,
-                                  SweepShape<R, T, V, BZ, BY, P>::MINB)
+template <int R, int T, int V, int BZ, int BY, int P, int MB>
+__global__ void __launch_bounds__(SweepShape<R, T, V, BZ, BY, P, MB>::NTB, MB)
 sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stencil st,
              const __grid_constant__ SweepMaps mp)
 {
-    using S = SweepShape<R, T, V, BZ, BY, P>;
+    using S = SweepShape<R, T, V, BZ, BY, P, MB>;
     constexpr int QL = 2 * R + 1;
     constexpr int ZW = V + 2 * S::RP;  // z window per thread (floats)
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -318,19 +318,48 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
     const int niter = (X1 - X0) + 2 * S::RT;
     const int c00 = X0 - S::RT;                        // plane of level n at iteration 0
 
-    // plane_start slices for [X0 - 2RT, X1 + RT], clamped (empty planes -> 0 points)
+    // Sparse tables of the planes this block visits, [X0 - 2RT, X1 + RT]:
+    // plane_start slices (clamped, so planes outside the grid hold 0 points)
+    // and a per-plane flag telling whether any point of that plane lies in
+    // this block's layout, so that other blocks never touch the tables.
     const int pbase = X0 - 2 * S::RT;
     const int plen = (X1 - X0) + 3 * S::RT + 2;
     int *prec = pinj + plen;
+    unsigned char *finj = reinterpret_cast<unsigned char *>(prec + plen);
+    unsigned char *frec = finj + plen;
     for (int k = tid; k < plen; k += S::NTB) {
         const int c = min(max(pbase + k, 0), a.nx);
-        pinj[k] = a.inj.plane_start != nullptr ? a.inj.plane_start[c] : 0;
-        prec[k] = a.rec.plane_start != nullptr ? a.rec.plane_start[c] : 0;
+        const int ci = min(max(pbase + k + 1, 0), a.nx);
+        int fi = 0, fr = 0;
+        if (a.inj.plane_start != nullptr) {
+            const int e0 = a.inj.plane_start[c], e1 = a.inj.plane_start[ci];
+            pinj[k] = e0;
+            for (int e = e0; e < e1 && !fi; ++e) {
+                const int4 pt = a.inj.pts[e];
+                fi = pt.x >= gy0 && pt.x < gy0 + S::H0 && pt.y >= gz0 + S::ZL && pt.y < gz0 + S::ZR;
+            }
+        } else {
+            pinj[k] = 0;
+        }
+        if (a.rec.plane_start != nullptr) {
+            const int e0 = a.rec.plane_start[c], e1 = a.rec.plane_start[ci];
+            prec[k] = e0;
+            for (int e = e0; e < e1 && !fr; ++e) {
+                const int4 pt = a.rec.pts[e];
+                fr = pt.x >= gy0 + S::RT && pt.x < gy0 + S::RT + BY && pt.y >= gz0 + S::A0 &&
+                     pt.y < gz0 + S::A0 + BZ;
+            }
+        } else {
+            prec[k] = 0;
+        }
+        finj[k] = (unsigned char)fi;
+        frec[k] = (unsigned char)fr;
     }
     for (int k = tid; k < 2 * (T - 1) * S::PLANE; k += S::NTB) splane[k] = 0.f;
     if (tid == 0) {
         for (int k = 0; k < S::DF; ++k) mbar_init(full + k, 1);
-        for (int k = 0; k < S::DF + S::DU + S::DK; ++k) mbar_init(empF + k, S::NT);
+        // release barriers count consumer warps: lane 0 arrives for its warp
+        for (int k = 0; k < S::DF + S::DU + S::DK; ++k) mbar_init(empF + k, S::NT / 32);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -378,7 +407,11 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
     }
 
     // ------------------------------ consumer threads ------------------------------
-    // q[0]: level n (stage 1's input), q[s-1]: level n+s-1 (stage s's input)
+    // Register queues, one per stage: q[s-1] holds level n+s-1 (stage s's
+    // input) on the 2R+1 planes around stage s's centre.  They are circular:
+    // the plane loop is unrolled QL times so that, in unrolled copy u, logical
+    // position k (0 = oldest) lives in q[.][(u + 1 + k) % QL] after that
+    // iteration's push, a compile-time index (no register moves).
     float q[T][QL][V];
 #pragma unroll
     for (int s = 0; s < T; ++s)
@@ -387,182 +420,188 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
 #pragma unroll
             for (int j = 0; j < V; ++j) q[s][k][j] = 0.f;
 
+    const bool lane0 = (tid & 31) == 0;
     int su = 0, sk = 0, sf = 0;  // ring slots of the current iteration
     uint32_t pf = 0;             // parity of the current full barrier phase
     int cur = 0;
-    for (int it = 0; it < niter; ++it) {
-        const int c0 = c00 + it;
-        if (!mbar_wait_bounded(full + sf, pf)) {
-            *abort_flag = 1;
-            atomicMin(a.status, -4 /* WAVE_ETIMEOUT */);
-            if (T == 1) break;  // T > 1: decided at the consumer barrier
-        }
-        mbar_arrive(empF + sf);  // this thread is past this phase of full[sf]
-        {
-            // level n of plane c0 enters stage 1's queue
-            float v[V];
-            ldv<V>(v, ringU + (size_t)su * (S::USLOT / 4) + ownU);
+    bool stop = false;
+    for (int it0 = 0; it0 < niter && !stop; it0 += QL) {
 #pragma unroll
-            for (int k = 0; k < QL - 1; ++k)
-#pragma unroll
-                for (int j = 0; j < V; ++j) q[0][k][j] = q[0][k + 1][j];
-#pragma unroll
-            for (int j = 0; j < V; ++j) q[0][QL - 1][j] = v[j];
-        }
-        const int suc = su - R < 0 ? su - R + S::DU : su - R;  // U slot of plane c0 - R
-        const unsigned char *kslot = ringK + (size_t)sk * S::KSLOT;
+        for (int u = 0; u < QL; ++u) {
+            const int it = it0 + u;
+            if (it >= niter || stop) break;
+            const int c0 = c00 + it;
+            if (!mbar_wait_bounded(full + sf, pf)) {
+                *abort_flag = 1;
+                atomicMin(a.status, -4 /* WAVE_ETIMEOUT */);
+                if (T == 1) {  // T > 1: decided at the consumer barrier
+                    stop = true;
+                    break;
+                }
+            }
+            __syncwarp();
+            if (lane0) mbar_arrive(empF + sf);  // this warp is past this phase of full[sf]
+            // level n of plane c0 enters stage 1's queue (replacing its oldest)
+            ldv<V>(q[0][u], ringU + (size_t)su * (S::USLOT / 4) + ownU);
+            const int suc = su - R < 0 ? su - R + S::DU : su - R;  // U slot of plane c0 - R
+            const unsigned char *kslot = ringK + (size_t)sk * S::KSLOT;
 
 #pragma unroll
-        for (int s = 1; s <= T; ++s) {
-            const int cs = c0 - s * R;  // plane computed by stage s
-            const bool rowok = row >= s * R && row < S::H0 - s * R;
-            const long long pidx = (long long)cs * a.sx + yz;
-            float un[V], dd[V], lap[V], cBv[V], cCv[V], up[V];
+            for (int s = 1; s <= T; ++s) {
+                float(&qs)[QL][V] = q[s - 1];
+                const int cs = c0 - s * R;  // plane computed by stage s
+                const bool rowok = row >= s * R && row < S::H0 - s * R;
+                const long long pidx = (long long)cs * a.sx + yz;
+                float un[V], dd[V], lap[V], cBv[V], cCv[V], up[V];
 #pragma unroll
-            for (int j = 0; j < V; ++j) { un[j] = 0.f; dd[j] = 0.f; }
-            if (rowok) {
-                const int kk = sk - (s - 1) * R;
-                const unsigned char *ks = ringK + (size_t)(kk < 0 ? kk + S::DK : kk) * S::KSLOT;
-                ldv<V>(cBv, reinterpret_cast<const float *>(ks + S::KBOXP) + ownK);
-                ldv<V>(cCv, reinterpret_cast<const float *>(ks + 2 * S::KBOXP) + ownK);
-                // centre plane of stage s: ring U (s = 1) or the exchanged plane
-                const float *Pc = s == 1 ? ringU + (size_t)suc * (S::USLOT / 4)
-                                         : splane + ((s - 2) * 2 + cur) * S::PLANE;
-                float zz[ZW / V][V];
+                for (int j = 0; j < V; ++j) { un[j] = 0.f; dd[j] = 0.f; }
+                if (rowok) {
+                    const int kk = sk - (s - 1) * R;
+                    const unsigned char *ks = ringK + (size_t)(kk < 0 ? kk + S::DK : kk) * S::KSLOT;
+                    ldv<V>(cBv, reinterpret_cast<const float *>(ks + S::KBOXP) + ownK);
+                    ldv<V>(cCv, reinterpret_cast<const float *>(ks + 2 * S::KBOXP) + ownK);
+                    // centre plane of stage s: ring U (s = 1) or the exchanged plane
+                    const float *Pc = s == 1 ? ringU + (size_t)suc * (S::USLOT / 4)
+                                             : splane + ((s - 2) * 2 + cur) * S::PLANE;
+                    float zz[ZW / V][V];
 #pragma unroll
-                for (int j = 0; j < ZW / V; ++j) ldv<V>(zz[j], Pc + ownU - S::RP + j * V);
+                    for (int j = 0; j < ZW / V; ++j) ldv<V>(zz[j], Pc + ownU - S::RP + j * V);
+                    const int qc = (u + 1 + R) % QL;  // centre (logical R)
 #pragma unroll
-                for (int j = 0; j < V; ++j) lap[j] = __fmul_rn(st.cc, q[s - 1][R][j]);
+                    for (int j = 0; j < V; ++j) lap[j] = __fmul_rn(st.cc, qs[qc][j]);
 #pragma unroll
-                for (int k = 1; k <= R; ++k) {
-                    float yp[V], ym[V];
-                    ldv<V>(yp, Pc + ownU + k * S::PW);
-                    ldv<V>(ym, Pc + ownU - k * S::PW);
+                    for (int k = 1; k <= R; ++k) {
+                        float yp[V], ym[V];
+                        ldv<V>(yp, Pc + ownU + k * S::PW);
+                        ldv<V>(ym, Pc + ownU - k * S::PW);
+                        const int qp = (u + 1 + R + k) % QL, qm = (u + 1 + R - k) % QL;
+#pragma unroll
+                        for (int j = 0; j < V; ++j) {
+                            lap[j] = __fmaf_rn(st.cx[k], __fadd_rn(qs[qp][j], qs[qm][j]), lap[j]);
+                            lap[j] = __fmaf_rn(st.cy[k], __fadd_rn(yp[j], ym[j]), lap[j]);
+                            lap[j] = __fmaf_rn(st.cz[k],
+                                               __fadd_rn(zz[(S::RP + j + k) / V][(S::RP + j + k) % V],
+                                                         zz[(S::RP + j - k) / V][(S::RP + j - k) % V]),
+                                               lap[j]);
+                        }
+                    }
+                    if (s == 1) {
+                        ldv<V>(up, reinterpret_cast<const float *>(kslot) + ownK);  // level n-1
+                    } else {
+                        // level n+s-2 on plane cs: oldest of stage s-1's queue
+#pragma unroll
+                        for (int j = 0; j < V; ++j) up[j] = q[s > 1 ? s - 2 : 0][(u + 1) % QL][j];
+                    }
 #pragma unroll
                     for (int j = 0; j < V; ++j) {
-                        lap[j] = __fmaf_rn(st.cx[k], __fadd_rn(q[s - 1][R + k][j], q[s - 1][R - k][j]),
-                                           lap[j]);
-                        lap[j] = __fmaf_rn(st.cy[k], __fadd_rn(yp[j], ym[j]), lap[j]);
-                        lap[j] = __fmaf_rn(st.cz[k],
-                                           __fadd_rn(zz[(S::RP + j + k) / V][(S::RP + j + k) % V],
-                                                     zz[(S::RP + j - k) / V][(S::RP + j - k) % V]),
-                                           lap[j]);
+                        const float u0 = qs[qc][j];
+                        un[j] = __fmaf_rn(cCv[j], lap[j], __fmaf_rn(cBv[j], __fsub_rn(u0, up[j]), u0));
+                    }
+                    const bool plane_in = cs >= 0 && cs < a.nx;
+                    if (a.dstore != nullptr && in_yz && plane_in) {
+                        // u^{n+1} - 2u^n + u^{n-1} = E (u^n - u^{n-1}) + C (L u^n + f^n)
+                        float e[V];
+                        ldgv<V>(e, a.cE + pidx);
+#pragma unroll
+                        for (int j = 0; j < V; ++j)
+                            dd[j] = __fmaf_rn(cCv[j], lap[j], __fmul_rn(e[j], __fsub_rn(qs[qc][j], up[j])));
+                    }
+                    // point sources: f = sum_s w q_s (ascending source order), u += C f
+                    if (finj[cs - pbase] && in_yz) {
+                        const int e0 = pinj[cs - pbase], e1 = pinj[cs - pbase + 1];
+                        // each grid point appears at most once in the table, but up
+                        // to V table points can fall in this thread's V z-points
+                        float fv[V];
+                        unsigned hits = 0u;
+#pragma unroll
+                        for (int j = 0; j < V; ++j) fv[j] = 0.f;
+                        for (int e = e0; e < e1; ++e) {
+                            const int4 pt = a.inj.pts[e];
+                            if (pt.x == gy && pt.y >= gz && pt.y < gz + V) {
+                                const long long qrow = (long long)(a.q_row0 + a.q_dir * (s - 1)) * a.nq;
+                                float f = 0.f;
+                                for (int itm = pt.z; itm < pt.w; ++itm)
+                                    f = __fmaf_rn(a.inj.w[itm], a.q[qrow + a.inj.item[itm]], f);
+                                const int jj = pt.y - gz;
+#pragma unroll
+                                for (int j = 0; j < V; ++j) fv[j] = jj == j ? f : fv[j];
+                                hits |= 1u << jj;
+                            }
+                        }
+#pragma unroll
+                        for (int j = 0; j < V; ++j)
+                            if (hits & (1u << j)) {
+                                un[j] = __fmaf_rn(cCv[j], fv[j], un[j]);
+                                dd[j] = __fmaf_rn(cCv[j], fv[j], dd[j]);
+                            }
                     }
                 }
-                if (s == 1) {
-                    ldv<V>(up, reinterpret_cast<const float *>(kslot) + ownK);  // level n-1
-                } else {
+                const bool own_pt = inner && cs >= X0 && cs < X1;
+                if (own_pt) {
+                    if (frec[cs - pbase]) {
+                        const int e0 = prec[cs - pbase], e1 = prec[cs - pbase + 1];
+                        float rv[V];
 #pragma unroll
-                    for (int j = 0; j < V; ++j) up[j] = q[s - 2][0][j];  // level n+s-2 on plane cs
-                }
+                        for (int j = 0; j < V; ++j) rv[j] = un[j];
+                        for (int e = e0; e < e1; ++e) {
+                            const int4 pt = a.rec.pts[e];
+                            if (pt.x == gy && pt.y >= gz && pt.y < gz + V) {
+                                const int jj = pt.y - gz;
+                                float v = rv[0];
 #pragma unroll
-                for (int j = 0; j < V; ++j) {
-                    const float u0 = q[s - 1][R][j];
-                    un[j] = __fmaf_rn(cCv[j], lap[j], __fmaf_rn(cBv[j], __fsub_rn(u0, up[j]), u0));
-                }
-                const bool plane_in = cs >= 0 && cs < a.nx;
-                if (a.dstore != nullptr && in_yz && plane_in) {
-                    // u^{n+1} - 2u^n + u^{n-1} = E (u^n - u^{n-1}) + C (L u^n + f^n)
-                    float e[V];
-                    ldgv<V>(e, a.cE + pidx);
-#pragma unroll
-                    for (int j = 0; j < V; ++j)
-                        dd[j] = __fmaf_rn(cCv[j], lap[j], __fmul_rn(e[j], __fsub_rn(q[s - 1][R][j], up[j])));
-                }
-                // point sources: f = sum_s w q_s (ascending source order), u += C f
-                const int e0 = pinj[cs - pbase], e1 = pinj[cs - pbase + 1];
-                if (e1 > e0 && in_yz) {
-                    // each grid point appears at most once in the table, but up
-                    // to V table points can fall in this thread's V z-points;
-                    // scalar selects keep fv[] in registers
-                    float fv[V];
-                    unsigned hits = 0u;
-#pragma unroll
-                    for (int j = 0; j < V; ++j) fv[j] = 0.f;
-                    for (int e = e0; e < e1; ++e) {
-                        const int4 pt = a.inj.pts[e];
-                        if (pt.x == gy && pt.y >= gz && pt.y < gz + V) {
-                            const long long qrow = (long long)(a.q_row0 + a.q_dir * (s - 1)) * a.nq;
-                            float f = 0.f;
-                            for (int itm = pt.z; itm < pt.w; ++itm)
-                                f = __fmaf_rn(a.inj.w[itm], a.q[qrow + a.inj.item[itm]], f);
-                            const int jj = pt.y - gz;
-#pragma unroll
-                            for (int j = 0; j < V; ++j) fv[j] = jj == j ? f : fv[j];
-                            hits |= 1u << jj;
+                                for (int j = 1; j < V; ++j) v = jj == j ? rv[j] : v;
+                                const long long crow = (long long)(a.c_row0 + a.c_dir * (s - 1)) * a.nslot;
+                                for (int itm = pt.z; itm < pt.w; ++itm) a.corner[crow + a.rec.item[itm]] = v;
+                            }
                         }
                     }
+                    if (s == T) stv<V>(a.out_hi + pidx, un);
+                    if (T >= 2 && s == T - 1) stv<V>(a.out_lo + pidx, un);
+                    if (a.dstore != nullptr)
+                        stv<V>(a.dstore + (a.d_row0 + (long long)a.d_dir * (s - 1)) * a.npad + pidx, dd);
+                    if (a.gacc != nullptr) {
+                        float dl[V], g[V];
+                        ldgv<V>(dl, a.dload + (a.l_row0 + (long long)a.l_dir * (s - 1)) * a.npad + pidx);
+                        ldv<V>(g, a.gacc + pidx);
 #pragma unroll
-                    for (int j = 0; j < V; ++j)
-                        if (hits & (1u << j)) {
-                            un[j] = __fmaf_rn(cCv[j], fv[j], un[j]);
-                            dd[j] = __fmaf_rn(cCv[j], fv[j], dd[j]);
-                        }
-                }
-            }
-            const bool own_pt = inner && cs >= X0 && cs < X1;
-            if (own_pt) {
-                const int e0 = prec[cs - pbase], e1 = prec[cs - pbase + 1];
-                if (e1 > e0) {
-                    float rv[V];
-#pragma unroll
-                    for (int j = 0; j < V; ++j) rv[j] = un[j];
-                    for (int e = e0; e < e1; ++e) {
-                        const int4 pt = a.rec.pts[e];
-                        if (pt.x == gy && pt.y >= gz && pt.y < gz + V) {
-                            const int jj = pt.y - gz;
-                            float v = rv[0];
-#pragma unroll
-                            for (int j = 1; j < V; ++j) v = jj == j ? rv[j] : v;
-                            const long long crow = (long long)(a.c_row0 + a.c_dir * (s - 1)) * a.nslot;
-                            for (int itm = pt.z; itm < pt.w; ++itm) a.corner[crow + a.rec.item[itm]] = v;
-                        }
+                        for (int j = 0; j < V; ++j) g[j] = __fmaf_rn(un[j], dl[j], g[j]);
+                        stv<V>(a.gacc + pidx, g);
                     }
                 }
-                if (s == T) stv<V>(a.out_hi + pidx, un);
-                if (T >= 2 && s == T - 1) stv<V>(a.out_lo + pidx, un);
-                if (a.dstore != nullptr)
-                    stv<V>(a.dstore + (a.d_row0 + (long long)a.d_dir * (s - 1)) * a.npad + pidx, dd);
-                if (a.gacc != nullptr) {
-                    float dl[V], g[V];
-                    ldgv<V>(dl, a.dload + (a.l_row0 + (long long)a.l_dir * (s - 1)) * a.npad + pidx);
-                    ldv<V>(g, a.gacc + pidx);
+                if (s < T) {
+                    // level n+s of plane cs enters stage s+1's queue (replacing its oldest)
 #pragma unroll
-                    for (int j = 0; j < V; ++j) g[j] = __fmaf_rn(un[j], dl[j], g[j]);
-                    stv<V>(a.gacc + pidx, g);
+                    for (int j = 0; j < V; ++j) q[s < T ? s : 0][u][j] = un[j];
                 }
             }
-            if (s < T) {
-                // level n+s of plane cs enters stage s+1's queue
-#pragma unroll
-                for (int k = 0; k < QL - 1; ++k)
-#pragma unroll
-                    for (int j = 0; j < V; ++j) q[s][k][j] = q[s][k + 1][j];
-#pragma unroll
-                for (int j = 0; j < V; ++j) q[s][QL - 1][j] = un[j];
-            }
-        }
 
-        // release the ring slots read for the last time: U slot of plane c0 - R
-        // (iteration it - R), K slot read by stage T (iteration it - (T-1)R).
-        // Slots of iterations before 0 were never filled and are not released.
-        if (it >= R) mbar_arrive(empU + suc);
-        if (it >= (T - 1) * R) {
-            const int kk = sk - (T - 1) * R;
-            mbar_arrive(empK + (kk < 0 ? kk + S::DK : kk));
-        }
-        if constexpr (T > 1) {
-            // centres of stages >= 2 for the next iteration
+            // release the ring slots read for the last time: U slot of plane
+            // c0 - R (iteration it - R), K slot read by stage T (iteration it -
+            // (T-1)R).  Slots of iterations before 0 were never filled.
+            __syncwarp();
+            if (lane0) {
+                if (it >= R) mbar_arrive(empU + suc);
+                if (it >= (T - 1) * R) {
+                    const int kk = sk - (T - 1) * R;
+                    mbar_arrive(empK + (kk < 0 ? kk + S::DK : kk));
+                }
+            }
+            if constexpr (T > 1) {
+                // centres of stages >= 2 for the next iteration (logical R+1)
 #pragma unroll
-            for (int s = 2; s <= T; ++s)
-                stv<V>(splane + ((s - 2) * 2 + (cur ^ 1)) * S::PLANE + ownU, q[s - 1][R + 1]);
-            const bool stop = consumer_sync_any(S::NT, *abort_flag != 0);
-            cur ^= 1;
-            if (stop) break;
+                for (int s = 2; s <= T; ++s)
+                    stv<V>(splane + ((s - 2) * 2 + (cur ^ 1)) * S::PLANE + ownU, q[s - 1][(u + 2 + R) % QL]);
+                const bool halt = consumer_sync_any(S::NT, *abort_flag != 0);
+                cur ^= 1;
+                if (halt) {
+                    stop = true;
+                    break;
+                }
+            }
+            if (++su == S::DU) su = 0;
+            if (++sk == S::DK) sk = 0;
+            if (++sf == S::DF) { sf = 0; pf ^= 1u; }
         }
-        if (++su == S::DU) su = 0;
-        if (++sk == S::DK) sk = 0;
-        if (++sf == S::DF) { sf = 0; pf ^= 1u; }
     }
 }
 

@@ -1,30 +1,31 @@
 // variants.h -- the sweep variants compiled into the library.
 //
-// X(R, T, V, BZ, BY, P): stencil radius R = space_order/2, time-tile depth T
+// X(R, T, V, BZ, BY, P, MB): stencil radius R = space_order/2, time-tile depth T
 // (T = 1: untiled sweep), V z-points per thread, output tile BZ (z) x BY (y)
-// per block, TMA prefetch distance P planes.  Shared memory holds the TMA
+// per block, TMA prefetch distance P planes, compiled for MB resident blocks
+// per SM (the __launch_bounds__ minimum, which caps registers per thread).  Shared memory holds the TMA
 // rings (R+1+P level-n planes with halos; (T-1)R+1+P iterations of level n-1
 // and coefficients) and the centre planes of stages >= 2; registers hold
 // T (2R+1) V floats of x-neighbour queues per thread.  (T, BY, V) is unique
 // per radius; shapes fit an SM without spills (checked with -Xptxas -v).
 #pragma once
 
-#define WAVE_SWEEP_VARIANTS_R1(X)                                                           \
-    X(1, 1, 4, 64, 16, 4) X(1, 1, 2, 64, 8, 4) X(1, 2, 4, 56, 16, 2) X(1, 3, 4, 56, 16, 2)  \
-    X(1, 4, 4, 56, 16, 2)
-#define WAVE_SWEEP_VARIANTS_R2(X)                                                           \
-    X(2, 1, 4, 64, 16, 4) X(2, 1, 2, 64, 16, 2) X(2, 1, 2, 64, 8, 4) X(2, 2, 4, 56, 16, 2)  \
-    X(2, 2, 2, 56, 16, 2) X(2, 3, 4, 56, 12, 2) X(2, 4, 4, 48, 8, 1)
+#define WAVE_SWEEP_VARIANTS_R1(X)                                                                  \
+    X(1, 1, 2, 64, 8, 3, 3) X(1, 1, 4, 64, 16, 4, 2) X(1, 2, 4, 56, 16, 1, 1) X(1, 3, 4, 56, 16, 2, 1) \
+    X(1, 4, 4, 56, 16, 2, 1)
+#define WAVE_SWEEP_VARIANTS_R2(X)                                                                  \
+    X(2, 1, 2, 64, 12, 2, 2) X(2, 1, 2, 64, 8, 3, 3) X(2, 1, 4, 64, 16, 4, 1)                      \
+    X(2, 2, 4, 56, 16, 1, 1) X(2, 2, 2, 56, 16, 2, 1) X(2, 3, 4, 56, 12, 2, 1) X(2, 4, 4, 48, 8, 1, 1)
 #define WAVE_SWEEP_VARIANTS_R3(X) \
-    X(3, 1, 4, 64, 16, 4) X(3, 1, 2, 64, 16, 2) X(3, 2, 4, 56, 16, 1)
-#define WAVE_SWEEP_VARIANTS_R4(X)                                                           \
-    X(4, 1, 4, 64, 16, 4) X(4, 1, 4, 64, 8, 4) X(4, 1, 2, 64, 16, 2) X(4, 1, 2, 64, 8, 4)   \
-    X(4, 2, 4, 40, 16, 1) X(4, 2, 4, 48, 8, 2) X(4, 2, 2, 40, 16, 2)
+    X(3, 1, 2, 64, 12, 2, 2) X(3, 1, 4, 64, 16, 4, 1) X(3, 2, 4, 56, 16, 1, 1)
+#define WAVE_SWEEP_VARIANTS_R4(X)                                                                  \
+    X(4, 1, 2, 64, 12, 2, 2) X(4, 1, 2, 64, 8, 3, 3) X(4, 1, 4, 64, 16, 4, 1) X(4, 1, 4, 64, 8, 3, 3) \
+    X(4, 2, 4, 56, 16, 1, 1) X(4, 2, 2, 48, 16, 1, 1) X(4, 2, 4, 48, 8, 2, 1)
 #define WAVE_SWEEP_VARIANTS_R5(X) \
-    X(5, 1, 4, 64, 12, 4) X(5, 1, 2, 64, 12, 2)
+    X(5, 1, 2, 64, 12, 2, 2) X(5, 1, 4, 64, 12, 4, 1)
 #define WAVE_SWEEP_VARIANTS_R6(X) \
-    X(6, 1, 4, 64, 12, 3) X(6, 1, 2, 64, 8, 3)
+    X(6, 1, 2, 64, 8, 2, 2) X(6, 1, 4, 64, 12, 3, 1)
 #define WAVE_SWEEP_VARIANTS_R7(X) \
-    X(7, 1, 4, 64, 8, 3) X(7, 1, 2, 64, 8, 3)
+    X(7, 1, 2, 64, 8, 2, 2) X(7, 1, 4, 64, 8, 3, 1)
 #define WAVE_SWEEP_VARIANTS_R8(X) \
-    X(8, 1, 4, 64, 8, 3) X(8, 1, 2, 64, 8, 3)
+    X(8, 1, 2, 64, 8, 2, 1) X(8, 1, 4, 64, 8, 3, 1)

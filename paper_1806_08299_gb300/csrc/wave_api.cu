@@ -373,13 +373,13 @@ int tiles(int n, int b) { return (n + b - 1) / b; }
 // Dynamic shared memory of a launch: planes + plane_start slices of the chunk.
 size_t launch_smem(const SweepVariant *v, int chunk)
 {
-    return v->smem + sizeof(int) * 2 * (size_t)(chunk + 3 * v->R * v->T + 2);
+    return v->smem + 10 * (size_t)(chunk + 3 * v->R * v->T + 2) + 16;
 }
 
-// Largest x-chunk whose plane_start slices still fit the per-block limit.
+// Largest x-chunk whose per-plane sparse slices still fit the per-block limit.
 int max_chunk(const SweepVariant *v)
 {
-    const long long room = (227LL * 1024 - (long long)v->smem) / 8 - 3LL * v->R * v->T - 2;
+    const long long room = (227LL * 1024 - 16 - (long long)v->smem) / 10 - 3LL * v->R * v->T - 2;
     return (int)std::max(16LL, std::min(room, 1LL << 20));
 }
 

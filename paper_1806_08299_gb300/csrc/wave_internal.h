@@ -40,32 +40,34 @@ cudaError_t launch_unpad(const float *src, int nx, int ny, int nz, int nzp, floa
 cudaError_t launch_gather(const float *corner, const float *w, int rows, int npts, int row_dir,
                           float *out, cudaStream_t s);
 
-template <int R, int T, int V, int BZ, int BY, int P>
+template <int R, int T, int V, int BZ, int BY, int P, int MB>
 cudaError_t launch_sweep(int nblocks, cudaStream_t stream, const SweepArgs &a, const Stencil &st,
                          const SweepMaps &m)
 {
-    using S = SweepShape<R, T, V, BZ, BY, P>;
+    using S = SweepShape<R, T, V, BZ, BY, P, MB>;
     const size_t smem = S::smem_bytes(a.chunk);
     static size_t attr_bytes = 0;
     if (smem > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R, T, V, BZ, BY, P>,
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R, T, V, BZ, BY, P, MB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_bytes = smem;
     }
-    sweep_kernel<R, T, V, BZ, BY, P><<<nblocks, S::NTB, smem, stream>>>(a, st, m);
+    sweep_kernel<R, T, V, BZ, BY, P, MB><<<nblocks, S::NTB, smem, stream>>>(a, st, m);
     return cudaGetLastError();
 }
 
 }  // namespace wt
 
-#define WAVE_VARIANT_ENTRY(R_, T_, V_, BZ_, BY_, P_)                                              \
-    {R_, T_, V_, BZ_, BY_, P_, wt::SweepShape<R_, T_, V_, BZ_, BY_, P_>::NTB,                     \
-     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_>::W0, wt::SweepShape<R_, T_, V_, BZ_, BY_, P_>::H0,  \
-     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_>::PW, wt::SweepShape<R_, T_, V_, BZ_, BY_, P_>::HK,  \
-     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_>::SMEM,                                             \
-     &wt::launch_sweep<R_, T_, V_, BZ_, BY_, P_>,                                                \
-     (const void *)&wt::sweep_kernel<R_, T_, V_, BZ_, BY_, P_>},
+#define WAVE_VARIANT_ENTRY(R_, T_, V_, BZ_, BY_, P_, MB_)                                         \
+    {R_, T_, V_, BZ_, BY_, P_, wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_>::NTB,                \
+     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_>::W0,                                          \
+     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_>::H0,                                          \
+     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_>::PW,                                          \
+     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_>::HK,                                          \
+     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_>::SMEM,                                        \
+     &wt::launch_sweep<R_, T_, V_, BZ_, BY_, P_, MB_>,                                           \
+     (const void *)&wt::sweep_kernel<R_, T_, V_, BZ_, BY_, P_, MB_>},
 
 #define WAVE_DEFINE_RADIUS(r_)                                                                    \
     namespace wt {                                                                                \
