@@ -70,6 +70,10 @@ extern "C" {
                                  (read back with wave_sweep_stats)                       */
 #define WAVE_AUTOTUNE_SHAPE 4 /* with time_tile = T >= 1: time the compiled variants of
                                  depth T (tile, vec, x-chunk) and keep the fastest       */
+#define WAVE_TEST_WITHHOLD 256 /* test hook: the sweep's producer issues no loads, so
+                                 every bounded wait of the call runs out (about 2 s per
+                                 launch) and wave_status reports WAVE_ETIMEOUT; the
+                                 CUDA context stays usable.  Results are undefined.     */
 
 typedef struct wave_grid {
     int32_t n[3];        /* nx, ny, nz >= space_order + 1 each                     */

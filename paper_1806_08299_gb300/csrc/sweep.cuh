@@ -95,6 +95,7 @@ struct SweepArgs {
     long long l_row0;
     int l_dir;
     float *gacc;
+    int withhold;            // test hook: the producer issues nothing (waits run out)
     int chunk;               // x planes per block
     int tiles_z, tiles_y;
     int *status;             // device status word (atomicMin of WAVE_E* codes)
@@ -367,7 +368,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
 
     if (tid >= S::NT) {
         // ------------------------------ producer warp ------------------------------
-        if (tid == S::NT) {
+        if (tid == S::NT && !a.withhold) {
             int ju = 0, jk = 0, jf = 0;  // slot of iteration j in ring U / ring K / full barriers
             int ru = 0, rk = 0, rf = 0;  // round of the slot: iteration j is its (r+1)-th use
             int j = 0;

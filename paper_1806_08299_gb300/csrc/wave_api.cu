@@ -6,6 +6,8 @@
 // the caller's workspace; nothing here allocates on the device.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -450,6 +452,50 @@ struct TuneKey {
 std::mutex g_tune_mu;
 std::map<TuneKey, Plan> g_tune_cache;
 
+bool tune_log()
+{
+    const char *e = std::getenv("WAVE_AUTOTUNE_LOG");
+    return e != nullptr && e[0] != '\0' && e[0] != '0';
+}
+
+// Optional persistent cache (env WAVE_TUNE_CACHE = path): one plan per line,
+//   nx ny nz space_order T_requested  ->  T tile_y vec chunk
+// Lines naming variants that are not compiled in are ignored.
+const SweepVariant *find_variant(int R, int T, int tile_y, int vec);
+
+bool cache_lookup_file(const TuneKey &k, Plan *out)
+{
+    const char *path = std::getenv("WAVE_TUNE_CACHE");
+    if (path == nullptr || !path[0]) return false;
+    FILE *f = std::fopen(path, "r");
+    if (f == nullptr) return false;
+    int nx, ny, nz, so, tr, T, by, vec, chunk;
+    bool found = false;
+    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d", &nx, &ny, &nz, &so, &tr, &T, &by, &vec, &chunk) == 9) {
+        if (nx == k.nx && ny == k.ny && nz == k.nz && so == k.so && tr == k.T) {
+            const SweepVariant *v = find_variant(so / 2, T, by, vec);
+            if (v != nullptr && chunk > 0) {
+                out->v = v;
+                out->chunk = chunk;
+                found = true;  // the last matching line wins
+            }
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store_file(const TuneKey &k, const Plan &p)
+{
+    const char *path = std::getenv("WAVE_TUNE_CACHE");
+    if (path == nullptr || !path[0]) return;
+    FILE *f = std::fopen(path, "a");
+    if (f == nullptr) return;
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d\n", k.nx, k.ny, k.nz, k.so, k.T, p.v->T, p.v->BY,
+                 p.v->V, p.chunk);
+    std::fclose(f);
+}
+
 TuneKey tune_key(const Dims &d, int so, int T)
 {
     int dev = 0;
@@ -468,6 +514,7 @@ struct Job {
     Stencil st;
     const float *cB, *cC, *cE;
     int *status = nullptr;
+    int withhold = 0;
     PointTable inj{};
     const float *q = nullptr;
     int nq = 0, q_base = 0, q_dir = 1;
@@ -585,6 +632,7 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         a.l_row0 = job.l_base + (long long)job.l_dir * j;
         a.l_dir = job.l_dir;
         a.gacc = job.gacc;
+        a.withhold = job.withhold;
         a.chunk = chunk;
         a.tiles_z = tiles(d.nzp, v->BZ);
         a.tiles_y = tiles(d.ny, v->BY);
@@ -640,17 +688,24 @@ int autotune(const Dims &d, const Stencil &st, const float *cB, const float *cC,
             job.status = status;
             State s;
             for (int k = 0; k < 4; ++k) s.buf[k] = U[k];
-            const int steps = 4 * v->T > 8 ? 4 * v->T : 8;
-            int rc = run_steps(job, s, v->T, p, stream);  // warm-up
+            // warm-up launch, then the best of two timed runs of >= 12 steps
+            const int steps = 12 * v->T > 12 ? 12 * v->T : 12;
+            int rc = run_steps(job, s, v->T, p, stream);
             if (rc) return rc;
-            CK(cudaEventRecord(e0, stream));
-            rc = run_steps(job, s, steps, p, stream);
-            if (rc) return rc;
-            CK(cudaEventRecord(e1, stream));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            const float per_step = ms / steps;
+            float per_step = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                CK(cudaEventRecord(e0, stream));
+                rc = run_steps(job, s, steps, p, stream);
+                if (rc) return rc;
+                CK(cudaEventRecord(e1, stream));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                per_step = std::min(per_step, ms / steps);
+            }
+            if (tune_log())
+                std::fprintf(stderr, "wave autotune: T=%d tile=%dx%d vec=%d P=%d chunk=%d: %.4f ms/step\n",
+                             v->T, v->BZ, v->BY, v->V, v->P, chunk, per_step);
             if (per_step < best) {
                 best = per_step;
                 bestp = p;
@@ -690,6 +745,12 @@ int resolve_plan(const Dims &d, const wave_grid *g, const wave_tuning *t, bool m
             *out = it->second;
             return WAVE_OK;
         }
+        Plan fp;
+        if (cache_lookup_file(key, &fp)) {
+            g_tune_cache[key] = fp;
+            *out = fp;
+            return WAVE_OK;
+        }
     }
     if (!may_tune) {
         out->v = shape_tune ? find_variant(R, T, 0, 0) : fallback_variant(R, 1);
@@ -702,6 +763,7 @@ int resolve_plan(const Dims &d, const wave_grid *g, const wave_tuning *t, bool m
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = p;
+    cache_store_file(key, p);
     *out = p;
     return WAVE_OK;
 }
@@ -830,6 +892,7 @@ int32_t wave_fwd(const wave_grid *g, const float *m, const float *damp, const wa
         job.rec = L.rec.view();
         job.corner = L.corner;
         job.nslot = 8 * nrec;
+        job.withhold = (tuning && (tuning->flags & WAVE_TEST_WITHHOLD)) ? 1 : 0;
         State s;
         for (int i = 0; i < 4; ++i) s.buf[i] = L.U[i];
         if ((rc = prof_begin(tuning, stream))) return rc;

@@ -1,0 +1,52 @@
+"""Time the compiled sweep variants on a synthetic workload.
+
+    python -m paper_1806_08299_gb300.sweep_bench --n 512 --so 8            # every variant
+    python -m paper_1806_08299_gb300.sweep_bench --n 256 --so 8 --time-tile 1 --tile-y 8 --vec 4
+
+The workload is the two-layer model of `inputs.c2` on an n^3 grid with a
+fixed number of steps.  For each variant it runs `--reps` forward calls and
+reports the best milliseconds per time step of the sweep launches (CUDA
+events the library records on the launch stream) and the resulting GPts/s.
+This is also the small case that the ncu summaries under profiles/ capture.
+"""
+import argparse
+import json
+
+import torch
+
+from . import inputs, wave
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--so", type=int, default=8)
+    ap.add_argument("--nt", type=int, default=8)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--time-tile", type=int, default=0, help="0 = every compiled variant")
+    ap.add_argument("--tile-y", type=int, default=0)
+    ap.add_argument("--vec", type=int, default=0)
+    args = ap.parse_args()
+    p = inputs.c2(nt=args.nt, n=(args.n,) * 3)
+    grid = wave.Grid(p.n, p.h, p.dt, p.nt, args.so)
+    tm, td, tq = (torch.from_numpy(a).cuda() for a in (p.m, p.damp, p.src_q))
+    if args.time_tile:
+        cands = [dict(time_tile=args.time_tile, tile_y=args.tile_y, vec=args.vec)]
+    else:
+        cands = wave.list_variants(args.so)
+    for v in cands:
+        tune = wave.Tuning(time_tile=v["time_tile"], tile_y=v["tile_y"], vec=v["vec"],
+                           flags=wave.WAVE_TIME_SWEEPS)
+        best = float("inf")
+        for _ in range(args.reps):
+            _, _, _, ws = wave.fwd(grid, tm, td, p.src_xyz, tq, p.rec_xyz, tuning=tune)
+            ms, launches, steps = wave.sweep_stats()
+            best = min(best, ms / steps)
+        status = wave.status(ws)
+        plan = wave.describe_plan(grid, tune)
+        print(json.dumps(dict(plan, n=args.n, so=args.so, ms_per_step=best,
+                              gpts=args.n ** 3 / (best / 1e3) / 1e9, status=status)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -25,6 +25,7 @@ WAVE_OP_FWD, WAVE_OP_ADJ, WAVE_OP_GRAD = 0, 1, 2
 WAVE_ALLOW_UNSTABLE = 1
 WAVE_TIME_SWEEPS = 2
 WAVE_AUTOTUNE_SHAPE = 4
+WAVE_TEST_WITHHOLD = 256
 
 EXPORTED = ["wave_version", "wave_strerror", "wave_fd_coefficients", "wave_cfl_dt",
             "wave_workspace_bytes", "wave_ckpt_bytes", "wave_fwd", "wave_adj", "wave_grad",

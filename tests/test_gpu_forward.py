@@ -228,3 +228,22 @@ def test_every_compiled_variant(wavelib, cuda, oracle, so):
         torch.cuda.synchronize()
         assert np.array_equal(uv.cpu().numpy(), u1), v
         assert np.array_equal(dv.cpu().numpy(), d1), v
+
+
+def test_bounded_wait_timeout_reports_status(wavelib, cuda, oracle):
+    # The test hook withholds every TMA load of the sweep, so each consumer's
+    # bounded mbarrier wait runs out (~2 s); the call must report
+    # WAVE_ETIMEOUT through wave_status and leave the context usable.
+    import torch
+    n, so, nt = (20, 18, 24), 4, 1
+    m, damp, src, q, rec = inputs.random_problem(n, so, nt, seed=77)
+    dt = 0.4 * wavelib.cfl_dt(so, (inputs.H,) * 3, 3.0)
+    grid = wavelib.Grid(n, (inputs.H,) * 3, dt, nt, so)
+    tune = wavelib.Tuning(time_tile=1, flags=wavelib.WAVE_TEST_WITHHOLD)
+    _, _, _, ws = wavelib.fwd(grid, _t(m, cuda), _t(damp, cuda), src, _t(q, cuda), rec, tuning=tune)
+    assert wavelib.status(ws) == wavelib.WAVE_ETIMEOUT
+    # the context still works: a normal call right after is correct
+    d, ul = _run(wavelib, cuda, grid, m, damp, src, q, rec, 1)
+    _, uref, _ = _oracle(oracle, grid, m, damp, src, q, rec)
+    assert _relerr(ul[0], uref[0]) <= TOL
+    torch.cuda.synchronize()
