@@ -207,6 +207,47 @@ int32_t wave_list_variants(int32_t space_order, int32_t *out, int32_t max);
  * WAVE_E* code. */
 int32_t wave_describe_plan(const wave_grid *g, const wave_tuning *tuning, int32_t *out);
 
+/* Size in bytes of the static device workspace behind wave_fwd_noalloc. */
+#define WAVE_NOALLOC_MAX_BYTES (32u * 1024u * 1024u)
+
+/* Forward modelling without a caller workspace.  The paper has no counterpart:
+ * this is a calling convention of this library, not part of the method.
+ *
+ * For callers that cannot allocate device memory: a C or Fortran host program
+ * with no device allocator of its own, a process whose device memory is
+ * handed in full to another allocator's pool, or a loop that must not pay the
+ * implicit device synchronisation of cudaMalloc / cudaFree.  The workspace is
+ * a static device array of WAVE_NOALLOC_MAX_BYTES in this library, reserved
+ * when CUDA loads the library's module on a device; the call itself
+ * allocates and frees no device memory.
+ *
+ * Arguments and results as wave_fwd (same kernels, same plan for the same
+ * tuning), without checkpoints.  `status` (HOST) may be NULL: then the call
+ * returns once the work is queued on `stream`; otherwise it waits for
+ * `stream` and stores the device status word there (as wave_status).
+ *
+ * Set-up: the first call on each device, with that device current, takes the
+ * array's address (cudaGetSymbolAddress) and keeps it; make that first call
+ * before any stream capture on that device.
+ *
+ * Sharing: every call on a device uses the same array.  Each call clears, in
+ * stream order before its first kernel, what must start at zero (the status
+ * words and the wavefield levels) and writes everything else before reading
+ * it.  Calls whose work overlaps on the GPU (different streams, or host
+ * threads without ordering between them) race on the array and give
+ * undefined results: issue them on one stream, or order them.
+ *
+ * Returns WAVE_ENOSPACE when wave_workspace_bytes(g, WAVE_OP_FWD, nsrc, nrec,
+ * 0, tuning) exceeds WAVE_NOALLOC_MAX_BYTES (roughly grids up to 100^3 with
+ * few receivers; the receiver buffer takes 32 * nt * nrec bytes), before
+ * anything is enqueued; otherwise the codes of wave_fwd.  With a NULL tuning
+ * the first call for a shape runs the autotuner, which creates and destroys
+ * two CUDA events. */
+int32_t wave_fwd_noalloc(const wave_grid *g, const float *m, const float *damp,
+                         const wave_points *src, const float *src_traces,
+                         const wave_points *rec, float *rec_traces, float *u_last,
+                         const wave_tuning *tuning, void *stream, int32_t *status);
+
 #ifdef __cplusplus
 }
 #endif

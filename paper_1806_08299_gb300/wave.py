@@ -26,10 +26,12 @@ WAVE_ALLOW_UNSTABLE = 1
 WAVE_TIME_SWEEPS = 2
 WAVE_AUTOTUNE_SHAPE = 4
 WAVE_TEST_WITHHOLD = 256
+WAVE_NOALLOC_MAX_BYTES = 32 * 1024 * 1024
 
 EXPORTED = ["wave_version", "wave_strerror", "wave_fd_coefficients", "wave_cfl_dt",
             "wave_workspace_bytes", "wave_ckpt_bytes", "wave_fwd", "wave_adj", "wave_grad",
-            "wave_status", "wave_describe_plan", "wave_sweep_stats", "wave_list_variants"]
+            "wave_status", "wave_describe_plan", "wave_sweep_stats", "wave_list_variants",
+            "wave_fwd_noalloc"]
 
 
 class WaveError(RuntimeError):
@@ -132,6 +134,8 @@ def _lib():
         lib.wave_sweep_stats.restype = i32
         lib.wave_list_variants.argtypes = [i32, ctypes.POINTER(i32), i32]
         lib.wave_list_variants.restype = i32
+        lib.wave_fwd_noalloc.argtypes = [gp, vp, vp, pp, vp, pp, vp, vp, tp, vp, ctypes.POINTER(i32)]
+        lib.wave_fwd_noalloc.restype = i32
         _LIB = lib
     return _LIB
 
@@ -307,6 +311,30 @@ def grad(grid, m, damp, src_xyz, src_traces, rec_xyz, rec_resid, ckpt, ckpt_ever
     del sa, ra
     _check(code, "wave_grad")
     return g_out, ws
+
+
+def fwd_noalloc(grid, m, damp, src_xyz, src_traces, rec_xyz, rec_out, u_last_out=None, *,
+                tuning=None, stream=None, wait=True):
+    """Forward modelling on the library's static workspace (wave_fwd_noalloc).
+    The outputs are the caller's: rec_out [nt][nrec] and optionally
+    u_last_out [2,...], both float32 on the device; nothing is allocated on
+    the device here.  Returns the device status word when `wait`, else None."""
+    n = tuple(grid.n)
+    sp, sa = _points(src_xyz)
+    rp, ra = _points(rec_xyz)
+    g = grid.c()
+    t = tuning.c() if tuning is not None else None
+    st = ctypes.c_int32(0)
+    code = _lib().wave_fwd_noalloc(
+        ctypes.byref(g), _dev_ptr(m, "m", n), _dev_ptr(damp, "damp", n), ctypes.byref(sp),
+        _dev_ptr(src_traces, "src_traces", (grid.nt, sp.npts)) if sp.npts else None,
+        ctypes.byref(rp), _dev_ptr(rec_out, "rec_out", (grid.nt, rp.npts)) if rp.npts else None,
+        _dev_ptr(u_last_out, "u_last_out", (2,) + n) if u_last_out is not None else None,
+        ctypes.byref(t) if t is not None else None, _stream(stream),
+        ctypes.byref(st) if wait else None)
+    del sa, ra
+    _check(code, "wave_fwd_noalloc")
+    return int(st.value) if wait else None
 
 
 def sweep_stats():
