@@ -95,7 +95,7 @@ typedef struct wave_points {
  *   tile_y    : output rows per block (0 = any compiled variant).
  *   tile_x    : x-chunk length streamed by one block (0 = default).
  *   vec       : z points per thread, 2 or 4 (0 = any compiled variant).
- *   flags     : WAVE_ALLOW_UNSTABLE | WAVE_TIME_SWEEPS. */
+ *   flags     : WAVE_ALLOW_UNSTABLE | WAVE_TIME_SWEEPS | WAVE_AUTOTUNE_SHAPE. */
 typedef struct wave_tuning {
     int32_t time_tile;
     int32_t tile_y;

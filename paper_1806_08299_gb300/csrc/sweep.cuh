@@ -5,12 +5,21 @@
 // time tiles with min/max bounding) for a GPU:
 //
 //  * Each block owns an output tile of BZ (z) x BY (y) columns and an x-chunk
-//    of `chunk` planes, and streams along x.  In iteration i, plane c0 = X0 -
-//    RT + i of level n enters, and stage s (1..T) computes level n+s on plane
-//    c0 - s*R: the skew by the stencil radius R per time step of Sec. 4.1, the
-//    minimum legal factor (Sec. 2.3.2.1).  Every x-dependence of a stage is
-//    then already computed, and T time levels are live on chip at once (the
-//    time buffer of Sec. 5.2.1).
+//    [X0, X1) of `chunk` planes, and streams along x.  In iteration i, plane
+//    c0 = X0 - RT + i of level n enters, and stage s (1..T) computes level
+//    n+s on plane c0 - s*R: the skew by the stencil radius R per time step of
+//    Sec. 4.1, the minimum legal factor (Sec. 2.3.2.1).  Every x-dependence
+//    of a stage is then already computed, and T time levels are live on chip
+//    at once (the time buffer of Sec. 5.2.1).  Stage s starts at iteration
+//    2sR, when its x-queue holds the chunk's own planes, so it computes
+//    exactly the planes [X0 - (T-s)R, X1 + (T-s)R) that later stages and
+//    stores need; the first 2R iterations load no ring-K data.  Block
+//    indices run z-tile fastest, then y-tile, then chunk, so blocks resident
+//    together stream neighbouring columns over the same x-range and share
+//    their overlapping halos through L2.
+//  * Point arithmetic runs on pairs of z points with the paired FP32
+//    instructions of sm_100-class GPUs (__ffma2_rn and friends), each lane
+//    rounded as its scalar counterpart.
 //  * In y and z, neighbouring blocks read overlapping halos of width R*T and
 //    recompute the shrinking halo of each stage, so blocks never wait on one
 //    another.
@@ -19,9 +28,10 @@
 //    shared-memory rings; "full" mbarriers (transaction counts) tell the
 //    consumer threads a slot has landed and "empty" mbarriers (one arrival per
 //    consumer thread) tell the producer a slot may be refilled, so consumer
-//    warps are never held in lock step by the loads.  Ring U holds the 2R+1+P most recent level-n planes with their
-//    y/z halos, so stage 1 reads all its x, y and z neighbours from shared
-//    memory.  Ring K holds, per iteration, level n-1 and the per-point
+//    warps are never held in lock step by the loads.  Ring U holds the
+//    R+1+P most recent level-n planes with their y/z halos; stage 1 reads its
+//    y and z neighbours there and its x neighbours from registers.  Ring K
+//    holds, per iteration, level n-1 and the per-point
 //    coefficients B, C of stage 1's plane; stage s reads the B, C that stage 1
 //    read (s-1)R iterations earlier, so ring K is (T-1)R+1+P iterations deep.
 //    TMA fills everything outside
@@ -56,13 +66,14 @@ namespace wt {
 constexpr int kMaxR = 8;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
 
-// Per-axis stencil coefficients c_k / h_a^2 in FP32; cc is the centre
+// Per-axis stencil coefficients c_k / h_a^2 in FP32, each stored twice (x
+// and y of a float2) for the paired FP32 instructions; cc is the centre
 // weight (c_0/hx^2 + c_0/hy^2) + c_0/hz^2 rounded once on the host.
 struct Stencil {
-    float cc;
-    float cx[kMaxR + 1];
-    float cy[kMaxR + 1];
-    float cz[kMaxR + 1];
+    float2 cc;
+    float2 cx[kMaxR + 1];
+    float2 cy[kMaxR + 1];
+    float2 cz[kMaxR + 1];
 };
 
 // Sparse points of one kind, sorted by (x, y, z).  plane_start[x] ..
@@ -97,7 +108,7 @@ struct SweepArgs {
     float *gacc;
     int withhold;            // test hook: the producer issues nothing (waits run out)
     int chunk;               // x planes per block
-    int tiles_z, tiles_y;
+    int tiles_z, tiles_y;    // column tiles of the grid
     int *status;             // device status word (atomicMin of WAVE_E* codes)
 };
 
@@ -108,6 +119,15 @@ struct SweepArgs {
 struct SweepMaps {
     CUtensorMap u, um, B, C;
 };
+
+// Shared memory of the per-plane sparse slices for an x-chunk of `chunk`
+// planes at time-tile radius rt = R*T: plane_start slices of the injection
+// and record tables (int each) and two relevance flags (byte each) per plane
+// visited.
+__host__ __device__ constexpr size_t sweep_table_bytes(int chunk, int rt)
+{
+    return (10 * (size_t)(chunk + 3 * rt + 2) + 15) / 16 * 16;
+}
 
 template <int R, int T, int V, int BZ, int BY, int P, int MB>
 struct SweepShape {
@@ -141,8 +161,7 @@ struct SweepShape {
     static constexpr size_t OFF_BAR = OFF_S + sizeof(float) * 2 * (T - 1) * PLANE;
     static constexpr size_t OFF_P = OFF_BAR + 8 * (2 * DF + DU + DK) + 16;
     static constexpr size_t SMEM = OFF_P;           // + per-plane sparse slices (smem_bytes)
-    // plane_start slices (2 ints) and relevance flags (2 bytes) per plane visited
-    static size_t smem_bytes(int chunk) { return OFF_P + 10 * (size_t)(chunk + 3 * RT + 2) + 16; }
+    static size_t smem_bytes(int chunk) { return OFF_P + sweep_table_bytes(chunk, RT) + 16; }
     // blocks per SM the variant is compiled for (__launch_bounds__ minimum):
     // bounds the registers per thread; must also fit shared memory
     static constexpr int MINB = MB;
@@ -274,6 +293,46 @@ __device__ __forceinline__ void stv(float *p, const float (&s)[V])
         *reinterpret_cast<float2 *>(p) = make_float2(s[0], s[1]);
 }
 
+// V consecutive floats as V/2 pairs (shared or global memory, 8V-byte aligned).
+template <int V>
+__device__ __forceinline__ void ld2(float2 *d, const float *p)
+{
+    if constexpr (V == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        d[0] = make_float2(t.x, t.y);
+        d[1] = make_float2(t.z, t.w);
+    } else {
+        d[0] = *reinterpret_cast<const float2 *>(p);
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void ldg2(float2 *d, const float *p)
+{
+    if constexpr (V == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        d[0] = make_float2(t.x, t.y);
+        d[1] = make_float2(t.z, t.w);
+    } else {
+        d[0] = __ldg(reinterpret_cast<const float2 *>(p));
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void st2(float *p, const float2 *s)
+{
+    if constexpr (V == 4)
+        *reinterpret_cast<float4 *>(p) = make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
+    else
+        *reinterpret_cast<float2 *>(p) = s[0];
+}
+
+// u - w of a pair, exactly as two IEEE subtractions (negation is exact).
+__device__ __forceinline__ float2 fsub2_rn(float2 u, float2 w)
+{
+    return __fadd2_rn(u, make_float2(-w.x, -w.y));
+}
+
 template <int R, int T, int V, int BZ, int BY, int P, int MB>
 __global__ void __launch_bounds__(SweepShape<R, T, V, BZ, BY, P, MB>::NTB, MB)
 sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stencil st,
@@ -291,7 +350,6 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
     uint64_t *empU = empF + S::DF;   // per ring-U slot: released by all consumers
     uint64_t *empK = empU + S::DU;   // per ring-K slot: released by all consumers
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empK + S::DK);
-    int *pinj = reinterpret_cast<int *>(smem_raw + S::OFF_P);
 
     if (blockDim.x != S::NTB) {  // launched with the wrong shape: report, do nothing
         if (threadIdx.x == 0 && blockIdx.x == 0) atomicMin(a.status, -1 /* WAVE_EINVAL */);
@@ -325,15 +383,16 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
     // this block's layout, so that other blocks never touch the tables.
     const int pbase = X0 - 2 * S::RT;
     const int plen = (X1 - X0) + 3 * S::RT + 2;
+    int *pinj = reinterpret_cast<int *>(smem_raw + S::OFF_P);
     int *prec = pinj + plen;
     unsigned char *finj = reinterpret_cast<unsigned char *>(prec + plen);
     unsigned char *frec = finj + plen;
     for (int k = tid; k < plen; k += S::NTB) {
-        const int c = min(max(pbase + k, 0), a.nx);
+        const int cp = min(max(pbase + k, 0), a.nx);
         const int ci = min(max(pbase + k + 1, 0), a.nx);
         int fi = 0, fr = 0;
         if (a.inj.plane_start != nullptr) {
-            const int e0 = a.inj.plane_start[c], e1 = a.inj.plane_start[ci];
+            const int e0 = a.inj.plane_start[cp], e1 = a.inj.plane_start[ci];
             pinj[k] = e0;
             for (int e = e0; e < e1 && !fi; ++e) {
                 const int4 pt = a.inj.pts[e];
@@ -343,7 +402,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
             pinj[k] = 0;
         }
         if (a.rec.plane_start != nullptr) {
-            const int e0 = a.rec.plane_start[c], e1 = a.rec.plane_start[ci];
+            const int e0 = a.rec.plane_start[cp], e1 = a.rec.plane_start[ci];
             prec[k] = e0;
             for (int e = e0; e < e1 && !fr; ++e) {
                 const int4 pt = a.rec.pts[e];
@@ -389,12 +448,17 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                 }
                 const int c0 = c00 + j;
                 uint64_t *bf = full + jf;
-                mbar_expect_tx(bf, S::TXB);
+                // (u^{n-1}, B, C) of plane c0 - R are first read by stage 1 at
+                // iteration 2R: the ring-K slots of earlier iterations stay unused
+                const bool kload = j >= 2 * R;
+                mbar_expect_tx(bf, kload ? S::TXB : S::UBOX);
                 tma_load_3d(ringU + (size_t)ju * (S::USLOT / 4), &mp.u, gz0 - S::RP, gy0, c0, bf);
-                unsigned char *kslot = ringK + (size_t)jk * S::KSLOT;
-                tma_load_3d(kslot, &mp.um, gz0, gy0 + R, c0 - R, bf);
-                tma_load_3d(kslot + S::KBOXP, &mp.B, gz0, gy0 + R, c0 - R, bf);
-                tma_load_3d(kslot + 2 * S::KBOXP, &mp.C, gz0, gy0 + R, c0 - R, bf);
+                if (kload) {
+                    unsigned char *kslot = ringK + (size_t)jk * S::KSLOT;
+                    tma_load_3d(kslot, &mp.um, gz0, gy0 + R, c0 - R, bf);
+                    tma_load_3d(kslot + S::KBOXP, &mp.B, gz0, gy0 + R, c0 - R, bf);
+                    tma_load_3d(kslot + 2 * S::KBOXP, &mp.C, gz0, gy0 + R, c0 - R, bf);
+                }
                 if (++ju == S::DU) { ju = 0; ++ru; }
                 if (++jk == S::DK) { jk = 0; ++rk; }
                 if (++jf == S::DF) { jf = 0; ++rf; }
@@ -413,13 +477,14 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
     // the plane loop is unrolled QL times so that, in unrolled copy u, logical
     // position k (0 = oldest) lives in q[.][(u + 1 + k) % QL] after that
     // iteration's push, a compile-time index (no register moves).
-    float q[T][QL][V];
+    constexpr int V2 = V / 2;  // point pairs per thread: arithmetic in paired FP32
+    float2 q[T][QL][V2];
 #pragma unroll
     for (int s = 0; s < T; ++s)
 #pragma unroll
         for (int k = 0; k < QL; ++k)
 #pragma unroll
-            for (int j = 0; j < V; ++j) q[s][k][j] = 0.f;
+            for (int j = 0; j < V2; ++j) q[s][k][j] = make_float2(0.f, 0.f);
 
     const bool lane0 = (tid & 31) == 0;
     int su = 0, sk = 0, sf = 0;  // ring slots of the current iteration
@@ -430,82 +495,101 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
 #pragma unroll
         for (int u = 0; u < QL; ++u) {
             const int it = it0 + u;
-            if (it >= niter || stop) break;
+            if (it >= niter) break;
+            // T == 1 has no per-plane consumer barrier: each warp stops on
+            // its own, at a warp-uniform point, once a wait anywhere in the
+            // block ran out
+            if (T == 1 && __any_sync(0xffffffffu, *abort_flag != 0)) {
+                stop = true;
+                break;
+            }
             const int c0 = c00 + it;
-            if (!mbar_wait_bounded(full + sf, pf)) {
-                *abort_flag = 1;
-                atomicMin(a.status, -4 /* WAVE_ETIMEOUT */);
+            const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(full + sf, pf));
+            if (!got) {
+                if (lane0) {
+                    *abort_flag = 1;
+                    atomicMin(a.status, -4 /* WAVE_ETIMEOUT */);
+                }
                 if (T == 1) {  // T > 1: decided at the consumer barrier
                     stop = true;
                     break;
                 }
             }
-            __syncwarp();
             if (lane0) mbar_arrive(empF + sf);  // this warp is past this phase of full[sf]
             // level n of plane c0 enters stage 1's queue (replacing its oldest)
-            ldv<V>(q[0][u], ringU + (size_t)su * (S::USLOT / 4) + ownU);
+            ld2<V>(q[0][u], ringU + (size_t)su * (S::USLOT / 4) + ownU);
             const int suc = su - R < 0 ? su - R + S::DU : su - R;  // U slot of plane c0 - R
             const unsigned char *kslot = ringK + (size_t)sk * S::KSLOT;
 
 #pragma unroll
             for (int s = 1; s <= T; ++s) {
-                float(&qs)[QL][V] = q[s - 1];
+                float2(&qs)[QL][V2] = q[s - 1];
                 const int cs = c0 - s * R;  // plane computed by stage s
-                const bool rowok = row >= s * R && row < S::H0 - s * R;
+                // rows this stage computes, and only once the item's own planes
+                // fill its x-queue (local iteration 2sR on); earlier iterations
+                // would only produce planes no later stage or store reads
+                const bool rowok = row >= s * R && row < S::H0 - s * R && it >= 2 * s * R;
                 const long long pidx = (long long)cs * a.sx + yz;
-                float un[V], dd[V], lap[V], cBv[V], cCv[V], up[V];
+                float2 un[V2], dd[V2];
 #pragma unroll
-                for (int j = 0; j < V; ++j) { un[j] = 0.f; dd[j] = 0.f; }
+                for (int j = 0; j < V2; ++j) { un[j] = make_float2(0.f, 0.f); dd[j] = un[j]; }
                 if (rowok) {
                     const int kk = sk - (s - 1) * R;
                     const unsigned char *ks = ringK + (size_t)(kk < 0 ? kk + S::DK : kk) * S::KSLOT;
-                    ldv<V>(cBv, reinterpret_cast<const float *>(ks + S::KBOXP) + ownK);
-                    ldv<V>(cCv, reinterpret_cast<const float *>(ks + 2 * S::KBOXP) + ownK);
+                    float2 cBv[V2], cCv[V2], up[V2], lap[V2];
+                    ld2<V>(cBv, reinterpret_cast<const float *>(ks + S::KBOXP) + ownK);
+                    ld2<V>(cCv, reinterpret_cast<const float *>(ks + 2 * S::KBOXP) + ownK);
                     // centre plane of stage s: ring U (s = 1) or the exchanged plane
                     const float *Pc = s == 1 ? ringU + (size_t)suc * (S::USLOT / 4)
                                              : splane + ((s - 2) * 2 + cur) * S::PLANE;
-                    float zz[ZW / V][V];
+                    // z window of the thread: pairs at even offsets (zz) and at odd
+                    // offsets (zo = (z[2i+1], z[2i+2])); own points start at RP
+                    float2 zz[ZW / 2], zo[ZW / 2 - 1];
 #pragma unroll
-                    for (int j = 0; j < ZW / V; ++j) ldv<V>(zz[j], Pc + ownU - S::RP + j * V);
+                    for (int j = 0; j < ZW / V; ++j) ld2<V>(zz + j * V2, Pc + ownU - S::RP + j * V);
+#pragma unroll
+                    for (int i = 0; i < ZW / 2 - 1; ++i) zo[i] = make_float2(zz[i].y, zz[i + 1].x);
                     const int qc = (u + 1 + R) % QL;  // centre (logical R)
 #pragma unroll
-                    for (int j = 0; j < V; ++j) lap[j] = __fmul_rn(st.cc, qs[qc][j]);
+                    for (int j = 0; j < V2; ++j) lap[j] = __fmul2_rn(st.cc, qs[qc][j]);
 #pragma unroll
                     for (int k = 1; k <= R; ++k) {
-                        float yp[V], ym[V];
-                        ldv<V>(yp, Pc + ownU + k * S::PW);
-                        ldv<V>(ym, Pc + ownU - k * S::PW);
+                        float2 yp[V2], ym[V2];
+                        ld2<V>(yp, Pc + ownU + k * S::PW);
+                        ld2<V>(ym, Pc + ownU - k * S::PW);
                         const int qp = (u + 1 + R + k) % QL, qm = (u + 1 + R - k) % QL;
 #pragma unroll
-                        for (int j = 0; j < V; ++j) {
-                            lap[j] = __fmaf_rn(st.cx[k], __fadd_rn(qs[qp][j], qs[qm][j]), lap[j]);
-                            lap[j] = __fmaf_rn(st.cy[k], __fadd_rn(yp[j], ym[j]), lap[j]);
-                            lap[j] = __fmaf_rn(st.cz[k],
-                                               __fadd_rn(zz[(S::RP + j + k) / V][(S::RP + j + k) % V],
-                                                         zz[(S::RP + j - k) / V][(S::RP + j - k) % V]),
-                                               lap[j]);
+                        for (int j = 0; j < V2; ++j) {
+                            const int op = S::RP + 2 * j + k, om = S::RP + 2 * j - k;
+                            const float2 zp = (op & 1) ? zo[(op - 1) >> 1] : zz[op >> 1];
+                            const float2 zm = (om & 1) ? zo[(om - 1) >> 1] : zz[om >> 1];
+                            lap[j] = __ffma2_rn(st.cx[k], __fadd2_rn(qs[qp][j], qs[qm][j]), lap[j]);
+                            lap[j] = __ffma2_rn(st.cy[k], __fadd2_rn(yp[j], ym[j]), lap[j]);
+                            lap[j] = __ffma2_rn(st.cz[k], __fadd2_rn(zp, zm), lap[j]);
                         }
                     }
                     if (s == 1) {
-                        ldv<V>(up, reinterpret_cast<const float *>(kslot) + ownK);  // level n-1
+                        ld2<V>(up, reinterpret_cast<const float *>(kslot) + ownK);  // level n-1
                     } else {
                         // level n+s-2 on plane cs: oldest of stage s-1's queue
 #pragma unroll
-                        for (int j = 0; j < V; ++j) up[j] = q[s > 1 ? s - 2 : 0][(u + 1) % QL][j];
+                        for (int j = 0; j < V2; ++j) up[j] = q[s > 1 ? s - 2 : 0][(u + 1) % QL][j];
                     }
+                    float2 du[V2];  // u^n - u^{n-1}
 #pragma unroll
-                    for (int j = 0; j < V; ++j) {
-                        const float u0 = qs[qc][j];
-                        un[j] = __fmaf_rn(cCv[j], lap[j], __fmaf_rn(cBv[j], __fsub_rn(u0, up[j]), u0));
+                    for (int j = 0; j < V2; ++j) {
+                        const float2 u0 = qs[qc][j];
+                        du[j] = fsub2_rn(u0, up[j]);
+                        un[j] = __ffma2_rn(cCv[j], lap[j], __ffma2_rn(cBv[j], du[j], u0));
                     }
                     const bool plane_in = cs >= 0 && cs < a.nx;
                     if (a.dstore != nullptr && in_yz && plane_in) {
                         // u^{n+1} - 2u^n + u^{n-1} = E (u^n - u^{n-1}) + C (L u^n + f^n)
-                        float e[V];
-                        ldgv<V>(e, a.cE + pidx);
+                        float2 e[V2];
+                        ldg2<V>(e, a.cE + pidx);
 #pragma unroll
-                        for (int j = 0; j < V; ++j)
-                            dd[j] = __fmaf_rn(cCv[j], lap[j], __fmul_rn(e[j], __fsub_rn(qs[qc][j], up[j])));
+                        for (int j = 0; j < V2; ++j)
+                            dd[j] = __ffma2_rn(cCv[j], lap[j], __fmul2_rn(e[j], du[j]));
                     }
                     // point sources: f = sum_s w q_s (ascending source order), u += C f
                     if (finj[cs - pbase] && in_yz) {
@@ -532,8 +616,11 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
 #pragma unroll
                         for (int j = 0; j < V; ++j)
                             if (hits & (1u << j)) {
-                                un[j] = __fmaf_rn(cCv[j], fv[j], un[j]);
-                                dd[j] = __fmaf_rn(cCv[j], fv[j], dd[j]);
+                                float &uj = (j & 1) ? un[j >> 1].y : un[j >> 1].x;
+                                float &dj = (j & 1) ? dd[j >> 1].y : dd[j >> 1].x;
+                                const float cj = (j & 1) ? cCv[j >> 1].y : cCv[j >> 1].x;
+                                uj = __fmaf_rn(cj, fv[j], uj);
+                                dj = __fmaf_rn(cj, fv[j], dj);
                             }
                     }
                 }
@@ -541,38 +628,35 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                 if (own_pt) {
                     if (frec[cs - pbase]) {
                         const int e0 = prec[cs - pbase], e1 = prec[cs - pbase + 1];
-                        float rv[V];
-#pragma unroll
-                        for (int j = 0; j < V; ++j) rv[j] = un[j];
                         for (int e = e0; e < e1; ++e) {
                             const int4 pt = a.rec.pts[e];
                             if (pt.x == gy && pt.y >= gz && pt.y < gz + V) {
                                 const int jj = pt.y - gz;
-                                float v = rv[0];
+                                float v = un[0].x;
 #pragma unroll
-                                for (int j = 1; j < V; ++j) v = jj == j ? rv[j] : v;
+                                for (int j = 1; j < V; ++j) v = jj == j ? ((j & 1) ? un[j >> 1].y : un[j >> 1].x) : v;
                                 const long long crow = (long long)(a.c_row0 + a.c_dir * (s - 1)) * a.nslot;
                                 for (int itm = pt.z; itm < pt.w; ++itm) a.corner[crow + a.rec.item[itm]] = v;
                             }
                         }
                     }
-                    if (s == T) stv<V>(a.out_hi + pidx, un);
-                    if (T >= 2 && s == T - 1) stv<V>(a.out_lo + pidx, un);
+                    if (s == T) st2<V>(a.out_hi + pidx, un);
+                    if (T >= 2 && s == T - 1) st2<V>(a.out_lo + pidx, un);
                     if (a.dstore != nullptr)
-                        stv<V>(a.dstore + (a.d_row0 + (long long)a.d_dir * (s - 1)) * a.npad + pidx, dd);
+                        st2<V>(a.dstore + (a.d_row0 + (long long)a.d_dir * (s - 1)) * a.npad + pidx, dd);
                     if (a.gacc != nullptr) {
-                        float dl[V], g[V];
-                        ldgv<V>(dl, a.dload + (a.l_row0 + (long long)a.l_dir * (s - 1)) * a.npad + pidx);
-                        ldv<V>(g, a.gacc + pidx);
+                        float2 dl[V2], g[V2];
+                        ldg2<V>(dl, a.dload + (a.l_row0 + (long long)a.l_dir * (s - 1)) * a.npad + pidx);
+                        ld2<V>(g, a.gacc + pidx);
 #pragma unroll
-                        for (int j = 0; j < V; ++j) g[j] = __fmaf_rn(un[j], dl[j], g[j]);
-                        stv<V>(a.gacc + pidx, g);
+                        for (int j = 0; j < V2; ++j) g[j] = __ffma2_rn(un[j], dl[j], g[j]);
+                        st2<V>(a.gacc + pidx, g);
                     }
                 }
                 if (s < T) {
                     // level n+s of plane cs enters stage s+1's queue (replacing its oldest)
 #pragma unroll
-                    for (int j = 0; j < V; ++j) q[s < T ? s : 0][u][j] = un[j];
+                    for (int j = 0; j < V2; ++j) q[s < T ? s : 0][u][j] = un[j];
                 }
             }
 
@@ -591,7 +675,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                 // centres of stages >= 2 for the next iteration (logical R+1)
 #pragma unroll
                 for (int s = 2; s <= T; ++s)
-                    stv<V>(splane + ((s - 2) * 2 + (cur ^ 1)) * S::PLANE + ownU, q[s - 1][(u + 2 + R) % QL]);
+                    st2<V>(splane + ((s - 2) * 2 + (cur ^ 1)) * S::PLANE + ownU, q[s - 1][(u + 2 + R) % QL]);
                 const bool halt = consumer_sync_any(S::NT, *abort_flag != 0);
                 cur ^= 1;
                 if (halt) {

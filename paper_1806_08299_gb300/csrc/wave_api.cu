@@ -126,11 +126,12 @@ Stencil make_stencil(const wave_grid *g)
     std::memset(&st, 0, sizeof(st));
     const double ih[3] = {1.0 / ((double)g->h[0] * g->h[0]), 1.0 / ((double)g->h[1] * g->h[1]),
                           1.0 / ((double)g->h[2] * g->h[2])};
-    st.cc = (float)((c[0] * ih[0] + c[0] * ih[1]) + c[0] * ih[2]);
+    auto both = [](double v) { return make_float2((float)v, (float)v); };
+    st.cc = both((c[0] * ih[0] + c[0] * ih[1]) + c[0] * ih[2]);
     for (int k = 1; k <= g->space_order / 2; ++k) {
-        st.cx[k] = (float)(c[k] * ih[0]);
-        st.cy[k] = (float)(c[k] * ih[1]);
-        st.cz[k] = (float)(c[k] * ih[2]);
+        st.cx[k] = both(c[k] * ih[0]);
+        st.cy[k] = both(c[k] * ih[1]);
+        st.cz[k] = both(c[k] * ih[2]);
     }
     return st;
 }
@@ -370,50 +371,66 @@ struct Plan {
 
 int tiles(int n, int b) { return (n + b - 1) / b; }
 
-// Default x-chunk: the split of x that best fills whole waves of resident
-// blocks, discounting the 2RT warm-up planes each chunk streams.
-// Dynamic shared memory of a launch: planes + plane_start slices of the chunk.
+// Dynamic shared memory of a launch: rings, barriers and the per-plane
+// sparse slices of an x-chunk.
 size_t launch_smem(const SweepVariant *v, int chunk)
 {
-    return v->smem + 10 * (size_t)(chunk + 3 * v->R * v->T + 2) + 16;
+    return v->smem + wt::sweep_table_bytes(chunk, v->R * v->T) + 16;
 }
 
-// Largest x-chunk whose per-plane sparse slices still fit the per-block limit.
+// Largest x-chunk whose sparse slices still fit the per-block limit.
 int max_chunk(const SweepVariant *v)
 {
-    const long long room = (227LL * 1024 - 16 - (long long)v->smem) / 10 - 3LL * v->R * v->T - 2;
+    const long long room = (227LL * 1024 - 16 - (long long)v->smem - 15) / 10 - 3LL * v->R * v->T - 2;
     return (int)std::max(16LL, std::min(room, 1LL << 20));
 }
 
+// Resident blocks per SM of variant v at `chunk` (cached per device).
 int occupancy(const SweepVariant *v, int chunk)
 {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, size_t>, int> cache;
     const size_t smem = launch_smem(v, chunk);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, v->func, smem);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
     cudaFuncSetAttribute(v->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(&occ, v->func, v->threads, smem,
                                                                cudaOccupancyDefault) != cudaSuccess ||
         occ < 1)
         occ = 1;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = occ;
     return occ;
 }
 
+// Default x-chunk.  Blocks (column tile x chunk) run in about ceil(blocks /
+// slots) waves of resident blocks.  A chunk of c planes streams c + 2RT
+// planes; its first 2R planes only fill the queue (no arithmetic, no
+// coefficient loads), counted at half a plane each, plus a few planes' worth
+// for the block's set-up.
 int default_chunk(const Dims &d, const SweepVariant *v)
 {
-    const int occ = occupancy(v, std::min(d.nx, max_chunk(v)));
-    const long long per_wave = (long long)sm_count() * occ;
     const long long cols = (long long)tiles(d.nzp, v->BZ) * tiles(d.ny, v->BY);
-    const int warm = 2 * v->R * v->T;
+    const int RT = v->R * v->T;
     int best = std::min(d.nx, max_chunk(v));
-    double best_eff = -1.0;
+    double best_cost = 1e300;
     for (int nch = 1; nch <= 64; ++nch) {
         const int chunk = tiles(d.nx, nch);
         if (chunk > max_chunk(v)) continue;
-        if (nch > 1 && chunk < 2 * warm) break;
+        if (nch > 1 && chunk < 2 * RT) break;
         const long long blocks = cols * tiles(d.nx, chunk);
-        const long long waves = (blocks + per_wave - 1) / per_wave;
-        const double eff = (double)blocks / (double)(waves * per_wave) * chunk / (double)(chunk + warm);
-        if (eff > best_eff + 1e-9) {
-            best_eff = eff;
+        const long long slots = (long long)sm_count() * occupancy(v, chunk);
+        const long long rounds = (blocks + slots - 1) / slots;
+        const double cost = (double)rounds * (chunk + 2.0 * RT - v->R + 4.0);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
             best = chunk;
         }
     }
@@ -458,9 +475,10 @@ bool tune_log()
     return e != nullptr && e[0] != '\0' && e[0] != '0';
 }
 
-// Optional persistent cache (env WAVE_TUNE_CACHE = path): one plan per line,
+// Optional plan cache file (env WAVE_TUNE_CACHE = path): one plan per line,
 //   nx ny nz space_order T_requested  ->  T tile_y vec chunk
-// Lines naming variants that are not compiled in are ignored.
+// Lines naming variants that are not compiled in, or of another format, are
+// ignored.
 const SweepVariant *find_variant(int R, int T, int tile_y, int vec);
 
 bool cache_lookup_file(const TuneKey &k, Plan *out)
@@ -471,7 +489,11 @@ bool cache_lookup_file(const TuneKey &k, Plan *out)
     if (f == nullptr) return false;
     int nx, ny, nz, so, tr, T, by, vec, chunk;
     bool found = false;
-    while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d", &nx, &ny, &nz, &so, &tr, &T, &by, &vec, &chunk) == 9) {
+    char line[256];
+    while (std::fgets(line, sizeof(line), f) != nullptr) {
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d", &nx, &ny, &nz, &so, &tr, &T, &by, &vec,
+                        &chunk) != 9)
+            continue;
         if (nx == k.nx && ny == k.ny && nz == k.nz && so == k.so && tr == k.T) {
             const SweepVariant *v = find_variant(so / 2, T, by, vec);
             if (v != nullptr && chunk > 0) {

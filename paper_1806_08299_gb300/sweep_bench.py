@@ -26,6 +26,7 @@ def main():
     ap.add_argument("--time-tile", type=int, default=0, help="0 = every compiled variant")
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--vec", type=int, default=0)
+    ap.add_argument("--tile-x", type=int, default=0, help="x-chunk (0 = default)")
     args = ap.parse_args()
     p = inputs.c2(nt=args.nt, n=(args.n,) * 3)
     grid = wave.Grid(p.n, p.h, p.dt, p.nt, args.so)
@@ -36,7 +37,7 @@ def main():
         cands = wave.list_variants(args.so)
     for v in cands:
         tune = wave.Tuning(time_tile=v["time_tile"], tile_y=v["tile_y"], vec=v["vec"],
-                           flags=wave.WAVE_TIME_SWEEPS)
+                           tile_x=args.tile_x, flags=wave.WAVE_TIME_SWEEPS)
         best = float("inf")
         for _ in range(args.reps):
             _, _, _, ws = wave.fwd(grid, tm, td, p.src_xyz, tq, p.rec_xyz, tuning=tune)

@@ -3,13 +3,14 @@ mbarrier protocol (csrc/sweep.cuh): a producer warp fills ring U (level-n
 planes, R+1+P deep) and ring K (level n-1 and coefficients, (T-1)R+1+P deep)
 with TMA copies completed on per-iteration "full" barriers; consumers release
 full phases through "consumed" barriers and ring slots through "empty"
-barriers.  The model checks, over random schedules, that no slot is
-overwritten while a consumer still reads it, that consumers never see a
-skipped phase, that the producer is never more than P+1 iterations ahead, and
-that the protocol cannot deadlock.  It also checks that the model detects the
-hazard of a protocol without the consumed barriers."""
+barriers.  The first 2R iterations of a block load no ring-K data and stage s
+reads only from iteration 2sR on.  The model checks,
+over random schedules, that every slot a consumer reads holds the iteration
+it expects, that no slot is overwritten while a consumer still reads it, that
+the producer is never more than P+1 iterations ahead, and that the protocol
+cannot deadlock.  It also checks that the model detects the hazard of a
+protocol without the consumed barriers."""
 import random
-import sys
 
 
 class MBar:
@@ -18,7 +19,6 @@ class MBar:
         self.pending = count
         self.tx = 0
         self.phase = 0          # number of completed phases
-        self.armed_tx = False
 
     def arrive(self):
         self.pending -= 1
@@ -52,17 +52,20 @@ def simulate(R, T, P, niter, NT, seed):
     empF = [MBar(NT) for _ in range(DF)]
     empU = [MBar(NT) for _ in range(DU)]
     empK = [MBar(NT) for _ in range(DK)]
+    total = niter
     slotU = [None] * DU   # iteration whose data is in the slot (None = garbage)
     slotK = [None] * DK
-    inflight = []         # (iteration, remaining steps)
-    # producer state
-    prod = dict(j=0, ju=0, jk=0, jf=0, ru=0, rk=0, rf=0, stage=0, done=False)
-    cons = [dict(it=0, su=0, sk=0, sf=0, pf=0, stage=0, done=False) for _ in range(NT)]
-    waited = [[False] * niter for _ in range(NT)]
+    inflight = []         # (iteration, U slot, K slot or None, full barrier)
+    prod = dict(j=0, ju=0, jk=0, jf=0, ru=0, rk=0, rf=0, done=False)
+    cons = [dict(g=0, su=0, sk=0, sf=0, pf=0, stage=0, done=False) for _ in range(NT)]
+    waited = [[False] * total for _ in range(NT)]
+    # the last iteration that reads a slot filled at iteration g
+    last_u = lambda g: g + R                 # noqa: E731  (stage 1 centre plane)
+    last_k = lambda g: g + (T - 1) * R       # noqa: E731  (stage T coefficients)
     steps = 0
     while True:
         steps += 1
-        if steps > 200000:
+        if steps > 400000:
             raise AssertionError("deadlock / livelock")
         actors = []
         if not prod["done"]:
@@ -73,17 +76,19 @@ def simulate(R, T, P, niter, NT, seed):
         if inflight:
             actors.append(("tma", None))
         if not actors:
+            assert all(c["done"] for c in cons) and prod["done"], "deadlock"
             break
         kind, i = rnd.choice(actors)
         if kind == "tma":
             k = rnd.randrange(len(inflight))
             itr, dst_u, dst_k, bf = inflight.pop(k)
             slotU[dst_u] = itr
-            slotK[dst_k] = itr
+            if dst_k is not None:
+                slotK[dst_k] = itr
             full[bf].complete_tx(1)
         elif kind == "p":
             p = prod
-            if p["j"] >= niter:
+            if p["j"] >= total:
                 # drain: all issued loads complete before exit
                 if inflight:
                     continue
@@ -107,15 +112,17 @@ def simulate(R, T, P, niter, NT, seed):
             old_u = slotU[p["ju"]]
             if old_u is not None:
                 for c in cons:
-                    assert c["done"] or c["it"] > old_u + R, "U slot overwritten while needed"
+                    assert c["done"] or c["g"] > last_u(old_u), "U slot overwritten while needed"
+            kload = j >= 2 * R
             old_k = slotK[p["jk"]]
-            if old_k is not None:
+            if kload and old_k is not None:
                 for c in cons:
-                    assert c["done"] or c["it"] > old_k + (T - 1) * R, "K slot overwritten while needed"
+                    assert c["done"] or c["g"] > last_k(old_k), "K slot overwritten while needed"
             full[p["jf"]].expect_tx(1)
             slotU[p["ju"]] = None
-            slotK[p["jk"]] = None
-            inflight.append((j, p["ju"], p["jk"], p["jf"]))
+            if kload:
+                slotK[p["jk"]] = None
+            inflight.append((j, p["ju"], p["jk"] if kload else None, p["jf"]))
             p["ju"] += 1
             if p["ju"] == DU:
                 p["ju"] = 0
@@ -131,33 +138,36 @@ def simulate(R, T, P, niter, NT, seed):
             p["j"] += 1
         else:
             c = cons[i]
-            it = c["it"]
-            if it >= niter:
+            g = c["g"]
+            if g >= total:
                 c["done"] = True
                 continue
+            it = g
             if c["stage"] == 0:
                 if not full[c["sf"]].try_wait(c["pf"]):
                     continue
-                # data of iteration it must be present
-                assert slotU[c["su"]] == it and slotK[c["sk"]] == it, "stale slot data"
-                waited[i][it] = True
+                # level n of this iteration's plane (pushed into the queue)
+                assert slotU[c["su"]] == g, "stale U slot data"
+                waited[i][g] = True
                 empF[c["sf"]].arrive()
                 c["stage"] = 1
                 continue
-            # compute: reads U slot of it - R and K slots of it .. it - (T-1)R
-            if it - R >= 0:
-                su = (c["su"] - R) % DU
-                assert slotU[su] == it - R, "U centre slot clobbered"
+            # stage s computes from local iteration 2sR on: stage 1 reads the
+            # U slot of iteration g - R, stage s the K slot of g - (s-1)R
             for s in range(1, T + 1):
-                jj = it - (s - 1) * R
-                if jj >= 0:
-                    assert slotK[(c["sk"] - (s - 1) * R) % DK] == jj, "K slot clobbered"
-            if it >= R:
+                if it < 2 * s * R:
+                    continue
+                if s == 1:
+                    assert slotU[(c["su"] - R) % DU] == g - R, "U centre slot clobbered"
+                jj = g - (s - 1) * R
+                assert jj >= 2 * R
+                assert slotK[(c["sk"] - (s - 1) * R) % DK] == jj, "K slot clobbered"
+            if g >= R:
                 empU[(c["su"] - R) % DU].arrive()
-            if it >= (T - 1) * R:
+            if g >= (T - 1) * R:
                 empK[(c["sk"] - (T - 1) * R) % DK].arrive()
             c["stage"] = 0
-            c["it"] += 1
+            c["g"] += 1
             c["su"] = (c["su"] + 1) % DU
             c["sk"] = (c["sk"] + 1) % DK
             c["sf"] += 1
@@ -174,23 +184,39 @@ import pytest  # noqa: E402
 @pytest.mark.parametrize("T", [1, 2, 3])
 @pytest.mark.parametrize("P", [1, 2, 4])
 def test_protocol_random_schedules(R, T, P):
-    for niter in (1, 3, 2 * R * T + 5, 40):
+    for niter in (1, 3, 2 * R * T + 1, 2 * R * T + 5, 40):
         for seed in range(3):
             simulate(R, T, P, niter, 3, seed)
 
 
-def test_model_detects_missing_consumed_barrier():
+_MUTATIONS = {
     # without the consumed barriers the producer can re-arm a full barrier
     # before every consumer waited on its previous phase (deep ring K, T >= 2)
+    "no consumed barrier": [('if p["rf"] > 0 and not empF[p["jf"]].try_wait((p["rf"] - 1) & 1):',
+                             "if False:")],
+    # slots released before they were ever filled
+    "release before the first fill": [("if g >= R:\n", "if g >= 0:\n")],
+    # a stage that starts before its x-queue holds the chunk's own planes
+    "stage starts early": [("if it < 2 * s * R:", "if it < 2 * (s - 1) * R:")],
+    # coefficient loads skipped for longer than the fill
+    "ring K skipped too long": [("kload = j >= 2 * R", "kload = j >= 3 * R")],
+}
+
+
+@pytest.mark.parametrize("name", sorted(_MUTATIONS))
+def test_model_detects_protocol_mistakes(name):
     import inspect
-    src = inspect.getsource(simulate).replace(
-        'if p["rf"] > 0 and not empF[p["jf"]].try_wait((p["rf"] - 1) & 1):', "if False:")
+    src = inspect.getsource(simulate)
+    for a, b in _MUTATIONS[name]:
+        assert a in src
+        src = src.replace(a, b)
     ns = dict(globals())
     exec(src, ns)
     caught = 0
-    for seed in range(20):
-        try:
-            ns["simulate"](4, 2, 2, 40, 3, seed)
-        except AssertionError:
-            caught += 1
+    for R, T, P in [(1, 1, 1), (2, 2, 1), (4, 2, 2), (2, 3, 2)]:
+        for seed in range(3):
+            try:
+                ns["simulate"](R, T, P, 2 * R * T + 30, 3, seed)
+            except AssertionError:
+                caught += 1
     assert caught > 0
