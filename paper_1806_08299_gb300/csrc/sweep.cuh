@@ -87,7 +87,7 @@ struct PointTable {
 };
 
 struct SweepArgs {
-    int nx, ny, nz;          // nz: padded z extent, a multiple of 4
+    int nx, ny, nz;          // nz: padded z extent, a multiple of 8
     long long sx;            // ny * nz
     long long npad;          // nx * ny * nz
     float *out_hi;           // level n+T (T == 1: may alias level n-1, updated in place)
@@ -167,7 +167,10 @@ struct SweepShape {
     static constexpr int MINB = MB;
     static_assert(MB >= 1 && (size_t)MB * (SMEM + 4096) <= 228 * 1024 && MB * NTB <= 2048,
                   "blocks per SM do not fit shared memory or thread slots");
-    static_assert(V == 2 || V == 4, "V must be 2 or 4");
+    static_assert(V == 2 || V == 4 || V == 8, "V must be 2, 4 or 8");
+    // a thread's V points start at a multiple of V (rows are padded to a
+    // multiple of 8), so they never straddle the end of a row
+    static_assert(V < 8 || ((A0 - ZL) % 8 == 0 && BZ % 8 == 0), "V = 8 needs 8-aligned thread columns");
     static_assert(BZ % 4 == 0, "BZ must keep 16-byte alignment");
     static_assert(NT % 32 == 0, "consumer threads must fill whole warps (named barrier)");
     static_assert(NTB <= 1024, "too many threads per block");
@@ -260,47 +263,18 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-template <int V>
-__device__ __forceinline__ void ldv(float (&d)[V], const float *p)
-{
-    if constexpr (V == 4) {
-        const float4 t = *reinterpret_cast<const float4 *>(p);
-        d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
-    } else {
-        const float2 t = *reinterpret_cast<const float2 *>(p);
-        d[0] = t.x; d[1] = t.y;
-    }
-}
-
-template <int V>
-__device__ __forceinline__ void ldgv(float (&d)[V], const float *p)
-{
-    if constexpr (V == 4) {
-        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
-        d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
-    } else {
-        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
-        d[0] = t.x; d[1] = t.y;
-    }
-}
-
-template <int V>
-__device__ __forceinline__ void stv(float *p, const float (&s)[V])
-{
-    if constexpr (V == 4)
-        *reinterpret_cast<float4 *>(p) = make_float4(s[0], s[1], s[2], s[3]);
-    else
-        *reinterpret_cast<float2 *>(p) = make_float2(s[0], s[1]);
-}
-
-// V consecutive floats as V/2 pairs (shared or global memory, 8V-byte aligned).
+// V consecutive floats as V/2 pairs (shared or global memory; 16-byte
+// aligned for V >= 4, 8-byte for V = 2).
 template <int V>
 __device__ __forceinline__ void ld2(float2 *d, const float *p)
 {
-    if constexpr (V == 4) {
-        const float4 t = *reinterpret_cast<const float4 *>(p);
-        d[0] = make_float2(t.x, t.y);
-        d[1] = make_float2(t.z, t.w);
+    if constexpr (V >= 4) {
+#pragma unroll
+        for (int i = 0; i < V / 4; ++i) {
+            const float4 t = reinterpret_cast<const float4 *>(p)[i];
+            d[2 * i] = make_float2(t.x, t.y);
+            d[2 * i + 1] = make_float2(t.z, t.w);
+        }
     } else {
         d[0] = *reinterpret_cast<const float2 *>(p);
     }
@@ -309,10 +283,13 @@ __device__ __forceinline__ void ld2(float2 *d, const float *p)
 template <int V>
 __device__ __forceinline__ void ldg2(float2 *d, const float *p)
 {
-    if constexpr (V == 4) {
-        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
-        d[0] = make_float2(t.x, t.y);
-        d[1] = make_float2(t.z, t.w);
+    if constexpr (V >= 4) {
+#pragma unroll
+        for (int i = 0; i < V / 4; ++i) {
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(p) + i);
+            d[2 * i] = make_float2(t.x, t.y);
+            d[2 * i + 1] = make_float2(t.z, t.w);
+        }
     } else {
         d[0] = __ldg(reinterpret_cast<const float2 *>(p));
     }
@@ -321,10 +298,13 @@ __device__ __forceinline__ void ldg2(float2 *d, const float *p)
 template <int V>
 __device__ __forceinline__ void st2(float *p, const float2 *s)
 {
-    if constexpr (V == 4)
-        *reinterpret_cast<float4 *>(p) = make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
-    else
+    if constexpr (V >= 4) {
+#pragma unroll
+        for (int i = 0; i < V / 4; ++i)
+            reinterpret_cast<float4 *>(p)[i] = make_float4(s[2 * i].x, s[2 * i].y, s[2 * i + 1].x, s[2 * i + 1].y);
+    } else {
         *reinterpret_cast<float2 *>(p) = s[0];
+    }
 }
 
 // u - w of a pair, exactly as two IEEE subtractions (negation is exact).
@@ -550,8 +530,10 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
 #pragma unroll
                     for (int i = 0; i < ZW / 2 - 1; ++i) zo[i] = make_float2(zz[i].y, zz[i + 1].x);
                     const int qc = (u + 1 + R) % QL;  // centre (logical R)
-#pragma unroll
-                    for (int j = 0; j < V2; ++j) lap[j] = __fmul2_rn(st.cc, qs[qc][j]);
+                    // R >= 3: three independent accumulation chains (centre and x,
+                    // y, z), summed at the end, L u = (lx + ly) + lz, for latency;
+                    // R <= 2: one chain, in the order centre, then per k x, y, z
+                    float2 ly[V2], lz[V2];
 #pragma unroll
                     for (int k = 1; k <= R; ++k) {
                         float2 yp[V2], ym[V2];
@@ -563,10 +545,28 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                             const int op = S::RP + 2 * j + k, om = S::RP + 2 * j - k;
                             const float2 zp = (op & 1) ? zo[(op - 1) >> 1] : zz[op >> 1];
                             const float2 zm = (om & 1) ? zo[(om - 1) >> 1] : zz[om >> 1];
-                            lap[j] = __ffma2_rn(st.cx[k], __fadd2_rn(qs[qp][j], qs[qm][j]), lap[j]);
-                            lap[j] = __ffma2_rn(st.cy[k], __fadd2_rn(yp[j], ym[j]), lap[j]);
-                            lap[j] = __ffma2_rn(st.cz[k], __fadd2_rn(zp, zm), lap[j]);
+                            const float2 sx = __fadd2_rn(qs[qp][j], qs[qm][j]);
+                            const float2 sy = __fadd2_rn(yp[j], ym[j]);
+                            const float2 sz = __fadd2_rn(zp, zm);
+                            if (R <= 2) {
+                                if (k == 1) lap[j] = __fmul2_rn(st.cc, qs[qc][j]);
+                                lap[j] = __ffma2_rn(st.cx[k], sx, lap[j]);
+                                lap[j] = __ffma2_rn(st.cy[k], sy, lap[j]);
+                                lap[j] = __ffma2_rn(st.cz[k], sz, lap[j]);
+                            } else if (k == 1) {
+                                lap[j] = __ffma2_rn(st.cx[1], sx, __fmul2_rn(st.cc, qs[qc][j]));
+                                ly[j] = __fmul2_rn(st.cy[1], sy);
+                                lz[j] = __fmul2_rn(st.cz[1], sz);
+                            } else {
+                                lap[j] = __ffma2_rn(st.cx[k], sx, lap[j]);
+                                ly[j] = __ffma2_rn(st.cy[k], sy, ly[j]);
+                                lz[j] = __ffma2_rn(st.cz[k], sz, lz[j]);
+                            }
                         }
+                    }
+                    if constexpr (R > 2) {
+#pragma unroll
+                        for (int j = 0; j < V2; ++j) lap[j] = __fadd2_rn(__fadd2_rn(lap[j], ly[j]), lz[j]);
                     }
                     if (s == 1) {
                         ld2<V>(up, reinterpret_cast<const float *>(kslot) + ownK);  // level n-1

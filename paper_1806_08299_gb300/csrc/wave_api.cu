@@ -57,7 +57,7 @@ int check_grid(const wave_grid *g, Dims *d)
     d->nx = g->n[0];
     d->ny = g->n[1];
     d->nz = g->n[2];
-    d->nzp = (g->n[2] + 3) / 4 * 4;
+    d->nzp = (g->n[2] + 7) / 8 * 8;  // rows of whole 8-point (32-byte) groups
     d->npad = (long long)d->nx * d->ny * d->nzp;
     d->n = (long long)d->nx * d->ny * d->nz;
     if (d->npad > (1LL << 36)) return WAVE_EINVAL;

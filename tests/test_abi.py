@@ -42,7 +42,7 @@ def test_cfl_matches_oracle(wavelib, oracle):
 
 def test_workspace_and_ckpt_sizes(wavelib):
     g = wavelib.Grid((33, 34, 35), (0.01,) * 3, 1e-3, 40, 8)
-    npad = 33 * 34 * 36
+    npad = 33 * 34 * 40  # z padded to a multiple of 8
     fwd = wavelib.workspace_bytes(g, wavelib.WAVE_OP_FWD, 2, 5)
     assert fwd >= 6 * 4 * npad + 40 * 8 * 5 * 4
     assert fwd % 256 == 0
