@@ -110,6 +110,23 @@ def _dist():
     return rank, world, local
 
 
+def max_over_ranks(x, dist=None, device=None):
+    """Largest x over the ranks of the default process group (x itself when
+    there is none): the job is as slow as its slowest replica."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(pts_per_rank, steps, ms, world):
+    """GPts/s of `world` replicas that each update pts_per_rank points per
+    step for `steps` steps, over the slowest rank's `ms` milliseconds."""
+    return world * pts_per_rank * steps / (ms / 1e3) / 1e9
+
+
 def _workload(args):
     from paper_1806_08299_gb300 import inputs
     if args.workload == "c1":
@@ -233,12 +250,8 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(x):
+        return max_over_ranks(x, dist, dev)
 
     # autotune once (outside any timed region), then fix the plans: the
     # time-tiled sweep over every depth and shape, the untiled baseline over
@@ -253,6 +266,9 @@ def run_ours(args):
     else:
         tiled = tuned(wave.Tuning(time_tile=0))
     untiled = tuned(wave.Tuning(time_tile=1, flags=wave.WAVE_AUTOTUNE_SHAPE))
+    deep = None  # fastest compiled shape of time-tile depth 2, reported beside the headline
+    if any(v["time_tile"] == 2 for v in wave.list_variants(p.space_order)):
+        deep = tuned(wave.Tuning(time_tile=2, flags=wave.WAVE_AUTOTUNE_SHAPE))
     plan = wave.describe_plan(grid, tiled)
     uplan = wave.describe_plan(grid, untiled)
     prof = wave.Tuning(tiled.time_tile, tiled.tile_y, tiled.tile_x, wave.WAVE_TIME_SWEEPS, tiled.vec)
@@ -266,8 +282,8 @@ def run_ours(args):
     ms, stats = _timed(lambda: fwd(prof), args.steps, stream)
     barrier()
     clocks = sampler.stop()
-    ms = max_over_ranks(ms)
-    value = world * pts * args.steps / (ms / 1e3) / 1e9
+    ms = slowest(ms)
+    value = whole_job_rate(pts, args.steps, ms, world)
     sweep_ms = sum(s[0] for s in stats)
     launches = sum(s[1] for s in stats)
 
@@ -276,8 +292,18 @@ def run_ours(args):
         fwd(untiled)
     barrier()
     ms_u, _ = _timed(lambda: fwd(untiled), args.steps, stream)
-    ms_u = max_over_ranks(ms_u)
-    untiled_gpts = world * pts * args.steps / (ms_u / 1e3) / 1e9
+    ms_u = slowest(ms_u)
+    untiled_gpts = whole_job_rate(pts, args.steps, ms_u, world)
+
+    # --- the fastest time-tiled (T >= 2) plan, same workload ----------------
+    deep_line = None
+    if deep is not None:
+        fwd(deep)
+        barrier()
+        ms_d, _ = _timed(lambda: fwd(deep), args.steps, stream)
+        ms_d = slowest(ms_d)
+        deep_line = {"gpts": whole_job_rate(pts, args.steps, ms_d, world),
+                     "plan": wave.describe_plan(grid, deep)}
 
     # --- end to end through the C ABI with host buffers --------------------
     hm = torch.from_numpy(p.m).pin_memory()
@@ -296,7 +322,7 @@ def run_ours(args):
     e2e_step()
     barrier()
     ms_e, _ = _timed(e2e_step, args.steps, stream)
-    ms_e = max_over_ranks(ms_e)
+    ms_e = slowest(ms_e)
     h2d = (hm.numel() + hd.numel() + hq.numel()) * 4
     d2h = hrec.numel() * 4
 
@@ -304,9 +330,14 @@ def run_ours(args):
     fwi = None
     if args.fwi and world == 1:
         fwi = _fwi_gradient(dev, inputs, wave, args)
+    survey = None
+    if args.survey and world == 1:
+        survey = _fwi_survey(dev, inputs, wave, args)
 
     # --- roofline of the sweep kernel --------------------------------------
     hbm, peak_kind = _peaks()
+    fp32_tflops, smem_tbs = wave.measure_peaks()
+    flops_per_pt = 7 * (p.space_order // 2) + 10  # per radius 6 adds + 1 FMA; centre and update
     T = plan["time_tile"]
     bytes_per_pt = 24 if T >= 2 else 20  # read u^n, u^{n-1}, B, C; write 2 levels (1 if untiled)
     alg_bytes = float(np.prod(p.n)) * bytes_per_pt
@@ -315,7 +346,11 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": args.traffic, "peak_kind": peak_kind,
                 "kernel": "sweep_kernel<R=%d,T=%d>" % (p.space_order // 2, T),
-                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_ms}
+                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_ms,
+                "alu": {"fp32_tflops_measured": fp32_tflops, "flops_per_point": flops_per_pt,
+                        "roof_gpts": fp32_tflops * 1e3 / flops_per_pt,
+                        "hbm_roof_gpts": hbm / bytes_per_pt},
+                "smem_tbs_measured": smem_tbs}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -332,8 +367,9 @@ def run_ours(args):
                        "tile_x": plan["tile_x"], "vec": plan["vec"], "untiled_gpts": untiled_gpts,
                        "untiled_plan": uplan,
                        "tiled_over_untiled": value / untiled_gpts,
+                       "best_time_tiled": deep_line,
                        "parallelism": "replicas" if world > 1 else "single"},
-            "e2e": {"value": world * pts * args.steps / (ms_e / 1e3) / 1e9, "unit": "GPts/s",
+            "e2e": {"value": whole_job_rate(pts, args.steps, ms_e, world), "unit": "GPts/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roofline,
             "gpu_launches": args.steps * (launches // max(args.steps, 1) + 2),
@@ -341,6 +377,8 @@ def run_ours(args):
         }
         if fwi is not None:
             line["fwi_gradient"] = fwi
+        if survey is not None:
+            line["fwi_survey"] = survey
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line))
@@ -375,6 +413,43 @@ def _fwi_gradient(dev, inputs, wave, args):
             "gpts_equiv": 3 * float(np.prod(p.n)) * p.nt / (ms / 1e3) / 1e9}
 
 
+def _fwi_survey(dev, inputs, wave, args):
+    """One FWI gradient step over the first shots of the c5 survey (windows of
+    one 512 x 512 x 256 model, so 8, 1500 steps, k = 50): the batched forward
+    for the predicted traces, then the batched gradient (forward with
+    checkpoints, recompute, adjoint and imaging condition) with the predicted
+    traces as residual (an all-zero observed-data stand-in).  s per shot."""
+    import torch
+    sv = inputs.c5(nshots=args.survey_shots, nt=args.survey_nt, true_model=False)
+    grid = wave.Grid(sv.n, sv.h, sv.dt, sv.nt, sv.space_order)
+    tm = torch.from_numpy(sv.m).to(dev)
+    td = torch.from_numpy(sv.damp).to(dev)
+    shots = [wave.Shot(origin=x["origin"], n=x["n"], src_xyz=x["src_xyz"], rec_xyz=x["rec_xyz"])
+             for x in sv.shots]
+    q = [torch.from_numpy(x).to(dev) for x in sv.src_q]
+    k, conc = 50, 4
+    tune = wave.Tuning(time_tile=1)
+    ws_f = torch.empty(wave.batch_workspace_bytes(grid, shots, 0, conc), dtype=torch.uint8, device=dev)
+    ws_g = torch.empty(wave.batch_workspace_bytes(grid, shots, k, conc), dtype=torch.uint8, device=dev)
+
+    def step():
+        d, _ = wave.fwd_batched(grid, shots, tm, td, q, concurrency=conc, tuning=tune, workspace=ws_f)
+        g, _ = wave.grad_batched(grid, shots, tm, td, q, d, k, concurrency=conc, tuning=tune,
+                                 workspace=ws_g)
+        return g
+
+    step()
+    torch.cuda.synchronize()
+    ms, _ = _timed(step, 1, torch.cuda.current_stream())
+    pts = sum(int(np.prod(x["n"])) for x in sv.shots)
+    return {"s_per_shot": ms / 1e3 / len(shots),
+            "workload": "c5: first %d of 64 shots (windows of a 512x512x256 layered model), so8, "
+                        "%d steps, k = %d, %d shots in flight; batched forward + batched gradient"
+                        % (len(shots), sv.nt, k, conc),
+            "status": wave.status(ws_g),
+            "gpts_equiv": 4 * pts * sv.nt / (ms / 1e3) / 1e9}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -386,6 +461,9 @@ def main():
     ap.add_argument("--nt", type=int, default=0)
     ap.add_argument("--time-tile", type=int, default=0)
     ap.add_argument("--no-fwi", dest="fwi", action="store_false")
+    ap.add_argument("--no-survey", dest="survey", action="store_false")
+    ap.add_argument("--survey-shots", type=int, default=8)
+    ap.add_argument("--survey-nt", type=int, default=1500)
     ap.add_argument("--fwi-nt", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,

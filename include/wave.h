@@ -207,6 +207,57 @@ int32_t wave_list_variants(int32_t space_order, int32_t *out, int32_t max);
  * WAVE_E* code. */
 int32_t wave_describe_plan(const wave_grid *g, const wave_tuning *tuning, int32_t *out);
 
+/* ------------------------------------------------------------------------
+ * Batched shots.  A seismic survey runs many independent shots over one
+ * model; each shot here is a window of the global grid (its own sources and
+ * receivers), and the FWI gradient of the survey is the sum of the shots'
+ * window gradients scattered into the global grid.  The paper times one
+ * operator at a time (Sec. 5.8); batching is how the same sweep fills a GPU
+ * whose one shot of a realistic survey leaves most SMs idle.
+ * ------------------------------------------------------------------------ */
+typedef struct wave_shot {
+    int32_t origin[3];   /* first global cell of the window, >= 0 per axis          */
+    int32_t n[3];        /* window extent; origin + n <= global n, n >= so + 1      */
+    wave_points src;     /* HOST coordinates relative to the window origin (km)     */
+    wave_points rec;
+} wave_shot;
+
+/* Device workspace for wave_fwd_batched (ckpt_every == 0) or
+ * wave_grad_batched (ckpt_every = k >= 1) with `concurrency` shots in flight
+ * (1..16; 0 = 4).  g is the global grid (nt, dt, h, space order shared by all
+ * shots).  Returns 0 on invalid arguments. */
+size_t wave_batch_workspace_bytes(const wave_grid *g, int32_t nshots, const wave_shot *shots,
+                                  int32_t ckpt_every, int32_t concurrency);
+
+/* Forward modelling of every shot.  m, damp: device, global [nx][ny][nz].
+ * src_traces: device, the shots' [nt][nsrc_s] blocks one after another (shot
+ * order); rec_traces: device out, the shots' [nt][nrec_s] blocks likewise.
+ * Each shot runs wave_fwd on its window (the window of m and damp is copied
+ * into the workspace first); up to `concurrency` shots run at once on
+ * library-owned streams that wait for `stream` at the start and that `stream`
+ * waits for at the end.  tuning applies to every shot; NULL or time_tile == 0
+ * means the library's default untiled variant (no per-shape autotuning).
+ * wave_status(ws, stream) reports the most severe device status of all shots.
+ * Results equal wave_fwd on each window, bit for bit. */
+int32_t wave_fwd_batched(const wave_grid *g, int32_t nshots, const wave_shot *shots,
+                         const float *m, const float *damp, const float *src_traces,
+                         float *rec_traces, int32_t concurrency, const wave_tuning *tuning,
+                         void *ws, size_t ws_bytes, void *stream);
+
+/* Gradient of J = sum over shots of J_s with respect to the global m, for
+ * fixed residuals rec_resid (device, the shots' [nt][nrec_s] blocks of
+ * dJ/dd_s, shot order).  Per shot: wave_fwd with checkpoints every
+ * ckpt_every steps on the window, then wave_grad on the window; the window
+ * gradients are added into per-slot global accumulators (shot i runs on
+ * slot i mod concurrency, in shot order), and the slots are summed in slot
+ * order into grad (device, global [nx][ny][nz], overwritten; zero outside
+ * every window).  The result is deterministic for a given concurrency. */
+int32_t wave_grad_batched(const wave_grid *g, int32_t nshots, const wave_shot *shots,
+                          const float *m, const float *damp, const float *src_traces,
+                          const float *rec_resid, int32_t ckpt_every, float *grad,
+                          int32_t concurrency, const wave_tuning *tuning, void *ws,
+                          size_t ws_bytes, void *stream);
+
 /* Size in bytes of the static device workspace behind wave_fwd_noalloc. */
 #define WAVE_NOALLOC_MAX_BYTES (32u * 1024u * 1024u)
 

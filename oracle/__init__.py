@@ -16,6 +16,10 @@ Functions and what pins them (see tests/test_oracle_*.py):
   forward_tiled        bitwise equal to forward (the paper's test)  (pinned)
   adjoint              dot-product test against forward             (pinned)
   gradient             central finite differences of the misfit    (pinned)
+  forward_batched,     per-shot forward / gradient on windows of one
+  gradient_batched     model, window gradients summed into the global
+                       grid; pinned by whole-grid shots, shot additivity
+                       and central finite differences of the survey misfit
 """
 import ctypes
 import os
@@ -184,4 +188,35 @@ def gradient(m, damp, h, dt, nt, space_order, src_xyz, src_q, rec_xyz, res):
         nsrc, _p(sx), _p(q), nrec, _p(rx), _p(res), _p(g))
     if rc:
         raise RuntimeError("oracle_gradient failed (%d)" % rc)
+    return g
+
+
+def _window(shot):
+    o, n = shot["origin"], shot["n"]
+    return tuple(slice(int(o[a]), int(o[a]) + int(n[a])) for a in range(3))
+
+
+def forward_batched(m, damp, h, dt, nt, space_order, shots, src_q):
+    """Receiver traces of every shot of a survey.  Shot s (a dict with
+    "origin", "n", "src", "rec"; coordinates relative to its window) sees the
+    window of the global m and damp it names; src_q[s] is its [nt][nsrc_s]
+    trace.  Returns the list of [nt][nrec_s] traces."""
+    m, damp = _arr(m), _arr(damp)
+    out = []
+    for shot, q in zip(shots, src_q):
+        w = _window(shot)
+        d, _, _ = forward(m[w], damp[w], h, dt, nt, space_order, shot["src"], q, shot["rec"])
+        out.append(d)
+    return out
+
+
+def gradient_batched(m, damp, h, dt, nt, space_order, shots, src_q, res):
+    """Gradient of J = sum_s <res_s, d_s> with respect to the global m: the
+    window gradient of each shot added into the global grid at its window
+    (zero outside every window), summed in shot order."""
+    m, damp = _arr(m), _arr(damp)
+    g = np.zeros(m.shape)
+    for shot, q, r in zip(shots, src_q, res):
+        w = _window(shot)
+        g[w] += gradient(m[w], damp[w], h, dt, nt, space_order, shot["src"], q, shot["rec"], r)
     return g

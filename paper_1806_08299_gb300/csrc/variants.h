@@ -7,19 +7,20 @@
 // rings (R+1+P level-n planes with halos; (T-1)R+1+P iterations of level n-1
 // and coefficients) and the centre planes of stages >= 2; registers hold
 // T (2R+1) V floats of x-neighbour queues per thread.  (T, BY, V) is unique
-// per radius; shapes fit an SM without spills (checked with -Xptxas -v).
+// per radius.  The first T = 1 entry of a radius is its default untiled
+// variant (the fastest measured on GB300 where one was measured).
 #pragma once
 
 #define WAVE_SWEEP_VARIANTS_R1(X)                                                                  \
     X(1, 1, 2, 64, 8, 3, 3) X(1, 1, 4, 64, 16, 4, 2) X(1, 1, 8, 64, 16, 2, 2) X(1, 2, 4, 56, 16, 1, 1) \
     X(1, 3, 4, 56, 16, 2, 1) X(1, 4, 4, 56, 16, 2, 1)
 #define WAVE_SWEEP_VARIANTS_R2(X)                                                                  \
-    X(2, 1, 2, 64, 12, 2, 2) X(2, 1, 2, 64, 8, 3, 3) X(2, 1, 4, 64, 16, 4, 1) X(2, 1, 8, 64, 16, 2, 2) \
+    X(2, 1, 8, 64, 16, 2, 2) X(2, 1, 2, 64, 12, 2, 2) X(2, 1, 2, 64, 8, 3, 3) X(2, 1, 4, 64, 16, 4, 1) \
     X(2, 2, 4, 56, 16, 1, 1) X(2, 2, 2, 56, 16, 2, 1) X(2, 3, 4, 56, 12, 2, 1) X(2, 4, 4, 48, 8, 1, 1)
 #define WAVE_SWEEP_VARIANTS_R3(X) \
     X(3, 1, 2, 64, 12, 2, 2) X(3, 1, 4, 64, 16, 4, 1) X(3, 1, 8, 64, 16, 2, 2) X(3, 2, 4, 56, 16, 1, 1)
 #define WAVE_SWEEP_VARIANTS_R4(X)                                                                  \
-    X(4, 1, 2, 64, 12, 2, 2) X(4, 1, 2, 64, 8, 3, 3) X(4, 1, 4, 64, 16, 4, 1) X(4, 1, 4, 64, 8, 3, 3) \
+    X(4, 1, 4, 64, 8, 3, 3) X(4, 1, 2, 64, 12, 2, 2) X(4, 1, 2, 64, 8, 3, 3) X(4, 1, 4, 64, 16, 4, 1) \
     X(4, 1, 8, 64, 12, 3, 2) X(4, 1, 8, 32, 24, 3, 2) X(4, 2, 4, 56, 16, 1, 1) X(4, 2, 2, 48, 16, 1, 1)     \
     X(4, 2, 4, 48, 8, 2, 1)
 #define WAVE_SWEEP_VARIANTS_R5(X) \

@@ -15,6 +15,10 @@ publishes no dataset, so every workload here is synthetic:
       (smoothed seeded noise), 40-point damping layer, 500 steps, one source.
   c4  FWI gradient, 256^3, so 8, 2.0 km/s with a 30-point sphere of
       2.2 km/s (true) or without it (initial), 2000 steps, 256 receivers.
+  c5  survey of 64 shots, each a window of one 512 x 512 x 256 model (four
+      layers 1.5 -> 3.0 km/s and a Gaussian anomaly), window sizes
+      nx, ny ~ U{128..320}, nz ~ U{128..256} at seeded offsets, one Ricker
+      10 Hz source and 128 receivers per shot, 1500 steps, so 8.
 
 dt is fixed per workload as a literal just below half the von Neumann limit
 of the scheme for the model's largest velocity (the tests check these
@@ -37,8 +41,9 @@ DT = {
     ("c3", 12): 0.482e-3,
     ("c3", 16): 0.470e-3,
     ("c4", 8): 1.029e-3,   # v_max 2.2
+    ("c5", 8): 0.752e-3,   # v_max 3.01 (layer 3.0 plus the anomaly tail)
 }
-V_MAX = {"c1": 1.5, "c2": 2.5 * 1.02, "c3": 4.5, "c4": 2.2}
+V_MAX = {"c1": 1.5, "c2": 2.5 * 1.02, "c3": 4.5, "c4": 2.2, "c5": 3.01}
 
 
 @dataclass
@@ -183,3 +188,58 @@ def random_problem(n, space_order, nt, seed, nsrc=2, nrec=5, damp_scale=3.0, h=(
     rec = (rng.random((nrec, 3)) * ext).astype(np.float32)
     q = rng.standard_normal((nt, nsrc)).astype(np.float32)
     return m, damp, src, q, rec
+
+
+@dataclass
+class Survey:
+    name: str
+    n: tuple                     # global grid
+    h: tuple
+    dt: float
+    nt: int
+    space_order: int
+    m: np.ndarray                # float32 global [nx][ny][nz]
+    damp: np.ndarray             # float32 global
+    shots: list                  # dicts: origin, n, src_xyz, rec_xyz (window-relative, km)
+    src_q: list                  # float32 [nt][nsrc_s] per shot
+
+    @property
+    def updates_per_sweep(self):
+        """Grid-point updates of one sweep over every shot's window."""
+        return int(sum(int(np.prod(s["n"])) for s in self.shots)) * self.nt
+
+
+def c5(nshots=64, nt=1500, n=(512, 512, 256), seed=5, true_model=True):
+    """Windowed-shot survey.  The global model has four layers in depth
+    (1.5, 2.0, 2.5, 3.0 km/s) and, for the true model, a Gaussian anomaly of
+    +0.2 km/s (radius parameter 24 cells) at mid depth; a 40-point damping
+    layer lines the global boundary.  Shot s: window extent nx, ny ~
+    U{128..320}, nz ~ U{128..256} (clipped to the grid) at a uniform offset
+    that keeps it inside, one Ricker 10 Hz source at the window's top centre
+    (depth 2h) and 128 receivers on a line along x at the window's centre y,
+    depth 2h."""
+    h = (H, H, H)
+    dt = DT[("c5", 8)]
+    rng = np.random.default_rng(seed)
+    z = np.arange(n[2])
+    v1 = np.choose(np.minimum(4 * z // n[2], 3), [1.5, 2.0, 2.5, 3.0]).astype(np.float32)
+    v = np.ascontiguousarray(np.broadcast_to(v1[None, None, :], n), dtype=np.float32)
+    if true_model:
+        idx = [np.arange(k) for k in n]
+        x, y, zz = np.meshgrid(*idx, indexing="ij", sparse=True)
+        r2 = (x - n[0] // 2) ** 2 + (y - n[1] // 2) ** 2 + (zz - n[2] // 2) ** 2
+        v = v + (0.2 * np.exp(-r2 / (2.0 * 24.0 ** 2))).astype(np.float32)
+    m = (1.0 / (v * v)).astype(np.float32)
+    damp = damping_profile(n, h, V_MAX["c5"])
+    shots, qs = [], []
+    w = ricker(10.0, dt, nt)[:, None]
+    for _ in range(nshots):
+        k = [min(int(rng.integers(128, 321)), n[0]), min(int(rng.integers(128, 321)), n[1]),
+             min(int(rng.integers(128, 257)), n[2])]
+        o = [int(rng.integers(0, n[a] - k[a] + 1)) for a in range(3)]
+        src = np.array([[(k[0] // 2) * H, (k[1] // 2) * H, 2 * H]], dtype=np.float32)
+        rec = np.stack([np.linspace(0.0, (k[0] - 1) * H, 128), np.full(128, (k[1] // 2) * H),
+                        np.full(128, 2 * H)], axis=1).astype(np.float32)
+        shots.append({"origin": tuple(o), "n": tuple(k), "src_xyz": src, "rec_xyz": rec})
+        qs.append(w.copy())
+    return Survey("c5", tuple(n), h, dt, nt, 8, m, damp, shots, qs)

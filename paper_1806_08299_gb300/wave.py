@@ -31,7 +31,8 @@ WAVE_NOALLOC_MAX_BYTES = 32 * 1024 * 1024
 EXPORTED = ["wave_version", "wave_strerror", "wave_fd_coefficients", "wave_cfl_dt",
             "wave_workspace_bytes", "wave_ckpt_bytes", "wave_fwd", "wave_adj", "wave_grad",
             "wave_status", "wave_describe_plan", "wave_sweep_stats", "wave_list_variants",
-            "wave_fwd_noalloc"]
+            "wave_fwd_noalloc", "wave_measure_peaks", "wave_batch_workspace_bytes",
+            "wave_fwd_batched", "wave_grad_batched"]
 
 
 class WaveError(RuntimeError):
@@ -47,6 +48,11 @@ class _Grid(ctypes.Structure):
 
 class _Points(ctypes.Structure):
     _fields_ = [("npts", ctypes.c_int32), ("xyz", ctypes.POINTER(ctypes.c_float))]
+
+
+class _Shot(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_int32 * 3), ("n", ctypes.c_int32 * 3), ("src", _Points),
+                ("rec", _Points)]
 
 
 class _Tuning(ctypes.Structure):
@@ -136,6 +142,16 @@ def _lib():
         lib.wave_list_variants.restype = i32
         lib.wave_fwd_noalloc.argtypes = [gp, vp, vp, pp, vp, pp, vp, vp, tp, vp, ctypes.POINTER(i32)]
         lib.wave_fwd_noalloc.restype = i32
+        lib.wave_measure_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
+        lib.wave_measure_peaks.restype = i32
+        sp_ = ctypes.POINTER(_Shot)
+        lib.wave_batch_workspace_bytes.argtypes = [gp, i32, sp_, i32, i32]
+        lib.wave_batch_workspace_bytes.restype = ctypes.c_size_t
+        lib.wave_fwd_batched.argtypes = [gp, i32, sp_, vp, vp, vp, vp, i32, tp, vp, ctypes.c_size_t, vp]
+        lib.wave_fwd_batched.restype = i32
+        lib.wave_grad_batched.argtypes = [gp, i32, sp_, vp, vp, vp, vp, i32, vp, i32, tp, vp,
+                                          ctypes.c_size_t, vp]
+        lib.wave_grad_batched.restype = i32
         _LIB = lib
     return _LIB
 
@@ -313,6 +329,108 @@ def grad(grid, m, damp, src_xyz, src_traces, rec_xyz, rec_resid, ckpt, ckpt_ever
     return g_out, ws
 
 
+@dataclass
+class Shot:
+    """One shot of a batch: a window [origin, origin + n) of the global grid,
+    source and receiver coordinates (km) relative to the window origin."""
+    origin: tuple
+    n: tuple
+    src_xyz: object = None
+    rec_xyz: object = None
+
+
+def _shots(shots):
+    arr = (_Shot * len(shots))()
+    keep = []
+    for c, s in zip(arr, shots):
+        c.origin[:] = [int(v) for v in s.origin]
+        c.n[:] = [int(v) for v in s.n]
+        sp, sa = _points(s.src_xyz)
+        rp, ra = _points(s.rec_xyz)
+        c.src, c.rec = sp, rp
+        keep += [sa, ra]
+    return arr, keep
+
+
+def batch_workspace_bytes(grid, shots, ckpt_every=0, concurrency=0):
+    arr, keep = _shots(shots)
+    g = grid.c()
+    n = int(_lib().wave_batch_workspace_bytes(ctypes.byref(g), len(shots), arr, int(ckpt_every),
+                                              int(concurrency)))
+    del keep
+    return n
+
+
+def _traces(x, name, nt, counts):
+    """Per-shot [nt][k_s] blocks, one after another: a list of tensors or one
+    flat tensor already in that layout."""
+    torch = _torch()
+    if isinstance(x, (list, tuple)):
+        for t, k in zip(x, counts):
+            if tuple(t.shape) != (nt, k):
+                raise ValueError("%s block has shape %s, expected %s" % (name, tuple(t.shape), (nt, k)))
+        x = torch.cat([t.reshape(-1) for t in x]) if x else None
+    if x is not None and x.numel() != nt * sum(counts):
+        raise ValueError("%s has %d values, expected %d" % (name, x.numel(), nt * sum(counts)))
+    return x
+
+
+def fwd_batched(grid, shots, m, damp, src_traces, *, concurrency=0, tuning=None, workspace=None,
+                stream=None):
+    """Forward modelling of every shot (wave_fwd_batched).  src_traces: list
+    of [nt][nsrc_s] tensors (or their flat concatenation).  Returns the list
+    of [nt][nrec_s] receiver traces and the workspace."""
+    torch = _torch()
+    n = tuple(grid.n)
+    ns = [0 if s.src_xyz is None else len(s.src_xyz) for s in shots]
+    nr = [0 if s.rec_xyz is None else len(s.rec_xyz) for s in shots]
+    q = _traces(src_traces, "src_traces", grid.nt, ns)
+    out = torch.empty(grid.nt * sum(nr), dtype=torch.float32, device=m.device)
+    ws = _workspace(batch_workspace_bytes(grid, shots, 0, concurrency), m.device, workspace)
+    arr, keep = _shots(shots)
+    g = grid.c()
+    t = tuning.c() if tuning is not None else None
+    code = _lib().wave_fwd_batched(
+        ctypes.byref(g), len(shots), arr, _dev_ptr(m, "m", n), _dev_ptr(damp, "damp", n),
+        _dev_ptr(q, "src_traces") if q is not None and q.numel() else None,
+        _dev_ptr(out, "rec_traces") if out.numel() else None, int(concurrency),
+        ctypes.byref(t) if t is not None else None, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+        _stream(stream))
+    del keep
+    _check(code, "wave_fwd_batched")
+    recs, o = [], 0
+    for k in nr:
+        recs.append(out[o:o + grid.nt * k].view(grid.nt, k))
+        o += grid.nt * k
+    return recs, ws
+
+
+def grad_batched(grid, shots, m, damp, src_traces, rec_resid, ckpt_every, *, concurrency=0,
+                 tuning=None, workspace=None, stream=None):
+    """dJ/dm over all shots (wave_grad_batched); rec_resid: list of [nt][nrec_s]
+    tensors of dJ/dd_s (or their flat concatenation).  Returns (grad, ws)."""
+    torch = _torch()
+    n = tuple(grid.n)
+    ns = [0 if s.src_xyz is None else len(s.src_xyz) for s in shots]
+    nr = [0 if s.rec_xyz is None else len(s.rec_xyz) for s in shots]
+    q = _traces(src_traces, "src_traces", grid.nt, ns)
+    r = _traces(rec_resid, "rec_resid", grid.nt, nr)
+    g_out = torch.empty(n, dtype=torch.float32, device=m.device)
+    ws = _workspace(batch_workspace_bytes(grid, shots, ckpt_every, concurrency), m.device, workspace)
+    arr, keep = _shots(shots)
+    g = grid.c()
+    t = tuning.c() if tuning is not None else None
+    code = _lib().wave_grad_batched(
+        ctypes.byref(g), len(shots), arr, _dev_ptr(m, "m", n), _dev_ptr(damp, "damp", n),
+        _dev_ptr(q, "src_traces") if q is not None and q.numel() else None,
+        _dev_ptr(r, "rec_resid") if r is not None and r.numel() else None, int(ckpt_every),
+        _dev_ptr(g_out, "grad"), int(concurrency), ctypes.byref(t) if t is not None else None,
+        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
+    del keep
+    _check(code, "wave_grad_batched")
+    return g_out, ws
+
+
 def fwd_noalloc(grid, m, damp, src_xyz, src_traces, rec_xyz, rec_out, u_last_out=None, *,
                 tuning=None, stream=None, wait=True):
     """Forward modelling on the library's static workspace (wave_fwd_noalloc).
@@ -335,6 +453,15 @@ def fwd_noalloc(grid, m, damp, src_xyz, src_traces, rec_xyz, rec_out, u_last_out
     del sa, ra
     _check(code, "wave_fwd_noalloc")
     return int(st.value) if wait else None
+
+
+def measure_peaks(stream=None):
+    """Measured (FP32 FMA TFLOP/s with paired FMAs, shared-memory load TB/s)
+    of the current device (wave_measure_peaks)."""
+    f, m = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(_lib().wave_measure_peaks(ctypes.byref(f), ctypes.byref(m), _stream(stream)),
+           "wave_measure_peaks")
+    return f.value, m.value
 
 
 def sweep_stats():
