@@ -36,6 +36,35 @@ METRIC = "acoustic stencil GPts/s tiled vs untiled, % roofline; FWI gradient s/s
 HBM_FALLBACK_GBS = 6800.0
 
 
+# DRAM traffic of one launch of the bench's sweep at full size
+# (dram__bytes_read.sum + dram__bytes_write.sum from one single-pass ncu capture;
+# profiles/traffic_sweep_t1_so8_512.md), valid only for the kernel sources it was
+# taken on: the SHA-256 of csrc/sweep.cuh + csrc/variants.h must match, else the
+# bench reports null.
+TRAFFIC_SRC_SHA256 = "22d121e37adb134db0641a1797f159dda1148f6d84f236078336a86b12c36fd4"
+TRAFFIC_BYTES = {  # ("R T V BZ BY P", chunk, n) -> bytes per launch
+    ("R4 T1 V4 BZ64 BY8 P3", 64, (512, 512, 512)): 2.18e9 + 518.32e6,
+}
+
+
+def _kernel_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("sweep.cuh", "variants.h"):
+        with open(os.path.join(ROOT, "paper_1806_08299_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _traffic(space_order, plan, n):
+    if TRAFFIC_SRC_SHA256 is None or _kernel_sha256() != TRAFFIC_SRC_SHA256:
+        return None
+    key = ("R%d T%d V%d BZ%d BY%d P%d" % (space_order // 2, plan["time_tile"], plan["vec"],
+                                          plan["tile_z"], plan["tile_y"], plan["prefetch"]),
+           plan["tile_x"], tuple(n))
+    return TRAFFIC_BYTES.get(key)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -344,7 +373,9 @@ def run_ours(args):
     avg_launch_ms = sweep_ms / max(launches, 1)
     achieved = alg_bytes / (avg_launch_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": args.traffic, "peak_kind": peak_kind,
+                "frac": achieved / hbm,
+                "traffic": args.traffic if args.traffic is not None else _traffic(p.space_order, plan, p.n),
+                "peak_kind": peak_kind,
                 "kernel": "sweep_kernel<R=%d,T=%d>" % (p.space_order // 2, T),
                 "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_ms,
                 "alu": {"fp32_tflops_measured": fp32_tflops, "flops_per_point": flops_per_pt,

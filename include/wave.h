@@ -76,7 +76,7 @@ extern "C" {
                                  CUDA context stays usable.  Results are undefined.     */
 
 typedef struct wave_grid {
-    int32_t n[3];        /* nx, ny, nz >= space_order + 1 each                     */
+    int32_t n[3];        /* nx, ny, nz >= space_order + 1 each; ny * nz < 2^31      */
     float h[3];          /* grid spacing per axis (km), > 0                          */
     float dt;            /* time step (s), > 0                                       */
     int32_t nt;          /* number of time steps, >= 1                               */
@@ -94,7 +94,7 @@ typedef struct wave_points {
  *               T >= 2 = T steps per launch (time-tile depth, Sec. 4.2).
  *   tile_y    : output rows per block (0 = any compiled variant).
  *   tile_x    : x-chunk length streamed by one block (0 = default).
- *   vec       : z points per thread, 2 or 4 (0 = any compiled variant).
+ *   vec       : z points per thread, 2, 4 or 8 (0 = any compiled variant).
  *   flags     : WAVE_ALLOW_UNSTABLE | WAVE_TIME_SWEEPS | WAVE_AUTOTUNE_SHAPE. */
 typedef struct wave_tuning {
     int32_t time_tile;

@@ -88,7 +88,7 @@ struct PointTable {
 
 struct SweepArgs {
     int nx, ny, nz;          // nz: padded z extent, a multiple of 8
-    long long sx;            // ny * nz
+    int sx;                  // ny * nz (< 2^31, checked on the host)
     long long npad;          // nx * ny * nz
     float *out_hi;           // level n+T (T == 1: may alias level n-1, updated in place)
     float *out_lo;           // level n+T-1 (T >= 2)
@@ -367,6 +367,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
     int *prec = pinj + plen;
     unsigned char *finj = reinterpret_cast<unsigned char *>(prec + plen);
     unsigned char *frec = finj + plen;
+    int my_inj = 0, my_rec = 0;  // this thread found a relevant point in some plane
     for (int k = tid; k < plen; k += S::NTB) {
         const int cp = min(max(pbase + k, 0), a.nx);
         const int ci = min(max(pbase + k + 1, 0), a.nx);
@@ -394,6 +395,8 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
         }
         finj[k] = (unsigned char)fi;
         frec[k] = (unsigned char)fr;
+        my_inj |= fi;
+        my_rec |= fr;
     }
     for (int k = tid; k < 2 * (T - 1) * S::PLANE; k += S::NTB) splane[k] = 0.f;
     if (tid == 0) {
@@ -403,7 +406,10 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
+    // whether any plane of this block holds a relevant point at all: most
+    // blocks hold none and then never read the per-plane flags
+    const bool any_inj = __syncthreads_or(my_inj) != 0;
+    const bool any_rec = __syncthreads_or(my_rec) != 0;
 
     if (tid >= S::NT) {
         // ------------------------------ producer warp ------------------------------
@@ -453,10 +459,11 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
 
     // ------------------------------ consumer threads ------------------------------
     // Register queues, one per stage: q[s-1] holds level n+s-1 (stage s's
-    // input) on the 2R+1 planes around stage s's centre.  They are circular:
-    // the plane loop is unrolled QL times so that, in unrolled copy u, logical
-    // position k (0 = oldest) lives in q[.][(u + 1 + k) % QL] after that
-    // iteration's push, a compile-time index (no register moves).
+    // input) on the 2R+1 planes around stage s's centre, oldest first
+    // (q[.][R] is the centre).  A push shifts the queue by one register pair
+    // per entry: a few moves per plane, but one copy of the loop body, whose
+    // instruction footprint a (2R+1)-fold unroll for compile-time rotation
+    // would multiply.
     constexpr int V2 = V / 2;  // point pairs per thread: arithmetic in paired FP32
     float2 q[T][QL][V2];
 #pragma unroll
@@ -471,15 +478,13 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
     uint32_t pf = 0;             // parity of the current full barrier phase
     int cur = 0;
     bool stop = false;
-    for (int it0 = 0; it0 < niter && !stop; it0 += QL) {
-#pragma unroll
-        for (int u = 0; u < QL; ++u) {
-            const int it = it0 + u;
-            if (it >= niter) break;
-            // T == 1 has no per-plane consumer barrier: each warp stops on
-            // its own, at a warp-uniform point, once a wait anywhere in the
-            // block ran out
-            if (T == 1 && __any_sync(0xffffffffu, *abort_flag != 0)) {
+#pragma unroll 1
+    for (int it = 0; it < niter && !stop; ++it) {
+        {
+            // T == 1 has no per-plane consumer barrier: every 8 planes each
+            // warp checks, at a warp-uniform point, whether a wait anywhere in
+            // the block ran out (its own expired waits stop it at once)
+            if (T == 1 && (it & 7) == 0 && __any_sync(0xffffffffu, *abort_flag != 0)) {
                 stop = true;
                 break;
             }
@@ -497,7 +502,11 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
             }
             if (lane0) mbar_arrive(empF + sf);  // this warp is past this phase of full[sf]
             // level n of plane c0 enters stage 1's queue (replacing its oldest)
-            ld2<V>(q[0][u], ringU + (size_t)su * (S::USLOT / 4) + ownU);
+            #pragma unroll
+            for (int k = 0; k < QL - 1; ++k)
+#pragma unroll
+                for (int j = 0; j < V2; ++j) q[0][k][j] = q[0][k + 1][j];
+            ld2<V>(q[0][QL - 1], ringU + (size_t)su * (S::USLOT / 4) + ownU);
             const int suc = su - R < 0 ? su - R + S::DU : su - R;  // U slot of plane c0 - R
             const unsigned char *kslot = ringK + (size_t)sk * S::KSLOT;
 
@@ -508,8 +517,9 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                 // rows this stage computes, and only once the item's own planes
                 // fill its x-queue (local iteration 2sR on); earlier iterations
                 // would only produce planes no later stage or store reads
-                const bool rowok = row >= s * R && row < S::H0 - s * R && it >= 2 * s * R;
-                const long long pidx = (long long)cs * a.sx + yz;
+                // (T = 1: every thread row is a stage-1 row)
+                const bool rowok = (T == 1 || (row >= s * R && row < S::H0 - s * R)) && it >= 2 * s * R;
+                const long long pidx = (long long)cs * a.sx + yz;  // 32 x 32 -> 64-bit product
                 float2 un[V2], dd[V2];
 #pragma unroll
                 for (int j = 0; j < V2; ++j) { un[j] = make_float2(0.f, 0.f); dd[j] = un[j]; }
@@ -529,7 +539,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                     for (int j = 0; j < ZW / V; ++j) ld2<V>(zz + j * V2, Pc + ownU - S::RP + j * V);
 #pragma unroll
                     for (int i = 0; i < ZW / 2 - 1; ++i) zo[i] = make_float2(zz[i].y, zz[i + 1].x);
-                    const int qc = (u + 1 + R) % QL;  // centre (logical R)
+                    const int qc = R;  // centre
                     // R >= 3: three independent accumulation chains (centre and x,
                     // y, z), summed at the end, L u = (lx + ly) + lz, for latency;
                     // R <= 2: one chain, in the order centre, then per k x, y, z
@@ -539,7 +549,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                         float2 yp[V2], ym[V2];
                         ld2<V>(yp, Pc + ownU + k * S::PW);
                         ld2<V>(ym, Pc + ownU - k * S::PW);
-                        const int qp = (u + 1 + R + k) % QL, qm = (u + 1 + R - k) % QL;
+                        const int qp = R + k, qm = R - k;
 #pragma unroll
                         for (int j = 0; j < V2; ++j) {
                             const int op = S::RP + 2 * j + k, om = S::RP + 2 * j - k;
@@ -573,7 +583,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                     } else {
                         // level n+s-2 on plane cs: oldest of stage s-1's queue
 #pragma unroll
-                        for (int j = 0; j < V2; ++j) up[j] = q[s > 1 ? s - 2 : 0][(u + 1) % QL][j];
+                        for (int j = 0; j < V2; ++j) up[j] = q[s > 1 ? s - 2 : 0][0][j];
                     }
                     float2 du[V2];  // u^n - u^{n-1}
 #pragma unroll
@@ -592,7 +602,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                             dd[j] = __ffma2_rn(cCv[j], lap[j], __fmul2_rn(e[j], du[j]));
                     }
                     // point sources: f = sum_s w q_s (ascending source order), u += C f
-                    if (finj[cs - pbase] && in_yz) {
+                    if (any_inj && finj[cs - pbase] && in_yz) {
                         const int e0 = pinj[cs - pbase], e1 = pinj[cs - pbase + 1];
                         // each grid point appears at most once in the table, but up
                         // to V table points can fall in this thread's V z-points
@@ -626,7 +636,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                 }
                 const bool own_pt = inner && cs >= X0 && cs < X1;
                 if (own_pt) {
-                    if (frec[cs - pbase]) {
+                    if (any_rec && frec[cs - pbase]) {
                         const int e0 = prec[cs - pbase], e1 = prec[cs - pbase + 1];
                         for (int e = e0; e < e1; ++e) {
                             const int4 pt = a.rec.pts[e];
@@ -654,9 +664,14 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                     }
                 }
                 if (s < T) {
-                    // level n+s of plane cs enters stage s+1's queue (replacing its oldest)
+                    // level n+s of plane cs enters stage s+1's queue (dropping its oldest)
+                    float2(&qn)[QL][V2] = q[s < T ? s : 0];
 #pragma unroll
-                    for (int j = 0; j < V2; ++j) q[s < T ? s : 0][u][j] = un[j];
+                    for (int k = 0; k < QL - 1; ++k)
+#pragma unroll
+                        for (int j = 0; j < V2; ++j) qn[k][j] = qn[k + 1][j];
+#pragma unroll
+                    for (int j = 0; j < V2; ++j) qn[QL - 1][j] = un[j];
                 }
             }
 
@@ -672,10 +687,10 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                 }
             }
             if constexpr (T > 1) {
-                // centres of stages >= 2 for the next iteration (logical R+1)
+                // centres of stages >= 2 for the next iteration (position R+1)
 #pragma unroll
                 for (int s = 2; s <= T; ++s)
-                    st2<V>(splane + ((s - 2) * 2 + (cur ^ 1)) * S::PLANE + ownU, q[s - 1][(u + 2 + R) % QL]);
+                    st2<V>(splane + ((s - 2) * 2 + (cur ^ 1)) * S::PLANE + ownU, q[s - 1][R + 1]);
                 const bool halt = consumer_sync_any(S::NT, *abort_flag != 0);
                 cur ^= 1;
                 if (halt) {

@@ -61,6 +61,7 @@ int check_grid(const wave_grid *g, Dims *d)
     d->npad = (long long)d->nx * d->ny * d->nzp;
     d->n = (long long)d->nx * d->ny * d->nz;
     if (d->npad > (1LL << 36)) return WAVE_EINVAL;
+    if ((long long)d->ny * d->nzp >= (1LL << 31)) return WAVE_EINVAL;  // one x-plane < 2^31 points
     return WAVE_OK;
 }
 
@@ -258,17 +259,6 @@ struct Carver {
     }
 };
 
-size_t table_bytes(const Dims &d, int np)
-{
-    Carver c(nullptr, 0, true);
-    c.take<int>(d.nx + 1);
-    c.take<int4>((size_t)8 * np);
-    c.take<int>((size_t)8 * np);
-    c.take<float>((size_t)8 * np);
-    c.take<float>((size_t)8 * np);
-    return c.off;
-}
-
 void carve_table(Carver &c, const Dims &d, int np, DevTable *t)
 {
     t->plane_start = c.take<int>(d.nx + 1);
@@ -399,7 +389,7 @@ int occupancy(const SweepVariant *v, int chunk)
         auto it = cache.find(key);
         if (it != cache.end()) return it->second;
     }
-    cudaFuncSetAttribute(v->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    wt::allow_max_dynamic_smem(v->func);
     int occ = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(&occ, v->func, v->threads, smem,
                                                                cudaOccupancyDefault) != cudaSuccess ||
@@ -618,7 +608,7 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         a.nx = d.nx;
         a.ny = d.ny;
         a.nz = d.nzp;
-        a.sx = (long long)d.ny * d.nzp;
+        a.sx = (int)((long long)d.ny * d.nzp);
         a.npad = d.npad;
         a.status = job.status;
         wt::SweepMaps maps;
@@ -814,6 +804,28 @@ int check_points(const wave_points *p, bool need_data_ptr, const void *data)
 int npts_of(const wave_points *p) { return p ? p->npts : 0; }
 
 }  // namespace
+
+namespace wt {
+
+cudaError_t allow_max_dynamic_smem(const void *func)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, bool> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, func})) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return e;
+    done[{dev, func}] = true;
+    return cudaSuccess;
+}
+
+}  // namespace wt
 
 // ===========================================================================
 // C ABI

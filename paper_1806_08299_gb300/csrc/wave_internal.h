@@ -40,19 +40,20 @@ cudaError_t launch_unpad(const float *src, int nx, int ny, int nz, int nzp, floa
 cudaError_t launch_gather(const float *corner, const float *w, int rows, int npts, int row_dir,
                           float *out, cudaStream_t s);
 
+// Raise the dynamic shared-memory limit of kernel `func` on the current
+// device to the device's opt-in maximum, once per (device, kernel); it is
+// never lowered, so occupancy queries and launches of any chunk size agree
+// (wave_api.cu).
+cudaError_t allow_max_dynamic_smem(const void *func);
+
 template <int R, int T, int V, int BZ, int BY, int P, int MB>
 cudaError_t launch_sweep(int nblocks, cudaStream_t stream, const SweepArgs &a, const Stencil &st,
                          const SweepMaps &m)
 {
     using S = SweepShape<R, T, V, BZ, BY, P, MB>;
     const size_t smem = S::smem_bytes(a.chunk);
-    static size_t attr_bytes = 0;
-    if (smem > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R, T, V, BZ, BY, P, MB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_bytes = smem;
-    }
+    cudaError_t e = allow_max_dynamic_smem((const void *)sweep_kernel<R, T, V, BZ, BY, P, MB>);
+    if (e != cudaSuccess) return e;
     sweep_kernel<R, T, V, BZ, BY, P, MB><<<nblocks, S::NTB, smem, stream>>>(a, st, m);
     return cudaGetLastError();
 }

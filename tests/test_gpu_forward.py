@@ -247,3 +247,17 @@ def test_bounded_wait_timeout_reports_status(wavelib, cuda, oracle):
     _, uref, _ = _oracle(oracle, grid, m, damp, src, q, rec)
     assert _relerr(ul[0], uref[0]) <= TOL
     torch.cuda.synchronize()
+
+
+def test_chunk_sizes_in_any_order(wavelib, cuda, oracle):
+    # A large x-chunk, then a shape whose default-chunk search queries many
+    # smaller chunks, then a mid-size chunk: every launch of the same kernel
+    # must get the dynamic shared memory it asks for.
+    so, nt = 8, 6
+    for n, tile_x in (((96, 20, 24), 96), ((300, 18, 20), 0), ((80, 20, 24), 40)):
+        m, damp, src, q, rec = inputs.random_problem(n, so, nt, seed=3)
+        dt = 0.4 * wavelib.cfl_dt(so, (inputs.H,) * 3, 3.0)
+        grid = wavelib.Grid(n, (inputs.H,) * 3, dt, nt, so)
+        d, ul = _run(wavelib, cuda, grid, m, damp, src, q, rec, 1, tile_x=tile_x)
+        _, uref, _ = _oracle(oracle, grid, m, damp, src, q, rec)
+        assert _relerr(ul[0], uref[0]) <= TOL
