@@ -192,10 +192,23 @@ def _cpu_sample(p, target_s=15.0, max_steps=64):
     steps = int(max(2, min(max_steps, target_s / max(t2 / 2, 1e-6))))
     dt_run = run(steps)
     pts = m.size * steps
+    # the paper's skewed time-tiled loop nest (time tile 4, 8 x 8 space tiles), and the untiled
+    # loop on one core, each on 8 steps of the same slab
+    t0 = time.perf_counter()
+    oracle.forward_tiled(m, damp, h, dt, 8, p.space_order, p.src_xyz.astype(np.float64), q[:8],
+                         p.rec_xyz.astype(np.float64), tt=4, bx=8, by=8)
+    t_tiled = time.perf_counter() - t0
+    oracle.set_threads(1)
+    t_one = run(2)
+    oracle.set_threads(ncores)
     return {"value": pts / dt_run / 1e9, "unit": "GPts/s", "cores": oracle.max_threads(),
             "kind": "oracle", "seconds": dt_run,
+            "tiled_value": m.size * 8 / t_tiled / 1e9,
+            "single_core_value": m.size * 2 / t_one / 1e9,
             "sample": "FP64 oracle forward (untiled loop, OpenMP) on the top %d-plane z-slab "
-                      "%dx%dx%d of the workload for %d steps" % (nzs, p.n[0], p.n[1], nzs, steps)}
+                      "%dx%dx%d of the workload for %d steps; tiled_value: the paper's skewed "
+                      "time-tiled loop (tt 4, 8x8 tiles) on 8 steps; single_core_value: the untiled "
+                      "loop on one core, 2 steps" % (nzs, p.n[0], p.n[1], nzs, steps)}
 
 
 def run_reference(args):
