@@ -116,8 +116,11 @@ struct SweepArgs {
 //   u    : level n, box (PW, H0, 1)
 //   um   : level n-1, box (W0, H0 - 2R, 1)
 //   B, C : coefficients, box (W0, H0 - 2R, 1)
+//   x0, x1 : the gradient sweeps' extra inputs (XB >= 1, same box as B):
+//          second-difference mode x0 = E; imaging-condition mode x0 = this
+//          step's stored D row, x1 = the gradient accumulator G
 struct SweepMaps {
-    CUtensorMap u, um, B, C;
+    CUtensorMap u, um, B, C, x0, x1;
 };
 
 // Shared memory of the per-plane sparse slices for an x-chunk of `chunk`
@@ -129,7 +132,10 @@ __host__ __device__ constexpr size_t sweep_table_bytes(int chunk, int rt)
     return (10 * (size_t)(chunk + 3 * rt + 2) + 15) / 16 * 16;
 }
 
-template <int R, int T, int V, int BZ, int BY, int P, int MB>
+// XB: extra ring-K boxes of the gradient sweeps (0 = none: forward and
+// adjoint; 1 = E, second-difference mode; 2 = D and G, imaging-condition
+// mode), loaded by TMA with the other inputs instead of by the consumers.
+template <int R, int T, int V, int BZ, int BY, int P, int MB, int XB = 0>
 struct SweepShape {
     static constexpr int RT = R * T;
     static constexpr int A0 = ((RT + 3) / 4) * 4;   // z halo, keeps 16-byte alignment
@@ -153,8 +159,8 @@ struct SweepShape {
     static constexpr unsigned KBOX = W0 * HK * 4;   // bytes of one K box (um, B or C)
     static constexpr unsigned USLOT = (UBOX + 127) / 128 * 128;
     static constexpr unsigned KBOXP = (KBOX + 127) / 128 * 128;
-    static constexpr unsigned KSLOT = 3 * KBOXP;
-    static constexpr unsigned TXB = UBOX + 3 * KBOX; // bytes landing per iteration
+    static constexpr unsigned KSLOT = (3 + XB) * KBOXP;
+    static constexpr unsigned TXB = UBOX + (3 + XB) * KBOX; // bytes landing per iteration
     static constexpr int PLANE = PW * H0;           // centre plane (floats), stages >= 2
     static constexpr size_t OFF_K = (size_t)DU * USLOT;
     static constexpr size_t OFF_S = OFF_K + (size_t)DK * KSLOT;
@@ -168,6 +174,7 @@ struct SweepShape {
     static_assert(MB >= 1 && (size_t)MB * (SMEM + 4096) <= 228 * 1024 && MB * NTB <= 2048,
                   "blocks per SM do not fit shared memory or thread slots");
     static_assert(V == 2 || V == 4 || V == 8, "V must be 2, 4 or 8");
+    static_assert(XB >= 0 && XB <= 2 && (XB == 0 || T == 1), "extra boxes only for untiled sweeps");
     // a thread's V points start at a multiple of V (rows are padded to a
     // multiple of 8), so they never straddle the end of a row
     static_assert(V < 8 || ((A0 - ZL) % 8 == 0 && BZ % 8 == 0), "V = 8 needs 8-aligned thread columns");
@@ -313,12 +320,12 @@ __device__ __forceinline__ float2 fsub2_rn(float2 u, float2 w)
     return __fadd2_rn(u, make_float2(-w.x, -w.y));
 }
 
-template <int R, int T, int V, int BZ, int BY, int P, int MB>
-__global__ void __launch_bounds__(SweepShape<R, T, V, BZ, BY, P, MB>::NTB, MB)
+template <int R, int T, int V, int BZ, int BY, int P, int MB, int XB = 0>
+__global__ void __launch_bounds__(SweepShape<R, T, V, BZ, BY, P, MB, XB>::NTB, MB)
 sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stencil st,
              const __grid_constant__ SweepMaps mp)
 {
-    using S = SweepShape<R, T, V, BZ, BY, P, MB>;
+    using S = SweepShape<R, T, V, BZ, BY, P, MB, XB>;
     constexpr int QL = 2 * R + 1;
     constexpr int ZW = V + 2 * S::RP;  // z window per thread (floats)
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -335,6 +342,12 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
         if (threadIdx.x == 0 && blockIdx.x == 0) atomicMin(a.status, -1 /* WAVE_EINVAL */);
         return;
     }
+    // Programmatic dependent launch: once every block of this launch has
+    // started, the next launch on the stream may start its blocks, which run
+    // their prologue (sparse-table scan, barrier set-up) and then wait below
+    // for this launch to complete before touching any field.  Without the
+    // launch attribute both instructions do nothing.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int tid = threadIdx.x;
     const int col = S::ZL + (tid % S::LZ) * V;  // layout column of this thread's V points
     const int row = R + tid / S::LZ;            // layout row
@@ -410,6 +423,9 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
     // blocks hold none and then never read the per-plane flags
     const bool any_inj = __syncthreads_or(my_inj) != 0;
     const bool any_rec = __syncthreads_or(my_rec) != 0;
+    // the previous launch on the stream (the previous time step) has completed
+    // and its writes are visible; every field access below comes after this
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     if (tid >= S::NT) {
         // ------------------------------ producer warp ------------------------------
@@ -444,6 +460,8 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                     tma_load_3d(kslot, &mp.um, gz0, gy0 + R, c0 - R, bf);
                     tma_load_3d(kslot + S::KBOXP, &mp.B, gz0, gy0 + R, c0 - R, bf);
                     tma_load_3d(kslot + 2 * S::KBOXP, &mp.C, gz0, gy0 + R, c0 - R, bf);
+                    if constexpr (XB >= 1) tma_load_3d(kslot + 3 * S::KBOXP, &mp.x0, gz0, gy0 + R, c0 - R, bf);
+                    if constexpr (XB >= 2) tma_load_3d(kslot + 4 * S::KBOXP, &mp.x1, gz0, gy0 + R, c0 - R, bf);
                 }
                 if (++ju == S::DU) { ju = 0; ++ru; }
                 if (++jk == S::DK) { jk = 0; ++rk; }
@@ -523,9 +541,9 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                 float2 un[V2], dd[V2];
 #pragma unroll
                 for (int j = 0; j < V2; ++j) { un[j] = make_float2(0.f, 0.f); dd[j] = un[j]; }
+                const int kk = sk - (s - 1) * R;
+                const unsigned char *ks = ringK + (size_t)(kk < 0 ? kk + S::DK : kk) * S::KSLOT;
                 if (rowok) {
-                    const int kk = sk - (s - 1) * R;
-                    const unsigned char *ks = ringK + (size_t)(kk < 0 ? kk + S::DK : kk) * S::KSLOT;
                     float2 cBv[V2], cCv[V2], up[V2], lap[V2];
                     ld2<V>(cBv, reinterpret_cast<const float *>(ks + S::KBOXP) + ownK);
                     ld2<V>(cCv, reinterpret_cast<const float *>(ks + 2 * S::KBOXP) + ownK);
@@ -596,7 +614,10 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                     if (a.dstore != nullptr && in_yz && plane_in) {
                         // u^{n+1} - 2u^n + u^{n-1} = E (u^n - u^{n-1}) + C (L u^n + f^n)
                         float2 e[V2];
-                        ldg2<V>(e, a.cE + pidx);
+                        if constexpr (XB == 1)
+                            ld2<V>(e, reinterpret_cast<const float *>(ks + 3 * S::KBOXP) + ownK);
+                        else
+                            ldg2<V>(e, a.cE + pidx);
 #pragma unroll
                         for (int j = 0; j < V2; ++j)
                             dd[j] = __ffma2_rn(cCv[j], lap[j], __fmul2_rn(e[j], du[j]));
@@ -656,8 +677,13 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
                         st2<V>(a.dstore + (a.d_row0 + (long long)a.d_dir * (s - 1)) * a.npad + pidx, dd);
                     if (a.gacc != nullptr) {
                         float2 dl[V2], g[V2];
-                        ldg2<V>(dl, a.dload + (a.l_row0 + (long long)a.l_dir * (s - 1)) * a.npad + pidx);
-                        ld2<V>(g, a.gacc + pidx);
+                        if constexpr (XB == 2) {
+                            ld2<V>(dl, reinterpret_cast<const float *>(ks + 3 * S::KBOXP) + ownK);
+                            ld2<V>(g, reinterpret_cast<const float *>(ks + 4 * S::KBOXP) + ownK);
+                        } else {
+                            ldg2<V>(dl, a.dload + (a.l_row0 + (long long)a.l_dir * (s - 1)) * a.npad + pidx);
+                            ld2<V>(g, a.gacc + pidx);
+                        }
 #pragma unroll
                         for (int j = 0; j < V2; ++j) g[j] = __ffma2_rn(un[j], dl[j], g[j]);
                         st2<V>(a.gacc + pidx, g);

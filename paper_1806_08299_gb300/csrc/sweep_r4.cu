@@ -3,3 +3,4 @@
 #include "wave_internal.h"
 
 WAVE_DEFINE_RADIUS(4)
+WAVE_DEFINE_MODES(4)

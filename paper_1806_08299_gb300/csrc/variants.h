@@ -12,11 +12,11 @@
 #pragma once
 
 #define WAVE_SWEEP_VARIANTS_R1(X)                                                                  \
-    X(1, 1, 2, 64, 8, 3, 3) X(1, 1, 4, 64, 16, 4, 2) X(1, 1, 8, 64, 16, 2, 2) X(1, 2, 4, 56, 16, 1, 1) \
-    X(1, 3, 4, 56, 16, 2, 1) X(1, 4, 4, 56, 16, 2, 1)
+    X(1, 1, 2, 64, 8, 3, 3) X(1, 1, 4, 64, 16, 4, 2) X(1, 1, 8, 64, 16, 2, 2) X(1, 2, 4, 56, 16, 2, 2) \
+    X(1, 3, 4, 56, 16, 2, 1) X(1, 4, 4, 56, 16, 2, 1) X(1, 4, 4, 56, 8, 1, 2)
 #define WAVE_SWEEP_VARIANTS_R2(X)                                                                  \
     X(2, 1, 8, 64, 16, 2, 2) X(2, 1, 2, 64, 12, 2, 2) X(2, 1, 2, 64, 8, 3, 3) X(2, 1, 4, 64, 16, 4, 1) \
-    X(2, 2, 4, 56, 16, 1, 1) X(2, 2, 2, 56, 16, 2, 1) X(2, 3, 4, 56, 12, 2, 1) X(2, 4, 4, 48, 8, 1, 1)
+    X(2, 2, 4, 56, 16, 1, 1) X(2, 2, 2, 56, 16, 2, 1) X(2, 2, 4, 56, 8, 2, 2) X(2, 3, 4, 56, 12, 2, 1) X(2, 4, 4, 48, 8, 1, 1)
 #define WAVE_SWEEP_VARIANTS_R3(X) \
     X(3, 1, 2, 64, 12, 2, 2) X(3, 1, 4, 64, 16, 4, 1) X(3, 1, 8, 64, 16, 2, 2) X(3, 2, 4, 56, 16, 1, 1)
 #define WAVE_SWEEP_VARIANTS_R4(X)                                                                  \
@@ -31,3 +31,12 @@
     X(7, 1, 2, 64, 8, 2, 2) X(7, 1, 4, 64, 8, 3, 1)
 #define WAVE_SWEEP_VARIANTS_R8(X) \
     X(8, 1, 2, 64, 8, 2, 1) X(8, 1, 4, 64, 8, 3, 1)
+
+// Gradient-mode variants Y(R, T, V, BZ, BY, P, MB, XB): the untiled default
+// shape of a radius with XB extra ring-K boxes (1: E for the second-difference
+// sweep; 2: D and G for the imaging-condition sweep), so that those sweeps
+// stream every input through TMA.  A shape without a mode variant runs its
+// gradient sweeps on the plain variant, which reads the extras with ordinary
+// loads.
+#define WAVE_SWEEP_MODE_VARIANTS_R2(Y) Y(2, 1, 8, 64, 16, 2, 2, 1) Y(2, 1, 8, 64, 16, 2, 2, 2)
+#define WAVE_SWEEP_MODE_VARIANTS_R4(Y) Y(4, 1, 4, 64, 8, 2, 3, 1) Y(4, 1, 4, 64, 8, 2, 3, 2)

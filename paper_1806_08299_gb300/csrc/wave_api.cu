@@ -427,6 +427,19 @@ int default_chunk(const Dims &d, const SweepVariant *v)
     return best;
 }
 
+// The gradient-mode variant (XB = mode) of untiled shape v, or nullptr.
+const SweepVariant *mode_variant(const SweepVariant *v, int mode)
+{
+    const SweepVariant *vs = nullptr;
+    int nv = 0;
+    if (v->R == 2) nv = wt::sweep_mode_variants_r2(&vs);
+    if (v->R == 4) nv = wt::sweep_mode_variants_r4(&vs);
+    for (int i = 0; i < nv; ++i)
+        if (vs[i].T == v->T && vs[i].V == v->V && vs[i].BZ == v->BZ && vs[i].BY == v->BY && vs[i].XB == mode)
+            return &vs[i];
+    return nullptr;
+}
+
 // Pick the variant for radius R with time tile T (and tile_y / vec if given).
 const SweepVariant *find_variant(int R, int T, int tile_y, int vec)
 {
@@ -601,8 +614,18 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         if (ckpt != nullptr) limit = std::min(limit, ckpt_every - (j0 + j) % ckpt_every);
         const SweepVariant *v = plan.v->T <= limit ? plan.v : fallback_variant(R, limit);
         if (v == nullptr) return WAVE_EUNSUPPORTED;
-        const int chunk =
+        int chunk =
             std::min((v == plan.v && plan.chunk > 0) ? plan.chunk : default_chunk(d, v), max_chunk(v));
+        // gradient sweeps: the mode variant of the same untiled shape, if compiled,
+        // streams their extra inputs (E, or D and G) through TMA
+        const int mode = job.gacc != nullptr ? 2 : (job.dstore != nullptr ? 1 : 0);
+        if (mode > 0 && v->T == 1) {
+            const SweepVariant *mv = mode_variant(v, mode);
+            if (mv != nullptr) {
+                v = mv;
+                chunk = std::min(chunk, max_chunk(mv));
+            }
+        }
         SweepArgs a;
         std::memset(&a, 0, sizeof(a));
         a.nx = d.nx;
@@ -616,6 +639,12 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         if (!rc) rc = encode_map(&maps.um, s.buf[s.b], d, v->W0, v->HK);
         if (!rc) rc = encode_map(&maps.B, job.cB, d, v->W0, v->HK);
         if (!rc) rc = encode_map(&maps.C, job.cC, d, v->W0, v->HK);
+        if (!rc && v->XB == 1) rc = encode_map(&maps.x0, job.cE, d, v->W0, v->HK);
+        if (!rc && v->XB == 2) {
+            const long long row = job.l_base + (long long)job.l_dir * j;  // this step's D row
+            rc = encode_map(&maps.x0, job.dload + row * d.npad, d, v->W0, v->HK);
+            if (!rc) rc = encode_map(&maps.x1, job.gacc, d, v->W0, v->HK);
+        }
         if (rc) return rc;
         int spare[2], ns = 0;
         for (int i = 0; i < 4; ++i)

@@ -16,6 +16,7 @@ struct SweepVariant {
     cudaError_t (*launch)(int nblocks, cudaStream_t stream, const SweepArgs &a, const Stencil &st,
                           const SweepMaps &m);
     const void *func;
+    int XB;  // extra ring-K boxes of a gradient-mode variant (0: forward and adjoint)
 };
 
 // Variants of radius r (defined in sweep_r<r>.cu).
@@ -27,6 +28,10 @@ int sweep_variants_r5(const SweepVariant **out);
 int sweep_variants_r6(const SweepVariant **out);
 int sweep_variants_r7(const SweepVariant **out);
 int sweep_variants_r8(const SweepVariant **out);
+
+// Gradient-mode variants (XB = 1, 2) of radius r; radii without any return 0.
+int sweep_mode_variants_r2(const SweepVariant **out);
+int sweep_mode_variants_r4(const SweepVariant **out);
 
 // Auxiliary kernels (aux_kernels.cu).  Status codes are written to status[0]
 // with atomicMin, so the most severe (most negative) error wins.
@@ -46,16 +51,28 @@ cudaError_t launch_gather(const float *corner, const float *w, int rows, int npt
 // (wave_api.cu).
 cudaError_t allow_max_dynamic_smem(const void *func);
 
-template <int R, int T, int V, int BZ, int BY, int P, int MB>
+template <int R, int T, int V, int BZ, int BY, int P, int MB, int XB = 0>
 cudaError_t launch_sweep(int nblocks, cudaStream_t stream, const SweepArgs &a, const Stencil &st,
                          const SweepMaps &m)
 {
-    using S = SweepShape<R, T, V, BZ, BY, P, MB>;
+    using S = SweepShape<R, T, V, BZ, BY, P, MB, XB>;
     const size_t smem = S::smem_bytes(a.chunk);
-    cudaError_t e = allow_max_dynamic_smem((const void *)sweep_kernel<R, T, V, BZ, BY, P, MB>);
+    cudaError_t e = allow_max_dynamic_smem((const void *)sweep_kernel<R, T, V, BZ, BY, P, MB, XB>);
     if (e != cudaSuccess) return e;
-    sweep_kernel<R, T, V, BZ, BY, P, MB><<<nblocks, S::NTB, smem, stream>>>(a, st, m);
-    return cudaGetLastError();
+    // programmatic dependent launch: the sweep may start while the previous
+    // kernel on the stream finishes (the kernel waits for it before any field
+    // access, see sweep.cuh)
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nblocks);
+    cfg.blockDim = dim3((unsigned)S::NTB);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sweep_kernel<R, T, V, BZ, BY, P, MB, XB>, a, st, m);
 }
 
 }  // namespace wt
@@ -68,7 +85,28 @@ cudaError_t launch_sweep(int nblocks, cudaStream_t stream, const SweepArgs &a, c
      wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_>::HK,                                          \
      wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_>::SMEM,                                        \
      &wt::launch_sweep<R_, T_, V_, BZ_, BY_, P_, MB_>,                                           \
-     (const void *)&wt::sweep_kernel<R_, T_, V_, BZ_, BY_, P_, MB_>},
+     (const void *)&wt::sweep_kernel<R_, T_, V_, BZ_, BY_, P_, MB_>, 0},
+
+#define WAVE_MODE_VARIANT_ENTRY(R_, T_, V_, BZ_, BY_, P_, MB_, XB_)                               \
+    {R_, T_, V_, BZ_, BY_, P_, wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>::NTB,           \
+     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>::W0,                                     \
+     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>::H0,                                     \
+     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>::PW,                                     \
+     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>::HK,                                     \
+     wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>::SMEM,                                   \
+     &wt::launch_sweep<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>,                                      \
+     (const void *)&wt::sweep_kernel<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>, XB_},
+
+#define WAVE_DEFINE_MODES(r_)                                                                     \
+    namespace wt {                                                                                \
+    static const SweepVariant kModeVariants_r##r_[] = {                                           \
+        WAVE_SWEEP_MODE_VARIANTS_R##r_(WAVE_MODE_VARIANT_ENTRY)};                                 \
+    int sweep_mode_variants_r##r_(const SweepVariant **out)                                       \
+    {                                                                                             \
+        *out = kModeVariants_r##r_;                                                               \
+        return (int)(sizeof(kModeVariants_r##r_) / sizeof(kModeVariants_r##r_[0]));               \
+    }                                                                                             \
+    }
 
 #define WAVE_DEFINE_RADIUS(r_)                                                                    \
     namespace wt {                                                                                \
