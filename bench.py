@@ -41,9 +41,9 @@ HBM_FALLBACK_GBS = 6800.0
 # profiles/traffic_sweep_t1_so8_512.md), valid only for the kernel sources it was
 # taken on: the SHA-256 of csrc/sweep.cuh + csrc/variants.h must match, else the
 # bench reports null.
-TRAFFIC_SRC_SHA256 = "22d121e37adb134db0641a1797f159dda1148f6d84f236078336a86b12c36fd4"
+TRAFFIC_SRC_SHA256 = "9f77c73d3aa79e0d17d678df377418655c41f9a550ee80f1824e995a6bdf07d1"
 TRAFFIC_BYTES = {  # ("R T V BZ BY P", chunk, n) -> bytes per launch
-    ("R4 T1 V4 BZ64 BY8 P3", 64, (512, 512, 512)): 2.18e9 + 518.32e6,
+    ("R4 T1 V4 BZ64 BY8 P3", 64, (512, 512, 512)): 2179188992 + 517769216,
 }
 
 
