@@ -232,13 +232,16 @@ size_t wave_batch_workspace_bytes(const wave_grid *g, int32_t nshots, const wave
 /* Forward modelling of every shot.  m, damp: device, global [nx][ny][nz].
  * src_traces: device, the shots' [nt][nsrc_s] blocks one after another (shot
  * order); rec_traces: device out, the shots' [nt][nrec_s] blocks likewise.
- * Each shot runs wave_fwd on its window (the window of m and damp is copied
- * into the workspace first); up to `concurrency` shots run at once on
- * library-owned streams that wait for `stream` at the start and that `stream`
- * waits for at the end.  tuning applies to every shot; NULL or time_tile == 0
- * means the library's default untiled variant (no per-shape autotuning).
- * wave_status(ws, stream) reports the most severe device status of all shots.
- * Results equal wave_fwd on each window, bit for bit. */
+ * Shots run in groups of `concurrency` consecutive shots; the window of m
+ * and damp of each is copied into the workspace first.  With the untiled
+ * default plan (tuning NULL or time_tile 0 or 1 with the default shape) the
+ * shots of a group advance in lockstep on `stream`: one launch of the batched
+ * sweep kernel per time step covers every shot of the group.  Any other plan
+ * runs wave_fwd per shot on library-owned streams that wait for `stream` at
+ * the start and that `stream` waits for at the end.  tuning applies to every
+ * shot; time_tile == 0 means the default untiled variant (no per-shape
+ * autotuning).  wave_status(ws, stream) reports the most severe device status
+ * of all shots.  Results equal wave_fwd on each window, bit for bit. */
 int32_t wave_fwd_batched(const wave_grid *g, int32_t nshots, const wave_shot *shots,
                          const float *m, const float *damp, const float *src_traces,
                          float *rec_traces, int32_t concurrency, const wave_tuning *tuning,
@@ -246,12 +249,12 @@ int32_t wave_fwd_batched(const wave_grid *g, int32_t nshots, const wave_shot *sh
 
 /* Gradient of J = sum over shots of J_s with respect to the global m, for
  * fixed residuals rec_resid (device, the shots' [nt][nrec_s] blocks of
- * dJ/dd_s, shot order).  Per shot: wave_fwd with checkpoints every
- * ckpt_every steps on the window, then wave_grad on the window; the window
- * gradients are added into per-slot global accumulators (shot i runs on
- * slot i mod concurrency, in shot order), and the slots are summed in slot
- * order into grad (device, global [nx][ny][nz], overwritten; zero outside
- * every window).  The result is deterministic for a given concurrency. */
+ * dJ/dd_s, shot order).  Per shot: the forward with checkpoints every
+ * ckpt_every steps on the window, then the gradient on the window (the steps
+ * of wave_grad), grouped and launched as in wave_fwd_batched.  The window
+ * gradients are added into grad (device, global [nx][ny][nz], overwritten;
+ * zero outside every window) in shot order, so the result is deterministic
+ * and independent of `concurrency`. */
 int32_t wave_grad_batched(const wave_grid *g, int32_t nshots, const wave_shot *shots,
                           const float *m, const float *damp, const float *src_traces,
                           const float *rec_resid, int32_t ckpt_every, float *grad,

@@ -1,12 +1,19 @@
 // batch.cu -- batched shots over windows of one global model (the
 // wave_*_batched entry points of include/wave.h).
 //
-// Shot i runs on slot i mod C (C = concurrency): a library-owned stream and a
-// slot of the caller's workspace holding the window of m and damp, the
-// single-shot workspace, and for the gradient the checkpoints, the window
-// gradient and a global-size accumulator.  The slot streams wait for the
-// caller's stream at the start and the caller's stream waits for them at the
-// end, so the call is ordered on `stream` like any other entry point.
+// Shots run in groups of C (C = concurrency).  Shot i uses slot i mod C of
+// the caller's workspace: the window of m and damp, the single-shot
+// workspace and, for the gradient, the checkpoints and the window gradient.
+//
+//  * Lockstep (the default untiled plan): the shots of a group advance
+//    together, one launch of the batched kernel per time step for all of
+//    them, on the caller's stream (host runtime, wave_api.cu).
+//  * Otherwise each shot runs wave_fwd / wave_grad on its slot's
+//    library-owned stream; the slot streams wait for the caller's stream at
+//    the start and the caller's stream waits for them at the end.
+//
+// Either way the window gradients are added into the global gradient in shot
+// order, so both give the same, deterministic result.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -15,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include "wave.h"
+#include "wave_internal.h"
 
 namespace {
 
@@ -62,15 +70,6 @@ __global__ void window_add_kernel(const float *__restrict__ w, int nx, int ny, i
     }
 }
 
-// out = a (first) or out + a
-__global__ void accumulate_kernel(const float *__restrict__ a, long long n, int first,
-                                  float *__restrict__ out)
-{
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x)
-        out[p] = first ? a[p] : __fadd_rn(out[p], a[p]);
-}
-
 // the most severe (most negative) status of a shot goes into the batch word
 __global__ void status_merge_kernel(const int *shot_status, int *batch_status)
 {
@@ -115,7 +114,7 @@ struct SlotLayout {
     size_t win = 0;    // bytes of one window field (largest shot)
     size_t ws = 0;     // single-shot workspace (largest shot)
     size_t ckpt = 0;   // checkpoints (gradient only)
-    size_t glob = 0;   // global accumulator (gradient only)
+    size_t table = 0;  // per-shot launch arguments of a lockstep group
     size_t slot = 0;   // bytes per slot
     size_t total = 0;  // whole batch workspace
 };
@@ -124,7 +123,6 @@ int layout(const wave_grid *G, int nshots, const wave_shot *shots, int k, int co
 {
     if (G == nullptr || nshots < 1 || shots == nullptr || k < 0 || conc < 1 || conc > kMaxConc)
         return WAVE_EINVAL;
-    const size_t glob_n = (size_t)G->n[0] * G->n[1] * G->n[2];
     if (wave_workspace_bytes(G, WAVE_OP_FWD, 0, 0, 0, nullptr) == 0) return WAVE_EINVAL;
     for (int i = 0; i < nshots; ++i) {
         wave_grid g;
@@ -143,10 +141,11 @@ int layout(const wave_grid *G, int nshots, const wave_shot *shots, int k, int co
         if (ws == 0) return WAVE_EINVAL;
         L->ws = std::max(L->ws, al(ws));
     }
-    if (k > 0) L->glob = al(sizeof(float) * glob_n);
-    // m and damp windows, workspace; gradient: checkpoints, window gradient, accumulator
-    L->slot = 2 * L->win + L->ws + (k > 0 ? L->ckpt + L->win + L->glob : 0);
-    L->total = kHead + (size_t)conc * L->slot;
+    for (int g0 = 0; g0 < nshots; g0 += conc)
+        L->table = std::max(L->table, al(wt::lockstep_table_bytes(G, std::min(conc, nshots - g0), shots + g0)));
+    // m and damp windows, workspace; gradient: checkpoints and the window gradient
+    L->slot = 2 * L->win + L->ws + (k > 0 ? L->ckpt + L->win : 0);
+    L->total = kHead + L->table + (size_t)conc * L->slot;
     return WAVE_OK;
 }
 
@@ -196,6 +195,165 @@ struct ForkJoin {
 
 int conc_of(int concurrency) { return concurrency == 0 ? 4 : concurrency; }
 
+// Everything one batched call needs to address its shots.
+struct Batch {
+    const wave_grid *g;
+    int nshots;
+    const wave_shot *shots;
+    SlotLayout L;
+    char *base;
+    std::vector<long long> so, ro;  // trace column offset of each shot (units of nt rows)
+
+    char *slot(int k) const { return base + kHead + L.table + (size_t)k * L.slot; }
+    void *table() const { return base + kHead; }
+    int *status() const { return (int *)base; }
+    wt::ShotSlot shot_slot(int i, int k, const float *src_traces, float *rec_traces, const float *resid) const
+    {
+        char *sl = slot(k);
+        wt::ShotSlot x;
+        x.shot = &shots[i];
+        x.mw = (float *)sl;
+        x.dw = (float *)(sl + L.win);
+        x.ws = sl + 2 * L.win;
+        x.ws_bytes = L.ws;
+        x.ckpt = L.ckpt ? (float *)(sl + 2 * L.win + L.ws) : nullptr;
+        x.gwin = L.ckpt ? (float *)(sl + 2 * L.win + L.ws + L.ckpt) : nullptr;
+        x.q = shots[i].src.npts ? src_traces + so[i] * g->nt : nullptr;
+        x.rec_out = (rec_traces && shots[i].rec.npts) ? rec_traces + ro[i] * g->nt : nullptr;
+        x.resid = (resid && shots[i].rec.npts) ? resid + ro[i] * g->nt : nullptr;
+        return x;
+    }
+};
+
+int batch_setup(const wave_grid *g, int nshots, const wave_shot *shots, int k, int conc, void *ws,
+                size_t ws_bytes, Batch *b)
+{
+    b->g = g;
+    b->nshots = nshots;
+    b->shots = shots;
+    int rc = layout(g, nshots, shots, k, conc, &b->L);
+    if (rc) return rc;
+    if (ws == nullptr || (uintptr_t)ws % kAlign) return WAVE_EINVAL;
+    if (ws_bytes < b->L.total) return WAVE_ENOSPACE;
+    b->base = (char *)ws;
+    b->so.assign(nshots, 0);
+    b->ro.assign(nshots, 0);
+    for (int i = 1; i < nshots; ++i) {
+        b->so[i] = b->so[i - 1] + shots[i - 1].src.npts;
+        b->ro[i] = b->ro[i - 1] + shots[i - 1].rec.npts;
+    }
+    return WAVE_OK;
+}
+
+int copy_windows(const Batch &b, const wt::ShotSlot &x, const float *m, const float *damp, cudaStream_t st)
+{
+    const wave_shot &s = *x.shot;
+    const long long n = (long long)s.n[0] * s.n[1] * s.n[2];
+    window_copy_kernel<<<grid_for(n), 256, 0, st>>>(m, b.g->n[1], b.g->n[2], s.origin[0], s.origin[1],
+                                                    s.origin[2], s.n[0], s.n[1], s.n[2], x.mw);
+    window_copy_kernel<<<grid_for(n), 256, 0, st>>>(damp, b.g->n[1], b.g->n[2], s.origin[0], s.origin[1],
+                                                    s.origin[2], s.n[0], s.n[1], s.n[2], x.dw);
+    return cudaGetLastError() == cudaSuccess ? WAVE_OK : WAVE_ECUDA;
+}
+
+int add_window(const Batch &b, const wt::ShotSlot &x, float *grad, cudaStream_t st)
+{
+    const wave_shot &s = *x.shot;
+    const long long n = (long long)s.n[0] * s.n[1] * s.n[2];
+    window_add_kernel<<<grid_for(n), 256, 0, st>>>(x.gwin, s.n[0], s.n[1], s.n[2], b.g->n[1], b.g->n[2],
+                                                   s.origin[0], s.origin[1], s.origin[2], grad);
+    return cudaGetLastError() == cudaSuccess ? WAVE_OK : WAVE_ECUDA;
+}
+
+int merge_status(const Batch &b, const wt::ShotSlot &x, cudaStream_t st)
+{
+    status_merge_kernel<<<1, 32, 0, st>>>((const int *)x.ws, b.status());
+    return cudaGetLastError() == cudaSuccess ? WAVE_OK : WAVE_ECUDA;
+}
+
+// Both entry points: lockstep groups on `stream` when the plan has a batched
+// kernel, else shots on slot streams.  k = 0: forward; k >= 1: gradient.
+int run_batch(const wave_grid *g, int nshots, const wave_shot *shots, const float *m, const float *damp,
+              const float *src_traces, float *rec_traces, const float *rec_resid, int k, float *grad,
+              int concurrency, const wave_tuning *tuning, void *ws, size_t ws_bytes, cudaStream_t stream)
+{
+    const int conc = conc_of(concurrency);
+    Batch b;
+    int rc = batch_setup(g, nshots, shots, k, conc, ws, ws_bytes, &b);
+    if (rc) return rc;
+    if (!m || !damp || (k > 0 && !grad)) return WAVE_EINVAL;
+    long long nsrc_all = 0, nrec_all = 0;
+    for (int i = 0; i < nshots; ++i) {
+        nsrc_all += shots[i].src.npts;
+        nrec_all += shots[i].rec.npts;
+    }
+    if (nsrc_all > 0 && !src_traces) return WAVE_EINVAL;
+    if (nrec_all > 0 && ((k == 0 && !rec_traces) || (k > 0 && !rec_resid))) return WAVE_EINVAL;
+    const wave_tuning tune = batch_tuning(tuning);
+    if (cudaMemsetAsync(b.status(), 0, sizeof(int), stream) != cudaSuccess) return WAVE_ECUDA;
+    if (k > 0 && cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)g->n[0] * g->n[1] * g->n[2], stream) !=
+                     cudaSuccess)
+        return WAVE_ECUDA;
+    const int used = std::min(conc, nshots);
+
+    if (wt::lockstep_supported(g, &tune)) {
+        for (int g0 = 0; g0 < nshots && rc == WAVE_OK; g0 += used) {
+            const int n = std::min(used, nshots - g0);
+            std::vector<wt::ShotSlot> sl(n);
+            for (int i = 0; i < n && rc == WAVE_OK; ++i) {
+                sl[i] = b.shot_slot(g0 + i, i, src_traces, rec_traces, rec_resid);
+                rc = copy_windows(b, sl[i], m, damp, stream);
+            }
+            if (rc == WAVE_OK) rc = wt::lockstep_group(g, n, sl.data(), k, &tune, b.table(), b.L.table, stream);
+            for (int i = 0; i < n && rc == WAVE_OK; ++i) {
+                rc = merge_status(b, sl[i], stream);
+                if (rc == WAVE_OK && k > 0) rc = add_window(b, sl[i], grad, stream);  // shot order
+            }
+        }
+        return rc;
+    }
+
+    cudaStream_t slots[kMaxConc];
+    if ((rc = pool_streams(used, slots))) return rc;
+    ForkJoin fj{stream, slots, used};
+    if ((rc = fj.begin())) return rc;
+    // window gradients go into grad in shot order: shot i's add waits for shot i-1's
+    cudaEvent_t added = nullptr;
+    for (int i = 0; i < nshots && rc == WAVE_OK; ++i) {
+        const int kslot = i % used;
+        cudaStream_t st = slots[kslot];
+        const wt::ShotSlot x = b.shot_slot(i, kslot, src_traces, rec_traces, rec_resid);
+        wave_grid gw;
+        shot_grid(g, shots[i], &gw);
+        rc = copy_windows(b, x, m, damp, st);
+        if (rc == WAVE_OK && k == 0)
+            rc = wave_fwd(&gw, x.mw, x.dw, &shots[i].src, x.q, &shots[i].rec, x.rec_out, nullptr, nullptr, 0,
+                          &tune, x.ws, x.ws_bytes, st);
+        if (rc == WAVE_OK && k > 0) {
+            // forward with checkpoints (no receivers needed), then the gradient
+            rc = wave_fwd(&gw, x.mw, x.dw, &shots[i].src, x.q, nullptr, nullptr, nullptr, x.ckpt, k, &tune, x.ws,
+                          x.ws_bytes, st);
+            if (rc == WAVE_OK) rc = merge_status(b, x, st);
+            if (rc == WAVE_OK)
+                rc = wave_grad(&gw, x.mw, x.dw, &shots[i].src, x.q, &shots[i].rec, x.resid, x.ckpt, k, x.gwin,
+                               &tune, x.ws, x.ws_bytes, st);
+        }
+        if (rc == WAVE_OK) rc = merge_status(b, x, st);
+        if (rc == WAVE_OK && k > 0) {
+            if (added != nullptr && cudaStreamWaitEvent(st, added, 0) != cudaSuccess) rc = WAVE_ECUDA;
+            if (rc == WAVE_OK) rc = add_window(b, x, grad, st);
+            if (added != nullptr) cudaEventDestroy(added);
+            added = nullptr;
+            if (rc == WAVE_OK && (cudaEventCreateWithFlags(&added, cudaEventDisableTiming) != cudaSuccess ||
+                                  cudaEventRecord(added, st) != cudaSuccess))
+                rc = WAVE_ECUDA;
+        }
+    }
+    if (added != nullptr) cudaEventDestroy(added);
+    const int rj = fj.end();
+    return rc ? rc : rj;
+}
+
 }  // namespace
 
 extern "C" {
@@ -211,144 +369,29 @@ size_t wave_batch_workspace_bytes(const wave_grid *g, int32_t nshots, const wave
 int32_t wave_fwd_batched(const wave_grid *g, int32_t nshots, const wave_shot *shots,
                          const float *m, const float *damp, const float *src_traces,
                          float *rec_traces, int32_t concurrency, const wave_tuning *tuning,
-                         void *ws, size_t ws_bytes, void *stream_)
+                         void *ws, size_t ws_bytes, void *stream)
 {
-    const int conc = conc_of(concurrency);
-    SlotLayout L;
-    int rc = layout(g, nshots, shots, 0, conc, &L);
-    if (rc) return rc;
-    if (!m || !damp || !ws || (uintptr_t)ws % kAlign) return WAVE_EINVAL;
-    if (ws_bytes < L.total) return WAVE_ENOSPACE;
-    long long nsrc_all = 0, nrec_all = 0;
-    for (int i = 0; i < nshots; ++i) {
-        nsrc_all += shots[i].src.npts;
-        nrec_all += shots[i].rec.npts;
+    try {
+        return run_batch(g, nshots, shots, m, damp, src_traces, rec_traces, nullptr, 0, nullptr, concurrency,
+                         tuning, ws, ws_bytes, (cudaStream_t)stream);
+    } catch (...) {
+        return WAVE_EINVAL;
     }
-    if ((nsrc_all > 0 && !src_traces) || (nrec_all > 0 && !rec_traces)) return WAVE_EINVAL;
-    const int used = std::min(conc, (int)nshots);
-    cudaStream_t slots[kMaxConc];
-    if ((rc = pool_streams(used, slots))) return rc;
-    cudaStream_t stream = (cudaStream_t)stream_;
-    char *base = (char *)ws;
-    int *bstatus = (int *)base;
-    if (cudaMemsetAsync(bstatus, 0, sizeof(int), stream) != cudaSuccess) return WAVE_ECUDA;
-    ForkJoin fj{stream, slots, used};
-    if ((rc = fj.begin())) return rc;
-    const wave_tuning tune = batch_tuning(tuning);
-    long long so = 0, ro = 0;  // trace column offsets of the shot (in units of nt rows)
-    for (int i = 0; i < nshots && rc == WAVE_OK; ++i) {
-        const wave_shot &s = shots[i];
-        wave_grid gw;
-        shot_grid(g, s, &gw);
-        const int k = i % used;
-        cudaStream_t st = slots[k];
-        char *slot = base + kHead + (size_t)k * L.slot;
-        float *mw = (float *)slot, *dw = (float *)(slot + L.win);
-        void *sws = slot + 2 * L.win;
-        const long long n = (long long)gw.n[0] * gw.n[1] * gw.n[2];
-        window_copy_kernel<<<grid_for(n), 256, 0, st>>>(m, g->n[1], g->n[2], s.origin[0], s.origin[1],
-                                                        s.origin[2], gw.n[0], gw.n[1], gw.n[2], mw);
-        window_copy_kernel<<<grid_for(n), 256, 0, st>>>(damp, g->n[1], g->n[2], s.origin[0], s.origin[1],
-                                                        s.origin[2], gw.n[0], gw.n[1], gw.n[2], dw);
-        if (cudaGetLastError() != cudaSuccess) rc = WAVE_ECUDA;
-        if (rc == WAVE_OK)
-            rc = wave_fwd(&gw, mw, dw, &s.src, s.src.npts ? src_traces + so * g->nt : nullptr, &s.rec,
-                          s.rec.npts ? rec_traces + ro * g->nt : nullptr, nullptr, nullptr, 0, &tune, sws,
-                          L.ws, st);
-        if (rc == WAVE_OK) {
-            status_merge_kernel<<<1, 32, 0, st>>>((const int *)sws, bstatus);
-            if (cudaGetLastError() != cudaSuccess) rc = WAVE_ECUDA;
-        }
-        so += s.src.npts;
-        ro += s.rec.npts;
-    }
-    const int rj = fj.end();
-    return rc ? rc : rj;
 }
 
 int32_t wave_grad_batched(const wave_grid *g, int32_t nshots, const wave_shot *shots,
                           const float *m, const float *damp, const float *src_traces,
                           const float *rec_resid, int32_t ckpt_every, float *grad,
                           int32_t concurrency, const wave_tuning *tuning, void *ws,
-                          size_t ws_bytes, void *stream_)
+                          size_t ws_bytes, void *stream)
 {
-    const int conc = conc_of(concurrency);
     if (ckpt_every < 1) return WAVE_EINVAL;
-    SlotLayout L;
-    int rc = layout(g, nshots, shots, ckpt_every, conc, &L);
-    if (rc) return rc;
-    if (!m || !damp || !grad || !ws || (uintptr_t)ws % kAlign) return WAVE_EINVAL;
-    if (ws_bytes < L.total) return WAVE_ENOSPACE;
-    long long nsrc_all = 0, nrec_all = 0;
-    for (int i = 0; i < nshots; ++i) {
-        nsrc_all += shots[i].src.npts;
-        nrec_all += shots[i].rec.npts;
+    try {
+        return run_batch(g, nshots, shots, m, damp, src_traces, nullptr, rec_resid, ckpt_every, grad,
+                         concurrency, tuning, ws, ws_bytes, (cudaStream_t)stream);
+    } catch (...) {
+        return WAVE_EINVAL;
     }
-    if ((nsrc_all > 0 && !src_traces) || (nrec_all > 0 && !rec_resid)) return WAVE_EINVAL;
-    const int used = std::min(conc, (int)nshots);
-    cudaStream_t slots[kMaxConc];
-    if ((rc = pool_streams(used, slots))) return rc;
-    cudaStream_t stream = (cudaStream_t)stream_;
-    char *base = (char *)ws;
-    int *bstatus = (int *)base;
-    const long long nglob = (long long)g->n[0] * g->n[1] * g->n[2];
-    if (cudaMemsetAsync(bstatus, 0, sizeof(int), stream) != cudaSuccess) return WAVE_ECUDA;
-    ForkJoin fj{stream, slots, used};
-    if ((rc = fj.begin())) return rc;
-    const wave_tuning tune = batch_tuning(tuning);
-    auto slot_ptr = [&](int k) { return base + kHead + (size_t)k * L.slot; };
-    for (int k = 0; k < used && rc == WAVE_OK; ++k) {
-        float *acc = (float *)(slot_ptr(k) + 2 * L.win + L.ws + L.ckpt + L.win);
-        if (cudaMemsetAsync(acc, 0, sizeof(float) * nglob, slots[k]) != cudaSuccess) rc = WAVE_ECUDA;
-    }
-    long long so = 0, ro = 0;
-    for (int i = 0; i < nshots && rc == WAVE_OK; ++i) {
-        const wave_shot &s = shots[i];
-        wave_grid gw;
-        shot_grid(g, s, &gw);
-        const int k = i % used;
-        cudaStream_t st = slots[k];
-        char *slot = slot_ptr(k);
-        float *mw = (float *)slot, *dw = (float *)(slot + L.win);
-        void *sws = slot + 2 * L.win;
-        float *ck = (float *)(slot + 2 * L.win + L.ws);
-        float *gwin = (float *)(slot + 2 * L.win + L.ws + L.ckpt);
-        float *acc = (float *)(slot + 2 * L.win + L.ws + L.ckpt + L.win);
-        const long long n = (long long)gw.n[0] * gw.n[1] * gw.n[2];
-        window_copy_kernel<<<grid_for(n), 256, 0, st>>>(m, g->n[1], g->n[2], s.origin[0], s.origin[1],
-                                                        s.origin[2], gw.n[0], gw.n[1], gw.n[2], mw);
-        window_copy_kernel<<<grid_for(n), 256, 0, st>>>(damp, g->n[1], g->n[2], s.origin[0], s.origin[1],
-                                                        s.origin[2], gw.n[0], gw.n[1], gw.n[2], dw);
-        if (cudaGetLastError() != cudaSuccess) rc = WAVE_ECUDA;
-        const float *q = s.src.npts ? src_traces + so * g->nt : nullptr;
-        // forward with checkpoints (no receivers needed), then the gradient
-        if (rc == WAVE_OK)
-            rc = wave_fwd(&gw, mw, dw, &s.src, q, nullptr, nullptr, nullptr, ck, ckpt_every, &tune, sws,
-                          L.ws, st);
-        if (rc == WAVE_OK) {
-            status_merge_kernel<<<1, 32, 0, st>>>((const int *)sws, bstatus);
-            rc = wave_grad(&gw, mw, dw, &s.src, q, &s.rec, s.rec.npts ? rec_resid + ro * g->nt : nullptr,
-                           ck, ckpt_every, gwin, &tune, sws, L.ws, st);
-        }
-        if (rc == WAVE_OK) {
-            status_merge_kernel<<<1, 32, 0, st>>>((const int *)sws, bstatus);
-            window_add_kernel<<<grid_for(n), 256, 0, st>>>(gwin, gw.n[0], gw.n[1], gw.n[2], g->n[1],
-                                                           g->n[2], s.origin[0], s.origin[1], s.origin[2],
-                                                           acc);
-            if (cudaGetLastError() != cudaSuccess) rc = WAVE_ECUDA;
-        }
-        so += s.src.npts;
-        ro += s.rec.npts;
-    }
-    const int rj = fj.end();
-    if (rc) return rc;
-    if (rj) return rj;
-    // slots summed in slot order on the caller's stream
-    for (int k = 0; k < used; ++k) {
-        const float *acc = (const float *)(slot_ptr(k) + 2 * L.win + L.ws + L.ckpt + L.win);
-        accumulate_kernel<<<grid_for(nglob), 256, 0, stream>>>(acc, nglob, k == 0, grad);
-    }
-    return cudaGetLastError() == cudaSuccess ? WAVE_OK : WAVE_ECUDA;
 }
 
 }  // extern "C"

@@ -260,6 +260,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
+// Acquire a TMA descriptor held in global memory (written by a host copy)
+// for the tensormap proxy; the calling thread may then load through it.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(map) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1,
                                             int c2, uint64_t *bar)
 {
@@ -320,10 +327,11 @@ __device__ __forceinline__ float2 fsub2_rn(float2 u, float2 w)
     return __fadd2_rn(u, make_float2(-w.x, -w.y));
 }
 
-template <int R, int T, int V, int BZ, int BY, int P, int MB, int XB = 0>
-__global__ void __launch_bounds__(SweepShape<R, T, V, BZ, BY, P, MB, XB>::NTB, MB)
-sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stencil st,
-             const __grid_constant__ SweepMaps mp)
+// The sweep of block `blk` of one problem: the body of the single-problem
+// kernel and of the batched kernel below.
+template <int R, int T, int V, int BZ, int BY, int P, int MB, int XB>
+__device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &st, const SweepMaps &mp,
+                                            const int blk)
 {
     using S = SweepShape<R, T, V, BZ, BY, P, MB, XB>;
     constexpr int QL = 2 * R + 1;
@@ -339,7 +347,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empK + S::DK);
 
     if (blockDim.x != S::NTB) {  // launched with the wrong shape: report, do nothing
-        if (threadIdx.x == 0 && blockIdx.x == 0) atomicMin(a.status, -1 /* WAVE_EINVAL */);
+        if (threadIdx.x == 0 && blk == 0) atomicMin(a.status, -1 /* WAVE_EINVAL */);
         return;
     }
     // Programmatic dependent launch: once every block of this launch has
@@ -351,7 +359,7 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
     const int tid = threadIdx.x;
     const int col = S::ZL + (tid % S::LZ) * V;  // layout column of this thread's V points
     const int row = R + tid / S::LZ;            // layout row
-    int b = blockIdx.x;
+    int b = blk;
     const int tzi = b % a.tiles_z;
     b /= a.tiles_z;
     const int tyi = b % a.tiles_y;
@@ -729,6 +737,53 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
             if (++sf == S::DF) { sf = 0; pf ^= 1u; }
         }
     }
+}
+
+// One problem per launch: arguments and TMA descriptors in parameter space.
+template <int R, int T, int V, int BZ, int BY, int P, int MB, int XB = 0>
+__global__ void __launch_bounds__(SweepShape<R, T, V, BZ, BY, P, MB, XB>::NTB, MB)
+sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stencil st,
+             const __grid_constant__ SweepMaps mp)
+{
+    sweep_block<R, T, V, BZ, BY, P, MB, XB>(a, st, mp, blockIdx.x);
+}
+
+// One shot of a batched launch, in device memory: its arguments and TMA
+// descriptors for both parities of its ping-pong buffers (the row fields of
+// the arguments hold the rows of step 0), and its first block in the launch.
+struct alignas(64) ShotSweep {
+    SweepMaps mp[2];
+    SweepArgs a[2];
+    int block0;
+};
+
+// Every shot of a batch advanced by one launch: block i belongs to shot
+// block_shot[i] (its blocks are consecutive), the launch is time step `step`
+// of all shots, and `parity` selects their buffers.  The shots share the
+// stencil (grid spacing and space order), nt and dt.
+template <int R, int T, int V, int BZ, int BY, int P, int MB>
+__global__ void __launch_bounds__(SweepShape<R, T, V, BZ, BY, P, MB>::NTB, MB)
+sweep_multi_kernel(const ShotSweep *__restrict__ shots, const int *__restrict__ block_shot,
+                   const __grid_constant__ Stencil st, int parity, int step)
+{
+    using S = SweepShape<R, T, V, BZ, BY, P, MB>;
+    const ShotSweep &sh = shots[block_shot[blockIdx.x]];
+    if (threadIdx.x == S::NT) {
+        // the producer thread's TMA reads these descriptors from global
+        // memory, which a host copy may have rewritten since a launch that
+        // read the same addresses: acquire them for the tensormap proxy first
+        const SweepMaps &m = sh.mp[parity];
+        tensormap_acquire(&m.u);
+        tensormap_acquire(&m.um);
+        tensormap_acquire(&m.B);
+        tensormap_acquire(&m.C);
+    }
+    SweepArgs la = sh.a[parity];
+    la.q_row0 += la.q_dir * step;
+    la.c_row0 += la.c_dir * step;
+    la.d_row0 += (long long)la.d_dir * step;
+    la.l_row0 += (long long)la.l_dir * step;
+    sweep_block<R, T, V, BZ, BY, P, MB, 0>(la, st, sh.mp[parity], (int)blockIdx.x - sh.block0);
 }
 
 }  // namespace wt

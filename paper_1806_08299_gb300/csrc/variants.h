@@ -40,3 +40,14 @@
 // loads.
 #define WAVE_SWEEP_MODE_VARIANTS_R2(Y) Y(2, 1, 8, 64, 16, 2, 2, 1) Y(2, 1, 8, 64, 16, 2, 2, 2)
 #define WAVE_SWEEP_MODE_VARIANTS_R4(Y) Y(4, 1, 4, 64, 8, 2, 3, 1) Y(4, 1, 4, 64, 8, 2, 3, 2)
+
+// Batched-kernel shape per radius (its default untiled shape): all shots of a
+// batch advance in one launch per time step.
+#define WAVE_MULTI_R1 1, 1, 2, 64, 8, 3, 3
+#define WAVE_MULTI_R2 2, 1, 8, 64, 16, 2, 2
+#define WAVE_MULTI_R3 3, 1, 2, 64, 12, 2, 2
+#define WAVE_MULTI_R4 4, 1, 4, 64, 8, 3, 3
+#define WAVE_MULTI_R5 5, 1, 2, 64, 12, 2, 2
+#define WAVE_MULTI_R6 6, 1, 2, 64, 8, 2, 2
+#define WAVE_MULTI_R7 7, 1, 2, 64, 8, 2, 2
+#define WAVE_MULTI_R8 8, 1, 2, 64, 8, 2, 1

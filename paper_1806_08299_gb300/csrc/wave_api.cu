@@ -593,6 +593,83 @@ struct State {
     int a = 0, b = 1;
 };
 
+// Arguments and TMA descriptors of the launch that advances state `s` of
+// `job` by variant v from local step j (rows of the step-dependent tables are
+// those of step j), with x-chunk `chunk`.  *nblocks receives the grid size.
+int build_launch(const Job &job, const State &s, int j, const SweepVariant *v, int chunk, SweepArgs *ap,
+                 wt::SweepMaps *mp, long long *nblocks)
+{
+    const Dims &d = job.d;
+    SweepArgs &a = *ap;
+    std::memset(&a, 0, sizeof(a));
+    std::memset(mp, 0, sizeof(*mp));
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.nz = d.nzp;
+    a.sx = (int)((long long)d.ny * d.nzp);
+    a.npad = d.npad;
+    a.status = job.status;
+    int rc = encode_map(&mp->u, s.buf[s.a], d, v->PW, v->H0);
+    if (!rc) rc = encode_map(&mp->um, s.buf[s.b], d, v->W0, v->HK);
+    if (!rc) rc = encode_map(&mp->B, job.cB, d, v->W0, v->HK);
+    if (!rc) rc = encode_map(&mp->C, job.cC, d, v->W0, v->HK);
+    if (!rc && v->XB == 1) rc = encode_map(&mp->x0, job.cE, d, v->W0, v->HK);
+    if (!rc && v->XB == 2) {
+        const long long row = job.l_base + (long long)job.l_dir * j;  // this step's D row
+        rc = encode_map(&mp->x0, job.dload + row * d.npad, d, v->W0, v->HK);
+        if (!rc) rc = encode_map(&mp->x1, job.gacc, d, v->W0, v->HK);
+    }
+    if (rc) return rc;
+    int spare[2], ns = 0;
+    for (int i = 0; i < 4; ++i)
+        if (i != s.a && i != s.b) spare[ns++] = i;
+    if (v->T == 1) {
+        a.out_hi = s.buf[s.b];
+    } else {
+        a.out_hi = s.buf[spare[0]];
+        a.out_lo = s.buf[spare[1]];
+    }
+    a.cE = job.cE;
+    a.inj = job.inj;
+    a.q = job.q;
+    a.nq = job.nq;
+    a.q_row0 = job.q_base + job.q_dir * j;
+    a.q_dir = job.q_dir;
+    a.rec = job.rec;
+    a.corner = job.corner;
+    a.nslot = job.nslot;
+    a.c_row0 = job.c_base + job.c_dir * j;
+    a.c_dir = job.c_dir;
+    a.dstore = job.dstore;
+    a.d_row0 = job.d_base + (long long)job.d_dir * j;
+    a.d_dir = job.d_dir;
+    a.dload = job.dload;
+    a.l_row0 = job.l_base + (long long)job.l_dir * j;
+    a.l_dir = job.l_dir;
+    a.gacc = job.gacc;
+    a.withhold = job.withhold;
+    a.chunk = chunk;
+    a.tiles_z = tiles(d.nzp, v->BZ);
+    a.tiles_y = tiles(d.ny, v->BY);
+    *nblocks = (long long)a.tiles_z * a.tiles_y * tiles(d.nx, chunk);
+    return *nblocks > 0x7fffffffLL ? WAVE_EINVAL : WAVE_OK;
+}
+
+// The state after one launch of depth T: T = 1 writes level n+1 where n-1
+// was; T >= 2 writes the two spare buffers.
+void advance_state(State &s, int T)
+{
+    if (T == 1) {
+        std::swap(s.a, s.b);
+    } else {
+        int spare[2], ns = 0;
+        for (int i = 0; i < 4; ++i)
+            if (i != s.a && i != s.b) spare[ns++] = i;
+        s.a = spare[0];
+        s.b = spare[1];
+    }
+}
+
 // Advance `st` by nsteps.  When ckpt != nullptr, state c = (u^{ck}, u^{ck-1})
 // is copied to ckpt + c * 2 * npad at every step count j0 + j that is a
 // multiple of ckpt_every (j counts from the run start, j0 = global offset).
@@ -627,69 +704,16 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
             }
         }
         SweepArgs a;
-        std::memset(&a, 0, sizeof(a));
-        a.nx = d.nx;
-        a.ny = d.ny;
-        a.nz = d.nzp;
-        a.sx = (int)((long long)d.ny * d.nzp);
-        a.npad = d.npad;
-        a.status = job.status;
         wt::SweepMaps maps;
-        int rc = encode_map(&maps.u, s.buf[s.a], d, v->PW, v->H0);
-        if (!rc) rc = encode_map(&maps.um, s.buf[s.b], d, v->W0, v->HK);
-        if (!rc) rc = encode_map(&maps.B, job.cB, d, v->W0, v->HK);
-        if (!rc) rc = encode_map(&maps.C, job.cC, d, v->W0, v->HK);
-        if (!rc && v->XB == 1) rc = encode_map(&maps.x0, job.cE, d, v->W0, v->HK);
-        if (!rc && v->XB == 2) {
-            const long long row = job.l_base + (long long)job.l_dir * j;  // this step's D row
-            rc = encode_map(&maps.x0, job.dload + row * d.npad, d, v->W0, v->HK);
-            if (!rc) rc = encode_map(&maps.x1, job.gacc, d, v->W0, v->HK);
-        }
+        long long nblocks = 0;
+        int rc = build_launch(job, s, j, v, chunk, &a, &maps, &nblocks);
         if (rc) return rc;
-        int spare[2], ns = 0;
-        for (int i = 0; i < 4; ++i)
-            if (i != s.a && i != s.b) spare[ns++] = i;
-        if (v->T == 1) {
-            a.out_hi = s.buf[s.b];
-        } else {
-            a.out_hi = s.buf[spare[0]];
-            a.out_lo = s.buf[spare[1]];
-        }
-        a.cE = job.cE;
-        a.inj = job.inj;
-        a.q = job.q;
-        a.nq = job.nq;
-        a.q_row0 = job.q_base + job.q_dir * j;
-        a.q_dir = job.q_dir;
-        a.rec = job.rec;
-        a.corner = job.corner;
-        a.nslot = job.nslot;
-        a.c_row0 = job.c_base + job.c_dir * j;
-        a.c_dir = job.c_dir;
-        a.dstore = job.dstore;
-        a.d_row0 = job.d_base + (long long)job.d_dir * j;
-        a.d_dir = job.d_dir;
-        a.dload = job.dload;
-        a.l_row0 = job.l_base + (long long)job.l_dir * j;
-        a.l_dir = job.l_dir;
-        a.gacc = job.gacc;
-        a.withhold = job.withhold;
-        a.chunk = chunk;
-        a.tiles_z = tiles(d.nzp, v->BZ);
-        a.tiles_y = tiles(d.ny, v->BY);
-        const long long nblocks = (long long)a.tiles_z * a.tiles_y * tiles(d.nx, chunk);
-        if (nblocks > 0x7fffffffLL) return WAVE_EINVAL;
         CK(v->launch((int)nblocks, stream, a, job.st, maps));
         if (g_prof.active) {
             g_prof.launches++;
             g_prof.steps += v->T;
         }
-        if (v->T == 1) {
-            std::swap(s.a, s.b);  // new level n+1 sits where n-1 was
-        } else {
-            s.a = spare[0];
-            s.b = spare[1];
-        }
+        advance_state(s, v->T);
         j += v->T;
     }
     return WAVE_OK;
@@ -841,9 +865,265 @@ int check_points(const wave_points *p, bool need_data_ptr, const void *data)
 
 int npts_of(const wave_points *p) { return p ? p->npts : 0; }
 
+// ---------------------------------------------------------------------------
+// Batched shots in lockstep: one launch of the batched kernel per time step
+// advances every shot of a group
+// ---------------------------------------------------------------------------
+
+const wt::MultiVariant *multi_variant(int R)
+{
+    const wt::MultiVariant *mv = nullptr;
+    switch (R) {
+    case 1: wt::sweep_multi_variant_r1(&mv); break;
+    case 2: wt::sweep_multi_variant_r2(&mv); break;
+    case 3: wt::sweep_multi_variant_r3(&mv); break;
+    case 4: wt::sweep_multi_variant_r4(&mv); break;
+    case 5: wt::sweep_multi_variant_r5(&mv); break;
+    case 6: wt::sweep_multi_variant_r6(&mv); break;
+    case 7: wt::sweep_multi_variant_r7(&mv); break;
+    case 8: wt::sweep_multi_variant_r8(&mv); break;
+    default: break;
+    }
+    return mv;
+}
+
+struct LockShot {
+    Dims d;
+    wave_grid g;
+    Layout L;
+    HostTable ti, tr;
+    Job job;        // forward (or recompute) job of the current phase
+    State s;        // forward / recompute state
+    State adj;      // adjoint state (gradient)
+    int chunk = 0;
+};
+
+size_t lock_table_bytes(int nshots, long long total_blocks)
+{
+    return align_up(sizeof(wt::ShotSweep) * (size_t)nshots) + align_up(sizeof(int) * (size_t)total_blocks);
+}
+
+// Enqueue `nsteps` launches of the batched kernel over every shot: shot i
+// advances its state `st_of(i)` with job `ls[i].job` from local step 0.  At
+// every multiple of ckpt_every (ckpt != nullptr) its state (u^n, u^{n-1}) is
+// copied to ckpts[i] first, as run_steps does.  The per-shot arguments of
+// both buffer parities go to the table at `table`.
+template <class StateOf>
+int lock_phase(std::vector<LockShot> &ls, StateOf st_of, int nsteps, const wt::MultiVariant *mv,
+               const SweepVariant *v, const Stencil &st, void *table, size_t table_bytes,
+               float *const *ckpts, int ckpt_every, cudaStream_t stream)
+{
+    const int n = (int)ls.size();
+    std::vector<wt::ShotSweep> tab(n);
+    std::vector<int> block_shot;
+    long long total = 0;
+    int max_chunk_all = 0;
+    for (int i = 0; i < n; ++i) {
+        for (int p = 0; p < 2; ++p) {
+            State sp = st_of(i);
+            if (p == 1) advance_state(sp, 1);
+            long long nb = 0;
+            int rc = build_launch(ls[i].job, sp, 0, v, ls[i].chunk, &tab[i].a[p], &tab[i].mp[p], &nb);
+            if (rc) return rc;
+            if (p == 0) {
+                tab[i].block0 = (int)total;
+                block_shot.insert(block_shot.end(), (size_t)nb, i);
+                total += nb;
+            }
+        }
+        max_chunk_all = std::max(max_chunk_all, ls[i].chunk);
+    }
+    if (total > 0x7fffffffLL || lock_table_bytes(n, total) > table_bytes) return WAVE_ENOSPACE;
+    wt::ShotSweep *dtab = (wt::ShotSweep *)table;
+    int *dbs = (int *)((char *)table + align_up(sizeof(wt::ShotSweep) * (size_t)n));
+    CK(cudaMemcpyAsync(dtab, tab.data(), sizeof(wt::ShotSweep) * (size_t)n, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(dbs, block_shot.data(), sizeof(int) * block_shot.size(), cudaMemcpyHostToDevice, stream));
+    const size_t smem = mv->smem + wt::sweep_table_bytes(max_chunk_all, mv->R * mv->T) + 16;
+    for (int j = 0; j < nsteps; ++j) {
+        if (ckpts != nullptr && j % ckpt_every == 0) {
+            for (int i = 0; i < n; ++i) {
+                State sj = st_of(i);
+                if (j & 1) advance_state(sj, 1);
+                float *dst = ckpts[i] + (size_t)(j / ckpt_every) * 2 * ls[i].d.npad;
+                CK(cudaMemcpyAsync(dst, sj.buf[sj.a], sizeof(float) * ls[i].d.npad, cudaMemcpyDeviceToDevice,
+                                   stream));
+                CK(cudaMemcpyAsync(dst + ls[i].d.npad, sj.buf[sj.b], sizeof(float) * ls[i].d.npad,
+                                   cudaMemcpyDeviceToDevice, stream));
+            }
+        }
+        CK(mv->launch((int)total, smem, stream, dtab, dbs, st, j & 1, j));
+    }
+    if (nsteps & 1)
+        for (int i = 0; i < n; ++i) advance_state(st_of(i), 1);
+    return WAVE_OK;
+}
+
 }  // namespace
 
 namespace wt {
+
+int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_every,
+                   const wave_tuning *tuning, void *table, size_t table_bytes, cudaStream_t stream)
+{
+    try {
+        const int R = G->space_order / 2;
+        const MultiVariant *mv = multi_variant(R);
+        if (mv == nullptr) return WAVE_EUNSUPPORTED;
+        const int tile_y = tuning ? tuning->tile_y : 0, vec = tuning ? tuning->vec : 0;
+        const SweepVariant *v = find_variant(R, 1, tile_y, vec);
+        if (tuning == nullptr || tuning->time_tile != 1 || v == nullptr || v->T != mv->T || v->V != mv->V ||
+            v->BZ != mv->BZ || v->BY != mv->BY || v->P != mv->P)
+            return WAVE_EUNSUPPORTED;
+        const bool grad = ckpt_every > 0;
+        const int nt = G->nt;
+        std::vector<LockShot> ls(n);
+        Stencil st;
+        for (int i = 0; i < n; ++i) {
+            LockShot &x = ls[i];
+            const wave_shot &sh = *slots[i].shot;
+            x.g = *G;
+            for (int a = 0; a < 3; ++a) x.g.n[a] = sh.n[a];
+            int rc = check_grid(&x.g, &x.d);
+            if (rc) return rc;
+            const int ns = sh.src.npts, nr = sh.rec.npts;
+            x.L = carve(slots[i].ws, slots[i].ws_bytes, false, x.d, grad ? WAVE_OP_GRAD : WAVE_OP_FWD, ns, nr, nt,
+                        grad ? ckpt_every : 0);
+            if (x.L.bytes > slots[i].ws_bytes) return WAVE_ENOSPACE;
+            if (build_table(x.d, x.g.h, &sh.src, false, &x.ti) ||
+                build_table(x.d, x.g.h, &sh.rec, !grad, &x.tr))
+                return WAVE_EINVAL;
+            st = make_stencil(&x.g);
+            if ((rc = prep_model(x.d, &x.g, tuning, slots[i].mw, slots[i].dw, x.L, stream))) return rc;
+            for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(x.L.U[k], 0, sizeof(float) * x.d.npad, stream));
+            if ((rc = upload_table(x.ti, x.L.inj, stream))) return rc;
+            if ((rc = upload_table(x.tr, grad ? x.L.inj2 : x.L.rec, stream))) return rc;
+            x.chunk = std::min(tuning->tile_x > 0 ? std::min(tuning->tile_x, x.d.nx) : default_chunk(x.d, v),
+                               max_chunk(v));
+            for (int k = 0; k < 4; ++k) x.s.buf[k] = x.L.U[k];
+            x.job = Job();
+            x.job.d = x.d;
+            x.job.st = st;
+            x.job.cB = x.L.cB;
+            x.job.cC = x.L.cC;
+            x.job.status = x.L.status;
+            x.job.inj = x.L.inj.view();
+            x.job.q = slots[i].q;
+            x.job.nq = ns;
+            if (!grad) {
+                x.job.rec = x.L.rec.view();
+                x.job.corner = x.L.corner;
+                x.job.nslot = 8 * nr;
+            }
+        }
+        CK(wt::allow_max_dynamic_smem(mv->func));
+        auto fwd_state = [&](int i) -> State & { return ls[i].s; };
+        if (!grad) {
+            int rc = lock_phase(ls, fwd_state, nt, mv, v, st, table, table_bytes, nullptr, 0, stream);
+            if (rc) return rc;
+            for (int i = 0; i < n; ++i)
+                if (slots[i].shot->rec.npts > 0 && slots[i].rec_out != nullptr)
+                    CK(wt::launch_gather(ls[i].L.corner, ls[i].L.rec.wts, nt, slots[i].shot->rec.npts, 1,
+                                         slots[i].rec_out, stream));
+            return WAVE_OK;
+        }
+        // gradient: forward with checkpoints, then per segment (last first)
+        // the recompute with stored second differences and the adjoint with
+        // the imaging condition, as wave_grad does for one shot
+        std::vector<float *> ck(n);
+        for (int i = 0; i < n; ++i) ck[i] = slots[i].ckpt;
+        int rc = lock_phase(ls, fwd_state, nt, mv, v, st, table, table_bytes, ck.data(), ckpt_every, stream);
+        if (rc) return rc;
+        for (int i = 0; i < n; ++i) {
+            LockShot &x = ls[i];
+            CK(cudaMemsetAsync(x.L.G, 0, sizeof(float) * x.d.npad, stream));
+            for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(x.L.V[k], 0, sizeof(float) * x.d.npad, stream));
+            for (int k = 0; k < 4; ++k) x.adj.buf[k] = x.L.V[k];
+        }
+        auto adj_state = [&](int i) -> State & { return ls[i].adj; };
+        const int nseg = (nt + ckpt_every - 1) / ckpt_every;
+        for (int c = nseg - 1; c >= 0; --c) {
+            const int s0 = c * ckpt_every;
+            const int len = std::min(ckpt_every, nt - s0);
+            for (int i = 0; i < n; ++i) {
+                LockShot &x = ls[i];
+                const float *cp = slots[i].ckpt + (size_t)c * 2 * x.d.npad;
+                for (int k = 0; k < 4; ++k) x.s.buf[k] = x.L.U[k];
+                x.s.a = 0;
+                x.s.b = 1;
+                CK(cudaMemcpyAsync(x.s.buf[0], cp, sizeof(float) * x.d.npad, cudaMemcpyDeviceToDevice, stream));
+                CK(cudaMemcpyAsync(x.s.buf[1], cp + x.d.npad, sizeof(float) * x.d.npad,
+                                   cudaMemcpyDeviceToDevice, stream));
+                Job &rj = x.job;
+                rj = Job();
+                rj.d = x.d;
+                rj.st = st;
+                rj.cB = x.L.cB;
+                rj.cC = x.L.cC;
+                rj.status = x.L.status;
+                rj.cE = x.L.cE;
+                rj.inj = x.L.inj.view();
+                rj.q = slots[i].q;
+                rj.nq = slots[i].shot->src.npts;
+                rj.q_base = s0;
+                rj.q_dir = 1;
+                rj.dstore = x.L.store;
+                rj.d_base = 0;
+                rj.d_dir = 1;
+            }
+            if ((rc = lock_phase(ls, fwd_state, len, mv, v, st, table, table_bytes, nullptr, 0, stream))) return rc;
+            for (int i = 0; i < n; ++i) {
+                LockShot &x = ls[i];
+                Job &aj = x.job;
+                aj = Job();
+                aj.d = x.d;
+                aj.st = st;
+                aj.cB = x.L.cB;
+                aj.cC = x.L.cC;
+                aj.status = x.L.status;
+                aj.inj = x.L.inj2.view();
+                aj.q = slots[i].resid;
+                aj.nq = slots[i].shot->rec.npts;
+                aj.q_base = s0 + len - 1;
+                aj.q_dir = -1;
+                aj.dload = x.L.store;
+                aj.l_base = len - 1;
+                aj.l_dir = -1;
+                aj.gacc = x.L.G;
+            }
+            if ((rc = lock_phase(ls, adj_state, len, mv, v, st, table, table_bytes, nullptr, 0, stream))) return rc;
+        }
+        const float scale = (float)(-1.0 / ((double)G->dt * (double)G->dt));
+        for (int i = 0; i < n; ++i)
+            CK(wt::launch_unpad(ls[i].L.G, ls[i].d.nx, ls[i].d.ny, ls[i].d.nz, ls[i].d.nzp, scale,
+                                slots[i].gwin, stream));
+        return WAVE_OK;
+    } catch (...) {
+        return WAVE_EINVAL;
+    }
+}
+
+bool lockstep_supported(const wave_grid *G, const wave_tuning *tuning)
+{
+    if (G == nullptr || tuning == nullptr || tuning->time_tile != 1) return false;
+    const int R = G->space_order / 2;
+    const MultiVariant *mv = multi_variant(R);
+    const SweepVariant *v = find_variant(R, 1, tuning->tile_y, tuning->vec);
+    return mv != nullptr && v != nullptr && v->V == mv->V && v->BZ == mv->BZ && v->BY == mv->BY &&
+           v->P == mv->P;
+}
+
+size_t lockstep_table_bytes(const wave_grid *G, int n, const wave_shot *shots)
+{
+    // an upper bound on the launch's blocks: every variant has BZ >= 24,
+    // BY >= 8, and an x-chunk of at least one plane
+    long long total = 0;
+    for (int i = 0; i < n; ++i) {
+        const long long nzp = (shots[i].n[2] + 7) / 8 * 8;
+        total += ((nzp + 23) / 24) * ((shots[i].n[1] + 7) / 8) * (long long)shots[i].n[0];
+    }
+    (void)G;
+    return lock_table_bytes(n, total);
+}
 
 cudaError_t allow_max_dynamic_smem(const void *func)
 {

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "sweep.cuh"
+#include "wave.h"
 
 namespace wt {
 
@@ -28,6 +29,51 @@ int sweep_variants_r5(const SweepVariant **out);
 int sweep_variants_r6(const SweepVariant **out);
 int sweep_variants_r7(const SweepVariant **out);
 int sweep_variants_r8(const SweepVariant **out);
+
+// Batched variants: the batched kernel for a shape of radius r, one per
+// radius (the default untiled shape).
+struct MultiVariant {
+    int R, T, V, BZ, BY, P, threads;
+    size_t smem;  // shared memory without the plane_start slices
+    cudaError_t (*launch)(int nblocks, size_t smem, cudaStream_t stream, const ShotSweep *shots,
+                          const int *block_shot, const Stencil &st, int parity, int step);
+    const void *func;
+};
+int sweep_multi_variant_r1(const MultiVariant **out);
+int sweep_multi_variant_r2(const MultiVariant **out);
+int sweep_multi_variant_r3(const MultiVariant **out);
+int sweep_multi_variant_r4(const MultiVariant **out);
+int sweep_multi_variant_r5(const MultiVariant **out);
+int sweep_multi_variant_r6(const MultiVariant **out);
+int sweep_multi_variant_r7(const MultiVariant **out);
+int sweep_multi_variant_r8(const MultiVariant **out);
+
+// One shot of a batched call: its device memory and its slices of the traces.
+struct ShotSlot {
+    const wave_shot *shot;
+    float *mw, *dw;     // the shot's window of m and damp (unpadded)
+    void *ws;           // single-shot workspace (WAVE_OP_FWD or WAVE_OP_GRAD layout)
+    size_t ws_bytes;
+    float *ckpt;        // checkpoints (gradient) or nullptr
+    float *gwin;        // window gradient out, unpadded and scaled (gradient) or nullptr
+    const float *q;     // source traces [nt][nsrc_s] or nullptr
+    float *rec_out;     // receiver traces out [nt][nrec_s] (forward) or nullptr
+    const float *resid; // residual [nt][nrec_s] (gradient) or nullptr
+};
+
+// Whether wave_*_batched can run with `tuning` on the batched kernel.
+bool lockstep_supported(const wave_grid *g, const wave_tuning *tuning);
+
+// Run a group of shots in lockstep (host runtime, wave_api.cu): the window of
+// m and damp is already in each slot (in stream order); every time step is one
+// launch of the batched kernel for all shots.  Forward (ckpt_every == 0):
+// traces into rec_out.  Gradient (ckpt_every >= 1): forward with checkpoints,
+// then per segment the recompute and the adjoint with the imaging condition;
+// window gradients into gwin.  `table` (table_bytes, from
+// lockstep_table_bytes) holds the per-shot launch arguments.
+int lockstep_group(const wave_grid *g, int n, const ShotSlot *slots, int ckpt_every,
+                   const wave_tuning *tuning, void *table, size_t table_bytes, cudaStream_t stream);
+size_t lockstep_table_bytes(const wave_grid *g, int n, const wave_shot *shots);
 
 // Gradient-mode variants (XB = 1, 2) of radius r; radii without any return 0.
 int sweep_mode_variants_r2(const SweepVariant **out);
@@ -75,6 +121,27 @@ cudaError_t launch_sweep(int nblocks, cudaStream_t stream, const SweepArgs &a, c
     return cudaLaunchKernelEx(&cfg, sweep_kernel<R, T, V, BZ, BY, P, MB, XB>, a, st, m);
 }
 
+template <int R, int T, int V, int BZ, int BY, int P, int MB>
+cudaError_t launch_sweep_multi(int nblocks, size_t smem, cudaStream_t stream, const ShotSweep *shots,
+                               const int *block_shot, const Stencil &st, int parity, int step)
+{
+    using S = SweepShape<R, T, V, BZ, BY, P, MB>;
+    cudaError_t e = allow_max_dynamic_smem((const void *)sweep_multi_kernel<R, T, V, BZ, BY, P, MB>);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nblocks);
+    cfg.blockDim = dim3((unsigned)S::NTB);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sweep_multi_kernel<R, T, V, BZ, BY, P, MB>, shots, block_shot, st,
+                              parity, step);
+}
+
 }  // namespace wt
 
 #define WAVE_VARIANT_ENTRY(R_, T_, V_, BZ_, BY_, P_, MB_)                                         \
@@ -96,6 +163,19 @@ cudaError_t launch_sweep(int nblocks, cudaStream_t stream, const SweepArgs &a, c
      wt::SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>::SMEM,                                   \
      &wt::launch_sweep<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>,                                      \
      (const void *)&wt::sweep_kernel<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>, XB_},
+
+#define WAVE_DEFINE_MULTI(R_, T_, V_, BZ_, BY_, P_, MB_)                                         \
+    namespace wt {                                                                                \
+    static const MultiVariant kMulti_r##R_ = {                                                    \
+        R_, T_, V_, BZ_, BY_, P_, SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_>::NTB,                  \
+        SweepShape<R_, T_, V_, BZ_, BY_, P_, MB_>::SMEM, &launch_sweep_multi<R_, T_, V_, BZ_, BY_, P_, MB_>, \
+        (const void *)&sweep_multi_kernel<R_, T_, V_, BZ_, BY_, P_, MB_>};                         \
+    int sweep_multi_variant_r##R_(const MultiVariant **out)                                       \
+    {                                                                                             \
+        *out = &kMulti_r##R_;                                                                     \
+        return 1;                                                                                 \
+    }                                                                                             \
+    }
 
 #define WAVE_DEFINE_MODES(r_)                                                                     \
     namespace wt {                                                                                \

@@ -1,10 +1,11 @@
 """GPU parity of the batched survey (wave_fwd_batched, wave_grad_batched).
 
-* every shot's traces equal wave_fwd on its window, bit for bit, untiled and
-  time-tiled, with more shots than concurrent slots;
-* the survey gradient equals the per-shot wave_grad gradients accumulated
-  per slot (shot i on slot i mod C, in shot order) and the slots summed in
-  slot order, bit for bit;
+* every shot's traces equal wave_fwd on its window, bit for bit, untiled
+  (shots in lockstep, one launch per step) and time-tiled (one stream per
+  shot), with more shots than concurrent slots;
+* the survey gradient equals the per-shot wave_grad gradients added into a
+  zero global array in shot order, bit for bit, for either engine and any
+  concurrency;
 * both match the FP64 oracle of the survey: traces within 1e-5 of max |d|,
   gradient rel-L2 <= 1e-5;
 * a window outside the global grid is refused before any work is queued.
@@ -78,38 +79,59 @@ def test_fwd_batched_equals_single_shots_and_oracle(wavelib, cuda, oracle, so, T
         assert np.abs(r.cpu().numpy() - dr).max() <= TOL * np.abs(dr).max()
 
 
-def test_grad_batched_equals_slot_sums_and_oracle(wavelib, cuda, oracle):
+@pytest.mark.parametrize("conc,tile", [(2, None), (3, None), (2, (12, 2))])
+def test_grad_batched_equals_shot_order_sum_and_oracle(wavelib, cuda, oracle, conc, tile):
+    """tile None: the default untiled shape, run in lockstep; (tile_y, vec):
+    another untiled shape, which has no batched kernel and runs per shot."""
     import torch
-    so, nt, k, conc = 8, 30, 7, 2
+    so, nt, k = 8, 30, 7
     grid, h, dt, m, damp, shots, q = _survey(wavelib, so, nt, seed=5)
     rng = np.random.default_rng(9)
     res = [rng.standard_normal((nt, len(s.rec_xyz))).astype(np.float32) for s in shots]
     tm, td = _t(m, cuda), _t(damp, cuda)
-    tune = wavelib.Tuning(time_tile=1)
+    tune = (wavelib.Tuning(time_tile=1) if tile is None
+            else wavelib.Tuning(time_tile=1, tile_y=tile[0], vec=tile[1]))
     g, ws = wavelib.grad_batched(grid, shots, tm, td, [_t(x, cuda) for x in q],
                                  [_t(x, cuda) for x in res], k, concurrency=conc, tuning=tune)
     assert wavelib.status(ws) == wavelib.WAVE_OK
-    # the same sums by hand: per-shot forward with checkpoints + wave_grad
-    acc = [torch.zeros(grid.n, dtype=torch.float32, device=cuda) for _ in range(conc)]
-    for i, (s, qq, rr) in enumerate(zip(shots, q, res)):
+    # the same sum by hand: per-shot forward with checkpoints + wave_grad
+    want = torch.zeros(grid.n, dtype=torch.float32, device=cuda)
+    for s, qq, rr in zip(shots, q, res):
         w = _win(s)
         gw = wavelib.Grid(s.n, grid.h, grid.dt, nt, so)
         mw, dw = tm[w].contiguous(), td[w].contiguous()
-        _, _, ck, _ = wavelib.fwd(gw, mw, dw, s.src_xyz, _t(qq, cuda), None, tuning=tune,
-                                  ckpt_every=k)
+        _, _, ck, _ = wavelib.fwd(gw, mw, dw, s.src_xyz, _t(qq, cuda), None,
+                                  tuning=wavelib.Tuning(time_tile=1), ckpt_every=k)
         gi, wsg = wavelib.grad(gw, mw, dw, s.src_xyz, _t(qq, cuda), s.rec_xyz, _t(rr, cuda), ck, k,
-                               tuning=tune)
+                               tuning=wavelib.Tuning(time_tile=1))
         assert wavelib.status(wsg) == wavelib.WAVE_OK
-        acc[i % conc][w] += gi
-    want = acc[0].clone()
-    for a in acc[1:]:
-        want += a
+        want[w] += gi
     torch.cuda.synchronize()
     assert torch.equal(g, want)
     gref = oracle.gradient_batched(np.float64(m), np.float64(damp), h, dt, nt, so, _oshots(shots),
                                    [np.float64(x) for x in q], [np.float64(x) for x in res])
     err = float(np.linalg.norm(g.cpu().numpy().astype(np.float64) - gref) / np.linalg.norm(gref))
     assert err <= TOL, err
+
+
+@pytest.mark.parametrize("so", [2, 4, 6, 8, 10, 12, 14, 16])
+def test_lockstep_fwd_equals_per_shot_every_order(wavelib, cuda, so):
+    """The batched kernel of every space order: each shot's traces equal
+    wave_fwd on its window, bit for bit, with the shots of a group of
+    different window sizes in one launch."""
+    import torch
+    nt = 9
+    grid, h, dt, m, damp, shots, q = _survey(wavelib, so, nt, seed=so)
+    tm, td = _t(m, cuda), _t(damp, cuda)
+    recs, ws = wavelib.fwd_batched(grid, shots, tm, td, [_t(x, cuda) for x in q], concurrency=4)
+    assert wavelib.status(ws) == wavelib.WAVE_OK
+    for s, r, qq in zip(shots, recs, q):
+        w = _win(s)
+        gw = wavelib.Grid(s.n, grid.h, grid.dt, nt, so)
+        d1, _, _, _ = wavelib.fwd(gw, tm[w].contiguous(), td[w].contiguous(), s.src_xyz,
+                                  _t(qq, cuda), s.rec_xyz, tuning=wavelib.Tuning(time_tile=1))
+        torch.cuda.synchronize()
+        assert np.array_equal(r.cpu().numpy(), d1.cpu().numpy())
 
 
 def test_batch_refuses_window_outside_grid(wavelib, cuda):
