@@ -41,9 +41,9 @@ HBM_FALLBACK_GBS = 6800.0
 # profiles/traffic_sweep_t1_so8_512.md), valid only for the kernel sources it was
 # taken on: the SHA-256 of csrc/sweep.cuh + csrc/variants.h must match, else the
 # bench reports null.
-TRAFFIC_SRC_SHA256 = "9f77c73d3aa79e0d17d678df377418655c41f9a550ee80f1824e995a6bdf07d1"
+TRAFFIC_SRC_SHA256 = "0b876a4f44565a300001be291108c39ecc2c1d23b1dc143378a4234669b8055c"
 TRAFFIC_BYTES = {  # ("R T V BZ BY P", chunk, n) -> bytes per launch
-    ("R4 T1 V4 BZ64 BY8 P3", 64, (512, 512, 512)): 2179188992 + 517769216,
+    ("R4 T1 V4 BZ64 BY8 P3", 64, (512, 512, 512)): 2178774784 + 518076928,
 }
 
 
@@ -471,7 +471,8 @@ def _fwi_survey(dev, inputs, wave, args):
     shots = [wave.Shot(origin=x["origin"], n=x["n"], src_xyz=x["src_xyz"], rec_xyz=x["rec_xyz"])
              for x in sv.shots]
     q = [torch.from_numpy(x).to(dev) for x in sv.src_q]
-    k, conc = 50, 4
+    k = 50
+    conc = min(len(shots), 16)  # every shot of the sample in one lockstep group
     tune = wave.Tuning(time_tile=1)
     ws_f = torch.empty(wave.batch_workspace_bytes(grid, shots, 0, conc), dtype=torch.uint8, device=dev)
     ws_g = torch.empty(wave.batch_workspace_bytes(grid, shots, k, conc), dtype=torch.uint8, device=dev)
@@ -488,7 +489,8 @@ def _fwi_survey(dev, inputs, wave, args):
     pts = sum(int(np.prod(x["n"])) for x in sv.shots)
     return {"s_per_shot": ms / 1e3 / len(shots),
             "workload": "c5: first %d of 64 shots (windows of a 512x512x256 layered model), so8, "
-                        "%d steps, k = %d, %d shots in flight; batched forward + batched gradient"
+                        "%d steps, k = %d, %d shots per lockstep group (one launch per time step, CUDA graph); "
+                        "batched forward + batched gradient"
                         % (len(shots), sv.nt, k, conc),
             "status": wave.status(ws_g),
             "gpts_equiv": 4 * pts * sv.nt / (ms / 1e3) / 1e9}

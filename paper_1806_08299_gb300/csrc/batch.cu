@@ -142,7 +142,7 @@ int layout(const wave_grid *G, int nshots, const wave_shot *shots, int k, int co
         L->ws = std::max(L->ws, al(ws));
     }
     for (int g0 = 0; g0 < nshots; g0 += conc)
-        L->table = std::max(L->table, al(wt::lockstep_table_bytes(G, std::min(conc, nshots - g0), shots + g0)));
+        L->table = std::max(L->table, al(wt::lockstep_table_bytes(G, std::min(conc, nshots - g0), shots + g0, k)));
     // m and damp windows, workspace; gradient: checkpoints and the window gradient
     L->slot = 2 * L->win + L->ws + (k > 0 ? L->ckpt + L->win : 0);
     L->total = kHead + L->table + (size_t)conc * L->slot;

@@ -896,48 +896,78 @@ struct LockShot {
     State s;        // forward / recompute state
     State adj;      // adjoint state (gradient)
     int chunk = 0;
+    long long nblocks = 0;  // blocks of one launch (the same in every phase)
 };
 
-size_t lock_table_bytes(int nshots, long long total_blocks)
+// Table of a lockstep group: the block -> shot array, then one row of
+// ShotSweep records (one per shot) per phase.
+size_t lock_table_bytes(int nshots, long long total_blocks, int nphases)
 {
-    return align_up(sizeof(wt::ShotSweep) * (size_t)nshots) + align_up(sizeof(int) * (size_t)total_blocks);
+    return align_up(sizeof(int) * (size_t)total_blocks) +
+           (size_t)nphases * align_up(sizeof(wt::ShotSweep) * (size_t)nshots);
 }
 
-// Enqueue `nsteps` launches of the batched kernel over every shot: shot i
-// advances its state `st_of(i)` with job `ls[i].job` from local step 0.  At
-// every multiple of ckpt_every (ckpt != nullptr) its state (u^n, u^{n-1}) is
-// copied to ckpts[i] first, as run_steps does.  The per-shot arguments of
-// both buffer parities go to the table at `table`.
+int lock_phases(int nt, int ckpt_every)
+{
+    return ckpt_every > 0 ? 1 + 2 * ((nt + ckpt_every - 1) / ckpt_every) : 1;
+}
+
+// The library's stream for capturing lockstep graphs on the current device.
+int capture_stream(cudaStream_t *out)
+{
+    constexpr int kMaxDev = 64;
+    static cudaStream_t streams[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDev) return WAVE_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(mu);
+    if (streams[dev] == nullptr) CK(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+    *out = streams[dev];
+    return WAVE_OK;
+}
+
+// Where one lockstep group's phases put their arguments: host rows appended
+// per phase, the device copy at `dev` (uploaded before the graph runs).
+struct LockTable {
+    std::vector<wt::ShotSweep> rows;
+    std::vector<int> block_shot;
+    int *dev_block_shot = nullptr;
+    char *dev_rows = nullptr;
+    size_t row_bytes = 0;  // one phase's records, aligned
+    int nphases = 0;
+};
+
+// Enqueue `nsteps` launches of the batched kernel over every shot on
+// `stream`: shot i advances its state `st_of(i)` with job `ls[i].job` from
+// local step 0.  At every multiple of ckpt_every (ckpts != nullptr) its state
+// (u^n, u^{n-1}) is copied to ckpts[i] first, as run_steps does.  The per-shot
+// arguments of both buffer parities become the next phase row of `tab`.
 template <class StateOf>
 int lock_phase(std::vector<LockShot> &ls, StateOf st_of, int nsteps, const wt::MultiVariant *mv,
-               const SweepVariant *v, const Stencil &st, void *table, size_t table_bytes,
-               float *const *ckpts, int ckpt_every, cudaStream_t stream)
+               const SweepVariant *v, const Stencil &st, LockTable &tab, float *const *ckpts, int ckpt_every,
+               cudaStream_t stream)
 {
     const int n = (int)ls.size();
-    std::vector<wt::ShotSweep> tab(n);
-    std::vector<int> block_shot;
-    long long total = 0;
-    int max_chunk_all = 0;
+    const int ph = tab.nphases++;
+    const size_t r0 = tab.rows.size();
+    tab.rows.resize(r0 + (size_t)n);
+    wt::ShotSweep *row = tab.rows.data() + r0;
+    int max_chunk_all = 0, block0 = 0;
     for (int i = 0; i < n; ++i) {
         for (int p = 0; p < 2; ++p) {
             State sp = st_of(i);
             if (p == 1) advance_state(sp, 1);
             long long nb = 0;
-            int rc = build_launch(ls[i].job, sp, 0, v, ls[i].chunk, &tab[i].a[p], &tab[i].mp[p], &nb);
+            int rc = build_launch(ls[i].job, sp, 0, v, ls[i].chunk, &row[i].a[p], &row[i].mp[p], &nb);
             if (rc) return rc;
-            if (p == 0) {
-                tab[i].block0 = (int)total;
-                block_shot.insert(block_shot.end(), (size_t)nb, i);
-                total += nb;
-            }
+            if (nb != ls[i].nblocks) return WAVE_EINVAL;
         }
+        row[i].block0 = block0;
+        block0 += (int)ls[i].nblocks;
         max_chunk_all = std::max(max_chunk_all, ls[i].chunk);
     }
-    if (total > 0x7fffffffLL || lock_table_bytes(n, total) > table_bytes) return WAVE_ENOSPACE;
-    wt::ShotSweep *dtab = (wt::ShotSweep *)table;
-    int *dbs = (int *)((char *)table + align_up(sizeof(wt::ShotSweep) * (size_t)n));
-    CK(cudaMemcpyAsync(dtab, tab.data(), sizeof(wt::ShotSweep) * (size_t)n, cudaMemcpyHostToDevice, stream));
-    CK(cudaMemcpyAsync(dbs, block_shot.data(), sizeof(int) * block_shot.size(), cudaMemcpyHostToDevice, stream));
+    const wt::ShotSweep *dtab = (const wt::ShotSweep *)(tab.dev_rows + (size_t)ph * tab.row_bytes);
     const size_t smem = mv->smem + wt::sweep_table_bytes(max_chunk_all, mv->R * mv->T) + 16;
     for (int j = 0; j < nsteps; ++j) {
         if (ckpts != nullptr && j % ckpt_every == 0) {
@@ -951,10 +981,120 @@ int lock_phase(std::vector<LockShot> &ls, StateOf st_of, int nsteps, const wt::M
                                    cudaMemcpyDeviceToDevice, stream));
             }
         }
-        CK(mv->launch((int)total, smem, stream, dtab, dbs, st, j & 1, j));
+        CK(mv->launch(block0, smem, stream, dtab, tab.dev_block_shot, st, j & 1, j));
     }
     if (nsteps & 1)
         for (int i = 0; i < n; ++i) advance_state(st_of(i), 1);
+    return WAVE_OK;
+}
+
+// Ends a stream capture however the enqueueing went; owns the graph.
+struct Capture {
+    cudaStream_t s = nullptr;
+    cudaGraph_t graph = nullptr;
+    bool open = false;
+    int begin(cudaStream_t st)
+    {
+        s = st;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        open = true;
+        return WAVE_OK;
+    }
+    int end()
+    {
+        open = false;
+        CK(cudaStreamEndCapture(s, &graph));
+        return graph != nullptr ? WAVE_OK : WAVE_ECUDA;
+    }
+    ~Capture()
+    {
+        if (open) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(s, &g);
+            if (g != nullptr) cudaGraphDestroy(g);
+            cudaGetLastError();  // the failed capture's error is reported through the return code
+        }
+        if (graph != nullptr) cudaGraphDestroy(graph);
+    }
+};
+
+// The gradient's time loops of a lockstep group on `stream`: forward with
+// checkpoints, then per segment (last first) the recompute with stored second
+// differences and the adjoint with the imaging condition, as wave_grad does
+// for one shot; window gradients (scaled by -1/dt^2) into slots[i].gwin.
+int lock_grad(std::vector<LockShot> &ls, const wt::ShotSlot *slots, int ckpt_every, const wt::MultiVariant *mv,
+              const SweepVariant *v, const Stencil &st, LockTable &tab, cudaStream_t stream, float dt)
+{
+    const int n = (int)ls.size();
+    const int nt = ls[0].g.nt;
+    auto fwd_state = [&](int i) -> State & { return ls[i].s; };
+    auto adj_state = [&](int i) -> State & { return ls[i].adj; };
+    std::vector<float *> ck(n);
+    for (int i = 0; i < n; ++i) ck[i] = slots[i].ckpt;
+    int rc = lock_phase(ls, fwd_state, nt, mv, v, st, tab, ck.data(), ckpt_every, stream);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+        LockShot &x = ls[i];
+        CK(cudaMemsetAsync(x.L.G, 0, sizeof(float) * x.d.npad, stream));
+        for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(x.L.V[k], 0, sizeof(float) * x.d.npad, stream));
+        for (int k = 0; k < 4; ++k) x.adj.buf[k] = x.L.V[k];
+    }
+    const int nseg = (nt + ckpt_every - 1) / ckpt_every;
+    for (int c = nseg - 1; c >= 0; --c) {
+        const int s0 = c * ckpt_every;
+        const int len = std::min(ckpt_every, nt - s0);
+        for (int i = 0; i < n; ++i) {
+            LockShot &x = ls[i];
+            const float *cp = slots[i].ckpt + (size_t)c * 2 * x.d.npad;
+            for (int k = 0; k < 4; ++k) x.s.buf[k] = x.L.U[k];
+            x.s.a = 0;
+            x.s.b = 1;
+            CK(cudaMemcpyAsync(x.s.buf[0], cp, sizeof(float) * x.d.npad, cudaMemcpyDeviceToDevice, stream));
+            CK(cudaMemcpyAsync(x.s.buf[1], cp + x.d.npad, sizeof(float) * x.d.npad, cudaMemcpyDeviceToDevice,
+                               stream));
+            Job &rj = x.job;
+            rj = Job();
+            rj.d = x.d;
+            rj.st = st;
+            rj.cB = x.L.cB;
+            rj.cC = x.L.cC;
+            rj.status = x.L.status;
+            rj.cE = x.L.cE;
+            rj.inj = x.L.inj.view();
+            rj.q = slots[i].q;
+            rj.nq = slots[i].shot->src.npts;
+            rj.q_base = s0;
+            rj.q_dir = 1;
+            rj.dstore = x.L.store;
+            rj.d_base = 0;
+            rj.d_dir = 1;
+        }
+        if ((rc = lock_phase(ls, fwd_state, len, mv, v, st, tab, nullptr, 0, stream))) return rc;
+        for (int i = 0; i < n; ++i) {
+            LockShot &x = ls[i];
+            Job &aj = x.job;
+            aj = Job();
+            aj.d = x.d;
+            aj.st = st;
+            aj.cB = x.L.cB;
+            aj.cC = x.L.cC;
+            aj.status = x.L.status;
+            aj.inj = x.L.inj2.view();
+            aj.q = slots[i].resid;
+            aj.nq = slots[i].shot->rec.npts;
+            aj.q_base = s0 + len - 1;
+            aj.q_dir = -1;
+            aj.dload = x.L.store;
+            aj.l_base = len - 1;
+            aj.l_dir = -1;
+            aj.gacc = x.L.G;
+        }
+        if ((rc = lock_phase(ls, adj_state, len, mv, v, st, tab, nullptr, 0, stream))) return rc;
+    }
+    const float scale = (float)(-1.0 / ((double)dt * (double)dt));
+    for (int i = 0; i < n; ++i)
+        CK(wt::launch_unpad(ls[i].L.G, ls[i].d.nx, ls[i].d.ny, ls[i].d.nz, ls[i].d.nzp, scale, slots[i].gwin,
+                            stream));
     return WAVE_OK;
 }
 
@@ -978,6 +1118,8 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
         const int nt = G->nt;
         std::vector<LockShot> ls(n);
         Stencil st;
+        long long total_blocks = 0;
+        // per-shot setup on `stream`: model coefficients, zero levels, point tables
         for (int i = 0; i < n; ++i) {
             LockShot &x = ls[i];
             const wave_shot &sh = *slots[i].shot;
@@ -999,6 +1141,8 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
             if ((rc = upload_table(x.tr, grad ? x.L.inj2 : x.L.rec, stream))) return rc;
             x.chunk = std::min(tuning->tile_x > 0 ? std::min(tuning->tile_x, x.d.nx) : default_chunk(x.d, v),
                                max_chunk(v));
+            x.nblocks = (long long)tiles(x.d.nzp, v->BZ) * tiles(x.d.ny, v->BY) * tiles(x.d.nx, x.chunk);
+            total_blocks += x.nblocks;
             for (int k = 0; k < 4; ++k) x.s.buf[k] = x.L.U[k];
             x.job = Job();
             x.job.d = x.d;
@@ -1016,87 +1160,51 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
             }
         }
         CK(wt::allow_max_dynamic_smem(mv->func));
+        const int nphases = lock_phases(nt, ckpt_every);
+        if (total_blocks > 0x7fffffffLL || lock_table_bytes(n, total_blocks, nphases) > table_bytes)
+            return WAVE_ENOSPACE;
+        LockTable tab;
+        tab.row_bytes = align_up(sizeof(wt::ShotSweep) * (size_t)n);
+        tab.dev_block_shot = (int *)table;
+        tab.dev_rows = (char *)table + align_up(sizeof(int) * (size_t)total_blocks);
+        tab.rows.reserve((size_t)nphases * n);
+        tab.block_shot.reserve((size_t)total_blocks);
+        for (int i = 0; i < n; ++i) tab.block_shot.insert(tab.block_shot.end(), (size_t)ls[i].nblocks, i);
+
+        // The time loops go into one CUDA graph, captured on the library's
+        // stream and launched on `stream` after the tables are uploaded.
+        cudaStream_t cs;
+        int rc = capture_stream(&cs);
+        if (rc) return rc;
+        Capture cap;
+        if ((rc = cap.begin(cs))) return rc;
         auto fwd_state = [&](int i) -> State & { return ls[i].s; };
         if (!grad) {
-            int rc = lock_phase(ls, fwd_state, nt, mv, v, st, table, table_bytes, nullptr, 0, stream);
-            if (rc) return rc;
-            for (int i = 0; i < n; ++i)
-                if (slots[i].shot->rec.npts > 0 && slots[i].rec_out != nullptr)
-                    CK(wt::launch_gather(ls[i].L.corner, ls[i].L.rec.wts, nt, slots[i].shot->rec.npts, 1,
-                                         slots[i].rec_out, stream));
-            return WAVE_OK;
+            rc = lock_phase(ls, fwd_state, nt, mv, v, st, tab, nullptr, 0, cs);
+            for (int i = 0; i < n && rc == WAVE_OK; ++i)
+                if (slots[i].shot->rec.npts > 0 && slots[i].rec_out != nullptr &&
+                    wt::launch_gather(ls[i].L.corner, ls[i].L.rec.wts, nt, slots[i].shot->rec.npts, 1,
+                                      slots[i].rec_out, cs) != cudaSuccess)
+                    rc = WAVE_ECUDA;
+        } else {
+            rc = lock_grad(ls, slots, ckpt_every, mv, v, st, tab, cs, G->dt);
         }
-        // gradient: forward with checkpoints, then per segment (last first)
-        // the recompute with stored second differences and the adjoint with
-        // the imaging condition, as wave_grad does for one shot
-        std::vector<float *> ck(n);
-        for (int i = 0; i < n; ++i) ck[i] = slots[i].ckpt;
-        int rc = lock_phase(ls, fwd_state, nt, mv, v, st, table, table_bytes, ck.data(), ckpt_every, stream);
         if (rc) return rc;
-        for (int i = 0; i < n; ++i) {
-            LockShot &x = ls[i];
-            CK(cudaMemsetAsync(x.L.G, 0, sizeof(float) * x.d.npad, stream));
-            for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(x.L.V[k], 0, sizeof(float) * x.d.npad, stream));
-            for (int k = 0; k < 4; ++k) x.adj.buf[k] = x.L.V[k];
-        }
-        auto adj_state = [&](int i) -> State & { return ls[i].adj; };
-        const int nseg = (nt + ckpt_every - 1) / ckpt_every;
-        for (int c = nseg - 1; c >= 0; --c) {
-            const int s0 = c * ckpt_every;
-            const int len = std::min(ckpt_every, nt - s0);
-            for (int i = 0; i < n; ++i) {
-                LockShot &x = ls[i];
-                const float *cp = slots[i].ckpt + (size_t)c * 2 * x.d.npad;
-                for (int k = 0; k < 4; ++k) x.s.buf[k] = x.L.U[k];
-                x.s.a = 0;
-                x.s.b = 1;
-                CK(cudaMemcpyAsync(x.s.buf[0], cp, sizeof(float) * x.d.npad, cudaMemcpyDeviceToDevice, stream));
-                CK(cudaMemcpyAsync(x.s.buf[1], cp + x.d.npad, sizeof(float) * x.d.npad,
-                                   cudaMemcpyDeviceToDevice, stream));
-                Job &rj = x.job;
-                rj = Job();
-                rj.d = x.d;
-                rj.st = st;
-                rj.cB = x.L.cB;
-                rj.cC = x.L.cC;
-                rj.status = x.L.status;
-                rj.cE = x.L.cE;
-                rj.inj = x.L.inj.view();
-                rj.q = slots[i].q;
-                rj.nq = slots[i].shot->src.npts;
-                rj.q_base = s0;
-                rj.q_dir = 1;
-                rj.dstore = x.L.store;
-                rj.d_base = 0;
-                rj.d_dir = 1;
-            }
-            if ((rc = lock_phase(ls, fwd_state, len, mv, v, st, table, table_bytes, nullptr, 0, stream))) return rc;
-            for (int i = 0; i < n; ++i) {
-                LockShot &x = ls[i];
-                Job &aj = x.job;
-                aj = Job();
-                aj.d = x.d;
-                aj.st = st;
-                aj.cB = x.L.cB;
-                aj.cC = x.L.cC;
-                aj.status = x.L.status;
-                aj.inj = x.L.inj2.view();
-                aj.q = slots[i].resid;
-                aj.nq = slots[i].shot->rec.npts;
-                aj.q_base = s0 + len - 1;
-                aj.q_dir = -1;
-                aj.dload = x.L.store;
-                aj.l_base = len - 1;
-                aj.l_dir = -1;
-                aj.gacc = x.L.G;
-            }
-            if ((rc = lock_phase(ls, adj_state, len, mv, v, st, table, table_bytes, nullptr, 0, stream))) return rc;
-        }
-        const float scale = (float)(-1.0 / ((double)G->dt * (double)G->dt));
-        for (int i = 0; i < n; ++i)
-            CK(wt::launch_unpad(ls[i].L.G, ls[i].d.nx, ls[i].d.ny, ls[i].d.nz, ls[i].d.nzp, scale,
-                                slots[i].gwin, stream));
-        return WAVE_OK;
+        if ((rc = cap.end())) return rc;
+        if ((int)tab.rows.size() != nphases * n) return WAVE_EINVAL;
+        cudaGraphExec_t exec = nullptr;
+        CK(cudaGraphInstantiate(&exec, cap.graph, 0));
+        rc = WAVE_OK;
+        if (cudaMemcpyAsync(tab.dev_block_shot, tab.block_shot.data(), sizeof(int) * tab.block_shot.size(),
+                            cudaMemcpyHostToDevice, stream) != cudaSuccess)
+            rc = WAVE_ECUDA;
+        for (int p = 0; p < nphases && rc == WAVE_OK; ++p)
+            if (cudaMemcpyAsync(tab.dev_rows + (size_t)p * tab.row_bytes, tab.rows.data() + (size_t)p * n,
+                                sizeof(wt::ShotSweep) * (size_t)n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+                rc = WAVE_ECUDA;
+        if (rc == WAVE_OK && cudaGraphLaunch(exec, stream) != cudaSuccess) rc = WAVE_ECUDA;
+        cudaGraphExecDestroy(exec);  // freed once the launch completes
+        return rc;
     } catch (...) {
         return WAVE_EINVAL;
     }
@@ -1112,7 +1220,7 @@ bool lockstep_supported(const wave_grid *G, const wave_tuning *tuning)
            v->P == mv->P;
 }
 
-size_t lockstep_table_bytes(const wave_grid *G, int n, const wave_shot *shots)
+size_t lockstep_table_bytes(const wave_grid *G, int n, const wave_shot *shots, int ckpt_every)
 {
     // an upper bound on the launch's blocks: every variant has BZ >= 24,
     // BY >= 8, and an x-chunk of at least one plane
@@ -1121,8 +1229,7 @@ size_t lockstep_table_bytes(const wave_grid *G, int n, const wave_shot *shots)
         const long long nzp = (shots[i].n[2] + 7) / 8 * 8;
         total += ((nzp + 23) / 24) * ((shots[i].n[1] + 7) / 8) * (long long)shots[i].n[0];
     }
-    (void)G;
-    return lock_table_bytes(n, total);
+    return lock_table_bytes(n, total, lock_phases(G->nt, ckpt_every));
 }
 
 cudaError_t allow_max_dynamic_smem(const void *func)

@@ -66,14 +66,15 @@ bool lockstep_supported(const wave_grid *g, const wave_tuning *tuning);
 
 // Run a group of shots in lockstep (host runtime, wave_api.cu): the window of
 // m and damp is already in each slot (in stream order); every time step is one
-// launch of the batched kernel for all shots.  Forward (ckpt_every == 0):
-// traces into rec_out.  Gradient (ckpt_every >= 1): forward with checkpoints,
-// then per segment the recompute and the adjoint with the imaging condition;
-// window gradients into gwin.  `table` (table_bytes, from
-// lockstep_table_bytes) holds the per-shot launch arguments.
+// launch of the batched kernel for all shots, and the time loops are one CUDA
+// graph launched on `stream`.  Forward (ckpt_every == 0): traces into
+// rec_out.  Gradient (ckpt_every >= 1): forward with checkpoints, then per
+// segment the recompute and the adjoint with the imaging condition; window
+// gradients into gwin.  `table` (table_bytes, from lockstep_table_bytes with
+// the same ckpt_every) holds the per-shot launch arguments of every phase.
 int lockstep_group(const wave_grid *g, int n, const ShotSlot *slots, int ckpt_every,
                    const wave_tuning *tuning, void *table, size_t table_bytes, cudaStream_t stream);
-size_t lockstep_table_bytes(const wave_grid *g, int n, const wave_shot *shots);
+size_t lockstep_table_bytes(const wave_grid *g, int n, const wave_shot *shots, int ckpt_every);
 
 // Gradient-mode variants (XB = 1, 2) of radius r; radii without any return 0.
 int sweep_mode_variants_r2(const SweepVariant **out);

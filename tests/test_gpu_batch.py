@@ -134,6 +134,35 @@ def test_lockstep_fwd_equals_per_shot_every_order(wavelib, cuda, so):
         assert np.array_equal(r.cpu().numpy(), d1.cpu().numpy())
 
 
+def test_lockstep_reused_workspace_and_side_stream(wavelib, cuda):
+    """Two different surveys through one workspace, the second on a side
+    stream: the per-shot tables and TMA descriptors the first call left at the
+    same addresses must not leak into the second, whose traces equal a call
+    on a fresh workspace."""
+    import torch
+    so, nt = 8, 11
+    grid, h, dt, m, damp, shots, q = _survey(wavelib, so, nt, seed=3)
+    tm, td = _t(m, cuda), _t(damp, cuda)
+    qa = [_t(x, cuda) for x in q]
+    # the second survey: the same windows in reverse order, other traces
+    shots_b, qb = shots[::-1], [2.0 * x for x in qa[::-1]]
+    nbytes = max(wavelib.batch_workspace_bytes(grid, shots, 0, 2),
+                 wavelib.batch_workspace_bytes(grid, shots_b, 0, 2))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=cuda)
+    fresh, _ = wavelib.fwd_batched(grid, shots_b, tm, td, qb, concurrency=2)
+    torch.cuda.synchronize()
+    wavelib.fwd_batched(grid, shots, tm, td, qa, concurrency=2, workspace=ws)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        again, _ = wavelib.fwd_batched(grid, shots_b, tm, td, qb, concurrency=2, workspace=ws,
+                                       stream=side)
+    side.synchronize()
+    assert wavelib.status(ws) == wavelib.WAVE_OK
+    for x, y in zip(again, fresh):
+        assert torch.equal(x, y)
+
+
 def test_batch_refuses_window_outside_grid(wavelib, cuda):
     import torch
     grid = wavelib.Grid((20, 20, 20), (inputs.H,) * 3, 1e-4, 4, 4)
