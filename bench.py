@@ -375,6 +375,9 @@ def run_ours(args):
     survey = None
     if args.survey and world == 1:
         survey = _fwi_survey(dev, inputs, wave, args)
+    orders = None
+    if args.orders and world == 1:
+        orders = _orders_sweep(dev, inputs, wave, args)
 
     # --- roofline of the sweep kernel --------------------------------------
     hbm, peak_kind = _peaks()
@@ -423,6 +426,8 @@ def run_ours(args):
             line["fwi_gradient"] = fwi
         if survey is not None:
             line["fwi_survey"] = survey
+        if orders is not None:
+            line["orders_c3"] = orders
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line))
@@ -496,6 +501,59 @@ def _fwi_survey(dev, inputs, wave, args):
             "gpts_equiv": 4 * pts * sv.nt / (ms / 1e3) / 1e9}
 
 
+def _orders_sweep(dev, inputs, wave, args):
+    """c3: 768 x 768 x 512, smooth random velocity 1.5-4.5 km/s, 40-point
+    damping, one source.  Per space order 4/8/12/16: the fastest untiled plan
+    and the fastest time-tiled plan (every compiled depth T >= 2, shapes
+    autotuned), each timed over args.orders_nt steps with the inputs resident,
+    as GPts/s and as a fraction of the HBM roof at the plan's algorithmic
+    bytes per point-update (20 untiled, 24/T time-tiled)."""
+    import torch
+    p0 = inputs.c3(space_order=4, nt=args.orders_nt)
+    tm = torch.from_numpy(p0.m).to(dev)
+    td = torch.from_numpy(p0.damp).to(dev)
+    hbm, _ = _peaks()
+    pts = float(np.prod(p0.n)) * p0.nt
+    stream = torch.cuda.current_stream()
+    out = {"workload": "c3: 768x768x512, smooth random velocity 1.5-4.5 km/s, 40-pt damping, "
+                       "1 Ricker 15 Hz source, %d steps per timing" % p0.nt}
+    for so in (4, 8, 12, 16):
+        dt = inputs.DT[("c3", so)]
+        grid = wave.Grid(p0.n, p0.h, dt, p0.nt, so)
+        q = np.ascontiguousarray(inputs.ricker(15.0, dt, p0.nt)[:, None], dtype=np.float32)
+        tq = torch.from_numpy(q).to(dev)
+        ws = torch.empty(wave.workspace_bytes(grid, wave.WAVE_OP_FWD, 1, 0), dtype=torch.uint8,
+                         device=dev)
+
+        def fwd(tune):
+            wave.fwd(grid, tm, td, p0.src_xyz, tq, None, tuning=tune, workspace=ws)
+
+        def best_at(T):
+            t = wave.Tuning(time_tile=T, flags=wave.WAVE_AUTOTUNE_SHAPE)
+            fwd(t)
+            pl = wave.describe_plan(grid, t)
+            fixed = wave.Tuning(time_tile=pl["time_tile"], tile_y=pl["tile_y"], tile_x=pl["tile_x"],
+                                vec=pl["vec"])
+            fwd(fixed)
+            ms, _ = _timed(lambda: fwd(fixed), 1, stream)
+            g = pts / (ms / 1e3) / 1e9
+            bpp = 20.0 if T == 1 else 24.0 / T
+            return {"gpts": g, "frac_hbm": g * bpp / hbm, "bytes_per_point": bpp, "plan": pl}
+
+        row = {"untiled": best_at(1)}
+        depths = sorted({v["time_tile"] for v in wave.list_variants(so) if v["time_tile"] >= 2})
+        tiled = [best_at(T) for T in depths]
+        row["time_tiled"] = max(tiled, key=lambda r: r["gpts"]) if tiled else None
+        row["tiled_over_untiled"] = (row["time_tiled"]["gpts"] / row["untiled"]["gpts"]
+                                     if tiled else None)
+        if not tiled:
+            row["note"] = "no time-tiled shape of this order fits the shared-memory and register budget"
+        out["so%d" % so] = row
+        del ws
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -510,6 +568,8 @@ def main():
     ap.add_argument("--no-survey", dest="survey", action="store_false")
     ap.add_argument("--survey-shots", type=int, default=8)
     ap.add_argument("--survey-nt", type=int, default=1500)
+    ap.add_argument("--no-orders", dest="orders", action="store_false")
+    ap.add_argument("--orders-nt", type=int, default=100)
     ap.add_argument("--fwi-nt", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,

@@ -34,6 +34,12 @@
 //    holds, per iteration, level n-1 and the per-point
 //    coefficients B, C of stage 1's plane; stage s reads the B, C that stage 1
 //    read (s-1)R iterations earlier, so ring K is (T-1)R+1+P iterations deep.
+//    The untiled sweep (T = 1) of radius R >= 3 keeps no ring U.  Each ring-K slot of it also
+//    takes the centre plane c0 - R with its halo and, separately, the
+//    level-n plane c0 in the K-box shape for the x-queue.  That plane comes
+//    twice from L2 instead of staying R iterations in shared memory, so a
+//    block needs 1+P slots instead of R+1+P planes, which at high orders
+//    lets more blocks share an SM.
 //    TMA fills everything outside
 //    the grid with zeros; with B = C = 0 there, points outside the grid are
 //    computed as exactly 0.  This plays the role of the paper's min/max bounds
@@ -42,7 +48,7 @@
 //    level per thread (V consecutive z points per thread).  Stages s >= 2
 //    exchange their centre plane through shared memory for the y and z
 //    neighbours (double buffered, one named barrier among the consumer threads
-//    per plane); stage 1 reads them from ring U.
+//    per plane); stage 1 reads them from ring U (T = 1: from the ring-K slot).
 //  * Sources are injected and receiver corners recorded inside the sweep (the
 //    imperfectly nested source/receiver loops the paper leaves open,
 //    Sec. 4.5.1 and Sec. 6.3.1).
@@ -110,6 +116,7 @@ struct SweepArgs {
     int chunk;               // x planes per block
     int tiles_z, tiles_y;    // column tiles of the grid
     int *status;             // device status word (atomicMin of WAVE_E* codes)
+    const int *order;        // launch order: block b sweeps tile order[b] (nullptr: tile b)
 };
 
 // TMA descriptors of the arrays the sweep reads (all [nx][ny][nz] float32):
@@ -121,6 +128,7 @@ struct SweepArgs {
 //          step's stored D row, x1 = the gradient accumulator G
 struct SweepMaps {
     CUtensorMap u, um, B, C, x0, x1;
+    CUtensorMap uk;  // level n with the K-box shape: the x-queue feed of T == 1
 };
 
 // Shared memory of the per-plane sparse slices for an x-chunk of `chunk`
@@ -152,15 +160,31 @@ struct SweepShape {
     static constexpr int RP = ((R + 3) / 4) * 4;    // z pad of ring-U rows / centre planes
     static constexpr int PW = W0 + 2 * RP;          // ring-U / centre-plane pitch
     static constexpr int HK = H0 - 2 * R;           // rows of ring-K boxes (from row R)
-    static constexpr int DU = R + 1 + P;            // ring-U depth (planes)
+    // T == 1 with R >= 3 keeps no ring U: each ring-K slot also holds the
+    // centre plane c0 - R with its halo (for the y and z neighbours) and the
+    // level-n plane c0 that enters the x-queue, so no slot has to outlive its
+    // iteration (for R <= 2 the R+1+P planes of ring U are the smaller store)
+    static constexpr bool SPLIT = T == 1 && R >= 3;
+    static constexpr int DU = SPLIT ? 0 : R + 1 + P;  // ring-U depth (planes)
     static constexpr int DK = (T - 1) * R + 1 + P;  // ring-K depth (iterations)
     static constexpr int DF = P + 1;                // iterations in flight (full barriers)
     static constexpr unsigned UBOX = PW * H0 * 4;   // bytes of one U box
     static constexpr unsigned KBOX = W0 * HK * 4;   // bytes of one K box (um, B or C)
     static constexpr unsigned USLOT = (UBOX + 127) / 128 * 128;
     static constexpr unsigned KBOXP = (KBOX + 127) / 128 * 128;
-    static constexpr unsigned KSLOT = (3 + XB) * KBOXP;
-    static constexpr unsigned TXB = UBOX + (3 + XB) * KBOX; // bytes landing per iteration
+    // byte offsets in a ring-K slot: [centre U box (T == 1)] u^{n-1}, B, C,
+    // [x0, x1], [level-n feed box (T == 1)]
+    static constexpr unsigned K_U = 0;
+    static constexpr unsigned K_UM = SPLIT ? USLOT : 0;
+    static constexpr unsigned K_B = K_UM + KBOXP;
+    static constexpr unsigned K_C = K_UM + 2 * KBOXP;
+    static constexpr unsigned K_X0 = K_UM + 3 * KBOXP;
+    static constexpr unsigned K_X1 = K_UM + 4 * KBOXP;
+    static constexpr unsigned K_F = K_UM + (3 + XB) * KBOXP;
+    static constexpr unsigned KSLOT = SPLIT ? K_F + KBOXP : (3 + XB) * KBOXP;
+    // bytes landing per iteration: from iteration 2R on, and before (fill)
+    static constexpr unsigned TXB = UBOX + (3 + XB) * KBOX + (SPLIT ? KBOX : 0);
+    static constexpr unsigned TX0 = SPLIT ? KBOX : UBOX;
     static constexpr int PLANE = PW * H0;           // centre plane (floats), stages >= 2
     static constexpr size_t OFF_K = (size_t)DU * USLOT;
     static constexpr size_t OFF_S = OFF_K + (size_t)DK * KSLOT;
@@ -359,7 +383,9 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
     const int tid = threadIdx.x;
     const int col = S::ZL + (tid % S::LZ) * V;  // layout column of this thread's V points
     const int row = R + tid / S::LZ;            // layout row
-    int b = blk;
+    // blocks that hold sparse points come first in the launch order, so their
+    // extra work overlaps the later waves instead of trailing the last one
+    int b = a.order != nullptr ? __ldg(a.order + blk) : blk;
     const int tzi = b % a.tiles_z;
     b /= a.tiles_z;
     const int tyi = b % a.tiles_y;
@@ -406,10 +432,18 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
         if (a.rec.plane_start != nullptr) {
             const int e0 = a.rec.plane_start[cp], e1 = a.rec.plane_start[ci];
             prec[k] = e0;
-            for (int e = e0; e < e1 && !fr; ++e) {
-                const int4 pt = a.rec.pts[e];
-                fr = pt.x >= gy0 + S::RT && pt.x < gy0 + S::RT + BY && pt.y >= gz0 + S::A0 &&
-                     pt.y < gz0 + S::A0 + BZ;
+            // four table points per round trip (a plane often holds a few)
+            for (int eb = e0; eb < e1 && !fr; eb += 4) {
+                int4 pt4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    pt4[u] = eb + u < e1 ? __ldg(a.rec.pts + eb + u) : make_int4(-(1 << 30), -(1 << 30), 0, 0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int4 pt = pt4[u];
+                    fr |= pt.x >= gy0 + S::RT && pt.x < gy0 + S::RT + BY && pt.y >= gz0 + S::A0 &&
+                          pt.y < gz0 + S::A0 + BZ;
+                }
             }
         } else {
             prec[k] = 0;
@@ -449,7 +483,8 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
                 // flight; empU / empK -- every consumer is done reading the slot.
                 bool ok = true;
                 if (rf > 0) ok = mbar_wait_bounded(empF + jf, (uint32_t)((rf - 1) & 1));
-                if (ok && ru > 0) ok = mbar_wait_bounded(empU + ju, (uint32_t)((ru - 1) & 1));
+                if constexpr (!S::SPLIT)
+                    if (ok && ru > 0) ok = mbar_wait_bounded(empU + ju, (uint32_t)((ru - 1) & 1));
                 if (ok && rk > 0) ok = mbar_wait_bounded(empK + jk, (uint32_t)((rk - 1) & 1));
                 if (!ok) {
                     *abort_flag = 1;
@@ -461,17 +496,25 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
                 // (u^{n-1}, B, C) of plane c0 - R are first read by stage 1 at
                 // iteration 2R: the ring-K slots of earlier iterations stay unused
                 const bool kload = j >= 2 * R;
-                mbar_expect_tx(bf, kload ? S::TXB : S::UBOX);
-                tma_load_3d(ringU + (size_t)ju * (S::USLOT / 4), &mp.u, gz0 - S::RP, gy0, c0, bf);
-                if (kload) {
-                    unsigned char *kslot = ringK + (size_t)jk * S::KSLOT;
-                    tma_load_3d(kslot, &mp.um, gz0, gy0 + R, c0 - R, bf);
-                    tma_load_3d(kslot + S::KBOXP, &mp.B, gz0, gy0 + R, c0 - R, bf);
-                    tma_load_3d(kslot + 2 * S::KBOXP, &mp.C, gz0, gy0 + R, c0 - R, bf);
-                    if constexpr (XB >= 1) tma_load_3d(kslot + 3 * S::KBOXP, &mp.x0, gz0, gy0 + R, c0 - R, bf);
-                    if constexpr (XB >= 2) tma_load_3d(kslot + 4 * S::KBOXP, &mp.x1, gz0, gy0 + R, c0 - R, bf);
+                unsigned char *kslot = ringK + (size_t)jk * S::KSLOT;
+                mbar_expect_tx(bf, kload ? S::TXB : S::TX0);
+                if constexpr (S::SPLIT) {
+                    // level n of plane c0 for the x-queue (rows of the threads
+                    // only), and from 2R on the centre plane c0 - R with halo
+                    tma_load_3d(kslot + S::K_F, &mp.uk, gz0, gy0 + R, c0, bf);
+                    if (kload) tma_load_3d(kslot + S::K_U, &mp.u, gz0 - S::RP, gy0, c0 - R, bf);
+                } else {
+                    tma_load_3d(ringU + (size_t)ju * (S::USLOT / 4), &mp.u, gz0 - S::RP, gy0, c0, bf);
                 }
-                if (++ju == S::DU) { ju = 0; ++ru; }
+                if (kload) {
+                    tma_load_3d(kslot + S::K_UM, &mp.um, gz0, gy0 + R, c0 - R, bf);
+                    tma_load_3d(kslot + S::K_B, &mp.B, gz0, gy0 + R, c0 - R, bf);
+                    tma_load_3d(kslot + S::K_C, &mp.C, gz0, gy0 + R, c0 - R, bf);
+                    if constexpr (XB >= 1) tma_load_3d(kslot + S::K_X0, &mp.x0, gz0, gy0 + R, c0 - R, bf);
+                    if constexpr (XB >= 2) tma_load_3d(kslot + S::K_X1, &mp.x1, gz0, gy0 + R, c0 - R, bf);
+                }
+                if constexpr (!S::SPLIT)
+                    if (++ju == S::DU) { ju = 0; ++ru; }
                 if (++jk == S::DK) { jk = 0; ++rk; }
                 if (++jf == S::DF) { jf = 0; ++rf; }
             }
@@ -532,9 +575,14 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
             for (int k = 0; k < QL - 1; ++k)
 #pragma unroll
                 for (int j = 0; j < V2; ++j) q[0][k][j] = q[0][k + 1][j];
-            ld2<V>(q[0][QL - 1], ringU + (size_t)su * (S::USLOT / 4) + ownU);
-            const int suc = su - R < 0 ? su - R + S::DU : su - R;  // U slot of plane c0 - R
             const unsigned char *kslot = ringK + (size_t)sk * S::KSLOT;
+            int suc = 0;  // ring-U slot of plane c0 - R (T > 1)
+            if constexpr (S::SPLIT) {
+                ld2<V>(q[0][QL - 1], reinterpret_cast<const float *>(kslot + S::K_F) + ownK);
+            } else {
+                ld2<V>(q[0][QL - 1], ringU + (size_t)su * (S::USLOT / 4) + ownU);
+                suc = su - R < 0 ? su - R + S::DU : su - R;
+            }
 
 #pragma unroll
             for (int s = 1; s <= T; ++s) {
@@ -553,10 +601,11 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
                 const unsigned char *ks = ringK + (size_t)(kk < 0 ? kk + S::DK : kk) * S::KSLOT;
                 if (rowok) {
                     float2 cBv[V2], cCv[V2], up[V2], lap[V2];
-                    ld2<V>(cBv, reinterpret_cast<const float *>(ks + S::KBOXP) + ownK);
-                    ld2<V>(cCv, reinterpret_cast<const float *>(ks + 2 * S::KBOXP) + ownK);
+                    ld2<V>(cBv, reinterpret_cast<const float *>(ks + S::K_B) + ownK);
+                    ld2<V>(cCv, reinterpret_cast<const float *>(ks + S::K_C) + ownK);
                     // centre plane of stage s: ring U (s = 1) or the exchanged plane
-                    const float *Pc = s == 1 ? ringU + (size_t)suc * (S::USLOT / 4)
+                    const float *Pc = s == 1 ? (S::SPLIT ? reinterpret_cast<const float *>(ks + S::K_U)
+                                                         : ringU + (size_t)suc * (S::USLOT / 4))
                                              : splane + ((s - 2) * 2 + cur) * S::PLANE;
                     // z window of the thread: pairs at even offsets (zz) and at odd
                     // offsets (zo = (z[2i+1], z[2i+2])); own points start at RP
@@ -605,7 +654,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
                         for (int j = 0; j < V2; ++j) lap[j] = __fadd2_rn(__fadd2_rn(lap[j], ly[j]), lz[j]);
                     }
                     if (s == 1) {
-                        ld2<V>(up, reinterpret_cast<const float *>(kslot) + ownK);  // level n-1
+                        ld2<V>(up, reinterpret_cast<const float *>(kslot + S::K_UM) + ownK);  // level n-1
                     } else {
                         // level n+s-2 on plane cs: oldest of stage s-1's queue
 #pragma unroll
@@ -623,7 +672,7 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
                         // u^{n+1} - 2u^n + u^{n-1} = E (u^n - u^{n-1}) + C (L u^n + f^n)
                         float2 e[V2];
                         if constexpr (XB == 1)
-                            ld2<V>(e, reinterpret_cast<const float *>(ks + 3 * S::KBOXP) + ownK);
+                            ld2<V>(e, reinterpret_cast<const float *>(ks + S::K_X0) + ownK);
                         else
                             ldg2<V>(e, a.cE + pidx);
 #pragma unroll
@@ -667,9 +716,15 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
                 if (own_pt) {
                     if (any_rec && frec[cs - pbase]) {
                         const int e0 = prec[cs - pbase], e1 = prec[cs - pbase + 1];
-                        for (int e = e0; e < e1; ++e) {
-                            const int4 pt = a.rec.pts[e];
-                            if (pt.x == gy && pt.y >= gz && pt.y < gz + V) {
+                        for (int eb = e0; eb < e1; eb += 4) {
+                            int4 pt4[4];  // four table points per round trip
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+                                pt4[u] = eb + u < e1 ? __ldg(a.rec.pts + eb + u) : make_int4(-1, -1, 0, 0);
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int4 pt = pt4[u];
+                                if (pt.x != gy || pt.y < gz || pt.y >= gz + V) continue;
                                 const int jj = pt.y - gz;
                                 float v = un[0].x;
 #pragma unroll
@@ -686,8 +741,8 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
                     if (a.gacc != nullptr) {
                         float2 dl[V2], g[V2];
                         if constexpr (XB == 2) {
-                            ld2<V>(dl, reinterpret_cast<const float *>(ks + 3 * S::KBOXP) + ownK);
-                            ld2<V>(g, reinterpret_cast<const float *>(ks + 4 * S::KBOXP) + ownK);
+                            ld2<V>(dl, reinterpret_cast<const float *>(ks + S::K_X0) + ownK);
+                            ld2<V>(g, reinterpret_cast<const float *>(ks + S::K_X1) + ownK);
                         } else {
                             ldg2<V>(dl, a.dload + (a.l_row0 + (long long)a.l_dir * (s - 1)) * a.npad + pidx);
                             ld2<V>(g, a.gacc + pidx);
@@ -714,7 +769,8 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
             // (T-1)R).  Slots of iterations before 0 were never filled.
             __syncwarp();
             if (lane0) {
-                if (it >= R) mbar_arrive(empU + suc);
+                if constexpr (!S::SPLIT)
+                    if (it >= R) mbar_arrive(empU + suc);
                 if (it >= (T - 1) * R) {
                     const int kk = sk - (T - 1) * R;
                     mbar_arrive(empK + (kk < 0 ? kk + S::DK : kk));
@@ -732,7 +788,8 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
                     break;
                 }
             }
-            if (++su == S::DU) su = 0;
+            if constexpr (!S::SPLIT)
+                if (++su == S::DU) su = 0;
             if (++sk == S::DK) sk = 0;
             if (++sf == S::DF) { sf = 0; pf ^= 1u; }
         }
@@ -750,24 +807,25 @@ sweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenci
 
 // One shot of a batched launch, in device memory: its arguments and TMA
 // descriptors for both parities of its ping-pong buffers (the row fields of
-// the arguments hold the rows of step 0), and its first block in the launch.
-struct alignas(64) ShotSweep {
+// the arguments hold the rows of step 0).
+struct ShotSweep {  // 128-byte aligned, as its tensor maps
     SweepMaps mp[2];
     SweepArgs a[2];
-    int block0;
 };
 
-// Every shot of a batch advanced by one launch: block i belongs to shot
-// block_shot[i] (its blocks are consecutive), the launch is time step `step`
-// of all shots, and `parity` selects their buffers.  The shots share the
-// stencil (grid spacing and space order), nt and dt.
+// Every shot of a batch advanced by one launch: block i sweeps tile
+// block_map[i].y of shot block_map[i].x (tiles holding sparse points of any
+// shot first), the launch is time step `step` of all shots, and `parity`
+// selects their buffers.  The shots share the stencil (grid spacing and space
+// order), nt and dt.
 template <int R, int T, int V, int BZ, int BY, int P, int MB>
 __global__ void __launch_bounds__(SweepShape<R, T, V, BZ, BY, P, MB>::NTB, MB)
-sweep_multi_kernel(const ShotSweep *__restrict__ shots, const int *__restrict__ block_shot,
+sweep_multi_kernel(const ShotSweep *__restrict__ shots, const int2 *__restrict__ block_map,
                    const __grid_constant__ Stencil st, int parity, int step)
 {
     using S = SweepShape<R, T, V, BZ, BY, P, MB>;
-    const ShotSweep &sh = shots[block_shot[blockIdx.x]];
+    const int2 bm = block_map[blockIdx.x];
+    const ShotSweep &sh = shots[bm.x];
     if (threadIdx.x == S::NT) {
         // the producer thread's TMA reads these descriptors from global
         // memory, which a host copy may have rewritten since a launch that
@@ -777,13 +835,15 @@ sweep_multi_kernel(const ShotSweep *__restrict__ shots, const int *__restrict__ 
         tensormap_acquire(&m.um);
         tensormap_acquire(&m.B);
         tensormap_acquire(&m.C);
+        tensormap_acquire(&m.uk);
     }
     SweepArgs la = sh.a[parity];
     la.q_row0 += la.q_dir * step;
     la.c_row0 += la.c_dir * step;
     la.d_row0 += (long long)la.d_dir * step;
     la.l_row0 += (long long)la.l_dir * step;
-    sweep_block<R, T, V, BZ, BY, P, MB, 0>(la, st, sh.mp[parity], (int)blockIdx.x - sh.block0);
+    la.order = nullptr;
+    sweep_block<R, T, V, BZ, BY, P, MB, 0>(la, st, sh.mp[parity], bm.y);
 }
 
 }  // namespace wt

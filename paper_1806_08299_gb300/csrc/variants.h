@@ -4,8 +4,10 @@
 // (T = 1: untiled sweep), V z-points per thread, output tile BZ (z) x BY (y)
 // per block, TMA prefetch distance P planes, compiled for MB resident blocks
 // per SM (the __launch_bounds__ minimum, which caps registers per thread).  Shared memory holds the TMA
-// rings (R+1+P level-n planes with halos; (T-1)R+1+P iterations of level n-1
-// and coefficients) and the centre planes of stages >= 2; registers hold
+// rings (T >= 2: R+1+P level-n planes with halos and (T-1)R+1+P iterations of
+// level n-1 and coefficients; T = 1: 1+P iterations of the centre plane,
+// the x-queue plane, level n-1 and coefficients) and the centre planes of
+// stages >= 2; registers hold
 // T (2R+1) V floats of x-neighbour queues per thread.  (T, BY, V) is unique
 // per radius.  The first T = 1 entry of a radius is its default untiled
 // variant (the fastest measured on GB300 where one was measured).
@@ -18,19 +20,20 @@
     X(2, 1, 8, 64, 16, 2, 2) X(2, 1, 2, 64, 12, 2, 2) X(2, 1, 2, 64, 8, 3, 3) X(2, 1, 4, 64, 16, 4, 1) \
     X(2, 2, 4, 56, 16, 1, 1) X(2, 2, 2, 56, 16, 2, 1) X(2, 2, 4, 56, 8, 2, 2) X(2, 3, 4, 56, 12, 2, 1) X(2, 4, 4, 48, 8, 1, 1)
 #define WAVE_SWEEP_VARIANTS_R3(X) \
-    X(3, 1, 2, 64, 12, 2, 2) X(3, 1, 4, 64, 16, 4, 1) X(3, 1, 8, 64, 16, 2, 2) X(3, 2, 4, 56, 16, 1, 1)
+    X(3, 1, 2, 64, 12, 2, 2) X(3, 1, 4, 64, 16, 4, 1) X(3, 1, 8, 64, 16, 2, 2) X(3, 1, 4, 64, 12, 3, 2) \
+    X(3, 2, 4, 56, 16, 1, 1)
 #define WAVE_SWEEP_VARIANTS_R4(X)                                                                  \
     X(4, 1, 4, 64, 8, 3, 3) X(4, 1, 2, 64, 12, 2, 2) X(4, 1, 2, 64, 8, 3, 3) X(4, 1, 4, 64, 16, 4, 1) \
     X(4, 1, 8, 64, 12, 3, 2) X(4, 1, 8, 32, 24, 3, 2) X(4, 2, 4, 56, 16, 1, 1) X(4, 2, 2, 48, 16, 1, 1)     \
     X(4, 2, 4, 48, 8, 2, 1)
 #define WAVE_SWEEP_VARIANTS_R5(X) \
-    X(5, 1, 2, 64, 12, 2, 2) X(5, 1, 4, 64, 12, 4, 1) X(5, 1, 8, 64, 8, 3, 2)
+    X(5, 1, 2, 64, 12, 2, 2) X(5, 1, 4, 64, 12, 3, 2) X(5, 1, 8, 64, 8, 3, 2) X(5, 1, 4, 64, 8, 3, 3)
 #define WAVE_SWEEP_VARIANTS_R6(X) \
-    X(6, 1, 2, 64, 8, 2, 2) X(6, 1, 4, 64, 12, 3, 1) X(6, 1, 8, 64, 8, 3, 2)
+    X(6, 1, 2, 64, 8, 2, 2) X(6, 1, 4, 64, 12, 3, 2) X(6, 1, 8, 64, 8, 3, 2) X(6, 1, 4, 64, 8, 3, 2)
 #define WAVE_SWEEP_VARIANTS_R7(X) \
-    X(7, 1, 2, 64, 8, 2, 2) X(7, 1, 4, 64, 8, 3, 1)
+    X(7, 1, 2, 64, 8, 2, 2) X(7, 1, 4, 64, 8, 3, 2)
 #define WAVE_SWEEP_VARIANTS_R8(X) \
-    X(8, 1, 2, 64, 8, 2, 1) X(8, 1, 4, 64, 8, 3, 1)
+    X(8, 1, 2, 64, 8, 2, 2) X(8, 1, 4, 64, 8, 3, 2)
 
 // Gradient-mode variants Y(R, T, V, BZ, BY, P, MB, XB): the untiled default
 // shape of a radius with XB extra ring-K boxes (1: E for the second-difference
@@ -50,4 +53,4 @@
 #define WAVE_MULTI_R5 5, 1, 2, 64, 12, 2, 2
 #define WAVE_MULTI_R6 6, 1, 2, 64, 8, 2, 2
 #define WAVE_MULTI_R7 7, 1, 2, 64, 8, 2, 2
-#define WAVE_MULTI_R8 8, 1, 2, 64, 8, 2, 1
+#define WAVE_MULTI_R8 8, 1, 2, 64, 8, 2, 2

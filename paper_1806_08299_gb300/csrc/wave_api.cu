@@ -290,6 +290,8 @@ struct Layout {
     float *store = nullptr;
     DevTable inj, rec, inj2;
     float *corner = nullptr;
+    int *order = nullptr;    // launch order of the sweep's blocks (order_cap entries)
+    long long order_cap = 0;
     size_t bytes = 0;
 };
 
@@ -318,6 +320,12 @@ Layout carve(void *ws, size_t cap, bool dry, const Dims &d, int op, int nsrc, in
         carve_table(c, d, ni, &L.inj);
         carve_table(c, d, nr, &L.rec);
         L.corner = c.take<float>((size_t)nt * 8 * std::max(nr, 0));
+    }
+    if (nsrc + nrec > 0) {
+        // as many blocks as the smallest compiled tile (32 x 8) with one-plane
+        // x-chunks can make
+        L.order_cap = (long long)((d.nzp + 31) / 32) * ((d.ny + 7) / 8) * d.nx;
+        L.order = c.take<int>((size_t)L.order_cap);
     }
     L.bytes = c.off;
     return L;
@@ -553,6 +561,11 @@ struct Job {
     long long l_base = 0;
     int l_dir = 1;
     float *gacc = nullptr;
+    // host copies of the injection / record tables and the device buffer for
+    // the heavy-first launch order (nullptr: natural order)
+    const HostTable *hinj = nullptr, *hrec = nullptr;
+    int *order = nullptr;
+    long long order_cap = 0;
 };
 
 // Events around the sweep launches of the last timed call on this thread.
@@ -613,6 +626,7 @@ int build_launch(const Job &job, const State &s, int j, const SweepVariant *v, i
     if (!rc) rc = encode_map(&mp->um, s.buf[s.b], d, v->W0, v->HK);
     if (!rc) rc = encode_map(&mp->B, job.cB, d, v->W0, v->HK);
     if (!rc) rc = encode_map(&mp->C, job.cC, d, v->W0, v->HK);
+    if (!rc && v->T == 1) rc = encode_map(&mp->uk, s.buf[s.a], d, v->W0, v->HK);
     if (!rc && v->XB == 1) rc = encode_map(&mp->x0, job.cE, d, v->W0, v->HK);
     if (!rc && v->XB == 2) {
         const long long row = job.l_base + (long long)job.l_dir * j;  // this step's D row
@@ -670,6 +684,73 @@ void advance_state(State &s, int T)
     }
 }
 
+long long floor_div(long long a, long long b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Mark the tiles of variant v with x-chunk `chunk` whose sweep handles a point
+// of table t: the kernel's own per-block relevance tests, on the host.  An
+// injection table (record false) concerns a block's whole layout
+// [gy0, gy0 + H0) x [gz0 + ZL, gz0 + ZR), a record table its own tile
+// [gy0 + RT, +BY) x [gz0 + A0, +BZ), over the planes [X0 - 2RT, X1 + RT + 2)
+// the block scans.  Returns whether any tile was marked.
+bool mark_heavy(const Dims &d, const SweepVariant *v, int chunk, const HostTable *t, bool record,
+                std::vector<char> &heavy)
+{
+    if (t == nullptr || t->pts.empty()) return false;
+    const int R = v->R, RT = v->R * v->T, BZ = v->BZ, BY = v->BY;
+    const int A0 = (RT + 3) / 4 * 4, H0 = BY + 2 * RT;
+    const int ZL = (A0 - (v->T - 1) * R) / 4 * 4, ZR = (A0 + BZ + (v->T - 1) * R + 3) / 4 * 4;
+    const int tz = tiles(d.nzp, BZ), ty = tiles(d.ny, BY), tx = tiles(d.nx, chunk);
+    heavy.resize((size_t)tz * ty * tx, 0);
+    const int ylo = record ? RT : 0, yhi = record ? RT + BY : H0;
+    const int zlo = record ? A0 : ZL, zhi = record ? A0 + BZ : ZR;
+    bool any = false;
+    for (int x = 0; x < d.nx; ++x) {
+        for (int e = t->plane_start[x]; e < t->plane_start[x + 1]; ++e) {
+            const long long y = t->pts[e].x, z = t->pts[e].y;
+            const long long x0 = std::max(0LL, floor_div(x - RT - 2, chunk) - 1);
+            const long long x1 = std::min<long long>(tx - 1, floor_div(x + 2 * RT, chunk));
+            const long long y0 = std::max(0LL, floor_div(y + RT - yhi, BY));
+            const long long y1 = std::min<long long>(ty - 1, floor_div(y + RT - ylo, BY));
+            const long long z0 = std::max(0LL, floor_div(z + A0 - zhi, BZ));
+            const long long z1 = std::min<long long>(tz - 1, floor_div(z + A0 - zlo, BZ));
+            for (long long txi = x0; txi <= x1; ++txi) {
+                const long long X0 = txi * chunk, X1 = std::min<long long>(X0 + chunk, d.nx);
+                if (x < X0 - 2 * RT || x >= X1 + RT + 2) continue;
+                for (long long tyi = y0; tyi <= y1; ++tyi) {
+                    const long long gy0 = tyi * BY - RT;
+                    if (y < gy0 + ylo || y >= gy0 + yhi) continue;
+                    for (long long tzi = z0; tzi <= z1; ++tzi) {
+                        const long long gz0 = tzi * BZ - A0;
+                        if (z < gz0 + zlo || z >= gz0 + zhi) continue;
+                        heavy[(size_t)(tzi + tz * (tyi + ty * txi))] = 1;
+                        any = true;
+                    }
+                }
+            }
+        }
+    }
+    return any;
+}
+
+// Launch order of the blocks of variant v with x-chunk `chunk`: the tiles
+// that handle a point of the injection or record table first, then the rest,
+// each group in natural order, so that the blocks with the extra sparse work
+// run in the first waves.  Empty when no tile is heavy.
+void heavy_first_order(const Dims &d, const SweepVariant *v, int chunk, const HostTable *inj,
+                       const HostTable *rec, std::vector<int> *order)
+{
+    order->clear();
+    std::vector<char> heavy;
+    const bool a = mark_heavy(d, v, chunk, inj, false, heavy);
+    const bool b = mark_heavy(d, v, chunk, rec, true, heavy);
+    if (!a && !b) return;
+    order->reserve(heavy.size());
+    for (size_t t = 0; t < heavy.size(); ++t)
+        if (heavy[t]) order->push_back((int)t);
+    for (size_t t = 0; t < heavy.size(); ++t)
+        if (!heavy[t]) order->push_back((int)t);
+}
+
 // Advance `st` by nsteps.  When ckpt != nullptr, state c = (u^{ck}, u^{ck-1})
 // is copied to ckpt + c * 2 * npad at every step count j0 + j that is a
 // multiple of ckpt_every (j counts from the run start, j0 = global offset).
@@ -678,6 +759,9 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
 {
     const Dims &d = job.d;
     const int R = plan.v->R;
+    const SweepVariant *ov = nullptr;  // launch shape the order buffer holds
+    int ochunk = 0;
+    bool ordered = false;
     int j = 0;
     while (j <= nsteps) {
         if (ckpt != nullptr && (j0 + j) % ckpt_every == 0 && j < nsteps) {
@@ -708,6 +792,17 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         long long nblocks = 0;
         int rc = build_launch(job, s, j, v, chunk, &a, &maps, &nblocks);
         if (rc) return rc;
+        if (job.order != nullptr && (v != ov || chunk != ochunk)) {
+            ov = v;
+            ochunk = chunk;
+            std::vector<int> ord;
+            heavy_first_order(d, v, chunk, job.hinj, job.hrec, &ord);
+            ordered = !ord.empty() && (long long)ord.size() == nblocks && nblocks <= job.order_cap;
+            if (ordered)
+                CK(cudaMemcpyAsync(job.order, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice,
+                                   stream));
+        }
+        a.order = ordered ? job.order : nullptr;
         CK(v->launch((int)nblocks, stream, a, job.st, maps));
         if (g_prof.active) {
             g_prof.launches++;
@@ -787,7 +882,10 @@ int autotune(const Dims &d, const Stencil &st, const float *cB, const float *cC,
             std::fprintf(stderr, "wave autotune: T=%d tile=%dx%d vec=%d P=%d chunk=%d: %.4f ms/step\n",
                          cands[c].v->T, cands[c].v->BZ, cands[c].v->BY, cands[c].v->V, cands[c].v->P,
                          cands[c].chunk, best[c]);
-        if (best[c] < best[bi]) bi = c;
+        // a later candidate must be clearly faster: timings within 1 % are
+        // ties, and ties keep the earlier one (the default variant and chunk
+        // come first), so run-to-run noise does not flip the plan
+        if (best[c] < 0.99f * best[bi]) bi = c;
     }
     *out = cands[bi];
     return WAVE_OK;
@@ -899,11 +997,11 @@ struct LockShot {
     long long nblocks = 0;  // blocks of one launch (the same in every phase)
 };
 
-// Table of a lockstep group: the block -> shot array, then one row of
+// Table of a lockstep group: the block -> (shot, tile) map, then one row of
 // ShotSweep records (one per shot) per phase.
 size_t lock_table_bytes(int nshots, long long total_blocks, int nphases)
 {
-    return align_up(sizeof(int) * (size_t)total_blocks) +
+    return align_up(sizeof(int2) * (size_t)total_blocks) +
            (size_t)nphases * align_up(sizeof(wt::ShotSweep) * (size_t)nshots);
 }
 
@@ -931,8 +1029,8 @@ int capture_stream(cudaStream_t *out)
 // per phase, the device copy at `dev` (uploaded before the graph runs).
 struct LockTable {
     std::vector<wt::ShotSweep> rows;
-    std::vector<int> block_shot;
-    int *dev_block_shot = nullptr;
+    std::vector<int2> block_map;  // launch block -> (shot, tile)
+    int2 *dev_block_map = nullptr;
     char *dev_rows = nullptr;
     size_t row_bytes = 0;  // one phase's records, aligned
     int nphases = 0;
@@ -953,7 +1051,7 @@ int lock_phase(std::vector<LockShot> &ls, StateOf st_of, int nsteps, const wt::M
     const size_t r0 = tab.rows.size();
     tab.rows.resize(r0 + (size_t)n);
     wt::ShotSweep *row = tab.rows.data() + r0;
-    int max_chunk_all = 0, block0 = 0;
+    int max_chunk_all = 0;
     for (int i = 0; i < n; ++i) {
         for (int p = 0; p < 2; ++p) {
             State sp = st_of(i);
@@ -963,8 +1061,6 @@ int lock_phase(std::vector<LockShot> &ls, StateOf st_of, int nsteps, const wt::M
             if (rc) return rc;
             if (nb != ls[i].nblocks) return WAVE_EINVAL;
         }
-        row[i].block0 = block0;
-        block0 += (int)ls[i].nblocks;
         max_chunk_all = std::max(max_chunk_all, ls[i].chunk);
     }
     const wt::ShotSweep *dtab = (const wt::ShotSweep *)(tab.dev_rows + (size_t)ph * tab.row_bytes);
@@ -981,7 +1077,7 @@ int lock_phase(std::vector<LockShot> &ls, StateOf st_of, int nsteps, const wt::M
                                    cudaMemcpyDeviceToDevice, stream));
             }
         }
-        CK(mv->launch(block0, smem, stream, dtab, tab.dev_block_shot, st, j & 1, j));
+        CK(mv->launch((int)tab.block_map.size(), smem, stream, dtab, tab.dev_block_map, st, j & 1, j));
     }
     if (nsteps & 1)
         for (int i = 0; i < n; ++i) advance_state(st_of(i), 1);
@@ -1165,11 +1261,22 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
             return WAVE_ENOSPACE;
         LockTable tab;
         tab.row_bytes = align_up(sizeof(wt::ShotSweep) * (size_t)n);
-        tab.dev_block_shot = (int *)table;
-        tab.dev_rows = (char *)table + align_up(sizeof(int) * (size_t)total_blocks);
+        tab.dev_block_map = (int2 *)table;
+        tab.dev_rows = (char *)table + align_up(sizeof(int2) * (size_t)total_blocks);
         tab.rows.reserve((size_t)nphases * n);
-        tab.block_shot.reserve((size_t)total_blocks);
-        for (int i = 0; i < n; ++i) tab.block_shot.insert(tab.block_shot.end(), (size_t)ls[i].nblocks, i);
+        // launch order: the tiles of every shot that handle a source or
+        // receiver point (in any phase) first, then the rest
+        tab.block_map.reserve((size_t)total_blocks);
+        std::vector<std::vector<char>> heavy(n);
+        for (int i = 0; i < n; ++i) {
+            mark_heavy(ls[i].d, v, ls[i].chunk, &ls[i].ti, false, heavy[i]);
+            mark_heavy(ls[i].d, v, ls[i].chunk, &ls[i].tr, !grad, heavy[i]);
+            heavy[i].resize((size_t)ls[i].nblocks, 0);
+        }
+        for (int pass = 1; pass >= 0; --pass)
+            for (int i = 0; i < n; ++i)
+                for (long long t = 0; t < ls[i].nblocks; ++t)
+                    if (heavy[i][(size_t)t] == pass) tab.block_map.push_back(make_int2(i, (int)t));
 
         // The time loops go into one CUDA graph, captured on the library's
         // stream and launched on `stream` after the tables are uploaded.
@@ -1195,7 +1302,7 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
         cudaGraphExec_t exec = nullptr;
         CK(cudaGraphInstantiate(&exec, cap.graph, 0));
         rc = WAVE_OK;
-        if (cudaMemcpyAsync(tab.dev_block_shot, tab.block_shot.data(), sizeof(int) * tab.block_shot.size(),
+        if (cudaMemcpyAsync(tab.dev_block_map, tab.block_map.data(), sizeof(int2) * tab.block_map.size(),
                             cudaMemcpyHostToDevice, stream) != cudaSuccess)
             rc = WAVE_ECUDA;
         for (int p = 0; p < nphases && rc == WAVE_OK; ++p)
@@ -1352,6 +1459,10 @@ int32_t wave_fwd(const wave_grid *g, const float *m, const float *damp, const wa
         job.corner = L.corner;
         job.nslot = 8 * nrec;
         job.withhold = (tuning && (tuning->flags & WAVE_TEST_WITHHOLD)) ? 1 : 0;
+        job.hinj = &ti;
+        job.hrec = &tr;
+        job.order = L.order;
+        job.order_cap = L.order_cap;
         State s;
         for (int i = 0; i < 4; ++i) s.buf[i] = L.U[i];
         if ((rc = prof_begin(tuning, stream))) return rc;
@@ -1414,6 +1525,10 @@ int32_t wave_adj(const wave_grid *g, const float *m, const float *damp, const wa
         job.nslot = 8 * nsrc;
         job.c_base = g->nt - 1;
         job.c_dir = -1;
+        job.hinj = &ti;
+        job.hrec = &tr;
+        job.order = L.order;
+        job.order_cap = L.order_cap;
         State s;
         for (int i = 0; i < 4; ++i) s.buf[i] = L.U[i];
         if ((rc = prof_begin(tuning, stream))) return rc;
@@ -1490,6 +1605,9 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
             rj.dstore = L.store;
             rj.d_base = 0;
             rj.d_dir = 1;
+            rj.hinj = &ts;
+            rj.order = L.order;
+            rj.order_cap = L.order_cap;
             if ((rc = run_steps(rj, fw, len, plan, stream))) return rc;
             // 2) adjoint over the segment, newest step first: reversed step
             //    for n = s0+len-1 .. s0 produces nu^{n+1}, injects res^n and
@@ -1509,6 +1627,9 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
             aj.l_base = len - 1;
             aj.l_dir = -1;
             aj.gacc = L.G;
+            aj.hinj = &tr;
+            aj.order = L.order;
+            aj.order_cap = L.order_cap;
             if ((rc = run_steps(aj, adj, len, plan, stream))) return rc;
         }
         if ((rc = prof_end(stream))) return rc;

@@ -36,7 +36,7 @@ struct MultiVariant {
     int R, T, V, BZ, BY, P, threads;
     size_t smem;  // shared memory without the plane_start slices
     cudaError_t (*launch)(int nblocks, size_t smem, cudaStream_t stream, const ShotSweep *shots,
-                          const int *block_shot, const Stencil &st, int parity, int step);
+                          const int2 *block_map, const Stencil &st, int parity, int step);
     const void *func;
 };
 int sweep_multi_variant_r1(const MultiVariant **out);
@@ -124,7 +124,7 @@ cudaError_t launch_sweep(int nblocks, cudaStream_t stream, const SweepArgs &a, c
 
 template <int R, int T, int V, int BZ, int BY, int P, int MB>
 cudaError_t launch_sweep_multi(int nblocks, size_t smem, cudaStream_t stream, const ShotSweep *shots,
-                               const int *block_shot, const Stencil &st, int parity, int step)
+                               const int2 *block_map, const Stencil &st, int parity, int step)
 {
     using S = SweepShape<R, T, V, BZ, BY, P, MB>;
     cudaError_t e = allow_max_dynamic_smem((const void *)sweep_multi_kernel<R, T, V, BZ, BY, P, MB>);
@@ -139,7 +139,7 @@ cudaError_t launch_sweep_multi(int nblocks, size_t smem, cudaStream_t stream, co
     cfg.stream = stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, sweep_multi_kernel<R, T, V, BZ, BY, P, MB>, shots, block_shot, st,
+    return cudaLaunchKernelEx(&cfg, sweep_multi_kernel<R, T, V, BZ, BY, P, MB>, shots, block_map, st,
                               parity, step);
 }
 
