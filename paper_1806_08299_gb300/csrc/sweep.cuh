@@ -85,6 +85,9 @@ struct Stencil {
 // Sparse points of one kind, sorted by (x, y, z).  plane_start[x] ..
 // plane_start[x+1] index `pts`; each pt = (y, z, item_begin, item_end).
 // Injection items: (source index, weight); record items: corner slot.
+// Per-plane point tables, sorted by (x, y, z), each grid point once:
+// pts = (y, z, begin, end) of its items in item (and w): the point index of
+// an injection, the corner slot of a record.
 struct PointTable {
     const int *plane_start;  // [nx + 1] or nullptr (no points)
     const int4 *pts;
@@ -422,9 +425,16 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
         if (a.inj.plane_start != nullptr) {
             const int e0 = a.inj.plane_start[cp], e1 = a.inj.plane_start[ci];
             pinj[k] = e0;
-            for (int e = e0; e < e1 && !fi; ++e) {
-                const int4 pt = a.inj.pts[e];
-                fi = pt.x >= gy0 && pt.x < gy0 + S::H0 && pt.y >= gz0 + S::ZL && pt.y < gz0 + S::ZR;
+            for (int eb = e0; eb < e1 && !fi; eb += 4) {
+                int4 pt4[4];  // four table points per round trip
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    pt4[u] = eb + u < e1 ? __ldg(a.inj.pts + eb + u) : make_int4(-(1 << 30), -(1 << 30), 0, 0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int4 pt = pt4[u];
+                    fi |= pt.x >= gy0 && pt.x < gy0 + S::H0 && pt.y >= gz0 + S::ZL && pt.y < gz0 + S::ZR;
+                }
             }
         } else {
             pinj[k] = 0;
@@ -688,13 +698,29 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
                         unsigned hits = 0u;
 #pragma unroll
                         for (int j = 0; j < V; ++j) fv[j] = 0.f;
-                        for (int e = e0; e < e1; ++e) {
-                            const int4 pt = a.inj.pts[e];
-                            if (pt.x == gy && pt.y >= gz && pt.y < gz + V) {
-                                const long long qrow = (long long)(a.q_row0 + a.q_dir * (s - 1)) * a.nq;
+                        const long long qrow = (long long)(a.q_row0 + a.q_dir * (s - 1)) * a.nq;
+                        for (int eb = e0; eb < e1; eb += 4) {
+                            int4 pt4[4];  // four table points per round trip
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+                                pt4[u] = eb + u < e1 ? __ldg(a.inj.pts + eb + u) : make_int4(-1, -1, 0, 0);
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int4 pt = pt4[u];
+                                if (pt.x != gy || pt.y < gz || pt.y >= gz + V) continue;
+                                // items two at a time: their loads overlap, the sum
+                                // keeps the ascending order
                                 float f = 0.f;
-                                for (int itm = pt.z; itm < pt.w; ++itm)
-                                    f = __fmaf_rn(a.inj.w[itm], a.q[qrow + a.inj.item[itm]], f);
+                                int itm = pt.z;
+                                for (; itm + 1 < pt.w; itm += 2) {
+                                    const int i0 = __ldg(a.inj.item + itm), i1 = __ldg(a.inj.item + itm + 1);
+                                    const float w0 = __ldg(a.inj.w + itm), w1 = __ldg(a.inj.w + itm + 1);
+                                    const float q0 = __ldg(a.q + qrow + i0), q1 = __ldg(a.q + qrow + i1);
+                                    f = __fmaf_rn(w0, q0, f);
+                                    f = __fmaf_rn(w1, q1, f);
+                                }
+                                if (itm < pt.w)
+                                    f = __fmaf_rn(__ldg(a.inj.w + itm), __ldg(a.q + qrow + __ldg(a.inj.item + itm)), f);
                                 const int jj = pt.y - gz;
 #pragma unroll
                                 for (int j = 0; j < V; ++j) fv[j] = jj == j ? f : fv[j];
@@ -730,7 +756,14 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
 #pragma unroll
                                 for (int j = 1; j < V; ++j) v = jj == j ? ((j & 1) ? un[j >> 1].y : un[j >> 1].x) : v;
                                 const long long crow = (long long)(a.c_row0 + a.c_dir * (s - 1)) * a.nslot;
-                                for (int itm = pt.z; itm < pt.w; ++itm) a.corner[crow + a.rec.item[itm]] = v;
+                                // corner slots two at a time (read-only loads ahead of the stores)
+                                int itm = pt.z;
+                                for (; itm + 1 < pt.w; itm += 2) {
+                                    const int s0 = __ldg(a.rec.item + itm), s1 = __ldg(a.rec.item + itm + 1);
+                                    a.corner[crow + s0] = v;
+                                    a.corner[crow + s1] = v;
+                                }
+                                if (itm < pt.w) a.corner[crow + __ldg(a.rec.item + itm)] = v;
                             }
                         }
                     }

@@ -275,8 +275,10 @@ int upload_table(const HostTable &h, const DevTable &t, cudaStream_t s)
     CK(cudaMemcpyAsync(t.plane_start, h.plane_start.data(), sizeof(int) * h.plane_start.size(),
                        cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(t.pts, h.pts.data(), sizeof(int4) * h.pts.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(t.item, h.item.data(), sizeof(int) * h.item.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(t.w, h.w.data(), sizeof(float) * h.w.size(), cudaMemcpyHostToDevice, s));
+    if (!h.item.empty()) {
+        CK(cudaMemcpyAsync(t.item, h.item.data(), sizeof(int) * h.item.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(t.w, h.w.data(), sizeof(float) * h.w.size(), cudaMemcpyHostToDevice, s));
+    }
     CK(cudaMemcpyAsync(t.wts, h.wts.data(), sizeof(float) * h.wts.size(), cudaMemcpyHostToDevice, s));
     return WAVE_OK;
 }
