@@ -740,7 +740,8 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
                 }
                 const bool own_pt = inner && cs >= X0 && cs < X1;
                 if (own_pt) {
-                    if (any_rec && frec[cs - pbase]) {
+                    // stages that store their level (s >= T-1) record after the sweep
+                    if (s < T - 1 && any_rec && frec[cs - pbase]) {
                         const int e0 = prec[cs - pbase], e1 = prec[cs - pbase + 1];
                         for (int eb = e0; eb < e1; eb += 4) {
                             int4 pt4[4];  // four table points per round trip
@@ -825,6 +826,33 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
                 if (++su == S::DU) su = 0;
             if (++sk == S::DK) sk = 0;
             if (++sf == S::DF) { sf = 0; pf ^= 1u; }
+        }
+    }
+
+    // Receiver corners of the stored levels (stage T: out_hi, stage T-1:
+    // out_lo), once the block's own points are written: the consumer threads
+    // share out the record entries of the block's own planes, so the few
+    // blocks holding receivers do not pay a chain of table loads per plane.
+    if (any_rec) {  // block-uniform; every consumer thread has left the loop
+        asm volatile("bar.sync 1, %0;" ::"r"(S::NT) : "memory");
+        const int k0 = X0 - pbase, k1 = X1 - pbase;  // own planes in the plane slices
+        const int E0 = prec[k0], E1 = prec[k1];      // their table entries, contiguous
+        for (int e = E0 + tid; e < E1; e += S::NT) {
+            int lo = k0, hi = k1 - 1;  // plane of entry e: last k with prec[k] <= e
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (prec[mid] <= e) lo = mid; else hi = mid - 1;
+            }
+            const int4 pt = __ldg(a.rec.pts + e);
+            if (pt.x < gy0 + S::RT || pt.x >= gy0 + S::RT + BY || pt.y < gz0 + S::A0 || pt.y >= gz0 + S::A0 + BZ)
+                continue;
+            const long long pix = (long long)(pbase + lo) * a.sx + (long long)pt.x * a.nz + pt.y;
+#pragma unroll
+            for (int st = (T > 1 ? T - 1 : 1); st <= T; ++st) {
+                const float v = (st == T ? a.out_hi : a.out_lo)[pix];  // written by this block
+                const long long crow = (long long)(a.c_row0 + a.c_dir * (st - 1)) * a.nslot;
+                for (int itm = pt.z; itm < pt.w; ++itm) a.corner[crow + __ldg(a.rec.item + itm)] = v;
+            }
         }
     }
 }
