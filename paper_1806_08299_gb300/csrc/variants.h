@@ -23,17 +23,17 @@
     X(3, 1, 2, 64, 12, 2, 2) X(3, 1, 4, 64, 16, 4, 1) X(3, 1, 8, 64, 16, 2, 2) X(3, 1, 4, 64, 12, 3, 2) \
     X(3, 2, 4, 56, 16, 1, 1)
 #define WAVE_SWEEP_VARIANTS_R4(X)                                                                  \
-    X(4, 1, 4, 64, 8, 3, 3) X(4, 1, 2, 64, 12, 2, 2) X(4, 1, 2, 64, 8, 3, 3) X(4, 1, 4, 64, 16, 4, 1) \
+    X(4, 1, 4, 64, 8, 2, 4) X(4, 1, 2, 64, 12, 2, 2) X(4, 1, 2, 64, 8, 3, 3) X(4, 1, 4, 64, 16, 4, 1) \
     X(4, 1, 8, 64, 12, 3, 2) X(4, 1, 8, 32, 24, 3, 2) X(4, 2, 4, 56, 16, 1, 1) X(4, 2, 2, 48, 16, 1, 1)     \
     X(4, 2, 4, 48, 8, 2, 1)
 #define WAVE_SWEEP_VARIANTS_R5(X) \
     X(5, 1, 2, 64, 12, 2, 2) X(5, 1, 4, 64, 12, 3, 2) X(5, 1, 8, 64, 8, 3, 2) X(5, 1, 4, 64, 8, 3, 3)
 #define WAVE_SWEEP_VARIANTS_R6(X) \
-    X(6, 1, 2, 64, 8, 2, 2) X(6, 1, 4, 64, 12, 3, 2) X(6, 1, 8, 64, 8, 3, 2) X(6, 1, 4, 64, 8, 3, 2)
+    X(6, 1, 2, 64, 8, 2, 2) X(6, 1, 4, 64, 12, 3, 2) X(6, 1, 8, 64, 8, 3, 2) X(6, 1, 4, 64, 8, 2, 3)
 #define WAVE_SWEEP_VARIANTS_R7(X) \
-    X(7, 1, 2, 64, 8, 2, 2) X(7, 1, 4, 64, 8, 3, 2)
+    X(7, 1, 2, 64, 8, 2, 2) X(7, 1, 4, 64, 8, 2, 3)
 #define WAVE_SWEEP_VARIANTS_R8(X) \
-    X(8, 1, 2, 64, 8, 2, 2) X(8, 1, 4, 64, 8, 3, 2)
+    X(8, 1, 2, 64, 8, 2, 2) X(8, 1, 4, 64, 8, 2, 3)
 
 // Gradient-mode variants Y(R, T, V, BZ, BY, P, MB, XB): the untiled default
 // shape of a radius with XB extra ring-K boxes (1: E for the second-difference
@@ -49,7 +49,7 @@
 #define WAVE_MULTI_R1 1, 1, 2, 64, 8, 3, 3
 #define WAVE_MULTI_R2 2, 1, 8, 64, 16, 2, 2
 #define WAVE_MULTI_R3 3, 1, 2, 64, 12, 2, 2
-#define WAVE_MULTI_R4 4, 1, 4, 64, 8, 3, 3
+#define WAVE_MULTI_R4 4, 1, 4, 64, 8, 2, 4
 #define WAVE_MULTI_R5 5, 1, 2, 64, 12, 2, 2
 #define WAVE_MULTI_R6 6, 1, 2, 64, 8, 2, 2
 #define WAVE_MULTI_R7 7, 1, 2, 64, 8, 2, 2

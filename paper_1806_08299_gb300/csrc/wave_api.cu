@@ -367,6 +367,7 @@ int sm_count()
 struct Plan {
     const SweepVariant *v = nullptr;
     int chunk = 0;
+    bool chunk_given = false;  // the caller's tile_x, kept for every variant of the run
 };
 
 int tiles(int n, int b) { return (n + b - 1) / b; }
@@ -785,8 +786,10 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         if (mode > 0 && v->T == 1) {
             const SweepVariant *mv = mode_variant(v, mode);
             if (mv != nullptr) {
+                // the plan's chunk was chosen for the plain variant, whose
+                // blocks per SM can differ: size the mode variant's own grid
                 v = mv;
-                chunk = std::min(chunk, max_chunk(mv));
+                chunk = std::min(plan.chunk_given ? chunk : default_chunk(d, mv), max_chunk(mv));
             }
         }
         SweepArgs a;
@@ -909,6 +912,7 @@ int resolve_plan(const Dims &d, const wave_grid *g, const wave_tuning *t, bool m
         if (v == nullptr) return WAVE_EUNSUPPORTED;
         out->v = v;
         out->chunk = (t && t->tile_x > 0) ? std::min(t->tile_x, d.nx) : default_chunk(d, v);
+        out->chunk_given = t && t->tile_x > 0;
         return WAVE_OK;
     }
     const TuneKey key = tune_key(d, g->space_order, T);
