@@ -44,6 +44,7 @@ HBM_FALLBACK_GBS = 6800.0
 TRAFFIC_SRC_SHA256 = "00db2c9942555fe24583d7012d4a8a446def5de7b842cd3cdafb0e82045aa5a5"
 TRAFFIC_BYTES = {  # ("R T V BZ BY P", chunk, n) -> bytes per launch
     ("R4 T1 V4 BZ64 BY8 P2", 64, (512, 512, 512)): 2174477312 + 519209984,
+    ("R4 T1 V4 BZ64 BY8 P2", 74, (512, 512, 512)): 2174204160 + 518409984,
 }
 
 
