@@ -261,3 +261,28 @@ def test_chunk_sizes_in_any_order(wavelib, cuda, oracle):
         d, ul = _run(wavelib, cuda, grid, m, damp, src, q, rec, 1, tile_x=tile_x)
         _, uref, _ = _oracle(oracle, grid, m, damp, src, q, rec)
         assert _relerr(ul[0], uref[0]) <= TOL
+
+
+@pytest.mark.parametrize("so,T", [(2, 1), (2, 2), (2, 4), (8, 1), (16, 1)])
+def test_dense_receiver_carpet(wavelib, cuda, oracle, so, T):
+    """A carpet of receivers: a 21 x 23 grid of off-grid points at one depth
+    plus a few more scattered points, so that one block holds hundreds of
+    record entries across its planes (more than it has threads), several
+    per plane and grid point.  Traces against the oracle, and against the
+    untiled sweep bit for bit."""
+    n = (36, 40, 44)
+    nt = 14
+    m, damp, src, q, _ = inputs.random_problem(n, so, nt, seed=7 + so + T, nsrc=2, nrec=1)
+    gx, gy = np.meshgrid(np.linspace(1.3, n[0] - 2.6, 21), np.linspace(0.7, n[1] - 3.2, 23), indexing="ij")
+    carpet = np.stack([gx.ravel(), gy.ravel(), np.full(gx.size, 3.4)], axis=1)
+    extra = np.random.default_rng(3).random((40, 3)) * (np.array(n) - 1)
+    rec = (np.concatenate([carpet, extra]) * inputs.H).astype(np.float32)
+    dt = 0.4 * wavelib.cfl_dt(so, (inputs.H,) * 3, 3.0)
+    grid = wavelib.Grid(n, (inputs.H,) * 3, dt, nt, so)
+    d, ul = _run(wavelib, cuda, grid, m, damp, src, q, rec, T, tile_x=12)
+    dref, uref, _ = _oracle(oracle, grid, m, damp, src, q, rec)
+    assert np.abs(d - dref).max() <= TOL * np.abs(dref).max()
+    assert _relerr(ul[0], uref[0]) <= TOL
+    if T > 1:
+        d1, ul1 = _run(wavelib, cuda, grid, m, damp, src, q, rec, 1)
+        assert np.array_equal(d, d1) and np.array_equal(ul, ul1)
