@@ -18,7 +18,7 @@
     X(1, 3, 4, 56, 16, 2, 1) X(1, 4, 4, 56, 16, 2, 1) X(1, 4, 4, 56, 8, 1, 2)
 #define WAVE_SWEEP_VARIANTS_R2(X)                                                                  \
     X(2, 1, 8, 64, 16, 2, 2) X(2, 1, 2, 64, 12, 2, 2) X(2, 1, 2, 64, 8, 3, 3) X(2, 1, 4, 64, 16, 4, 1) \
-    X(2, 2, 4, 56, 16, 1, 1) X(2, 2, 2, 56, 16, 2, 1) X(2, 2, 4, 56, 8, 2, 2) X(2, 3, 4, 56, 12, 2, 1) X(2, 4, 4, 48, 8, 1, 1)
+    X(2, 2, 4, 56, 16, 1, 1) X(2, 2, 2, 56, 16, 2, 1) X(2, 2, 4, 56, 8, 2, 2) X(2, 2, 4, 56, 12, 2, 2) X(2, 3, 4, 56, 12, 2, 1) X(2, 4, 4, 48, 8, 1, 1)
 #define WAVE_SWEEP_VARIANTS_R3(X) \
     X(3, 1, 2, 64, 12, 2, 2) X(3, 1, 4, 64, 16, 4, 1) X(3, 1, 8, 64, 16, 2, 2) X(3, 1, 4, 64, 12, 3, 2) \
     X(3, 2, 4, 56, 16, 1, 1)
@@ -31,9 +31,9 @@
 #define WAVE_SWEEP_VARIANTS_R6(X) \
     X(6, 1, 2, 64, 8, 2, 2) X(6, 1, 4, 64, 12, 3, 2) X(6, 1, 8, 64, 8, 3, 2) X(6, 1, 4, 64, 8, 2, 3)
 #define WAVE_SWEEP_VARIANTS_R7(X) \
-    X(7, 1, 2, 64, 8, 2, 2) X(7, 1, 4, 64, 8, 2, 3)
+    X(7, 1, 2, 64, 8, 2, 2) X(7, 1, 4, 64, 8, 2, 3) X(7, 1, 4, 64, 12, 2, 2)
 #define WAVE_SWEEP_VARIANTS_R8(X) \
-    X(8, 1, 2, 64, 8, 2, 2) X(8, 1, 4, 64, 8, 2, 3)
+    X(8, 1, 2, 64, 8, 2, 2) X(8, 1, 4, 64, 8, 2, 3) X(8, 1, 4, 64, 12, 2, 2)
 
 // Gradient-mode variants Y(R, T, V, BZ, BY, P, MB, XB): the untiled default
 // shape of a radius with XB extra ring-K boxes (1: E for the second-difference
