@@ -264,6 +264,27 @@ def _timed(fn, steps, stream):
     return e0.elapsed_time(e1), extra
 
 
+def _per_call(fn, n, stream):
+    """Device time of each of n consecutive calls (CUDA events on the stream
+    between calls): the spread behind the timed mean."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(n):
+        fn()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    return [ev[i].elapsed_time(ev[i + 1]) for i in range(n)]
+
+
+def _spread(ms_list, pts):
+    ms_sorted = sorted(ms_list)
+    med = float(np.median(ms_sorted))
+    return {"runs": len(ms_list), "min_ms": ms_sorted[0], "median_ms": med,
+            "max_gpts": pts / (ms_sorted[0] / 1e3) / 1e9, "median_gpts": pts / (med / 1e3) / 1e9}
+
+
 def run_ours(args):
     import torch
     from paper_1806_08299_gb300 import inputs, wave
@@ -348,6 +369,12 @@ def run_ours(args):
         deep_line = {"gpts": whole_job_rate(pts, args.steps, ms_d, world),
                      "plan": wave.describe_plan(grid, deep)}
 
+    # --- spread over single calls (after the timed region) -----------------
+    spread = None
+    if args.spread_runs > 0:
+        spread = {"tiled": _spread(_per_call(lambda: fwd(tiled), args.spread_runs, stream), pts),
+                  "untiled": _spread(_per_call(lambda: fwd(untiled), args.spread_runs, stream), pts)}
+
     # --- end to end through the C ABI with host buffers --------------------
     hm = torch.from_numpy(p.m).pin_memory()
     hd = torch.from_numpy(p.damp).pin_memory()
@@ -379,6 +406,9 @@ def run_ours(args):
     orders = None
     if args.orders and world == 1:
         orders = _orders_sweep(dev, inputs, wave, args)
+    laplace = None
+    if args.laplace and world == 1:
+        laplace = _laplace_sweep(dev, inputs, wave, args)
 
     # --- roofline of the sweep kernel --------------------------------------
     hbm, peak_kind = _peaks()
@@ -416,6 +446,7 @@ def run_ours(args):
                        "untiled_plan": uplan,
                        "tiled_over_untiled": value / untiled_gpts,
                        "best_time_tiled": deep_line,
+                       "per_call_spread": spread,
                        "parallelism": "replicas" if world > 1 else "single"},
             "e2e": {"value": whole_job_rate(pts, args.steps, ms_e, world), "unit": "GPts/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -429,6 +460,8 @@ def run_ours(args):
             line["fwi_survey"] = survey
         if orders is not None:
             line["orders_c3"] = orders
+        if laplace is not None:
+            line["laplace"] = laplace
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line))
@@ -555,6 +588,66 @@ def _orders_sweep(dev, inputs, wave, args):
     return out
 
 
+def _laplace_sweep(dev, inputs, wave, args):
+    """The Laplace (heat) operator of Sec. 5.7 on its 600^3 grid, 16 steps:
+    explicit Euler for u_t = lap u from a smooth seeded field, per space
+    order 2/4/8/16 the fastest untiled plan and the fastest time-tiled plan
+    (every compiled depth T >= 2, shapes autotuned), GPts/s of the sweeps
+    (best of three calls; call_gpts: whole calls, set-up included).  The sweep
+    is the wave sweep with B = 0, so it still reads level n-1 and B (20 B per
+    point-update where the operator needs 12)."""
+    import torch
+    n = (args.laplace_n,) * 3
+    nt = 16
+    h = (inputs.H,) * 3
+    rng = np.random.default_rng(7)
+    idx = [np.arange(k, dtype=np.float32) / k for k in n]
+    u0 = (np.sin(2 * np.pi * idx[0])[:, None, None] * np.cos(4 * np.pi * idx[1])[None, :, None]
+          * np.sin(6 * np.pi * idx[2])[None, None, :]).astype(np.float32)
+    u0 += np.float32(0.01) * rng.standard_normal(n).astype(np.float32)
+    tu = torch.from_numpy(u0).to(dev)
+    del u0
+    pts = float(np.prod(n)) * nt
+    stream = torch.cuda.current_stream()
+    out = {"workload": "Laplace operator (Sec. 5.7): %dx%dx%d, %d steps, explicit Euler, "
+                       "smooth seeded field" % (n + (nt,))}
+    for so in (2, 4, 8, 16):
+        c = wave.fd_coefficients(so)  # |symbol| at the Nyquist corner bounds explicit Euler
+        sig = abs(c[0] + 2 * sum(c[k] * (-1) ** k for k in range(1, len(c))))
+        lam = sum(sig / (hh * hh) for hh in h)
+        grid = wave.Grid(n, h, float(np.float32(0.4 * 2.0 / lam)), nt, so)
+        ws = torch.empty(wave.workspace_bytes(grid, wave.WAVE_OP_FWD, 0, 0), dtype=torch.uint8,
+                         device=dev)
+
+        def run(tune):
+            wave.heat(grid, tu, None, None, None, None, tuning=tune, workspace=ws)
+
+        def best_at(T):
+            t = wave.Tuning(time_tile=T, flags=wave.WAVE_AUTOTUNE_SHAPE)
+            run(t)
+            pl = wave.describe_plan(grid, t)
+            fixed = wave.Tuning(time_tile=pl["time_tile"], tile_y=pl["tile_y"], tile_x=pl["tile_x"],
+                                vec=pl["vec"], flags=wave.WAVE_TIME_SWEEPS)
+            run(fixed)
+            best = float("inf")
+            for _ in range(3):  # the sweeps alone (16 steps leave per-call set-up visible)
+                run(fixed)
+                best = min(best, wave.sweep_stats()[0])
+            ms, _ = _timed(lambda: run(fixed), 3, stream)
+            return {"gpts": pts / (best / 1e3) / 1e9, "call_gpts": 3 * pts / (ms / 1e3) / 1e9, "plan": pl}
+
+        row = {"untiled": best_at(1)}
+        depths = sorted({v["time_tile"] for v in wave.list_variants(so) if v["time_tile"] >= 2})
+        tiled = [best_at(T) for T in depths]
+        row["time_tiled"] = max(tiled, key=lambda r: r["gpts"]) if tiled else None
+        row["tiled_over_untiled"] = (row["time_tiled"]["gpts"] / row["untiled"]["gpts"]
+                                     if tiled else None)
+        out["so%d" % so] = row
+        del ws
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -570,6 +663,10 @@ def main():
     ap.add_argument("--survey-shots", type=int, default=8)
     ap.add_argument("--survey-nt", type=int, default=1500)
     ap.add_argument("--no-orders", dest="orders", action="store_false")
+    ap.add_argument("--no-laplace", dest="laplace", action="store_false")
+    ap.add_argument("--laplace-n", type=int, default=600)
+    ap.add_argument("--spread-runs", type=int, default=10,
+                    help="single calls timed one by one after the timed region (min / median)")
     ap.add_argument("--orders-nt", type=int, default=100)
     ap.add_argument("--fwi-nt", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -180,6 +180,27 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp,
                   const float *ckpt, int32_t ckpt_every, float *grad,
                   const wave_tuning *tuning, void *ws, size_t ws_bytes, void *stream);
 
+/* The heat (Laplace) operator of Sec. 5.7 through the same time-tiled sweep:
+ * explicit Euler for u_t = kappa (lap u + f),
+ *   u^{n+1} = u^n + dt kappa (L u^n + f^n),   n = 0 .. nt-1,
+ * with L the order-so Laplacian of wave_fwd (zero outside the grid) and f^n
+ * the trilinear spread of the source traces at step n.  It is the leapfrog
+ * update with B = 0 and C = dt kappa, so every tiling gives the same bits.
+ *   kappa        device [nx][ny][nz] diffusivity >= 0, or NULL for 1
+ *   u0           device [nx][ny][nz] initial field
+ *   src / src_traces, rec / rec_traces   as wave_fwd (rec_traces[n] holds
+ *                the interpolated u^{n+1})
+ *   u_out        device [nx][ny][nz] out: u^nt
+ *   tuning       as wave_fwd (NULL = autotune); WAVE_ALLOW_UNSTABLE skips the
+ *                stability check dt kappa |L| <= 2, else WAVE_EUNSTABLE is
+ *                reported through the status word
+ *   ws, ws_bytes workspace of WAVE_OP_FWD for the same points
+ * g->dt and g->nt give the step and the number of steps. */
+int32_t wave_heat(const wave_grid *g, const float *kappa, const float *u0,
+                  const wave_points *src, const float *src_traces,
+                  const wave_points *rec, float *rec_traces, float *u_out,
+                  const wave_tuning *tuning, void *ws, size_t ws_bytes, void *stream);
+
 /* Wait for `stream`, then read the device status word that kernels of the
  * last call using workspace `ws` may have set.  Returns WAVE_OK,
  * WAVE_ETIMEOUT or WAVE_ECUDA. */

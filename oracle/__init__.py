@@ -16,6 +16,10 @@ Functions and what pins them (see tests/test_oracle_*.py):
   forward_tiled        bitwise equal to forward (the paper's test)  (pinned)
   adjoint              dot-product test against forward             (pinned)
   gradient             central finite differences of the misfit    (pinned)
+  heat                 explicit Euler for the Laplace operator: exact decay
+                       of a discrete Dirichlet sine mode (so 2), one step
+                       of a quadratic exact away from the boundary, a
+                       source on a node, linearity in u0 and f    (pinned)
   forward_batched,     per-shot forward / gradient on windows of one
   gradient_batched     model, window gradients summed into the global
                        grid; pinned by whole-grid shots, shot additivity
@@ -54,6 +58,8 @@ def _load():
         lib.oracle_adjoint.restype = i
         lib.oracle_gradient.argtypes = [ip, dp, d, i, i, dp, dp, dp, i, dp, dp, i, dp, dp, dp]
         lib.oracle_gradient.restype = i
+        lib.oracle_heat.argtypes = [ip, dp, d, i, i, dp, dp, dp, i, dp, dp, i, dp, dp, dp]
+        lib.oracle_heat.restype = i
         _lib = lib
     return _lib
 
@@ -189,6 +195,26 @@ def gradient(m, damp, h, dt, nt, space_order, src_xyz, src_q, rec_xyz, res):
     if rc:
         raise RuntimeError("oracle_gradient failed (%d)" % rc)
     return g
+
+
+def heat(u0, h, dt, nt, space_order, kappa=None, src_xyz=None, src_q=None, rec_xyz=None):
+    """Explicit Euler for u_t = kappa (lap u + f) (the Laplace operator of
+    Sec. 5.7).  Returns (rec_d [nt][nrec], u^nt)."""
+    u0 = _arr(u0)
+    n = u0.shape
+    nsrc, sx = _pts(src_xyz)
+    nrec, rx = _pts(rec_xyz)
+    q = _arr(src_q, (nt, nsrc)) if nsrc else np.zeros((1,))
+    d = np.zeros((nt, max(nrec, 1)))
+    u_last = np.zeros(n)
+    c = _coeffs(space_order)
+    rc = _load().oracle_heat(
+        _ints(n), _p(_arr(h)), float(dt), int(nt), space_order // 2, _p(c),
+        _p(_arr(kappa, n)) if kappa is not None else None, _p(u0),
+        nsrc, _p(sx), _p(q), nrec, _p(rx), _p(d), _p(u_last))
+    if rc:
+        raise RuntimeError("oracle_heat failed (%d)" % rc)
+    return d[:, :nrec], u_last
 
 
 def _window(shot):

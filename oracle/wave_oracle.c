@@ -368,6 +368,50 @@ int oracle_forward(const int *n, const double *h, double dt, int nt, int r, cons
     return 0;
 }
 
+/* The Laplace (heat) operator of Sec. 5.7, explicit Euler in time:
+ *   u^{n+1} = u^n + dt kappa (L u^n + f^n)
+ * with the same Laplacian, zero halo, source spread and receiver recording
+ * (receivers read u^{n+1}) as oracle_forward.  kappa may be NULL (1). */
+int oracle_heat(const int *n, const double *h, double dt, int nt, int r, const double *c,
+                const double *kappa, const double *u0,
+                int nsrc, const double *src_xyz, const double *src_q,
+                int nrec, const double *rec_xyz, double *rec_d, double *u_last)
+{
+    long N = npts(n);
+    srcmap_t sm;
+    recmap_t rm;
+    if (srcmap_build(&sm, n, h, nsrc, src_xyz) || recmap_build(&rm, n, h, nrec, rec_xyz)) return -1;
+    double *u = (double *)calloc(N, sizeof(double));
+    double *up = (double *)calloc(N, sizeof(double));
+    double *corners = (double *)calloc((size_t)nt * 8 * (nrec > 0 ? nrec : 1), sizeof(double));
+    if (!u || !up || !corners) return -1;
+    if (u0) memcpy(u, u0, sizeof(double) * N);
+    for (int step = 0; step < nt; step++) {
+#pragma omp parallel for schedule(static)
+        for (long x = 0; x < n[0]; x++)
+            for (long y = 0; y < n[1]; y++)
+                for (long z = 0; z < n[2]; z++) {
+                    long p = at(n, x, y, z);
+                    double lap = lap_at(n, h, r, c, 0, u, x, y, z);
+                    double f = src_term(&sm, src_q, step, p);
+                    double k = kappa ? kappa[p] : 1.0;
+                    up[p] = u[p] + dt * k * (lap + f);
+                    rec_record(&rm, corners, step, p, up[p]);
+                }
+        double *t = u;
+        u = up;
+        up = t;
+    }
+    if (nrec > 0 && rec_d) rec_finish(&rm, corners, nt, rec_d);
+    if (u_last) memcpy(u_last, u, sizeof(double) * N);
+    free(u);
+    free(up);
+    free(corners);
+    srcmap_free(&sm);
+    recmap_free(&rm);
+    return 0;
+}
+
 static long lmax(long a, long b) { return a > b ? a : b; }
 static long lmin(long a, long b) { return a < b ? a : b; }
 

@@ -100,6 +100,41 @@ static int grid_for(long long n)
     return (int)b;
 }
 
+// Heat (Laplace) operator, Sec. 5.7: u^{n+1} = u^n + dt kappa (L u^n + f^n) is
+// the leapfrog update with B = 0 and C = dt kappa (kappa = 1 when null).
+// Explicit Euler is stable while dt kappa |L| <= 2: stab = dt |L| (0 skips).
+__global__ void heat_prep_kernel(const float *__restrict__ kappa, int nx, int ny, int nz, int nzp,
+                                 float dt, float stab, float *__restrict__ cB, float *__restrict__ cC,
+                                 int *status)
+{
+    const long long npad = (long long)nx * ny * nzp;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npad;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int z = (int)(p % nzp);
+        const long long xy = p / nzp;
+        float c = 0.f;
+        if (z < nz) {
+            const float k = kappa != nullptr ? kappa[xy * nz + z] : 1.f;
+            if (!(k >= 0.f) || !(k < 3.0e38f)) {
+                atomicMin(status, -1 /* WAVE_EINVAL */);
+            } else {
+                if (stab > 0.f && __fmul_rn(k, stab) > 2.f) atomicMin(status, -2 /* WAVE_EUNSTABLE */);
+                c = __fmul_rn(dt, k);
+            }
+        }
+        cB[p] = 0.f;
+        cC[p] = c;
+    }
+}
+
+cudaError_t launch_heat_prep(const float *kappa, int nx, int ny, int nz, int nzp, float dt, float stab,
+                             float *cB, float *cC, int *status, cudaStream_t s)
+{
+    heat_prep_kernel<<<grid_for((long long)nx * ny * nzp), 256, 0, s>>>(kappa, nx, ny, nz, nzp, dt, stab,
+                                                                       cB, cC, status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prep(const float *m, const float *damp, int nx, int ny, int nz, int nzp,
                         float dt, float stab_lhs, float *cB, float *cC, float *cE, int *status,
                         cudaStream_t s)

@@ -1647,6 +1647,70 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
     }
 }
 
+int32_t wave_heat(const wave_grid *g, const float *kappa, const float *u0, const wave_points *src,
+                  const float *src_traces, const wave_points *rec, float *rec_traces, float *u_out,
+                  const wave_tuning *tuning, void *ws, size_t ws_bytes, void *stream_)
+{
+    try {
+        Dims d;
+        int rc = check_grid(g, &d);
+        if (rc) return rc;
+        if (!u0 || !u_out || !ws) return WAVE_EINVAL;
+        if (check_points(src, true, src_traces) || check_points(rec, false, nullptr)) return WAVE_EINVAL;
+        if ((uintptr_t)ws % kAlign) return WAVE_EINVAL;
+        const int nsrc = npts_of(src), nrec = npts_of(rec);
+        const Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_FWD, nsrc, nrec, g->nt, 0);
+        if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
+        HostTable ti, tr;
+        if (build_table(d, g->h, src, false, &ti) || build_table(d, g->h, rec, true, &tr))
+            return WAVE_EINVAL;
+        cudaStream_t stream = (cudaStream_t)stream_;
+        const Stencil st = make_stencil(g);
+        // B = 0, C = dt kappa; stability dt kappa |L| <= 2 (|L| at the Nyquist corner)
+        const bool allow = tuning && (tuning->flags & WAVE_ALLOW_UNSTABLE);
+        double stot = 0.0;
+        for (int a = 0; a < 3; ++a) stot += symbol_at_pi(g->space_order) / ((double)g->h[a] * g->h[a]);
+        CK(cudaMemsetAsync(L.status, 0, sizeof(int) * kStatusWords, stream));
+        CK(wt::launch_heat_prep(kappa, d.nx, d.ny, d.nz, d.nzp, g->dt, allow ? 0.f : (float)(g->dt * stot),
+                                L.cB, L.cC, L.status, stream));
+        Plan plan;
+        if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, L.status, stream, &plan))) return rc;
+        // level 0 = u0; level -1 is never weighted (B = 0) but must be finite
+        // (the other two buffers are written before they are read)
+        CK(cudaMemsetAsync(L.U[1], 0, sizeof(float) * d.npad, stream));
+        CK(wt::launch_pad(u0, d.nx, d.ny, d.nz, d.nzp, L.U[0], stream));
+        if ((rc = upload_table(ti, L.inj, stream)) || (rc = upload_table(tr, L.rec, stream))) return rc;
+        Job job;
+        job.d = d;
+        job.st = st;
+        job.cB = L.cB;
+        job.cC = L.cC;
+        job.status = L.status;
+        job.cE = nullptr;
+        job.inj = L.inj.view();
+        job.q = src_traces;
+        job.nq = nsrc;
+        job.rec = L.rec.view();
+        job.corner = L.corner;
+        job.nslot = 8 * nrec;
+        job.hinj = &ti;
+        job.hrec = &tr;
+        job.order = L.order;
+        job.order_cap = L.order_cap;
+        State s;
+        for (int i = 0; i < 4; ++i) s.buf[i] = L.U[i];
+        if ((rc = prof_begin(tuning, stream))) return rc;
+        if ((rc = run_steps(job, s, g->nt, plan, stream))) return rc;
+        if ((rc = prof_end(stream))) return rc;
+        if (nrec > 0 && rec_traces != nullptr)
+            CK(wt::launch_gather(L.corner, L.rec.wts, g->nt, nrec, 1, rec_traces, stream));
+        CK(wt::launch_unpad(s.buf[s.a], d.nx, d.ny, d.nz, d.nzp, 1.f, u_out, stream));
+        return WAVE_OK;
+    } catch (...) {
+        return WAVE_EINVAL;
+    }
+}
+
 int32_t wave_status(const void *ws, void *stream_)
 {
     if (ws == nullptr) return WAVE_EINVAL;

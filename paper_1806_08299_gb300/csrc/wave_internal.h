@@ -85,6 +85,8 @@ int sweep_mode_variants_r4(const SweepVariant **out);
 cudaError_t launch_prep(const float *m, const float *damp, int nx, int ny, int nz, int nzp,
                         float dt, float stab_lhs, float *cB, float *cC, float *cE, int *status,
                         cudaStream_t s);
+cudaError_t launch_heat_prep(const float *kappa, int nx, int ny, int nz, int nzp, float dt, float stab,
+                             float *cB, float *cC, int *status, cudaStream_t s);
 cudaError_t launch_pad(const float *src, int nx, int ny, int nz, int nzp, float *dst,
                        cudaStream_t s);
 cudaError_t launch_unpad(const float *src, int nx, int ny, int nz, int nzp, float scale,

@@ -32,7 +32,7 @@ EXPORTED = ["wave_version", "wave_strerror", "wave_fd_coefficients", "wave_cfl_d
             "wave_workspace_bytes", "wave_ckpt_bytes", "wave_fwd", "wave_adj", "wave_grad",
             "wave_status", "wave_describe_plan", "wave_sweep_stats", "wave_list_variants",
             "wave_fwd_noalloc", "wave_measure_peaks", "wave_batch_workspace_bytes",
-            "wave_fwd_batched", "wave_grad_batched"]
+            "wave_fwd_batched", "wave_grad_batched", "wave_heat"]
 
 
 class WaveError(RuntimeError):
@@ -131,6 +131,8 @@ def _lib():
         lib.wave_adj.restype = i32
         lib.wave_grad.argtypes = [gp, vp, vp, pp, vp, pp, vp, vp, i32, vp, tp, vp, ctypes.c_size_t, vp]
         lib.wave_grad.restype = i32
+        lib.wave_heat.argtypes = [gp, vp, vp, pp, vp, pp, vp, vp, tp, vp, ctypes.c_size_t, vp]
+        lib.wave_heat.restype = i32
         lib.wave_status.argtypes = [vp, vp]
         lib.wave_status.restype = i32
         lib.wave_describe_plan.argtypes = [gp, tp, ctypes.POINTER(i32)]
@@ -327,6 +329,33 @@ def grad(grid, m, damp, src_xyz, src_traces, rec_xyz, rec_resid, ckpt, ckpt_ever
     del sa, ra
     _check(code, "wave_grad")
     return g_out, ws
+
+
+def heat(grid, u0, kappa=None, src_xyz=None, src_traces=None, rec_xyz=None, *, tuning=None,
+         workspace=None, stream=None):
+    """Heat (Laplace) operator, explicit Euler for u_t = kappa (lap u + f)
+    (wave_heat).  u0: initial field; kappa: diffusivity field or None for 1.
+    Returns (u^nt, rec_traces [nt][nrec], workspace)."""
+    torch = _torch()
+    n = tuple(grid.n)
+    sp, sa = _points(src_xyz)
+    rp, ra = _points(rec_xyz)
+    dev = u0.device
+    rec = torch.empty((grid.nt, rp.npts), dtype=torch.float32, device=dev)
+    u_out = torch.empty(n, dtype=torch.float32, device=dev)
+    ws = _workspace(workspace_bytes(grid, WAVE_OP_FWD, sp.npts, rp.npts), dev, workspace)
+    g = grid.c()
+    t = tuning.c() if tuning is not None else None
+    code = _lib().wave_heat(
+        ctypes.byref(g), _dev_ptr(kappa, "kappa", n) if kappa is not None else None,
+        _dev_ptr(u0, "u0", n), ctypes.byref(sp),
+        _dev_ptr(src_traces, "src_traces", (grid.nt, sp.npts)) if sp.npts else None,
+        ctypes.byref(rp), _dev_ptr(rec, "rec") if rp.npts else None, _dev_ptr(u_out, "u_out"),
+        ctypes.byref(t) if t is not None else None, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+        _stream(stream))
+    del sa, ra
+    _check(code, "wave_heat")
+    return u_out, rec, ws
 
 
 @dataclass
