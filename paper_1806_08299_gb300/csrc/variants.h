@@ -18,7 +18,8 @@
     X(1, 3, 4, 56, 16, 2, 1) X(1, 4, 4, 56, 16, 2, 1) X(1, 4, 4, 56, 8, 1, 2)
 #define WAVE_SWEEP_VARIANTS_R2(X)                                                                  \
     X(2, 1, 8, 64, 16, 2, 2) X(2, 1, 2, 64, 12, 2, 2) X(2, 1, 2, 64, 8, 3, 3) X(2, 1, 4, 64, 16, 4, 1) \
-    X(2, 2, 4, 56, 16, 1, 1) X(2, 2, 2, 56, 16, 2, 1) X(2, 2, 4, 56, 8, 2, 2) X(2, 2, 4, 56, 12, 2, 2) X(2, 3, 4, 56, 12, 2, 1) X(2, 4, 4, 48, 8, 1, 1)
+    X(2, 2, 4, 56, 16, 1, 1) X(2, 2, 2, 56, 16, 2, 1) X(2, 2, 4, 56, 8, 2, 2) X(2, 2, 4, 56, 12, 2, 2) \
+    X(2, 2, 4, 120, 14, 1, 1) X(2, 2, 4, 120, 10, 2, 1) X(2, 3, 4, 56, 12, 2, 1) X(2, 4, 4, 48, 8, 1, 1)
 #define WAVE_SWEEP_VARIANTS_R3(X) \
     X(3, 1, 2, 64, 12, 2, 2) X(3, 1, 4, 64, 16, 4, 1) X(3, 1, 8, 64, 16, 2, 2) X(3, 1, 4, 64, 12, 3, 2) \
     X(3, 2, 4, 56, 16, 1, 1)
