@@ -41,10 +41,9 @@ HBM_FALLBACK_GBS = 6800.0
 # profiles/traffic_sweep_t1_so8_512.md), valid only for the kernel sources it was
 # taken on: the SHA-256 of csrc/sweep.cuh + csrc/variants.h must match, else the
 # bench reports null.
-TRAFFIC_SRC_SHA256 = "00db2c9942555fe24583d7012d4a8a446def5de7b842cd3cdafb0e82045aa5a5"
+TRAFFIC_SRC_SHA256 = "45c1bab882f620e82af09cd2d75303c752bba70e1a82ddfb85eb56a50cc5b2f4"
 TRAFFIC_BYTES = {  # ("R T V BZ BY P", chunk, n) -> bytes per launch
-    ("R4 T1 V4 BZ64 BY8 P2", 64, (512, 512, 512)): 2174477312 + 519209984,
-    ("R4 T1 V4 BZ64 BY8 P2", 74, (512, 512, 512)): 2174204160 + 518409984,
+    ("R4 T1 V4 BZ64 BY8 P2", 74, (512, 512, 512)): 2173332224 + 518286336,
 }
 
 
