@@ -354,13 +354,13 @@ int variants_for(int R, const SweepVariant **out)
 
 int sm_count()
 {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
+    static const int n = [] {  // thread-safe one-time initialisation
+        int dev = 0, c = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-            n = 152;
-    }
+            cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0)
+            c = 152;
+        return c;
+    }();
     return n;
 }
 
@@ -1016,6 +1016,10 @@ int lock_phases(int nt, int ckpt_every)
     return ckpt_every > 0 ? 1 + 2 * ((nt + ckpt_every - 1) / ckpt_every) : 1;
 }
 
+// Held while a host thread captures on the library's capture stream: the
+// stream is shared by every thread of the process.
+std::mutex g_capture_mu;
+
 // The library's stream for capturing lockstep graphs on the current device.
 int capture_stream(cudaStream_t *out)
 {
@@ -1289,6 +1293,7 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
         cudaStream_t cs;
         int rc = capture_stream(&cs);
         if (rc) return rc;
+        std::lock_guard<std::mutex> capture_lock(g_capture_mu);  // released after `cap` ends
         Capture cap;
         if ((rc = cap.begin(cs))) return rc;
         auto fwd_state = [&](int i) -> State & { return ls[i].s; };
