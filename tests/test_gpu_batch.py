@@ -163,6 +163,47 @@ def test_lockstep_reused_workspace_and_side_stream(wavelib, cuda):
         assert torch.equal(x, y)
 
 
+def test_lockstep_from_two_host_threads(wavelib, cuda):
+    """Two host threads run batched surveys at the same time, each on its own
+    stream and workspace (the library's graph capture is shared): both equal
+    the same calls made one after the other."""
+    import threading
+    import torch
+    so, nt = 8, 9
+    grid, h, dt, m, damp, shots, q = _survey(wavelib, so, nt, seed=11)
+    tm, td = _t(m, cuda), _t(damp, cuda)
+    qa = [_t(x, cuda) for x in q]
+    qb = [3.0 * x for x in qa]
+    want_a, _ = wavelib.fwd_batched(grid, shots, tm, td, qa, concurrency=2)
+    want_b, _ = wavelib.fwd_batched(grid, shots, tm, td, qb, concurrency=3)
+    torch.cuda.synchronize()
+    got, errors = {}, []
+
+    def run(name, qq, conc):
+        try:
+            st = torch.cuda.Stream()
+            st.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(st):
+                for _ in range(3):
+                    r, ws = wavelib.fwd_batched(grid, shots, tm, td, qq, concurrency=conc, stream=st)
+            st.synchronize()
+            assert wavelib.status(ws) == wavelib.WAVE_OK
+            got[name] = r
+        except Exception as e:  # reported on the main thread
+            errors.append(e)
+
+    th = [threading.Thread(target=run, args=("a", qa, 2)), threading.Thread(target=run, args=("b", qb, 3))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors, errors
+    for x, y in zip(got["a"], want_a):
+        assert torch.equal(x, y)
+    for x, y in zip(got["b"], want_b):
+        assert torch.equal(x, y)
+
+
 def test_batch_refuses_window_outside_grid(wavelib, cuda):
     import torch
     grid = wavelib.Grid((20, 20, 20), (inputs.H,) * 3, 1e-4, 4, 4)
