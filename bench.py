@@ -323,7 +323,7 @@ def run_ours(args):
         fwd(tune)
         pl = wave.describe_plan(grid, tune)
         return wave.Tuning(time_tile=pl["time_tile"], tile_y=pl["tile_y"], tile_x=pl["tile_x"],
-                           vec=pl["vec"])
+                           vec=pl["vec"], tile_z=pl["tile_z"])
     if args.time_tile:
         tiled = tuned(wave.Tuning(time_tile=args.time_tile, flags=wave.WAVE_AUTOTUNE_SHAPE))
     else:
@@ -334,7 +334,8 @@ def run_ours(args):
         deep = tuned(wave.Tuning(time_tile=2, flags=wave.WAVE_AUTOTUNE_SHAPE))
     plan = wave.describe_plan(grid, tiled)
     uplan = wave.describe_plan(grid, untiled)
-    prof = wave.Tuning(tiled.time_tile, tiled.tile_y, tiled.tile_x, wave.WAVE_TIME_SWEEPS, tiled.vec)
+    prof = wave.Tuning(tiled.time_tile, tiled.tile_y, tiled.tile_x, wave.WAVE_TIME_SWEEPS, tiled.vec,
+                       tiled.tile_z)
 
     # --- device-timed, inputs resident: tiled sweep (headline) -------------
     for _ in range(args.warmup):
@@ -566,7 +567,7 @@ def _orders_sweep(dev, inputs, wave, args):
             fwd(t)
             pl = wave.describe_plan(grid, t)
             fixed = wave.Tuning(time_tile=pl["time_tile"], tile_y=pl["tile_y"], tile_x=pl["tile_x"],
-                                vec=pl["vec"])
+                                vec=pl["vec"], tile_z=pl["tile_z"])
             fwd(fixed)
             ms, _ = _timed(lambda: fwd(fixed), 1, stream)
             g = pts / (ms / 1e3) / 1e9
@@ -626,7 +627,7 @@ def _laplace_sweep(dev, inputs, wave, args):
             run(t)
             pl = wave.describe_plan(grid, t)
             fixed = wave.Tuning(time_tile=pl["time_tile"], tile_y=pl["tile_y"], tile_x=pl["tile_x"],
-                                vec=pl["vec"], flags=wave.WAVE_TIME_SWEEPS)
+                                vec=pl["vec"], flags=wave.WAVE_TIME_SWEEPS, tile_z=pl["tile_z"])
             run(fixed)
             best = float("inf")
             for _ in range(3):  # the sweeps alone (16 steps leave per-call set-up visible)

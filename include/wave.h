@@ -95,13 +95,16 @@ typedef struct wave_points {
  *   tile_y    : output rows per block (0 = any compiled variant).
  *   tile_x    : x-chunk length streamed by one block (0 = default).
  *   vec       : z points per thread, 2, 4 or 8 (0 = any compiled variant).
- *   flags     : WAVE_ALLOW_UNSTABLE | WAVE_TIME_SWEEPS | WAVE_AUTOTUNE_SHAPE. */
+ *   flags     : WAVE_ALLOW_UNSTABLE | WAVE_TIME_SWEEPS | WAVE_AUTOTUNE_SHAPE.
+ *   tile_z    : output columns per block (0 = the first compiled variant
+ *               matching the other fields). */
 typedef struct wave_tuning {
     int32_t time_tile;
     int32_t tile_y;
     int32_t tile_x;
     int32_t vec;
     int32_t flags;
+    int32_t tile_z;
 } wave_tuning;
 
 /* Library version (major*10000 + minor*100 + patch). */

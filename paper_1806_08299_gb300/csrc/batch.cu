@@ -159,6 +159,7 @@ wave_tuning batch_tuning(const wave_tuning *t)
         u.tile_y = 0;
         u.tile_x = 0;
         u.vec = 0;
+        u.tile_z = 0;
     }
     u.flags &= ~(WAVE_TIME_SWEEPS | WAVE_AUTOTUNE_SHAPE);
     return u;

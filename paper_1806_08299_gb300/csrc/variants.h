@@ -8,8 +8,8 @@
 // level n-1 and coefficients; T = 1: 1+P iterations of the centre plane,
 // the x-queue plane, level n-1 and coefficients) and the centre planes of
 // stages >= 2; registers hold
-// T (2R+1) V floats of x-neighbour queues per thread.  (T, BY, V) is unique
-// per radius.  The first T = 1 entry of a radius is its default untiled
+// T (2R+1) V floats of x-neighbour queues per thread.  (T, BY, V, BZ) is
+// unique per radius.  The first T = 1 entry of a radius is its default untiled
 // variant (the fastest measured on GB300 where one was measured).
 #pragma once
 
@@ -19,7 +19,7 @@
 #define WAVE_SWEEP_VARIANTS_R2(X)                                                                  \
     X(2, 1, 8, 64, 16, 2, 2) X(2, 1, 2, 64, 12, 2, 2) X(2, 1, 2, 64, 8, 3, 3) X(2, 1, 4, 64, 16, 4, 1) \
     X(2, 2, 4, 56, 16, 1, 1) X(2, 2, 2, 56, 16, 2, 1) X(2, 2, 4, 56, 8, 2, 2) X(2, 2, 4, 56, 12, 2, 2) \
-    X(2, 2, 4, 120, 14, 1, 1) X(2, 2, 4, 120, 10, 2, 1) X(2, 3, 4, 56, 12, 2, 1) X(2, 4, 4, 48, 8, 1, 1)
+    X(2, 2, 4, 120, 14, 1, 1) X(2, 2, 4, 120, 10, 2, 1) X(2, 2, 4, 128, 12, 1, 1) X(2, 3, 4, 56, 12, 2, 1) X(2, 4, 4, 48, 8, 1, 1)
 #define WAVE_SWEEP_VARIANTS_R3(X) \
     X(3, 1, 2, 64, 12, 2, 2) X(3, 1, 4, 64, 16, 4, 1) X(3, 1, 8, 64, 16, 2, 2) X(3, 1, 4, 64, 12, 3, 2) \
     X(3, 2, 4, 56, 16, 1, 1)

@@ -452,12 +452,15 @@ const SweepVariant *mode_variant(const SweepVariant *v, int mode)
 }
 
 // Pick the variant for radius R with time tile T (and tile_y / vec if given).
-const SweepVariant *find_variant(int R, int T, int tile_y, int vec)
+// The first compiled variant of radius R and depth T with the given shape
+// (0 = any value of that field).
+const SweepVariant *find_variant(int R, int T, int tile_y, int vec, int tile_z = 0)
 {
     const SweepVariant *vs;
     const int nv = variants_for(R, &vs);
     for (int i = 0; i < nv; ++i)
-        if (vs[i].T == T && (tile_y == 0 || vs[i].BY == tile_y) && (vec == 0 || vs[i].V == vec))
+        if (vs[i].T == T && (tile_y == 0 || vs[i].BY == tile_y) && (vec == 0 || vs[i].V == vec) &&
+            (tile_z == 0 || vs[i].BZ == tile_z))
             return &vs[i];
     return nullptr;
 }
@@ -490,10 +493,9 @@ bool tune_log()
 }
 
 // Optional plan cache file (env WAVE_TUNE_CACHE = path): one plan per line,
-//   nx ny nz space_order T_requested  ->  T tile_y vec chunk
+//   nx ny nz space_order T_requested  ->  T tile_y vec chunk [tile_z]
 // Lines naming variants that are not compiled in, or of another format, are
-// ignored.
-const SweepVariant *find_variant(int R, int T, int tile_y, int vec);
+// ignored; a line without tile_z takes the first variant of that shape.
 
 bool cache_lookup_file(const TuneKey &k, Plan *out)
 {
@@ -501,15 +503,16 @@ bool cache_lookup_file(const TuneKey &k, Plan *out)
     if (path == nullptr || !path[0]) return false;
     FILE *f = std::fopen(path, "r");
     if (f == nullptr) return false;
-    int nx, ny, nz, so, tr, T, by, vec, chunk;
+    int nx, ny, nz, so, tr, T, by, vec, chunk, bz;
     bool found = false;
     char line[256];
     while (std::fgets(line, sizeof(line), f) != nullptr) {
-        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d", &nx, &ny, &nz, &so, &tr, &T, &by, &vec,
-                        &chunk) != 9)
-            continue;
+        bz = 0;
+        const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d", &nx, &ny, &nz, &so, &tr, &T, &by,
+                                    &vec, &chunk, &bz);
+        if (got != 9 && got != 10) continue;
         if (nx == k.nx && ny == k.ny && nz == k.nz && so == k.so && tr == k.T) {
-            const SweepVariant *v = find_variant(so / 2, T, by, vec);
+            const SweepVariant *v = find_variant(so / 2, T, by, vec, bz);
             if (v != nullptr && chunk > 0) {
                 out->v = v;
                 out->chunk = chunk;
@@ -527,8 +530,8 @@ void cache_store_file(const TuneKey &k, const Plan &p)
     if (path == nullptr || !path[0]) return;
     FILE *f = std::fopen(path, "a");
     if (f == nullptr) return;
-    std::fprintf(f, "%d %d %d %d %d %d %d %d %d\n", k.nx, k.ny, k.nz, k.so, k.T, p.v->T, p.v->BY,
-                 p.v->V, p.chunk);
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d\n", k.nx, k.ny, k.nz, k.so, k.T, p.v->T, p.v->BY,
+                 p.v->V, p.chunk, p.v->BZ);
     std::fclose(f);
 }
 
@@ -908,7 +911,7 @@ int resolve_plan(const Dims &d, const wave_grid *g, const wave_tuning *t, bool m
     const bool shape_tune = T > 0 && t && (t->flags & WAVE_AUTOTUNE_SHAPE);
     if (shape_tune && fallback_variant(R, T) == nullptr) return WAVE_EUNSUPPORTED;
     if (T > 0 && !shape_tune) {
-        const SweepVariant *v = find_variant(R, T, t ? t->tile_y : 0, t ? t->vec : 0);
+        const SweepVariant *v = find_variant(R, T, t ? t->tile_y : 0, t ? t->vec : 0, t ? t->tile_z : 0);
         if (v == nullptr) return WAVE_EUNSUPPORTED;
         out->v = v;
         out->chunk = (t && t->tile_x > 0) ? std::min(t->tile_x, d.nx) : default_chunk(d, v);
@@ -1216,7 +1219,7 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
         const MultiVariant *mv = multi_variant(R);
         if (mv == nullptr) return WAVE_EUNSUPPORTED;
         const int tile_y = tuning ? tuning->tile_y : 0, vec = tuning ? tuning->vec : 0;
-        const SweepVariant *v = find_variant(R, 1, tile_y, vec);
+        const SweepVariant *v = find_variant(R, 1, tile_y, vec, tuning ? tuning->tile_z : 0);
         if (tuning == nullptr || tuning->time_tile != 1 || v == nullptr || v->T != mv->T || v->V != mv->V ||
             v->BZ != mv->BZ || v->BY != mv->BY || v->P != mv->P)
             return WAVE_EUNSUPPORTED;
@@ -1333,7 +1336,7 @@ bool lockstep_supported(const wave_grid *G, const wave_tuning *tuning)
     if (G == nullptr || tuning == nullptr || tuning->time_tile != 1) return false;
     const int R = G->space_order / 2;
     const MultiVariant *mv = multi_variant(R);
-    const SweepVariant *v = find_variant(R, 1, tuning->tile_y, tuning->vec);
+    const SweepVariant *v = find_variant(R, 1, tuning->tile_y, tuning->vec, tuning->tile_z);
     return mv != nullptr && v != nullptr && v->V == mv->V && v->BZ == mv->BZ && v->BY == mv->BY &&
            v->P == mv->P;
 }

@@ -26,18 +26,19 @@ def main():
     ap.add_argument("--time-tile", type=int, default=0, help="0 = every compiled variant")
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--vec", type=int, default=0)
+    ap.add_argument("--tile-z", type=int, default=0)
     ap.add_argument("--tile-x", type=int, default=0, help="x-chunk (0 = default)")
     args = ap.parse_args()
     p = inputs.c2(nt=args.nt, n=(args.n,) * 3)
     grid = wave.Grid(p.n, p.h, p.dt, p.nt, args.so)
     tm, td, tq = (torch.from_numpy(a).cuda() for a in (p.m, p.damp, p.src_q))
     if args.time_tile:
-        cands = [dict(time_tile=args.time_tile, tile_y=args.tile_y, vec=args.vec)]
+        cands = [dict(time_tile=args.time_tile, tile_y=args.tile_y, vec=args.vec, tile_z=args.tile_z)]
     else:
         cands = wave.list_variants(args.so)
     for v in cands:
         tune = wave.Tuning(time_tile=v["time_tile"], tile_y=v["tile_y"], vec=v["vec"],
-                           tile_x=args.tile_x, flags=wave.WAVE_TIME_SWEEPS)
+                           tile_x=args.tile_x, flags=wave.WAVE_TIME_SWEEPS, tile_z=v.get("tile_z", 0))
         best = float("inf")
         for _ in range(args.reps):
             _, _, _, ws = wave.fwd(grid, tm, td, p.src_xyz, tq, p.rec_xyz, tuning=tune)

@@ -57,7 +57,8 @@ class _Shot(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("time_tile", ctypes.c_int32), ("tile_y", ctypes.c_int32),
-                ("tile_x", ctypes.c_int32), ("vec", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("tile_x", ctypes.c_int32), ("vec", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("tile_z", ctypes.c_int32)]
 
 
 @dataclass
@@ -82,16 +83,18 @@ class Grid:
 @dataclass
 class Tuning:
     """time_tile: 0 autotune, 1 untiled, T >= 2 time-tile depth; tile_y, vec
-    (z points per thread) and tile_x pick a compiled variant and x-chunk."""
+    (z points per thread) and tile_z pick a compiled variant, tile_x its
+    x-chunk."""
     time_tile: int = 0
     tile_y: int = 0
     tile_x: int = 0
     flags: int = 0
     vec: int = 0
+    tile_z: int = 0
 
     def c(self):
         return _Tuning(int(self.time_tile), int(self.tile_y), int(self.tile_x), int(self.vec),
-                       int(self.flags))
+                       int(self.flags), int(self.tile_z))
 
 
 _LIB = None

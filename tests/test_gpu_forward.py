@@ -222,7 +222,7 @@ def test_every_compiled_variant(wavelib, cuda, oracle, so):
         import torch
         dv, uv, _, ws = wavelib.fwd(grid, _t(m, cuda), _t(damp, cuda), src, _t(q, cuda), rec,
                                     tuning=wavelib.Tuning(time_tile=v["time_tile"], tile_y=v["tile_y"],
-                                                          vec=v["vec"]),
+                                                          vec=v["vec"], tile_z=v["tile_z"]),
                                     want_u_last=True)
         assert wavelib.status(ws) == 0
         torch.cuda.synchronize()
