@@ -39,20 +39,27 @@ HBM_FALLBACK_GBS = 6800.0
 # DRAM traffic of one launch of the bench's sweep at full size
 # (dram__bytes_read.sum + dram__bytes_write.sum from one single-pass ncu capture;
 # profiles/traffic_sweep_t1_so8_512.md), valid only for the kernel sources it was
-# taken on: the SHA-256 of csrc/sweep.cuh + csrc/variants.h must match, else the
-# bench reports null.
-TRAFFIC_SRC_SHA256 = "45c1bab882f620e82af09cd2d75303c752bba70e1a82ddfb85eb56a50cc5b2f4"
+# taken on: the SHA-256 of csrc/sweep.cuh + the radius-4 variant list must match,
+# else the bench reports null.
+TRAFFIC_SRC_SHA256 = "37d44d9d9a35ac45b636cf5dd5e1819d3356df6966f44508c1998b5922a555b9"
 TRAFFIC_BYTES = {  # ("R T V BZ BY P", chunk, n) -> bytes per launch
     ("R4 T1 V4 BZ64 BY8 P2", 74, (512, 512, 512)): 2173332224 + 518286336,
 }
 
 
 def _kernel_sha256():
+    """SHA-256 of what the bench kernel is built from: csrc/sweep.cuh and the
+    radius-4 variant list of csrc/variants.h (other radii do not change it)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("sweep.cuh", "variants.h"):
-        with open(os.path.join(ROOT, "paper_1806_08299_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_1806_08299_gb300", "csrc")
+    with open(os.path.join(csrc, "sweep.cuh"), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(csrc, "variants.h"), "r") as fh:
+        text = fh.read()
+    a = text.index("#define WAVE_SWEEP_VARIANTS_R4(")
+    b = text.index("#define", a + 1)
+    h.update(text[a:b].encode())
     return h.hexdigest()
 
 
