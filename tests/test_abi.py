@@ -74,3 +74,37 @@ def test_strerror(wavelib):
     lib = wavelib._lib()
     for code in (0, -1, -2, -3, -4, -5, -6, -99):
         assert isinstance(lib.wave_strerror(code), bytes)
+
+
+def test_binding_structs_match_header_layout(wavelib, tmp_path):
+    """The ctypes structs of the binding have the header's field names, sizes
+    and offsets: a small C program compiled against include/wave.h prints
+    them (gcc, host only)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = {"wave_grid": wavelib._Grid, "wave_points": wavelib._Points,
+               "wave_tuning": wavelib._Tuning, "wave_shot": wavelib._Shot}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "wave.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", INCLUDE, str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                        text=True).stdout.splitlines())
+    for cname, cls in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert int(got["%s.%s" % (cname, fname)]) == getattr(cls, fname).offset, (cname, fname)
+        # and the header declares no field the binding lacks
+        body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (cname, cname),
+                         open(os.path.join(INCLUDE, "wave.h")).read(), flags=re.S).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        declared = re.findall(r"\b([a-z_][a-z0-9_]*)\s*(?:\[\d+\])?\s*;", body)
+        assert declared == [f for f, _ in cls._fields_], (cname, declared)
