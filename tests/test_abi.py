@@ -108,3 +108,27 @@ def test_binding_structs_match_header_layout(wavelib, tmp_path):
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
         declared = re.findall(r"\b([a-z_][a-z0-9_]*)\s*(?:\[\d+\])?\s*;", body)
         assert declared == [f for f, _ in cls._fields_], (cname, declared)
+
+
+def test_tile_z_and_plan_cache_file_without_gpu(wavelib, tmp_path, monkeypatch):
+    """tile_z picks among compiled shapes that differ only in z-width, and the
+    plan cache file keeps it (a line without it takes the first such shape);
+    plan queries need no GPU."""
+    g = wavelib.Grid((200, 180, 512), (0.01,) * 3, 1e-4, 10, 4)
+    first = wavelib.describe_plan(g, wavelib.Tuning(time_tile=2, tile_y=12, vec=4))
+    wide = wavelib.describe_plan(g, wavelib.Tuning(time_tile=2, tile_y=12, vec=4, tile_z=128, tile_x=77))
+    assert (first["tile_z"], wide["tile_z"], wide["tile_x"]) == (56, 128, 77)
+    with pytest.raises(wavelib.WaveError):
+        wavelib.describe_plan(g, wavelib.Tuning(time_tile=2, tile_y=12, vec=4, tile_z=72))
+    cache = tmp_path / "plans.txt"
+    # nx ny nz so T_requested -> T tile_y vec chunk [tile_z]
+    cache.write_text("201 181 513 4 0 2 12 4 96 128\n"
+                     "202 182 514 4 0 2 12 4 64\n"
+                     "this line is ignored\n")
+    monkeypatch.setenv("WAVE_TUNE_CACHE", str(cache))
+    a = wavelib.describe_plan(wavelib.Grid((201, 181, 513), (0.01,) * 3, 1e-4, 10, 4),
+                              wavelib.Tuning(time_tile=0))
+    b = wavelib.describe_plan(wavelib.Grid((202, 182, 514), (0.01,) * 3, 1e-4, 10, 4),
+                              wavelib.Tuning(time_tile=0))
+    assert (a["time_tile"], a["tile_y"], a["tile_x"], a["tile_z"]) == (2, 12, 96, 128)
+    assert (b["time_tile"], b["tile_y"], b["tile_x"], b["tile_z"]) == (2, 12, 64, 56)
