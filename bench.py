@@ -270,6 +270,16 @@ def _timed(fn, steps, stream):
     return e0.elapsed_time(e1), extra
 
 
+def _model_line(space_order, plan):
+    """Traffic model of the plan's shape: DRAM and L2 -> shared-memory bytes
+    per point-update (paper_1806_08299_gb300.traffic_model)."""
+    from paper_1806_08299_gb300 import traffic_model as tm
+    shape = tm.Shape(R=space_order // 2, T=plan["time_tile"], V=plan["vec"], BZ=plan["tile_z"],
+                     BY=plan["tile_y"])
+    return {"dram_bytes_per_point": tm.dram_bytes_per_update(plan["time_tile"]),
+            "l2_bytes_per_point": tm.l2_bytes_per_update(shape)}
+
+
 def _per_call(fn, n, stream):
     """Device time of each of n consecutive calls (CUDA events on the stream
     between calls): the spread behind the timed mean."""
@@ -435,7 +445,8 @@ def run_ours(args):
                 "alu": {"fp32_tflops_measured": fp32_tflops, "flops_per_point": flops_per_pt,
                         "roof_gpts": fp32_tflops * 1e3 / flops_per_pt,
                         "hbm_roof_gpts": hbm / bytes_per_pt},
-                "smem_tbs_measured": smem_tbs}
+                "smem_tbs_measured": smem_tbs,
+                "model": _model_line(p.space_order, plan)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -1,0 +1,34 @@
+"""The host-side traffic model (paper_1806_08299_gb300/traffic_model.py):
+closed forms of its DRAM figures and of the TMA box bytes of a shape."""
+import pytest
+
+from paper_1806_08299_gb300 import traffic_model as tm
+
+
+def test_dram_bytes_closed_forms():
+    assert tm.dram_bytes_per_update(1) == 20.0
+    assert tm.dram_bytes_per_update(2) == 12.0
+    assert tm.dram_bytes_per_update(4) == 6.0
+    assert tm.dram_bytes_per_update(1, "recompute") == 28.0
+    assert tm.dram_bytes_per_update(1, "imaging") == 32.0
+    with pytest.raises(ValueError):
+        tm.dram_bytes_per_update(2, "imaging")
+    assert tm.roof_gpts(20.0, 6696.2) == pytest.approx(334.81)
+
+
+def test_l2_bytes_of_the_default_so8_shape():
+    # 64x8 tile, R = 4: centre box 80 x 16, K boxes 72 x 8, no ring U (split)
+    s = tm.Shape(R=4, T=1, V=4, BZ=64, BY=8)
+    assert (s.PW, s.H0, s.W0, s.HK, s.split) == (80, 16, 72, 8, True)
+    per_plane = 4 * 80 * 16 + 4 * (4 * 72 * 8)
+    assert tm.l2_bytes_per_update(s) == per_plane / (64 * 8)
+
+
+def test_l2_bytes_fall_with_tile_size_and_depth_shares_the_load():
+    small = tm.l2_bytes_per_update(tm.Shape(R=2, T=2, V=4, BZ=56, BY=12))
+    wide = tm.l2_bytes_per_update(tm.Shape(R=2, T=2, V=4, BZ=120, BY=14))
+    assert wide < small
+    # a ring-U shape (R <= 2) loads its centre box once per plane, no separate feed box
+    s = tm.Shape(R=2, T=1, V=8, BZ=64, BY=16)
+    assert not s.split
+    assert tm.l2_bytes_per_update(s) == (4 * s.PW * s.H0 + 3 * 4 * s.W0 * s.HK) / (64 * 16)
