@@ -97,7 +97,12 @@ typedef struct wave_points {
  *   vec       : z points per thread, 2, 4 or 8 (0 = any compiled variant).
  *   flags     : WAVE_ALLOW_UNSTABLE | WAVE_TIME_SWEEPS | WAVE_AUTOTUNE_SHAPE.
  *   tile_z    : output columns per block (0 = the first compiled variant
- *               matching the other fields). */
+ *               matching the other fields).
+ *   kernel    : sweep kernel family (0 = any): WAVE_KERNEL_SHARED, every time
+ *               step of a tile on the same warps; WAVE_KERNEL_STAGED, each
+ *               time step of a tile on its own warps (T = 1 or 2).  All
+ *               families and shapes give bitwise the same results.
+ *   rows      : output rows per thread (0 = any; the shared family has 1). */
 typedef struct wave_tuning {
     int32_t time_tile;
     int32_t tile_y;
@@ -105,7 +110,12 @@ typedef struct wave_tuning {
     int32_t vec;
     int32_t flags;
     int32_t tile_z;
+    int32_t kernel;
+    int32_t rows;
 } wave_tuning;
+
+#define WAVE_KERNEL_SHARED 1 /* wave_tuning.kernel: stages of a time tile share warps */
+#define WAVE_KERNEL_STAGED 2 /* wave_tuning.kernel: one group of warps per stage      */
 
 /* Library version (major*10000 + minor*100 + patch). */
 int32_t wave_version(void);
@@ -219,16 +229,17 @@ int32_t wave_status(const void *ws, void *stream);
 int32_t wave_sweep_stats(float *ms, int32_t *launches, int32_t *steps);
 
 /* Compiled sweep variants for `space_order`: writes up to `max` records of
- * six int32 each to out (HOST) -- time_tile, tile_y, tile_z, vec, TMA
- * prefetch distance, threads per block -- and returns the number of variants
- * (negative WAVE_EINVAL on bad arguments). */
+ * eight int32 each to out (HOST) -- time_tile, tile_y, tile_z, vec, TMA
+ * prefetch distance, threads per block, kernel family (WAVE_KERNEL_*), rows
+ * per thread -- and returns the number of variants (negative WAVE_EINVAL on
+ * bad arguments). */
 int32_t wave_list_variants(int32_t space_order, int32_t *out, int32_t max);
 
 /* Sweep variant the library would run for grid g with `tuning` (the cached
  * autotuned plan when tuning->time_tile == 0 and the autotuner already ran
- * for this shape, otherwise the untiled default): out[0..5] = time_tile,
- * tile_y, tile_x, tile_z, vec, TMA prefetch distance.  Returns WAVE_OK or a
- * WAVE_E* code. */
+ * for this shape, otherwise the untiled default): out[0..7] = time_tile,
+ * tile_y, tile_x, tile_z, vec, TMA prefetch distance, kernel family
+ * (WAVE_KERNEL_*), rows per thread.  Returns WAVE_OK or a WAVE_E* code. */
 int32_t wave_describe_plan(const wave_grid *g, const wave_tuning *tuning, int32_t *out);
 
 /* ------------------------------------------------------------------------
@@ -302,11 +313,17 @@ int32_t wave_grad_batched(const wave_grid *g, int32_t nshots, const wave_shot *s
  * Arguments and results as wave_fwd (same kernels, same plan for the same
  * tuning), without checkpoints.  `status` (HOST) may be NULL: then the call
  * returns once the work is queued on `stream`; otherwise it waits for
- * `stream` and stores the device status word there (as wave_status).
+ * `stream` and stores the device status word there (the value wave_status
+ * would return).  If that wait or the read of the word fails, the call returns
+ * WAVE_ECUDA and leaves *status unchanged, so *status never holds a host-side
+ * error.
  *
- * Set-up: the first call on each device, with that device current, takes the
- * array's address (cudaGetSymbolAddress) and keeps it; make that first call
- * before any stream capture on that device.
+ * Set-up: the first call in each CUDA context (normally the primary context
+ * of each device), with that context current, takes the array's address
+ * (cudaGetSymbolAddress) and keeps it, keyed by the driver's unique context
+ * id.  A context created later for the same device (for example after
+ * cudaDeviceReset) is set up again by its own first call.  Make each
+ * context's first call before any stream capture in it.
  *
  * Sharing: every call on a device uses the same array.  Each call clears, in
  * stream order before its first kernel, what must start at zero (the status

@@ -32,23 +32,28 @@ __global__ void __launch_bounds__(kThreads) fma2_kernel(int iters, float2 a, flo
     if (s.x == 12345.f && s.y == -12345.f) g_peak_sink[0] = s.x;
 }
 
-// Conflict-free 16-byte shared loads: thread t reads float4 t + 256 k; the
-// loads are volatile so none is hoisted out of the loop.
+// Conflict-free 16-byte shared loads: in iteration n, load k of thread t
+// reads float4 t + 256 ((4n + k) mod 8).  The address changes with n, so the
+// compiler cannot keep a loaded value across iterations (with a fixed address
+// every load is loop-invariant and may be hoisted, which would time the adds
+// instead of the loads).
 __global__ void __launch_bounds__(kThreads) lds_kernel(int iters)
 {
-    __shared__ float4 buf[4 * kThreads];
-    for (int k = 0; k < 4; ++k)
+    __shared__ float4 buf[8 * kThreads];
+    for (int k = 0; k < 8; ++k)
         buf[threadIdx.x + kThreads * k] = make_float4(threadIdx.x, k, 1.f, 2.f);
     __syncthreads();
     const uint32_t base = (uint32_t)__cvta_generic_to_shared(buf + threadIdx.x);
     float2 lo = make_float2(0.f, 0.f), hi = lo;
     for (int n = 0; n < iters; ++n) {
+        const uint32_t half = (uint32_t)(n & 1) * (16u * kThreads * 4);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             float4 v;
-            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+            asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                          : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                         : "r"(base + 16u * kThreads * k));
+                         : "r"(base + half + 16u * kThreads * k)
+                         : "memory");
             lo = __fadd2_rn(lo, make_float2(v.x, v.y));
             hi = __fadd2_rn(hi, make_float2(v.z, v.w));
         }

@@ -1,0 +1,629 @@
+// tsweep.cuh -- the stage-specialised sweep for sm_103a: one launch advances
+// the wavefield by T = 1 or T = 2 time steps, each time step on its own
+// group of warps.
+//
+// This is the paper's time tiling (Sec. 4.1 skewing by the stencil radius,
+// Sec. 4.2 time tiles) laid out for a GPU block, with the stages of a tile
+// given to different warps instead of one loop nest:
+//
+//  * A block owns an output tile of BZ (z) x BY (y) columns and an x-chunk
+//    [X0, X1) of planes, and streams along x.  In iteration i the level-n
+//    plane c0 = X0 - RT + i enters; stage s computes level n+s on plane
+//    c0 - sR (the skew by R per time step).  Stage 1 starts at iteration 2R,
+//    once its x-queue holds the planes c0 - 2R .. c0; stage 2 at 4R.
+//  * Stage 1 (warps [0, N1)) computes level n+1 over the tile widened by R
+//    rows and RP columns on each side (T = 2) -- the halo stage 2 reads --
+//    or over the tile itself (T = 1, writing level n+1 to global memory).
+//    Its inputs arrive through TMA in ring A: the level-n plane c0 for the
+//    x-queue, the centre plane c0 - R with the y/z halo of the stencil, and
+//    level n-1, B and C on plane c0 - R.
+//  * Stage 2 (warps [N1, N1 + N2), T = 2) computes level n+2 over the tile.
+//    Stage 1 hands it each plane of level n+1 through ring 1 in shared
+//    memory; stage 2 pushes it into its own x-queue and reads the y/z
+//    neighbours of its centre plane c0 - 2R, written R iterations earlier,
+//    from the same ring.  Level n, B and C of plane c0 - 2R come through TMA
+//    in ring B (from L2: ring A loaded them R iterations before).  Stage 2
+//    writes levels n+2 and n+1 of the tile.
+//  * A producer warp issues the TMA loads: lane 0 fills ring A, lane 1 ring
+//    B, each up to P iterations ahead.  Every hand-off is an mbarrier
+//    ("full" with transaction counts from the producer or one arrival per
+//    stage-1 warp; "empty" with one arrival per consuming warp), so the two
+//    stages and the producer run decoupled: stage 1 may run up to D1 - R
+//    iterations ahead of stage 2.
+//  * Each thread holds VY rows x V z-points.  The x-neighbours come from a
+//    register queue of 2R+1 planes, the y-neighbours from shared memory
+//    (rows of the thread's own VY rows from the queue centre), the
+//    z-neighbours from a window whose middle V points are again the queue
+//    centre and whose halos of RP points come from shared memory.  Point
+//    pairs at odd z offsets are summed by two scalar additions into a fresh
+//    register pair rather than regrouped by moves.
+//  * TMA fills everything outside the grid with zeros, and B = C = 0 there,
+//    so points outside the grid compute to exactly 0 without branches (the
+//    paper's min/max bounds, Sec. 4.2.2).
+//  * Every mbarrier wait is bounded by %globaltimer; on expiry the warp
+//    records WAVE_ETIMEOUT in the status word, raises the block's abort
+//    flag and leaves its loop; the warps waiting on it run out in turn, and
+//    the producer waits (bounded) for its copies in flight before exiting.
+//
+// Bit-exactness: every point update is the sequence of IEEE-rounded
+// operations of sweep.cuh (same chains, same order), so this kernel, the
+// sweep of sweep.cuh, every T and every tile agree bit for bit (Sec. 4.3,
+// Sec. 5.4.3).
+#pragma once
+#include "sweep.cuh"
+
+namespace wt {
+
+// TMA descriptors of the stage-specialised sweep (all [nx][ny][nzp] float32).
+struct TMaps {
+    CUtensorMap uc;         // level n, centre box (WC x HC) of stage 1
+    CUtensorMap uf, um;     // level n and n-1 over the stage-1 region (W1 x H1)
+    CUtensorMap B, C;       // coefficients over the stage-1 region
+    CUtensorMap u2, B2, C2; // level n and coefficients over the output tile (BZ x BY), T = 2
+};
+
+template <int R, int T, int V, int VY, int BZ, int BY, int P>
+struct TShape {
+    static constexpr int RT = R * T;
+    static constexpr int RP = (R + 3) / 4 * 4;            // z halo of one stencil, 16-byte aligned
+    static constexpr int H1 = BY + 2 * (T - 1) * R;       // stage-1 rows
+    static constexpr int W1 = BZ + 2 * (T - 1) * RP;      // stage-1 columns (ring-1 pitch)
+    static constexpr int HC = H1 + 2 * R;                 // centre box rows
+    static constexpr int WC = W1 + 2 * RP;                // centre box columns (pitch)
+    static constexpr int LZ1 = W1 / V, LY1 = H1 / VY;     // stage-1 thread grid
+    static constexpr int N1 = (LZ1 * LY1 + 31) / 32 * 32;
+    static constexpr int LZ2 = BZ / V, LY2 = BY / VY;     // stage-2 thread grid
+    static constexpr int N2 = T == 2 ? (LZ2 * LY2 + 31) / 32 * 32 : 0;
+    static constexpr int NTB = N1 + N2 + 32;              // + the producer warp
+    static constexpr int DA = P + 1;                      // ring A slots
+    static constexpr int DB = T == 2 ? P + 1 : 0;         // ring B slots
+    static constexpr int D1 = T == 2 ? R + 3 : 0;         // ring 1 planes
+    static constexpr unsigned CBOX = WC * HC * 4, FBOX = W1 * H1 * 4, SBOX = BZ * BY * 4;
+    static constexpr unsigned CBOXP = (CBOX + 127) / 128 * 128;
+    static constexpr unsigned FBOXP = (FBOX + 127) / 128 * 128;
+    static constexpr unsigned SBOXP = (SBOX + 127) / 128 * 128;
+    // ring A slot: centre box, level n (queue feed), level n-1, B, C
+    static constexpr unsigned A_C = 0, A_F = CBOXP, A_UM = A_F + FBOXP, A_B = A_UM + FBOXP,
+                              A_CC = A_B + FBOXP, ASLOT = A_CC + FBOXP;
+    // ring B slot: level n, B, C over the output tile
+    static constexpr unsigned B_UM = 0, B_B = SBOXP, B_C = 2 * SBOXP, BSLOT = 3 * SBOXP;
+    static constexpr size_t OFF_B = (size_t)DA * ASLOT;
+    static constexpr size_t OFF_1 = OFF_B + (size_t)DB * BSLOT;
+    static constexpr size_t OFF_BAR = OFF_1 + (size_t)D1 * FBOXP;
+    static constexpr size_t OFF_P = OFF_BAR + 8 * (2 * DA + 2 * DB + 2 * D1) + 16;
+    static constexpr size_t SMEM = OFF_P;                 // + per-plane sparse slices
+    static size_t smem_bytes(int chunk) { return OFF_P + sweep_table_bytes(chunk, RT) + 16; }
+    static constexpr unsigned TXA = CBOX + 4 * FBOX;      // bytes of a ring-A slot from iteration 2R on
+    static constexpr unsigned TXF = FBOX;                 // before (queue fill only)
+    static constexpr unsigned TXB = 3 * SBOX;
+    static_assert(T == 1 || T == 2, "stage-specialised sweep: T = 1 or 2");
+    static_assert(V == 4, "four z points per thread (two pairs)");
+    static_assert(VY == 1 || VY == 2, "one or two rows per thread");
+    static_assert(BZ % 4 == 0 && BY % VY == 0 && H1 % VY == 0, "tile must split into thread blocks");
+    static_assert(R >= 1 && R <= kMaxR, "radius out of range");
+    static_assert(WC <= 256 && HC <= 256, "TMA box dimension above 256");
+    static_assert(TXA < (1u << 20), "mbarrier tx count");
+    static_assert(NTB <= 1024, "too many threads per block");
+    static_assert(SMEM <= 200 * 1024, "shared memory above the per-block limit");
+};
+
+// Level n+1 of a thread's VY x V points (VY rows, V/2 pairs each) from the
+// x-queue q of level n (q[R] = the centre plane at the thread's own points),
+// the centre plane pc (shared memory at the thread's first point, pitch PC
+// floats) and level n-1, B, C (shared memory at the first point, pitch PK).
+// cC receives C for the source injection.  The operations and their order
+// are those of sweep_block in sweep.cuh: R <= 2 one chain (centre, then per
+// k the x, y, z pair sums); R >= 3 three chains (centre + x), y, z summed as
+// (x + y) + z; then u^{n+1} = u^n + B (u^n - u^{n-1}) + C L u^n.
+template <int R, int V, int VY, int PC, int PK>
+__device__ __forceinline__ void tstage_update(float2 (&un)[VY][V / 2], float2 (&cC)[VY][V / 2],
+                                              const float2 (&q)[2 * R + 1][VY][V / 2], const float *pc,
+                                              const float *pum, const float *pB, const float *pCc,
+                                              const Stencil &st)
+{
+    constexpr int V2 = V / 2;
+    constexpr int RP = (R + 3) / 4 * 4;
+    constexpr int ZW = V + 2 * RP;  // z window of a row: halo, own points (queue centre), halo
+    float2 lap[VY][V2], ly[VY][V2], lz[VY][V2];
+    // z windows, as scalars: w[v][RP .. RP + V) are the row's own points
+    float w[VY][ZW];
+#pragma unroll
+    for (int v = 0; v < VY; ++v) {
+#pragma unroll
+        for (int i = 0; i < RP / 4; ++i) {
+            const float4 l = reinterpret_cast<const float4 *>(pc + v * PC - RP)[i];
+            const float4 r = reinterpret_cast<const float4 *>(pc + v * PC + V)[i];
+            w[v][4 * i] = l.x; w[v][4 * i + 1] = l.y; w[v][4 * i + 2] = l.z; w[v][4 * i + 3] = l.w;
+            w[v][RP + V + 4 * i] = r.x; w[v][RP + V + 4 * i + 1] = r.y;
+            w[v][RP + V + 4 * i + 2] = r.z; w[v][RP + V + 4 * i + 3] = r.w;
+        }
+#pragma unroll
+        for (int j = 0; j < V2; ++j) {
+            w[v][RP + 2 * j] = q[R][v][j].x;
+            w[v][RP + 2 * j + 1] = q[R][v][j].y;
+        }
+    }
+#pragma unroll
+    for (int k = 1; k <= R; ++k) {
+#pragma unroll
+        for (int v = 0; v < VY; ++v) {
+            // rows v + k and v - k: the thread's own rows from the queue
+            // centre, the others from shared memory (a row shared by two own
+            // rows is loaded once: the loads repeat the same address)
+            const int dp = v + k, dm = v - k;
+            float2 yp[V2], ym[V2];
+            if (dp < VY) {
+#pragma unroll
+                for (int j = 0; j < V2; ++j) yp[j] = q[R][dp < VY ? dp : 0][j];
+            } else {
+                ld2<V>(yp, pc + dp * PC);
+            }
+            if (dm >= 0) {
+#pragma unroll
+                for (int j = 0; j < V2; ++j) ym[j] = q[R][dm >= 0 ? dm : 0][j];
+            } else {
+                ld2<V>(ym, pc + dm * PC);
+            }
+#pragma unroll
+            for (int j = 0; j < V2; ++j) {
+                const float2 u0 = q[R][v][j];
+                const float2 sx = __fadd2_rn(q[R + k][v][j], q[R - k][v][j]);
+                const float2 sy = __fadd2_rn(yp[j], ym[j]);
+                const int a = RP + 2 * j + k, b = RP + 2 * j - k;
+                float2 sz;
+                if ((k & 1) == 0) {
+                    sz = __fadd2_rn(make_float2(w[v][a], w[v][a + 1]), make_float2(w[v][b], w[v][b + 1]));
+                } else {
+                    sz.x = __fadd_rn(w[v][a], w[v][b]);
+                    sz.y = __fadd_rn(w[v][a + 1], w[v][b + 1]);
+                }
+                if (R <= 2) {
+                    if (k == 1) lap[v][j] = __fmul2_rn(st.cc, u0);
+                    lap[v][j] = __ffma2_rn(st.cx[k], sx, lap[v][j]);
+                    lap[v][j] = __ffma2_rn(st.cy[k], sy, lap[v][j]);
+                    lap[v][j] = __ffma2_rn(st.cz[k], sz, lap[v][j]);
+                } else if (k == 1) {
+                    lap[v][j] = __ffma2_rn(st.cx[1], sx, __fmul2_rn(st.cc, u0));
+                    ly[v][j] = __fmul2_rn(st.cy[1], sy);
+                    lz[v][j] = __fmul2_rn(st.cz[1], sz);
+                } else {
+                    lap[v][j] = __ffma2_rn(st.cx[k], sx, lap[v][j]);
+                    ly[v][j] = __ffma2_rn(st.cy[k], sy, ly[v][j]);
+                    lz[v][j] = __ffma2_rn(st.cz[k], sz, lz[v][j]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < VY; ++v) {
+        float2 cB[V2], up[V2];
+        ld2<V>(cB, pB + v * PK);
+        ld2<V>(cC[v], pCc + v * PK);
+        ld2<V>(up, pum + v * PK);
+#pragma unroll
+        for (int j = 0; j < V2; ++j) {
+            if constexpr (R > 2) lap[v][j] = __fadd2_rn(__fadd2_rn(lap[v][j], ly[v][j]), lz[v][j]);
+            const float2 u0 = q[R][v][j];
+            const float2 du = fsub2_rn(u0, up[j]);
+            un[v][j] = __ffma2_rn(cC[v][j], lap[v][j], __ffma2_rn(cB[j], du, u0));
+        }
+    }
+}
+
+// Point sources of plane cs on a thread's VY x V points at global row gy
+// (first row) and column gz: u += C f, f = sum of w q_s in ascending source
+// order (the injection loop of sweep_block).
+template <int V, int VY>
+__device__ __forceinline__ void tstage_inject(float2 (&un)[VY][V / 2], const float2 (&cC)[VY][V / 2],
+                                              const SweepArgs &a, int e0, int e1, int gy, int gz, int qrow)
+{
+    const long long qbase = (long long)qrow * a.nq;
+#pragma unroll
+    for (int v = 0; v < VY; ++v) {
+        float fv[V];
+        unsigned hits = 0u;
+#pragma unroll
+        for (int j = 0; j < V; ++j) fv[j] = 0.f;
+        for (int eb = e0; eb < e1; eb += 4) {
+            int4 pt4[4];  // four table points per round trip
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                pt4[u] = eb + u < e1 ? __ldg(a.inj.pts + eb + u) : make_int4(-1, -1, 0, 0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int4 pt = pt4[u];
+                if (pt.x != gy + v || pt.y < gz || pt.y >= gz + V) continue;
+                float f = 0.f;
+                int itm = pt.z;
+                for (; itm + 1 < pt.w; itm += 2) {  // items in pairs, ascending sum
+                    const int i0 = __ldg(a.inj.item + itm), i1 = __ldg(a.inj.item + itm + 1);
+                    const float w0 = __ldg(a.inj.w + itm), w1 = __ldg(a.inj.w + itm + 1);
+                    const float q0 = __ldg(a.q + qbase + i0), q1 = __ldg(a.q + qbase + i1);
+                    f = __fmaf_rn(w0, q0, f);
+                    f = __fmaf_rn(w1, q1, f);
+                }
+                if (itm < pt.w)
+                    f = __fmaf_rn(__ldg(a.inj.w + itm), __ldg(a.q + qbase + __ldg(a.inj.item + itm)), f);
+                const int jj = pt.y - gz;
+#pragma unroll
+                for (int j = 0; j < V; ++j) fv[j] = jj == j ? f : fv[j];
+                hits |= 1u << jj;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+            if (hits & (1u << j)) {
+                float &uj = (j & 1) ? un[v][j >> 1].y : un[v][j >> 1].x;
+                const float cj = (j & 1) ? cC[v][j >> 1].y : cC[v][j >> 1].x;
+                uj = __fmaf_rn(cj, fv[j], uj);
+            }
+    }
+}
+
+__device__ __forceinline__ void tstage_abort(volatile int *abort_flag, int *status)
+{
+    *abort_flag = 1;
+    atomicMin(status, -4 /* WAVE_ETIMEOUT */);
+}
+
+template <int R, int T, int V, int VY, int BZ, int BY, int P>
+__device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &st, const TMaps &mp,
+                                             const int blk)
+{
+    using S = TShape<R, T, V, VY, BZ, BY, P>;
+    constexpr int QL = 2 * R + 1, V2 = V / 2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *ringA = smem_raw;
+    unsigned char *ringB = smem_raw + S::OFF_B;
+    float *ring1 = reinterpret_cast<float *>(smem_raw + S::OFF_1);
+    uint64_t *fullA = reinterpret_cast<uint64_t *>(smem_raw + S::OFF_BAR);
+    uint64_t *emptyA = fullA + S::DA;
+    uint64_t *fullB = emptyA + S::DA;
+    uint64_t *emptyB = fullB + S::DB;
+    uint64_t *full1 = emptyB + S::DB;
+    uint64_t *empty1 = full1 + S::D1;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(empty1 + S::D1);
+
+    if (blockDim.x != S::NTB) {  // launched with the wrong shape: report, do nothing
+        if (threadIdx.x == 0 && blk == 0) atomicMin(a.status, -1 /* WAVE_EINVAL */);
+        return;
+    }
+    // programmatic dependent launch (see sweep_block)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int tid = threadIdx.x;
+    int b = a.order != nullptr ? __ldg(a.order + blk) : blk;
+    const int tzi = b % a.tiles_z;
+    b /= a.tiles_z;
+    const int tyi = b % a.tiles_y;
+    const int txi = b / a.tiles_y;
+    const int X0 = txi * a.chunk;
+    const int X1 = min(X0 + a.chunk, a.nx);
+    const int ty0 = tyi * BY, tz0 = tzi * BZ;      // output tile origin
+    const int gy0 = ty0 - (T - 1) * R;             // stage-1 region origin
+    const int gz0 = tz0 - (T - 1) * S::RP;
+    const int niter = (X1 - X0) + 2 * S::RT;
+    const int c00 = X0 - S::RT;                    // level-n plane of iteration 0
+
+    // Sparse tables of the planes this block visits, [X0 - 2RT, X1 + RT]
+    // (as in sweep_block): injection relevant over the stage-1 region,
+    // records over the output tile.
+    const int pbase = X0 - 2 * S::RT;
+    const int plen = (X1 - X0) + 3 * S::RT + 2;
+    int *pinj = reinterpret_cast<int *>(smem_raw + S::OFF_P);
+    int *prec = pinj + plen;
+    unsigned char *finj = reinterpret_cast<unsigned char *>(prec + plen);
+    unsigned char *frec = finj + plen;
+    int my_inj = 0, my_rec = 0;
+    for (int k = tid; k < plen; k += S::NTB) {
+        const int cp = min(max(pbase + k, 0), a.nx);
+        const int ci = min(max(pbase + k + 1, 0), a.nx);
+        int fi = 0, fr = 0;
+        if (a.inj.plane_start != nullptr) {
+            const int e0 = a.inj.plane_start[cp], e1 = a.inj.plane_start[ci];
+            pinj[k] = e0;
+            for (int eb = e0; eb < e1 && !fi; eb += 4) {
+                int4 pt4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    pt4[u] = eb + u < e1 ? __ldg(a.inj.pts + eb + u) : make_int4(-(1 << 30), -(1 << 30), 0, 0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int4 pt = pt4[u];
+                    fi |= pt.x >= gy0 && pt.x < gy0 + S::H1 && pt.y >= gz0 && pt.y < gz0 + S::W1;
+                }
+            }
+        } else {
+            pinj[k] = 0;
+        }
+        if (a.rec.plane_start != nullptr) {
+            const int e0 = a.rec.plane_start[cp], e1 = a.rec.plane_start[ci];
+            prec[k] = e0;
+            for (int eb = e0; eb < e1 && !fr; eb += 4) {
+                int4 pt4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    pt4[u] = eb + u < e1 ? __ldg(a.rec.pts + eb + u) : make_int4(-(1 << 30), -(1 << 30), 0, 0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int4 pt = pt4[u];
+                    fr |= pt.x >= ty0 && pt.x < ty0 + BY && pt.y >= tz0 && pt.y < tz0 + BZ;
+                }
+            }
+        } else {
+            prec[k] = 0;
+        }
+        finj[k] = (unsigned char)fi;
+        frec[k] = (unsigned char)fr;
+        my_inj |= fi;
+        my_rec |= fr;
+    }
+    if (tid == 0) {
+        for (int k = 0; k < S::DA; ++k) {
+            mbar_init(fullA + k, 1);
+            mbar_init(emptyA + k, S::N1 / 32);
+        }
+        for (int k = 0; k < S::DB; ++k) {
+            mbar_init(fullB + k, 1);
+            mbar_init(emptyB + k, S::N2 / 32);
+        }
+        for (int k = 0; k < S::D1; ++k) {
+            mbar_init(full1 + k, S::N1 / 32);
+            mbar_init(empty1 + k, S::N2 / 32);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const bool any_inj = __syncthreads_or(my_inj) != 0;
+    const bool any_rec = __syncthreads_or(my_rec) != 0;
+    // the previous launch on the stream has completed; every field access
+    // below comes after this
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const bool lane0 = (tid & 31) == 0;
+    constexpr unsigned FULL = 0xffffffffu;
+
+    if (tid >= S::N1 + S::N2) {
+        // ------------------------------ producer warp ------------------------------
+        const int lane = tid & 31;
+        if (a.withhold) return;
+        if (lane == 0) {
+            // ring A: the stage-1 inputs of iteration i
+            int i = 0, s = 0, r = 0;
+            for (; i < niter; ++i) {
+                if (*abort_flag) break;
+                if (r > 0 && !mbar_wait_bounded(emptyA + s, (uint32_t)((r - 1) & 1))) {
+                    tstage_abort(abort_flag, a.status);
+                    break;
+                }
+                const int c0 = c00 + i;
+                unsigned char *sl = ringA + (size_t)s * S::ASLOT;
+                const bool full_slot = i >= 2 * R;
+                mbar_expect_tx(fullA + s, full_slot ? S::TXA : S::TXF);
+                tma_load_3d(sl + S::A_F, &mp.uf, gz0, gy0, c0, fullA + s);
+                if (full_slot) {
+                    tma_load_3d(sl + S::A_C, &mp.uc, gz0 - S::RP, gy0 - R, c0 - R, fullA + s);
+                    tma_load_3d(sl + S::A_UM, &mp.um, gz0, gy0, c0 - R, fullA + s);
+                    tma_load_3d(sl + S::A_B, &mp.B, gz0, gy0, c0 - R, fullA + s);
+                    tma_load_3d(sl + S::A_CC, &mp.C, gz0, gy0, c0 - R, fullA + s);
+                }
+                if (++s == S::DA) { s = 0; ++r; }
+            }
+            // no copy into this block's shared memory may still be in flight
+            for (int k = (i > S::DA ? i - S::DA : 0); k < i; ++k)
+                mbar_wait_bounded(fullA + k % S::DA, (uint32_t)((k / S::DA) & 1));
+        } else if (T == 2 && lane == 1) {
+            // ring B: level n, B, C over the tile for stage 2 (plane X0 + j)
+            const int nj = niter - 4 * R;
+            int j = 0, s = 0, r = 0;
+            for (; j < nj; ++j) {
+                if (*abort_flag) break;
+                if (r > 0 && !mbar_wait_bounded(emptyB + s, (uint32_t)((r - 1) & 1))) {
+                    tstage_abort(abort_flag, a.status);
+                    break;
+                }
+                unsigned char *sl = ringB + (size_t)s * S::BSLOT;
+                mbar_expect_tx(fullB + s, S::TXB);
+                tma_load_3d(sl + S::B_UM, &mp.u2, tz0, ty0, X0 + j, fullB + s);
+                tma_load_3d(sl + S::B_B, &mp.B2, tz0, ty0, X0 + j, fullB + s);
+                tma_load_3d(sl + S::B_C, &mp.C2, tz0, ty0, X0 + j, fullB + s);
+                if (++s == S::DB) { s = 0; ++r; }
+            }
+            if constexpr (T == 2)
+                for (int k = (j > S::DB ? j - S::DB : 0); k < j; ++k)
+                    mbar_wait_bounded(fullB + k % S::DB, (uint32_t)((k / S::DB) & 1));
+        }
+        return;
+    }
+
+    if (tid < S::N1) {
+        // ------------------------------ stage 1 ------------------------------
+        const bool act = tid < S::LZ1 * S::LY1;
+        const int t = act ? tid : 0;
+        const int ry = (t / S::LZ1) * VY, cz = (t % S::LZ1) * V;
+        const int offF = ry * S::W1 + cz;                 // in stage-1 boxes and ring-1 planes
+        const int offC = (ry + R) * S::WC + cz + S::RP;   // in the centre box
+        const int gy = gy0 + ry, gz = gz0 + cz;
+        float2 q[QL][VY][V2];
+#pragma unroll
+        for (int k = 0; k < QL; ++k)
+#pragma unroll
+            for (int v = 0; v < VY; ++v)
+#pragma unroll
+                for (int j = 0; j < V2; ++j) q[k][v][j] = make_float2(0.f, 0.f);
+        // T = 1: stage 1 writes level n+1 of its own points (planes [X0, X1))
+        float *outp = nullptr;
+        bool sok[VY];
+        if constexpr (T == 1) {
+            outp = a.out_hi + ((long long)X0 * a.sx + (long long)gy * a.nz + gz);
+#pragma unroll
+            for (int v = 0; v < VY; ++v) sok[v] = act && gy + v < a.ny && gz < a.nz;
+        }
+        int sa = 0;
+        uint32_t pa = 0;
+        int s1 = 0, r1 = 0;  // ring-1 slot of the next stage-1 plane, and its round
+#pragma unroll 1
+        for (int i = 0; i < niter; ++i) {
+            if (!__all_sync(FULL, mbar_wait_bounded(fullA + sa, pa))) {
+                if (lane0) tstage_abort(abort_flag, a.status);
+                break;
+            }
+            const float *sl = reinterpret_cast<const float *>(ringA + (size_t)sa * S::ASLOT);
+            // level n of plane c0 enters the x-queue (replacing its oldest)
+#pragma unroll
+            for (int k = 0; k < QL - 1; ++k)
+#pragma unroll
+                for (int v = 0; v < VY; ++v)
+#pragma unroll
+                    for (int j = 0; j < V2; ++j) q[k][v][j] = q[k + 1][v][j];
+#pragma unroll
+            for (int v = 0; v < VY; ++v) ld2<V>(q[QL - 1][v], sl + S::A_F / 4 + offF + v * S::W1);
+            if (i >= 2 * R) {
+                float2 un[VY][V2], cC[VY][V2];
+                tstage_update<R, V, VY, S::WC, S::W1>(un, cC, q, sl + S::A_C / 4 + offC,
+                                                      sl + S::A_UM / 4 + offF, sl + S::A_B / 4 + offF,
+                                                      sl + S::A_CC / 4 + offF, st);
+                const int cs = c00 + i - R;  // plane of level n+1
+                if (any_inj && finj[cs - pbase])
+                    tstage_inject<V, VY>(un, cC, a, pinj[cs - pbase], pinj[cs - pbase + 1], gy, gz, a.q_row0);
+                if constexpr (T == 1) {
+#pragma unroll
+                    for (int v = 0; v < VY; ++v)
+                        if (sok[v]) st2<V>(outp + (long long)v * a.nz, un[v]);
+                    outp += a.sx;
+                } else {
+                    // hand the plane to stage 2 through ring 1
+                    if (r1 > 0 && !__all_sync(FULL, mbar_wait_bounded(empty1 + s1, (uint32_t)((r1 - 1) & 1)))) {
+                        if (lane0) tstage_abort(abort_flag, a.status);
+                        break;
+                    }
+                    if (act) {
+#pragma unroll
+                        for (int v = 0; v < VY; ++v)
+                            st2<V>(ring1 + (size_t)s1 * (S::FBOXP / 4) + offF + v * S::W1, un[v]);
+                    }
+                    __syncwarp();
+                    if (lane0) mbar_arrive(full1 + s1);
+                    if (++s1 == S::D1) { s1 = 0; ++r1; }
+                }
+            }
+            __syncwarp();
+            if (lane0) mbar_arrive(emptyA + sa);
+            if (++sa == S::DA) { sa = 0; pa ^= 1u; }
+        }
+    }
+
+    if constexpr (T == 2) {
+        if (tid >= S::N1) {
+            // ------------------------------ stage 2 ------------------------------
+            const int t2 = tid - S::N1;
+            const bool act = t2 < S::LZ2 * S::LY2;
+            const int t = act ? t2 : 0;
+            const int ry = (t / S::LZ2) * VY, cz = (t % S::LZ2) * V;
+            const int off1 = (ry + R) * S::W1 + cz + S::RP;  // in ring-1 planes
+            const int offS = ry * BZ + cz;                   // in ring-B boxes
+            const int gy = ty0 + ry, gz = tz0 + cz;
+            bool sok[VY];
+#pragma unroll
+            for (int v = 0; v < VY; ++v) sok[v] = act && gy + v < a.ny && gz < a.nz;
+            const long long o0 = (long long)X0 * a.sx + (long long)gy * a.nz + gz;
+            float *oh = a.out_hi + o0, *ol = a.out_lo + o0;
+            float2 q[QL][VY][V2];
+#pragma unroll
+            for (int k = 0; k < QL; ++k)
+#pragma unroll
+                for (int v = 0; v < VY; ++v)
+#pragma unroll
+                    for (int j = 0; j < V2; ++j) q[k][v][j] = make_float2(0.f, 0.f);
+            int s1 = 0;            // ring-1 slot of the plane stage 1 produced this iteration
+            uint32_t p1 = 0;
+            int sc = 0;            // ring-1 slot of the centre plane (produced R iterations earlier)
+            int sb = 0;
+            uint32_t pb = 0;
+#pragma unroll 1
+            for (int i = 2 * R; i < niter; ++i) {
+                if (!__all_sync(FULL, mbar_wait_bounded(full1 + s1, p1))) {
+                    if (lane0) tstage_abort(abort_flag, a.status);
+                    break;
+                }
+                const float *rp = ring1 + (size_t)s1 * (S::FBOXP / 4);
+#pragma unroll
+                for (int k = 0; k < QL - 1; ++k)
+#pragma unroll
+                    for (int v = 0; v < VY; ++v)
+#pragma unroll
+                        for (int j = 0; j < V2; ++j) q[k][v][j] = q[k + 1][v][j];
+#pragma unroll
+                for (int v = 0; v < VY; ++v) ld2<V>(q[QL - 1][v], rp + off1 + v * S::W1);
+                if (i >= 4 * R) {
+                    if (!__all_sync(FULL, mbar_wait_bounded(fullB + sb, pb))) {
+                        if (lane0) tstage_abort(abort_flag, a.status);
+                        break;
+                    }
+                    const float *bp = reinterpret_cast<const float *>(ringB + (size_t)sb * S::BSLOT);
+                    float2 un[VY][V2], cC[VY][V2];
+                    tstage_update<R, V, VY, S::W1, BZ>(un, cC, q, ring1 + (size_t)sc * (S::FBOXP / 4) + off1,
+                                                       bp + S::B_UM / 4 + offS, bp + S::B_B / 4 + offS,
+                                                       bp + S::B_C / 4 + offS, st);
+                    const int cs = c00 + i - 2 * R;  // plane of level n+2, in [X0, X1)
+                    if (any_inj && finj[cs - pbase])
+                        tstage_inject<V, VY>(un, cC, a, pinj[cs - pbase], pinj[cs - pbase + 1], gy, gz,
+                                             a.q_row0 + a.q_dir);
+#pragma unroll
+                    for (int v = 0; v < VY; ++v)
+                        if (sok[v]) {
+                            st2<V>(oh + (long long)v * a.nz, un[v]);
+                            st2<V>(ol + (long long)v * a.nz, q[R][v]);
+                        }
+                    oh += a.sx;
+                    ol += a.sx;
+                    __syncwarp();
+                    if (lane0) mbar_arrive(emptyB + sb);
+                    if (++sb == S::DB) { sb = 0; pb ^= 1u; }
+                }
+                if (i >= 3 * R) {
+                    // the plane produced R iterations ago is read for the last time
+                    __syncwarp();
+                    if (lane0) mbar_arrive(empty1 + sc);
+                    if (++sc == S::D1) sc = 0;
+                }
+                if (++s1 == S::D1) { s1 = 0; p1 ^= 1u; }
+            }
+        }
+    }
+
+    // Receiver corners of the stored levels (T: out_hi, T-1: out_lo), once
+    // the block's own points are written, shared out over the threads of the
+    // last stage (see sweep_block).
+    constexpr int NL = T == 2 ? S::N2 : S::N1;  // threads of the last stage
+    const int tl = T == 2 ? tid - S::N1 : tid;
+    if (any_rec && tl >= 0 && tl < NL) {
+        asm volatile("bar.sync 1, %0;" ::"r"(NL) : "memory");
+        const int k0 = X0 - pbase, k1 = X1 - pbase;
+        const int E0 = prec[k0], E1 = prec[k1];
+        for (int e = E0 + tl; e < E1; e += NL) {
+            int lo = k0, hi = k1 - 1;  // plane of entry e: last k with prec[k] <= e
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (prec[mid] <= e) lo = mid; else hi = mid - 1;
+            }
+            const int4 pt = __ldg(a.rec.pts + e);
+            if (pt.x < ty0 || pt.x >= ty0 + BY || pt.y < tz0 || pt.y >= tz0 + BZ) continue;
+            const long long pix = (long long)(pbase + lo) * a.sx + (long long)pt.x * a.nz + pt.y;
+#pragma unroll
+            for (int sg = (T > 1 ? T - 1 : 1); sg <= T; ++sg) {
+                const float v = (sg == T ? a.out_hi : a.out_lo)[pix];  // written by this block
+                const long long crow = (long long)(a.c_row0 + a.c_dir * (sg - 1)) * a.nslot;
+                for (int itm = pt.z; itm < pt.w; ++itm) a.corner[crow + __ldg(a.rec.item + itm)] = v;
+            }
+        }
+    }
+}
+
+template <int R, int T, int V, int VY, int BZ, int BY, int P>
+__global__ void __launch_bounds__(TShape<R, T, V, VY, BZ, BY, P>::NTB, 1)
+tsweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stencil st,
+              const __grid_constant__ TMaps mp)
+{
+    tsweep_block<R, T, V, VY, BZ, BY, P>(a, st, mp, blockIdx.x);
+}
+
+}  // namespace wt

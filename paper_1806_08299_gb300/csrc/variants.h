@@ -36,6 +36,24 @@
 #define WAVE_SWEEP_VARIANTS_R8(X) \
     X(8, 1, 2, 64, 8, 2, 2) X(8, 1, 4, 64, 8, 2, 3) X(8, 1, 4, 64, 12, 2, 2)
 
+// Stage-specialised variants Z(R, T, V, VY, BZ, BY, P) of tsweep.cuh: time
+// step T on its own warps (T = 1 or 2), VY rows x V z-points per thread,
+// output tile BZ x BY, TMA prefetch distance P.  Shared memory holds P+1
+// slots of the stage-1 inputs (centre box with halo, level n, level n-1, B,
+// C over the stage-1 region), for T = 2 also P+1 slots of the stage-2 inputs
+// over the tile and R+3 planes of level n+1 handed from stage 1 to stage 2.
+#define WAVE_TSWEEP_VARIANTS_R1(Z)
+#define WAVE_TSWEEP_VARIANTS_R2(Z) \
+    Z(2, 1, 4, 1, 64, 8, 2) Z(2, 2, 4, 1, 56, 16, 2) Z(2, 2, 4, 2, 56, 24, 2) Z(2, 2, 4, 2, 120, 12, 1)
+#define WAVE_TSWEEP_VARIANTS_R3(Z)
+#define WAVE_TSWEEP_VARIANTS_R4(Z) \
+    Z(4, 1, 4, 1, 64, 8, 2) Z(4, 1, 4, 2, 64, 16, 2) Z(4, 2, 4, 1, 56, 16, 2) Z(4, 2, 4, 2, 56, 16, 2) \
+    Z(4, 2, 4, 2, 56, 24, 1)
+#define WAVE_TSWEEP_VARIANTS_R5(Z)
+#define WAVE_TSWEEP_VARIANTS_R6(Z)
+#define WAVE_TSWEEP_VARIANTS_R7(Z)
+#define WAVE_TSWEEP_VARIANTS_R8(Z)
+
 // Gradient-mode variants Y(R, T, V, BZ, BY, P, MB, XB): the untiled default
 // shape of a radius with XB extra ring-K boxes (1: E for the second-difference
 // sweep; 2: D and G for the imaging-condition sweep), so that those sweeps

@@ -451,28 +451,42 @@ const SweepVariant *mode_variant(const SweepVariant *v, int mode)
     return nullptr;
 }
 
+// Rows per thread of a variant (sweep.cuh variants: one).
+int rows_of(const SweepVariant *v) { return v->VY > 0 ? v->VY : 1; }
+
+// Whether variant v is of the kernel family `kernel` names (wave_tuning.kernel:
+// 0 any, 1 the sweep of sweep.cuh, 2 the stage-specialised sweep).
+bool kernel_matches(const SweepVariant *v, int kernel) { return kernel == 0 || kernel == v->kind + 1; }
+
 // Pick the variant for radius R with time tile T (and tile_y / vec if given).
 // The first compiled variant of radius R and depth T with the given shape
 // (0 = any value of that field).
-const SweepVariant *find_variant(int R, int T, int tile_y, int vec, int tile_z = 0)
+const SweepVariant *find_variant(int R, int T, int tile_y, int vec, int tile_z = 0, int kernel = 0,
+                                 int rows = 0)
 {
     const SweepVariant *vs;
     const int nv = variants_for(R, &vs);
     for (int i = 0; i < nv; ++i)
         if (vs[i].T == T && (tile_y == 0 || vs[i].BY == tile_y) && (vec == 0 || vs[i].V == vec) &&
-            (tile_z == 0 || vs[i].BZ == tile_z))
+            (tile_z == 0 || vs[i].BZ == tile_z) && kernel_matches(&vs[i], kernel) &&
+            (rows == 0 || rows_of(&vs[i]) == rows))
             return &vs[i];
     return nullptr;
 }
 
-// Largest-T variant of radius R with T <= limit (T = 1 always exists).
-const SweepVariant *fallback_variant(int R, int limit)
+// Largest-T variant of radius R with T <= limit (T = 1 always exists), of
+// kernel family `kind` where one exists (any family otherwise; -1: any).
+const SweepVariant *fallback_variant(int R, int limit, int kind = -1)
 {
     const SweepVariant *vs;
     const int nv = variants_for(R, &vs);
     const SweepVariant *best = nullptr;
-    for (int i = 0; i < nv; ++i)
-        if (vs[i].T <= limit && (best == nullptr || vs[i].T > best->T)) best = &vs[i];
+    for (int i = 0; i < nv; ++i) {
+        if (vs[i].T > limit) continue;
+        const bool better = best == nullptr || vs[i].T > best->T ||
+                            (vs[i].T == best->T && kind >= 0 && vs[i].kind == kind && best->kind != kind);
+        if (better) best = &vs[i];
+    }
     return best;
 }
 
@@ -493,9 +507,10 @@ bool tune_log()
 }
 
 // Optional plan cache file (env WAVE_TUNE_CACHE = path): one plan per line,
-//   nx ny nz space_order T_requested  ->  T tile_y vec chunk [tile_z]
+//   nx ny nz space_order T_requested  ->  T tile_y vec chunk [tile_z [kernel rows]]
 // Lines naming variants that are not compiled in, or of another format, are
-// ignored; a line without tile_z takes the first variant of that shape.
+// ignored; a line without tile_z takes the first variant of that shape, and a
+// line without kernel and rows the first of either kernel family.
 
 bool cache_lookup_file(const TuneKey &k, Plan *out)
 {
@@ -503,16 +518,16 @@ bool cache_lookup_file(const TuneKey &k, Plan *out)
     if (path == nullptr || !path[0]) return false;
     FILE *f = std::fopen(path, "r");
     if (f == nullptr) return false;
-    int nx, ny, nz, so, tr, T, by, vec, chunk, bz;
+    int nx, ny, nz, so, tr, T, by, vec, chunk, bz, kern, rows;
     bool found = false;
     char line[256];
     while (std::fgets(line, sizeof(line), f) != nullptr) {
-        bz = 0;
-        const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d", &nx, &ny, &nz, &so, &tr, &T, &by,
-                                    &vec, &chunk, &bz);
-        if (got != 9 && got != 10) continue;
+        bz = kern = rows = 0;
+        const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d", &nx, &ny, &nz, &so, &tr, &T,
+                                    &by, &vec, &chunk, &bz, &kern, &rows);
+        if (got != 9 && got != 10 && got != 12) continue;
         if (nx == k.nx && ny == k.ny && nz == k.nz && so == k.so && tr == k.T) {
-            const SweepVariant *v = find_variant(so / 2, T, by, vec, bz);
+            const SweepVariant *v = find_variant(so / 2, T, by, vec, bz, kern, rows);
             if (v != nullptr && chunk > 0) {
                 out->v = v;
                 out->chunk = chunk;
@@ -530,8 +545,8 @@ void cache_store_file(const TuneKey &k, const Plan &p)
     if (path == nullptr || !path[0]) return;
     FILE *f = std::fopen(path, "a");
     if (f == nullptr) return;
-    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d\n", k.nx, k.ny, k.nz, k.so, k.T, p.v->T, p.v->BY,
-                 p.v->V, p.chunk, p.v->BZ);
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d\n", k.nx, k.ny, k.nz, k.so, k.T, p.v->T, p.v->BY,
+                 p.v->V, p.chunk, p.v->BZ, p.v->kind + 1, rows_of(p.v));
     std::fclose(f);
 }
 
@@ -616,23 +631,39 @@ struct State {
 // `job` by variant v from local step j (rows of the step-dependent tables are
 // those of step j), with x-chunk `chunk`.  *nblocks receives the grid size.
 int build_launch(const Job &job, const State &s, int j, const SweepVariant *v, int chunk, SweepArgs *ap,
-                 wt::SweepMaps *mp, long long *nblocks)
+                 wt::SweepMaps *mp, wt::TMaps *tm, long long *nblocks)
 {
     const Dims &d = job.d;
     SweepArgs &a = *ap;
     std::memset(&a, 0, sizeof(a));
     std::memset(mp, 0, sizeof(*mp));
+    std::memset(tm, 0, sizeof(*tm));
     a.nx = d.nx;
     a.ny = d.ny;
     a.nz = d.nzp;
     a.sx = (int)((long long)d.ny * d.nzp);
     a.npad = d.npad;
     a.status = job.status;
-    int rc = encode_map(&mp->u, s.buf[s.a], d, v->PW, v->H0);
-    if (!rc) rc = encode_map(&mp->um, s.buf[s.b], d, v->W0, v->HK);
-    if (!rc) rc = encode_map(&mp->B, job.cB, d, v->W0, v->HK);
-    if (!rc) rc = encode_map(&mp->C, job.cC, d, v->W0, v->HK);
-    if (!rc && v->T == 1) rc = encode_map(&mp->uk, s.buf[s.a], d, v->W0, v->HK);
+    int rc = WAVE_OK;
+    if (v->kind == 1) {
+        // stage-specialised sweep: stage-1 boxes, its centre box, and the
+        // output-tile boxes of stage 2
+        rc = encode_map(&tm->uc, s.buf[s.a], d, v->WC, v->HC);
+        if (!rc) rc = encode_map(&tm->uf, s.buf[s.a], d, v->W1, v->H1);
+        if (!rc) rc = encode_map(&tm->um, s.buf[s.b], d, v->W1, v->H1);
+        if (!rc) rc = encode_map(&tm->B, job.cB, d, v->W1, v->H1);
+        if (!rc) rc = encode_map(&tm->C, job.cC, d, v->W1, v->H1);
+        if (!rc && v->T == 2) rc = encode_map(&tm->u2, s.buf[s.a], d, v->BZ, v->BY);
+        if (!rc && v->T == 2) rc = encode_map(&tm->B2, job.cB, d, v->BZ, v->BY);
+        if (!rc && v->T == 2) rc = encode_map(&tm->C2, job.cC, d, v->BZ, v->BY);
+        if (rc) return rc;
+    } else {
+        rc = encode_map(&mp->u, s.buf[s.a], d, v->PW, v->H0);
+        if (!rc) rc = encode_map(&mp->um, s.buf[s.b], d, v->W0, v->HK);
+        if (!rc) rc = encode_map(&mp->B, job.cB, d, v->W0, v->HK);
+        if (!rc) rc = encode_map(&mp->C, job.cC, d, v->W0, v->HK);
+    }
+    if (!rc && v->kind == 0 && v->T == 1) rc = encode_map(&mp->uk, s.buf[s.a], d, v->W0, v->HK);
     if (!rc && v->XB == 1) rc = encode_map(&mp->x0, job.cE, d, v->W0, v->HK);
     if (!rc && v->XB == 2) {
         const long long row = job.l_base + (long long)job.l_dir * j;  // this step's D row
@@ -707,8 +738,19 @@ bool mark_heavy(const Dims &d, const SweepVariant *v, int chunk, const HostTable
     const int ZL = (A0 - (v->T - 1) * R) / 4 * 4, ZR = (A0 + BZ + (v->T - 1) * R + 3) / 4 * 4;
     const int tz = tiles(d.nzp, BZ), ty = tiles(d.ny, BY), tx = tiles(d.nx, chunk);
     heavy.resize((size_t)tz * ty * tx, 0);
-    const int ylo = record ? RT : 0, yhi = record ? RT + BY : H0;
-    const int zlo = record ? A0 : ZL, zhi = record ? A0 + BZ : ZR;
+    // y and z ranges relative to (tile origin - RT, tile origin - A0):
+    // sweep.cuh injects over its layout [0, H0) x [ZL, ZR); the
+    // stage-specialised sweep over its stage-1 region (the tile widened by
+    // (T-1)R rows and (T-1)RP columns); both record over the tile itself
+    int ylo = record ? RT : 0, yhi = record ? RT + BY : H0;
+    int zlo = record ? A0 : ZL, zhi = record ? A0 + BZ : ZR;
+    if (v->kind == 1 && !record) {
+        const int RP = (R + 3) / 4 * 4;
+        ylo = RT - (v->T - 1) * R;
+        yhi = ylo + v->H1;
+        zlo = A0 - (v->T - 1) * RP;
+        zhi = zlo + v->W1;
+    }
     bool any = false;
     for (int x = 0; x < d.nx; ++x) {
         for (int e = t->plane_start[x]; e < t->plane_start[x + 1]; ++e) {
@@ -779,13 +821,22 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         if (j == nsteps) break;
         int limit = nsteps - j;
         if (ckpt != nullptr) limit = std::min(limit, ckpt_every - (j0 + j) % ckpt_every);
-        const SweepVariant *v = plan.v->T <= limit ? plan.v : fallback_variant(R, limit);
+        const SweepVariant *v = plan.v->T <= limit ? plan.v : fallback_variant(R, limit, plan.v->kind);
         if (v == nullptr) return WAVE_EUNSUPPORTED;
         int chunk =
             std::min((v == plan.v && plan.chunk > 0) ? plan.chunk : default_chunk(d, v), max_chunk(v));
         // gradient sweeps: the mode variant of the same untiled shape, if compiled,
         // streams their extra inputs (E, or D and G) through TMA
         const int mode = job.gacc != nullptr ? 2 : (job.dstore != nullptr ? 1 : 0);
+        if (mode > 0 && v->kind == 1) {
+            // the stage-specialised sweep has no second-difference or
+            // imaging-condition mode: the sweep.cuh variant of the same depth
+            // (bitwise the same wavefield) runs the gradient sweeps
+            const SweepVariant *cv = find_variant(R, v->T, 0, 0, 0, 1);
+            if (cv == nullptr) cv = fallback_variant(R, v->T, 0);
+            v = cv;
+            chunk = std::min(plan.chunk_given ? chunk : default_chunk(d, v), max_chunk(v));
+        }
         if (mode > 0 && v->T == 1) {
             const SweepVariant *mv = mode_variant(v, mode);
             if (mv != nullptr) {
@@ -797,8 +848,9 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         }
         SweepArgs a;
         wt::SweepMaps maps;
+        wt::TMaps tmaps;
         long long nblocks = 0;
-        int rc = build_launch(job, s, j, v, chunk, &a, &maps, &nblocks);
+        int rc = build_launch(job, s, j, v, chunk, &a, &maps, &tmaps, &nblocks);
         if (rc) return rc;
         if (job.order != nullptr && (v != ov || chunk != ochunk)) {
             ov = v;
@@ -811,7 +863,10 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
                                    stream));
         }
         a.order = ordered ? job.order : nullptr;
-        CK(v->launch((int)nblocks, stream, a, job.st, maps));
+        if (v->kind == 1)
+            CK(v->launch_t((int)nblocks, stream, a, job.st, tmaps));
+        else
+            CK(v->launch((int)nblocks, stream, a, job.st, maps));
         if (g_prof.active) {
             g_prof.launches++;
             g_prof.steps += v->T;
@@ -887,9 +942,9 @@ int autotune(const Dims &d, const Stencil &st, const float *cB, const float *cC,
     size_t bi = 0;
     for (size_t c = 0; c < cands.size(); ++c) {
         if (tune_log())
-            std::fprintf(stderr, "wave autotune: T=%d tile=%dx%d vec=%d P=%d chunk=%d: %.4f ms/step\n",
-                         cands[c].v->T, cands[c].v->BZ, cands[c].v->BY, cands[c].v->V, cands[c].v->P,
-                         cands[c].chunk, best[c]);
+            std::fprintf(stderr, "wave autotune: kernel=%d T=%d tile=%dx%d vec=%d rows=%d P=%d chunk=%d: %.4f ms/step\n",
+                         cands[c].v->kind + 1, cands[c].v->T, cands[c].v->BZ, cands[c].v->BY, cands[c].v->V,
+                         rows_of(cands[c].v), cands[c].v->P, cands[c].chunk, best[c]);
         // a later candidate must be clearly faster: timings within 1 % are
         // ties, and ties keep the earlier one (the default variant and chunk
         // come first), so run-to-run noise does not flip the plan
@@ -907,11 +962,14 @@ int resolve_plan(const Dims &d, const wave_grid *g, const wave_tuning *t, bool m
 {
     const int R = g->space_order / 2;
     const int T = t ? t->time_tile : 0;
-    if (T < 0 || (t && (t->tile_x < 0 || t->tile_y < 0 || t->vec < 0))) return WAVE_EINVAL;
+    if (T < 0 || (t && (t->tile_x < 0 || t->tile_y < 0 || t->vec < 0 || t->kernel < 0 || t->kernel > 2 ||
+                        t->rows < 0)))
+        return WAVE_EINVAL;
     const bool shape_tune = T > 0 && t && (t->flags & WAVE_AUTOTUNE_SHAPE);
     if (shape_tune && fallback_variant(R, T) == nullptr) return WAVE_EUNSUPPORTED;
     if (T > 0 && !shape_tune) {
-        const SweepVariant *v = find_variant(R, T, t ? t->tile_y : 0, t ? t->vec : 0, t ? t->tile_z : 0);
+        const SweepVariant *v = find_variant(R, T, t ? t->tile_y : 0, t ? t->vec : 0, t ? t->tile_z : 0,
+                                             t ? t->kernel : 0, t ? t->rows : 0);
         if (v == nullptr) return WAVE_EUNSUPPORTED;
         out->v = v;
         out->chunk = (t && t->tile_x > 0) ? std::min(t->tile_x, d.nx) : default_chunk(d, v);
@@ -1070,7 +1128,8 @@ int lock_phase(std::vector<LockShot> &ls, StateOf st_of, int nsteps, const wt::M
             State sp = st_of(i);
             if (p == 1) advance_state(sp, 1);
             long long nb = 0;
-            int rc = build_launch(ls[i].job, sp, 0, v, ls[i].chunk, &row[i].a[p], &row[i].mp[p], &nb);
+            wt::TMaps unused;  // the batched kernel is of the sweep.cuh family
+            int rc = build_launch(ls[i].job, sp, 0, v, ls[i].chunk, &row[i].a[p], &row[i].mp[p], &unused, &nb);
             if (rc) return rc;
             if (nb != ls[i].nblocks) return WAVE_EINVAL;
         }
@@ -1219,8 +1278,9 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
         const MultiVariant *mv = multi_variant(R);
         if (mv == nullptr) return WAVE_EUNSUPPORTED;
         const int tile_y = tuning ? tuning->tile_y : 0, vec = tuning ? tuning->vec : 0;
-        const SweepVariant *v = find_variant(R, 1, tile_y, vec, tuning ? tuning->tile_z : 0);
-        if (tuning == nullptr || tuning->time_tile != 1 || v == nullptr || v->T != mv->T || v->V != mv->V ||
+        const SweepVariant *v = find_variant(R, 1, tile_y, vec, tuning ? tuning->tile_z : 0, 1);
+        if (tuning == nullptr || tuning->time_tile != 1 || tuning->kernel == 2 || v == nullptr ||
+            v->T != mv->T || v->V != mv->V ||
             v->BZ != mv->BZ || v->BY != mv->BY || v->P != mv->P)
             return WAVE_EUNSUPPORTED;
         const bool grad = ckpt_every > 0;
@@ -1333,10 +1393,10 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
 
 bool lockstep_supported(const wave_grid *G, const wave_tuning *tuning)
 {
-    if (G == nullptr || tuning == nullptr || tuning->time_tile != 1) return false;
+    if (G == nullptr || tuning == nullptr || tuning->time_tile != 1 || tuning->kernel == 2) return false;
     const int R = G->space_order / 2;
     const MultiVariant *mv = multi_variant(R);
-    const SweepVariant *v = find_variant(R, 1, tuning->tile_y, tuning->vec, tuning->tile_z);
+    const SweepVariant *v = find_variant(R, 1, tuning->tile_y, tuning->vec, tuning->tile_z, 1);
     return mv != nullptr && v != nullptr && v->V == mv->V && v->BZ == mv->BZ && v->BY == mv->BY &&
            v->P == mv->P;
 }
@@ -1746,13 +1806,15 @@ int32_t wave_list_variants(int32_t space_order, int32_t *out, int32_t max)
     const SweepVariant *vs;
     const int nv = variants_for(space_order / 2, &vs);
     for (int i = 0; i < nv && i < max; ++i) {
-        int32_t *o = out + 6 * i;
+        int32_t *o = out + 8 * i;
         o[0] = vs[i].T;
         o[1] = vs[i].BY;
         o[2] = vs[i].BZ;
         o[3] = vs[i].V;
         o[4] = vs[i].P;
         o[5] = vs[i].threads;
+        o[6] = vs[i].kind + 1;
+        o[7] = rows_of(&vs[i]);
     }
     return nv;
 }
@@ -1772,6 +1834,8 @@ int32_t wave_describe_plan(const wave_grid *g, const wave_tuning *tuning, int32_
     out[3] = p.v->BZ;
     out[4] = p.v->V;
     out[5] = p.v->P;
+    out[6] = p.v->kind + 1;
+    out[7] = rows_of(p.v);
     return WAVE_OK;
 }
 

@@ -5,19 +5,27 @@
 #include <stdint.h>
 
 #include "sweep.cuh"
+#include "tsweep.cuh"
 #include "wave.h"
 
 namespace wt {
 
-// One compiled sweep variant, its layout and its launcher.
+// One compiled sweep variant, its layout and its launcher.  kind 0 is the
+// sweep of sweep.cuh (all stages on the same warps; launch, maps SweepMaps),
+// kind 1 the stage-specialised sweep of tsweep.cuh (launch_t, maps TMaps).
 struct SweepVariant {
     int R, T, V, BZ, BY, P, threads;  // threads: consumers + the producer warp
-    int W0, H0, PW, HK;  // layout width/rows, ring-U pitch, ring-K rows
+    int W0, H0, PW, HK;  // kind 0: layout width/rows, ring-U pitch, ring-K rows
     size_t smem;         // shared memory without the plane_start slices
     cudaError_t (*launch)(int nblocks, cudaStream_t stream, const SweepArgs &a, const Stencil &st,
                           const SweepMaps &m);
     const void *func;
-    int XB;  // extra ring-K boxes of a gradient-mode variant (0: forward and adjoint)
+    int XB;    // extra ring-K boxes of a gradient-mode variant (0: forward and adjoint)
+    int kind;  // 0: sweep.cuh, 1: tsweep.cuh
+    int VY;    // rows per thread (kind 1; kind 0: 1)
+    int W1, H1, WC, HC;  // kind 1: stage-1 region and centre box (columns, rows)
+    cudaError_t (*launch_t)(int nblocks, cudaStream_t stream, const SweepArgs &a, const Stencil &st,
+                            const TMaps &m);
 };
 
 // Variants of radius r (defined in sweep_r<r>.cu).
@@ -124,6 +132,28 @@ cudaError_t launch_sweep(int nblocks, cudaStream_t stream, const SweepArgs &a, c
     return cudaLaunchKernelEx(&cfg, sweep_kernel<R, T, V, BZ, BY, P, MB, XB>, a, st, m);
 }
 
+template <int R, int T, int V, int VY, int BZ, int BY, int P>
+cudaError_t launch_tsweep(int nblocks, cudaStream_t stream, const SweepArgs &a, const Stencil &st,
+                          const TMaps &m)
+{
+    using S = TShape<R, T, V, VY, BZ, BY, P>;
+    const size_t smem = S::smem_bytes(a.chunk);
+    cudaError_t e = allow_max_dynamic_smem((const void *)tsweep_kernel<R, T, V, VY, BZ, BY, P>);
+    if (e != cudaSuccess) return e;
+    // programmatic dependent launch, as launch_sweep
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nblocks);
+    cfg.blockDim = dim3((unsigned)S::NTB);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tsweep_kernel<R, T, V, VY, BZ, BY, P>, a, st, m);
+}
+
 template <int R, int T, int V, int BZ, int BY, int P, int MB>
 cudaError_t launch_sweep_multi(int nblocks, size_t smem, cudaStream_t stream, const ShotSweep *shots,
                                const int2 *block_map, const Stencil &st, int parity, int step)
@@ -167,6 +197,14 @@ cudaError_t launch_sweep_multi(int nblocks, size_t smem, cudaStream_t stream, co
      &wt::launch_sweep<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>,                                      \
      (const void *)&wt::sweep_kernel<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>, XB_},
 
+#define WAVE_TVARIANT_ENTRY(R_, T_, V_, VY_, BZ_, BY_, P_)                                       \
+    {R_, T_, V_, BZ_, BY_, P_, wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_>::NTB, 0, 0, 0, 0,          \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_>::SMEM, nullptr,                                     \
+     (const void *)&wt::tsweep_kernel<R_, T_, V_, VY_, BZ_, BY_, P_>, 0, 1, VY_,                   \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_>::W1, wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_>::H1, \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_>::WC, wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_>::HC, \
+     &wt::launch_tsweep<R_, T_, V_, VY_, BZ_, BY_, P_>},
+
 #define WAVE_DEFINE_MULTI(R_, T_, V_, BZ_, BY_, P_, MB_)                                         \
     namespace wt {                                                                                \
     static const MultiVariant kMulti_r##R_ = {                                                    \
@@ -193,7 +231,8 @@ cudaError_t launch_sweep_multi(int nblocks, size_t smem, cudaStream_t stream, co
 
 #define WAVE_DEFINE_RADIUS(r_)                                                                    \
     namespace wt {                                                                                \
-    static const SweepVariant kVariants_r##r_[] = {WAVE_SWEEP_VARIANTS_R##r_(WAVE_VARIANT_ENTRY)}; \
+    static const SweepVariant kVariants_r##r_[] = {WAVE_SWEEP_VARIANTS_R##r_(WAVE_VARIANT_ENTRY) \
+                                                   WAVE_TSWEEP_VARIANTS_R##r_(WAVE_TVARIANT_ENTRY)}; \
     int sweep_variants_r##r_(const SweepVariant **out)                                            \
     {                                                                                             \
         *out = kVariants_r##r_;                                                                   \

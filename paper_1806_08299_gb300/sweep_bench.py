@@ -28,17 +28,21 @@ def main():
     ap.add_argument("--vec", type=int, default=0)
     ap.add_argument("--tile-z", type=int, default=0)
     ap.add_argument("--tile-x", type=int, default=0, help="x-chunk (0 = default)")
+    ap.add_argument("--kernel", type=int, default=0, help="1 shared-warp, 2 stage-specialised (0 = any)")
+    ap.add_argument("--rows", type=int, default=0, help="rows per thread (0 = any)")
     args = ap.parse_args()
     p = inputs.c2(nt=args.nt, n=(args.n,) * 3)
     grid = wave.Grid(p.n, p.h, p.dt, p.nt, args.so)
     tm, td, tq = (torch.from_numpy(a).cuda() for a in (p.m, p.damp, p.src_q))
     if args.time_tile:
-        cands = [dict(time_tile=args.time_tile, tile_y=args.tile_y, vec=args.vec, tile_z=args.tile_z)]
+        cands = [dict(time_tile=args.time_tile, tile_y=args.tile_y, vec=args.vec, tile_z=args.tile_z,
+                      kernel=args.kernel, rows=args.rows)]
     else:
         cands = wave.list_variants(args.so)
     for v in cands:
         tune = wave.Tuning(time_tile=v["time_tile"], tile_y=v["tile_y"], vec=v["vec"],
-                           tile_x=args.tile_x, flags=wave.WAVE_TIME_SWEEPS, tile_z=v.get("tile_z", 0))
+                           tile_x=args.tile_x, flags=wave.WAVE_TIME_SWEEPS, tile_z=v.get("tile_z", 0),
+                           kernel=v.get("kernel", 0), rows=v.get("rows", 0))
         best = float("inf")
         for _ in range(args.reps):
             _, _, _, ws = wave.fwd(grid, tm, td, p.src_xyz, tq, p.rec_xyz, tuning=tune)

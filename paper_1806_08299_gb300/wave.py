@@ -26,6 +26,7 @@ WAVE_ALLOW_UNSTABLE = 1
 WAVE_TIME_SWEEPS = 2
 WAVE_AUTOTUNE_SHAPE = 4
 WAVE_TEST_WITHHOLD = 256
+WAVE_KERNEL_SHARED, WAVE_KERNEL_STAGED = 1, 2
 WAVE_NOALLOC_MAX_BYTES = 32 * 1024 * 1024
 
 EXPORTED = ["wave_version", "wave_strerror", "wave_fd_coefficients", "wave_cfl_dt",
@@ -58,7 +59,7 @@ class _Shot(ctypes.Structure):
 class _Tuning(ctypes.Structure):
     _fields_ = [("time_tile", ctypes.c_int32), ("tile_y", ctypes.c_int32),
                 ("tile_x", ctypes.c_int32), ("vec", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("tile_z", ctypes.c_int32)]
+                ("tile_z", ctypes.c_int32), ("kernel", ctypes.c_int32), ("rows", ctypes.c_int32)]
 
 
 @dataclass
@@ -83,18 +84,20 @@ class Grid:
 @dataclass
 class Tuning:
     """time_tile: 0 autotune, 1 untiled, T >= 2 time-tile depth; tile_y, vec
-    (z points per thread) and tile_z pick a compiled variant, tile_x its
-    x-chunk."""
+    (z points per thread), tile_z, kernel (WAVE_KERNEL_SHARED / _STAGED) and
+    rows (rows per thread) pick a compiled variant, tile_x its x-chunk."""
     time_tile: int = 0
     tile_y: int = 0
     tile_x: int = 0
     flags: int = 0
     vec: int = 0
     tile_z: int = 0
+    kernel: int = 0
+    rows: int = 0
 
     def c(self):
         return _Tuning(int(self.time_tile), int(self.tile_y), int(self.tile_x), int(self.vec),
-                       int(self.flags), int(self.tile_z))
+                       int(self.flags), int(self.tile_z), int(self.kernel), int(self.rows))
 
 
 _LIB = None
@@ -177,10 +180,11 @@ def cfl_dt(space_order, h, v_max):
     return float(_lib().wave_cfl_dt(int(space_order), hh, float(v_max)))
 
 
-def workspace_bytes(grid, op, nsrc, nrec, ckpt_every=0):
+def workspace_bytes(grid, op, nsrc, nrec, ckpt_every=0, tuning=None):
     g = grid.c()
+    t = tuning.c() if tuning is not None else None
     return int(_lib().wave_workspace_bytes(ctypes.byref(g), int(op), int(nsrc), int(nrec),
-                                           int(ckpt_every), None))
+                                           int(ckpt_every), ctypes.byref(t) if t is not None else None))
 
 
 def ckpt_bytes(grid, ckpt_every):
@@ -194,20 +198,20 @@ def list_variants(space_order):
     n = _lib().wave_list_variants(int(space_order), None, 0)
     if n < 0:
         raise WaveError(n, "wave_list_variants")
-    out = (ctypes.c_int32 * (6 * max(n, 1)))()
+    out = (ctypes.c_int32 * (8 * max(n, 1)))()
     _lib().wave_list_variants(int(space_order), out, n)
-    keys = ("time_tile", "tile_y", "tile_z", "vec", "prefetch", "threads")
-    return [dict(zip(keys, out[6 * i:6 * i + 6])) for i in range(n)]
+    keys = ("time_tile", "tile_y", "tile_z", "vec", "prefetch", "threads", "kernel", "rows")
+    return [dict(zip(keys, out[8 * i:8 * i + 8])) for i in range(n)]
 
 
 def describe_plan(grid, tuning=None):
     g = grid.c()
-    out = (ctypes.c_int32 * 6)()
+    out = (ctypes.c_int32 * 8)()
     t = tuning.c() if tuning is not None else None
     _check(_lib().wave_describe_plan(ctypes.byref(g), ctypes.byref(t) if t else None, out),
            "wave_describe_plan")
     return dict(time_tile=out[0], tile_y=out[1], tile_x=out[2], tile_z=out[3], vec=out[4],
-                prefetch=out[5])
+                prefetch=out[5], kernel=out[6], rows=out[7])
 
 
 # --------------------------------------------------------------------------

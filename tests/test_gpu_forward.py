@@ -26,10 +26,11 @@ def _t(x, dev):
     return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev)
 
 
-def _run(wavelib, dev, grid, m, damp, src, q, rec, T, tile_x=0, tile_y=0):
+def _run(wavelib, dev, grid, m, damp, src, q, rec, T, tile_x=0, tile_y=0, kernel=0, rows=0):
     import torch
     d, ul, _, ws = wavelib.fwd(grid, _t(m, dev), _t(damp, dev), src, _t(q, dev) if len(src) else None,
-                               rec, tuning=wavelib.Tuning(time_tile=T, tile_x=tile_x, tile_y=tile_y),
+                               rec, tuning=wavelib.Tuning(time_tile=T, tile_x=tile_x, tile_y=tile_y,
+                                                          kernel=kernel, rows=rows),
                                want_u_last=True)
     assert wavelib.status(ws) == 0
     torch.cuda.synchronize()
@@ -222,7 +223,8 @@ def test_every_compiled_variant(wavelib, cuda, oracle, so):
         import torch
         dv, uv, _, ws = wavelib.fwd(grid, _t(m, cuda), _t(damp, cuda), src, _t(q, cuda), rec,
                                     tuning=wavelib.Tuning(time_tile=v["time_tile"], tile_y=v["tile_y"],
-                                                          vec=v["vec"], tile_z=v["tile_z"]),
+                                                          vec=v["vec"], tile_z=v["tile_z"],
+                                                          kernel=v["kernel"], rows=v["rows"]),
                                     want_u_last=True)
         assert wavelib.status(ws) == 0
         torch.cuda.synchronize()
@@ -263,8 +265,9 @@ def test_chunk_sizes_in_any_order(wavelib, cuda, oracle):
         assert _relerr(ul[0], uref[0]) <= TOL
 
 
-@pytest.mark.parametrize("so,T", [(2, 1), (2, 2), (2, 4), (8, 1), (16, 1)])
-def test_dense_receiver_carpet(wavelib, cuda, oracle, so, T):
+@pytest.mark.parametrize("so,T,kernel", [(2, 1, 0), (2, 2, 0), (2, 4, 0), (8, 1, 0), (16, 1, 0),
+                                         (4, 2, 2), (8, 2, 2), (8, 1, 2)])
+def test_dense_receiver_carpet(wavelib, cuda, oracle, so, T, kernel):
     """A carpet of receivers: a 21 x 23 grid of off-grid points at one depth
     plus a few more scattered points, so that one block holds hundreds of
     record entries across its planes (more than it has threads), several
@@ -279,10 +282,45 @@ def test_dense_receiver_carpet(wavelib, cuda, oracle, so, T):
     rec = (np.concatenate([carpet, extra]) * inputs.H).astype(np.float32)
     dt = 0.4 * wavelib.cfl_dt(so, (inputs.H,) * 3, 3.0)
     grid = wavelib.Grid(n, (inputs.H,) * 3, dt, nt, so)
-    d, ul = _run(wavelib, cuda, grid, m, damp, src, q, rec, T, tile_x=12)
+    d, ul = _run(wavelib, cuda, grid, m, damp, src, q, rec, T, tile_x=12, kernel=kernel)
     dref, uref, _ = _oracle(oracle, grid, m, damp, src, q, rec)
     assert np.abs(d - dref).max() <= TOL * np.abs(dref).max()
     assert _relerr(ul[0], uref[0]) <= TOL
-    if T > 1:
-        d1, ul1 = _run(wavelib, cuda, grid, m, damp, src, q, rec, 1)
+    if T > 1 or kernel:
+        d1, ul1 = _run(wavelib, cuda, grid, m, damp, src, q, rec, 1, kernel=wavelib.WAVE_KERNEL_SHARED)
         assert np.array_equal(d, d1) and np.array_equal(ul, ul1)
+
+
+@pytest.mark.parametrize("so", [4, 8])
+def test_staged_kernel_splits_bitwise(wavelib, cuda, oracle, so):
+    """The stage-specialised sweep (each time step of a tile on its own
+    warps) at T = 1 and 2 and both rows-per-thread shapes, with x-chunks from
+    5 planes (shorter than the stencil reach 2RT) to the whole grid and an
+    odd step count (the last step of T = 2 falls back to T = 1): bitwise
+    equal to the untiled sweep of the other kernel family, which is at parity
+    with the oracle.  Sources sit on chunk and tile boundaries."""
+    n = (41, 53, 61)
+    nt = 11
+    m, damp, src, q, rec = inputs.random_problem(n, so, nt, seed=90 + so, nsrc=3, nrec=9)
+    src[0] = np.array([10.0, 16.0, 28.0], np.float32) * inputs.H  # on x/y/z tile edges
+    src[1] = np.array([20.5, 15.5, 27.5], np.float32) * inputs.H
+    dt = 0.4 * wavelib.cfl_dt(so, (inputs.H,) * 3, 3.0)
+    grid = wavelib.Grid(n, (inputs.H,) * 3, dt, nt, so)
+    d1, u1 = _run(wavelib, cuda, grid, m, damp, src, q, rec, 1, kernel=wavelib.WAVE_KERNEL_SHARED)
+    dref, uref, _ = _oracle(oracle, grid, m, damp, src, q, rec)
+    assert _relerr(u1[0], uref[0]) <= TOL
+    assert np.abs(d1 - dref).max() <= TOL * np.abs(dref).max()
+    shapes = [(v["time_tile"], v["rows"], v["tile_y"], v["tile_z"]) for v in wavelib.list_variants(so)
+              if v["kernel"] == wavelib.WAVE_KERNEL_STAGED]
+    assert shapes
+    for T, rows, ty, tz in shapes:
+        for tile_x in (5, 10, 23, n[0]):
+            import torch
+            d, ul, _, ws = wavelib.fwd(grid, _t(m, cuda), _t(damp, cuda), src, _t(q, cuda), rec,
+                                       tuning=wavelib.Tuning(time_tile=T, tile_x=tile_x, tile_y=ty, tile_z=tz,
+                                                             kernel=wavelib.WAVE_KERNEL_STAGED, rows=rows),
+                                       want_u_last=True)
+            assert wavelib.status(ws) == 0
+            torch.cuda.synchronize()
+            assert np.array_equal(ul.cpu().numpy(), u1), (T, rows, ty, tz, tile_x)
+            assert np.array_equal(d.cpu().numpy(), d1), (T, rows, ty, tz, tile_x)
