@@ -340,7 +340,7 @@ def run_ours(args):
         fwd(tune)
         pl = wave.describe_plan(grid, tune)
         return wave.Tuning(time_tile=pl["time_tile"], tile_y=pl["tile_y"], tile_x=pl["tile_x"],
-                           vec=pl["vec"], tile_z=pl["tile_z"])
+                           vec=pl["vec"], tile_z=pl["tile_z"], kernel=pl["kernel"], rows=pl["rows"])
     if args.time_tile:
         tiled = tuned(wave.Tuning(time_tile=args.time_tile, flags=wave.WAVE_AUTOTUNE_SHAPE))
     else:
@@ -352,7 +352,7 @@ def run_ours(args):
     plan = wave.describe_plan(grid, tiled)
     uplan = wave.describe_plan(grid, untiled)
     prof = wave.Tuning(tiled.time_tile, tiled.tile_y, tiled.tile_x, wave.WAVE_TIME_SWEEPS, tiled.vec,
-                       tiled.tile_z)
+                       tiled.tile_z, tiled.kernel, tiled.rows)
 
     # --- device-timed, inputs resident: tiled sweep (headline) -------------
     for _ in range(args.warmup):
@@ -585,7 +585,7 @@ def _orders_sweep(dev, inputs, wave, args):
             fwd(t)
             pl = wave.describe_plan(grid, t)
             fixed = wave.Tuning(time_tile=pl["time_tile"], tile_y=pl["tile_y"], tile_x=pl["tile_x"],
-                                vec=pl["vec"], tile_z=pl["tile_z"])
+                                vec=pl["vec"], tile_z=pl["tile_z"], kernel=pl["kernel"], rows=pl["rows"])
             fwd(fixed)
             ms, _ = _timed(lambda: fwd(fixed), 1, stream)
             g = pts / (ms / 1e3) / 1e9
@@ -645,7 +645,8 @@ def _laplace_sweep(dev, inputs, wave, args):
             run(t)
             pl = wave.describe_plan(grid, t)
             fixed = wave.Tuning(time_tile=pl["time_tile"], tile_y=pl["tile_y"], tile_x=pl["tile_x"],
-                                vec=pl["vec"], flags=wave.WAVE_TIME_SWEEPS, tile_z=pl["tile_z"])
+                                vec=pl["vec"], flags=wave.WAVE_TIME_SWEEPS, tile_z=pl["tile_z"],
+                                kernel=pl["kernel"], rows=pl["rows"])
             run(fixed)
             best = float("inf")
             for _ in range(3):  # the sweeps alone (16 steps leave per-call set-up visible)

@@ -304,6 +304,15 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// Ask for the box of `map` at (c0, c1, c2) to be brought into L2 (no shared
+// memory, no barrier): a later tma_load_3d of it then waits for L2, not HBM.
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *map, int c0, int c1, int c2)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"((uint64_t)map),
+                 "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
+
 // V consecutive floats as V/2 pairs (shared or global memory; 16-byte
 // aligned for V >= 4, 8-byte for V = 2).
 template <int V>

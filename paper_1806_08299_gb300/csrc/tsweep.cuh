@@ -75,6 +75,12 @@ struct TShape {
     static constexpr int LZ2 = BZ / V, LY2 = BY / VY;     // stage-2 thread grid
     static constexpr int N2 = T == 2 ? (LZ2 * LY2 + 31) / 32 * 32 : 0;
     static constexpr int NTB = N1 + N2 + 32;              // + the producer warp
+    // L2 prefetch distance in iterations (0: none).  With one slot of
+    // lookahead (P = 1) a ring-A load is issued about one iteration before
+    // its use, which does not cover HBM latency, so its inputs are first
+    // brought into L2 four iterations ahead; with P >= 2 the ring itself
+    // covers the latency and the extra requests only cost.
+    static constexpr int LP = P == 1 ? 4 : 0;
     static constexpr int DA = P + 1;                      // ring A slots
     static constexpr int DB = T == 2 ? P + 1 : 0;         // ring B slots
     static constexpr int D1 = T == 2 ? R + 3 : 0;         // ring 1 planes
@@ -104,7 +110,7 @@ struct TShape {
     static_assert(WC <= 256 && HC <= 256, "TMA box dimension above 256");
     static_assert(TXA < (1u << 20), "mbarrier tx count");
     static_assert(NTB <= 1024, "too many threads per block");
-    static_assert(SMEM <= 200 * 1024, "shared memory above the per-block limit");
+    static_assert(SMEM <= 215 * 1024, "shared memory above the per-block limit");
 };
 
 // Level n+1 of a thread's VY x V points (VY rows, V/2 pairs each) from the
@@ -405,6 +411,18 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                     tma_load_3d(sl + S::A_B, &mp.B, gz0, gy0, c0 - R, fullA + s);
                     tma_load_3d(sl + S::A_CC, &mp.C, gz0, gy0, c0 - R, fullA + s);
                 }
+                // bring the first-touch inputs of iteration i + LP into L2, so
+                // that its loads above wait for L2 rather than HBM (the centre
+                // box is the level-n plane that entered as feed R iterations
+                // before it is used, and ring B re-reads planes ring A loaded)
+                if (S::LP > 0 && i + S::LP < niter) {
+                    tma_prefetch_3d(&mp.uf, gz0, gy0, c0 + S::LP);
+                    if (i + S::LP >= 2 * R) {
+                        tma_prefetch_3d(&mp.um, gz0, gy0, c0 + S::LP - R);
+                        tma_prefetch_3d(&mp.B, gz0, gy0, c0 + S::LP - R);
+                        tma_prefetch_3d(&mp.C, gz0, gy0, c0 + S::LP - R);
+                    }
+                }
                 if (++s == S::DA) { s = 0; ++r; }
             }
             // no copy into this block's shared memory may still be in flight
@@ -460,7 +478,9 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
         int sa = 0;
         uint32_t pa = 0;
         int s1 = 0, r1 = 0;  // ring-1 slot of the next stage-1 plane, and its round
-#pragma unroll 1
+        // unrolled by three: the x-queue shift of each copy becomes register
+        // renaming, and only the shift by three at the loop edge moves values
+#pragma unroll 3
         for (int i = 0; i < niter; ++i) {
             if (!__all_sync(FULL, mbar_wait_bounded(fullA + sa, pa))) {
                 if (lane0) tstage_abort(abort_flag, a.status);
@@ -538,7 +558,7 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
             int sc = 0;            // ring-1 slot of the centre plane (produced R iterations earlier)
             int sb = 0;
             uint32_t pb = 0;
-#pragma unroll 1
+#pragma unroll 3  // as stage 1
             for (int i = 2 * R; i < niter; ++i) {
                 if (!__all_sync(FULL, mbar_wait_bounded(full1 + s1, p1))) {
                     if (lane0) tstage_abort(abort_flag, a.status);
@@ -618,8 +638,10 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
     }
 }
 
+// Untiled blocks are small (one warp group), so two of them are asked to fit
+// on an SM; a depth-2 block fills the SM's registers alone.
 template <int R, int T, int V, int VY, int BZ, int BY, int P>
-__global__ void __launch_bounds__(TShape<R, T, V, VY, BZ, BY, P>::NTB, 1)
+__global__ void __launch_bounds__(TShape<R, T, V, VY, BZ, BY, P>::NTB, T == 1 ? 2 : 1)
 tsweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stencil st,
               const __grid_constant__ TMaps mp)
 {

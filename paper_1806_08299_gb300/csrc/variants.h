@@ -43,16 +43,17 @@
 // C over the stage-1 region), for T = 2 also P+1 slots of the stage-2 inputs
 // over the tile and R+3 planes of level n+1 handed from stage 1 to stage 2.
 #define WAVE_TSWEEP_VARIANTS_R1(Z)
-#define WAVE_TSWEEP_VARIANTS_R2(Z) \
-    Z(2, 1, 4, 1, 64, 8, 2) Z(2, 2, 4, 1, 56, 16, 2) Z(2, 2, 4, 2, 56, 24, 2) Z(2, 2, 4, 2, 120, 12, 1)
+#define WAVE_TSWEEP_VARIANTS_R2(Z)                                                                 \
+    Z(2, 1, 4, 1, 64, 8, 2) Z(2, 1, 4, 2, 64, 16, 2) Z(2, 2, 4, 2, 56, 24, 2) Z(2, 2, 4, 2, 120, 12, 1) \
+    Z(2, 2, 4, 2, 128, 12, 1) Z(2, 2, 4, 2, 64, 24, 1) Z(2, 2, 4, 1, 56, 16, 2)
 #define WAVE_TSWEEP_VARIANTS_R3(Z)
-#define WAVE_TSWEEP_VARIANTS_R4(Z) \
-    Z(4, 1, 4, 1, 64, 8, 2) Z(4, 1, 4, 2, 64, 16, 2) Z(4, 2, 4, 1, 56, 16, 2) Z(4, 2, 4, 2, 56, 16, 2) \
-    Z(4, 2, 4, 2, 56, 24, 1)
+#define WAVE_TSWEEP_VARIANTS_R4(Z)                                                                 \
+    Z(4, 1, 4, 1, 64, 8, 2) Z(4, 1, 4, 2, 64, 16, 2) Z(4, 2, 4, 2, 56, 24, 1) Z(4, 2, 4, 2, 64, 24, 1) \
+    Z(4, 2, 4, 2, 32, 32, 2) Z(4, 2, 4, 2, 56, 16, 2) Z(4, 2, 4, 1, 56, 16, 2)
 #define WAVE_TSWEEP_VARIANTS_R5(Z)
-#define WAVE_TSWEEP_VARIANTS_R6(Z)
+#define WAVE_TSWEEP_VARIANTS_R6(Z) Z(6, 1, 4, 1, 64, 8, 2) Z(6, 1, 4, 2, 64, 16, 2)
 #define WAVE_TSWEEP_VARIANTS_R7(Z)
-#define WAVE_TSWEEP_VARIANTS_R8(Z)
+#define WAVE_TSWEEP_VARIANTS_R8(Z) Z(8, 1, 4, 1, 64, 8, 2) Z(8, 1, 4, 2, 64, 16, 2)
 
 // Gradient-mode variants Y(R, T, V, BZ, BY, P, MB, XB): the untiled default
 // shape of a radius with XB extra ring-K boxes (1: E for the second-difference

@@ -38,7 +38,7 @@ def main():
         cands = [dict(time_tile=args.time_tile, tile_y=args.tile_y, vec=args.vec, tile_z=args.tile_z,
                       kernel=args.kernel, rows=args.rows)]
     else:
-        cands = wave.list_variants(args.so)
+        cands = [v for v in wave.list_variants(args.so) if args.kernel in (0, v["kernel"])]
     for v in cands:
         tune = wave.Tuning(time_tile=v["time_tile"], tile_y=v["tile_y"], vec=v["vec"],
                            tile_x=args.tile_x, flags=wave.WAVE_TIME_SWEEPS, tile_z=v.get("tile_z", 0),
