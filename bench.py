@@ -275,9 +275,10 @@ def _model_line(space_order, plan):
     per point-update (paper_1806_08299_gb300.traffic_model)."""
     from paper_1806_08299_gb300 import traffic_model as tm
     shape = tm.Shape(R=space_order // 2, T=plan["time_tile"], V=plan["vec"], BZ=plan["tile_z"],
-                     BY=plan["tile_y"])
+                     BY=plan["tile_y"], kernel=plan["kernel"])
     return {"dram_bytes_per_point": tm.dram_bytes_per_update(plan["time_tile"]),
-            "l2_bytes_per_point": tm.l2_bytes_per_update(shape)}
+            "l2_bytes_per_point": tm.l2_bytes_per_update(shape),
+            "stage_points_per_update": shape.stage_points_per_update()}
 
 
 def _per_call(fn, n, stream):
@@ -334,27 +335,30 @@ def run_ours(args):
         return max_over_ranks(x, dist, dev)
 
     # autotune once (outside any timed region), then fix the plans: the
-    # time-tiled sweep over every depth and shape, the untiled baseline over
-    # every T = 1 shape
+    # product plan (every depth, shape and kernel family), the fastest untiled
+    # sweep (every T = 1 shape of both families) and the fastest time-tiled
+    # sweep (every T >= 2 shape of both families)
     def tuned(tune):
         fwd(tune)
         pl = wave.describe_plan(grid, tune)
         return wave.Tuning(time_tile=pl["time_tile"], tile_y=pl["tile_y"], tile_x=pl["tile_x"],
                            vec=pl["vec"], tile_z=pl["tile_z"], kernel=pl["kernel"], rows=pl["rows"])
+
+    def timing(t):
+        return wave.Tuning(t.time_tile, t.tile_y, t.tile_x, wave.WAVE_TIME_SWEEPS, t.vec, t.tile_z,
+                           t.kernel, t.rows)
     if args.time_tile:
         tiled = tuned(wave.Tuning(time_tile=args.time_tile, flags=wave.WAVE_AUTOTUNE_SHAPE))
     else:
         tiled = tuned(wave.Tuning(time_tile=0))
     untiled = tuned(wave.Tuning(time_tile=1, flags=wave.WAVE_AUTOTUNE_SHAPE))
-    deep = None  # fastest compiled shape of time-tile depth 2, reported beside the headline
-    if any(v["time_tile"] == 2 for v in wave.list_variants(p.space_order)):
-        deep = tuned(wave.Tuning(time_tile=2, flags=wave.WAVE_AUTOTUNE_SHAPE))
+    depths = sorted({v["time_tile"] for v in wave.list_variants(p.space_order) if v["time_tile"] >= 2})
+    deep_plans = [tuned(wave.Tuning(time_tile=T, flags=wave.WAVE_AUTOTUNE_SHAPE)) for T in depths]
     plan = wave.describe_plan(grid, tiled)
     uplan = wave.describe_plan(grid, untiled)
-    prof = wave.Tuning(tiled.time_tile, tiled.tile_y, tiled.tile_x, wave.WAVE_TIME_SWEEPS, tiled.vec,
-                       tiled.tile_z, tiled.kernel, tiled.rows)
+    prof = timing(tiled)
 
-    # --- device-timed, inputs resident: tiled sweep (headline) -------------
+    # --- device-timed, inputs resident: the product plan (headline) --------
     for _ in range(args.warmup):
         fwd(prof)
     sampler = ClockSampler(local)
@@ -368,28 +372,30 @@ def run_ours(args):
     sweep_ms = sum(s[0] for s in stats)
     launches = sum(s[1] for s in stats)
 
-    # --- untiled sweep, same workload --------------------------------------
-    for _ in range(max(1, args.warmup)):
-        fwd(untiled)
-    barrier()
-    ms_u, _ = _timed(lambda: fwd(untiled), args.steps, stream)
-    ms_u = slowest(ms_u)
-    untiled_gpts = whole_job_rate(pts, args.steps, ms_u, world)
-
-    # --- the fastest time-tiled (T >= 2) plan, same workload ----------------
-    deep_line = None
-    if deep is not None:
-        fwd(deep)
+    def side(t):
+        """The same workload on a fixed plan: whole-call rate and the mean
+        duration of its sweep launches."""
+        tt = timing(t)
+        fwd(tt)
         barrier()
-        ms_d, _ = _timed(lambda: fwd(deep), args.steps, stream)
-        ms_d = slowest(ms_d)
-        deep_line = {"gpts": whole_job_rate(pts, args.steps, ms_d, world),
-                     "plan": wave.describe_plan(grid, deep)}
+        ms_s, st = _timed(lambda: fwd(tt), args.steps, stream)
+        ms_s = slowest(ms_s)
+        pl = wave.describe_plan(grid, t)
+        sw = sum(x[0] for x in st)
+        nl = sum(x[1] for x in st)
+        return {"gpts": whole_job_rate(pts, args.steps, ms_s, world), "plan": pl,
+                "avg_launch_ms": sw / max(nl, 1), "launches_per_call": nl // max(args.steps, 1)}
+
+    # --- the fastest untiled and time-tiled plans, same workload ------------
+    untiled_line = side(untiled)
+    untiled_gpts = untiled_line["gpts"]
+    deep_lines = [side(t) for t in deep_plans]
+    deep_line = max(deep_lines, key=lambda r: r["gpts"]) if deep_lines else None
 
     # --- spread over single calls (after the timed region) -----------------
     spread = None
     if args.spread_runs > 0:
-        spread = {"tiled": _spread(_per_call(lambda: fwd(tiled), args.spread_runs, stream), pts),
+        spread = {"product": _spread(_per_call(lambda: fwd(tiled), args.spread_runs, stream), pts),
                   "untiled": _spread(_per_call(lambda: fwd(untiled), args.spread_runs, stream), pts)}
 
     # --- end to end through the C ABI with host buffers --------------------
@@ -427,26 +433,43 @@ def run_ours(args):
     if args.laplace and world == 1:
         laplace = _laplace_sweep(dev, inputs, wave, args)
 
-    # --- roofline of the sweep kernel --------------------------------------
+    # --- roofline of the sweep kernels ---------------------------------------
     hbm, peak_kind = _peaks()
     fp32_tflops, smem_tbs = wave.measure_peaks()
     flops_per_pt = 7 * (p.space_order // 2) + 10  # per radius 6 adds + 1 FMA; centre and update
-    T = plan["time_tile"]
-    bytes_per_pt = 24 if T >= 2 else 20  # read u^n, u^{n-1}, B, C; write 2 levels (1 if untiled)
-    alg_bytes = float(np.prod(p.n)) * bytes_per_pt
-    avg_launch_ms = sweep_ms / max(launches, 1)
-    achieved = alg_bytes / (avg_launch_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm,
-                "traffic": args.traffic if args.traffic is not None else _traffic(p.space_order, plan, p.n),
-                "peak_kind": peak_kind,
-                "kernel": "sweep_kernel<R=%d,T=%d>" % (p.space_order // 2, T),
-                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_ms,
+
+    def roof(pl, avg_ms, traffic=None):
+        """Algorithmic HBM bytes of one launch (24 B per point for a time tile
+        -- read u^n, u^{n-1}, B, C, write two levels -- 20 B untiled) over its
+        mean duration, against the measured copy bandwidth; and the same
+        launch's point-updates against the FP32 FMA roof at F(r) flops each."""
+        T = pl["time_tile"]
+        bpp = 24 if T >= 2 else 20
+        alg = float(np.prod(p.n)) * bpp
+        ach = alg / (avg_ms / 1e3) / 1e9
+        gpts = float(np.prod(p.n)) * T / (avg_ms / 1e3) / 1e9
+        alu_roof = fp32_tflops * 1e3 / flops_per_pt
+        fam = "tsweep_kernel" if pl["kernel"] == wave.WAVE_KERNEL_STAGED else "sweep_kernel"
+        return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "%s<R=%d,T=%d>" % (fam, p.space_order // 2, T),
+                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": avg_ms,
+                "hbm_roof_gpts": hbm / (bpp / T), "sweep_gpts": gpts,
                 "alu": {"fp32_tflops_measured": fp32_tflops, "flops_per_point": flops_per_pt,
-                        "roof_gpts": fp32_tflops * 1e3 / flops_per_pt,
-                        "hbm_roof_gpts": hbm / bytes_per_pt},
+                        "roof_gpts": alu_roof, "frac": gpts / alu_roof},
                 "smem_tbs_measured": smem_tbs,
-                "model": _model_line(p.space_order, plan)}
+                "model": _model_line(p.space_order, pl)}
+
+    T = plan["time_tile"]
+    avg_launch_ms = sweep_ms / max(launches, 1)
+    roofline = roof(plan, avg_launch_ms,
+                    args.traffic if args.traffic is not None else _traffic(p.space_order, plan, p.n))
+    untiled_line["roofline"] = roof(uplan, untiled_line["avg_launch_ms"])
+    if deep_line is not None:
+        deep_line["roofline"] = roof(deep_line["plan"], deep_line["avg_launch_ms"])
+        deep_line["tiled_over_untiled"] = deep_line["gpts"] / untiled_gpts
+        deep_line["all_depths"] = [{"time_tile": r["plan"]["time_tile"], "gpts": r["gpts"]}
+                                   for r in deep_lines]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -459,13 +482,11 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": desc, "l2": "inputs larger than L2 (512 MiB per field)",
-                       "time_tile": T, "tile_y": plan["tile_y"], "tile_z": plan["tile_z"],
-                       "tile_x": plan["tile_x"], "vec": plan["vec"], "untiled_gpts": untiled_gpts,
-                       "untiled_plan": uplan,
-                       "tiled_over_untiled": value / untiled_gpts,
-                       "best_time_tiled": deep_line,
-                       "per_call_spread": spread,
+                       "plan": plan, "per_call_spread": spread,
                        "parallelism": "replicas" if world > 1 else "single"},
+            "untiled": untiled_line,
+            "time_tiled": deep_line,
+            "tiled_over_untiled": deep_line["tiled_over_untiled"] if deep_line else None,
             "e2e": {"value": whole_job_rate(pts, args.steps, ms_e, world), "unit": "GPts/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roofline,
@@ -529,7 +550,7 @@ def _fwi_survey(dev, inputs, wave, args):
              for x in sv.shots]
     q = [torch.from_numpy(x).to(dev) for x in sv.src_q]
     k = 50
-    conc = min(len(shots), 16)  # every shot of the sample in one lockstep group
+    conc = min(len(shots), 8)  # shots per lockstep group (8 groups of 8 for the whole survey)
     tune = wave.Tuning(time_tile=1)
     ws_f = torch.empty(wave.batch_workspace_bytes(grid, shots, 0, conc), dtype=torch.uint8, device=dev)
     ws_g = torch.empty(wave.batch_workspace_bytes(grid, shots, k, conc), dtype=torch.uint8, device=dev)
@@ -545,7 +566,7 @@ def _fwi_survey(dev, inputs, wave, args):
     ms, _ = _timed(step, 1, torch.cuda.current_stream())
     pts = sum(int(np.prod(x["n"])) for x in sv.shots)
     return {"s_per_shot": ms / 1e3 / len(shots),
-            "workload": "c5: first %d of 64 shots (windows of a 512x512x256 layered model), so8, "
+            "workload": "c5: %d of 64 shots (windows of a 512x512x256 layered model), so8, "
                         "%d steps, k = %d, %d shots per lockstep group (one launch per time step, CUDA graph); "
                         "batched forward + batched gradient"
                         % (len(shots), sv.nt, k, conc),
@@ -679,14 +700,14 @@ def main():
     ap.add_argument("--time-tile", type=int, default=0)
     ap.add_argument("--no-fwi", dest="fwi", action="store_false")
     ap.add_argument("--no-survey", dest="survey", action="store_false")
-    ap.add_argument("--survey-shots", type=int, default=8)
+    ap.add_argument("--survey-shots", type=int, default=64)
     ap.add_argument("--survey-nt", type=int, default=1500)
     ap.add_argument("--no-orders", dest="orders", action="store_false")
     ap.add_argument("--no-laplace", dest="laplace", action="store_false")
     ap.add_argument("--laplace-n", type=int, default=600)
     ap.add_argument("--spread-runs", type=int, default=10,
                     help="single calls timed one by one after the timed region (min / median)")
-    ap.add_argument("--orders-nt", type=int, default=100)
+    ap.add_argument("--orders-nt", type=int, default=500)
     ap.add_argument("--fwi-nt", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,

@@ -22,13 +22,16 @@ from dataclasses import dataclass
 @dataclass(frozen=True)
 class Shape:
     """A compiled sweep shape: radius R, depth T, z-points per thread V,
-    output tile BZ x BY, gradient-mode extra boxes XB."""
+    output tile BZ x BY, gradient-mode extra boxes XB, kernel family
+    (1: every stage of a tile on the same warps, sweep.cuh; 2: one group of
+    warps per stage, tsweep.cuh)."""
     R: int
     T: int
     V: int
     BZ: int
     BY: int
     XB: int = 0
+    kernel: int = 1
 
     @property
     def RT(self):
@@ -62,6 +65,23 @@ class Shape:
     def split(self):
         return self.T == 1 and self.R >= 3        # no ring U: centre and x-queue boxes per slot
 
+    # the stage-specialised sweep: stage 1 covers the tile widened by the
+    # halo stage 2 reads, (T-1)R rows and (T-1)RP columns per side
+    @property
+    def W1(self):
+        return self.BZ + 2 * (self.T - 1) * self.RP
+
+    @property
+    def H1(self):
+        return self.BY + 2 * (self.T - 1) * self.R
+
+    def stage_points_per_update(self):
+        """Point updates computed per output point-update: stage 1 repeats
+        the halo that stage 2 reads."""
+        if self.kernel == 2:
+            return (self.W1 * self.H1 + (self.T - 1) * self.BZ * self.BY) / (self.T * self.BZ * self.BY)
+        return 1.0
+
 
 def dram_bytes_per_update(T, mode="wave"):
     """Algorithmic DRAM bytes per point-update of one sweep of depth T.
@@ -80,6 +100,13 @@ def dram_bytes_per_update(T, mode="wave"):
 
 def l2_bytes_per_update(s):
     """Bytes a block loads from L2 through TMA per output point-update."""
+    if s.kernel == 2:
+        # per plane: the centre box of stage 1 (its region with the stencil
+        # halo), level n, n-1, B and C over its region, and for T = 2 level
+        # n, B and C over the tile for stage 2
+        cbox = 4 * (s.W1 + 2 * s.RP) * (s.H1 + 2 * s.R)
+        per_plane = cbox + 4 * 4 * s.W1 * s.H1 + (3 * 4 * s.BZ * s.BY if s.T == 2 else 0)
+        return per_plane / (s.BZ * s.BY * s.T)
     ubox = 4 * s.PW * s.H0                       # haloed level-n plane
     kbox = 4 * s.W0 * s.HK                       # u^{n-1}, B, C (and XB extras) per plane
     per_plane = ubox + (3 + s.XB) * kbox + (kbox if s.split else 0)

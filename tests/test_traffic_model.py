@@ -32,3 +32,17 @@ def test_l2_bytes_fall_with_tile_size_and_depth_shares_the_load():
     s = tm.Shape(R=2, T=1, V=8, BZ=64, BY=16)
     assert not s.split
     assert tm.l2_bytes_per_update(s) == (4 * s.PW * s.H0 + 3 * 4 * s.W0 * s.HK) / (64 * 16)
+
+
+def test_staged_shape_boxes_and_redundancy():
+    # depth-2 staged 64 x 24 tile at so 8: stage 1 covers 72 x 32 (RP = 4 columns,
+    # R = 4 rows per side), its centre box 80 x 40; stage 2 loads three 64 x 24 boxes
+    s = tm.Shape(R=4, T=2, V=4, BZ=64, BY=24, kernel=2)
+    assert (s.W1, s.H1) == (72, 32)
+    per_plane = 4 * 80 * 40 + 4 * 4 * 72 * 32 + 3 * 4 * 64 * 24
+    assert tm.l2_bytes_per_update(s) == per_plane / (64 * 24 * 2)
+    assert s.stage_points_per_update() == (72 * 32 + 64 * 24) / (2 * 64 * 24)
+    # the untiled staged sweep computes each point once and loads its own tile
+    u = tm.Shape(R=4, T=1, V=4, BZ=64, BY=16, kernel=2)
+    assert (u.W1, u.H1, u.stage_points_per_update()) == (64, 16, 1.0)
+    assert tm.l2_bytes_per_update(u) == (4 * 72 * 24 + 4 * 4 * 64 * 16) / (64 * 16)
