@@ -38,36 +38,41 @@ HBM_FALLBACK_GBS = 6800.0
 
 # DRAM traffic of one launch of the bench's sweep at full size
 # (dram__bytes_read.sum + dram__bytes_write.sum from one single-pass ncu capture;
-# profiles/traffic_sweep_t1_so8_512.md), valid only for the kernel sources it was
-# taken on: the SHA-256 of csrc/sweep.cuh + the radius-4 variant list must match,
-# else the bench reports null.
-TRAFFIC_SRC_SHA256 = "37d44d9d9a35ac45b636cf5dd5e1819d3356df6966f44508c1998b5922a555b9"
-TRAFFIC_BYTES = {  # ("R T V BZ BY P", chunk, n) -> bytes per launch
-    ("R4 T1 V4 BZ64 BY8 P2", 74, (512, 512, 512)): 2173332224 + 518286336,
+# profiles/traffic_tsweep_t2_so8_512.md), valid only for the kernel sources it was
+# taken on: the SHA-256 of csrc/sweep.cuh, csrc/tsweep.cuh and the radius-4
+# variant lists must match, else the bench reports null.
+TRAFFIC_SRC_SHA256 = "089368b8f2fc9c2566b43ec08f0506407be91301a132c4cad407e58474e4138a"
+TRAFFIC_BYTES = {  # ("family R T V rows BZ BY P", chunk, n) -> bytes per launch
+    ("staged R4 T2 V4 rows2 BZ64 BY24 P1", 103, (512, 512, 512)): 2532920320 + 1047564544,
 }
 
 
 def _kernel_sha256():
-    """SHA-256 of what the bench kernel is built from: csrc/sweep.cuh and the
-    radius-4 variant list of csrc/variants.h (other radii do not change it)."""
+    """SHA-256 of what the bench kernel is built from: csrc/sweep.cuh (its
+    PTX helpers), csrc/tsweep.cuh and the radius-4 variant lists of
+    csrc/variants.h (other radii do not change it)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1806_08299_gb300", "csrc")
-    with open(os.path.join(csrc, "sweep.cuh"), "rb") as fh:
-        h.update(fh.read())
+    for f in ("sweep.cuh", "tsweep.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     with open(os.path.join(csrc, "variants.h"), "r") as fh:
         text = fh.read()
-    a = text.index("#define WAVE_SWEEP_VARIANTS_R4(")
-    b = text.index("#define", a + 1)
-    h.update(text[a:b].encode())
+    for key in ("#define WAVE_SWEEP_VARIANTS_R4(", "#define WAVE_TSWEEP_VARIANTS_R4("):
+        a = text.index(key)
+        b = text.index("#define", a + 1)
+        h.update(text[a:b].encode())
     return h.hexdigest()
 
 
 def _traffic(space_order, plan, n):
     if TRAFFIC_SRC_SHA256 is None or _kernel_sha256() != TRAFFIC_SRC_SHA256:
         return None
-    key = ("R%d T%d V%d BZ%d BY%d P%d" % (space_order // 2, plan["time_tile"], plan["vec"],
-                                          plan["tile_z"], plan["tile_y"], plan["prefetch"]),
+    fam = "staged" if plan.get("kernel") == 2 else "shared"
+    key = ("%s R%d T%d V%d rows%d BZ%d BY%d P%d" % (fam, space_order // 2, plan["time_tile"], plan["vec"],
+                                                   plan["rows"], plan["tile_z"], plan["tile_y"],
+                                                   plan["prefetch"]),
            plan["tile_x"], tuple(n))
     return TRAFFIC_BYTES.get(key)
 
