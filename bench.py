@@ -356,6 +356,10 @@ def run_ours(args):
         tiled = tuned(wave.Tuning(time_tile=args.time_tile, flags=wave.WAVE_AUTOTUNE_SHAPE))
     else:
         tiled = tuned(wave.Tuning(time_tile=0))
+    try:  # candidates the autotuner considered and those its runtime bound pruned
+        tune_stats = dict(zip(("candidates", "pruned"), wave.autotune_stats()))
+    except wave.WaveError:  # plan read from the plan cache: no autotuner ran
+        tune_stats = None
     untiled = tuned(wave.Tuning(time_tile=1, flags=wave.WAVE_AUTOTUNE_SHAPE))
     depths = sorted({v["time_tile"] for v in wave.list_variants(p.space_order) if v["time_tile"] >= 2})
     deep_plans = [tuned(wave.Tuning(time_tile=T, flags=wave.WAVE_AUTOTUNE_SHAPE)) for T in depths]
@@ -487,7 +491,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": desc, "l2": "inputs larger than L2 (512 MiB per field)",
-                       "plan": plan, "per_call_spread": spread,
+                       "plan": plan, "per_call_spread": spread, "autotune": tune_stats,
                        "parallelism": "replicas" if world > 1 else "single"},
             "untiled": untiled_line,
             "time_tiled": deep_line,
@@ -609,6 +613,10 @@ def _orders_sweep(dev, inputs, wave, args):
         def best_at(T):
             t = wave.Tuning(time_tile=T, flags=wave.WAVE_AUTOTUNE_SHAPE)
             fwd(t)
+            try:
+                st = dict(zip(("candidates", "pruned"), wave.autotune_stats()))
+            except wave.WaveError:
+                st = None
             pl = wave.describe_plan(grid, t)
             fixed = wave.Tuning(time_tile=pl["time_tile"], tile_y=pl["tile_y"], tile_x=pl["tile_x"],
                                 vec=pl["vec"], tile_z=pl["tile_z"], kernel=pl["kernel"], rows=pl["rows"])
@@ -616,7 +624,8 @@ def _orders_sweep(dev, inputs, wave, args):
             ms, _ = _timed(lambda: fwd(fixed), 1, stream)
             g = pts / (ms / 1e3) / 1e9
             bpp = 20.0 if T == 1 else 24.0 / T
-            return {"gpts": g, "frac_hbm": g * bpp / hbm, "bytes_per_point": bpp, "plan": pl}
+            return {"gpts": g, "frac_hbm": g * bpp / hbm, "bytes_per_point": bpp, "plan": pl,
+                    "autotune": st}
 
         row = {"untiled": best_at(1)}
         depths = sorted({v["time_tile"] for v in wave.list_variants(so) if v["time_tile"] >= 2})

@@ -235,6 +235,30 @@ int32_t wave_sweep_stats(float *ms, int32_t *launches, int32_t *steps);
  * bad arguments). */
 int32_t wave_list_variants(int32_t space_order, int32_t *out, int32_t max);
 
+/* Counts of the last autotuner run on this host thread: *candidates (HOST) the
+ * (variant, x-chunk) plans it considered, *pruned (HOST) those it did not time
+ * because their runtime bound (wave_plan_bound) exceeded the best time it had
+ * already measured -- the paper's proposal to prune the auto-tuner's search
+ * space with a bound that assumes perfect scheduling (Sec. 6.3.3).  Candidates
+ * are timed in order of their bound; WAVE_TUNE_NOPRUNE=1 in the environment
+ * times every one.  Returns WAVE_OK, or WAVE_EINVAL when the last call on this
+ * thread that needed an autotuned plan took it from a cache (or none did). */
+int32_t wave_autotune_stats(int32_t *candidates, int32_t *pruned);
+
+/* Lower bound, in milliseconds per time step, on the sweep of the plan that
+ * `tuning` selects (time_tile >= 1) for grid g, assuming perfect scheduling:
+ * the larger of (a) the compulsory DRAM bytes -- 20 per point-update untiled,
+ * 24/T for depth T -- at hbm_gbs GB/s, counted when five fields exceed twice
+ * l2_bytes (l2_bytes < 0: always), and (b) the bytes the kernel's code moves
+ * through the SM's shared-memory (LSU) pipe for every point each stage
+ * computes, the recomputed halo, x-chunk margins and overhanging tiles
+ * included, at lsu_gbs GB/s.  Arguments <= 0 (l2_bytes == 0) take the current
+ * device's figures: theoretical memory bandwidth, 128 bytes per clock per SM at
+ * the maximum SM clock, its L2 size.  *ms (HOST) receives the bound.  Returns
+ * WAVE_OK, WAVE_EINVAL, WAVE_EUNSUPPORTED or WAVE_ECUDA. */
+int32_t wave_plan_bound(const wave_grid *g, const wave_tuning *tuning, double hbm_gbs, double lsu_gbs,
+                        double l2_bytes, double *ms);
+
 /* Sweep variant the library would run for grid g with `tuning` (the cached
  * autotuned plan when tuning->time_tile == 0 and the autotuner already ran
  * for this shape, otherwise the untiled default): out[0..7] = time_tile,

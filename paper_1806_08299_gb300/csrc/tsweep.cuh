@@ -62,7 +62,7 @@ struct TMaps {
     CUtensorMap u2, B2, C2; // level n and coefficients over the output tile (BZ x BY), T = 2
 };
 
-template <int R, int T, int V, int VY, int BZ, int BY, int P>
+template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB>
 struct TShape {
     static constexpr int RT = R * T;
     static constexpr int RP = (R + 3) / 4 * 4;            // z halo of one stencil, 16-byte aligned
@@ -111,6 +111,8 @@ struct TShape {
     static_assert(TXA < (1u << 20), "mbarrier tx count");
     static_assert(NTB <= 1024, "too many threads per block");
     static_assert(SMEM <= 215 * 1024, "shared memory above the per-block limit");
+    static_assert(MB >= 1 && (size_t)MB * (SMEM + 4096) <= 228 * 1024 && MB * NTB <= 2048,
+                  "blocks per SM do not fit shared memory or thread slots");
 };
 
 // Level n+1 of a thread's VY x V points (VY rows, V/2 pairs each) from the
@@ -272,11 +274,11 @@ __device__ __forceinline__ void tstage_abort(volatile int *abort_flag, int *stat
     atomicMin(status, -4 /* WAVE_ETIMEOUT */);
 }
 
-template <int R, int T, int V, int VY, int BZ, int BY, int P>
+template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB>
 __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &st, const TMaps &mp,
                                              const int blk)
 {
-    using S = TShape<R, T, V, VY, BZ, BY, P>;
+    using S = TShape<R, T, V, VY, BZ, BY, P, MB>;
     constexpr int QL = 2 * R + 1, V2 = V / 2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *ringA = smem_raw;
@@ -638,14 +640,14 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
     }
 }
 
-// Untiled blocks are small (one warp group), so two of them are asked to fit
-// on an SM; a depth-2 block fills the SM's registers alone.
-template <int R, int T, int V, int VY, int BZ, int BY, int P>
-__global__ void __launch_bounds__(TShape<R, T, V, VY, BZ, BY, P>::NTB, T == 1 ? 2 : 1)
+// MB: resident blocks per SM the variant is compiled for (the
+// __launch_bounds__ minimum, which caps the registers per thread).
+template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB>
+__global__ void __launch_bounds__(TShape<R, T, V, VY, BZ, BY, P, MB>::NTB, MB)
 tsweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stencil st,
               const __grid_constant__ TMaps mp)
 {
-    tsweep_block<R, T, V, VY, BZ, BY, P>(a, st, mp, blockIdx.x);
+    tsweep_block<R, T, V, VY, BZ, BY, P, MB>(a, st, mp, blockIdx.x);
 }
 
 }  // namespace wt

@@ -36,24 +36,33 @@
 #define WAVE_SWEEP_VARIANTS_R8(X) \
     X(8, 1, 2, 64, 8, 2, 2) X(8, 1, 4, 64, 8, 2, 3) X(8, 1, 4, 64, 12, 2, 2)
 
-// Stage-specialised variants Z(R, T, V, VY, BZ, BY, P) of tsweep.cuh: time
-// step T on its own warps (T = 1 or 2), VY rows x V z-points per thread,
-// output tile BZ x BY, TMA prefetch distance P.  Shared memory holds P+1
-// slots of the stage-1 inputs (centre box with halo, level n, level n-1, B,
-// C over the stage-1 region), for T = 2 also P+1 slots of the stage-2 inputs
-// over the tile and R+3 planes of level n+1 handed from stage 1 to stage 2.
-#define WAVE_TSWEEP_VARIANTS_R1(Z)
+// Stage-specialised variants Z(R, T, V, VY, BZ, BY, P, MB) of tsweep.cuh:
+// time step T on its own warps (T = 1 or 2), VY rows x V z-points per
+// thread, output tile BZ x BY, TMA prefetch distance P, compiled for MB
+// resident blocks per SM.  Shared memory holds P+1 slots of the stage-1
+// inputs (centre box with halo, level n, level n-1, B, C over the stage-1
+// region), for T = 2 also P+1 slots of the stage-2 inputs over the tile and
+// R+3 planes of level n+1 handed from stage 1 to stage 2.  Registers hold a
+// (2R+1)-plane x-queue of VY x V points per thread.  Each quarter of an SM
+// has its own 16K registers and takes every fourth warp, so a block of w
+// warps (times MB) can give a thread at most 16384 / (32 ceil(w MB / 4))
+// registers: at so 16 (about 200 registers) no more than eight warps.
+#define WAVE_TSWEEP_VARIANTS_R1(Z) Z(1, 1, 4, 1, 64, 8, 2, 3) Z(1, 2, 4, 2, 128, 12, 1, 1)
 #define WAVE_TSWEEP_VARIANTS_R2(Z)                                                                 \
-    Z(2, 1, 4, 1, 64, 8, 2) Z(2, 1, 4, 2, 64, 16, 2) Z(2, 2, 4, 2, 56, 24, 2) Z(2, 2, 4, 2, 120, 12, 1) \
-    Z(2, 2, 4, 2, 128, 12, 1) Z(2, 2, 4, 2, 64, 24, 1) Z(2, 2, 4, 1, 56, 16, 2)
-#define WAVE_TSWEEP_VARIANTS_R3(Z)
+    Z(2, 1, 4, 1, 64, 8, 2, 2) Z(2, 1, 4, 2, 64, 16, 2, 2) Z(2, 2, 4, 2, 56, 24, 2, 1)            \
+    Z(2, 2, 4, 2, 120, 12, 1, 1) Z(2, 2, 4, 2, 128, 12, 1, 1) Z(2, 2, 4, 2, 64, 24, 1, 1)           \
+    Z(2, 2, 4, 1, 56, 16, 2, 1)
+#define WAVE_TSWEEP_VARIANTS_R3(Z) Z(3, 1, 4, 2, 64, 16, 2, 2) Z(3, 2, 4, 2, 64, 24, 1, 1)
 #define WAVE_TSWEEP_VARIANTS_R4(Z)                                                                 \
-    Z(4, 1, 4, 1, 64, 8, 2) Z(4, 1, 4, 2, 64, 16, 2) Z(4, 2, 4, 2, 56, 24, 1) Z(4, 2, 4, 2, 64, 24, 1) \
-    Z(4, 2, 4, 2, 32, 32, 2) Z(4, 2, 4, 2, 56, 16, 2) Z(4, 2, 4, 1, 56, 16, 2)
-#define WAVE_TSWEEP_VARIANTS_R5(Z)
-#define WAVE_TSWEEP_VARIANTS_R6(Z) Z(6, 1, 4, 1, 64, 8, 2) Z(6, 1, 4, 2, 64, 16, 2)
-#define WAVE_TSWEEP_VARIANTS_R7(Z)
-#define WAVE_TSWEEP_VARIANTS_R8(Z) Z(8, 1, 4, 1, 64, 8, 2) Z(8, 1, 4, 2, 64, 16, 2)
+    Z(4, 1, 4, 1, 64, 8, 2, 2) Z(4, 1, 4, 2, 64, 16, 2, 2) Z(4, 2, 4, 2, 56, 24, 1, 1)             \
+    Z(4, 2, 4, 2, 64, 24, 1, 1) Z(4, 2, 4, 2, 32, 32, 2, 1) Z(4, 2, 4, 2, 56, 16, 2, 1)            \
+    Z(4, 2, 4, 1, 56, 16, 2, 1)
+#define WAVE_TSWEEP_VARIANTS_R5(Z) Z(5, 1, 4, 2, 64, 16, 2, 2)
+#define WAVE_TSWEEP_VARIANTS_R6(Z) \
+    Z(6, 1, 4, 1, 64, 8, 2, 2) Z(6, 1, 4, 2, 64, 16, 2, 2) Z(6, 1, 4, 2, 64, 32, 2, 1) Z(6, 2, 4, 2, 32, 24, 1, 1)
+#define WAVE_TSWEEP_VARIANTS_R7(Z) Z(7, 1, 4, 2, 64, 16, 2, 1)
+#define WAVE_TSWEEP_VARIANTS_R8(Z) \
+    Z(8, 1, 4, 1, 64, 8, 2, 2) Z(8, 1, 4, 2, 64, 16, 2, 1) Z(8, 1, 4, 2, 64, 24, 2, 1) Z(8, 2, 4, 2, 32, 8, 1, 1)
 
 // Gradient-mode variants Y(R, T, V, BZ, BY, P, MB, XB): the untiled default
 // shape of a radius with XB extra ring-K boxes (1: E for the second-difference

@@ -830,11 +830,11 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         const int mode = job.gacc != nullptr ? 2 : (job.dstore != nullptr ? 1 : 0);
         if (mode > 0 && v->kind == 1) {
             // the stage-specialised sweep has no second-difference or
-            // imaging-condition mode: the sweep.cuh variant of the same depth
-            // (bitwise the same wavefield) runs the gradient sweeps
-            const SweepVariant *cv = find_variant(R, v->T, 0, 0, 0, 1);
-            if (cv == nullptr) cv = fallback_variant(R, v->T, 0);
-            v = cv;
+            // imaging-condition mode: the untiled default of sweep.cuh (whose
+            // gradient-mode variants stream the extra arrays through TMA, and
+            // whose wavefield is bitwise the same) runs the gradient sweeps
+            v = find_variant(R, 1, 0, 0, 0, 1);
+            if (v == nullptr) return WAVE_EUNSUPPORTED;
             chunk = std::min(plan.chunk_given ? chunk : default_chunk(d, v), max_chunk(v));
         }
         if (mode > 0 && v->T == 1) {
@@ -877,6 +877,107 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
     return WAVE_OK;
 }
 
+// Device figures the runtime bound of a plan uses: theoretical memory
+// bandwidth (bytes/s), shared-memory (LSU data pipe) bandwidth at 128 bytes per
+// clock per SM at the maximum SM clock (bytes/s), and the L2 size (bytes).
+struct DevicePeaks {
+    double hbm = 0.0, lsu = 0.0, l2 = 0.0;
+};
+
+DevicePeaks device_peaks()
+{
+    static std::mutex mu;
+    static std::map<int, DevicePeaks> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int mem_khz = 0, bus_bits = 0, sm_khz = 0, l2 = 0;
+    DevicePeaks p;
+    if (cudaDeviceGetAttribute(&mem_khz, cudaDevAttrMemoryClockRate, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&bus_bits, cudaDevAttrGlobalMemoryBusWidth, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sm_khz, cudaDevAttrClockRate, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess) {
+        p.hbm = 2.0 * mem_khz * 1e3 * bus_bits / 8.0;  // double data rate
+        p.lsu = (double)sm_count() * 128.0 * sm_khz * 1e3;
+        p.l2 = l2;
+    }
+    cache[dev] = p;
+    return p;
+}
+
+// Bytes one point-update of stage s (1-based, of depth T) moves through the
+// SM's LSU data pipe -- the shared-memory and global loads and stores of the
+// kernel's code, per point -- for variant v.  TMA copies into shared memory
+// do not pass through that pipe.
+double lsu_bytes_per_point(const SweepVariant *v, int s)
+{
+    const int R = v->R, RP = (R + 3) / 4 * 4;
+    if (v->kind == 1) {
+        // per thread and plane (VY rows x 4 points): the queue feed, the z
+        // halos, 2R rows of y-neighbours, level n-1 (or n), B and C, and the
+        // plane's output (T = 1: stored; T = 2 stage 1: into ring 1, whose
+        // stage-2 feed read is the stage-2 feed above; stage 2: two levels)
+        const double VY = v->VY;
+        const double out = v->T == 1 ? 16.0 * VY : (s == 1 ? 16.0 * VY : 32.0 * VY);
+        return (16.0 * VY + 8.0 * RP * VY + 32.0 * R + 48.0 * VY + out) / (4.0 * VY);
+    }
+    // sweep.cuh, V points per thread: the feed (stage 1) or the exchanged
+    // centre plane, the z window, 2R rows of y-neighbours, B and C, level n-1
+    // (stage 1), and the stored or exchanged output
+    const double V = v->V;
+    return 4.0 + (V + 2.0 * RP) * 4.0 / V + 8.0 * R + 8.0 + (s == 1 ? 4.0 : 0.0) + 4.0;
+}
+
+// Lower bound on the milliseconds of one time step of plan (v, chunk) on grid
+// d, assuming perfect scheduling: the paper's proposal for pruning the
+// auto-tuner's search space (Sec. 6.3.3).  The larger of
+//  * DRAM: the compulsory bytes (20 per point-update untiled, 24/T for depth T)
+//    at the theoretical memory bandwidth, counted only when the fields are
+//    larger than L2 (otherwise they may be served by it);
+//  * LSU: lsu_bytes_per_point for every point each stage computes -- the
+//    tile and the halo its stage recomputes, over the planes of each x-chunk
+//    plus the chunk margins that stage computes, and the tiles overhanging
+//    the grid -- at the LSU data-pipe bandwidth.
+// hbm, lsu > 0 override the device figures (bytes/s); l2 < 0 ignores L2.
+double plan_bound_ms(const Dims &d, const SweepVariant *v, int chunk, double hbm, double lsu, double l2)
+{
+    const double N = (double)d.npad;
+    const int T = v->T, R = v->R, RP = (R + 3) / 4 * 4;
+    const double tz = tiles(d.nzp, v->BZ), ty = tiles(d.ny, v->BY), tx = tiles(d.nx, chunk);
+    double lsu_bytes = 0.0;
+    for (int s = 1; s <= T; ++s) {
+        double rows, cols;  // the region stage s computes per tile and plane
+        if (v->kind == 1) {
+            rows = v->BY + 2.0 * (T - s) * R;
+            cols = v->BZ + 2.0 * (T - s) * RP;
+        } else {
+            rows = v->BY + 2.0 * (T - s) * R;
+            cols = v->BZ + 2.0 * (T - s) * R;
+        }
+        const double planes = d.nx + tx * 2.0 * (T - s) * R;
+        lsu_bytes += tz * ty * planes * rows * cols * lsu_bytes_per_point(v, s);
+    }
+    const double dram_bytes = N * (T == 1 ? 20.0 : 24.0);
+    const bool over_l2 = l2 < 0 || 5.0 * 4.0 * N > 2.0 * l2;
+    const double t_dram = over_l2 && hbm > 0 ? dram_bytes / hbm : 0.0;
+    const double t_lsu = lsu > 0 ? lsu_bytes / lsu : 0.0;
+    return 1e3 * std::max(t_dram, t_lsu) / T;
+}
+
+// Counts of the last autotuner run on this host thread.
+struct TuneStats {
+    int candidates = 0, pruned = 0;
+};
+thread_local TuneStats g_tune_stats;
+
+bool tune_prune()
+{
+    const char *e = std::getenv("WAVE_TUNE_NOPRUNE");
+    return e == nullptr || e[0] == '\0' || e[0] == '0';
+}
+
 // Time candidate plans on the real coefficients (zero wavefield, no sparse
 // points) and cache the fastest: the paper's auto-tuner extended to the time
 // tile (Sec. 4.4, Sec. 5.2.2), here over (T, tile, x-chunk).  Candidates are
@@ -906,13 +1007,30 @@ int autotune(const Dims &d, const Stencil &st, const float *cB, const float *cC,
         }
     }
     if (cands.empty()) return WAVE_EUNSUPPORTED;
+    // Candidates are timed in order of their runtime bound, lowest first; one
+    // whose bound exceeds the best time measured so far cannot win and is
+    // not timed (WAVE_TUNE_NOPRUNE=1 times every candidate).
+    const DevicePeaks pk = device_peaks();
+    std::vector<double> bound(cands.size());
+    std::vector<size_t> order(cands.size());
+    for (size_t c = 0; c < cands.size(); ++c) {
+        bound[c] = plan_bound_ms(d, cands[c].v, cands[c].chunk, pk.hbm, pk.lsu, pk.l2);
+        order[c] = c;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return bound[a] < bound[b]; });
+    const bool prune = tune_prune();
+    std::vector<char> skip(cands.size(), 0);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     std::vector<float> best(cands.size(), 1e30f);
+    float best_all = 1e30f;
     int rc = WAVE_OK;
     for (int pass = 0; pass < 2 && rc == WAVE_OK; ++pass) {
-        for (size_t c = 0; c < cands.size() && rc == WAVE_OK; ++c) {
+        for (size_t oi = 0; oi < cands.size() && rc == WAVE_OK; ++oi) {
+            const size_t c = order[oi];
+            if (pass == 0 && prune && bound[c] > (double)best_all) skip[c] = 1;
+            if (skip[c]) continue;
             const Plan &p = cands[c];
             Job job;
             job.d = d;
@@ -934,17 +1052,33 @@ int autotune(const Dims &d, const Stencil &st, const float *cB, const float *cC,
                 break;
             }
             best[c] = std::min(best[c], ms / steps);
+            best_all = std::min(best_all, best[c]);
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    size_t bi = 0;
+    g_tune_stats.candidates = (int)cands.size();
+    g_tune_stats.pruned = (int)std::count(skip.begin(), skip.end(), 1);
+    size_t bi = order[0];
+    for (size_t c = 0; c < cands.size(); ++c)
+        if (!skip[c]) {
+            bi = c;
+            break;
+        }
     for (size_t c = 0; c < cands.size(); ++c) {
+        if (skip[c]) {
+            if (tune_log())
+                std::fprintf(stderr, "wave autotune: kernel=%d T=%d tile=%dx%d vec=%d rows=%d P=%d chunk=%d: "
+                             "bound %.4f ms/step, not timed\n", cands[c].v->kind + 1, cands[c].v->T,
+                             cands[c].v->BZ, cands[c].v->BY, cands[c].v->V, rows_of(cands[c].v), cands[c].v->P,
+                             cands[c].chunk, bound[c]);
+            continue;
+        }
         if (tune_log())
-            std::fprintf(stderr, "wave autotune: kernel=%d T=%d tile=%dx%d vec=%d rows=%d P=%d chunk=%d: %.4f ms/step\n",
-                         cands[c].v->kind + 1, cands[c].v->T, cands[c].v->BZ, cands[c].v->BY, cands[c].v->V,
-                         rows_of(cands[c].v), cands[c].v->P, cands[c].chunk, best[c]);
+            std::fprintf(stderr, "wave autotune: kernel=%d T=%d tile=%dx%d vec=%d rows=%d P=%d chunk=%d: %.4f ms/step "
+                         "(bound %.4f)\n", cands[c].v->kind + 1, cands[c].v->T, cands[c].v->BZ, cands[c].v->BY,
+                         cands[c].v->V, rows_of(cands[c].v), cands[c].v->P, cands[c].chunk, best[c], bound[c]);
         // a later candidate must be clearly faster: timings within 1 % are
         // ties, and ties keep the earlier one (the default variant and chunk
         // come first), so run-to-run noise does not flip the plan
@@ -977,6 +1111,9 @@ int resolve_plan(const Dims &d, const wave_grid *g, const wave_tuning *t, bool m
         return WAVE_OK;
     }
     const TuneKey key = tune_key(d, g->space_order, T);
+    // wave_autotune_stats describes the autotuner run of the last call that
+    // resolved a plan this way; a plan from a cache leaves none
+    if (may_tune) g_tune_stats = TuneStats();
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -1817,6 +1954,37 @@ int32_t wave_list_variants(int32_t space_order, int32_t *out, int32_t max)
         o[7] = rows_of(&vs[i]);
     }
     return nv;
+}
+
+int32_t wave_autotune_stats(int32_t *candidates, int32_t *pruned)
+{
+    if (candidates == nullptr || pruned == nullptr) return WAVE_EINVAL;
+    if (g_tune_stats.candidates == 0) return WAVE_EINVAL;
+    *candidates = g_tune_stats.candidates;
+    *pruned = g_tune_stats.pruned;
+    return WAVE_OK;
+}
+
+int32_t wave_plan_bound(const wave_grid *g, const wave_tuning *tuning, double hbm_gbs, double lsu_gbs,
+                        double l2_bytes, double *ms)
+{
+    Dims d;
+    int rc = check_grid(g, &d);
+    if (rc) return rc;
+    if (ms == nullptr || tuning == nullptr || tuning->time_tile < 1) return WAVE_EINVAL;
+    Plan p;
+    float *U[4] = {nullptr, nullptr, nullptr, nullptr};
+    if ((rc = resolve_plan(d, g, tuning, false, nullptr, nullptr, nullptr, U, nullptr, nullptr, &p))) return rc;
+    double hbm = hbm_gbs * 1e9, lsu = lsu_gbs * 1e9, l2 = l2_bytes;
+    if (hbm_gbs <= 0.0 || lsu_gbs <= 0.0 || l2_bytes == 0.0) {
+        const DevicePeaks pk = device_peaks();
+        if (hbm_gbs <= 0.0) hbm = pk.hbm;
+        if (lsu_gbs <= 0.0) lsu = pk.lsu;
+        if (l2_bytes == 0.0) l2 = pk.l2;
+    }
+    if (hbm <= 0.0 || lsu <= 0.0) return WAVE_ECUDA;
+    *ms = plan_bound_ms(d, p.v, p.chunk, hbm, lsu, l2);
+    return WAVE_OK;
 }
 
 int32_t wave_describe_plan(const wave_grid *g, const wave_tuning *tuning, int32_t *out)

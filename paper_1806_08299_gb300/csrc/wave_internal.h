@@ -132,13 +132,13 @@ cudaError_t launch_sweep(int nblocks, cudaStream_t stream, const SweepArgs &a, c
     return cudaLaunchKernelEx(&cfg, sweep_kernel<R, T, V, BZ, BY, P, MB, XB>, a, st, m);
 }
 
-template <int R, int T, int V, int VY, int BZ, int BY, int P>
+template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB>
 cudaError_t launch_tsweep(int nblocks, cudaStream_t stream, const SweepArgs &a, const Stencil &st,
                           const TMaps &m)
 {
-    using S = TShape<R, T, V, VY, BZ, BY, P>;
+    using S = TShape<R, T, V, VY, BZ, BY, P, MB>;
     const size_t smem = S::smem_bytes(a.chunk);
-    cudaError_t e = allow_max_dynamic_smem((const void *)tsweep_kernel<R, T, V, VY, BZ, BY, P>);
+    cudaError_t e = allow_max_dynamic_smem((const void *)tsweep_kernel<R, T, V, VY, BZ, BY, P, MB>);
     if (e != cudaSuccess) return e;
     // programmatic dependent launch, as launch_sweep
     cudaLaunchAttribute attr[1];
@@ -151,7 +151,7 @@ cudaError_t launch_tsweep(int nblocks, cudaStream_t stream, const SweepArgs &a, 
     cfg.stream = stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, tsweep_kernel<R, T, V, VY, BZ, BY, P>, a, st, m);
+    return cudaLaunchKernelEx(&cfg, tsweep_kernel<R, T, V, VY, BZ, BY, P, MB>, a, st, m);
 }
 
 template <int R, int T, int V, int BZ, int BY, int P, int MB>
@@ -197,13 +197,15 @@ cudaError_t launch_sweep_multi(int nblocks, size_t smem, cudaStream_t stream, co
      &wt::launch_sweep<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>,                                      \
      (const void *)&wt::sweep_kernel<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>, XB_},
 
-#define WAVE_TVARIANT_ENTRY(R_, T_, V_, VY_, BZ_, BY_, P_)                                       \
-    {R_, T_, V_, BZ_, BY_, P_, wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_>::NTB, 0, 0, 0, 0,          \
-     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_>::SMEM, nullptr,                                     \
-     (const void *)&wt::tsweep_kernel<R_, T_, V_, VY_, BZ_, BY_, P_>, 0, 1, VY_,                   \
-     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_>::W1, wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_>::H1, \
-     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_>::WC, wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_>::HC, \
-     &wt::launch_tsweep<R_, T_, V_, VY_, BZ_, BY_, P_>},
+#define WAVE_TVARIANT_ENTRY(R_, T_, V_, VY_, BZ_, BY_, P_, MB_)                                  \
+    {R_, T_, V_, BZ_, BY_, P_, wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>::NTB, 0, 0, 0, 0,     \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>::SMEM, nullptr,                                \
+     (const void *)&wt::tsweep_kernel<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>, 0, 1, VY_,              \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>::W1,                                           \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>::H1,                                           \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>::WC,                                           \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>::HC,                                           \
+     &wt::launch_tsweep<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>},
 
 #define WAVE_DEFINE_MULTI(R_, T_, V_, BZ_, BY_, P_, MB_)                                         \
     namespace wt {                                                                                \

@@ -32,6 +32,7 @@ WAVE_NOALLOC_MAX_BYTES = 32 * 1024 * 1024
 EXPORTED = ["wave_version", "wave_strerror", "wave_fd_coefficients", "wave_cfl_dt",
             "wave_workspace_bytes", "wave_ckpt_bytes", "wave_fwd", "wave_adj", "wave_grad",
             "wave_status", "wave_describe_plan", "wave_sweep_stats", "wave_list_variants",
+            "wave_autotune_stats", "wave_plan_bound",
             "wave_fwd_noalloc", "wave_measure_peaks", "wave_batch_workspace_bytes",
             "wave_fwd_batched", "wave_grad_batched", "wave_heat"]
 
@@ -146,6 +147,11 @@ def _lib():
         lib.wave_sweep_stats.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32),
                                          ctypes.POINTER(i32)]
         lib.wave_sweep_stats.restype = i32
+        lib.wave_autotune_stats.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.wave_autotune_stats.restype = i32
+        lib.wave_plan_bound.argtypes = [gp, tp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.POINTER(ctypes.c_double)]
+        lib.wave_plan_bound.restype = i32
         lib.wave_list_variants.argtypes = [i32, ctypes.POINTER(i32), i32]
         lib.wave_list_variants.restype = i32
         lib.wave_fwd_noalloc.argtypes = [gp, vp, vp, pp, vp, pp, vp, vp, tp, vp, ctypes.POINTER(i32)]
@@ -509,6 +515,24 @@ def sweep_stats():
     _check(_lib().wave_sweep_stats(ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(ns)),
            "wave_sweep_stats")
     return float(ms.value), int(nl.value), int(ns.value)
+
+
+def autotune_stats():
+    """(candidates, pruned) of the last autotuner run on this thread."""
+    c, p = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib().wave_autotune_stats(ctypes.byref(c), ctypes.byref(p)), "wave_autotune_stats")
+    return int(c.value), int(p.value)
+
+
+def plan_bound(grid, tuning, hbm_gbs=0.0, lsu_gbs=0.0, l2_bytes=0.0):
+    """Runtime bound (ms per time step) of the plan `tuning` selects
+    (wave_plan_bound); zero arguments take the current device's figures."""
+    g = grid.c()
+    t = tuning.c()
+    out = ctypes.c_double()
+    _check(_lib().wave_plan_bound(ctypes.byref(g), ctypes.byref(t), float(hbm_gbs), float(lsu_gbs),
+                                  float(l2_bytes), ctypes.byref(out)), "wave_plan_bound")
+    return float(out.value)
 
 
 def status(ws, stream=None):

@@ -132,3 +132,39 @@ def test_tile_z_and_plan_cache_file_without_gpu(wavelib, tmp_path, monkeypatch):
                               wavelib.Tuning(time_tile=0))
     assert (a["time_tile"], a["tile_y"], a["tile_x"], a["tile_z"]) == (2, 12, 96, 128)
     assert (b["time_tile"], b["tile_y"], b["tile_x"], b["tile_z"]) == (2, 12, 64, 56)
+
+
+def test_plan_bound_closed_forms_without_gpu(wavelib):
+    """wave_plan_bound with explicit bandwidths: the larger of the DRAM and LSU
+    terms, worked out by hand for two plans of the 512^3 so-8 grid."""
+    g = wavelib.Grid((512, 512, 512), (0.01,) * 3, 1e-4, 10, 8)
+    N = 512 ** 3
+    hbm, lsu = 8000.0, 40000.0  # GB/s
+    # staged untiled 64x16 tile, 2 rows of 4 z-points per thread, x-chunk 64:
+    # every point once; per thread and plane it moves 2 x 16 B of queue feed,
+    # 2 rows x 2 z-halos of 4 floats, 8 y-neighbour rows of 16 B, 3 x 2 x 16 B
+    # of n-1, B, C and 2 x 16 B of output: 352 B for 8 points
+    t1 = wavelib.Tuning(time_tile=1, tile_y=16, tile_z=64, kernel=2, rows=2, tile_x=64)
+    dram = 20.0 * N / (hbm * 1e9) * 1e3
+    lsu_ms = N * 44.0 / (lsu * 1e9) * 1e3
+    assert wavelib.plan_bound(g, t1, hbm, lsu, -1) == pytest.approx(max(dram, lsu_ms), rel=1e-12)
+    assert dram > lsu_ms  # DRAM binds the untiled sweep
+    # staged depth 2, 64x24 tile, x-chunk 103: stage 1 covers 72 x 32 over each
+    # chunk's planes plus 4 on either side (552 planes), stage 2 the tile over
+    # 512 planes; 8 x 22 tiles (the last row of tiles overhangs 512); stage 2
+    # stores two levels (64 B per thread and plane instead of 32)
+    t2 = wavelib.Tuning(time_tile=2, tile_y=24, tile_z=64, kernel=2, rows=2, tile_x=103)
+    lsu_b = 8 * 22 * (552 * 32 * 72 * 44.0 + 512 * 24 * 64 * 48.0)
+    want = max(24.0 * N / (hbm * 1e9), lsu_b / (lsu * 1e9)) * 1e3 / 2
+    assert wavelib.plan_bound(g, t2, hbm, lsu, -1) == pytest.approx(want, rel=1e-12)
+    # fields inside L2 drop the DRAM term; a wider recomputed halo raises the bound
+    small = wavelib.Grid((64, 64, 64), (0.01,) * 3, 1e-4, 10, 8)
+    t1s = wavelib.Tuning(time_tile=1, tile_y=16, tile_z=64, kernel=2, rows=2, tile_x=64)
+    assert wavelib.plan_bound(small, t1s, hbm, lsu, 128e6) == pytest.approx(
+        64 ** 3 * 44.0 / (lsu * 1e9) * 1e3, rel=1e-12)
+    g16 = wavelib.Grid((512, 512, 512), (0.01,) * 3, 1e-4, 10, 16)
+    deep = wavelib.plan_bound(g16, wavelib.Tuning(time_tile=2, tile_y=8, tile_z=32, kernel=2, rows=2,
+                                                  tile_x=64), hbm, lsu, -1)
+    flat = wavelib.plan_bound(g16, wavelib.Tuning(time_tile=1, tile_y=24, tile_z=64, kernel=2, rows=2,
+                                                  tile_x=64), hbm, lsu, -1)
+    assert deep > flat
