@@ -60,9 +60,14 @@ struct TMaps {
     CUtensorMap uf, um;     // level n and n-1 over the stage-1 region (W1 x H1)
     CUtensorMap B, C;       // coefficients over the stage-1 region
     CUtensorMap u2, B2, C2; // level n and coefficients over the output tile (BZ x BY), T = 2
+    // gradient modes: stage-1 boxes x0, x1 (W1 x H1), stage-2 boxes y0..y2 (BZ x BY):
+    //   MODE 1: x0 = E; y0 = E (T = 2)
+    //   MODE 2: T = 1: x0 = D row l_row0, x1 = G;  T = 2: y0, y1 = D rows l_row0,
+    //           l_row0 + l_dir, y2 = G
+    CUtensorMap x0, x1, y0, y1, y2;
 };
 
-template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB>
+template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB, int MODE = 0>
 struct TShape {
     static constexpr int RT = R * T;
     static constexpr int RP = (R + 3) / 4 * 4;            // z halo of one stencil, 16-byte aligned
@@ -88,20 +93,25 @@ struct TShape {
     static constexpr unsigned CBOXP = (CBOX + 127) / 128 * 128;
     static constexpr unsigned FBOXP = (FBOX + 127) / 128 * 128;
     static constexpr unsigned SBOXP = (SBOX + 127) / 128 * 128;
-    // ring A slot: centre box, level n (queue feed), level n-1, B, C
+    // extra boxes of the gradient modes per ring-A / ring-B slot
+    static constexpr int XA = MODE == 0 ? 0 : (T == 1 ? MODE : (MODE == 1 ? 1 : 0));
+    static constexpr int XBB = T == 2 ? (MODE == 1 ? 1 : (MODE == 2 ? 3 : 0)) : 0;
+    // ring A slot: centre box, level n (queue feed), level n-1, B, C, [x0, x1]
     static constexpr unsigned A_C = 0, A_F = CBOXP, A_UM = A_F + FBOXP, A_B = A_UM + FBOXP,
-                              A_CC = A_B + FBOXP, ASLOT = A_CC + FBOXP;
-    // ring B slot: level n, B, C over the output tile
-    static constexpr unsigned B_UM = 0, B_B = SBOXP, B_C = 2 * SBOXP, BSLOT = 3 * SBOXP;
+                              A_CC = A_B + FBOXP, A_X0 = A_CC + FBOXP, A_X1 = A_X0 + FBOXP,
+                              ASLOT = A_X0 + XA * FBOXP;
+    // ring B slot: level n, B, C over the output tile, [y0, y1, y2]
+    static constexpr unsigned B_UM = 0, B_B = SBOXP, B_C = 2 * SBOXP, B_Y0 = 3 * SBOXP,
+                              B_Y1 = 4 * SBOXP, B_Y2 = 5 * SBOXP, BSLOT = (3 + XBB) * SBOXP;
     static constexpr size_t OFF_B = (size_t)DA * ASLOT;
     static constexpr size_t OFF_1 = OFF_B + (size_t)DB * BSLOT;
     static constexpr size_t OFF_BAR = OFF_1 + (size_t)D1 * FBOXP;
     static constexpr size_t OFF_P = OFF_BAR + 8 * (2 * DA + 2 * DB + 2 * D1) + 16;
     static constexpr size_t SMEM = OFF_P;                 // + per-plane sparse slices
     static size_t smem_bytes(int chunk) { return OFF_P + sweep_table_bytes(chunk, RT) + 16; }
-    static constexpr unsigned TXA = CBOX + 4 * FBOX;      // bytes of a ring-A slot from iteration 2R on
-    static constexpr unsigned TXF = FBOX;                 // before (queue fill only)
-    static constexpr unsigned TXB = 3 * SBOX;
+    static constexpr unsigned TXA = CBOX + (4 + XA) * FBOX;  // bytes of a ring-A slot from iteration 2R on
+    static constexpr unsigned TXF = FBOX;                    // before (queue fill only)
+    static constexpr unsigned TXB = (3 + XBB) * SBOX;
     static_assert(T == 1 || T == 2, "stage-specialised sweep: T = 1 or 2");
     static_assert(V == 4, "four z points per thread (two pairs)");
     static_assert(VY == 1 || VY == 2, "one or two rows per thread");
@@ -113,6 +123,7 @@ struct TShape {
     static_assert(SMEM <= 215 * 1024, "shared memory above the per-block limit");
     static_assert(MB >= 1 && (size_t)MB * (SMEM + 4096) <= 228 * 1024 && MB * NTB <= 2048,
                   "blocks per SM do not fit shared memory or thread slots");
+    static_assert(MODE >= 0 && MODE <= 2, "mode: 0 plain, 1 second differences, 2 imaging condition");
 };
 
 // Level n+1 of a thread's VY x V points (VY rows, V/2 pairs each) from the
@@ -123,11 +134,15 @@ struct TShape {
 // are those of sweep_block in sweep.cuh: R <= 2 one chain (centre, then per
 // k the x, y, z pair sums); R >= 3 three chains (centre + x), y, z summed as
 // (x + y) + z; then u^{n+1} = u^n + B (u^n - u^{n-1}) + C L u^n.
-template <int R, int V, int VY, int PC, int PK>
+// DD: also the second difference u^{n+1} - 2u^n + u^{n-1} = E (u^n - u^{n-1})
+// + C L u^n into dd (before sources), from the caller's e = E, as sweep_block's
+// second-difference mode computes it.
+template <int R, int V, int VY, int PC, int PK, bool DD = false>
 __device__ __forceinline__ void tstage_update(float2 (&un)[VY][V / 2], float2 (&cC)[VY][V / 2],
                                               const float2 (&q)[2 * R + 1][VY][V / 2], const float *pc,
                                               const float *pum, const float *pB, const float *pCc,
-                                              const Stencil &st)
+                                              const Stencil &st, const float2 (*e)[V / 2] = nullptr,
+                                              float2 (*dd)[V / 2] = nullptr)
 {
     constexpr int V2 = V / 2;
     constexpr int RP = (R + 3) / 4 * 4;
@@ -214,57 +229,99 @@ __device__ __forceinline__ void tstage_update(float2 (&un)[VY][V / 2], float2 (&
             const float2 u0 = q[R][v][j];
             const float2 du = fsub2_rn(u0, up[j]);
             un[v][j] = __ffma2_rn(cC[v][j], lap[v][j], __ffma2_rn(cB[j], du, u0));
+            if constexpr (DD) dd[v][j] = __ffma2_rn(cC[v][j], lap[v][j], __fmul2_rn(e[v][j], du));
         }
     }
 }
 
 // Point sources of plane cs on a thread's VY x V points at global row gy
 // (first row) and column gz: u += C f, f = sum of w q_s in ascending source
-// order (the injection loop of sweep_block).
-template <int V, int VY>
+// order (the injection of sweep_block).  The warp scans the plane's table
+// entries together: each lane loads one entry, a ballot keeps those inside the
+// warp's rows [wy0, wy1) and columns [wz0, wz1), and every lane tests only
+// those against its own points, so warps without a point of the plane pay one
+// load and one vote per 32 entries.  Called by whole warps (block-uniform
+// condition).  Each grid point appears once in the table, so the order in
+// which its entry is met does not matter; its items are summed in order.
+template <int V, int VY, bool DD = false>
 __device__ __forceinline__ void tstage_inject(float2 (&un)[VY][V / 2], const float2 (&cC)[VY][V / 2],
-                                              const SweepArgs &a, int e0, int e1, int gy, int gz, int qrow)
+                                              const SweepArgs &a, int e0, int e1, int gy, int gz, int qrow,
+                                              int wy0, int wy1, int wz0, int wz1,
+                                              float2 (*dd)[V / 2] = nullptr)
 {
     const long long qbase = (long long)qrow * a.nq;
+    const int lane = threadIdx.x & 31;
+    float fv[VY][V];
+    unsigned hits[VY];
 #pragma unroll
     for (int v = 0; v < VY; ++v) {
-        float fv[V];
-        unsigned hits = 0u;
+        hits[v] = 0u;
 #pragma unroll
-        for (int j = 0; j < V; ++j) fv[j] = 0.f;
-        for (int eb = e0; eb < e1; eb += 4) {
-            int4 pt4[4];  // four table points per round trip
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                pt4[u] = eb + u < e1 ? __ldg(a.inj.pts + eb + u) : make_int4(-1, -1, 0, 0);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int4 pt = pt4[u];
-                if (pt.x != gy + v || pt.y < gz || pt.y >= gz + V) continue;
-                float f = 0.f;
-                int itm = pt.z;
-                for (; itm + 1 < pt.w; itm += 2) {  // items in pairs, ascending sum
-                    const int i0 = __ldg(a.inj.item + itm), i1 = __ldg(a.inj.item + itm + 1);
-                    const float w0 = __ldg(a.inj.w + itm), w1 = __ldg(a.inj.w + itm + 1);
-                    const float q0 = __ldg(a.q + qbase + i0), q1 = __ldg(a.q + qbase + i1);
-                    f = __fmaf_rn(w0, q0, f);
-                    f = __fmaf_rn(w1, q1, f);
-                }
-                if (itm < pt.w)
-                    f = __fmaf_rn(__ldg(a.inj.w + itm), __ldg(a.q + qbase + __ldg(a.inj.item + itm)), f);
-                const int jj = pt.y - gz;
-#pragma unroll
-                for (int j = 0; j < V; ++j) fv[j] = jj == j ? f : fv[j];
-                hits |= 1u << jj;
+        for (int j = 0; j < V; ++j) fv[v][j] = 0.f;
+    }
+    for (int eb = e0; eb < e1; eb += 32) {
+        const int4 mine = eb + lane < e1 ? __ldg(a.inj.pts + eb + lane) : make_int4(-1, -1, 0, 0);
+        const bool rel = mine.x >= wy0 && mine.x < wy1 && mine.y >= wz0 && mine.y < wz1;
+        unsigned m = __ballot_sync(0xffffffffu, rel);
+        while (m != 0u) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1u;
+            int4 pt;
+            pt.x = __shfl_sync(0xffffffffu, mine.x, l);
+            pt.y = __shfl_sync(0xffffffffu, mine.y, l);
+            pt.z = __shfl_sync(0xffffffffu, mine.z, l);
+            pt.w = __shfl_sync(0xffffffffu, mine.w, l);
+            const int v = pt.x - gy, jj = pt.y - gz;
+            if (v < 0 || v >= VY || jj < 0 || jj >= V) continue;
+            float f = 0.f;
+            int itm = pt.z;
+            for (; itm + 1 < pt.w; itm += 2) {  // items in pairs, ascending sum
+                const int i0 = __ldg(a.inj.item + itm), i1 = __ldg(a.inj.item + itm + 1);
+                const float w0 = __ldg(a.inj.w + itm), w1 = __ldg(a.inj.w + itm + 1);
+                const float q0 = __ldg(a.q + qbase + i0), q1 = __ldg(a.q + qbase + i1);
+                f = __fmaf_rn(w0, q0, f);
+                f = __fmaf_rn(w1, q1, f);
             }
+            if (itm < pt.w)
+                f = __fmaf_rn(__ldg(a.inj.w + itm), __ldg(a.q + qbase + __ldg(a.inj.item + itm)), f);
+#pragma unroll
+            for (int vv = 0; vv < VY; ++vv)
+#pragma unroll
+                for (int j = 0; j < V; ++j)
+                    if (vv == v && j == jj) fv[vv][j] = f;
+            hits[v < VY ? v : 0] |= 1u << jj;
         }
+    }
+#pragma unroll
+    for (int v = 0; v < VY; ++v)
 #pragma unroll
         for (int j = 0; j < V; ++j)
-            if (hits & (1u << j)) {
+            if (hits[v] & (1u << j)) {
                 float &uj = (j & 1) ? un[v][j >> 1].y : un[v][j >> 1].x;
                 const float cj = (j & 1) ? cC[v][j >> 1].y : cC[v][j >> 1].x;
-                uj = __fmaf_rn(cj, fv[j], uj);
+                uj = __fmaf_rn(cj, fv[v][j], uj);
+                if constexpr (DD) {
+                    float &dj = (j & 1) ? dd[v][j >> 1].y : dd[v][j >> 1].x;
+                    dj = __fmaf_rn(cj, fv[v][j], dj);
+                }
             }
+}
+
+// The rows [y0, y1) and columns [z0, z1) that the lanes of the calling warp
+// cover with their VY x V points at (gy, gz) (whole warp).
+template <int V, int VY>
+__device__ __forceinline__ void warp_extent(int gy, int gz, int &y0, int &y1, int &z0, int &z1)
+{
+    y0 = gy;
+    y1 = gy + VY;
+    z0 = gz;
+    z1 = gz + V;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        y0 = min(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        y1 = max(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+        z0 = min(z0, __shfl_xor_sync(0xffffffffu, z0, o));
+        z1 = max(z1, __shfl_xor_sync(0xffffffffu, z1, o));
     }
 }
 
@@ -274,11 +331,18 @@ __device__ __forceinline__ void tstage_abort(volatile int *abort_flag, int *stat
     atomicMin(status, -4 /* WAVE_ETIMEOUT */);
 }
 
-template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB>
+// MODE 0: forward / adjoint.  MODE 1 (the recompute sweep of the gradient):
+// each stage also stores the second difference D of its level at its own
+// points into row d_row0 + d_dir (s-1) of dstore, from E (cE) read with plain
+// loads.  MODE 2 (the adjoint sweep with the imaging condition): the
+// accumulator gacc at each own point takes g += level(n+s) D[l_row0 + l_dir
+// (s-1)] for s = 1..T in that order; with T = 2 stage 2 does both, its queue
+// centre being level n+1 of its own points.
+template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB, int MODE>
 __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &st, const TMaps &mp,
                                              const int blk)
 {
-    using S = TShape<R, T, V, VY, BZ, BY, P, MB>;
+    using S = TShape<R, T, V, VY, BZ, BY, P, MB, MODE>;
     constexpr int QL = 2 * R + 1, V2 = V / 2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *ringA = smem_raw;
@@ -412,6 +476,8 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                     tma_load_3d(sl + S::A_UM, &mp.um, gz0, gy0, c0 - R, fullA + s);
                     tma_load_3d(sl + S::A_B, &mp.B, gz0, gy0, c0 - R, fullA + s);
                     tma_load_3d(sl + S::A_CC, &mp.C, gz0, gy0, c0 - R, fullA + s);
+                    if constexpr (S::XA >= 1) tma_load_3d(sl + S::A_X0, &mp.x0, gz0, gy0, c0 - R, fullA + s);
+                    if constexpr (S::XA >= 2) tma_load_3d(sl + S::A_X1, &mp.x1, gz0, gy0, c0 - R, fullA + s);
                 }
                 // bring the first-touch inputs of iteration i + LP into L2, so
                 // that its loads above wait for L2 rather than HBM (the centre
@@ -423,6 +489,8 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                         tma_prefetch_3d(&mp.um, gz0, gy0, c0 + S::LP - R);
                         tma_prefetch_3d(&mp.B, gz0, gy0, c0 + S::LP - R);
                         tma_prefetch_3d(&mp.C, gz0, gy0, c0 + S::LP - R);
+                        if constexpr (S::XA >= 1) tma_prefetch_3d(&mp.x0, gz0, gy0, c0 + S::LP - R);
+                        if constexpr (S::XA >= 2) tma_prefetch_3d(&mp.x1, gz0, gy0, c0 + S::LP - R);
                     }
                 }
                 if (++s == S::DA) { s = 0; ++r; }
@@ -445,6 +513,18 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                 tma_load_3d(sl + S::B_UM, &mp.u2, tz0, ty0, X0 + j, fullB + s);
                 tma_load_3d(sl + S::B_B, &mp.B2, tz0, ty0, X0 + j, fullB + s);
                 tma_load_3d(sl + S::B_C, &mp.C2, tz0, ty0, X0 + j, fullB + s);
+                if constexpr (S::XBB >= 1) tma_load_3d(sl + S::B_Y0, &mp.y0, tz0, ty0, X0 + j, fullB + s);
+                if constexpr (S::XBB >= 2) tma_load_3d(sl + S::B_Y1, &mp.y1, tz0, ty0, X0 + j, fullB + s);
+                if constexpr (S::XBB >= 3) tma_load_3d(sl + S::B_Y2, &mp.y2, tz0, ty0, X0 + j, fullB + s);
+                // the gradient-mode arrays are first read here: into L2 ahead
+                if constexpr (S::XBB >= 1) {
+                    constexpr int LB = S::DB + 3;
+                    if (j + LB < nj) {
+                        tma_prefetch_3d(&mp.y0, tz0, ty0, X0 + j + LB);
+                        if constexpr (S::XBB >= 2) tma_prefetch_3d(&mp.y1, tz0, ty0, X0 + j + LB);
+                        if constexpr (S::XBB >= 3) tma_prefetch_3d(&mp.y2, tz0, ty0, X0 + j + LB);
+                    }
+                }
                 if (++s == S::DB) { s = 0; ++r; }
             }
             if constexpr (T == 2)
@@ -462,6 +542,8 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
         const int offF = ry * S::W1 + cz;                 // in stage-1 boxes and ring-1 planes
         const int offC = (ry + R) * S::WC + cz + S::RP;   // in the centre box
         const int gy = gy0 + ry, gz = gz0 + cz;
+        int wy0, wy1, wz0, wz1;  // the warp's rows and columns (injection scan)
+        warp_extent<V, VY>(gy, gz, wy0, wy1, wz0, wz1);
         float2 q[QL][VY][V2];
 #pragma unroll
         for (int k = 0; k < QL; ++k)
@@ -500,12 +582,46 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
             for (int v = 0; v < VY; ++v) ld2<V>(q[QL - 1][v], sl + S::A_F / 4 + offF + v * S::W1);
             if (i >= 2 * R) {
                 float2 un[VY][V2], cC[VY][V2];
-                tstage_update<R, V, VY, S::WC, S::W1>(un, cC, q, sl + S::A_C / 4 + offC,
-                                                      sl + S::A_UM / 4 + offF, sl + S::A_B / 4 + offF,
-                                                      sl + S::A_CC / 4 + offF, st);
                 const int cs = c00 + i - R;  // plane of level n+1
+                // gradient modes: the points of this plane the stage owns (T = 1:
+                // the tile; T = 2: the tile inside the stage-1 region, stage 1's
+                // second differences only), their index and E or D, G
+                constexpr bool DD1 = MODE == 1;
+                bool own[VY];
+                long long pix = 0;
+                float2 ex[VY][V2], dd[VY][V2];
+                if constexpr (S::XA >= 1) {
+                    // E (MODE 1) or this step's D row (MODE 2, T = 1) from the slot
+                    pix = (long long)cs * a.sx + (long long)gy * a.nz + gz;
+#pragma unroll
+                    for (int v = 0; v < VY; ++v) {
+                        own[v] = act && cs >= X0 && cs < X1 && gy + v >= ty0 && gy + v < ty0 + BY &&
+                                 gy + v < a.ny && gz >= tz0 && gz < tz0 + BZ && gz < a.nz;
+                        ld2<V>(ex[v], sl + S::A_X0 / 4 + offF + v * S::W1);
+                    }
+                }
+                tstage_update<R, V, VY, S::WC, S::W1, DD1>(un, cC, q, sl + S::A_C / 4 + offC,
+                                                           sl + S::A_UM / 4 + offF, sl + S::A_B / 4 + offF,
+                                                           sl + S::A_CC / 4 + offF, st, ex, dd);
                 if (any_inj && finj[cs - pbase])
-                    tstage_inject<V, VY>(un, cC, a, pinj[cs - pbase], pinj[cs - pbase + 1], gy, gz, a.q_row0);
+                    tstage_inject<V, VY, DD1>(un, cC, a, pinj[cs - pbase], pinj[cs - pbase + 1], gy, gz,
+                                              a.q_row0, wy0, wy1, wz0, wz1, dd);
+                if constexpr (MODE == 1) {
+#pragma unroll
+                    for (int v = 0; v < VY; ++v)
+                        if (own[v]) st2<V>(a.dstore + a.d_row0 * a.npad + pix + (long long)v * a.nz, dd[v]);
+                }
+                if constexpr (MODE == 2 && T == 1) {
+#pragma unroll
+                    for (int v = 0; v < VY; ++v)
+                        if (own[v]) {
+                            float2 g[V2];
+                            ld2<V>(g, sl + S::A_X1 / 4 + offF + v * S::W1);
+#pragma unroll
+                            for (int j = 0; j < V2; ++j) g[j] = __ffma2_rn(un[v][j], ex[v][j], g[j]);
+                            st2<V>(a.gacc + pix + (long long)v * a.nz, g);
+                        }
+                }
                 if constexpr (T == 1) {
 #pragma unroll
                     for (int v = 0; v < VY; ++v)
@@ -543,6 +659,8 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
             const int off1 = (ry + R) * S::W1 + cz + S::RP;  // in ring-1 planes
             const int offS = ry * BZ + cz;                   // in ring-B boxes
             const int gy = ty0 + ry, gz = tz0 + cz;
+            int wy0, wy1, wz0, wz1;
+            warp_extent<V, VY>(gy, gz, wy0, wy1, wz0, wz1);
             bool sok[VY];
 #pragma unroll
             for (int v = 0; v < VY; ++v) sok[v] = act && gy + v < a.ny && gz < a.nz;
@@ -582,18 +700,47 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                     }
                     const float *bp = reinterpret_cast<const float *>(ringB + (size_t)sb * S::BSLOT);
                     float2 un[VY][V2], cC[VY][V2];
-                    tstage_update<R, V, VY, S::W1, BZ>(un, cC, q, ring1 + (size_t)sc * (S::FBOXP / 4) + off1,
-                                                       bp + S::B_UM / 4 + offS, bp + S::B_B / 4 + offS,
-                                                       bp + S::B_C / 4 + offS, st);
+                    constexpr bool DD1 = MODE == 1;
+                    const long long pix = (long long)(c00 + i - 2 * R) * a.sx + (long long)gy * a.nz + gz;
+                    float2 ex[VY][V2], dd[VY][V2], d0[VY][V2];
+                    if constexpr (MODE != 0) {
+                        // E (MODE 1) or the two D rows (MODE 2) from the ring-B slot
+#pragma unroll
+                        for (int v = 0; v < VY; ++v) {
+                            if constexpr (MODE == 1) {
+                                ld2<V>(ex[v], bp + S::B_Y0 / 4 + offS + v * BZ);
+                            } else {
+                                ld2<V>(d0[v], bp + S::B_Y0 / 4 + offS + v * BZ);
+                                ld2<V>(ex[v], bp + S::B_Y1 / 4 + offS + v * BZ);
+                            }
+                        }
+                    }
+                    tstage_update<R, V, VY, S::W1, BZ, DD1>(un, cC, q, ring1 + (size_t)sc * (S::FBOXP / 4) + off1,
+                                                            bp + S::B_UM / 4 + offS, bp + S::B_B / 4 + offS,
+                                                            bp + S::B_C / 4 + offS, st, ex, dd);
                     const int cs = c00 + i - 2 * R;  // plane of level n+2, in [X0, X1)
                     if (any_inj && finj[cs - pbase])
-                        tstage_inject<V, VY>(un, cC, a, pinj[cs - pbase], pinj[cs - pbase + 1], gy, gz,
-                                             a.q_row0 + a.q_dir);
+                        tstage_inject<V, VY, DD1>(un, cC, a, pinj[cs - pbase], pinj[cs - pbase + 1], gy, gz,
+                                                  a.q_row0 + a.q_dir, wy0, wy1, wz0, wz1, dd);
 #pragma unroll
                     for (int v = 0; v < VY; ++v)
                         if (sok[v]) {
                             st2<V>(oh + (long long)v * a.nz, un[v]);
                             st2<V>(ol + (long long)v * a.nz, q[R][v]);
+                            if constexpr (MODE == 1)
+                                st2<V>(a.dstore + (a.d_row0 + a.d_dir) * a.npad + pix + (long long)v * a.nz, dd[v]);
+                            if constexpr (MODE == 2) {
+                                // g += nu^{n+1} D[row 0] (stage 1's level: this
+                                // queue's centre), then g += nu^{n+2} D[row 1]
+                                float2 g[V2];
+                                ld2<V>(g, bp + S::B_Y2 / 4 + offS + v * BZ);
+#pragma unroll
+                                for (int j = 0; j < V2; ++j) {
+                                    g[j] = __ffma2_rn(q[R][v][j], d0[v][j], g[j]);
+                                    g[j] = __ffma2_rn(un[v][j], ex[v][j], g[j]);
+                                }
+                                st2<V>(a.gacc + pix + (long long)v * a.nz, g);
+                            }
                         }
                     oh += a.sx;
                     ol += a.sx;
@@ -642,12 +789,12 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
 
 // MB: resident blocks per SM the variant is compiled for (the
 // __launch_bounds__ minimum, which caps the registers per thread).
-template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB>
-__global__ void __launch_bounds__(TShape<R, T, V, VY, BZ, BY, P, MB>::NTB, MB)
+template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB, int MODE = 0>
+__global__ void __launch_bounds__(TShape<R, T, V, VY, BZ, BY, P, MB, MODE>::NTB, MB)
 tsweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stencil st,
               const __grid_constant__ TMaps mp)
 {
-    tsweep_block<R, T, V, VY, BZ, BY, P, MB>(a, st, mp, blockIdx.x);
+    tsweep_block<R, T, V, VY, BZ, BY, P, MB, MODE>(a, st, mp, blockIdx.x);
 }
 
 }  // namespace wt

@@ -73,6 +73,19 @@
 #define WAVE_SWEEP_MODE_VARIANTS_R2(Y) Y(2, 1, 8, 64, 16, 2, 2, 1) Y(2, 1, 8, 64, 16, 2, 2, 2)
 #define WAVE_SWEEP_MODE_VARIANTS_R4(Y) Y(4, 1, 4, 64, 8, 2, 3, 1) Y(4, 1, 4, 64, 8, 2, 3, 2)
 
+// Gradient-mode variants of the stage-specialised sweep, Z(R, T, V, VY, BZ, BY,
+// P, MB, MODE): MODE 1 (second differences stored; E streamed through TMA),
+// MODE 2 (imaging condition; the D rows and G streamed through TMA).  A
+// stage-specialised plan runs the mode variant of its own shape, or else the
+// first of its depth (every shape gives the same bits); the extra boxes make
+// the depth-2 slots larger, so so 8 has its own 32x32 shape.
+#define WAVE_TSWEEP_MODE_VARIANTS_R2(Z)                                                            \
+    Z(2, 1, 4, 1, 64, 8, 2, 2, 1) Z(2, 1, 4, 1, 64, 8, 2, 2, 2) Z(2, 2, 4, 2, 128, 12, 1, 1, 1)    \
+    Z(2, 2, 4, 2, 128, 12, 1, 1, 2)
+#define WAVE_TSWEEP_MODE_VARIANTS_R4(Z)                                                            \
+    Z(4, 1, 4, 2, 64, 16, 2, 2, 1) Z(4, 1, 4, 2, 64, 16, 2, 2, 2) Z(4, 2, 4, 2, 32, 32, 1, 1, 1)   \
+    Z(4, 2, 4, 2, 32, 32, 1, 1, 2)
+
 // Batched-kernel shape per radius (its default untiled shape): all shots of a
 // batch advance in one launch per time step.
 #define WAVE_MULTI_R1 1, 1, 2, 64, 8, 3, 3

@@ -438,7 +438,11 @@ int default_chunk(const Dims &d, const SweepVariant *v)
     return best;
 }
 
-// The gradient-mode variant (XB = mode) of untiled shape v, or nullptr.
+// Rows per thread of a variant (sweep.cuh variants: one).
+int rows_of(const SweepVariant *v) { return v->VY > 0 ? v->VY : 1; }
+
+// The gradient-mode variant (XB = mode) of shape v (same kernel family,
+// tile, rows and, for the stage-specialised sweep, prefetch), or nullptr.
 const SweepVariant *mode_variant(const SweepVariant *v, int mode)
 {
     const SweepVariant *vs = nullptr;
@@ -446,13 +450,14 @@ const SweepVariant *mode_variant(const SweepVariant *v, int mode)
     if (v->R == 2) nv = wt::sweep_mode_variants_r2(&vs);
     if (v->R == 4) nv = wt::sweep_mode_variants_r4(&vs);
     for (int i = 0; i < nv; ++i)
-        if (vs[i].T == v->T && vs[i].V == v->V && vs[i].BZ == v->BZ && vs[i].BY == v->BY && vs[i].XB == mode)
+        if (vs[i].T == v->T && vs[i].V == v->V && vs[i].BZ == v->BZ && vs[i].BY == v->BY && vs[i].XB == mode &&
+            vs[i].kind == v->kind && rows_of(&vs[i]) == rows_of(v) && (v->kind == 0 || vs[i].P == v->P))
             return &vs[i];
+    if (v->kind == 1)  // another shape of the same family and depth
+        for (int i = 0; i < nv; ++i)
+            if (vs[i].T == v->T && vs[i].XB == mode && vs[i].kind == 1) return &vs[i];
     return nullptr;
 }
-
-// Rows per thread of a variant (sweep.cuh variants: one).
-int rows_of(const SweepVariant *v) { return v->VY > 0 ? v->VY : 1; }
 
 // Whether variant v is of the kernel family `kernel` names (wave_tuning.kernel:
 // 0 any, 1 the sweep of sweep.cuh, 2 the stage-specialised sweep).
@@ -656,6 +661,22 @@ int build_launch(const Job &job, const State &s, int j, const SweepVariant *v, i
         if (!rc && v->T == 2) rc = encode_map(&tm->u2, s.buf[s.a], d, v->BZ, v->BY);
         if (!rc && v->T == 2) rc = encode_map(&tm->B2, job.cB, d, v->BZ, v->BY);
         if (!rc && v->T == 2) rc = encode_map(&tm->C2, job.cC, d, v->BZ, v->BY);
+        // gradient modes (XB = MODE): E, or this launch's D rows and G
+        if (!rc && v->XB == 1) {
+            rc = encode_map(&tm->x0, job.cE, d, v->W1, v->H1);
+            if (!rc && v->T == 2) rc = encode_map(&tm->y0, job.cE, d, v->BZ, v->BY);
+        }
+        if (!rc && v->XB == 2) {
+            const long long row = job.l_base + (long long)job.l_dir * j;  // the launch's first D row
+            if (v->T == 1) {
+                rc = encode_map(&tm->x0, job.dload + row * d.npad, d, v->W1, v->H1);
+                if (!rc) rc = encode_map(&tm->x1, job.gacc, d, v->W1, v->H1);
+            } else {
+                rc = encode_map(&tm->y0, job.dload + row * d.npad, d, v->BZ, v->BY);
+                if (!rc) rc = encode_map(&tm->y1, job.dload + (row + job.l_dir) * d.npad, d, v->BZ, v->BY);
+                if (!rc) rc = encode_map(&tm->y2, job.gacc, d, v->BZ, v->BY);
+            }
+        }
         if (rc) return rc;
     } else {
         rc = encode_map(&mp->u, s.buf[s.a], d, v->PW, v->H0);
@@ -664,8 +685,10 @@ int build_launch(const Job &job, const State &s, int j, const SweepVariant *v, i
         if (!rc) rc = encode_map(&mp->C, job.cC, d, v->W0, v->HK);
     }
     if (!rc && v->kind == 0 && v->T == 1) rc = encode_map(&mp->uk, s.buf[s.a], d, v->W0, v->HK);
-    if (!rc && v->XB == 1) rc = encode_map(&mp->x0, job.cE, d, v->W0, v->HK);
-    if (!rc && v->XB == 2) {
+    // the extra boxes of sweep.cuh's gradient modes (the stage-specialised
+    // sweep reads its gradient-mode arrays with plain loads)
+    if (!rc && v->kind == 0 && v->XB == 1) rc = encode_map(&mp->x0, job.cE, d, v->W0, v->HK);
+    if (!rc && v->kind == 0 && v->XB == 2) {
         const long long row = job.l_base + (long long)job.l_dir * j;  // this step's D row
         rc = encode_map(&mp->x0, job.dload + row * d.npad, d, v->W0, v->HK);
         if (!rc) rc = encode_map(&mp->x1, job.gacc, d, v->W0, v->HK);
@@ -829,15 +852,16 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         // streams their extra inputs (E, or D and G) through TMA
         const int mode = job.gacc != nullptr ? 2 : (job.dstore != nullptr ? 1 : 0);
         if (mode > 0 && v->kind == 1) {
-            // the stage-specialised sweep has no second-difference or
-            // imaging-condition mode: the untiled default of sweep.cuh (whose
+            // a stage-specialised shape runs its gradient-mode variant where one
+            // is compiled; otherwise the untiled default of sweep.cuh (whose
             // gradient-mode variants stream the extra arrays through TMA, and
             // whose wavefield is bitwise the same) runs the gradient sweeps
-            v = find_variant(R, 1, 0, 0, 0, 1);
+            const SweepVariant *mv = mode_variant(v, mode);
+            v = mv != nullptr ? mv : find_variant(R, 1, 0, 0, 0, 1);
             if (v == nullptr) return WAVE_EUNSUPPORTED;
             chunk = std::min(plan.chunk_given ? chunk : default_chunk(d, v), max_chunk(v));
         }
-        if (mode > 0 && v->T == 1) {
+        if (mode > 0 && v->kind == 0 && v->T == 1) {
             const SweepVariant *mv = mode_variant(v, mode);
             if (mv != nullptr) {
                 // the plan's chunk was chosen for the plain variant, whose
@@ -1141,6 +1165,133 @@ int resolve_plan(const Dims &d, const wave_grid *g, const wave_tuning *t, bool m
     g_tune_cache[key] = p;
     cache_store_file(key, p);
     *out = p;
+    return WAVE_OK;
+}
+
+// The family that runs the gradient sweeps of wave_grad (the recompute sweep
+// storing second differences, and the adjoint sweep with the imaging
+// condition).  Which family and depth is fastest there depends on the grid --
+// the shared-warp untiled sweep streams E, D and G through TMA with three or
+// four blocks per SM, the stage-specialised sweeps save DRAM bytes but hold
+// fewer warps, and a block that injects many points waits on their table and
+// trace loads every plane -- so the candidates are timed once per (grid,
+// forward plan, source and receiver counts) on the workspace's scratch state
+// with the call's own sources and receivers, a few steps of each mode, and
+// the fastest kept.  Returns the plan run_steps is given for those sweeps; run_steps picks
+// the mode variant of its shape.  Every candidate gives the same bits.
+struct GradKey {
+    int nx, ny, nz, so, dev, nsrc, nrec;
+    const SweepVariant *v;
+    bool operator<(const GradKey &o) const
+    {
+        return std::tie(nx, ny, nz, so, dev, nsrc, nrec, v) <
+               std::tie(o.nx, o.ny, o.nz, o.so, o.dev, o.nsrc, o.nrec, o.v);
+    }
+};
+std::mutex g_grad_mu;
+std::map<GradKey, Plan> g_grad_cache;
+
+int grad_plan(const Dims &d, const wave_grid *g, const Plan &fwd, const Stencil &st, const float *cB,
+              const float *cC, const float *cE, float *const U[4], float *store, int store_rows, float *G,
+              int *status, const PointTable &src, const float *src_traces, int nsrc, const PointTable &rec,
+              const float *rec_resid, int nrec, cudaStream_t stream, Plan *out)
+{
+    const int R = g->space_order / 2;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const GradKey key{d.nx, d.ny, d.nz, g->space_order, dev, nsrc, nrec, fwd.v};
+    {
+        std::lock_guard<std::mutex> lk(g_grad_mu);
+        auto it = g_grad_cache.find(key);
+        if (it != g_grad_cache.end()) {
+            *out = it->second;
+            return WAVE_OK;
+        }
+    }
+    std::vector<Plan> cands;
+    Plan p0;  // the untiled default of sweep.cuh: its own mode variants
+    p0.v = find_variant(R, 1, 0, 0, 0, 1);
+    if (p0.v == nullptr) return WAVE_EUNSUPPORTED;
+    p0.chunk = default_chunk(d, p0.v);
+    cands.push_back(p0);
+    if (fwd.v->kind == 1) {
+        // the plan's own depth, and the untiled staged shape, where mode variants exist
+        for (int T : {fwd.v->T, 1}) {
+            const SweepVariant *base = T == fwd.v->T ? fwd.v : find_variant(R, 1, 0, 0, 0, 2);
+            if (base == nullptr || mode_variant(base, 1) == nullptr || mode_variant(base, 2) == nullptr) continue;
+            Plan p;
+            p.v = base;
+            p.chunk = fwd.chunk_given ? fwd.chunk : default_chunk(d, mode_variant(base, 2));
+            p.chunk_given = fwd.chunk_given;
+            bool dup = false;
+            for (const Plan &c : cands) dup |= mode_variant(c.v, 2) == mode_variant(p.v, 2);
+            if (!dup) cands.push_back(p);
+        }
+    }
+    Plan best = cands[0];
+    if (cands.size() > 1) {
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        int rc = WAVE_OK;
+        const int steps = std::min(8, store_rows);  // rows of the second-difference store
+        for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(U[k], 0, sizeof(float) * d.npad, stream));
+        for (int pass = 0; pass < 2 && rc == WAVE_OK; ++pass) {
+            for (const Plan &p : cands) {
+                // recompute (second differences into store rows 0..7) then
+                // adjoint (imaging condition from those rows into G), on zero
+                // fields without sparse points
+                Job rj;
+                rj.d = d;
+                rj.st = st;
+                rj.cB = cB;
+                rj.cC = cC;
+                rj.cE = cE;
+                rj.status = status;
+                rj.dstore = store;
+                rj.inj = src;
+                rj.q = src_traces;
+                rj.nq = nsrc;
+                Job aj = rj;
+                aj.dstore = nullptr;
+                aj.cE = nullptr;
+                aj.inj = rec;
+                aj.q = rec_resid;
+                aj.nq = nrec;
+                aj.q_base = steps - 1;
+                aj.q_dir = -1;
+                aj.dload = store;
+                aj.l_base = steps - 1;
+                aj.l_dir = -1;
+                aj.gacc = G;
+                State s1, s2;
+                for (int k = 0; k < 4; ++k) s1.buf[k] = s2.buf[k] = U[k];
+                float ms = 0.f;
+                if (cudaEventRecord(e0, stream) != cudaSuccess) { rc = WAVE_ECUDA; break; }
+                if ((rc = run_steps(rj, s1, steps, p, stream))) break;
+                if ((rc = run_steps(aj, s2, steps, p, stream))) break;
+                if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    rc = WAVE_ECUDA;
+                    break;
+                }
+                if (pass == 1 && ms < 0.99f * best_ms) {  // ties keep the earlier candidate
+                    best_ms = ms;
+                    best = p;
+                }
+                if (tune_log() && pass == 1)
+                    std::fprintf(stderr, "wave gradient sweeps: kernel=%d T=%d tile=%dx%d: %.4f ms for %d steps\n",
+                                 p.v->kind + 1, p.v->T, p.v->BZ, p.v->BY, ms, 2 * steps);
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) return rc;
+    }
+    std::lock_guard<std::mutex> lk(g_grad_mu);
+    g_grad_cache[key] = best;
+    *out = best;
     return WAVE_OK;
 }
 
@@ -1781,7 +1932,13 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
         if ((rc = prep_model(d, g, tuning, m, damp, L, stream))) return rc;
         Plan plan;
         if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, L.status, stream, &plan))) return rc;
+        // the sweeps below run in the gradient modes: the family chosen for them
+        Plan fplan = plan;
+        const int store_rows = std::max(1, std::min(ckpt_every, nt));
         if ((rc = upload_table(ts, L.inj, stream)) || (rc = upload_table(tr, L.inj2, stream))) return rc;
+        if ((rc = grad_plan(d, g, fplan, st, L.cB, L.cC, L.cE, L.U, L.store, store_rows, L.G, L.status,
+                            L.inj.view(), src_traces, nsrc, L.inj2.view(), rec_resid, nrec, stream, &plan)))
+            return rc;
         CK(cudaMemsetAsync(L.G, 0, sizeof(float) * d.npad, stream));
         for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.V[i], 0, sizeof(float) * d.npad, stream));
         State adj;

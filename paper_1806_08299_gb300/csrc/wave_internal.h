@@ -132,13 +132,13 @@ cudaError_t launch_sweep(int nblocks, cudaStream_t stream, const SweepArgs &a, c
     return cudaLaunchKernelEx(&cfg, sweep_kernel<R, T, V, BZ, BY, P, MB, XB>, a, st, m);
 }
 
-template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB>
+template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB, int MODE = 0>
 cudaError_t launch_tsweep(int nblocks, cudaStream_t stream, const SweepArgs &a, const Stencil &st,
                           const TMaps &m)
 {
-    using S = TShape<R, T, V, VY, BZ, BY, P, MB>;
+    using S = TShape<R, T, V, VY, BZ, BY, P, MB, MODE>;
     const size_t smem = S::smem_bytes(a.chunk);
-    cudaError_t e = allow_max_dynamic_smem((const void *)tsweep_kernel<R, T, V, VY, BZ, BY, P, MB>);
+    cudaError_t e = allow_max_dynamic_smem((const void *)tsweep_kernel<R, T, V, VY, BZ, BY, P, MB, MODE>);
     if (e != cudaSuccess) return e;
     // programmatic dependent launch, as launch_sweep
     cudaLaunchAttribute attr[1];
@@ -151,7 +151,7 @@ cudaError_t launch_tsweep(int nblocks, cudaStream_t stream, const SweepArgs &a, 
     cfg.stream = stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, tsweep_kernel<R, T, V, VY, BZ, BY, P, MB>, a, st, m);
+    return cudaLaunchKernelEx(&cfg, tsweep_kernel<R, T, V, VY, BZ, BY, P, MB, MODE>, a, st, m);
 }
 
 template <int R, int T, int V, int BZ, int BY, int P, int MB>
@@ -197,15 +197,17 @@ cudaError_t launch_sweep_multi(int nblocks, size_t smem, cudaStream_t stream, co
      &wt::launch_sweep<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>,                                      \
      (const void *)&wt::sweep_kernel<R_, T_, V_, BZ_, BY_, P_, MB_, XB_>, XB_},
 
-#define WAVE_TVARIANT_ENTRY(R_, T_, V_, VY_, BZ_, BY_, P_, MB_)                                  \
-    {R_, T_, V_, BZ_, BY_, P_, wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>::NTB, 0, 0, 0, 0,     \
-     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>::SMEM, nullptr,                                \
-     (const void *)&wt::tsweep_kernel<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>, 0, 1, VY_,              \
-     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>::W1,                                           \
-     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>::H1,                                           \
-     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>::WC,                                           \
-     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>::HC,                                           \
-     &wt::launch_tsweep<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>},
+#define WAVE_TMODE_ENTRY(R_, T_, V_, VY_, BZ_, BY_, P_, MB_, M_)                                 \
+    {R_, T_, V_, BZ_, BY_, P_, wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, M_>::NTB, 0, 0, 0, 0, \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, M_>::SMEM, nullptr,                            \
+     (const void *)&wt::tsweep_kernel<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, M_>, M_, 1, VY_,         \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, M_>::W1,                                       \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, M_>::H1,                                       \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, M_>::WC,                                       \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, M_>::HC,                                       \
+     &wt::launch_tsweep<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, M_>},
+#define WAVE_TVARIANT_ENTRY(R_, T_, V_, VY_, BZ_, BY_, P_, MB_) \
+    WAVE_TMODE_ENTRY(R_, T_, V_, VY_, BZ_, BY_, P_, MB_, 0)
 
 #define WAVE_DEFINE_MULTI(R_, T_, V_, BZ_, BY_, P_, MB_)                                         \
     namespace wt {                                                                                \
@@ -223,7 +225,8 @@ cudaError_t launch_sweep_multi(int nblocks, size_t smem, cudaStream_t stream, co
 #define WAVE_DEFINE_MODES(r_)                                                                     \
     namespace wt {                                                                                \
     static const SweepVariant kModeVariants_r##r_[] = {                                           \
-        WAVE_SWEEP_MODE_VARIANTS_R##r_(WAVE_MODE_VARIANT_ENTRY)};                                 \
+        WAVE_SWEEP_MODE_VARIANTS_R##r_(WAVE_MODE_VARIANT_ENTRY)                                    \
+            WAVE_TSWEEP_MODE_VARIANTS_R##r_(WAVE_TMODE_ENTRY)};                                     \
     int sweep_mode_variants_r##r_(const SweepVariant **out)                                       \
     {                                                                                             \
         *out = kModeVariants_r##r_;                                                               \

@@ -106,3 +106,37 @@ def test_autograd_matches_wave_grad(wavelib, cuda):
     torch.cuda.synchronize()
     assert torch.equal(tm.grad, g)
     assert torch.isfinite(g).all() and g.abs().max() > 0
+
+
+@pytest.mark.parametrize("so", [8, 4])
+def test_staged_gradient_modes_bitwise(wavelib, cuda, oracle, so):
+    """The gradient sweeps of the stage-specialised kernel (second differences
+    stored by the recompute sweep, imaging condition fused into the adjoint
+    sweep, at depth 1 and 2) give the untiled gradient of the shared-warp
+    kernel bit for bit, which is at parity with the oracle; ragged last
+    segment, x-chunks shorter and longer than the stencil reach."""
+    import torch
+    n = (37, 52, 45)
+    nt, k = 23, 9
+    grid, h, dt, m, damp, src, q, rec = _setup(wavelib, n, so, nt, seed=41 + so, nsrc=2, nrec=7)
+    res = np.random.default_rng(5).standard_normal((nt, len(rec))).astype(np.float32)
+    tm, td, tq, tr = _t(m, cuda), _t(damp, cuda), _t(q, cuda), _t(res, cuda)
+
+    def grad(tune):
+        _, _, ckpt, _ = wavelib.fwd(grid, tm, td, src, tq, rec, tuning=tune, ckpt_every=k)
+        g, ws = wavelib.grad(grid, tm, td, src, tq, rec, tr, ckpt, k, tuning=tune)
+        assert wavelib.status(ws) == 0
+        torch.cuda.synchronize()
+        return g.cpu().numpy()
+
+    g1 = grad(wavelib.Tuning(time_tile=1, kernel=wavelib.WAVE_KERNEL_SHARED))
+    gref = oracle.gradient(_f64(m), _f64(damp), h, dt, nt, so, _f64(src), _f64(q), _f64(rec), _f64(res))
+    assert _relerr(g1, gref) <= TOL
+    for T in (1, 2):
+        shapes = [v for v in wavelib.list_variants(so)
+                  if v["kernel"] == wavelib.WAVE_KERNEL_STAGED and v["time_tile"] == T]
+        for v in shapes:
+            for tile_x in (5, 17):
+                tune = wavelib.Tuning(time_tile=T, tile_y=v["tile_y"], tile_z=v["tile_z"], tile_x=tile_x,
+                                      kernel=wavelib.WAVE_KERNEL_STAGED, rows=v["rows"])
+                assert np.array_equal(grad(tune), g1), (T, v, tile_x)
