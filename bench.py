@@ -560,7 +560,7 @@ def _fwi_survey(dev, inputs, wave, args):
     q = [torch.from_numpy(x).to(dev) for x in sv.src_q]
     k = 50
     conc = min(len(shots), 8)  # shots per lockstep group (8 groups of 8 for the whole survey)
-    tune = wave.Tuning(time_tile=1)
+    tune = wave.Tuning()  # each group times its forward kernel (once per group shape, cached)
     ws_f = torch.empty(wave.batch_workspace_bytes(grid, shots, 0, conc), dtype=torch.uint8, device=dev)
     ws_g = torch.empty(wave.batch_workspace_bytes(grid, shots, k, conc), dtype=torch.uint8, device=dev)
 
@@ -574,11 +574,22 @@ def _fwi_survey(dev, inputs, wave, args):
     torch.cuda.synchronize()
     ms, _ = _timed(step, 1, torch.cuda.current_stream())
     pts = sum(int(np.prod(x["n"])) for x in sv.shots)
+    plan_f = wave.describe_batch_plan(grid, shots, 0, conc, tune)
+    plan_g = wave.describe_batch_plan(grid, shots, k, conc, tune)
+
+    def kname(p):
+        if p is None:
+            return "per shot"
+        return "%s T=%d %dx%d rows %d" % ("staged" if p["kernel"] == wave.WAVE_KERNEL_STAGED else "shared-warp",
+                                          p["time_tile"], p["tile_z"], p["tile_y"], p["rows"])
     return {"s_per_shot": ms / 1e3 / len(shots),
             "workload": "c5: %d of 64 shots (windows of a 512x512x256 layered model), so8, "
-                        "%d steps, k = %d, %d shots per lockstep group (one launch per time step, CUDA graph); "
-                        "batched forward + batched gradient"
+                        "%d steps, k = %d, %d shots per lockstep group (one launch per step or per T steps, "
+                        "CUDA graph); batched forward + batched gradient"
                         % (len(shots), sv.nt, k, conc),
+            "forward_kernel": kname(plan_f),
+            "gradient_forward_kernel": kname(plan_g),
+            "gradient_recompute_adjoint_kernel": "shared-warp batched kernel, T=1",
             "status": wave.status(ws_g),
             "gpts_equiv": 4 * pts * sv.nt / (ms / 1e3) / 1e9}
 

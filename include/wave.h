@@ -292,15 +292,25 @@ size_t wave_batch_workspace_bytes(const wave_grid *g, int32_t nshots, const wave
  * src_traces: device, the shots' [nt][nsrc_s] blocks one after another (shot
  * order); rec_traces: device out, the shots' [nt][nrec_s] blocks likewise.
  * Shots run in groups of `concurrency` consecutive shots; the window of m
- * and damp of each is copied into the workspace first.  With the untiled
- * default plan (tuning NULL or time_tile 0 or 1 with the default shape) the
- * shots of a group advance in lockstep on `stream`: one launch of the batched
- * sweep kernel per time step covers every shot of the group.  Any other plan
- * runs wave_fwd per shot on library-owned streams that wait for `stream` at
- * the start and that `stream` waits for at the end.  tuning applies to every
- * shot; time_tile == 0 means the default untiled variant (no per-shape
- * autotuning).  wave_status(ws, stream) reports the most severe device status
- * of all shots.  Results equal wave_fwd on each window, bit for bit. */
+ * and damp of each is copied into the workspace first.  The shots of a group
+ * advance in lockstep on `stream` when a batched kernel runs the plan: one
+ * launch covers every shot of the group per time step (batched kernel of the
+ * shared-warp family) or per T steps (batched stage-specialised kernel).
+ *   - tuning NULL or time_tile 0: the group times the forward kernel (the
+ *     shared-warp batched kernel and every batched stage-specialised shape
+ *     whose depth divides nt and ckpt_every) on its own shots for a few
+ *     steps, once per device, order and group shape, and caches the choice;
+ *   - kernel WAVE_KERNEL_STAGED with time_tile T: the batched
+ *     stage-specialised shape of depth T (and tile_y, tile_z, vec, rows where
+ *     given), if compiled and T divides nt and ckpt_every;
+ *   - time_tile 1 with the default shape: the shared-warp batched kernel.
+ * Any other plan runs wave_fwd per shot on library-owned streams that wait
+ * for `stream` at the start and that `stream` waits for at the end.  tuning
+ * applies to every shot; the per-shape autotuning flags are ignored.  The
+ * gradient's recompute and adjoint phases run on the shared-warp batched
+ * kernel.  wave_status(ws, stream) reports the most severe device status of
+ * all shots.  Results equal wave_fwd on each window, bit for bit, whichever
+ * kernel runs. */
 int32_t wave_fwd_batched(const wave_grid *g, int32_t nshots, const wave_shot *shots,
                          const float *m, const float *damp, const float *src_traces,
                          float *rec_traces, int32_t concurrency, const wave_tuning *tuning,
@@ -319,6 +329,17 @@ int32_t wave_grad_batched(const wave_grid *g, int32_t nshots, const wave_shot *s
                           const float *rec_resid, int32_t ckpt_every, float *grad,
                           int32_t concurrency, const wave_tuning *tuning, void *ws,
                           size_t ws_bytes, void *stream);
+
+/* The forward kernel the first group of a batched call with these
+ * arguments runs: out[0..7] as wave_describe_plan (time_tile, tile_y, 0,
+ * tile_z, vec, prefetch, kernel family, rows), out[8] = 1 for lockstep
+ * groups.  All nine are 0 when the plan runs shot by shot, and out[0] is 0
+ * while an autotuned group (time_tile 0) has not been timed yet on the
+ * current device.  out: HOST, 9 ints.  Returns WAVE_OK, WAVE_EINVAL or
+ * WAVE_ECUDA.  No device work is queued. */
+int32_t wave_describe_batch_plan(const wave_grid *g, int32_t nshots, const wave_shot *shots,
+                                 int32_t ckpt_every, int32_t concurrency, const wave_tuning *tuning,
+                                 int32_t *out);
 
 /* Size in bytes of the static device workspace behind wave_fwd_noalloc. */
 #define WAVE_NOALLOC_MAX_BYTES (32u * 1024u * 1024u)

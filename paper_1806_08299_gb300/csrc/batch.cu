@@ -5,9 +5,10 @@
 // the caller's workspace: the window of m and damp, the single-shot
 // workspace and, for the gradient, the checkpoints and the window gradient.
 //
-//  * Lockstep (the default untiled plan): the shots of a group advance
-//    together, one launch of the batched kernel per time step for all of
-//    them, on the caller's stream (host runtime, wave_api.cu).
+//  * Lockstep (the default plan, or a plan of a batched kernel): the shots
+//    of a group advance together, one launch of a batched kernel per time
+//    step (or per T steps of the stage-specialised one) for all of them, on
+//    the caller's stream (host runtime, wave_api.cu).
 //  * Otherwise each shot runs wave_fwd / wave_grad on its slot's
 //    library-owned stream; the slot streams wait for the caller's stream at
 //    the start and the caller's stream waits for them at the end.
@@ -154,12 +155,13 @@ wave_tuning batch_tuning(const wave_tuning *t)
     wave_tuning u;
     std::memset(&u, 0, sizeof(u));
     if (t != nullptr) u = *t;
-    if (u.time_tile == 0) {
-        u.time_tile = 1;
+    if (u.time_tile == 0) {  // the lockstep engine times its forward kernel
         u.tile_y = 0;
         u.tile_x = 0;
         u.vec = 0;
         u.tile_z = 0;
+        u.rows = 0;
+        u.kernel = 0;
     }
     u.flags &= ~(WAVE_TIME_SWEEPS | WAVE_AUTOTUNE_SHAPE);
     return u;
@@ -297,7 +299,7 @@ int run_batch(const wave_grid *g, int nshots, const wave_shot *shots, const floa
         return WAVE_ECUDA;
     const int used = std::min(conc, nshots);
 
-    if (wt::lockstep_supported(g, &tune)) {
+    if (wt::lockstep_supported(g, &tune, k)) {
         for (int g0 = 0; g0 < nshots && rc == WAVE_OK; g0 += used) {
             const int n = std::min(used, nshots - g0);
             std::vector<wt::ShotSlot> sl(n);
@@ -375,6 +377,22 @@ int32_t wave_fwd_batched(const wave_grid *g, int32_t nshots, const wave_shot *sh
     try {
         return run_batch(g, nshots, shots, m, damp, src_traces, rec_traces, nullptr, 0, nullptr, concurrency,
                          tuning, ws, ws_bytes, (cudaStream_t)stream);
+    } catch (...) {
+        return WAVE_EINVAL;
+    }
+}
+
+int32_t wave_describe_batch_plan(const wave_grid *g, int32_t nshots, const wave_shot *shots,
+                                 int32_t ckpt_every, int32_t concurrency, const wave_tuning *tuning,
+                                 int32_t *out)
+{
+    SlotLayout L;
+    if (out == nullptr || ckpt_every < 0 || layout(g, nshots, shots, ckpt_every, conc_of(concurrency), &L))
+        return WAVE_EINVAL;
+    try {
+        const wave_tuning tune = batch_tuning(tuning);
+        return wt::lockstep_describe(g, std::min(conc_of(concurrency), (int)nshots), shots, ckpt_every, &tune,
+                                     out);
     } catch (...) {
         return WAVE_EINVAL;
     }

@@ -6,3 +6,4 @@ WAVE_DEFINE_RADIUS(4)
 #define WAVE_MULTI_ARGS(...) WAVE_DEFINE_MULTI(__VA_ARGS__)
 WAVE_MULTI_ARGS(WAVE_MULTI_R4)
 WAVE_DEFINE_MODES(4)
+WAVE_DEFINE_TMULTI(4)

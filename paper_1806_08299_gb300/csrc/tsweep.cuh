@@ -798,3 +798,50 @@ tsweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stenc
 }
 
 }  // namespace wt
+
+namespace wt {
+
+// One shot of a batched launch of the stage-specialised sweep, in device
+// memory: its arguments and TMA descriptors for both parities of its buffer
+// rotation (the row fields of the arguments hold the rows of step 0).
+struct ShotTSweep {  // 128-byte aligned, as its tensor maps
+    TMaps mp[2];
+    SweepArgs a[2];
+};
+
+// Every shot of a batch advanced by one launch (T time steps): block i sweeps
+// tile block_map[i].y of shot block_map[i].x, the launch starts at time step
+// `step` of every shot, and `parity` selects their buffers (forward and
+// adjoint sweeps; the gradient modes run on the batched kernel of sweep.cuh).
+template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB>
+__global__ void __launch_bounds__(TShape<R, T, V, VY, BZ, BY, P, MB, 0>::NTB, MB)
+tsweep_multi_kernel(const ShotTSweep *__restrict__ shots, const int2 *__restrict__ block_map,
+                    const __grid_constant__ Stencil st, int parity, int step)
+{
+    using S = TShape<R, T, V, VY, BZ, BY, P, MB, 0>;
+    const int2 bm = block_map[blockIdx.x];
+    const ShotTSweep &sh = shots[bm.x];
+    const int pl = (int)threadIdx.x - (S::N1 + S::N2);  // producer lane
+    // the producer lanes' TMA reads these descriptors from global memory,
+    // which a host copy may have rewritten since a launch that read the same
+    // addresses: each lane acquires the ones it loads through
+    const TMaps &m = sh.mp[parity];
+    if (pl == 0) {
+        tensormap_acquire(&m.uc);
+        tensormap_acquire(&m.uf);
+        tensormap_acquire(&m.um);
+        tensormap_acquire(&m.B);
+        tensormap_acquire(&m.C);
+    } else if (T == 2 && pl == 1) {
+        tensormap_acquire(&m.u2);
+        tensormap_acquire(&m.B2);
+        tensormap_acquire(&m.C2);
+    }
+    SweepArgs la = sh.a[parity];
+    la.q_row0 += la.q_dir * step;
+    la.c_row0 += la.c_dir * step;
+    la.order = nullptr;
+    tsweep_block<R, T, V, VY, BZ, BY, P, MB, 0>(la, st, m, bm.y);
+}
+
+}  // namespace wt

@@ -86,6 +86,18 @@
     Z(4, 1, 4, 2, 64, 16, 2, 2, 1) Z(4, 1, 4, 2, 64, 16, 2, 2, 2) Z(4, 2, 4, 2, 32, 32, 1, 1, 1)   \
     Z(4, 2, 4, 2, 32, 32, 1, 1, 2)
 
+// Batched stage-specialised variants M(R, T, V, VY, BZ, BY, P, MB): the
+// forward and adjoint sweeps of a survey group on the stage-specialised
+// kernel, each the batched form of the single-shot variant of the same shape.
+#define WAVE_TMULTI_VARIANTS_R1(M)
+#define WAVE_TMULTI_VARIANTS_R2(M) M(2, 1, 4, 1, 64, 8, 2, 2) M(2, 2, 4, 2, 128, 12, 1, 1)
+#define WAVE_TMULTI_VARIANTS_R3(M)
+#define WAVE_TMULTI_VARIANTS_R4(M) M(4, 1, 4, 2, 64, 16, 2, 2) M(4, 2, 4, 2, 64, 24, 1, 1)
+#define WAVE_TMULTI_VARIANTS_R5(M)
+#define WAVE_TMULTI_VARIANTS_R6(M)
+#define WAVE_TMULTI_VARIANTS_R7(M)
+#define WAVE_TMULTI_VARIANTS_R8(M)
+
 // Batched-kernel shape per radius (its default untiled shape): all shots of a
 // batch advance in one launch per time step.
 #define WAVE_MULTI_R1 1, 1, 2, 64, 8, 3, 3

@@ -1340,6 +1340,27 @@ const wt::MultiVariant *multi_variant(int R)
     return mv;
 }
 
+int tmulti_variants(int R, const wt::TMultiVariant **out)
+{
+    switch (R) {
+    case 1: return wt::sweep_tmulti_variants_r1(out);
+    case 2: return wt::sweep_tmulti_variants_r2(out);
+    case 3: return wt::sweep_tmulti_variants_r3(out);
+    case 4: return wt::sweep_tmulti_variants_r4(out);
+    case 5: return wt::sweep_tmulti_variants_r5(out);
+    case 6: return wt::sweep_tmulti_variants_r6(out);
+    case 7: return wt::sweep_tmulti_variants_r7(out);
+    case 8: return wt::sweep_tmulti_variants_r8(out);
+    default: *out = nullptr; return 0;
+    }
+}
+
+// The single-shot variant whose shape a batched stage-specialised variant has.
+const SweepVariant *tmulti_shape(const wt::TMultiVariant *tm)
+{
+    return find_variant(tm->R, tm->T, tm->BY, tm->V, tm->BZ, 2, tm->VY);
+}
+
 struct LockShot {
     Dims d;
     wave_grid g;
@@ -1348,16 +1369,25 @@ struct LockShot {
     Job job;        // forward (or recompute) job of the current phase
     State s;        // forward / recompute state
     State adj;      // adjoint state (gradient)
-    int chunk = 0;
-    long long nblocks = 0;  // blocks of one launch (the same in every phase)
+    int chunk = 0;          // x-chunk of the batched kernel of sweep.cuh
+    long long nblocks = 0;  // its blocks per launch
+    int chunk_f = 0;          // x-chunk of the forward phase's stage-specialised kernel
+    long long nblocks_f = 0;  // its blocks per launch
 };
 
-// Table of a lockstep group: the block -> (shot, tile) map, then one row of
-// ShotSweep records (one per shot) per phase.
-size_t lock_table_bytes(int nshots, long long total_blocks, int nphases)
+// Bytes of one phase's per-shot records (either batched kernel's form).
+size_t lock_row_bytes(int nshots)
 {
-    return align_up(sizeof(int2) * (size_t)total_blocks) +
-           (size_t)nphases * align_up(sizeof(wt::ShotSweep) * (size_t)nshots);
+    return align_up(std::max(sizeof(wt::ShotSweep), sizeof(wt::ShotTSweep)) * (size_t)nshots);
+}
+
+// Table of a lockstep group: the block -> (shot, tile) maps of the batched
+// kernel of sweep.cuh and of the forward phase's stage-specialised kernel,
+// then one row of per-shot records per phase.
+size_t lock_table_bytes(int nshots, long long total_blocks, long long total_blocks_f, int nphases)
+{
+    return align_up(sizeof(int2) * (size_t)total_blocks) + align_up(sizeof(int2) * (size_t)total_blocks_f) +
+           (size_t)nphases * lock_row_bytes(nshots);
 }
 
 int lock_phases(int nt, int ckpt_every)
@@ -1384,63 +1414,98 @@ int capture_stream(cudaStream_t *out)
     return WAVE_OK;
 }
 
-// Where one lockstep group's phases put their arguments: host rows appended
-// per phase, the device copy at `dev` (uploaded before the graph runs).
 struct LockTable {
-    std::vector<wt::ShotSweep> rows;
-    std::vector<int2> block_map;  // launch block -> (shot, tile)
+    std::vector<char> rows;          // one row of per-shot records per phase, lock_row_bytes each
+    std::vector<int2> block_map;     // sweep.cuh batched kernel: launch block -> (shot, tile)
+    std::vector<int2> block_map_f;   // the forward phase's stage-specialised kernel (if any)
     int2 *dev_block_map = nullptr;
+    int2 *dev_block_map_f = nullptr;
     char *dev_rows = nullptr;
-    size_t row_bytes = 0;  // one phase's records, aligned
+    size_t row_bytes = 0;
     int nphases = 0;
 };
 
-// Enqueue `nsteps` launches of the batched kernel over every shot on
-// `stream`: shot i advances its state `st_of(i)` with job `ls[i].job` from
-// local step 0.  At every multiple of ckpt_every (ckpts != nullptr) its state
-// (u^n, u^{n-1}) is copied to ckpts[i] first, as run_steps does.  The per-shot
+// The kernel of a lockstep group's forward phases: the batched kernel of
+// sweep.cuh (tm == nullptr) or a batched stage-specialised variant of depth
+// tm->T, whose single-shot shape is tv.
+struct LockFwd {
+    const wt::TMultiVariant *tm = nullptr;
+    const SweepVariant *tv = nullptr;
+};
+
+// Checkpoint copies of every shot at local step j of a phase.
+template <class StateOf>
+int lock_ckpt(std::vector<LockShot> &ls, StateOf st_of, int j, int T, float *const *ckpts, int ckpt_every,
+              cudaStream_t stream)
+{
+    for (size_t i = 0; i < ls.size(); ++i) {
+        State sj = st_of((int)i);
+        if ((j / T) & 1) advance_state(sj, T);
+        float *dst = ckpts[i] + (size_t)(j / ckpt_every) * 2 * ls[i].d.npad;
+        CK(cudaMemcpyAsync(dst, sj.buf[sj.a], sizeof(float) * ls[i].d.npad, cudaMemcpyDeviceToDevice, stream));
+        CK(cudaMemcpyAsync(dst + ls[i].d.npad, sj.buf[sj.b], sizeof(float) * ls[i].d.npad,
+                           cudaMemcpyDeviceToDevice, stream));
+    }
+    return WAVE_OK;
+}
+
+// Enqueue `nsteps` steps of every shot on `stream`: shot i advances its state
+// `st_of(i)` with job `ls[i].job` from local step 0, one batched launch per
+// time step (the batched kernel of sweep.cuh, fw.tm == nullptr) or per T
+// steps (the stage-specialised one; nsteps and ckpt_every are multiples of
+// T).  At every multiple of ckpt_every (ckpts != nullptr) its state (u^n,
+// u^{n-1}) is copied to ckpts[i] first, as run_steps does.  The per-shot
 // arguments of both buffer parities become the next phase row of `tab`.
 template <class StateOf>
 int lock_phase(std::vector<LockShot> &ls, StateOf st_of, int nsteps, const wt::MultiVariant *mv,
-               const SweepVariant *v, const Stencil &st, LockTable &tab, float *const *ckpts, int ckpt_every,
-               cudaStream_t stream)
+               const SweepVariant *v, const LockFwd &fw, const Stencil &st, LockTable &tab,
+               float *const *ckpts, int ckpt_every, cudaStream_t stream)
 {
     const int n = (int)ls.size();
     const int ph = tab.nphases++;
+    const bool staged = fw.tm != nullptr;
+    const int T = staged ? fw.tm->T : 1;
     const size_t r0 = tab.rows.size();
-    tab.rows.resize(r0 + (size_t)n);
-    wt::ShotSweep *row = tab.rows.data() + r0;
+    tab.rows.resize(r0 + tab.row_bytes, 0);
     int max_chunk_all = 0;
     for (int i = 0; i < n; ++i) {
         for (int p = 0; p < 2; ++p) {
             State sp = st_of(i);
-            if (p == 1) advance_state(sp, 1);
+            if (p == 1) advance_state(sp, T);
             long long nb = 0;
-            wt::TMaps unused;  // the batched kernel is of the sweep.cuh family
-            int rc = build_launch(ls[i].job, sp, 0, v, ls[i].chunk, &row[i].a[p], &row[i].mp[p], &unused, &nb);
-            if (rc) return rc;
-            if (nb != ls[i].nblocks) return WAVE_EINVAL;
-        }
-        max_chunk_all = std::max(max_chunk_all, ls[i].chunk);
-    }
-    const wt::ShotSweep *dtab = (const wt::ShotSweep *)(tab.dev_rows + (size_t)ph * tab.row_bytes);
-    const size_t smem = mv->smem + wt::sweep_table_bytes(max_chunk_all, mv->R * mv->T) + 16;
-    for (int j = 0; j < nsteps; ++j) {
-        if (ckpts != nullptr && j % ckpt_every == 0) {
-            for (int i = 0; i < n; ++i) {
-                State sj = st_of(i);
-                if (j & 1) advance_state(sj, 1);
-                float *dst = ckpts[i] + (size_t)(j / ckpt_every) * 2 * ls[i].d.npad;
-                CK(cudaMemcpyAsync(dst, sj.buf[sj.a], sizeof(float) * ls[i].d.npad, cudaMemcpyDeviceToDevice,
-                                   stream));
-                CK(cudaMemcpyAsync(dst + ls[i].d.npad, sj.buf[sj.b], sizeof(float) * ls[i].d.npad,
-                                   cudaMemcpyDeviceToDevice, stream));
+            int rc;
+            if (staged) {
+                wt::ShotTSweep *row = reinterpret_cast<wt::ShotTSweep *>(tab.rows.data() + r0) + i;
+                wt::SweepMaps unused;
+                rc = build_launch(ls[i].job, sp, 0, fw.tv, ls[i].chunk_f, &row->a[p], &unused, &row->mp[p], &nb);
+                if (!rc && nb != ls[i].nblocks_f) rc = WAVE_EINVAL;
+            } else {
+                wt::ShotSweep *row = reinterpret_cast<wt::ShotSweep *>(tab.rows.data() + r0) + i;
+                wt::TMaps unused;
+                rc = build_launch(ls[i].job, sp, 0, v, ls[i].chunk, &row->a[p], &row->mp[p], &unused, &nb);
+                if (!rc && nb != ls[i].nblocks) rc = WAVE_EINVAL;
             }
+            if (rc) return rc;
         }
-        CK(mv->launch((int)tab.block_map.size(), smem, stream, dtab, tab.dev_block_map, st, j & 1, j));
+        max_chunk_all = std::max(max_chunk_all, staged ? ls[i].chunk_f : ls[i].chunk);
     }
-    if (nsteps & 1)
-        for (int i = 0; i < n; ++i) advance_state(st_of(i), 1);
+    const char *drow = tab.dev_rows + (size_t)ph * tab.row_bytes;
+    const size_t smem = (staged ? fw.tm->smem : mv->smem) +
+                        wt::sweep_table_bytes(max_chunk_all, staged ? fw.tm->R * T : mv->R * mv->T) + 16;
+    for (int j = 0; j < nsteps; j += T) {
+        if (ckpts != nullptr && j % ckpt_every == 0) {
+            const int rc = lock_ckpt(ls, st_of, j, T, ckpts, ckpt_every, stream);
+            if (rc) return rc;
+        }
+        if (staged)
+            CK(fw.tm->launch((int)tab.block_map_f.size(), smem, stream, (const wt::ShotTSweep *)drow,
+                             tab.dev_block_map_f, st, (j / T) & 1, j));
+        else
+            CK(mv->launch((int)tab.block_map.size(), smem, stream, (const wt::ShotSweep *)drow, tab.dev_block_map,
+                          st, j & 1, j));
+    }
+    if ((nsteps / T) & 1)
+        for (int i = 0; i < n; ++i) advance_state(st_of(i), T);
     return WAVE_OK;
 }
 
@@ -1475,11 +1540,13 @@ struct Capture {
 };
 
 // The gradient's time loops of a lockstep group on `stream`: forward with
-// checkpoints, then per segment (last first) the recompute with stored second
-// differences and the adjoint with the imaging condition, as wave_grad does
-// for one shot; window gradients (scaled by -1/dt^2) into slots[i].gwin.
+// checkpoints (on the forward kernel fw), then per segment (last first) the
+// recompute with stored second differences and the adjoint with the imaging
+// condition (on the batched kernel of sweep.cuh), as wave_grad does for one
+// shot; window gradients (scaled by -1/dt^2) into slots[i].gwin.
 int lock_grad(std::vector<LockShot> &ls, const wt::ShotSlot *slots, int ckpt_every, const wt::MultiVariant *mv,
-              const SweepVariant *v, const Stencil &st, LockTable &tab, cudaStream_t stream, float dt)
+              const SweepVariant *v, const LockFwd &fw, const Stencil &st, LockTable &tab, cudaStream_t stream,
+              float dt)
 {
     const int n = (int)ls.size();
     const int nt = ls[0].g.nt;
@@ -1487,7 +1554,7 @@ int lock_grad(std::vector<LockShot> &ls, const wt::ShotSlot *slots, int ckpt_eve
     auto adj_state = [&](int i) -> State & { return ls[i].adj; };
     std::vector<float *> ck(n);
     for (int i = 0; i < n; ++i) ck[i] = slots[i].ckpt;
-    int rc = lock_phase(ls, fwd_state, nt, mv, v, st, tab, ck.data(), ckpt_every, stream);
+    int rc = lock_phase(ls, fwd_state, nt, mv, v, fw, st, tab, ck.data(), ckpt_every, stream);
     if (rc) return rc;
     for (int i = 0; i < n; ++i) {
         LockShot &x = ls[i];
@@ -1495,6 +1562,7 @@ int lock_grad(std::vector<LockShot> &ls, const wt::ShotSlot *slots, int ckpt_eve
         for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(x.L.V[k], 0, sizeof(float) * x.d.npad, stream));
         for (int k = 0; k < 4; ++k) x.adj.buf[k] = x.L.V[k];
     }
+    const LockFwd classic;
     const int nseg = (nt + ckpt_every - 1) / ckpt_every;
     for (int c = nseg - 1; c >= 0; --c) {
         const int s0 = c * ckpt_every;
@@ -1525,7 +1593,7 @@ int lock_grad(std::vector<LockShot> &ls, const wt::ShotSlot *slots, int ckpt_eve
             rj.d_base = 0;
             rj.d_dir = 1;
         }
-        if ((rc = lock_phase(ls, fwd_state, len, mv, v, st, tab, nullptr, 0, stream))) return rc;
+        if ((rc = lock_phase(ls, fwd_state, len, mv, v, classic, st, tab, nullptr, 0, stream))) return rc;
         for (int i = 0; i < n; ++i) {
             LockShot &x = ls[i];
             Job &aj = x.job;
@@ -1545,12 +1613,69 @@ int lock_grad(std::vector<LockShot> &ls, const wt::ShotSlot *slots, int ckpt_eve
             aj.l_dir = -1;
             aj.gacc = x.L.G;
         }
-        if ((rc = lock_phase(ls, adj_state, len, mv, v, st, tab, nullptr, 0, stream))) return rc;
+        if ((rc = lock_phase(ls, adj_state, len, mv, v, classic, st, tab, nullptr, 0, stream))) return rc;
     }
     const float scale = (float)(-1.0 / ((double)dt * (double)dt));
     for (int i = 0; i < n; ++i)
         CK(wt::launch_unpad(ls[i].L.G, ls[i].d.nx, ls[i].d.ny, ls[i].d.nz, ls[i].d.nzp, scale, slots[i].gwin,
                             stream));
+    return WAVE_OK;
+}
+
+// Whether the batched stage-specialised variant tm can run a group's forward
+// phases: its depth must divide nt and the checkpoint interval.
+bool tmulti_fits(const wt::TMultiVariant *tm, int nt, int ckpt_every)
+{
+    return tm != nullptr && tmulti_shape(tm) != nullptr && nt % tm->T == 0 &&
+           (ckpt_every <= 0 || ckpt_every % tm->T == 0);
+}
+
+// The batched stage-specialised variant a tuning names (kernel 2, depth
+// time_tile, tile_y / tile_z / rows if given), or nullptr.
+const wt::TMultiVariant *tmulti_named(int R, const wave_tuning *t)
+{
+    const wt::TMultiVariant *tms = nullptr;
+    const int nv = tmulti_variants(R, &tms);
+    for (int i = 0; i < nv; ++i)
+        if (tms[i].T == t->time_tile && (t->tile_y == 0 || tms[i].BY == t->tile_y) &&
+            (t->tile_z == 0 || tms[i].BZ == t->tile_z) && (t->rows == 0 || tms[i].VY == t->rows) &&
+            (t->vec == 0 || tms[i].V == t->vec))
+            return &tms[i];
+    return nullptr;
+}
+
+// Forward-phase choice of autotuned survey groups, per (device, order, group
+// shape): index into the radius's batched stage-specialised variants, or -1
+// for the batched kernel of sweep.cuh.
+struct LockKey {
+    int dev, so, n;
+    long long pts;
+    int mx, my, mz;
+    bool operator<(const LockKey &o) const
+    {
+        return std::tie(dev, so, n, pts, mx, my, mz) < std::tie(o.dev, o.so, o.n, o.pts, o.mx, o.my, o.mz);
+    }
+};
+std::mutex g_lock_mu;
+std::map<LockKey, int> g_lock_cache;
+
+// The key of a group of n shots of grid G (their windows' extents).
+int lock_key(const wave_grid *G, int n, const wave_shot *shots, LockKey *key)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    *key = LockKey{dev, G->space_order, n, 0, 0, 0, 0};
+    for (int i = 0; i < n; ++i) {
+        wave_grid g = *G;
+        for (int a = 0; a < 3; ++a) g.n[a] = shots[i].n[a];
+        Dims d;
+        const int rc = check_grid(&g, &d);
+        if (rc) return rc;
+        key->pts += d.npad;
+        key->mx = std::max(key->mx, d.nx);
+        key->my = std::max(key->my, d.ny);
+        key->mz = std::max(key->mz, d.nz);
+    }
     return WAVE_OK;
 }
 
@@ -1564,15 +1689,28 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
     try {
         const int R = G->space_order / 2;
         const MultiVariant *mv = multi_variant(R);
-        if (mv == nullptr) return WAVE_EUNSUPPORTED;
-        const int tile_y = tuning ? tuning->tile_y : 0, vec = tuning ? tuning->vec : 0;
-        const SweepVariant *v = find_variant(R, 1, tile_y, vec, tuning ? tuning->tile_z : 0, 1);
-        if (tuning == nullptr || tuning->time_tile != 1 || tuning->kernel == 2 || v == nullptr ||
-            v->T != mv->T || v->V != mv->V ||
-            v->BZ != mv->BZ || v->BY != mv->BY || v->P != mv->P)
-            return WAVE_EUNSUPPORTED;
+        if (mv == nullptr || tuning == nullptr) return WAVE_EUNSUPPORTED;
+        // the batched kernel of sweep.cuh runs its default untiled shape (and
+        // every gradient-mode phase)
+        const SweepVariant *v = find_variant(R, 1, mv->BY, mv->V, mv->BZ, 1);
+        if (v == nullptr || v->P != mv->P) return WAVE_EUNSUPPORTED;
         const bool grad = ckpt_every > 0;
         const int nt = G->nt;
+        // forward phases: named by the tuning, or timed below (time_tile 0)
+        LockFwd fw;
+        bool tune_fwd = false;
+        if (tuning->time_tile == 0) {
+            tune_fwd = true;
+        } else if (tuning->kernel == 2) {
+            fw.tm = tmulti_named(R, tuning);
+            if (!tmulti_fits(fw.tm, nt, ckpt_every)) return WAVE_EUNSUPPORTED;
+            fw.tv = tmulti_shape(fw.tm);
+        } else if (tuning->time_tile != 1 || (tuning->tile_y && tuning->tile_y != v->BY) ||
+                   (tuning->vec && tuning->vec != v->V) || (tuning->tile_z && tuning->tile_z != v->BZ)) {
+            return WAVE_EUNSUPPORTED;
+        }
+        const wt::TMultiVariant *tms = nullptr;
+        const int ntm = tmulti_variants(R, &tms);
         std::vector<LockShot> ls(n);
         Stencil st;
         long long total_blocks = 0;
@@ -1596,7 +1734,8 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
             for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(x.L.U[k], 0, sizeof(float) * x.d.npad, stream));
             if ((rc = upload_table(x.ti, x.L.inj, stream))) return rc;
             if ((rc = upload_table(x.tr, grad ? x.L.inj2 : x.L.rec, stream))) return rc;
-            x.chunk = std::min(tuning->tile_x > 0 ? std::min(tuning->tile_x, x.d.nx) : default_chunk(x.d, v),
+            x.chunk = std::min(tuning->tile_x > 0 && !fw.tm && !tune_fwd ? std::min(tuning->tile_x, x.d.nx)
+                                                                          : default_chunk(x.d, v),
                                max_chunk(v));
             x.nblocks = (long long)tiles(x.d.nzp, v->BZ) * tiles(x.d.ny, v->BY) * tiles(x.d.nx, x.chunk);
             total_blocks += x.nblocks;
@@ -1618,26 +1757,162 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
         }
         CK(wt::allow_max_dynamic_smem(mv->func));
         const int nphases = lock_phases(nt, ckpt_every);
-        if (total_blocks > 0x7fffffffLL || lock_table_bytes(n, total_blocks, nphases) > table_bytes)
-            return WAVE_ENOSPACE;
         LockTable tab;
-        tab.row_bytes = align_up(sizeof(wt::ShotSweep) * (size_t)n);
-        tab.dev_block_map = (int2 *)table;
-        tab.dev_rows = (char *)table + align_up(sizeof(int2) * (size_t)total_blocks);
-        tab.rows.reserve((size_t)nphases * n);
+        tab.row_bytes = lock_row_bytes(n);
         // launch order: the tiles of every shot that handle a source or
         // receiver point (in any phase) first, then the rest
-        tab.block_map.reserve((size_t)total_blocks);
-        std::vector<std::vector<char>> heavy(n);
-        for (int i = 0; i < n; ++i) {
-            mark_heavy(ls[i].d, v, ls[i].chunk, &ls[i].ti, false, heavy[i]);
-            mark_heavy(ls[i].d, v, ls[i].chunk, &ls[i].tr, !grad, heavy[i]);
-            heavy[i].resize((size_t)ls[i].nblocks, 0);
+        auto block_map = [&](const SweepVariant *sv, bool fwd_kernel, std::vector<int2> &out) {
+            out.clear();
+            std::vector<std::vector<char>> heavy(n);
+            for (int i = 0; i < n; ++i) {
+                const int ch = fwd_kernel ? ls[i].chunk_f : ls[i].chunk;
+                const long long nb = fwd_kernel ? ls[i].nblocks_f : ls[i].nblocks;
+                mark_heavy(ls[i].d, sv, ch, &ls[i].ti, false, heavy[i]);
+                mark_heavy(ls[i].d, sv, ch, &ls[i].tr, !grad, heavy[i]);
+                heavy[i].resize((size_t)nb, 0);
+            }
+            for (int pass = 1; pass >= 0; --pass)
+                for (int i = 0; i < n; ++i) {
+                    const long long nb = fwd_kernel ? ls[i].nblocks_f : ls[i].nblocks;
+                    for (long long t = 0; t < nb; ++t)
+                        if (heavy[i][(size_t)t] == pass) out.push_back(make_int2(i, (int)t));
+                }
+        };
+        auto set_forward = [&](const LockFwd &f) -> long long {
+            long long tot = 0;
+            for (int i = 0; i < n; ++i) {
+                LockShot &x = ls[i];
+                if (f.tm == nullptr) {
+                    x.chunk_f = 0;
+                    x.nblocks_f = 0;
+                    continue;
+                }
+                x.chunk_f = std::min(tuning->tile_x > 0 && !tune_fwd ? std::min(tuning->tile_x, x.d.nx)
+                                                                      : default_chunk(x.d, f.tv),
+                                     max_chunk(f.tv));
+                x.nblocks_f = (long long)tiles(x.d.nzp, f.tv->BZ) * tiles(x.d.ny, f.tv->BY) *
+                              tiles(x.d.nx, x.chunk_f);
+                tot += x.nblocks_f;
+            }
+            return tot;
+        };
+        const size_t map_bytes = align_up(sizeof(int2) * (size_t)total_blocks);
+        tab.dev_block_map = (int2 *)table;
+        block_map(v, false, tab.block_map);
+        if (total_blocks > 0x7fffffffLL) return WAVE_ENOSPACE;
+
+        if (tune_fwd) {
+            // Time the forward phase of the group on every candidate kernel: a
+            // few launches on the group's zeroed levels with its own sources
+            // and receivers, best of two passes; ties keep the earlier.
+            std::vector<wave_shot> gs(n);
+            for (int i = 0; i < n; ++i) gs[i] = *slots[i].shot;
+            LockKey key;
+            int rc = lock_key(G, n, gs.data(), &key);
+            if (rc) return rc;
+            int choice = -2;
+            {
+                std::lock_guard<std::mutex> lk(g_lock_mu);
+                auto it = g_lock_cache.find(key);
+                if (it != g_lock_cache.end()) choice = it->second;
+            }
+            if (choice == -2) {
+                std::vector<int> cands = {-1};
+                for (int c = 0; c < ntm; ++c)
+                    if (tmulti_fits(&tms[c], nt, ckpt_every)) cands.push_back(c);
+                cudaEvent_t e0, e1;
+                CK(cudaEventCreate(&e0));
+                CK(cudaEventCreate(&e1));
+                std::vector<float> best(cands.size(), 1e30f);
+                const int steps = std::min(8, nt);  // a multiple of every candidate's depth
+                for (int pass = 0; pass < 2 && rc == WAVE_OK; ++pass)
+                    for (size_t c = 0; c < cands.size() && rc == WAVE_OK; ++c) {
+                        LockFwd f;
+                        if (cands[c] >= 0) {
+                            f.tm = &tms[cands[c]];
+                            f.tv = tmulti_shape(f.tm);
+                        }
+                        const long long tot_f = set_forward(f);
+                        if (lock_table_bytes(n, total_blocks, tot_f, 1) > table_bytes || tot_f > 0x7fffffffLL) {
+                            best[c] = 1e30f;  // the workspace's table does not hold this kernel's map
+                            continue;
+                        }
+                        LockTable tt;
+                        tt.row_bytes = tab.row_bytes;
+                        tt.block_map = tab.block_map;
+                        tt.dev_block_map = tab.dev_block_map;
+                        tt.dev_block_map_f = (int2 *)((char *)table + map_bytes);
+                        tt.dev_rows = (char *)table + map_bytes + align_up(sizeof(int2) * (size_t)tot_f);
+                        if (f.tm) block_map(f.tv, true, tt.block_map_f);
+                        auto st_of = [&](int i) -> State & { return ls[i].s; };
+                        float ms = 0.f;
+                        if (cudaMemcpyAsync(tt.dev_block_map, tt.block_map.data(), sizeof(int2) * tt.block_map.size(),
+                                            cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+                            (f.tm && cudaMemcpyAsync(tt.dev_block_map_f, tt.block_map_f.data(),
+                                                     sizeof(int2) * tt.block_map_f.size(), cudaMemcpyHostToDevice,
+                                                     stream) != cudaSuccess)) {
+                            rc = WAVE_ECUDA;
+                            break;
+                        }
+                        // the phase row is built on the host first, then uploaded before its launches
+                        tt.rows.reserve(tt.row_bytes);
+                        {
+                            // build the row without launching: zero steps
+                            if ((rc = lock_phase(ls, st_of, 0, mv, v, f, st, tt, nullptr, 0, stream))) break;
+                            tt.nphases = 0;
+                            if (cudaMemcpyAsync(tt.dev_rows, tt.rows.data(), tt.row_bytes, cudaMemcpyHostToDevice,
+                                                stream) != cudaSuccess) {
+                                rc = WAVE_ECUDA;
+                                break;
+                            }
+                            tt.rows.clear();
+                        }
+                        if (cudaEventRecord(e0, stream) != cudaSuccess) { rc = WAVE_ECUDA; break; }
+                        if ((rc = lock_phase(ls, st_of, steps, mv, v, f, st, tt, nullptr, 0, stream))) break;
+                        if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                            rc = WAVE_ECUDA;
+                            break;
+                        }
+                        best[c] = std::min(best[c], ms);
+                        if (tune_log() && pass == 1)
+                            std::fprintf(stderr, "wave survey group: forward kernel=%d T=%d: %.4f ms for %d steps\n",
+                                         f.tm ? 2 : 1, f.tm ? f.tm->T : 1, ms, steps);
+                    }
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (rc) return rc;
+                size_t bi = 0;
+                for (size_t c = 1; c < cands.size(); ++c)
+                    if (best[c] < 0.99f * best[bi]) bi = c;
+                choice = cands[bi];
+                std::lock_guard<std::mutex> lk(g_lock_mu);
+                g_lock_cache[key] = choice;
+            }
+            if (choice >= 0) {
+                fw.tm = &tms[choice];
+                fw.tv = tmulti_shape(fw.tm);
+            }
+            // the timed launches left the levels dirty: start from zero again
+            for (int i = 0; i < n; ++i) {
+                ls[i].s = State();
+                for (int k = 0; k < 4; ++k) {
+                    ls[i].s.buf[k] = ls[i].L.U[k];
+                    CK(cudaMemsetAsync(ls[i].L.U[k], 0, sizeof(float) * ls[i].d.npad, stream));
+                }
+            }
         }
-        for (int pass = 1; pass >= 0; --pass)
-            for (int i = 0; i < n; ++i)
-                for (long long t = 0; t < ls[i].nblocks; ++t)
-                    if (heavy[i][(size_t)t] == pass) tab.block_map.push_back(make_int2(i, (int)t));
+        const long long total_blocks_f = set_forward(fw);
+        if (total_blocks_f > 0x7fffffffLL ||
+            lock_table_bytes(n, total_blocks, total_blocks_f, nphases) > table_bytes)
+            return WAVE_ENOSPACE;
+        tab.dev_block_map_f = (int2 *)((char *)table + map_bytes);
+        tab.dev_rows = (char *)table + map_bytes + align_up(sizeof(int2) * (size_t)total_blocks_f);
+        tab.rows.reserve((size_t)nphases * tab.row_bytes);
+        if (fw.tm) {
+            block_map(fw.tv, true, tab.block_map_f);
+            CK(wt::allow_max_dynamic_smem(fw.tm->func));
+        }
 
         // The time loops go into one CUDA graph, captured on the library's
         // stream and launched on `stream` after the tables are uploaded.
@@ -1649,28 +1924,31 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
         if ((rc = cap.begin(cs))) return rc;
         auto fwd_state = [&](int i) -> State & { return ls[i].s; };
         if (!grad) {
-            rc = lock_phase(ls, fwd_state, nt, mv, v, st, tab, nullptr, 0, cs);
+            rc = lock_phase(ls, fwd_state, nt, mv, v, fw, st, tab, nullptr, 0, cs);
             for (int i = 0; i < n && rc == WAVE_OK; ++i)
                 if (slots[i].shot->rec.npts > 0 && slots[i].rec_out != nullptr &&
                     wt::launch_gather(ls[i].L.corner, ls[i].L.rec.wts, nt, slots[i].shot->rec.npts, 1,
                                       slots[i].rec_out, cs) != cudaSuccess)
                     rc = WAVE_ECUDA;
         } else {
-            rc = lock_grad(ls, slots, ckpt_every, mv, v, st, tab, cs, G->dt);
+            rc = lock_grad(ls, slots, ckpt_every, mv, v, fw, st, tab, cs, G->dt);
         }
         if (rc) return rc;
         if ((rc = cap.end())) return rc;
-        if ((int)tab.rows.size() != nphases * n) return WAVE_EINVAL;
+        if (tab.nphases != nphases || tab.rows.size() != (size_t)nphases * tab.row_bytes) return WAVE_EINVAL;
         cudaGraphExec_t exec = nullptr;
         CK(cudaGraphInstantiate(&exec, cap.graph, 0));
         rc = WAVE_OK;
         if (cudaMemcpyAsync(tab.dev_block_map, tab.block_map.data(), sizeof(int2) * tab.block_map.size(),
                             cudaMemcpyHostToDevice, stream) != cudaSuccess)
             rc = WAVE_ECUDA;
-        for (int p = 0; p < nphases && rc == WAVE_OK; ++p)
-            if (cudaMemcpyAsync(tab.dev_rows + (size_t)p * tab.row_bytes, tab.rows.data() + (size_t)p * n,
-                                sizeof(wt::ShotSweep) * (size_t)n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
-                rc = WAVE_ECUDA;
+        if (rc == WAVE_OK && !tab.block_map_f.empty() &&
+            cudaMemcpyAsync(tab.dev_block_map_f, tab.block_map_f.data(), sizeof(int2) * tab.block_map_f.size(),
+                            cudaMemcpyHostToDevice, stream) != cudaSuccess)
+            rc = WAVE_ECUDA;
+        if (rc == WAVE_OK && cudaMemcpyAsync(tab.dev_rows, tab.rows.data(), tab.rows.size(), cudaMemcpyHostToDevice,
+                                             stream) != cudaSuccess)
+            rc = WAVE_ECUDA;
         if (rc == WAVE_OK && cudaGraphLaunch(exec, stream) != cudaSuccess) rc = WAVE_ECUDA;
         cudaGraphExecDestroy(exec);  // freed once the launch completes
         return rc;
@@ -1679,26 +1957,63 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
     }
 }
 
-bool lockstep_supported(const wave_grid *G, const wave_tuning *tuning)
+bool lockstep_supported(const wave_grid *G, const wave_tuning *tuning, int ckpt_every)
 {
-    if (G == nullptr || tuning == nullptr || tuning->time_tile != 1 || tuning->kernel == 2) return false;
+    if (G == nullptr || tuning == nullptr) return false;
     const int R = G->space_order / 2;
     const MultiVariant *mv = multi_variant(R);
+    if (mv == nullptr) return false;
+    if (tuning->time_tile == 0) return true;  // the forward kernel is timed; sweep.cuh's always fits
+    if (tuning->kernel == 2) return tmulti_fits(tmulti_named(R, tuning), G->nt, ckpt_every);
     const SweepVariant *v = find_variant(R, 1, tuning->tile_y, tuning->vec, tuning->tile_z, 1);
-    return mv != nullptr && v != nullptr && v->V == mv->V && v->BZ == mv->BZ && v->BY == mv->BY &&
+    return tuning->time_tile == 1 && v != nullptr && v->V == mv->V && v->BZ == mv->BZ && v->BY == mv->BY &&
            v->P == mv->P;
+}
+
+int lockstep_describe(const wave_grid *G, int n, const wave_shot *shots, int ckpt_every,
+                      const wave_tuning *tuning, int32_t *out)
+{
+    const int R = G->space_order / 2;
+    const MultiVariant *mv = multi_variant(R);
+    for (int k = 0; k < 9; ++k) out[k] = 0;
+    if (!lockstep_supported(G, tuning, ckpt_every)) return WAVE_OK;  // per-shot streams
+    out[8] = 1;
+    const wt::TMultiVariant *tm = nullptr;
+    if (tuning->time_tile == 0) {
+        LockKey key;
+        const int rc = lock_key(G, n, shots, &key);
+        if (rc) return rc;
+        std::lock_guard<std::mutex> lk(g_lock_mu);
+        auto it = g_lock_cache.find(key);
+        if (it == g_lock_cache.end()) return WAVE_OK;  // not timed yet: out[0] = 0
+        if (it->second >= 0) {
+            const wt::TMultiVariant *tms = nullptr;
+            tmulti_variants(R, &tms);
+            tm = &tms[it->second];
+        }
+    } else if (tuning->kernel == 2) {
+        tm = tmulti_named(R, tuning);
+    }
+    if (tm != nullptr) {
+        const int v[8] = {tm->T, tm->BY, 0, tm->BZ, tm->V, tm->P, WAVE_KERNEL_STAGED, tm->VY};
+        for (int k = 0; k < 8; ++k) out[k] = v[k];
+    } else {
+        const int v[8] = {1, mv->BY, 0, mv->BZ, mv->V, mv->P, WAVE_KERNEL_SHARED, 1};
+        for (int k = 0; k < 8; ++k) out[k] = v[k];
+    }
+    return WAVE_OK;
 }
 
 size_t lockstep_table_bytes(const wave_grid *G, int n, const wave_shot *shots, int ckpt_every)
 {
-    // an upper bound on the launch's blocks: every variant has BZ >= 24,
-    // BY >= 8, and an x-chunk of at least one plane
+    // an upper bound on the launch's blocks, for either map: every variant
+    // has BZ >= 24, BY >= 8, and an x-chunk of at least one plane
     long long total = 0;
     for (int i = 0; i < n; ++i) {
         const long long nzp = (shots[i].n[2] + 7) / 8 * 8;
         total += ((nzp + 23) / 24) * ((shots[i].n[1] + 7) / 8) * (long long)shots[i].n[0];
     }
-    return lock_table_bytes(n, total, lock_phases(G->nt, ckpt_every));
+    return lock_table_bytes(n, total, total, lock_phases(G->nt, ckpt_every));
 }
 
 cudaError_t allow_max_dynamic_smem(const void *func)

@@ -56,6 +56,25 @@ int sweep_multi_variant_r6(const MultiVariant **out);
 int sweep_multi_variant_r7(const MultiVariant **out);
 int sweep_multi_variant_r8(const MultiVariant **out);
 
+// Batched variants of the stage-specialised sweep (forward and adjoint
+// sweeps of a lockstep group), per radius; each has the single-shot variant of
+// the same shape (kind 1) for its geometry.
+struct TMultiVariant {
+    int R, T, V, VY, BZ, BY, P, threads;
+    size_t smem;  // shared memory without the plane_start slices
+    cudaError_t (*launch)(int nblocks, size_t smem, cudaStream_t stream, const ShotTSweep *shots,
+                          const int2 *block_map, const Stencil &st, int parity, int step);
+    const void *func;
+};
+int sweep_tmulti_variants_r1(const TMultiVariant **out);
+int sweep_tmulti_variants_r2(const TMultiVariant **out);
+int sweep_tmulti_variants_r3(const TMultiVariant **out);
+int sweep_tmulti_variants_r4(const TMultiVariant **out);
+int sweep_tmulti_variants_r5(const TMultiVariant **out);
+int sweep_tmulti_variants_r6(const TMultiVariant **out);
+int sweep_tmulti_variants_r7(const TMultiVariant **out);
+int sweep_tmulti_variants_r8(const TMultiVariant **out);
+
 // One shot of a batched call: its device memory and its slices of the traces.
 struct ShotSlot {
     const wave_shot *shot;
@@ -69,8 +88,15 @@ struct ShotSlot {
     const float *resid; // residual [nt][nrec_s] (gradient) or nullptr
 };
 
-// Whether wave_*_batched can run with `tuning` on the batched kernel.
-bool lockstep_supported(const wave_grid *g, const wave_tuning *tuning);
+// Whether wave_*_batched can run with `tuning` (time_tile 0: the batch's
+// forward kernel is chosen by timing) on a batched kernel; ckpt_every as for
+// lockstep_group.
+bool lockstep_supported(const wave_grid *g, const wave_tuning *tuning, int ckpt_every);
+// The forward kernel of a lockstep group of the n shots (out[0..7] in the
+// form of wave_describe_plan, out[8] = 1; all 0 when the group runs per shot,
+// out[0] = 0 while an autotuned choice is not made yet).
+int lockstep_describe(const wave_grid *g, int n, const wave_shot *shots, int ckpt_every,
+                      const wave_tuning *tuning, int32_t *out);
 
 // Run a group of shots in lockstep (host runtime, wave_api.cu): the window of
 // m and damp is already in each slot (in stream order); every time step is one
@@ -154,6 +180,26 @@ cudaError_t launch_tsweep(int nblocks, cudaStream_t stream, const SweepArgs &a, 
     return cudaLaunchKernelEx(&cfg, tsweep_kernel<R, T, V, VY, BZ, BY, P, MB, MODE>, a, st, m);
 }
 
+template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB>
+cudaError_t launch_tsweep_multi(int nblocks, size_t smem, cudaStream_t stream, const ShotTSweep *shots,
+                                const int2 *block_map, const Stencil &st, int parity, int step)
+{
+    cudaError_t e = allow_max_dynamic_smem((const void *)tsweep_multi_kernel<R, T, V, VY, BZ, BY, P, MB>);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nblocks);
+    cfg.blockDim = dim3((unsigned)TShape<R, T, V, VY, BZ, BY, P, MB, 0>::NTB);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tsweep_multi_kernel<R, T, V, VY, BZ, BY, P, MB>, shots, block_map, st,
+                              parity, step);
+}
+
 template <int R, int T, int V, int BZ, int BY, int P, int MB>
 cudaError_t launch_sweep_multi(int nblocks, size_t smem, cudaStream_t stream, const ShotSweep *shots,
                                const int2 *block_map, const Stencil &st, int parity, int step)
@@ -219,6 +265,24 @@ cudaError_t launch_sweep_multi(int nblocks, size_t smem, cudaStream_t stream, co
     {                                                                                             \
         *out = &kMulti_r##R_;                                                                     \
         return 1;                                                                                 \
+    }                                                                                             \
+    }
+
+#define WAVE_TMULTI_ENTRY(R_, T_, V_, VY_, BZ_, BY_, P_, MB_)                                     \
+    {R_, T_, V_, VY_, BZ_, BY_, P_, wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, 0>::NTB,        \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, 0>::SMEM,                                      \
+     &wt::launch_tsweep_multi<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>,                                 \
+     (const void *)&wt::tsweep_multi_kernel<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>},
+
+// the list may be empty: a zero sentinel keeps the array non-empty
+#define WAVE_DEFINE_TMULTI(r_)                                                                    \
+    namespace wt {                                                                                \
+    static const TMultiVariant kTMulti_r##r_[] = {WAVE_TMULTI_VARIANTS_R##r_(WAVE_TMULTI_ENTRY)   \
+                                                  {0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr, nullptr}}; \
+    int sweep_tmulti_variants_r##r_(const TMultiVariant **out)                                    \
+    {                                                                                             \
+        *out = kTMulti_r##r_;                                                                     \
+        return (int)(sizeof(kTMulti_r##r_) / sizeof(kTMulti_r##r_[0])) - 1;                       \
     }                                                                                             \
     }
 

@@ -34,7 +34,7 @@ EXPORTED = ["wave_version", "wave_strerror", "wave_fd_coefficients", "wave_cfl_d
             "wave_status", "wave_describe_plan", "wave_sweep_stats", "wave_list_variants",
             "wave_autotune_stats", "wave_plan_bound",
             "wave_fwd_noalloc", "wave_measure_peaks", "wave_batch_workspace_bytes",
-            "wave_fwd_batched", "wave_grad_batched", "wave_heat"]
+            "wave_fwd_batched", "wave_grad_batched", "wave_describe_batch_plan", "wave_heat"]
 
 
 class WaveError(RuntimeError):
@@ -161,6 +161,8 @@ def _lib():
         sp_ = ctypes.POINTER(_Shot)
         lib.wave_batch_workspace_bytes.argtypes = [gp, i32, sp_, i32, i32]
         lib.wave_batch_workspace_bytes.restype = ctypes.c_size_t
+        lib.wave_describe_batch_plan.argtypes = [gp, i32, sp_, i32, i32, tp, ctypes.POINTER(i32)]
+        lib.wave_describe_batch_plan.restype = i32
         lib.wave_fwd_batched.argtypes = [gp, i32, sp_, vp, vp, vp, vp, i32, tp, vp, ctypes.c_size_t, vp]
         lib.wave_fwd_batched.restype = i32
         lib.wave_grad_batched.argtypes = [gp, i32, sp_, vp, vp, vp, vp, i32, vp, i32, tp, vp,
@@ -401,6 +403,24 @@ def batch_workspace_bytes(grid, shots, ckpt_every=0, concurrency=0):
                                               int(concurrency)))
     del keep
     return n
+
+
+def describe_batch_plan(grid, shots, ckpt_every=0, concurrency=0, tuning=None):
+    """Forward kernel of the first group of a batched call
+    (wave_describe_batch_plan): None when the shots run one by one, else the
+    keys of describe_plan plus lockstep=True (time_tile 0 while an autotuned
+    group has not been timed yet)."""
+    arr, keep = _shots(shots)
+    g = grid.c()
+    out = (ctypes.c_int32 * 9)()
+    t = tuning.c() if tuning is not None else None
+    _check(_lib().wave_describe_batch_plan(ctypes.byref(g), len(shots), arr, int(ckpt_every), int(concurrency),
+                                           ctypes.byref(t) if t else None, out), "wave_describe_batch_plan")
+    del keep
+    if out[8] == 0:
+        return None
+    return dict(time_tile=out[0], tile_y=out[1], tile_x=out[2], tile_z=out[3], vec=out[4],
+                prefetch=out[5], kernel=out[6], rows=out[7], lockstep=True)
 
 
 def _traces(x, name, nt, counts):

@@ -168,3 +168,28 @@ def test_plan_bound_closed_forms_without_gpu(wavelib):
     flat = wavelib.plan_bound(g16, wavelib.Tuning(time_tile=1, tile_y=24, tile_z=64, kernel=2, rows=2,
                                                   tile_x=64), hbm, lsu, -1)
     assert deep > flat
+
+
+def test_batch_plan_of_named_tunings_without_gpu(wavelib):
+    """Which kernel a batched call's groups run, for tunings that name it (no
+    timing needed): the batched stage-specialised shape of the named depth
+    when it divides nt and the checkpoint interval, the shared-warp batched
+    kernel for the default untiled shape, shot by shot otherwise."""
+    g = wavelib.Grid((48, 40, 44), (0.01,) * 3, 1e-3, 24, 4)
+    shots = [wavelib.Shot(origin=(0, 0, 0), n=(30, 30, 30), src_xyz=[[0.1, 0.1, 0.1]],
+                          rec_xyz=[[0.2, 0.2, 0.2]]),
+             wavelib.Shot(origin=(10, 5, 8), n=(32, 30, 34), src_xyz=[[0.1, 0.1, 0.1]],
+                          rec_xyz=[[0.2, 0.1, 0.2]])]
+    staged = wavelib.WAVE_KERNEL_STAGED
+    p = wavelib.describe_batch_plan(g, shots, 0, 2, wavelib.Tuning(time_tile=2, kernel=staged))
+    assert p["lockstep"] and (p["time_tile"], p["kernel"]) == (2, staged)
+    p = wavelib.describe_batch_plan(g, shots, 6, 2, wavelib.Tuning(time_tile=2, kernel=staged))
+    assert (p["time_tile"], p["kernel"]) == (2, staged)
+    # depth 2 does not divide a checkpoint interval of 5: shot by shot
+    assert wavelib.describe_batch_plan(g, shots, 5, 2, wavelib.Tuning(time_tile=2, kernel=staged)) is None
+    p = wavelib.describe_batch_plan(g, shots, 0, 2, wavelib.Tuning(time_tile=1))
+    assert (p["time_tile"], p["kernel"]) == (1, wavelib.WAVE_KERNEL_SHARED)
+    # a shared-warp depth-2 tile has no batched kernel
+    assert wavelib.describe_batch_plan(g, shots, 0, 2, wavelib.Tuning(time_tile=2)) is None
+    odd = wavelib.Grid((48, 40, 44), (0.01,) * 3, 1e-3, 23, 4)
+    assert wavelib.describe_batch_plan(odd, shots, 0, 2, wavelib.Tuning(time_tile=2, kernel=staged)) is None

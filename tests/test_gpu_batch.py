@@ -213,3 +213,98 @@ def test_batch_refuses_window_outside_grid(wavelib, cuda):
     with pytest.raises(wavelib.WaveError):
         wavelib.fwd_batched(grid, bad, tm, tm, [torch.zeros((4, 0), device=cuda)], concurrency=1,
                             workspace=torch.empty(1 << 20, dtype=torch.uint8, device=cuda))
+
+
+def _per_shot_fwd(wavelib, cuda, grid, shots, tm, td, q, nt, so):
+    import torch
+    out = []
+    for s, qq in zip(shots, q):
+        w = _win(s)
+        gw = wavelib.Grid(s.n, grid.h, grid.dt, nt, so)
+        d1, _, _, _ = wavelib.fwd(gw, tm[w].contiguous(), td[w].contiguous(), s.src_xyz,
+                                  _t(qq, cuda), s.rec_xyz, tuning=wavelib.Tuning(time_tile=1))
+        out.append(d1)
+    torch.cuda.synchronize()
+    return out
+
+
+@pytest.mark.parametrize("so,T", [(2, 1), (2, 2), (4, 1), (4, 2)])
+def test_lockstep_staged_fwd_equals_per_shot(wavelib, cuda, so, T):
+    """The batched stage-specialised kernel (depth 1 and 2) runs the shots of
+    a group in lockstep: each shot's traces equal wave_fwd on its window, bit
+    for bit, and the group's forward kernel is the one the tuning names."""
+    import torch
+    nt = 24
+    grid, h, dt, m, damp, shots, q = _survey(wavelib, so, nt, seed=40 + so + T)
+    tm, td = _t(m, cuda), _t(damp, cuda)
+    tune = wavelib.Tuning(time_tile=T, kernel=wavelib.WAVE_KERNEL_STAGED)
+    recs, ws = wavelib.fwd_batched(grid, shots, tm, td, [_t(x, cuda) for x in q], concurrency=3,
+                                   tuning=tune)
+    assert wavelib.status(ws) == wavelib.WAVE_OK
+    want = _per_shot_fwd(wavelib, cuda, grid, shots, tm, td, q, nt, so)
+    for r, d1 in zip(recs, want):
+        assert torch.equal(r, d1)
+
+
+@pytest.mark.parametrize("T", [1, 2])
+def test_lockstep_staged_grad_equals_shot_order_sum(wavelib, cuda, T):
+    """Gradient groups whose forward phases (with checkpoints every k steps,
+    k a multiple of T) run on the batched stage-specialised kernel: the
+    survey gradient equals the per-shot wave_grad gradients added in shot
+    order, bit for bit."""
+    import torch
+    so, nt, k = 4, 30, 6
+    grid, h, dt, m, damp, shots, q = _survey(wavelib, so, nt, seed=17)
+    rng = np.random.default_rng(4)
+    res = [rng.standard_normal((nt, len(s.rec_xyz))).astype(np.float32) for s in shots]
+    tm, td = _t(m, cuda), _t(damp, cuda)
+    tune = wavelib.Tuning(time_tile=T, kernel=wavelib.WAVE_KERNEL_STAGED)
+    g, ws = wavelib.grad_batched(grid, shots, tm, td, [_t(x, cuda) for x in q],
+                                 [_t(x, cuda) for x in res], k, concurrency=2, tuning=tune)
+    assert wavelib.status(ws) == wavelib.WAVE_OK
+    want = torch.zeros(grid.n, dtype=torch.float32, device=cuda)
+    for s, qq, rr in zip(shots, q, res):
+        w = _win(s)
+        gw = wavelib.Grid(s.n, grid.h, grid.dt, nt, so)
+        mw, dw = tm[w].contiguous(), td[w].contiguous()
+        _, _, ck, _ = wavelib.fwd(gw, mw, dw, s.src_xyz, _t(qq, cuda), None,
+                                  tuning=wavelib.Tuning(time_tile=1), ckpt_every=k)
+        gi, wsg = wavelib.grad(gw, mw, dw, s.src_xyz, _t(qq, cuda), s.rec_xyz, _t(rr, cuda), ck, k,
+                               tuning=wavelib.Tuning(time_tile=1))
+        assert wavelib.status(wsg) == wavelib.WAVE_OK
+        want[w] += gi
+    torch.cuda.synchronize()
+    assert torch.equal(g, want)
+
+
+@pytest.mark.parametrize("so,nt,k", [(4, 24, 0), (2, 23, 0), (4, 30, 6), (4, 30, 5)])
+def test_lockstep_autotuned_forward_kernel(wavelib, cuda, so, nt, k):
+    """time_tile 0: the group times its forward kernel (the batched kernel of
+    sweep.cuh or a batched stage-specialised one whose depth divides nt and
+    the checkpoint interval) and gives the per-shot results bit for bit,
+    whichever it picks; the second call takes the cached choice."""
+    import torch
+    grid, h, dt, m, damp, shots, q = _survey(wavelib, so, nt, seed=60 + nt)
+    tm, td = _t(m, cuda), _t(damp, cuda)
+    qd = [_t(x, cuda) for x in q]
+    if k == 0:
+        want = _per_shot_fwd(wavelib, cuda, grid, shots, tm, td, q, nt, so)
+        for _ in range(2):
+            recs, ws = wavelib.fwd_batched(grid, shots, tm, td, qd, concurrency=4)
+            assert wavelib.status(ws) == wavelib.WAVE_OK
+            for r, d1 in zip(recs, want):
+                assert torch.equal(r, d1)
+        p = wavelib.describe_batch_plan(grid, shots, 0, 4)
+        assert p["lockstep"] and p["time_tile"] >= 1 and nt % p["time_tile"] == 0
+        return
+    rng = np.random.default_rng(8)
+    res = [_t(rng.standard_normal((nt, len(s.rec_xyz))), cuda) for s in shots]
+    ref, _ = wavelib.grad_batched(grid, shots, tm, td, qd, res, k, concurrency=3,
+                                  tuning=wavelib.Tuning(time_tile=1))
+    for _ in range(2):
+        g, ws = wavelib.grad_batched(grid, shots, tm, td, qd, res, k, concurrency=3)
+        assert wavelib.status(ws) == wavelib.WAVE_OK
+        torch.cuda.synchronize()
+        assert torch.equal(g, ref)
+    p = wavelib.describe_batch_plan(grid, shots, k, 3)
+    assert p["lockstep"] and p["time_tile"] >= 1 and k % p["time_tile"] == 0
