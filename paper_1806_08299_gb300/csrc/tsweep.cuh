@@ -79,7 +79,21 @@ struct TShape {
     static constexpr int N1 = (LZ1 * LY1 + 31) / 32 * 32;
     static constexpr int LZ2 = BZ / V, LY2 = BY / VY;     // stage-2 thread grid
     static constexpr int N2 = T == 2 ? (LZ2 * LY2 + 31) / 32 * 32 : 0;
-    static constexpr int NTB = N1 + N2 + 32;              // + the producer warp
+    // MB = 0: one block per SM whose consumer warps take over the registers
+    // of a producer warpgroup (setmaxnreg).  Each quarter of an SM has its
+    // own 16K registers for every fourth warp, so a block of 8 consumer
+    // warps and a producer warp is capped at 168 registers per thread; with
+    // the producer widened to a warpgroup (one warp of it works) that gives
+    // up all but PREG, the consumers run with CREG.
+    static constexpr bool RSPLIT = MB == 0;
+    static constexpr int MINB = RSPLIT ? 1 : MB;          // __launch_bounds__ minimum
+    static constexpr int NP = RSPLIT ? 128 : 32;          // producer threads
+    static constexpr int NTB = N1 + N2 + NP;
+    static constexpr int LREG_ = (65536 / NTB) / 8 * 8;
+    static constexpr int LREG = LREG_ > 255 ? 255 : LREG_;  // registers per thread at launch
+    static constexpr int PREG = 40;
+    static constexpr int CREG_ = ((LREG * NTB - PREG * NP) / (N1 + N2)) / 8 * 8;
+    static constexpr int CREG = CREG_ > 232 ? 232 : CREG_;
     // L2 prefetch distance in iterations (0: none).  With one slot of
     // lookahead (P = 1) a ring-A load is issued about one iteration before
     // its use, which does not cover HBM latency, so its inputs are first
@@ -121,8 +135,14 @@ struct TShape {
     static_assert(TXA < (1u << 20), "mbarrier tx count");
     static_assert(NTB <= 1024, "too many threads per block");
     static_assert(SMEM <= 215 * 1024, "shared memory above the per-block limit");
-    static_assert(MB >= 1 && (size_t)MB * (SMEM + 4096) <= 228 * 1024 && MB * NTB <= 2048,
+    static_assert(MB >= 0 && (size_t)MINB * (SMEM + 4096) <= 228 * 1024 && MINB * NTB <= 2048,
                   "blocks per SM do not fit shared memory or thread slots");
+    // the split: warpgroup-aligned roles, the consumers' registers within the
+    // block's launch allocation and, per SM quarter, within its 16K
+    static_assert(!RSPLIT || ((N1 + N2) % 128 == 0 && CREG >= LREG &&
+                              (long long)CREG * (N1 + N2) + (long long)PREG * NP <= (long long)LREG * NTB &&
+                              ((N1 + N2) / 128 * CREG + PREG) * 32 <= 16384),
+                  "register split does not fit");
     static_assert(MODE >= 0 && MODE <= 2, "mode: 0 plain, 1 second differences, 2 imaging condition");
 };
 
@@ -455,7 +475,8 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
 
     if (tid >= S::N1 + S::N2) {
         // ------------------------------ producer warp ------------------------------
-        const int lane = tid & 31;
+        if constexpr (S::RSPLIT) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(S::PREG));
+        const int lane = tid - (S::N1 + S::N2);  // lanes 0 and 1 of the first producer warp work
         if (a.withhold) return;
         if (lane == 0) {
             // ring A: the stage-1 inputs of iteration i
@@ -534,6 +555,7 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
         return;
     }
 
+    if constexpr (S::RSPLIT) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(S::CREG));
     if (tid < S::N1) {
         // ------------------------------ stage 1 ------------------------------
         const bool act = tid < S::LZ1 * S::LY1;
@@ -788,9 +810,11 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
 }
 
 // MB: resident blocks per SM the variant is compiled for (the
-// __launch_bounds__ minimum, which caps the registers per thread).
+// __launch_bounds__ minimum, which caps the registers per thread); 0: one
+// block per SM with the registers split between producer and consumers.
 template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB, int MODE = 0>
-__global__ void __launch_bounds__(TShape<R, T, V, VY, BZ, BY, P, MB, MODE>::NTB, MB)
+__global__ void __launch_bounds__(TShape<R, T, V, VY, BZ, BY, P, MB, MODE>::NTB,
+                                  TShape<R, T, V, VY, BZ, BY, P, MB, MODE>::MINB)
 tsweep_kernel(const __grid_constant__ SweepArgs a, const __grid_constant__ Stencil st,
               const __grid_constant__ TMaps mp)
 {
@@ -814,7 +838,7 @@ struct ShotTSweep {  // 128-byte aligned, as its tensor maps
 // `step` of every shot, and `parity` selects their buffers (forward and
 // adjoint sweeps; the gradient modes run on the batched kernel of sweep.cuh).
 template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB>
-__global__ void __launch_bounds__(TShape<R, T, V, VY, BZ, BY, P, MB, 0>::NTB, MB)
+__global__ void __launch_bounds__(TShape<R, T, V, VY, BZ, BY, P, MB, 0>::NTB, TShape<R, T, V, VY, BZ, BY, P, MB, 0>::MINB)
 tsweep_multi_kernel(const ShotTSweep *__restrict__ shots, const int2 *__restrict__ block_map,
                     const __grid_constant__ Stencil st, int parity, int step)
 {

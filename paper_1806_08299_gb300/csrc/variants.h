@@ -47,6 +47,9 @@
 // has its own 16K registers and takes every fourth warp, so a block of w
 // warps (times MB) can give a thread at most 16384 / (32 ceil(w MB / 4))
 // registers: at so 16 (about 200 registers) no more than eight warps.
+// MB = 0 is one block per SM of eight consumer warps and a producer
+// warpgroup whose registers the consumers take over (setmaxnreg): eight
+// consumer warps at up to 232 registers.
 #define WAVE_TSWEEP_VARIANTS_R1(Z) Z(1, 1, 4, 1, 64, 8, 2, 3) Z(1, 2, 4, 2, 128, 12, 1, 1)
 #define WAVE_TSWEEP_VARIANTS_R2(Z)                                                                 \
     Z(2, 1, 4, 1, 64, 8, 2, 2) Z(2, 1, 4, 2, 64, 16, 2, 2) Z(2, 2, 4, 2, 56, 24, 2, 1)            \
@@ -60,9 +63,12 @@
 #define WAVE_TSWEEP_VARIANTS_R5(Z) Z(5, 1, 4, 2, 64, 16, 2, 2)
 #define WAVE_TSWEEP_VARIANTS_R6(Z) \
     Z(6, 1, 4, 1, 64, 8, 2, 2) Z(6, 1, 4, 2, 64, 16, 2, 2) Z(6, 1, 4, 2, 64, 32, 2, 1) Z(6, 2, 4, 2, 32, 24, 1, 1)
-#define WAVE_TSWEEP_VARIANTS_R7(Z) Z(7, 1, 4, 2, 64, 16, 2, 1)
-#define WAVE_TSWEEP_VARIANTS_R8(Z) \
-    Z(8, 1, 4, 1, 64, 8, 2, 2) Z(8, 1, 4, 2, 64, 16, 2, 1) Z(8, 1, 4, 2, 64, 24, 2, 1) Z(8, 2, 4, 2, 32, 8, 1, 1)
+#define WAVE_TSWEEP_VARIANTS_R7(Z) \
+    Z(7, 1, 4, 2, 64, 16, 2, 1) Z(7, 1, 4, 2, 64, 32, 2, 0) Z(7, 1, 4, 2, 64, 32, 1, 0)
+#define WAVE_TSWEEP_VARIANTS_R8(Z)                                                                 \
+    Z(8, 1, 4, 1, 64, 8, 2, 2) Z(8, 1, 4, 2, 64, 16, 2, 1) Z(8, 1, 4, 2, 64, 24, 2, 1)             \
+    Z(8, 2, 4, 2, 32, 8, 1, 1) Z(8, 1, 4, 2, 64, 32, 2, 0) Z(8, 1, 4, 2, 64, 32, 1, 0)             \
+    Z(8, 1, 4, 2, 32, 64, 2, 0)
 
 // Gradient-mode variants Y(R, T, V, BZ, BY, P, MB, XB): the untiled default
 // shape of a radius with XB extra ring-K boxes (1: E for the second-difference

@@ -1,5 +1,6 @@
 // wave_internal.h -- declarations shared by the library's translation units.
 #pragma once
+#include <atomic>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -158,6 +159,32 @@ cudaError_t launch_sweep(int nblocks, cudaStream_t stream, const SweepArgs &a, c
     return cudaLaunchKernelEx(&cfg, sweep_kernel<R, T, V, BZ, BY, P, MB, XB>, a, st, m);
 }
 
+// A register-split shape (MB = 0) relies on its kernel being compiled with
+// the launch register count the split assumes; with fewer, the consumers'
+// setmaxnreg.inc would wait for registers the block does not hold.  Checked
+// once per kernel before its first launch.
+template <class S>
+cudaError_t check_regsplit(const void *func)
+{
+    if constexpr (!S::RSPLIT) {
+        return cudaSuccess;
+    } else {
+        static std::atomic<int> state{0};  // 0: not checked, 1: fits, 2: does not
+        int s = state.load();
+        if (s == 0) {
+            cudaFuncAttributes fa;
+            const cudaError_t e = cudaFuncGetAttributes(&fa, func);
+            if (e != cudaSuccess) return e;
+            s = (long long)fa.numRegs * S::NTB >=
+                        (long long)S::CREG * (S::N1 + S::N2) + (long long)S::PREG * S::NP
+                    ? 1
+                    : 2;
+            state.store(s);
+        }
+        return s == 1 ? cudaSuccess : cudaErrorInvalidConfiguration;
+    }
+}
+
 template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB, int MODE = 0>
 cudaError_t launch_tsweep(int nblocks, cudaStream_t stream, const SweepArgs &a, const Stencil &st,
                           const TMaps &m)
@@ -165,6 +192,7 @@ cudaError_t launch_tsweep(int nblocks, cudaStream_t stream, const SweepArgs &a, 
     using S = TShape<R, T, V, VY, BZ, BY, P, MB, MODE>;
     const size_t smem = S::smem_bytes(a.chunk);
     cudaError_t e = allow_max_dynamic_smem((const void *)tsweep_kernel<R, T, V, VY, BZ, BY, P, MB, MODE>);
+    if (e == cudaSuccess) e = check_regsplit<S>((const void *)tsweep_kernel<R, T, V, VY, BZ, BY, P, MB, MODE>);
     if (e != cudaSuccess) return e;
     // programmatic dependent launch, as launch_sweep
     cudaLaunchAttribute attr[1];
@@ -185,6 +213,9 @@ cudaError_t launch_tsweep_multi(int nblocks, size_t smem, cudaStream_t stream, c
                                 const int2 *block_map, const Stencil &st, int parity, int step)
 {
     cudaError_t e = allow_max_dynamic_smem((const void *)tsweep_multi_kernel<R, T, V, VY, BZ, BY, P, MB>);
+    if (e == cudaSuccess)
+        e = check_regsplit<TShape<R, T, V, VY, BZ, BY, P, MB, 0>>(
+            (const void *)tsweep_multi_kernel<R, T, V, VY, BZ, BY, P, MB>);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

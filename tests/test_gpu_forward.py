@@ -291,7 +291,7 @@ def test_dense_receiver_carpet(wavelib, cuda, oracle, so, T, kernel):
         assert np.array_equal(d, d1) and np.array_equal(ul, ul1)
 
 
-@pytest.mark.parametrize("so", [4, 8])
+@pytest.mark.parametrize("so", [4, 8, 14, 16])
 def test_staged_kernel_splits_bitwise(wavelib, cuda, oracle, so):
     """The stage-specialised sweep (each time step of a tile on its own
     warps) at T = 1 and 2 and both rows-per-thread shapes, with x-chunks from
