@@ -20,6 +20,9 @@ Functions and what pins them (see tests/test_oracle_*.py):
                        of a discrete Dirichlet sine mode (so 2), one step
                        of a quadratic exact away from the boundary, a
                        source on a node, linearity in u0 and f    (pinned)
+  born                 linearised modelling (the derivative of forward
+                       in m): central finite differences of forward,
+                       the dot identity with gradient, linearity    (pinned)
   forward_batched,     per-shot forward / gradient on windows of one
   gradient_batched     model, window gradients summed into the global
                        grid; pinned by whole-grid shots, shot additivity
@@ -60,6 +63,8 @@ def _load():
         lib.oracle_gradient.restype = i
         lib.oracle_heat.argtypes = [ip, dp, d, i, i, dp, dp, dp, i, dp, dp, i, dp, dp, dp]
         lib.oracle_heat.restype = i
+        lib.oracle_born.argtypes = [ip, dp, d, i, i, dp, dp, dp, dp, i, dp, dp, i, dp, dp, dp]
+        lib.oracle_born.restype = i
         _lib = lib
     return _lib
 
@@ -195,6 +200,29 @@ def gradient(m, damp, h, dt, nt, space_order, src_xyz, src_q, rec_xyz, res):
     if rc:
         raise RuntimeError("oracle_gradient failed (%d)" % rc)
     return g
+
+
+def born(m, damp, dm, h, dt, nt, space_order, src_xyz, src_q, rec_xyz):
+    """Born (linearised) modelling: the derivative of the receiver traces
+    with respect to m in the direction dm.  Returns (dd [nt][nrec],
+    du_last [2][...] = (du^nt, du^{nt-1})).  Not in the paper: the
+    linearisation of the leapfrog scheme written out in wave_oracle.c."""
+    m = _arr(m)
+    n = m.shape
+    damp = _arr(damp, n)
+    dm = _arr(dm, n)
+    nsrc, sx = _pts(src_xyz)
+    nrec, rx = _pts(rec_xyz)
+    q = _arr(src_q, (nt, nsrc)) if nsrc else np.zeros((1,))
+    dd = np.zeros((nt, max(nrec, 1)))
+    du_last = np.zeros((2,) + n)
+    c = _coeffs(space_order)
+    rc = _load().oracle_born(
+        _ints(n), _p(_arr(h)), float(dt), int(nt), space_order // 2, _p(c), _p(m), _p(damp), _p(dm),
+        nsrc, _p(sx), _p(q), nrec, _p(rx), _p(dd), _p(du_last))
+    if rc:
+        raise RuntimeError("oracle_born failed (%d)" % rc)
+    return dd[:, :nrec], du_last
 
 
 def heat(u0, h, dt, nt, space_order, kappa=None, src_xyz=None, src_q=None, rec_xyz=None):

@@ -595,3 +595,77 @@ int oracle_gradient(const int *n, const double *h, double dt, int nt, int r, con
     free(lam_all);
     return 0;
 }
+
+/* Born (linearised) modelling: the derivative of the forward map m -> d in
+ * the direction dm (not in the paper; the textbook linearisation of the
+ * scheme above).  With N = 2 m u^n - (m - eta) u^{n-1} + dt^2 (L u^n + f^n),
+ * u^{n+1} = alpha N and d alpha / dm = -alpha^2, d N / dm = 2 u^n - u^{n-1}:
+ *   du^{n+1} = alpha (2 m du^n - (m - eta) du^{n-1} + dt^2 L du^n)
+ *              - alpha dm (u^{n+1} - 2 u^n + u^{n-1}),
+ *   du^0 = du^-1 = 0,   dd^n[r] = sum_p w_{r,p} du^{n+1}[p].
+ * Each step advances u over the whole grid first, then du. */
+int oracle_born(const int *n, const double *h, double dt, int nt, int r, const double *c,
+                const double *m, const double *damp, const double *dm,
+                int nsrc, const double *src_xyz, const double *src_q,
+                int nrec, const double *rec_xyz, double *rec_dd, double *du_last)
+{
+    long N = npts(n);
+    srcmap_t sm;
+    recmap_t rm;
+    if (srcmap_build(&sm, n, h, nsrc, src_xyz) || recmap_build(&rm, n, h, nrec, rec_xyz)) return -1;
+    double *um = (double *)calloc(N, sizeof(double));
+    double *u = (double *)calloc(N, sizeof(double));
+    double *up = (double *)calloc(N, sizeof(double));
+    double *vm = (double *)calloc(N, sizeof(double));
+    double *v = (double *)calloc(N, sizeof(double));
+    double *vp = (double *)calloc(N, sizeof(double));
+    double *corners = (double *)calloc((size_t)nt * 8 * (nrec > 0 ? nrec : 1), sizeof(double));
+    if (!um || !u || !up || !vm || !v || !vp || !corners) return -1;
+    for (int step = 0; step < nt; step++) {
+#pragma omp parallel for schedule(static)
+        for (long x = 0; x < n[0]; x++)
+            for (long y = 0; y < n[1]; y++)
+                for (long z = 0; z < n[2]; z++) {
+                    long p = at(n, x, y, z);
+                    double lap = lap_at(n, h, r, c, 0, u, x, y, z);
+                    double f = src_term(&sm, src_q, step, p);
+                    up[p] = update_point(m[p], damp[p], dt, u[p], um[p], lap, f);
+                }
+#pragma omp parallel for schedule(static)
+        for (long x = 0; x < n[0]; x++)
+            for (long y = 0; y < n[1]; y++)
+                for (long z = 0; z < n[2]; z++) {
+                    long p = at(n, x, y, z);
+                    double eta = damp[p] * dt / 2.0;
+                    double alpha = 1.0 / (m[p] + eta);
+                    double lap = lap_at(n, h, r, c, 0, v, x, y, z);
+                    double d2 = up[p] - 2.0 * u[p] + um[p];
+                    vp[p] = alpha * (2.0 * m[p] * v[p] - (m[p] - eta) * vm[p] + dt * dt * lap)
+                            - alpha * dm[p] * d2;
+                    rec_record(&rm, corners, step, p, vp[p]);
+                }
+        double *t = um;
+        um = u;
+        u = up;
+        up = t;
+        t = vm;
+        vm = v;
+        v = vp;
+        vp = t;
+    }
+    if (nrec > 0 && rec_dd) rec_finish(&rm, corners, nt, rec_dd);
+    if (du_last) {
+        memcpy(du_last, v, sizeof(double) * N);
+        memcpy(du_last + N, vm, sizeof(double) * N);
+    }
+    free(um);
+    free(u);
+    free(up);
+    free(vm);
+    free(v);
+    free(vp);
+    free(corners);
+    srcmap_free(&sm);
+    recmap_free(&rm);
+    return 0;
+}
