@@ -63,6 +63,8 @@ extern "C" {
 #define WAVE_OP_FWD 0
 #define WAVE_OP_ADJ 1
 #define WAVE_OP_GRAD 2
+#define WAVE_OP_REVOLVE 3 /* wave_grad_revolve; the ckpt_every argument is nslots */
+#define WAVE_OP_BORN 4    /* wave_born */
 
 /* wave_tuning.flags */
 #define WAVE_ALLOW_UNSTABLE 1 /* skip the dt <= CFL check                              */
@@ -192,6 +194,66 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp,
                   const wave_points *rec, const float *rec_resid,
                   const float *ckpt, int32_t ckpt_every, float *grad,
                   const wave_tuning *tuning, void *ws, size_t ws_bytes, void *stream);
+
+/* The same gradient as wave_grad, without a previous wave_fwd: binomial
+ * checkpointing (revolve; A. Griewank, Optim. Methods Softw. 1, 1992;
+ * A. Griewank and A. Walther, ACM TOMS 26, 2000) reverses the nt steps with
+ * nslots stored states (0 <= nslots <= nt) in the workspace.  The paper uses
+ * uniform checkpoints; this schedule needs far less memory for long runs at
+ * the price of recomputed forward steps, the fewest possible for nslots
+ * states: wave_revolve_forward_steps(nt, nslots) of them in all, counting
+ * the recomputation inside each reversed step (2 nt - 1 when nslots >=
+ * nt - 1, as wave_fwd plus wave_grad less one; nt (nt + 1) / 2 with
+ * nslots = 0).  Each reversed step n
+ * recomputes u^{n+1} from a restored or current state with D^n stored, then
+ * runs the adjoint step of n with the imaging condition, so the result is
+ * wave_grad's, bit for bit, for any checkpoint interval.  Arguments as
+ * wave_grad; workspace: wave_workspace_bytes(g, WAVE_OP_REVOLVE, nsrc, nrec,
+ * nslots, tuning). */
+int32_t wave_grad_revolve(const wave_grid *g, const float *m, const float *damp,
+                          const wave_points *src, const float *src_traces,
+                          const wave_points *rec, const float *rec_resid, int32_t nslots,
+                          float *grad, const wave_tuning *tuning, void *ws, size_t ws_bytes,
+                          void *stream);
+
+/* Born (linearised) modelling: the derivative of the receiver traces of
+ * wave_fwd with respect to m in the direction dm (not in the paper; the
+ * linearisation of its scheme).  With D^n = u^{n+1} - 2u^n + u^{n-1} of the
+ * background wavefield u (sources as wave_fwd) and alpha = 1 / (m + eta),
+ *   du^{n+1} = alpha (2 m du^n - (m - eta) du^{n-1} + dt^2 L du^n) - alpha dm D^n,
+ *   du^0 = du^-1 = 0,   rec_traces[n][r] = sum_p w_{r,p} du^{n+1}[p].
+ * Its adjoint is wave_grad: <born(dm), r> = <dm, grad(r)>.  Each step runs
+ * the background sweep, storing D^n, then the perturbation sweep, which
+ * adds C (P D^n) with P = -dm / dt^2 (C = alpha dt^2) to its new level.
+ *   m, damp, dm  device [nx][ny][nz]
+ *   src / src_traces, rec   as wave_fwd
+ *   rec_traces   device [nt][nrec] out (linearised data)
+ *   du_last      device [2][nx][ny][nz] out (du^nt, du^{nt-1}), or NULL
+ *   tuning       as wave_fwd: the plan of the background sweep; the
+ *                perturbation sweep runs the one untiled variant of its order
+ *   ws, ws_bytes wave_workspace_bytes(g, WAVE_OP_BORN, nsrc, nrec, 0, tuning)
+ * Returns WAVE_OK or a WAVE_E* code; device status as wave_fwd. */
+int32_t wave_born(const wave_grid *g, const float *m, const float *damp, const float *dm,
+                  const wave_points *src, const float *src_traces, const wave_points *rec,
+                  float *rec_traces, float *du_last, const wave_tuning *tuning, void *ws,
+                  size_t ws_bytes, void *stream);
+
+/* Forward steps (recomputations included, one per reversed step) of the
+ * schedule wave_grad_revolve runs for nt steps and nslots states, or -1 for
+ * invalid arguments.  Host only. */
+int64_t wave_revolve_forward_steps(int32_t nt, int32_t nslots);
+
+/* The schedule itself, host only: returns the number of actions and writes
+ * the first min(cap, count) as (kind, a, b) triples into actions (HOST):
+ *   0 ADVANCE a b   forward from the current state (step a) to step b
+ *   1 TAKESHOT a k  store the current state (step a) in slot k
+ *   2 RESTORE a k   make the state of step a in slot k current (k = -1: the
+ *                   zero initial state of step 0)
+ *   3 YOUTURN a 0   one forward step from the current state (step a) storing
+ *                   D^a, then the adjoint step of time index a
+ * The run starts with the zero state of step 0 current.  WAVE_EINVAL for
+ * invalid arguments. */
+int32_t wave_revolve_schedule(int32_t nt, int32_t nslots, int32_t *actions, int32_t cap);
 
 /* The heat (Laplace) operator of Sec. 5.7 through the same time-tiled sweep:
  * explicit Euler for u_t = kappa (lap u + f),

@@ -47,7 +47,9 @@ __global__ void prep_kernel(const float *__restrict__ m, const float *__restrict
     }
 }
 
-__global__ void pad_kernel(const float *__restrict__ src, int nx, int ny, int nz, int nzp,
+// dst = scale src in the z-padded layout, 0 in the padding (scale 1 copies
+// the values exactly)
+__global__ void pad_kernel(const float *__restrict__ src, int nx, int ny, int nz, int nzp, float scale,
                            float *__restrict__ dst)
 {
     const long long npad = (long long)nx * ny * nzp;
@@ -55,7 +57,7 @@ __global__ void pad_kernel(const float *__restrict__ src, int nx, int ny, int nz
          p += (long long)gridDim.x * blockDim.x) {
         const int z = (int)(p % nzp);
         const long long xy = p / nzp;
-        dst[p] = z < nz ? src[xy * nz + z] : 0.f;
+        dst[p] = z < nz ? __fmul_rn(scale, src[xy * nz + z]) : 0.f;
     }
 }
 
@@ -145,9 +147,9 @@ cudaError_t launch_prep(const float *m, const float *damp, int nx, int ny, int n
 }
 
 cudaError_t launch_pad(const float *src, int nx, int ny, int nz, int nzp, float *dst,
-                       cudaStream_t s)
+                       cudaStream_t s, float scale)
 {
-    pad_kernel<<<grid_for((long long)nx * ny * nzp), 256, 0, s>>>(src, nx, ny, nz, nzp, dst);
+    pad_kernel<<<grid_for((long long)nx * ny * nzp), 256, 0, s>>>(src, nx, ny, nz, nzp, scale, dst);
     return cudaGetLastError();
 }
 

@@ -5,4 +5,5 @@
 WAVE_DEFINE_RADIUS(5)
 #define WAVE_MULTI_ARGS(...) WAVE_DEFINE_MULTI(__VA_ARGS__)
 WAVE_MULTI_ARGS(WAVE_MULTI_R5)
+WAVE_DEFINE_MODES(5)
 WAVE_DEFINE_TMULTI(5)

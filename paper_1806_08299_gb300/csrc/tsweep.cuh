@@ -64,6 +64,7 @@ struct TMaps {
     //   MODE 1: x0 = E; y0 = E (T = 2)
     //   MODE 2: T = 1: x0 = D row l_row0, x1 = G;  T = 2: y0, y1 = D rows l_row0,
     //           l_row0 + l_dir, y2 = G
+    //   MODE 3: T = 1: x0 = D row l_row0, x1 = P (Born source coefficient)
     CUtensorMap x0, x1, y0, y1, y2;
 };
 
@@ -108,7 +109,7 @@ struct TShape {
     static constexpr unsigned FBOXP = (FBOX + 127) / 128 * 128;
     static constexpr unsigned SBOXP = (SBOX + 127) / 128 * 128;
     // extra boxes of the gradient modes per ring-A / ring-B slot
-    static constexpr int XA = MODE == 0 ? 0 : (T == 1 ? MODE : (MODE == 1 ? 1 : 0));
+    static constexpr int XA = MODE == 0 ? 0 : (T == 1 ? (MODE == 3 ? 2 : MODE) : (MODE == 1 ? 1 : 0));
     static constexpr int XBB = T == 2 ? (MODE == 1 ? 1 : (MODE == 2 ? 3 : 0)) : 0;
     // ring A slot: centre box, level n (queue feed), level n-1, B, C, [x0, x1]
     static constexpr unsigned A_C = 0, A_F = CBOXP, A_UM = A_F + FBOXP, A_B = A_UM + FBOXP,
@@ -143,7 +144,8 @@ struct TShape {
                               (long long)CREG * (N1 + N2) + (long long)PREG * NP <= (long long)LREG * NTB &&
                               ((N1 + N2) / 128 * CREG + PREG) * 32 <= 16384),
                   "register split does not fit");
-    static_assert(MODE >= 0 && MODE <= 2, "mode: 0 plain, 1 second differences, 2 imaging condition");
+    static_assert(MODE >= 0 && MODE <= 3 && (MODE != 3 || T == 1),
+                  "mode: 0 plain, 1 second differences, 2 imaging condition, 3 Born source (T = 1)");
 };
 
 // Level n+1 of a thread's VY x V points (VY rows, V/2 pairs each) from the
@@ -357,7 +359,10 @@ __device__ __forceinline__ void tstage_abort(volatile int *abort_flag, int *stat
 // loads.  MODE 2 (the adjoint sweep with the imaging condition): the
 // accumulator gacc at each own point takes g += level(n+s) D[l_row0 + l_dir
 // (s-1)] for s = 1..T in that order; with T = 2 stage 2 does both, its queue
-// centre being level n+1 of its own points.
+// centre being level n+1 of its own points.  MODE 3 (the perturbation sweep
+// of Born modelling, T = 1): the new level takes the dense source C P D of
+// the background's second difference D (row l_row0 of dload) with the
+// per-point coefficient P = -dm / dt^2, as u^{n+1} + C (P D).
 template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB, int MODE>
 __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &st, const TMaps &mp,
                                              const int blk)
@@ -613,7 +618,7 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                 long long pix = 0;
                 float2 ex[VY][V2], dd[VY][V2];
                 if constexpr (S::XA >= 1) {
-                    // E (MODE 1) or this step's D row (MODE 2, T = 1) from the slot
+                    // E (MODE 1) or this step's D row (MODE 2 and 3, T = 1) from the slot
                     pix = (long long)cs * a.sx + (long long)gy * a.nz + gz;
 #pragma unroll
                     for (int v = 0; v < VY; ++v) {
@@ -643,6 +648,16 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                             for (int j = 0; j < V2; ++j) g[j] = __ffma2_rn(un[v][j], ex[v][j], g[j]);
                             st2<V>(a.gacc + pix + (long long)v * a.nz, g);
                         }
+                }
+                if constexpr (MODE == 3) {
+#pragma unroll
+                    for (int v = 0; v < VY; ++v) {
+                        float2 pb[V2];
+                        ld2<V>(pb, sl + S::A_X1 / 4 + offF + v * S::W1);
+#pragma unroll
+                        for (int j = 0; j < V2; ++j)
+                            un[v][j] = __ffma2_rn(cC[v][j], __fmul2_rn(pb[j], ex[v][j]), un[v][j]);
+                    }
                 }
                 if constexpr (T == 1) {
 #pragma unroll

@@ -76,21 +76,35 @@
 // stream every input through TMA.  A shape without a mode variant runs its
 // gradient sweeps on the plain variant, which reads the extras with ordinary
 // loads.
+#define WAVE_SWEEP_MODE_VARIANTS_R1(Y)
 #define WAVE_SWEEP_MODE_VARIANTS_R2(Y) Y(2, 1, 8, 64, 16, 2, 2, 1) Y(2, 1, 8, 64, 16, 2, 2, 2)
+#define WAVE_SWEEP_MODE_VARIANTS_R3(Y)
 #define WAVE_SWEEP_MODE_VARIANTS_R4(Y) Y(4, 1, 4, 64, 8, 2, 3, 1) Y(4, 1, 4, 64, 8, 2, 3, 2)
+#define WAVE_SWEEP_MODE_VARIANTS_R5(Y)
+#define WAVE_SWEEP_MODE_VARIANTS_R6(Y)
+#define WAVE_SWEEP_MODE_VARIANTS_R7(Y)
+#define WAVE_SWEEP_MODE_VARIANTS_R8(Y)
 
 // Gradient-mode variants of the stage-specialised sweep, Z(R, T, V, VY, BZ, BY,
 // P, MB, MODE): MODE 1 (second differences stored; E streamed through TMA),
 // MODE 2 (imaging condition; the D rows and G streamed through TMA).  A
 // stage-specialised plan runs the mode variant of its own shape, or else the
 // first of its depth (every shape gives the same bits); the extra boxes make
-// the depth-2 slots larger, so so 8 has its own 32x32 shape.
+// the depth-2 slots larger, so so 8 has its own 32x32 shape.  MODE 3 (the
+// Born perturbation sweep: D and the source coefficient streamed through
+// TMA) has one untiled shape per radius, the only kernel that runs it.
+#define WAVE_TSWEEP_MODE_VARIANTS_R1(Z) Z(1, 1, 4, 1, 64, 8, 2, 2, 3)
 #define WAVE_TSWEEP_MODE_VARIANTS_R2(Z)                                                            \
     Z(2, 1, 4, 1, 64, 8, 2, 2, 1) Z(2, 1, 4, 1, 64, 8, 2, 2, 2) Z(2, 2, 4, 2, 128, 12, 1, 1, 1)    \
-    Z(2, 2, 4, 2, 128, 12, 1, 1, 2)
+    Z(2, 2, 4, 2, 128, 12, 1, 1, 2) Z(2, 1, 4, 1, 64, 8, 2, 2, 3)
+#define WAVE_TSWEEP_MODE_VARIANTS_R3(Z) Z(3, 1, 4, 2, 64, 16, 2, 2, 3)
 #define WAVE_TSWEEP_MODE_VARIANTS_R4(Z)                                                            \
     Z(4, 1, 4, 2, 64, 16, 2, 2, 1) Z(4, 1, 4, 2, 64, 16, 2, 2, 2) Z(4, 2, 4, 2, 32, 32, 1, 1, 1)   \
-    Z(4, 2, 4, 2, 32, 32, 1, 1, 2)
+    Z(4, 2, 4, 2, 32, 32, 1, 1, 2) Z(4, 1, 4, 2, 64, 16, 2, 2, 3)
+#define WAVE_TSWEEP_MODE_VARIANTS_R5(Z) Z(5, 1, 4, 2, 64, 16, 2, 2, 3)
+#define WAVE_TSWEEP_MODE_VARIANTS_R6(Z) Z(6, 1, 4, 2, 64, 16, 2, 2, 3)
+#define WAVE_TSWEEP_MODE_VARIANTS_R7(Z) Z(7, 1, 4, 2, 64, 32, 2, 0, 3)
+#define WAVE_TSWEEP_MODE_VARIANTS_R8(Z) Z(8, 1, 4, 2, 64, 32, 2, 0, 3)
 
 // Batched stage-specialised variants M(R, T, V, VY, BZ, BY, P, MB): the
 // forward and adjoint sweeps of a survey group on the stage-specialised

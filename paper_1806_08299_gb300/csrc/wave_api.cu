@@ -290,6 +290,7 @@ struct Layout {
     float *V[4] = {nullptr, nullptr, nullptr, nullptr};
     float *G = nullptr;
     float *store = nullptr;
+    float *slots = nullptr;  // revolve: nslots states of two levels
     DevTable inj, rec, inj2;
     float *corner = nullptr;
     int *order = nullptr;    // launch order of the sweep's blocks (order_cap entries)
@@ -300,20 +301,34 @@ struct Layout {
 // op FWD: inj = sources, rec = receivers, corner [nt][8 nrec]
 // op ADJ: inj = receivers, rec = sources, corner [nt][8 nsrc]
 // op GRAD: inj = sources (recompute), inj2 = receivers (adjoint), V, G, store [k]
+// op REVOLVE: as GRAD with one store row, then ckpt_every (= nslots) states
+// op BORN: E, U (background), V (perturbation), G = the Born coefficient P,
+//          one store row (the background's D), inj = sources, rec = receivers
+//          (recording the perturbation), corner [nt][8 nrec]
 Layout carve(void *ws, size_t cap, bool dry, const Dims &d, int op, int nsrc, int nrec, int nt,
              int ckpt_every)
 {
     Carver c(ws, cap, dry);
     Layout L;
+    const bool grad = op == WAVE_OP_GRAD || op == WAVE_OP_REVOLVE;
     L.status = c.take<int>(kStatusWords);
     L.cB = c.take<float>(d.npad);
     L.cC = c.take<float>(d.npad);
-    if (op == WAVE_OP_GRAD) L.cE = c.take<float>(d.npad);
+    if (grad || op == WAVE_OP_BORN) L.cE = c.take<float>(d.npad);
     for (int i = 0; i < 4; ++i) L.U[i] = c.take<float>(d.npad);
-    if (op == WAVE_OP_GRAD) {
+    if (op == WAVE_OP_BORN) {
         for (int i = 0; i < 4; ++i) L.V[i] = c.take<float>(d.npad);
         L.G = c.take<float>(d.npad);
-        L.store = c.take<float>((size_t)d.npad * (size_t)std::max(1, std::min(ckpt_every, nt)));
+        L.store = c.take<float>(d.npad);
+        carve_table(c, d, nsrc, &L.inj);
+        carve_table(c, d, nrec, &L.rec);
+        L.corner = c.take<float>((size_t)nt * 8 * std::max(nrec, 0));
+    } else if (grad) {
+        for (int i = 0; i < 4; ++i) L.V[i] = c.take<float>(d.npad);
+        L.G = c.take<float>(d.npad);
+        const int rows = op == WAVE_OP_REVOLVE ? 1 : std::max(1, std::min(ckpt_every, nt));
+        L.store = c.take<float>((size_t)d.npad * (size_t)rows);
+        if (op == WAVE_OP_REVOLVE) L.slots = c.take<float>((size_t)d.npad * 2 * (size_t)std::max(0, ckpt_every));
         carve_table(c, d, nsrc, &L.inj);
         carve_table(c, d, nrec, &L.inj2);
     } else {
@@ -443,12 +458,35 @@ int rows_of(const SweepVariant *v) { return v->VY > 0 ? v->VY : 1; }
 
 // The gradient-mode variant (XB = mode) of shape v (same kernel family,
 // tile, rows and, for the stage-specialised sweep, prefetch), or nullptr.
+int mode_variants_for(int R, const SweepVariant **out)
+{
+    switch (R) {
+    case 1: return wt::sweep_mode_variants_r1(out);
+    case 2: return wt::sweep_mode_variants_r2(out);
+    case 3: return wt::sweep_mode_variants_r3(out);
+    case 4: return wt::sweep_mode_variants_r4(out);
+    case 5: return wt::sweep_mode_variants_r5(out);
+    case 6: return wt::sweep_mode_variants_r6(out);
+    case 7: return wt::sweep_mode_variants_r7(out);
+    case 8: return wt::sweep_mode_variants_r8(out);
+    default: *out = nullptr; return 0;
+    }
+}
+
+// The variant of the Born perturbation sweep (mode 3) of radius R.
+const SweepVariant *born_variant(int R)
+{
+    const SweepVariant *vs = nullptr;
+    const int nv = mode_variants_for(R, &vs);
+    for (int i = 0; i < nv; ++i)
+        if (vs[i].XB == 3) return &vs[i];
+    return nullptr;
+}
+
 const SweepVariant *mode_variant(const SweepVariant *v, int mode)
 {
     const SweepVariant *vs = nullptr;
-    int nv = 0;
-    if (v->R == 2) nv = wt::sweep_mode_variants_r2(&vs);
-    if (v->R == 4) nv = wt::sweep_mode_variants_r4(&vs);
+    const int nv = mode_variants_for(v->R, &vs);
     for (int i = 0; i < nv; ++i)
         if (vs[i].T == v->T && vs[i].V == v->V && vs[i].BZ == v->BZ && vs[i].BY == v->BY && vs[i].XB == mode &&
             vs[i].kind == v->kind && rows_of(&vs[i]) == rows_of(v) && (v->kind == 0 || vs[i].P == v->P))
@@ -587,6 +625,7 @@ struct Job {
     long long l_base = 0;
     int l_dir = 1;
     float *gacc = nullptr;
+    const float *born = nullptr;  // Born perturbation sweep: the coefficient P = -dm / dt^2 (padded)
     // host copies of the injection / record tables and the device buffer for
     // the heavy-first launch order (nullptr: natural order)
     const HostTable *hinj = nullptr, *hrec = nullptr;
@@ -676,6 +715,11 @@ int build_launch(const Job &job, const State &s, int j, const SweepVariant *v, i
                 if (!rc) rc = encode_map(&tm->y1, job.dload + (row + job.l_dir) * d.npad, d, v->BZ, v->BY);
                 if (!rc) rc = encode_map(&tm->y2, job.gacc, d, v->BZ, v->BY);
             }
+        }
+        if (!rc && v->XB == 3) {
+            const long long row = job.l_base + (long long)job.l_dir * j;  // the background's D row
+            rc = encode_map(&tm->x0, job.dload + row * d.npad, d, v->W1, v->H1);
+            if (!rc) rc = encode_map(&tm->x1, job.born, d, v->W1, v->H1);
         }
         if (rc) return rc;
     } else {
@@ -850,8 +894,13 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
             std::min((v == plan.v && plan.chunk > 0) ? plan.chunk : default_chunk(d, v), max_chunk(v));
         // gradient sweeps: the mode variant of the same untiled shape, if compiled,
         // streams their extra inputs (E, or D and G) through TMA
-        const int mode = job.gacc != nullptr ? 2 : (job.dstore != nullptr ? 1 : 0);
-        if (mode > 0 && v->kind == 1) {
+        const int mode = job.gacc != nullptr ? 2 : (job.dstore != nullptr ? 1 : (job.born != nullptr ? 3 : 0));
+        if (mode == 3) {
+            // the Born perturbation sweep has one untiled variant per radius
+            v = born_variant(R);
+            if (v == nullptr) return WAVE_EUNSUPPORTED;
+            chunk = std::min(default_chunk(d, v), max_chunk(v));
+        } else if (mode > 0 && v->kind == 1) {
             // a stage-specialised shape runs its gradient-mode variant where one
             // is compiled; otherwise the untiled default of sweep.cuh (whose
             // gradient-mode variants stream the extra arrays through TMA, and
@@ -2040,6 +2089,118 @@ cudaError_t allow_max_dynamic_smem(const void *func)
 // C ABI
 // ===========================================================================
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Binomial checkpointing (revolve): A. Griewank, "Achieving logarithmic growth
+// of temporal and spatial complexity in reverse automatic differentiation",
+// Optim. Methods Softw. 1 (1992); A. Griewank and A. Walther, "Algorithm 799:
+// revolve", ACM TOMS 26 (2000).  The paper uses uniform checkpoints; this
+// schedule reverses nt steps with a fixed number of stored states and the
+// fewest recomputed forward steps.
+// ---------------------------------------------------------------------------
+
+enum RevKind { REV_ADVANCE = 0, REV_TAKESHOT = 1, REV_RESTORE = 2, REV_YOUTURN = 3 };
+// ADVANCE a b: forward from the current state (step a) to step b
+// TAKESHOT a k: store the current state (step a) in slot k
+// RESTORE a k: make the state of step a in slot k current (k = -1: the zero
+//              initial state, step 0)
+// YOUTURN a: from the current state (step a) one forward step that stores
+//            D^a, then the adjoint step of time index a
+struct RevAction {
+    int kind, a, b;
+};
+
+// C(n, k) saturated at cap (the partial products C(n-k+i, i) grow with i).
+long long binom_sat(long long n, long long k, long long cap)
+{
+    if (k < 0 || k > n) return 0;
+    k = std::min(k, n - k);
+    unsigned __int128 c = 1;
+    for (long long i = 1; i <= k; ++i) {
+        c = c * (unsigned __int128)(n - k + i) / (unsigned __int128)i;
+        if (c > (unsigned __int128)cap) return cap;
+    }
+    return (long long)c;
+}
+
+// Forward steps (besides the one of each reversed step) that reverse l steps
+// from a held start state with s free slots: with c = s + 1 stored states
+// and r the least integer with C(c + r, c) >= l, the minimum is
+// r l - C(c + r, r - 1) (Griewank 1992); s = 0 recomputes from the start.
+long long rev_cost(long long l, long long s)
+{
+    if (l <= 1) return 0;
+    if (s == 0) return l * (l - 1) / 2;
+    long long r = 0;
+    while (binom_sat(s + 1 + r, s + 1, l) < l) ++r;
+    return r * l - binom_sat(s + 1 + r, r - 1, (long long)1 << 60);
+}
+
+struct RevGen {
+    int nslots;
+    int cur = 0;  // step of the current state (-1: none); the run starts at the zero state
+    std::vector<RevAction> out;
+
+    void ensure(int a, int slot)
+    {
+        if (cur != a) {
+            out.push_back({REV_RESTORE, a, slot});
+            cur = a;
+        }
+    }
+    // reverse steps [a, b) given the state of step a in `slot` (or current),
+    // s slots free (slots nslots - s .. nslots - 1)
+    void reverse(int a, int b, int s, int slot)
+    {
+        const int l = b - a;
+        if (l <= 0) return;
+        if (l == 1) {
+            ensure(a, slot);
+            out.push_back({REV_YOUTURN, a, 0});
+            cur = a + 1;
+            return;
+        }
+        if (s == 0) {
+            for (int k = b - 1; k >= a; --k) {
+                ensure(a, slot);
+                if (k > a) out.push_back({REV_ADVANCE, a, k});
+                out.push_back({REV_YOUTURN, k, 0});
+                cur = k + 1;
+            }
+            return;
+        }
+        // first stored state at a + m: m + cost(m, s) + cost(l - m, s - 1)
+        // is least; the smallest such m
+        long long best = -1;
+        int m = 1;
+        for (int j = 1; j < l; ++j) {
+            const long long c = j + rev_cost(j, s) + rev_cost(l - j, s - 1);
+            if (best < 0 || c < best) {
+                best = c;
+                m = j;
+            }
+        }
+        ensure(a, slot);
+        out.push_back({REV_ADVANCE, a, a + m});
+        const int k = nslots - s;
+        out.push_back({REV_TAKESHOT, a + m, k});
+        cur = a + m;
+        reverse(a + m, b, s - 1, k);
+        reverse(a, a + m, s, slot);
+    }
+};
+
+std::vector<RevAction> revolve_schedule(int nt, int nslots)
+{
+    RevGen g;
+    g.nslots = nslots;
+    g.reverse(0, nt, nslots, -1);
+    return g.out;
+}
+
+}  // namespace
+
 extern "C" {
 
 int32_t wave_version(void) { return 100; }
@@ -2082,8 +2243,9 @@ size_t wave_workspace_bytes(const wave_grid *g, int32_t op, int32_t nsrc, int32_
 {
     (void)tuning;
     Dims d;
-    if (check_grid(g, &d) || nsrc < 0 || nrec < 0 || op < WAVE_OP_FWD || op > WAVE_OP_GRAD) return 0;
+    if (check_grid(g, &d) || nsrc < 0 || nrec < 0 || op < WAVE_OP_FWD || op > WAVE_OP_BORN) return 0;
     if (op == WAVE_OP_GRAD && ckpt_every < 1) return 0;
+    if (op == WAVE_OP_REVOLVE && (ckpt_every < 0 || ckpt_every > g->nt)) return 0;
     return carve(nullptr, 0, true, d, op, nsrc, nrec, g->nt, ckpt_every).bytes;
 }
 
@@ -2314,6 +2476,252 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
             aj.order = L.order;
             aj.order_cap = L.order_cap;
             if ((rc = run_steps(aj, adj, len, plan, stream))) return rc;
+        }
+        if ((rc = prof_end(stream))) return rc;
+        const float scale = (float)(-1.0 / ((double)g->dt * (double)g->dt));
+        CK(wt::launch_unpad(L.G, d.nx, d.ny, d.nz, d.nzp, scale, grad, stream));
+        return WAVE_OK;
+    } catch (...) {
+        return WAVE_EINVAL;
+    }
+}
+
+int32_t wave_born(const wave_grid *g, const float *m, const float *damp, const float *dm,
+                  const wave_points *src, const float *src_traces, const wave_points *rec, float *rec_traces,
+                  float *du_last, const wave_tuning *tuning, void *ws, size_t ws_bytes, void *stream_)
+{
+    try {
+        Dims d;
+        int rc = check_grid(g, &d);
+        if (rc) return rc;
+        if (!m || !damp || !dm || !ws) return WAVE_EINVAL;
+        if (check_points(src, true, src_traces) || check_points(rec, true, rec_traces)) return WAVE_EINVAL;
+        if ((uintptr_t)ws % kAlign) return WAVE_EINVAL;
+        const int nsrc = npts_of(src), nrec = npts_of(rec);
+        const int nt = g->nt;
+        const Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_BORN, nsrc, nrec, nt, 0);
+        if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
+        HostTable ts, tr;
+        if (build_table(d, g->h, src, false, &ts) || build_table(d, g->h, rec, true, &tr)) return WAVE_EINVAL;
+        cudaStream_t stream = (cudaStream_t)stream_;
+        const Stencil st = make_stencil(g);
+        // B, C and E of the background model; P = -dm / dt^2
+        if ((rc = prep_model(d, g, tuning, m, damp, L, stream))) return rc;
+        CK(wt::launch_pad(dm, d.nx, d.ny, d.nz, d.nzp, L.G, stream,
+                          (float)(-1.0 / ((double)g->dt * (double)g->dt))));
+        Plan plan;
+        if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, L.status, stream, &plan))) return rc;
+        if ((rc = upload_table(ts, L.inj, stream)) || (rc = upload_table(tr, L.rec, stream))) return rc;
+        for (int i = 0; i < 4; ++i) {
+            CK(cudaMemsetAsync(L.U[i], 0, sizeof(float) * d.npad, stream));
+            CK(cudaMemsetAsync(L.V[i], 0, sizeof(float) * d.npad, stream));
+        }
+        State bg, pt;
+        for (int i = 0; i < 4; ++i) {
+            bg.buf[i] = L.U[i];
+            pt.buf[i] = L.V[i];
+        }
+        // step n: the background sweep stores D^n = u^{n+1} - 2u^n + u^{n-1}
+        // (sources included), then the perturbation sweep takes C P D^n and
+        // records the receivers from du^{n+1}
+        Job bj;
+        bj.d = d;
+        bj.st = st;
+        bj.cB = L.cB;
+        bj.cC = L.cC;
+        bj.cE = L.cE;
+        bj.status = L.status;
+        bj.inj = L.inj.view();
+        bj.q = src_traces;
+        bj.nq = nsrc;
+        bj.dstore = L.store;
+        bj.d_base = 0;
+        bj.d_dir = 0;
+        bj.hinj = &ts;
+        bj.order = L.order;
+        bj.order_cap = L.order_cap;
+        Job pj;
+        pj.d = d;
+        pj.st = st;
+        pj.cB = L.cB;
+        pj.cC = L.cC;
+        pj.status = L.status;
+        pj.rec = L.rec.view();
+        pj.corner = L.corner;
+        pj.nslot = 8 * nrec;
+        pj.dload = L.store;
+        pj.l_base = 0;
+        pj.l_dir = 0;
+        pj.born = L.G;
+        pj.hrec = &tr;
+        pj.order = L.order;
+        pj.order_cap = L.order_cap;
+        if ((rc = prof_begin(tuning, stream))) return rc;
+        for (int n = 0; n < nt; ++n) {
+            bj.q_base = n;
+            if ((rc = run_steps(bj, bg, 1, plan, stream))) return rc;
+            pj.c_base = n;
+            if ((rc = run_steps(pj, pt, 1, plan, stream))) return rc;
+        }
+        if ((rc = prof_end(stream))) return rc;
+        if (nrec > 0) CK(wt::launch_gather(L.corner, L.rec.wts, nt, nrec, 1, rec_traces, stream));
+        if (du_last != nullptr) {
+            CK(wt::launch_unpad(pt.buf[pt.a], d.nx, d.ny, d.nz, d.nzp, 1.f, du_last, stream));
+            CK(wt::launch_unpad(pt.buf[pt.b], d.nx, d.ny, d.nz, d.nzp, 1.f, du_last + (size_t)d.nx * d.ny * d.nz,
+                                stream));
+        }
+        return WAVE_OK;
+    } catch (...) {
+        return WAVE_EINVAL;
+    }
+}
+
+int64_t wave_revolve_forward_steps(int32_t nt, int32_t nslots)
+{
+    if (nt < 1 || nslots < 0 || nslots > nt) return -1;
+    try {
+        long long n = 0;
+        for (const RevAction &x : revolve_schedule(nt, nslots)) {
+            if (x.kind == REV_ADVANCE) n += x.b - x.a;
+            if (x.kind == REV_YOUTURN) n += 1;
+        }
+        return n;
+    } catch (...) {
+        return -1;
+    }
+}
+
+int32_t wave_revolve_schedule(int32_t nt, int32_t nslots, int32_t *actions, int32_t cap)
+{
+    if (nt < 1 || nslots < 0 || nslots > nt || cap < 0 || (cap > 0 && actions == nullptr)) return WAVE_EINVAL;
+    try {
+        const std::vector<RevAction> v = revolve_schedule(nt, nslots);
+        for (int i = 0; i < (int)v.size() && i < cap; ++i) {
+            actions[3 * i] = v[i].kind;
+            actions[3 * i + 1] = v[i].a;
+            actions[3 * i + 2] = v[i].b;
+        }
+        return (int32_t)v.size();
+    } catch (...) {
+        return WAVE_EINVAL;
+    }
+}
+
+int32_t wave_grad_revolve(const wave_grid *g, const float *m, const float *damp, const wave_points *src,
+                          const float *src_traces, const wave_points *rec, const float *rec_resid,
+                          int32_t nslots, float *grad, const wave_tuning *tuning, void *ws, size_t ws_bytes,
+                          void *stream_)
+{
+    try {
+        Dims d;
+        int rc = check_grid(g, &d);
+        if (rc) return rc;
+        const int nt = g->nt;
+        if (!m || !damp || !ws || !grad || nslots < 0 || nslots > nt) return WAVE_EINVAL;
+        if (check_points(src, true, src_traces) || check_points(rec, true, rec_resid)) return WAVE_EINVAL;
+        if ((uintptr_t)ws % kAlign) return WAVE_EINVAL;
+        const int nsrc = npts_of(src), nrec = npts_of(rec);
+        const Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_REVOLVE, nsrc, nrec, nt, nslots);
+        if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
+        HostTable ts, tr;
+        if (build_table(d, g->h, src, false, &ts) || build_table(d, g->h, rec, false, &tr))
+            return WAVE_EINVAL;
+        const std::vector<RevAction> sched = revolve_schedule(nt, nslots);
+        cudaStream_t stream = (cudaStream_t)stream_;
+        const Stencil st = make_stencil(g);
+        if ((rc = prep_model(d, g, tuning, m, damp, L, stream))) return rc;
+        // forward advances on the forward plan, the reversed steps on the
+        // family the gradient modes run fastest on (as wave_grad)
+        Plan fplan, gplan;
+        if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, L.status, stream, &fplan))) return rc;
+        if ((rc = upload_table(ts, L.inj, stream)) || (rc = upload_table(tr, L.inj2, stream))) return rc;
+        if ((rc = grad_plan(d, g, fplan, st, L.cB, L.cC, L.cE, L.U, L.store, 1, L.G, L.status, L.inj.view(),
+                            src_traces, nsrc, L.inj2.view(), rec_resid, nrec, stream, &gplan)))
+            return rc;
+        CK(cudaMemsetAsync(L.G, 0, sizeof(float) * d.npad, stream));
+        for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.V[i], 0, sizeof(float) * d.npad, stream));
+        for (int i = 0; i < 2; ++i) CK(cudaMemsetAsync(L.U[i], 0, sizeof(float) * d.npad, stream));
+        State fw, adj;
+        for (int i = 0; i < 4; ++i) {
+            fw.buf[i] = L.U[i];
+            adj.buf[i] = L.V[i];
+        }
+        const size_t lvl = sizeof(float) * d.npad;
+        if ((rc = prof_begin(tuning, stream))) return rc;
+        for (const RevAction &x : sched) {
+            if (x.kind == REV_RESTORE) {
+                fw.a = 0;
+                fw.b = 1;
+                if (x.b < 0) {  // the zero state of step 0
+                    CK(cudaMemsetAsync(L.U[0], 0, lvl, stream));
+                    CK(cudaMemsetAsync(L.U[1], 0, lvl, stream));
+                } else {
+                    const float *sp = L.slots + (size_t)x.b * 2 * d.npad;
+                    CK(cudaMemcpyAsync(L.U[0], sp, lvl, cudaMemcpyDeviceToDevice, stream));
+                    CK(cudaMemcpyAsync(L.U[1], sp + d.npad, lvl, cudaMemcpyDeviceToDevice, stream));
+                }
+            } else if (x.kind == REV_TAKESHOT) {
+                float *sp = L.slots + (size_t)x.b * 2 * d.npad;
+                CK(cudaMemcpyAsync(sp, fw.buf[fw.a], lvl, cudaMemcpyDeviceToDevice, stream));
+                CK(cudaMemcpyAsync(sp + d.npad, fw.buf[fw.b], lvl, cudaMemcpyDeviceToDevice, stream));
+            } else if (x.kind == REV_ADVANCE) {
+                Job fj;
+                fj.d = d;
+                fj.st = st;
+                fj.cB = L.cB;
+                fj.cC = L.cC;
+                fj.status = L.status;
+                fj.inj = L.inj.view();
+                fj.q = src_traces;
+                fj.nq = nsrc;
+                fj.q_base = x.a;
+                fj.q_dir = 1;
+                fj.hinj = &ts;
+                fj.order = L.order;
+                fj.order_cap = L.order_cap;
+                if ((rc = run_steps(fj, fw, x.b - x.a, fplan, stream))) return rc;
+            } else {
+                // one recompute step from u^a storing D^a, then the adjoint
+                // step of time index a (nu^{a+1}, res^a, G += nu^{a+1} D^a)
+                Job rj;
+                rj.d = d;
+                rj.st = st;
+                rj.cB = L.cB;
+                rj.cC = L.cC;
+                rj.status = L.status;
+                rj.cE = L.cE;
+                rj.inj = L.inj.view();
+                rj.q = src_traces;
+                rj.nq = nsrc;
+                rj.q_base = x.a;
+                rj.q_dir = 1;
+                rj.dstore = L.store;
+                rj.d_base = 0;
+                rj.d_dir = 1;
+                rj.hinj = &ts;
+                rj.order = L.order;
+                rj.order_cap = L.order_cap;
+                if ((rc = run_steps(rj, fw, 1, gplan, stream))) return rc;
+                Job aj;
+                aj.d = d;
+                aj.st = st;
+                aj.cB = L.cB;
+                aj.cC = L.cC;
+                aj.status = L.status;
+                aj.inj = L.inj2.view();
+                aj.q = rec_resid;
+                aj.nq = nrec;
+                aj.q_base = x.a;
+                aj.q_dir = -1;
+                aj.dload = L.store;
+                aj.l_base = 0;
+                aj.l_dir = -1;
+                aj.gacc = L.G;
+                aj.hinj = &tr;
+                aj.order = L.order;
+                aj.order_cap = L.order_cap;
+                if ((rc = run_steps(aj, adj, 1, gplan, stream))) return rc;
+            }
         }
         if ((rc = prof_end(stream))) return rc;
         const float scale = (float)(-1.0 / ((double)g->dt * (double)g->dt));

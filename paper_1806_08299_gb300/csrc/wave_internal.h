@@ -112,8 +112,14 @@ int lockstep_group(const wave_grid *g, int n, const ShotSlot *slots, int ckpt_ev
 size_t lockstep_table_bytes(const wave_grid *g, int n, const wave_shot *shots, int ckpt_every);
 
 // Gradient-mode variants (XB = 1, 2) of radius r; radii without any return 0.
+int sweep_mode_variants_r1(const SweepVariant **out);
 int sweep_mode_variants_r2(const SweepVariant **out);
+int sweep_mode_variants_r3(const SweepVariant **out);
 int sweep_mode_variants_r4(const SweepVariant **out);
+int sweep_mode_variants_r5(const SweepVariant **out);
+int sweep_mode_variants_r6(const SweepVariant **out);
+int sweep_mode_variants_r7(const SweepVariant **out);
+int sweep_mode_variants_r8(const SweepVariant **out);
 
 // Auxiliary kernels (aux_kernels.cu).  Status codes are written to status[0]
 // with atomicMin, so the most severe (most negative) error wins.
@@ -123,7 +129,7 @@ cudaError_t launch_prep(const float *m, const float *damp, int nx, int ny, int n
 cudaError_t launch_heat_prep(const float *kappa, int nx, int ny, int nz, int nzp, float dt, float stab,
                              float *cB, float *cC, int *status, cudaStream_t s);
 cudaError_t launch_pad(const float *src, int nx, int ny, int nz, int nzp, float *dst,
-                       cudaStream_t s);
+                       cudaStream_t s, float scale = 1.f);
 cudaError_t launch_unpad(const float *src, int nx, int ny, int nz, int nzp, float scale,
                          float *dst, cudaStream_t s);
 cudaError_t launch_gather(const float *corner, const float *w, int rows, int npts, int row_dir,

@@ -21,7 +21,7 @@ WAVE_ECUDA = -3
 WAVE_ETIMEOUT = -4
 WAVE_ENOSPACE = -5
 WAVE_EUNSUPPORTED = -6
-WAVE_OP_FWD, WAVE_OP_ADJ, WAVE_OP_GRAD = 0, 1, 2
+WAVE_OP_FWD, WAVE_OP_ADJ, WAVE_OP_GRAD, WAVE_OP_REVOLVE, WAVE_OP_BORN = 0, 1, 2, 3, 4
 WAVE_ALLOW_UNSTABLE = 1
 WAVE_TIME_SWEEPS = 2
 WAVE_AUTOTUNE_SHAPE = 4
@@ -34,7 +34,8 @@ EXPORTED = ["wave_version", "wave_strerror", "wave_fd_coefficients", "wave_cfl_d
             "wave_status", "wave_describe_plan", "wave_sweep_stats", "wave_list_variants",
             "wave_autotune_stats", "wave_plan_bound",
             "wave_fwd_noalloc", "wave_measure_peaks", "wave_batch_workspace_bytes",
-            "wave_fwd_batched", "wave_grad_batched", "wave_describe_batch_plan", "wave_heat"]
+            "wave_fwd_batched", "wave_grad_batched", "wave_describe_batch_plan", "wave_heat",
+            "wave_grad_revolve", "wave_revolve_forward_steps", "wave_revolve_schedule", "wave_born"]
 
 
 class WaveError(RuntimeError):
@@ -138,6 +139,14 @@ def _lib():
         lib.wave_adj.restype = i32
         lib.wave_grad.argtypes = [gp, vp, vp, pp, vp, pp, vp, vp, i32, vp, tp, vp, ctypes.c_size_t, vp]
         lib.wave_grad.restype = i32
+        lib.wave_born.argtypes = [gp, vp, vp, vp, pp, vp, pp, vp, vp, tp, vp, ctypes.c_size_t, vp]
+        lib.wave_born.restype = i32
+        lib.wave_grad_revolve.argtypes = [gp, vp, vp, pp, vp, pp, vp, i32, vp, tp, vp, ctypes.c_size_t, vp]
+        lib.wave_grad_revolve.restype = i32
+        lib.wave_revolve_forward_steps.argtypes = [i32, i32]
+        lib.wave_revolve_forward_steps.restype = ctypes.c_int64
+        lib.wave_revolve_schedule.argtypes = [i32, i32, ctypes.POINTER(i32), i32]
+        lib.wave_revolve_schedule.restype = i32
         lib.wave_heat.argtypes = [gp, vp, vp, pp, vp, pp, vp, vp, tp, vp, ctypes.c_size_t, vp]
         lib.wave_heat.restype = i32
         lib.wave_status.argtypes = [vp, vp]
@@ -344,6 +353,75 @@ def grad(grid, m, damp, src_xyz, src_traces, rec_xyz, rec_resid, ckpt, ckpt_ever
     del sa, ra
     _check(code, "wave_grad")
     return g_out, ws
+
+
+def grad_revolve(grid, m, damp, src_xyz, src_traces, rec_xyz, rec_resid, nslots, *, tuning=None,
+                 workspace=None, stream=None):
+    """dJ/dm for the residual rec_resid = dJ/dd by binomial checkpointing
+    with nslots stored states (wave_grad_revolve); no forward call first."""
+    torch = _torch()
+    n = tuple(grid.n)
+    sp, sa = _points(src_xyz)
+    rp, ra = _points(rec_xyz)
+    dev = m.device
+    g_out = torch.empty(n, dtype=torch.float32, device=dev)
+    ws = _workspace(workspace_bytes(grid, WAVE_OP_REVOLVE, sp.npts, rp.npts, nslots), dev, workspace)
+    g = grid.c()
+    t = tuning.c() if tuning is not None else None
+    code = _lib().wave_grad_revolve(
+        ctypes.byref(g), _dev_ptr(m, "m", n), _dev_ptr(damp, "damp", n), ctypes.byref(sp),
+        _dev_ptr(src_traces, "src_traces", (grid.nt, sp.npts)) if sp.npts else None,
+        ctypes.byref(rp), _dev_ptr(rec_resid, "rec_resid", (grid.nt, rp.npts)) if rp.npts else None,
+        int(nslots), _dev_ptr(g_out, "grad"), ctypes.byref(t) if t is not None else None,
+        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
+    del sa, ra
+    _check(code, "wave_grad_revolve")
+    return g_out, ws
+
+
+def born(grid, m, damp, dm, src_xyz, src_traces, rec_xyz, *, tuning=None, want_du_last=False,
+         workspace=None, stream=None):
+    """Born (linearised) modelling, the derivative of the traces in m in the
+    direction dm (wave_born).  Returns (dd [nt][nrec], du_last [2,...] or
+    None, workspace)."""
+    torch = _torch()
+    n = tuple(grid.n)
+    sp, sa = _points(src_xyz)
+    rp, ra = _points(rec_xyz)
+    dev = m.device
+    dd = torch.empty((grid.nt, rp.npts), dtype=torch.float32, device=dev)
+    du = torch.empty((2,) + n, dtype=torch.float32, device=dev) if want_du_last else None
+    ws = _workspace(workspace_bytes(grid, WAVE_OP_BORN, sp.npts, rp.npts), dev, workspace)
+    g = grid.c()
+    t = tuning.c() if tuning is not None else None
+    code = _lib().wave_born(
+        ctypes.byref(g), _dev_ptr(m, "m", n), _dev_ptr(damp, "damp", n), _dev_ptr(dm, "dm", n),
+        ctypes.byref(sp), _dev_ptr(src_traces, "src_traces", (grid.nt, sp.npts)) if sp.npts else None,
+        ctypes.byref(rp), _dev_ptr(dd, "rec") if rp.npts else None,
+        _dev_ptr(du, "du_last") if du is not None else None,
+        ctypes.byref(t) if t is not None else None, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+        _stream(stream))
+    del sa, ra
+    _check(code, "wave_born")
+    return dd, du, ws
+
+
+def revolve_forward_steps(nt, nslots):
+    """Forward steps of the revolve schedule (-1: invalid arguments)."""
+    return int(_lib().wave_revolve_forward_steps(int(nt), int(nslots)))
+
+
+def revolve_schedule(nt, nslots):
+    """The revolve schedule as a list of (kind, a, b): 0 advance a->b,
+    1 takeshot (step a into slot b), 2 restore (step a from slot b, -1 = zero
+    state), 3 youturn at a."""
+    lib = _lib()
+    n = int(lib.wave_revolve_schedule(int(nt), int(nslots), None, 0))
+    if n < 0:
+        _check(n, "wave_revolve_schedule")
+    buf = (ctypes.c_int32 * (3 * max(n, 1)))()
+    _check(min(0, int(lib.wave_revolve_schedule(int(nt), int(nslots), buf, n))), "wave_revolve_schedule")
+    return [(buf[3 * i], buf[3 * i + 1], buf[3 * i + 2]) for i in range(n)]
 
 
 def heat(grid, u0, kappa=None, src_xyz=None, src_traces=None, rec_xyz=None, *, tuning=None,
