@@ -20,6 +20,11 @@ Functions and what pins them (see tests/test_oracle_*.py):
                        of a discrete Dirichlet sine mode (so 2), one step
                        of a quadratic exact away from the boundary, a
                        source on a node, linearity in u0 and f    (pinned)
+  heat_ab2             two-step Adams-Bashforth for the Laplace operator:
+                       exact amplification of a discrete Dirichlet sine
+                       mode (the closed form of the two-step recurrence),
+                       second-order convergence in dt to the exact decay,
+                       Euler start, linearity                     (pinned)
   born                 linearised modelling (the derivative of forward
                        in m): central finite differences of forward,
                        the dot identity with gradient, linearity    (pinned)
@@ -65,6 +70,8 @@ def _load():
         lib.oracle_heat.restype = i
         lib.oracle_born.argtypes = [ip, dp, d, i, i, dp, dp, dp, dp, i, dp, dp, i, dp, dp, dp]
         lib.oracle_born.restype = i
+        lib.oracle_heat_ab2.argtypes = [ip, dp, d, i, i, dp, dp, dp, i, dp, dp, i, dp, dp, dp]
+        lib.oracle_heat_ab2.restype = i
         _lib = lib
     return _lib
 
@@ -242,6 +249,27 @@ def heat(u0, h, dt, nt, space_order, kappa=None, src_xyz=None, src_q=None, rec_x
         nsrc, _p(sx), _p(q), nrec, _p(rx), _p(d), _p(u_last))
     if rc:
         raise RuntimeError("oracle_heat failed (%d)" % rc)
+    return d[:, :nrec], u_last
+
+
+def heat_ab2(u0, h, dt, nt, space_order, kappa=None, src_xyz=None, src_q=None, rec_xyz=None):
+    """Two-step Adams-Bashforth for u_t = kappa (lap u + f) with an Euler first
+    step (a time dependence of two levels; the multi-step methods of Sec. 6).
+    Returns (rec_d [nt][nrec], u^nt)."""
+    u0 = _arr(u0)
+    n = u0.shape
+    nsrc, sx = _pts(src_xyz)
+    nrec, rx = _pts(rec_xyz)
+    q = _arr(src_q, (nt, nsrc)) if nsrc else np.zeros((1,))
+    d = np.zeros((nt, max(nrec, 1)))
+    u_last = np.zeros(n)
+    c = _coeffs(space_order)
+    rc = _load().oracle_heat_ab2(
+        _ints(n), _p(_arr(h)), float(dt), int(nt), space_order // 2, _p(c),
+        _p(_arr(kappa, n)) if kappa is not None else None, _p(u0),
+        nsrc, _p(sx), _p(q), nrec, _p(rx), _p(d), _p(u_last))
+    if rc:
+        raise RuntimeError("oracle_heat_ab2 failed (%d)" % rc)
     return d[:, :nrec], u_last
 
 

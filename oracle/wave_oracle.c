@@ -669,3 +669,66 @@ int oracle_born(const int *n, const double *h, double dt, int nt, int r, const d
     recmap_free(&rm);
     return 0;
 }
+
+/* A multi-step (time dependence 2) form of the Laplace operator: the
+ * two-step Adams-Bashforth scheme for u_t = kappa (lap u + f), the kind of
+ * multi-step linear method the paper names for stencils with a larger time
+ * dependence (Sec. 6, "Time-tiling with larger time dependences"):
+ *   F^n     = L u^n + f^n,
+ *   u^{n+1} = u^n + dt kappa (3/2 F^n - 1/2 F^{n-1}),   n >= 1,
+ *   u^1     = u^0 + dt kappa F^0                          (Euler start),
+ * receivers reading u^{n+1} as oracle_heat.  kappa may be NULL (1). */
+int oracle_heat_ab2(const int *n, const double *h, double dt, int nt, int r, const double *c,
+                    const double *kappa, const double *u0,
+                    int nsrc, const double *src_xyz, const double *src_q,
+                    int nrec, const double *rec_xyz, double *rec_d, double *u_last)
+{
+    long N = npts(n);
+    srcmap_t sm;
+    recmap_t rm;
+    if (srcmap_build(&sm, n, h, nsrc, src_xyz) || recmap_build(&rm, n, h, nrec, rec_xyz)) return -1;
+    double *u = (double *)calloc(N, sizeof(double));
+    double *up = (double *)calloc(N, sizeof(double));
+    double *F = (double *)calloc(N, sizeof(double));
+    double *Fm = (double *)calloc(N, sizeof(double));
+    double *corners = (double *)calloc((size_t)nt * 8 * (nrec > 0 ? nrec : 1), sizeof(double));
+    if (!u || !up || !F || !Fm || !corners) return -1;
+    if (u0) memcpy(u, u0, sizeof(double) * N);
+    for (int step = 0; step < nt; step++) {
+#pragma omp parallel for schedule(static)
+        for (long x = 0; x < n[0]; x++)
+            for (long y = 0; y < n[1]; y++)
+                for (long z = 0; z < n[2]; z++) {
+                    long p = at(n, x, y, z);
+                    F[p] = lap_at(n, h, r, c, 0, u, x, y, z) + src_term(&sm, src_q, step, p);
+                }
+#pragma omp parallel for schedule(static)
+        for (long p = 0; p < N; p++) {
+            double k = kappa ? kappa[p] : 1.0;
+            double rate = step == 0 ? F[p] : 1.5 * F[p] - 0.5 * Fm[p];
+            up[p] = u[p] + dt * k * rate;
+        }
+        for (long x = 0; x < n[0]; x++)
+            for (long y = 0; y < n[1]; y++)
+                for (long z = 0; z < n[2]; z++) {
+                    long p = at(n, x, y, z);
+                    rec_record(&rm, corners, step, p, up[p]);
+                }
+        double *t = u;
+        u = up;
+        up = t;
+        t = Fm;
+        Fm = F;
+        F = t;
+    }
+    if (nrec > 0 && rec_d) rec_finish(&rm, corners, nt, rec_d);
+    if (u_last) memcpy(u_last, u, sizeof(double) * N);
+    free(u);
+    free(up);
+    free(F);
+    free(Fm);
+    free(corners);
+    srcmap_free(&sm);
+    recmap_free(&rm);
+    return 0;
+}
