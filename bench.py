@@ -307,6 +307,15 @@ def _spread(ms_list, pts):
             "max_gpts": pts / (ms_sorted[0] / 1e3) / 1e9, "median_gpts": pts / (med / 1e3) / 1e9}
 
 
+def run_survey_only(args):
+    """The survey section alone (one GPU), for profiling its batched kernels."""
+    import torch
+    from paper_1806_08299_gb300 import inputs, wave
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    print(json.dumps({"fwi_survey": _fwi_survey(dev, inputs, wave, args)}))
+
+
 def run_ours(args):
     import torch
     from paper_1806_08299_gb300 import inputs, wave
@@ -589,7 +598,10 @@ def _fwi_survey(dev, inputs, wave, args):
                         % (len(shots), sv.nt, k, conc),
             "forward_kernel": kname(plan_f),
             "gradient_forward_kernel": kname(plan_g),
-            "gradient_recompute_adjoint_kernel": "shared-warp batched kernel, T=1",
+            "gradient_recompute_adjoint_kernel": (
+                "per shot" if plan_g is None else "%s T=%d" % (
+                    "staged" if plan_g["grad_kernel"] == wave.WAVE_KERNEL_STAGED else "shared-warp",
+                    plan_g["grad_time_tile"])),
             "status": wave.status(ws_g),
             "gpts_equiv": 4 * pts * sv.nt / (ms / 1e3) / 1e9}
 
@@ -659,7 +671,11 @@ def _laplace_sweep(dev, inputs, wave, args):
     (every compiled depth T >= 2, shapes autotuned), GPts/s of the sweeps
     (best of three calls; call_gpts: whole calls, set-up included).  The sweep
     is the wave sweep with B = 0, so it still reads level n-1 and B (20 B per
-    point-update where the operator needs 12)."""
+    point-update where the operator needs 12).  adams_bashforth2: the same
+    operator by the two-step Adams-Bashforth scheme (a time dependence of two
+    levels, Sec. 6), untiled (20 B per point-update) and at depth 2 (10 B),
+    sweep time of the call's launches (its first step is an untiled Euler
+    step)."""
     import torch
     n = (args.laplace_n,) * 3
     nt = 16
@@ -707,6 +723,28 @@ def _laplace_sweep(dev, inputs, wave, args):
         row["time_tiled"] = max(tiled, key=lambda r: r["gpts"]) if tiled else None
         row["tiled_over_untiled"] = (row["time_tiled"]["gpts"] / row["untiled"]["gpts"]
                                      if tiled else None)
+
+        # the two-step Adams-Bashforth form (time dependence 2): untiled and
+        # depth 2 (where compiled), dt within its limit dt |L| <= 1
+        grid2 = wave.Grid(n, h, float(np.float32(0.4 / lam)), nt, so)
+
+        def ab2_at(T):
+            t = wave.Tuning(time_tile=T, flags=wave.WAVE_TIME_SWEEPS)
+            wave.heat_ab2(grid2, tu, None, None, None, None, tuning=t, workspace=ws)
+            best, launches = float("inf"), 0
+            for _ in range(3):
+                wave.heat_ab2(grid2, tu, None, None, None, None, tuning=t, workspace=ws)
+                st = wave.sweep_stats()
+                best, launches = min(best, st[0]), st[1]
+            return {"gpts": pts / (best / 1e3) / 1e9, "launches_per_call": launches,
+                    "dram_bytes_per_point": 20.0 if T == 1 else 10.0}
+
+        ab1 = ab2_at(1)
+        ab = {"untiled": ab1}
+        if so in (2, 4, 8):
+            ab["time_tiled"] = ab2_at(2)
+            ab["tiled_over_untiled"] = ab["time_tiled"]["gpts"] / ab1["gpts"]
+        row["adams_bashforth2"] = ab
         out["so%d" % so] = row
         del ws
         torch.cuda.empty_cache()
@@ -737,9 +775,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per sweep launch, when captured for this kernel")
+    ap.add_argument("--only-survey", action="store_true",
+                    help="run only the batched survey (FWI gradient step over c5 shots) and print its entry")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only_survey:
+        run_survey_only(args)
     else:
         run_ours(args)
 

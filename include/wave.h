@@ -276,6 +276,25 @@ int32_t wave_heat(const wave_grid *g, const float *kappa, const float *u0,
                   const wave_points *rec, float *rec_traces, float *u_out,
                   const wave_tuning *tuning, void *ws, size_t ws_bytes, void *stream);
 
+/* A multi-step form of the same operator (a time dependence of two levels,
+ * the larger time dependences the paper names for further work: multi-step
+ * linear methods such as Adams-Bashforth, Sec. 6): the two-step
+ * Adams-Bashforth scheme for u_t = kappa (lap u + f),
+ *   F^n = L u^n + f^n,  u^{n+1} = u^n + dt kappa (3/2 F^n - 1/2 F^{n-1}),
+ * with an Euler first step u^1 = u^0 + dt kappa F^0.  The sweep carries the
+ * rate F in place of the leapfrog's level n-1, so an untiled step moves 20 B
+ * per point (read u^n, F^{n-1}, C; write u^{n+1}, F^n) and a depth-2 tile 10
+ * (the new level and rate only; level n+1 stays on chip), against 12 for a
+ * depth-2 leapfrog tile.  Arguments as wave_heat; depth 2 runs when compiled
+ * for the order (so 2, 4, 8), no receivers are given (a depth-2 launch does
+ * not store the level between its steps) and tuning->time_tile is not 1.
+ * Stability: dt kappa |L| <= 1, else WAVE_EUNSTABLE through the status word
+ * (unless WAVE_ALLOW_UNSTABLE).  Workspace: WAVE_OP_FWD. */
+int32_t wave_heat_ab2(const wave_grid *g, const float *kappa, const float *u0,
+                      const wave_points *src, const float *src_traces,
+                      const wave_points *rec, float *rec_traces, float *u_out,
+                      const wave_tuning *tuning, void *ws, size_t ws_bytes, void *stream);
+
 /* Wait for `stream`, then read the device status word that kernels of the
  * last call using workspace `ws` may have set.  Returns WAVE_OK,
  * WAVE_ETIMEOUT or WAVE_ECUDA. */
@@ -369,9 +388,11 @@ size_t wave_batch_workspace_bytes(const wave_grid *g, int32_t nshots, const wave
  * Any other plan runs wave_fwd per shot on library-owned streams that wait
  * for `stream` at the start and that `stream` waits for at the end.  tuning
  * applies to every shot; the per-shape autotuning flags are ignored.  The
- * gradient's recompute and adjoint phases run on the shared-warp batched
- * kernel.  wave_status(ws, stream) reports the most severe device status of
- * all shots.  Results equal wave_fwd on each window, bit for bit, whichever
+ * gradient's recompute and adjoint phases run on a batched
+ * stage-specialised gradient shape (the first of the named depth, or the
+ * fastest timed one) or on the shared-warp batched kernel.
+ * wave_status(ws, stream) reports the most severe device status of all
+ * shots.  Results equal wave_fwd on each window, bit for bit, whichever
  * kernel runs. */
 int32_t wave_fwd_batched(const wave_grid *g, int32_t nshots, const wave_shot *shots,
                          const float *m, const float *damp, const float *src_traces,
@@ -392,13 +413,15 @@ int32_t wave_grad_batched(const wave_grid *g, int32_t nshots, const wave_shot *s
                           int32_t concurrency, const wave_tuning *tuning, void *ws,
                           size_t ws_bytes, void *stream);
 
-/* The forward kernel the first group of a batched call with these
- * arguments runs: out[0..7] as wave_describe_plan (time_tile, tile_y, 0,
- * tile_z, vec, prefetch, kernel family, rows), out[8] = 1 for lockstep
- * groups.  All nine are 0 when the plan runs shot by shot, and out[0] is 0
- * while an autotuned group (time_tile 0) has not been timed yet on the
- * current device.  out: HOST, 9 ints.  Returns WAVE_OK, WAVE_EINVAL or
- * WAVE_ECUDA.  No device work is queued. */
+/* The kernels the first group of a batched call with these arguments runs:
+ * out[0..7] the forward phases' kernel as wave_describe_plan (time_tile,
+ * tile_y, 0, tile_z, vec, prefetch, kernel family, rows), out[8] = 1 for
+ * lockstep groups, and for the gradient (ckpt_every >= 1) the family and
+ * depth of the recompute and adjoint phases' kernel in out[9] and out[10].
+ * All are 0 when the plan runs shot by shot, and out[0] is 0 while an
+ * autotuned group (time_tile 0) has not been timed yet on the current
+ * device.  out: HOST, 11 ints.  Returns WAVE_OK, WAVE_EINVAL or WAVE_ECUDA.
+ * No device work is queued. */
 int32_t wave_describe_batch_plan(const wave_grid *g, int32_t nshots, const wave_shot *shots,
                                  int32_t ckpt_every, int32_t concurrency, const wave_tuning *tuning,
                                  int32_t *out);

@@ -115,6 +115,7 @@ struct SweepArgs {
     long long l_row0;
     int l_dir;
     float *gacc;
+    float ab1, ab0;          // two-step Adams-Bashforth weights of stage 1 (3/2, -1/2; 1, 0 to start)
     int withhold;            // test hook: the producer issues nothing (waits run out)
     int chunk;               // x planes per block
     int tiles_z, tiles_y;    // column tiles of the grid

@@ -65,6 +65,12 @@ struct TMaps {
     //   MODE 2: T = 1: x0 = D row l_row0, x1 = G;  T = 2: y0, y1 = D rows l_row0,
     //           l_row0 + l_dir, y2 = G
     //   MODE 3: T = 1: x0 = D row l_row0, x1 = P (Born source coefficient)
+    //   MODE 4 (two-step Adams-Bashforth heat): um is the rate F^{n-1}; B and
+    //           the stage-2 boxes u2, B2 are not loaded
+    // The D maps cover the whole store [rows][nx][ny][nzp] as one tensor of
+    // rows * nx planes: row r, plane x is plane r * nx + x.  Every D box lies
+    // in [X0, X1) in x, so none reaches into a neighbouring row, and one map
+    // serves every step (the batched kernel reads it from a per-shot table).
     CUtensorMap x0, x1, y0, y1, y2;
 };
 
@@ -104,29 +110,34 @@ struct TShape {
     static constexpr int DA = P + 1;                      // ring A slots
     static constexpr int DB = T == 2 ? P + 1 : 0;         // ring B slots
     static constexpr int D1 = T == 2 ? R + 3 : 0;         // ring 1 planes
+    static constexpr bool AB = MODE == 4;                 // two-step Adams-Bashforth (heat)
     static constexpr unsigned CBOX = WC * HC * 4, FBOX = W1 * H1 * 4, SBOX = BZ * BY * 4;
     static constexpr unsigned CBOXP = (CBOX + 127) / 128 * 128;
     static constexpr unsigned FBOXP = (FBOX + 127) / 128 * 128;
     static constexpr unsigned SBOXP = (SBOX + 127) / 128 * 128;
     // extra boxes of the gradient modes per ring-A / ring-B slot
-    static constexpr int XA = MODE == 0 ? 0 : (T == 1 ? (MODE == 3 ? 2 : MODE) : (MODE == 1 ? 1 : 0));
+    static constexpr int XA =
+        (MODE == 0 || MODE == 4) ? 0 : (T == 1 ? (MODE == 3 ? 2 : MODE) : (MODE == 1 ? 1 : 0));
     static constexpr int XBB = T == 2 ? (MODE == 1 ? 1 : (MODE == 2 ? 3 : 0)) : 0;
     // ring A slot: centre box, level n (queue feed), level n-1, B, C, [x0, x1]
-    static constexpr unsigned A_C = 0, A_F = CBOXP, A_UM = A_F + FBOXP, A_B = A_UM + FBOXP,
+    // (AB: the rate F^{n-1} in the level n-1 box, no B box)
+    static constexpr unsigned A_C = 0, A_F = CBOXP, A_UM = A_F + FBOXP, A_B = AB ? A_UM : A_UM + FBOXP,
                               A_CC = A_B + FBOXP, A_X0 = A_CC + FBOXP, A_X1 = A_X0 + FBOXP,
                               ASLOT = A_X0 + XA * FBOXP;
-    // ring B slot: level n, B, C over the output tile, [y0, y1, y2]
-    static constexpr unsigned B_UM = 0, B_B = SBOXP, B_C = 2 * SBOXP, B_Y0 = 3 * SBOXP,
-                              B_Y1 = 4 * SBOXP, B_Y2 = 5 * SBOXP, BSLOT = (3 + XBB) * SBOXP;
+    // ring B slot: level n, B, C over the output tile, [y0, y1, y2] (AB: C only)
+    static constexpr unsigned B_UM = 0, B_B = AB ? 0 : SBOXP, B_C = AB ? 0 : 2 * SBOXP, B_Y0 = 3 * SBOXP,
+                              B_Y1 = 4 * SBOXP, B_Y2 = 5 * SBOXP, BSLOT = AB ? SBOXP : (3 + XBB) * SBOXP;
+    // ring 1 slot: level n+1 over the stage-1 region (AB: then the rate F^n)
+    static constexpr unsigned R1SLOT = (AB ? 2 : 1) * FBOXP;
     static constexpr size_t OFF_B = (size_t)DA * ASLOT;
     static constexpr size_t OFF_1 = OFF_B + (size_t)DB * BSLOT;
-    static constexpr size_t OFF_BAR = OFF_1 + (size_t)D1 * FBOXP;
+    static constexpr size_t OFF_BAR = OFF_1 + (size_t)D1 * R1SLOT;
     static constexpr size_t OFF_P = OFF_BAR + 8 * (2 * DA + 2 * DB + 2 * D1) + 16;
     static constexpr size_t SMEM = OFF_P;                 // + per-plane sparse slices
     static size_t smem_bytes(int chunk) { return OFF_P + sweep_table_bytes(chunk, RT) + 16; }
-    static constexpr unsigned TXA = CBOX + (4 + XA) * FBOX;  // bytes of a ring-A slot from iteration 2R on
+    static constexpr unsigned TXA = CBOX + ((AB ? 3 : 4) + XA) * FBOX;  // bytes of a ring-A slot from iteration 2R on
     static constexpr unsigned TXF = FBOX;                    // before (queue fill only)
-    static constexpr unsigned TXB = (3 + XBB) * SBOX;
+    static constexpr unsigned TXB = (AB ? 1 : 3 + XBB) * SBOX;
     static_assert(T == 1 || T == 2, "stage-specialised sweep: T = 1 or 2");
     static_assert(V == 4, "four z points per thread (two pairs)");
     static_assert(VY == 1 || VY == 2, "one or two rows per thread");
@@ -144,8 +155,9 @@ struct TShape {
                               (long long)CREG * (N1 + N2) + (long long)PREG * NP <= (long long)LREG * NTB &&
                               ((N1 + N2) / 128 * CREG + PREG) * 32 <= 16384),
                   "register split does not fit");
-    static_assert(MODE >= 0 && MODE <= 3 && (MODE != 3 || T == 1),
-                  "mode: 0 plain, 1 second differences, 2 imaging condition, 3 Born source (T = 1)");
+    static_assert(MODE >= 0 && MODE <= 4 && (MODE != 3 || T == 1),
+                  "mode: 0 plain, 1 second differences, 2 imaging condition, 3 Born source (T = 1), "
+                  "4 two-step Adams-Bashforth");
 };
 
 // Level n+1 of a thread's VY x V points (VY rows, V/2 pairs each) from the
@@ -159,7 +171,7 @@ struct TShape {
 // DD: also the second difference u^{n+1} - 2u^n + u^{n-1} = E (u^n - u^{n-1})
 // + C L u^n into dd (before sources), from the caller's e = E, as sweep_block's
 // second-difference mode computes it.
-template <int R, int V, int VY, int PC, int PK, bool DD = false>
+template <int R, int V, int VY, int PC, int PK, bool DD = false, bool AB = false>
 __device__ __forceinline__ void tstage_update(float2 (&un)[VY][V / 2], float2 (&cC)[VY][V / 2],
                                               const float2 (&q)[2 * R + 1][VY][V / 2], const float *pc,
                                               const float *pum, const float *pB, const float *pCc,
@@ -239,6 +251,20 @@ __device__ __forceinline__ void tstage_update(float2 (&un)[VY][V / 2], float2 (&
             }
         }
     }
+    if constexpr (AB) {
+        // the rate's Laplacian only: un = L u^n (the caller adds f and forms
+        // the two-step update)
+#pragma unroll
+        for (int v = 0; v < VY; ++v) {
+            ld2<V>(cC[v], pCc + v * PK);
+#pragma unroll
+            for (int j = 0; j < V2; ++j) {
+                if constexpr (R > 2) lap[v][j] = __fadd2_rn(__fadd2_rn(lap[v][j], ly[v][j]), lz[v][j]);
+                un[v][j] = lap[v][j];
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int v = 0; v < VY; ++v) {
         float2 cB[V2], up[V2];
@@ -254,6 +280,26 @@ __device__ __forceinline__ void tstage_update(float2 (&un)[VY][V / 2], float2 (&
             if constexpr (DD) dd[v][j] = __ffma2_rn(cC[v][j], lap[v][j], __fmul2_rn(e[v][j], du));
         }
     }
+}
+
+// The two-step Adams-Bashforth update of a thread's points from the rate
+// F^n (in un on entry, sources included), F^{n-1} (fm) and the level u^n
+// (the queue centre u0): u^{n+1} = u^n + C (w1 F^n + w0 F^{n-1}).  On return
+// un holds u^{n+1} and fn the rate F^n.
+template <int V, int VY>
+__device__ __forceinline__ void ab2_finish(float2 (&un)[VY][V / 2], float2 (&fn)[VY][V / 2],
+                                           const float2 (&cC)[VY][V / 2], const float2 (&fm)[VY][V / 2],
+                                           const float2 (&u0)[VY][V / 2], float w1, float w0)
+{
+    const float2 a1 = make_float2(w1, w1), a0 = make_float2(w0, w0);
+#pragma unroll
+    for (int v = 0; v < VY; ++v)
+#pragma unroll
+        for (int j = 0; j < V / 2; ++j) {
+            fn[v][j] = un[v][j];
+            const float2 rate = __ffma2_rn(a1, fn[v][j], __fmul2_rn(a0, fm[v][j]));
+            un[v][j] = __ffma2_rn(cC[v][j], rate, u0[v][j]);
+        }
 }
 
 // Point sources of plane cs on a thread's VY x V points at global row gy
@@ -362,7 +408,13 @@ __device__ __forceinline__ void tstage_abort(volatile int *abort_flag, int *stat
 // centre being level n+1 of its own points.  MODE 3 (the perturbation sweep
 // of Born modelling, T = 1): the new level takes the dense source C P D of
 // the background's second difference D (row l_row0 of dload) with the
-// per-point coefficient P = -dm / dt^2, as u^{n+1} + C (P D).
+// per-point coefficient P = -dm / dt^2, as u^{n+1} + C (P D).  MODE 4 (the
+// two-step Adams-Bashforth heat operator): level n-1 is replaced by the rate
+// F^{n-1} = L u^{n-1} + f^{n-1}; each stage forms F = L u + f and
+// u + C (3/2 F - 1/2 F_prev) (stage 1 with the launch's weights ab1, ab0,
+// which start the scheme with an Euler step), hands F to stage 2 beside its
+// level through ring 1, and the last stage stores the new level (out_hi)
+// and its rate (out_lo).
 template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB, int MODE>
 __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &st, const TMaps &mp,
                                              const int blk)
@@ -483,6 +535,10 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
         if constexpr (S::RSPLIT) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(S::PREG));
         const int lane = tid - (S::N1 + S::N2);  // lanes 0 and 1 of the first producer warp work
         if (a.withhold) return;
+        // plane offsets of this launch's D rows in the store tensor (MODE 2, 3)
+        const int xrow = (T == 1 && MODE >= 2) ? (int)(a.l_row0 * a.nx) : 0;
+        const int yrow0 = (T == 2 && MODE == 2) ? (int)(a.l_row0 * a.nx) : 0;
+        const int yrow1 = (T == 2 && MODE == 2) ? (int)((a.l_row0 + a.l_dir) * a.nx) : 0;
         if (lane == 0) {
             // ring A: the stage-1 inputs of iteration i
             int i = 0, s = 0, r = 0;
@@ -500,9 +556,9 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                 if (full_slot) {
                     tma_load_3d(sl + S::A_C, &mp.uc, gz0 - S::RP, gy0 - R, c0 - R, fullA + s);
                     tma_load_3d(sl + S::A_UM, &mp.um, gz0, gy0, c0 - R, fullA + s);
-                    tma_load_3d(sl + S::A_B, &mp.B, gz0, gy0, c0 - R, fullA + s);
+                    if constexpr (!S::AB) tma_load_3d(sl + S::A_B, &mp.B, gz0, gy0, c0 - R, fullA + s);
                     tma_load_3d(sl + S::A_CC, &mp.C, gz0, gy0, c0 - R, fullA + s);
-                    if constexpr (S::XA >= 1) tma_load_3d(sl + S::A_X0, &mp.x0, gz0, gy0, c0 - R, fullA + s);
+                    if constexpr (S::XA >= 1) tma_load_3d(sl + S::A_X0, &mp.x0, gz0, gy0, c0 - R + xrow, fullA + s);
                     if constexpr (S::XA >= 2) tma_load_3d(sl + S::A_X1, &mp.x1, gz0, gy0, c0 - R, fullA + s);
                 }
                 // bring the first-touch inputs of iteration i + LP into L2, so
@@ -513,9 +569,9 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                     tma_prefetch_3d(&mp.uf, gz0, gy0, c0 + S::LP);
                     if (i + S::LP >= 2 * R) {
                         tma_prefetch_3d(&mp.um, gz0, gy0, c0 + S::LP - R);
-                        tma_prefetch_3d(&mp.B, gz0, gy0, c0 + S::LP - R);
+                        if constexpr (!S::AB) tma_prefetch_3d(&mp.B, gz0, gy0, c0 + S::LP - R);
                         tma_prefetch_3d(&mp.C, gz0, gy0, c0 + S::LP - R);
-                        if constexpr (S::XA >= 1) tma_prefetch_3d(&mp.x0, gz0, gy0, c0 + S::LP - R);
+                        if constexpr (S::XA >= 1) tma_prefetch_3d(&mp.x0, gz0, gy0, c0 + S::LP - R + xrow);
                         if constexpr (S::XA >= 2) tma_prefetch_3d(&mp.x1, gz0, gy0, c0 + S::LP - R);
                     }
                 }
@@ -536,18 +592,20 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                 }
                 unsigned char *sl = ringB + (size_t)s * S::BSLOT;
                 mbar_expect_tx(fullB + s, S::TXB);
-                tma_load_3d(sl + S::B_UM, &mp.u2, tz0, ty0, X0 + j, fullB + s);
-                tma_load_3d(sl + S::B_B, &mp.B2, tz0, ty0, X0 + j, fullB + s);
+                if constexpr (!S::AB) {
+                    tma_load_3d(sl + S::B_UM, &mp.u2, tz0, ty0, X0 + j, fullB + s);
+                    tma_load_3d(sl + S::B_B, &mp.B2, tz0, ty0, X0 + j, fullB + s);
+                }
                 tma_load_3d(sl + S::B_C, &mp.C2, tz0, ty0, X0 + j, fullB + s);
-                if constexpr (S::XBB >= 1) tma_load_3d(sl + S::B_Y0, &mp.y0, tz0, ty0, X0 + j, fullB + s);
-                if constexpr (S::XBB >= 2) tma_load_3d(sl + S::B_Y1, &mp.y1, tz0, ty0, X0 + j, fullB + s);
+                if constexpr (S::XBB >= 1) tma_load_3d(sl + S::B_Y0, &mp.y0, tz0, ty0, X0 + j + yrow0, fullB + s);
+                if constexpr (S::XBB >= 2) tma_load_3d(sl + S::B_Y1, &mp.y1, tz0, ty0, X0 + j + yrow1, fullB + s);
                 if constexpr (S::XBB >= 3) tma_load_3d(sl + S::B_Y2, &mp.y2, tz0, ty0, X0 + j, fullB + s);
                 // the gradient-mode arrays are first read here: into L2 ahead
                 if constexpr (S::XBB >= 1) {
                     constexpr int LB = S::DB + 3;
                     if (j + LB < nj) {
-                        tma_prefetch_3d(&mp.y0, tz0, ty0, X0 + j + LB);
-                        if constexpr (S::XBB >= 2) tma_prefetch_3d(&mp.y1, tz0, ty0, X0 + j + LB);
+                        tma_prefetch_3d(&mp.y0, tz0, ty0, X0 + j + LB + yrow0);
+                        if constexpr (S::XBB >= 2) tma_prefetch_3d(&mp.y1, tz0, ty0, X0 + j + LB + yrow1);
                         if constexpr (S::XBB >= 3) tma_prefetch_3d(&mp.y2, tz0, ty0, X0 + j + LB);
                     }
                 }
@@ -578,11 +636,13 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
             for (int v = 0; v < VY; ++v)
 #pragma unroll
                 for (int j = 0; j < V2; ++j) q[k][v][j] = make_float2(0.f, 0.f);
-        // T = 1: stage 1 writes level n+1 of its own points (planes [X0, X1))
-        float *outp = nullptr;
+        // T = 1: stage 1 writes level n+1 of its own points (planes [X0, X1)),
+        // and with AB the rate F^n beside it
+        float *outp = nullptr, *outf = nullptr;
         bool sok[VY];
         if constexpr (T == 1) {
             outp = a.out_hi + ((long long)X0 * a.sx + (long long)gy * a.nz + gz);
+            if constexpr (S::AB) outf = a.out_lo + ((long long)X0 * a.sx + (long long)gy * a.nz + gz);
 #pragma unroll
             for (int v = 0; v < VY; ++v) sok[v] = act && gy + v < a.ny && gz < a.nz;
         }
@@ -627,12 +687,29 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                         ld2<V>(ex[v], sl + S::A_X0 / 4 + offF + v * S::W1);
                     }
                 }
-                tstage_update<R, V, VY, S::WC, S::W1, DD1>(un, cC, q, sl + S::A_C / 4 + offC,
-                                                           sl + S::A_UM / 4 + offF, sl + S::A_B / 4 + offF,
-                                                           sl + S::A_CC / 4 + offF, st, ex, dd);
-                if (any_inj && finj[cs - pbase])
+                tstage_update<R, V, VY, S::WC, S::W1, DD1, S::AB>(un, cC, q, sl + S::A_C / 4 + offC,
+                                                                  sl + S::A_UM / 4 + offF, sl + S::A_B / 4 + offF,
+                                                                  sl + S::A_CC / 4 + offF, st, ex, dd);
+                float2 fn[VY][V2];  // AB: the rate F^n
+                if constexpr (S::AB) {
+                    // F^n = L u^n + f^n, then u^{n+1} = u^n + C (w1 F^n + w0 F^{n-1})
+                    if (any_inj && finj[cs - pbase]) {
+                        float2 one[VY][V2];
+#pragma unroll
+                        for (int v = 0; v < VY; ++v)
+#pragma unroll
+                            for (int j = 0; j < V2; ++j) one[v][j] = make_float2(1.f, 1.f);
+                        tstage_inject<V, VY>(un, one, a, pinj[cs - pbase], pinj[cs - pbase + 1], gy, gz, a.q_row0,
+                                             wy0, wy1, wz0, wz1);
+                    }
+                    float2 fm[VY][V2];
+#pragma unroll
+                    for (int v = 0; v < VY; ++v) ld2<V>(fm[v], sl + S::A_UM / 4 + offF + v * S::W1);
+                    ab2_finish<V, VY>(un, fn, cC, fm, q[R], a.ab1, a.ab0);
+                } else if (any_inj && finj[cs - pbase]) {
                     tstage_inject<V, VY, DD1>(un, cC, a, pinj[cs - pbase], pinj[cs - pbase + 1], gy, gz,
                                               a.q_row0, wy0, wy1, wz0, wz1, dd);
+                }
                 if constexpr (MODE == 1) {
 #pragma unroll
                     for (int v = 0; v < VY; ++v)
@@ -662,8 +739,12 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                 if constexpr (T == 1) {
 #pragma unroll
                     for (int v = 0; v < VY; ++v)
-                        if (sok[v]) st2<V>(outp + (long long)v * a.nz, un[v]);
+                        if (sok[v]) {
+                            st2<V>(outp + (long long)v * a.nz, un[v]);
+                            if constexpr (S::AB) st2<V>(outf + (long long)v * a.nz, fn[v]);
+                        }
                     outp += a.sx;
+                    if constexpr (S::AB) outf += a.sx;
                 } else {
                     // hand the plane to stage 2 through ring 1
                     if (r1 > 0 && !__all_sync(FULL, mbar_wait_bounded(empty1 + s1, (uint32_t)((r1 - 1) & 1)))) {
@@ -672,8 +753,11 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                     }
                     if (act) {
 #pragma unroll
-                        for (int v = 0; v < VY; ++v)
-                            st2<V>(ring1 + (size_t)s1 * (S::FBOXP / 4) + offF + v * S::W1, un[v]);
+                        for (int v = 0; v < VY; ++v) {
+                            st2<V>(ring1 + (size_t)s1 * (S::R1SLOT / 4) + offF + v * S::W1, un[v]);
+                            if constexpr (S::AB)
+                                st2<V>(ring1 + (size_t)s1 * (S::R1SLOT / 4) + S::FBOXP / 4 + offF + v * S::W1, fn[v]);
+                        }
                     }
                     __syncwarp();
                     if (lane0) mbar_arrive(full1 + s1);
@@ -721,7 +805,7 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                     if (lane0) tstage_abort(abort_flag, a.status);
                     break;
                 }
-                const float *rp = ring1 + (size_t)s1 * (S::FBOXP / 4);
+                const float *rp = ring1 + (size_t)s1 * (S::R1SLOT / 4);
 #pragma unroll
                 for (int k = 0; k < QL - 1; ++k)
 #pragma unroll
@@ -752,18 +836,42 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                             }
                         }
                     }
-                    tstage_update<R, V, VY, S::W1, BZ, DD1>(un, cC, q, ring1 + (size_t)sc * (S::FBOXP / 4) + off1,
-                                                            bp + S::B_UM / 4 + offS, bp + S::B_B / 4 + offS,
-                                                            bp + S::B_C / 4 + offS, st, ex, dd);
+                    tstage_update<R, V, VY, S::W1, BZ, DD1, S::AB>(un, cC, q,
+                                                                   ring1 + (size_t)sc * (S::R1SLOT / 4) + off1,
+                                                                   bp + S::B_UM / 4 + offS, bp + S::B_B / 4 + offS,
+                                                                   bp + S::B_C / 4 + offS, st, ex, dd);
                     const int cs = c00 + i - 2 * R;  // plane of level n+2, in [X0, X1)
-                    if (any_inj && finj[cs - pbase])
+                    float2 fn[VY][V2];  // AB: the rate F^{n+1}
+                    if constexpr (S::AB) {
+                        if (any_inj && finj[cs - pbase]) {
+                            float2 one[VY][V2];
+#pragma unroll
+                            for (int v = 0; v < VY; ++v)
+#pragma unroll
+                                for (int j = 0; j < V2; ++j) one[v][j] = make_float2(1.f, 1.f);
+                            tstage_inject<V, VY>(un, one, a, pinj[cs - pbase], pinj[cs - pbase + 1], gy, gz,
+                                                 a.q_row0 + a.q_dir, wy0, wy1, wz0, wz1);
+                        }
+                        // F^n of the own points: stage 1's rate, in the same ring-1 slot
+                        float2 fm[VY][V2];
+#pragma unroll
+                        for (int v = 0; v < VY; ++v)
+                            ld2<V>(fm[v], ring1 + (size_t)sc * (S::R1SLOT / 4) + S::FBOXP / 4 + off1 + v * S::W1);
+                        ab2_finish<V, VY>(un, fn, cC, fm, q[R], 1.5f, -0.5f);
+                    } else if (any_inj && finj[cs - pbase]) {
                         tstage_inject<V, VY, DD1>(un, cC, a, pinj[cs - pbase], pinj[cs - pbase + 1], gy, gz,
                                                   a.q_row0 + a.q_dir, wy0, wy1, wz0, wz1, dd);
+                    }
 #pragma unroll
                     for (int v = 0; v < VY; ++v)
                         if (sok[v]) {
                             st2<V>(oh + (long long)v * a.nz, un[v]);
-                            st2<V>(ol + (long long)v * a.nz, q[R][v]);
+                            // level n+1, or with AB the rate F^{n+1} (level n+1 is
+                            // not kept: no receiver reads it, see the host)
+                            if constexpr (S::AB)
+                                st2<V>(ol + (long long)v * a.nz, fn[v]);
+                            else
+                                st2<V>(ol + (long long)v * a.nz, q[R][v]);
                             if constexpr (MODE == 1)
                                 st2<V>(a.dstore + (a.d_row0 + a.d_dir) * a.npad + pix + (long long)v * a.nz, dd[v]);
                             if constexpr (MODE == 2) {
@@ -850,14 +958,16 @@ struct ShotTSweep {  // 128-byte aligned, as its tensor maps
 
 // Every shot of a batch advanced by one launch (T time steps): block i sweeps
 // tile block_map[i].y of shot block_map[i].x, the launch starts at time step
-// `step` of every shot, and `parity` selects their buffers (forward and
-// adjoint sweeps; the gradient modes run on the batched kernel of sweep.cuh).
-template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB>
-__global__ void __launch_bounds__(TShape<R, T, V, VY, BZ, BY, P, MB, 0>::NTB, TShape<R, T, V, VY, BZ, BY, P, MB, 0>::MINB)
+// `step` of every shot, and `parity` selects their buffers.  MODE as
+// tsweep_block: forward and adjoint sweeps (0), and the gradient's recompute
+// (1) and imaging-condition (2) sweeps, whose D rows advance with `step`.
+template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB, int MODE>
+__global__ void __launch_bounds__(TShape<R, T, V, VY, BZ, BY, P, MB, MODE>::NTB,
+                                  TShape<R, T, V, VY, BZ, BY, P, MB, MODE>::MINB)
 tsweep_multi_kernel(const ShotTSweep *__restrict__ shots, const int2 *__restrict__ block_map,
                     const __grid_constant__ Stencil st, int parity, int step)
 {
-    using S = TShape<R, T, V, VY, BZ, BY, P, MB, 0>;
+    using S = TShape<R, T, V, VY, BZ, BY, P, MB, MODE>;
     const int2 bm = block_map[blockIdx.x];
     const ShotTSweep &sh = shots[bm.x];
     const int pl = (int)threadIdx.x - (S::N1 + S::N2);  // producer lane
@@ -871,16 +981,23 @@ tsweep_multi_kernel(const ShotTSweep *__restrict__ shots, const int2 *__restrict
         tensormap_acquire(&m.um);
         tensormap_acquire(&m.B);
         tensormap_acquire(&m.C);
+        if constexpr (S::XA >= 1) tensormap_acquire(&m.x0);
+        if constexpr (S::XA >= 2) tensormap_acquire(&m.x1);
     } else if (T == 2 && pl == 1) {
         tensormap_acquire(&m.u2);
         tensormap_acquire(&m.B2);
         tensormap_acquire(&m.C2);
+        if constexpr (S::XBB >= 1) tensormap_acquire(&m.y0);
+        if constexpr (S::XBB >= 2) tensormap_acquire(&m.y1);
+        if constexpr (S::XBB >= 3) tensormap_acquire(&m.y2);
     }
     SweepArgs la = sh.a[parity];
     la.q_row0 += la.q_dir * step;
     la.c_row0 += la.c_dir * step;
+    la.d_row0 += (long long)la.d_dir * step;
+    la.l_row0 += (long long)la.l_dir * step;
     la.order = nullptr;
-    tsweep_block<R, T, V, VY, BZ, BY, P, MB, 0>(la, st, m, bm.y);
+    tsweep_block<R, T, V, VY, BZ, BY, P, MB, MODE>(la, st, m, bm.y);
 }
 
 }  // namespace wt

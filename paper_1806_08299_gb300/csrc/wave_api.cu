@@ -94,6 +94,16 @@ int encode_map(CUtensorMap *map, const float *base, const Dims &d, int bz, int b
     return r == CUDA_SUCCESS ? WAVE_OK : WAVE_ECUDA;
 }
 
+// A second-difference store [rows][nx][ny][nzp] as one tensor of rows * nx
+// planes (row r, plane x = plane r * nx + x), box bz x by x 1.
+int encode_rows_map(CUtensorMap *map, const float *base, const Dims &d, long long rows, int bz, int by)
+{
+    if (rows < 1 || (long long)d.nx * rows > 0x7fffffffLL) return WAVE_EINVAL;
+    Dims dr = d;
+    dr.nx = (int)(d.nx * rows);
+    return encode_map(map, base, dr, bz, by);
+}
+
 // c_k = 2 (-1)^(k+1) (r!)^2 / (k^2 (r-k)! (r+k)!) by the product form
 // (r!)^2/((r-k)!(r+k)!) = prod_{j=1..k} (r-k+j)/(r+j), exact to double rounding.
 void fd_coeffs(int so, double *c)
@@ -473,6 +483,16 @@ int mode_variants_for(int R, const SweepVariant **out)
     }
 }
 
+// The two-step Adams-Bashforth variant (mode 4) of radius R and depth T.
+const SweepVariant *ab2_variant(int R, int T)
+{
+    const SweepVariant *vs = nullptr;
+    const int nv = mode_variants_for(R, &vs);
+    for (int i = 0; i < nv; ++i)
+        if (vs[i].XB == 4 && vs[i].T == T) return &vs[i];
+    return nullptr;
+}
+
 // The variant of the Born perturbation sweep (mode 3) of radius R.
 const SweepVariant *born_variant(int R)
 {
@@ -624,8 +644,10 @@ struct Job {
     const float *dload = nullptr;
     long long l_base = 0;
     int l_dir = 1;
+    long long l_rows = 1;  // rows of the store dload points at
     float *gacc = nullptr;
     const float *born = nullptr;  // Born perturbation sweep: the coefficient P = -dm / dt^2 (padded)
+    int ab2 = 0;                  // two-step Adams-Bashforth heat: its depth (1 or 2); 0: not that scheme
     // host copies of the injection / record tables and the device buffer for
     // the heavy-first launch order (nullptr: natural order)
     const HostTable *hinj = nullptr, *hrec = nullptr;
@@ -705,20 +727,19 @@ int build_launch(const Job &job, const State &s, int j, const SweepVariant *v, i
             rc = encode_map(&tm->x0, job.cE, d, v->W1, v->H1);
             if (!rc && v->T == 2) rc = encode_map(&tm->y0, job.cE, d, v->BZ, v->BY);
         }
+        // the D rows: the whole store, the launch's rows chosen by l_row0
         if (!rc && v->XB == 2) {
-            const long long row = job.l_base + (long long)job.l_dir * j;  // the launch's first D row
             if (v->T == 1) {
-                rc = encode_map(&tm->x0, job.dload + row * d.npad, d, v->W1, v->H1);
+                rc = encode_rows_map(&tm->x0, job.dload, d, job.l_rows, v->W1, v->H1);
                 if (!rc) rc = encode_map(&tm->x1, job.gacc, d, v->W1, v->H1);
             } else {
-                rc = encode_map(&tm->y0, job.dload + row * d.npad, d, v->BZ, v->BY);
-                if (!rc) rc = encode_map(&tm->y1, job.dload + (row + job.l_dir) * d.npad, d, v->BZ, v->BY);
+                rc = encode_rows_map(&tm->y0, job.dload, d, job.l_rows, v->BZ, v->BY);
+                if (!rc) rc = encode_rows_map(&tm->y1, job.dload, d, job.l_rows, v->BZ, v->BY);
                 if (!rc) rc = encode_map(&tm->y2, job.gacc, d, v->BZ, v->BY);
             }
         }
         if (!rc && v->XB == 3) {
-            const long long row = job.l_base + (long long)job.l_dir * j;  // the background's D row
-            rc = encode_map(&tm->x0, job.dload + row * d.npad, d, v->W1, v->H1);
+            rc = encode_rows_map(&tm->x0, job.dload, d, job.l_rows, v->W1, v->H1);
             if (!rc) rc = encode_map(&tm->x1, job.born, d, v->W1, v->H1);
         }
         if (rc) return rc;
@@ -741,9 +762,11 @@ int build_launch(const Job &job, const State &s, int j, const SweepVariant *v, i
     int spare[2], ns = 0;
     for (int i = 0; i < 4; ++i)
         if (i != s.a && i != s.b) spare[ns++] = i;
-    if (v->T == 1) {
+    if (v->T == 1 && !(v->kind == 1 && v->XB == 4)) {
         a.out_hi = s.buf[s.b];
     } else {
+        // T >= 2, and the two-step Adams-Bashforth sweep at any depth: the new
+        // level and the new rate (the old ones are still read by neighbours)
         a.out_hi = s.buf[spare[0]];
         a.out_lo = s.buf[spare[1]];
     }
@@ -765,6 +788,9 @@ int build_launch(const Job &job, const State &s, int j, const SweepVariant *v, i
     a.l_row0 = job.l_base + (long long)job.l_dir * j;
     a.l_dir = job.l_dir;
     a.gacc = job.gacc;
+    // the two-step Adams-Bashforth weights of stage 1: an Euler step first
+    a.ab1 = job.ab2 != 0 && job.q_base + j == 0 ? 1.f : 1.5f;
+    a.ab0 = job.ab2 != 0 && job.q_base + j == 0 ? 0.f : -0.5f;
     a.withhold = job.withhold;
     a.chunk = chunk;
     a.tiles_z = tiles(d.nzp, v->BZ);
@@ -894,8 +920,19 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
             std::min((v == plan.v && plan.chunk > 0) ? plan.chunk : default_chunk(d, v), max_chunk(v));
         // gradient sweeps: the mode variant of the same untiled shape, if compiled,
         // streams their extra inputs (E, or D and G) through TMA
-        const int mode = job.gacc != nullptr ? 2 : (job.dstore != nullptr ? 1 : (job.born != nullptr ? 3 : 0));
-        if (mode == 3) {
+        const int mode = job.ab2 != 0 ? 4
+                         : job.gacc != nullptr ? 2
+                         : job.dstore != nullptr ? 1
+                         : job.born != nullptr ? 3 : 0;
+        if (mode == 4) {
+            // the Adams-Bashforth heat sweep: the first step (the Euler start)
+            // and a last odd step run untiled
+            const int Tw = (j == 0 || limit < 2) ? 1 : job.ab2;
+            v = ab2_variant(R, Tw);
+            if (v == nullptr) v = ab2_variant(R, 1);
+            if (v == nullptr) return WAVE_EUNSUPPORTED;
+            chunk = std::min(plan.chunk_given && v->T == plan.v->T ? plan.chunk : default_chunk(d, v), max_chunk(v));
+        } else if (mode == 3) {
             // the Born perturbation sweep has one untiled variant per radius
             v = born_variant(R);
             if (v == nullptr) return WAVE_EUNSUPPORTED;
@@ -944,7 +981,7 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
             g_prof.launches++;
             g_prof.steps += v->T;
         }
-        advance_state(s, v->T);
+        advance_state(s, mode == 4 ? 2 : v->T);  // Adams-Bashforth: new level and rate in the spares
         j += v->T;
     }
     return WAVE_OK;
@@ -1311,6 +1348,7 @@ int grad_plan(const Dims &d, const wave_grid *g, const Plan &fwd, const Stencil 
                 aj.q_base = steps - 1;
                 aj.q_dir = -1;
                 aj.dload = store;
+                aj.l_rows = store_rows;
                 aj.l_base = steps - 1;
                 aj.l_dir = -1;
                 aj.gacc = G;
@@ -1404,24 +1442,50 @@ int tmulti_variants(int R, const wt::TMultiVariant **out)
     }
 }
 
-// The single-shot variant whose shape a batched stage-specialised variant has.
+// The single-shot variant (kind 1) of a batched stage-specialised variant's
+// shape and mode: its geometry and launch arguments.
 const SweepVariant *tmulti_shape(const wt::TMultiVariant *tm)
 {
-    return find_variant(tm->R, tm->T, tm->BY, tm->V, tm->BZ, 2, tm->VY);
+    if (tm->mode == 0) return find_variant(tm->R, tm->T, tm->BY, tm->V, tm->BZ, 2, tm->VY);
+    const SweepVariant *vs = nullptr;
+    const int nv = mode_variants_for(tm->R, &vs);
+    for (int i = 0; i < nv; ++i)
+        if (vs[i].kind == 1 && vs[i].XB == tm->mode && vs[i].T == tm->T && vs[i].BY == tm->BY &&
+            vs[i].BZ == tm->BZ && vs[i].V == tm->V && rows_of(&vs[i]) == tm->VY)
+            return &vs[i];
+    return nullptr;
 }
+
+// The kernel of a lockstep phase: the batched kernel of sweep.cuh (tm ==
+// nullptr) or a batched stage-specialised variant tm with its single-shot
+// shape tv.  `map` names the block map it launches with: 0 that of sweep.cuh's
+// kernel, 1 the forward phases' stage-specialised shape, 2 the gradient
+// phases' one.
+struct LockKernel {
+    const wt::TMultiVariant *tm = nullptr;
+    const SweepVariant *tv = nullptr;
+    int map = 0;
+    int T() const { return tm != nullptr ? tm->T : 1; }
+};
+
+// The gradient phases' kernels: recompute (mode 1) and adjoint with the
+// imaging condition (mode 2), of one shape.
+struct LockGrad {
+    LockKernel rec, adj;
+};
+
+constexpr int kLockMaps = 3;
 
 struct LockShot {
     Dims d;
     wave_grid g;
     Layout L;
     HostTable ti, tr;
-    Job job;        // forward (or recompute) job of the current phase
+    Job job;        // job of the current phase
     State s;        // forward / recompute state
     State adj;      // adjoint state (gradient)
-    int chunk = 0;          // x-chunk of the batched kernel of sweep.cuh
-    long long nblocks = 0;  // its blocks per launch
-    int chunk_f = 0;          // x-chunk of the forward phase's stage-specialised kernel
-    long long nblocks_f = 0;  // its blocks per launch
+    int chunk[kLockMaps] = {0, 0, 0};            // x-chunk of each block map's kernel
+    long long nblocks[kLockMaps] = {0, 0, 0};    // its blocks per launch
 };
 
 // Bytes of one phase's per-shot records (either batched kernel's form).
@@ -1430,13 +1494,27 @@ size_t lock_row_bytes(int nshots)
     return align_up(std::max(sizeof(wt::ShotSweep), sizeof(wt::ShotTSweep)) * (size_t)nshots);
 }
 
-// Table of a lockstep group: the block -> (shot, tile) maps of the batched
-// kernel of sweep.cuh and of the forward phase's stage-specialised kernel,
-// then one row of per-shot records per phase.
-size_t lock_table_bytes(int nshots, long long total_blocks, long long total_blocks_f, int nphases)
+// An upper bound on the blocks one launch of any batched kernel gives the
+// group: every variant has BZ >= 24, BY >= 8 and an x-chunk of at least one
+// plane.
+long long lock_block_bound(int n, const wave_shot *shots)
 {
-    return align_up(sizeof(int2) * (size_t)total_blocks) + align_up(sizeof(int2) * (size_t)total_blocks_f) +
-           (size_t)nphases * lock_row_bytes(nshots);
+    long long total = 0;
+    for (int i = 0; i < n; ++i) {
+        const long long nzp = (shots[i].n[2] + 7) / 8 * 8;
+        total += ((nzp + 23) / 24) * ((shots[i].n[1] + 7) / 8) * (long long)shots[i].n[0];
+    }
+    return total;
+}
+
+// Table of a lockstep group: three block maps (launch block -> (shot, tile)),
+// each with room for `bound` blocks, then one row of per-shot records per
+// phase.
+size_t lock_map_bytes(long long bound) { return align_up(sizeof(int2) * (size_t)bound); }
+
+size_t lock_table_bytes(int nshots, long long bound, int nphases)
+{
+    return kLockMaps * lock_map_bytes(bound) + (size_t)nphases * lock_row_bytes(nshots);
 }
 
 int lock_phases(int nt, int ckpt_every)
@@ -1464,25 +1542,15 @@ int capture_stream(cudaStream_t *out)
 }
 
 struct LockTable {
-    std::vector<char> rows;          // one row of per-shot records per phase, lock_row_bytes each
-    std::vector<int2> block_map;     // sweep.cuh batched kernel: launch block -> (shot, tile)
-    std::vector<int2> block_map_f;   // the forward phase's stage-specialised kernel (if any)
-    int2 *dev_block_map = nullptr;
-    int2 *dev_block_map_f = nullptr;
+    std::vector<char> rows;                  // one row of per-shot records per phase, row_bytes each
+    std::vector<int2> map[kLockMaps];        // launch block -> (shot, tile), per kernel shape
+    int2 *dev_map[kLockMaps] = {nullptr, nullptr, nullptr};
     char *dev_rows = nullptr;
     size_t row_bytes = 0;
     int nphases = 0;
 };
 
-// The kernel of a lockstep group's forward phases: the batched kernel of
-// sweep.cuh (tm == nullptr) or a batched stage-specialised variant of depth
-// tm->T, whose single-shot shape is tv.
-struct LockFwd {
-    const wt::TMultiVariant *tm = nullptr;
-    const SweepVariant *tv = nullptr;
-};
-
-// Checkpoint copies of every shot at local step j of a phase.
+// Checkpoint copies of every shot at local step j of a phase of depth T.
 template <class StateOf>
 int lock_ckpt(std::vector<LockShot> &ls, StateOf st_of, int j, int T, float *const *ckpts, int ckpt_every,
               cudaStream_t stream)
@@ -1499,21 +1567,21 @@ int lock_ckpt(std::vector<LockShot> &ls, StateOf st_of, int j, int T, float *con
 }
 
 // Enqueue `nsteps` steps of every shot on `stream`: shot i advances its state
-// `st_of(i)` with job `ls[i].job` from local step 0, one batched launch per
-// time step (the batched kernel of sweep.cuh, fw.tm == nullptr) or per T
-// steps (the stage-specialised one; nsteps and ckpt_every are multiples of
-// T).  At every multiple of ckpt_every (ckpts != nullptr) its state (u^n,
-// u^{n-1}) is copied to ckpts[i] first, as run_steps does.  The per-shot
-// arguments of both buffer parities become the next phase row of `tab`.
+// `st_of(i)` with job `ls[i].job` from local step 0, one launch of kernel k
+// per T steps (nsteps and ckpt_every are multiples of T).  At every multiple
+// of ckpt_every (ckpts != nullptr) its state (u^n, u^{n-1}) is copied to
+// ckpts[i] first, as run_steps does.  The per-shot arguments of both buffer
+// parities become the next phase row of `tab`.
 template <class StateOf>
 int lock_phase(std::vector<LockShot> &ls, StateOf st_of, int nsteps, const wt::MultiVariant *mv,
-               const SweepVariant *v, const LockFwd &fw, const Stencil &st, LockTable &tab,
+               const SweepVariant *v, const LockKernel &k, const Stencil &st, LockTable &tab,
                float *const *ckpts, int ckpt_every, cudaStream_t stream)
 {
     const int n = (int)ls.size();
     const int ph = tab.nphases++;
-    const bool staged = fw.tm != nullptr;
-    const int T = staged ? fw.tm->T : 1;
+    const bool staged = k.tm != nullptr;
+    const int T = k.T();
+    const int mp = staged ? k.map : 0;
     const size_t r0 = tab.rows.size();
     tab.rows.resize(r0 + tab.row_bytes, 0);
     int max_chunk_all = 0;
@@ -1526,32 +1594,31 @@ int lock_phase(std::vector<LockShot> &ls, StateOf st_of, int nsteps, const wt::M
             if (staged) {
                 wt::ShotTSweep *row = reinterpret_cast<wt::ShotTSweep *>(tab.rows.data() + r0) + i;
                 wt::SweepMaps unused;
-                rc = build_launch(ls[i].job, sp, 0, fw.tv, ls[i].chunk_f, &row->a[p], &unused, &row->mp[p], &nb);
-                if (!rc && nb != ls[i].nblocks_f) rc = WAVE_EINVAL;
+                rc = build_launch(ls[i].job, sp, 0, k.tv, ls[i].chunk[mp], &row->a[p], &unused, &row->mp[p], &nb);
             } else {
                 wt::ShotSweep *row = reinterpret_cast<wt::ShotSweep *>(tab.rows.data() + r0) + i;
                 wt::TMaps unused;
-                rc = build_launch(ls[i].job, sp, 0, v, ls[i].chunk, &row->a[p], &row->mp[p], &unused, &nb);
-                if (!rc && nb != ls[i].nblocks) rc = WAVE_EINVAL;
+                rc = build_launch(ls[i].job, sp, 0, v, ls[i].chunk[mp], &row->a[p], &row->mp[p], &unused, &nb);
             }
+            if (!rc && nb != ls[i].nblocks[mp]) rc = WAVE_EINVAL;
             if (rc) return rc;
         }
-        max_chunk_all = std::max(max_chunk_all, staged ? ls[i].chunk_f : ls[i].chunk);
+        max_chunk_all = std::max(max_chunk_all, ls[i].chunk[mp]);
     }
     const char *drow = tab.dev_rows + (size_t)ph * tab.row_bytes;
-    const size_t smem = (staged ? fw.tm->smem : mv->smem) +
-                        wt::sweep_table_bytes(max_chunk_all, staged ? fw.tm->R * T : mv->R * mv->T) + 16;
+    const size_t smem = (staged ? k.tm->smem : mv->smem) +
+                        wt::sweep_table_bytes(max_chunk_all, staged ? k.tm->R * T : mv->R * mv->T) + 16;
     for (int j = 0; j < nsteps; j += T) {
         if (ckpts != nullptr && j % ckpt_every == 0) {
             const int rc = lock_ckpt(ls, st_of, j, T, ckpts, ckpt_every, stream);
             if (rc) return rc;
         }
         if (staged)
-            CK(fw.tm->launch((int)tab.block_map_f.size(), smem, stream, (const wt::ShotTSweep *)drow,
-                             tab.dev_block_map_f, st, (j / T) & 1, j));
+            CK(k.tm->launch((int)tab.map[mp].size(), smem, stream, (const wt::ShotTSweep *)drow, tab.dev_map[mp],
+                            st, (j / T) & 1, j));
         else
-            CK(mv->launch((int)tab.block_map.size(), smem, stream, (const wt::ShotSweep *)drow, tab.dev_block_map,
-                          st, j & 1, j));
+            CK(mv->launch((int)tab.map[0].size(), smem, stream, (const wt::ShotSweep *)drow, tab.dev_map[0], st,
+                          j & 1, j));
     }
     if ((nsteps / T) & 1)
         for (int i = 0; i < n; ++i) advance_state(st_of(i), T);
@@ -1588,17 +1655,84 @@ struct Capture {
     }
 };
 
+// The forward job of shot x from step 0: sources, and receivers recorded
+// unless the group computes a gradient.
+void forward_job(LockShot &x, const wt::ShotSlot &slot, const Stencil &st, bool grad)
+{
+    Job &j = x.job;
+    j = Job();
+    j.d = x.d;
+    j.st = st;
+    j.cB = x.L.cB;
+    j.cC = x.L.cC;
+    j.status = x.L.status;
+    j.inj = x.L.inj.view();
+    j.q = slot.q;
+    j.nq = slot.shot->src.npts;
+    if (!grad) {
+        j.rec = x.L.rec.view();
+        j.corner = x.L.corner;
+        j.nslot = 8 * slot.shot->rec.npts;
+    }
+}
+
+// The recompute job of shot x over the segment from step s0: second
+// differences into store rows 0.. (as wave_grad).
+void recompute_job(LockShot &x, const wt::ShotSlot &slot, const Stencil &st, int s0)
+{
+    Job &rj = x.job;
+    rj = Job();
+    rj.d = x.d;
+    rj.st = st;
+    rj.cB = x.L.cB;
+    rj.cC = x.L.cC;
+    rj.status = x.L.status;
+    rj.cE = x.L.cE;
+    rj.inj = x.L.inj.view();
+    rj.q = slot.q;
+    rj.nq = slot.shot->src.npts;
+    rj.q_base = s0;
+    rj.q_dir = 1;
+    rj.dstore = x.L.store;
+    rj.d_base = 0;
+    rj.d_dir = 1;
+}
+
+// The adjoint job of shot x over the segment [s0, s0 + len), newest step
+// first, with the imaging condition from store rows len-1 .. 0 (as wave_grad).
+void adjoint_job(LockShot &x, const wt::ShotSlot &slot, const Stencil &st, int s0, int len, int rows)
+{
+    Job &aj = x.job;
+    aj = Job();
+    aj.d = x.d;
+    aj.st = st;
+    aj.cB = x.L.cB;
+    aj.cC = x.L.cC;
+    aj.status = x.L.status;
+    aj.inj = x.L.inj2.view();
+    aj.q = slot.resid;
+    aj.nq = slot.shot->rec.npts;
+    aj.q_base = s0 + len - 1;
+    aj.q_dir = -1;
+    aj.dload = x.L.store;
+    aj.l_rows = rows;
+    aj.l_base = len - 1;
+    aj.l_dir = -1;
+    aj.gacc = x.L.G;
+}
+
 // The gradient's time loops of a lockstep group on `stream`: forward with
-// checkpoints (on the forward kernel fw), then per segment (last first) the
-// recompute with stored second differences and the adjoint with the imaging
-// condition (on the batched kernel of sweep.cuh), as wave_grad does for one
-// shot; window gradients (scaled by -1/dt^2) into slots[i].gwin.
+// checkpoints (kernel fw), then per segment (last first) the recompute with
+// stored second differences and the adjoint with the imaging condition
+// (kernels gr), as wave_grad does for one shot; window gradients (scaled by
+// -1/dt^2) into slots[i].gwin.
 int lock_grad(std::vector<LockShot> &ls, const wt::ShotSlot *slots, int ckpt_every, const wt::MultiVariant *mv,
-              const SweepVariant *v, const LockFwd &fw, const Stencil &st, LockTable &tab, cudaStream_t stream,
-              float dt)
+              const SweepVariant *v, const LockKernel &fw, const LockGrad &gr, const Stencil &st, LockTable &tab,
+              cudaStream_t stream, float dt)
 {
     const int n = (int)ls.size();
     const int nt = ls[0].g.nt;
+    const int rows = std::max(1, std::min(ckpt_every, nt));
     auto fwd_state = [&](int i) -> State & { return ls[i].s; };
     auto adj_state = [&](int i) -> State & { return ls[i].adj; };
     std::vector<float *> ck(n);
@@ -1609,9 +1743,9 @@ int lock_grad(std::vector<LockShot> &ls, const wt::ShotSlot *slots, int ckpt_eve
         LockShot &x = ls[i];
         CK(cudaMemsetAsync(x.L.G, 0, sizeof(float) * x.d.npad, stream));
         for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(x.L.V[k], 0, sizeof(float) * x.d.npad, stream));
+        x.adj = State();
         for (int k = 0; k < 4; ++k) x.adj.buf[k] = x.L.V[k];
     }
-    const LockFwd classic;
     const int nseg = (nt + ckpt_every - 1) / ckpt_every;
     for (int c = nseg - 1; c >= 0; --c) {
         const int s0 = c * ckpt_every;
@@ -1619,50 +1753,16 @@ int lock_grad(std::vector<LockShot> &ls, const wt::ShotSlot *slots, int ckpt_eve
         for (int i = 0; i < n; ++i) {
             LockShot &x = ls[i];
             const float *cp = slots[i].ckpt + (size_t)c * 2 * x.d.npad;
+            x.s = State();
             for (int k = 0; k < 4; ++k) x.s.buf[k] = x.L.U[k];
-            x.s.a = 0;
-            x.s.b = 1;
             CK(cudaMemcpyAsync(x.s.buf[0], cp, sizeof(float) * x.d.npad, cudaMemcpyDeviceToDevice, stream));
             CK(cudaMemcpyAsync(x.s.buf[1], cp + x.d.npad, sizeof(float) * x.d.npad, cudaMemcpyDeviceToDevice,
                                stream));
-            Job &rj = x.job;
-            rj = Job();
-            rj.d = x.d;
-            rj.st = st;
-            rj.cB = x.L.cB;
-            rj.cC = x.L.cC;
-            rj.status = x.L.status;
-            rj.cE = x.L.cE;
-            rj.inj = x.L.inj.view();
-            rj.q = slots[i].q;
-            rj.nq = slots[i].shot->src.npts;
-            rj.q_base = s0;
-            rj.q_dir = 1;
-            rj.dstore = x.L.store;
-            rj.d_base = 0;
-            rj.d_dir = 1;
+            recompute_job(x, slots[i], st, s0);
         }
-        if ((rc = lock_phase(ls, fwd_state, len, mv, v, classic, st, tab, nullptr, 0, stream))) return rc;
-        for (int i = 0; i < n; ++i) {
-            LockShot &x = ls[i];
-            Job &aj = x.job;
-            aj = Job();
-            aj.d = x.d;
-            aj.st = st;
-            aj.cB = x.L.cB;
-            aj.cC = x.L.cC;
-            aj.status = x.L.status;
-            aj.inj = x.L.inj2.view();
-            aj.q = slots[i].resid;
-            aj.nq = slots[i].shot->rec.npts;
-            aj.q_base = s0 + len - 1;
-            aj.q_dir = -1;
-            aj.dload = x.L.store;
-            aj.l_base = len - 1;
-            aj.l_dir = -1;
-            aj.gacc = x.L.G;
-        }
-        if ((rc = lock_phase(ls, adj_state, len, mv, v, classic, st, tab, nullptr, 0, stream))) return rc;
+        if ((rc = lock_phase(ls, fwd_state, len, mv, v, gr.rec, st, tab, nullptr, 0, stream))) return rc;
+        for (int i = 0; i < n; ++i) adjoint_job(ls[i], slots[i], st, s0, len, rows);
+        if ((rc = lock_phase(ls, adj_state, len, mv, v, gr.adj, st, tab, nullptr, 0, stream))) return rc;
     }
     const float scale = (float)(-1.0 / ((double)dt * (double)dt));
     for (int i = 0; i < n; ++i)
@@ -1671,49 +1771,81 @@ int lock_grad(std::vector<LockShot> &ls, const wt::ShotSlot *slots, int ckpt_eve
     return WAVE_OK;
 }
 
-// Whether the batched stage-specialised variant tm can run a group's forward
-// phases: its depth must divide nt and the checkpoint interval.
+// Whether the batched stage-specialised variant tm (of depth T) can run a
+// group's phases: T must divide nt and the checkpoint interval, so that every
+// phase (forward, and each segment's recompute and adjoint) is a whole
+// number of launches.
 bool tmulti_fits(const wt::TMultiVariant *tm, int nt, int ckpt_every)
 {
     return tm != nullptr && tmulti_shape(tm) != nullptr && nt % tm->T == 0 &&
            (ckpt_every <= 0 || ckpt_every % tm->T == 0);
 }
 
-// The batched stage-specialised variant a tuning names (kernel 2, depth
-// time_tile, tile_y / tile_z / rows if given), or nullptr.
+// The forward-mode batched stage-specialised variant a tuning names (kernel
+// 2, depth time_tile, tile_y / tile_z / rows / vec if given), or nullptr.
 const wt::TMultiVariant *tmulti_named(int R, const wave_tuning *t)
 {
     const wt::TMultiVariant *tms = nullptr;
     const int nv = tmulti_variants(R, &tms);
     for (int i = 0; i < nv; ++i)
-        if (tms[i].T == t->time_tile && (t->tile_y == 0 || tms[i].BY == t->tile_y) &&
+        if (tms[i].mode == 0 && tms[i].T == t->time_tile && (t->tile_y == 0 || tms[i].BY == t->tile_y) &&
             (t->tile_z == 0 || tms[i].BZ == t->tile_z) && (t->rows == 0 || tms[i].VY == t->rows) &&
             (t->vec == 0 || tms[i].V == t->vec))
             return &tms[i];
     return nullptr;
 }
 
-// Forward-phase choice of autotuned survey groups, per (device, order, group
-// shape): index into the radius's batched stage-specialised variants, or -1
-// for the batched kernel of sweep.cuh.
+// The mode-2 partner (same shape) of the mode-1 batched variant tms[i1], or -1.
+int tmulti_partner(const wt::TMultiVariant *tms, int ntm, int i1)
+{
+    for (int i = 0; i < ntm; ++i)
+        if (tms[i].mode == 2 && tms[i].T == tms[i1].T && tms[i].BZ == tms[i1].BZ && tms[i].BY == tms[i1].BY &&
+            tms[i].V == tms[i1].V && tms[i].VY == tms[i1].VY)
+            return i;
+    return -1;
+}
+
+// The gradient kernels of choice c: -1 sweep.cuh's batched kernel, else the
+// mode-1 batched variant tms[c] and its mode-2 partner (map 2).
+LockGrad lock_grad_kernels(const wt::TMultiVariant *tms, int ntm, int c)
+{
+    LockGrad g;
+    if (c < 0) return g;
+    const int c2 = tmulti_partner(tms, ntm, c);
+    if (c2 < 0) return g;
+    g.rec.tm = &tms[c];
+    g.rec.tv = tmulti_shape(g.rec.tm);
+    g.rec.map = 2;
+    g.adj.tm = &tms[c2];
+    g.adj.tv = tmulti_shape(g.adj.tm);
+    g.adj.map = 2;
+    if (g.rec.tv == nullptr || g.adj.tv == nullptr) return LockGrad();
+    return g;
+}
+
+// Kernel choices of autotuned survey groups, per (device, order, group shape,
+// nt, checkpoint interval): forward (index into the radius's batched
+// stage-specialised variants, or -1 for sweep.cuh's batched kernel) and
+// gradient phases (the mode-1 variant, or -1).
 struct LockKey {
     int dev, so, n;
     long long pts;
-    int mx, my, mz;
+    int mx, my, mz, nt, ck;
     bool operator<(const LockKey &o) const
     {
-        return std::tie(dev, so, n, pts, mx, my, mz) < std::tie(o.dev, o.so, o.n, o.pts, o.mx, o.my, o.mz);
+        return std::tie(dev, so, n, pts, mx, my, mz, nt, ck) <
+               std::tie(o.dev, o.so, o.n, o.pts, o.mx, o.my, o.mz, o.nt, o.ck);
     }
 };
 std::mutex g_lock_mu;
-std::map<LockKey, int> g_lock_cache;
+std::map<LockKey, std::pair<int, int>> g_lock_cache;
 
 // The key of a group of n shots of grid G (their windows' extents).
-int lock_key(const wave_grid *G, int n, const wave_shot *shots, LockKey *key)
+int lock_key(const wave_grid *G, int n, const wave_shot *shots, int ckpt_every, LockKey *key)
 {
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    *key = LockKey{dev, G->space_order, n, 0, 0, 0, 0};
+    *key = LockKey{dev, G->space_order, n, 0, 0, 0, 0, G->nt, ckpt_every};
     for (int i = 0; i < n; ++i) {
         wave_grid g = *G;
         for (int a = 0; a < 3; ++a) g.n[a] = shots[i].n[a];
@@ -1739,30 +1871,33 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
         const int R = G->space_order / 2;
         const MultiVariant *mv = multi_variant(R);
         if (mv == nullptr || tuning == nullptr) return WAVE_EUNSUPPORTED;
-        // the batched kernel of sweep.cuh runs its default untiled shape (and
-        // every gradient-mode phase)
+        // the batched kernel of sweep.cuh runs its default untiled shape
         const SweepVariant *v = find_variant(R, 1, mv->BY, mv->V, mv->BZ, 1);
         if (v == nullptr || v->P != mv->P) return WAVE_EUNSUPPORTED;
         const bool grad = ckpt_every > 0;
         const int nt = G->nt;
-        // forward phases: named by the tuning, or timed below (time_tile 0)
-        LockFwd fw;
-        bool tune_fwd = false;
-        if (tuning->time_tile == 0) {
-            tune_fwd = true;
-        } else if (tuning->kernel == 2) {
+        const int rows = grad ? std::max(1, std::min(ckpt_every, nt)) : 0;
+        const wt::TMultiVariant *tms = nullptr;
+        const int ntm = tmulti_variants(R, &tms);
+        // kernels: named by the tuning, or timed below (time_tile 0)
+        LockKernel fw;
+        LockGrad gr;
+        const bool tune = tuning->time_tile == 0;
+        if (!tune && tuning->kernel == 2) {
             fw.tm = tmulti_named(R, tuning);
             if (!tmulti_fits(fw.tm, nt, ckpt_every)) return WAVE_EUNSUPPORTED;
             fw.tv = tmulti_shape(fw.tm);
-        } else if (tuning->time_tile != 1 || (tuning->tile_y && tuning->tile_y != v->BY) ||
-                   (tuning->vec && tuning->vec != v->V) || (tuning->tile_z && tuning->tile_z != v->BZ)) {
+            fw.map = 1;
+            // the gradient phases on the first mode shape of the same depth
+            for (int c = 0; c < ntm && grad && gr.rec.tm == nullptr; ++c)
+                if (tms[c].mode == 1 && tms[c].T == fw.tm->T && tmulti_fits(&tms[c], nt, ckpt_every))
+                    gr = lock_grad_kernels(tms, ntm, c);
+        } else if (!tune && (tuning->time_tile != 1 || (tuning->tile_y && tuning->tile_y != v->BY) ||
+                             (tuning->vec && tuning->vec != v->V) || (tuning->tile_z && tuning->tile_z != v->BZ))) {
             return WAVE_EUNSUPPORTED;
         }
-        const wt::TMultiVariant *tms = nullptr;
-        const int ntm = tmulti_variants(R, &tms);
         std::vector<LockShot> ls(n);
         Stencil st;
-        long long total_blocks = 0;
         // per-shot setup on `stream`: model coefficients, zero levels, point tables
         for (int i = 0; i < n; ++i) {
             LockShot &x = ls[i];
@@ -1783,191 +1918,201 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
             for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(x.L.U[k], 0, sizeof(float) * x.d.npad, stream));
             if ((rc = upload_table(x.ti, x.L.inj, stream))) return rc;
             if ((rc = upload_table(x.tr, grad ? x.L.inj2 : x.L.rec, stream))) return rc;
-            x.chunk = std::min(tuning->tile_x > 0 && !fw.tm && !tune_fwd ? std::min(tuning->tile_x, x.d.nx)
-                                                                          : default_chunk(x.d, v),
-                               max_chunk(v));
-            x.nblocks = (long long)tiles(x.d.nzp, v->BZ) * tiles(x.d.ny, v->BY) * tiles(x.d.nx, x.chunk);
-            total_blocks += x.nblocks;
             for (int k = 0; k < 4; ++k) x.s.buf[k] = x.L.U[k];
-            x.job = Job();
-            x.job.d = x.d;
-            x.job.st = st;
-            x.job.cB = x.L.cB;
-            x.job.cC = x.L.cC;
-            x.job.status = x.L.status;
-            x.job.inj = x.L.inj.view();
-            x.job.q = slots[i].q;
-            x.job.nq = ns;
-            if (!grad) {
-                x.job.rec = x.L.rec.view();
-                x.job.corner = x.L.corner;
-                x.job.nslot = 8 * nr;
-            }
+            forward_job(x, slots[i], st, grad);
         }
         CK(wt::allow_max_dynamic_smem(mv->func));
         const int nphases = lock_phases(nt, ckpt_every);
+        std::vector<wave_shot> gs(n);
+        for (int i = 0; i < n; ++i) gs[i] = *slots[i].shot;
+        const long long bound = lock_block_bound(n, gs.data());
+        if (bound > 0x7fffffffLL || lock_table_bytes(n, bound, nphases) > table_bytes) return WAVE_ENOSPACE;
         LockTable tab;
         tab.row_bytes = lock_row_bytes(n);
-        // launch order: the tiles of every shot that handle a source or
-        // receiver point (in any phase) first, then the rest
-        auto block_map = [&](const SweepVariant *sv, bool fwd_kernel, std::vector<int2> &out) {
-            out.clear();
+        for (int k = 0; k < kLockMaps; ++k) tab.dev_map[k] = (int2 *)((char *)table + k * lock_map_bytes(bound));
+        tab.dev_rows = (char *)table + kLockMaps * lock_map_bytes(bound);
+
+        // x-chunks and the block map of a kernel: the tiles of every shot that
+        // handle a source or receiver point (in any phase) first, then the rest
+        auto set_map = [&](const LockKernel &k) -> int {
+            const int mp = k.tm != nullptr ? k.map : 0;
+            const SweepVariant *sv = k.tm != nullptr ? k.tv : v;
             std::vector<std::vector<char>> heavy(n);
-            for (int i = 0; i < n; ++i) {
-                const int ch = fwd_kernel ? ls[i].chunk_f : ls[i].chunk;
-                const long long nb = fwd_kernel ? ls[i].nblocks_f : ls[i].nblocks;
-                mark_heavy(ls[i].d, sv, ch, &ls[i].ti, false, heavy[i]);
-                mark_heavy(ls[i].d, sv, ch, &ls[i].tr, !grad, heavy[i]);
-                heavy[i].resize((size_t)nb, 0);
-            }
-            for (int pass = 1; pass >= 0; --pass)
-                for (int i = 0; i < n; ++i) {
-                    const long long nb = fwd_kernel ? ls[i].nblocks_f : ls[i].nblocks;
-                    for (long long t = 0; t < nb; ++t)
-                        if (heavy[i][(size_t)t] == pass) out.push_back(make_int2(i, (int)t));
-                }
-        };
-        auto set_forward = [&](const LockFwd &f) -> long long {
             long long tot = 0;
             for (int i = 0; i < n; ++i) {
                 LockShot &x = ls[i];
-                if (f.tm == nullptr) {
-                    x.chunk_f = 0;
-                    x.nblocks_f = 0;
-                    continue;
-                }
-                x.chunk_f = std::min(tuning->tile_x > 0 && !tune_fwd ? std::min(tuning->tile_x, x.d.nx)
-                                                                      : default_chunk(x.d, f.tv),
-                                     max_chunk(f.tv));
-                x.nblocks_f = (long long)tiles(x.d.nzp, f.tv->BZ) * tiles(x.d.ny, f.tv->BY) *
-                              tiles(x.d.nx, x.chunk_f);
-                tot += x.nblocks_f;
+                const bool own_chunk = tuning->tile_x > 0 && !tune && (mp == 0 ? fw.tm == nullptr : mp == 1);
+                x.chunk[mp] = std::min(own_chunk ? std::min(tuning->tile_x, x.d.nx) : default_chunk(x.d, sv),
+                                       max_chunk(sv));
+                x.nblocks[mp] = (long long)tiles(x.d.nzp, sv->BZ) * tiles(x.d.ny, sv->BY) * tiles(x.d.nx, x.chunk[mp]);
+                tot += x.nblocks[mp];
+                mark_heavy(x.d, sv, x.chunk[mp], &x.ti, false, heavy[i]);
+                mark_heavy(x.d, sv, x.chunk[mp], &x.tr, !grad, heavy[i]);
+                heavy[i].resize((size_t)x.nblocks[mp], 0);
             }
-            return tot;
+            if (tot > bound) return WAVE_ENOSPACE;
+            std::vector<int2> &out = tab.map[mp];
+            out.clear();
+            for (int pass = 1; pass >= 0; --pass)
+                for (int i = 0; i < n; ++i)
+                    for (long long t = 0; t < ls[i].nblocks[mp]; ++t)
+                        if (heavy[i][(size_t)t] == pass) out.push_back(make_int2(i, (int)t));
+            if (k.tm != nullptr) CK(wt::allow_max_dynamic_smem(k.tm->func));
+            return WAVE_OK;
         };
-        const size_t map_bytes = align_up(sizeof(int2) * (size_t)total_blocks);
-        tab.dev_block_map = (int2 *)table;
-        block_map(v, false, tab.block_map);
-        if (total_blocks > 0x7fffffffLL) return WAVE_ENOSPACE;
+        auto upload_map = [&](int mp) -> int {
+            CK(cudaMemcpyAsync(tab.dev_map[mp], tab.map[mp].data(), sizeof(int2) * tab.map[mp].size(),
+                               cudaMemcpyHostToDevice, stream));
+            return WAVE_OK;
+        };
+        int rc = set_map(LockKernel());
+        if (rc) return rc;
 
-        if (tune_fwd) {
-            // Time the forward phase of the group on every candidate kernel: a
-            // few launches on the group's zeroed levels with its own sources
-            // and receivers, best of two passes; ties keep the earlier.
-            std::vector<wave_shot> gs(n);
-            for (int i = 0; i < n; ++i) gs[i] = *slots[i].shot;
+        if (tune) {
+            // Time the group's own shots on every candidate kernel, a few steps
+            // from zeroed levels, best of two passes, per step; ties keep the
+            // earlier (sweep.cuh's batched kernel first).  The forward phases
+            // and, for the gradient, the recompute + adjoint phases are timed
+            // separately; the choice is cached per group shape.
             LockKey key;
-            int rc = lock_key(G, n, gs.data(), &key);
-            if (rc) return rc;
-            int choice = -2;
+            if ((rc = lock_key(G, n, gs.data(), ckpt_every, &key))) return rc;
+            std::pair<int, int> choice(-2, -2);
             {
                 std::lock_guard<std::mutex> lk(g_lock_mu);
                 auto it = g_lock_cache.find(key);
                 if (it != g_lock_cache.end()) choice = it->second;
             }
-            if (choice == -2) {
-                std::vector<int> cands = {-1};
-                for (int c = 0; c < ntm; ++c)
-                    if (tmulti_fits(&tms[c], nt, ckpt_every)) cands.push_back(c);
+            if (choice.first == -2) {
                 cudaEvent_t e0, e1;
                 CK(cudaEventCreate(&e0));
                 CK(cudaEventCreate(&e1));
-                std::vector<float> best(cands.size(), 1e30f);
-                const int steps = std::min(8, nt);  // a multiple of every candidate's depth
-                for (int pass = 0; pass < 2 && rc == WAVE_OK; ++pass)
-                    for (size_t c = 0; c < cands.size() && rc == WAVE_OK; ++c) {
-                        LockFwd f;
-                        if (cands[c] >= 0) {
-                            f.tm = &tms[cands[c]];
-                            f.tv = tmulti_shape(f.tm);
-                        }
-                        const long long tot_f = set_forward(f);
-                        if (lock_table_bytes(n, total_blocks, tot_f, 1) > table_bytes || tot_f > 0x7fffffffLL) {
-                            best[c] = 1e30f;  // the workspace's table does not hold this kernel's map
-                            continue;
-                        }
-                        LockTable tt;
-                        tt.row_bytes = tab.row_bytes;
-                        tt.block_map = tab.block_map;
-                        tt.dev_block_map = tab.dev_block_map;
-                        tt.dev_block_map_f = (int2 *)((char *)table + map_bytes);
-                        tt.dev_rows = (char *)table + map_bytes + align_up(sizeof(int2) * (size_t)tot_f);
-                        if (f.tm) block_map(f.tv, true, tt.block_map_f);
-                        auto st_of = [&](int i) -> State & { return ls[i].s; };
-                        float ms = 0.f;
-                        if (cudaMemcpyAsync(tt.dev_block_map, tt.block_map.data(), sizeof(int2) * tt.block_map.size(),
-                                            cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-                            (f.tm && cudaMemcpyAsync(tt.dev_block_map_f, tt.block_map_f.data(),
-                                                     sizeof(int2) * tt.block_map_f.size(), cudaMemcpyHostToDevice,
-                                                     stream) != cudaSuccess)) {
-                            rc = WAVE_ECUDA;
+                auto st_fwd = [&](int i) -> State & { return ls[i].s; };
+                auto st_adj = [&](int i) -> State & { return ls[i].adj; };
+                // run `fn` (which enqueues launches) between events: ms, or < 0 on failure
+                auto timed = [&](auto fn) -> float {
+                    float ms = -1.f;
+                    if (cudaEventRecord(e0, stream) != cudaSuccess) return -1.f;
+                    if (fn() != WAVE_OK) return -1.f;
+                    if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                        return -1.f;
+                    return ms;
+                };
+                // a phase's rows built on the host and uploaded before its launches
+                auto run_phase = [&](auto st_of, int steps, const LockKernel &k) -> int {
+                    LockTable tt;
+                    tt.row_bytes = tab.row_bytes;
+                    for (int m = 0; m < kLockMaps; ++m) {
+                        tt.map[m] = tab.map[m];
+                        tt.dev_map[m] = tab.dev_map[m];
+                    }
+                    tt.dev_rows = tab.dev_rows;
+                    int r = lock_phase(ls, st_of, 0, mv, v, k, st, tt, nullptr, 0, stream);  // the row only
+                    if (r) return r;
+                    CK(cudaMemcpyAsync(tt.dev_rows, tt.rows.data(), tt.row_bytes, cudaMemcpyHostToDevice, stream));
+                    tt.rows.clear();
+                    tt.nphases = 0;
+                    return lock_phase(ls, st_of, steps, mv, v, k, st, tt, nullptr, 0, stream);
+                };
+                int best_f = -1, best_g = -1;
+                float tbest_f = 1e30f, tbest_g = 1e30f;
+                std::vector<int> cf = {-1};
+                for (int c = 0; c < ntm; ++c)
+                    if (tms[c].mode == 0 && tmulti_fits(&tms[c], nt, ckpt_every)) cf.push_back(c);
+                std::vector<int> cg = {-1};
+                for (int c = 0; c < ntm && grad; ++c)
+                    if (tms[c].mode == 1 && tmulti_fits(&tms[c], nt, ckpt_every) &&
+                        lock_grad_kernels(tms, ntm, c).rec.tm != nullptr)
+                        cg.push_back(c);
+                for (int pass = 0; pass < 2 && rc == WAVE_OK; ++pass) {
+                    for (size_t ci = 0; ci < cf.size() && rc == WAVE_OK; ++ci) {
+                        LockKernel k;
+                        if (cf[ci] >= 0) {
+                            k.tm = &tms[cf[ci]];
+                            k.tv = tmulti_shape(k.tm);
+                            k.map = 1;
+                            if ((rc = set_map(k)) || (rc = upload_map(1))) break;
+                        } else if ((rc = upload_map(0))) {
                             break;
                         }
-                        // the phase row is built on the host first, then uploaded before its launches
-                        tt.rows.reserve(tt.row_bytes);
-                        {
-                            // build the row without launching: zero steps
-                            if ((rc = lock_phase(ls, st_of, 0, mv, v, f, st, tt, nullptr, 0, stream))) break;
-                            tt.nphases = 0;
-                            if (cudaMemcpyAsync(tt.dev_rows, tt.rows.data(), tt.row_bytes, cudaMemcpyHostToDevice,
-                                                stream) != cudaSuccess) {
-                                rc = WAVE_ECUDA;
-                                break;
-                            }
-                            tt.rows.clear();
-                        }
-                        if (cudaEventRecord(e0, stream) != cudaSuccess) { rc = WAVE_ECUDA; break; }
-                        if ((rc = lock_phase(ls, st_of, steps, mv, v, f, st, tt, nullptr, 0, stream))) break;
-                        if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                            rc = WAVE_ECUDA;
-                            break;
-                        }
-                        best[c] = std::min(best[c], ms);
+                        const int steps = std::min(8, nt);  // a multiple of every candidate's depth
+                        for (int i = 0; i < n; ++i) forward_job(ls[i], slots[i], st, grad);
+                        const float ms = timed([&] { return run_phase(st_fwd, steps, k); });
+                        if (ms < 0.f) { rc = WAVE_ECUDA; break; }
                         if (tune_log() && pass == 1)
                             std::fprintf(stderr, "wave survey group: forward kernel=%d T=%d: %.4f ms for %d steps\n",
-                                         f.tm ? 2 : 1, f.tm ? f.tm->T : 1, ms, steps);
+                                         k.tm ? 2 : 1, k.T(), ms, steps);
+                        if (pass == 1 && ms / steps < 0.99f * tbest_f) {
+                            tbest_f = ms / steps;
+                            best_f = cf[ci];
+                        }
                     }
+                    for (size_t ci = 0; ci < cg.size() && rc == WAVE_OK && grad; ++ci) {
+                        const LockGrad g = lock_grad_kernels(tms, ntm, cg[ci]);
+                        const int T = g.rec.T();
+                        const int steps = std::min(8, rows) / T * T;
+                        if (steps < 1) continue;
+                        if (g.rec.tm != nullptr) {
+                            if ((rc = set_map(g.rec)) || (rc = upload_map(2))) break;
+                        } else if ((rc = upload_map(0))) {
+                            break;
+                        }
+                        for (int i = 0; i < n; ++i) {
+                            ls[i].adj = State();
+                            for (int k = 0; k < 4; ++k) ls[i].adj.buf[k] = ls[i].L.V[k];
+                        }
+                        const float ms = timed([&] {
+                            for (int i = 0; i < n; ++i) recompute_job(ls[i], slots[i], st, 0);
+                            int r = run_phase(st_fwd, steps, g.rec);
+                            if (r) return r;
+                            for (int i = 0; i < n; ++i) adjoint_job(ls[i], slots[i], st, 0, steps, rows);
+                            return run_phase(st_adj, steps, g.adj);
+                        });
+                        if (ms < 0.f) { rc = WAVE_ECUDA; break; }
+                        if (tune_log() && pass == 1)
+                            std::fprintf(stderr,
+                                         "wave survey group: gradient kernel=%d T=%d: %.4f ms for %d + %d steps\n",
+                                         g.rec.tm ? 2 : 1, T, ms, steps, steps);
+                        if (pass == 1 && ms / steps < 0.99f * tbest_g) {
+                            tbest_g = ms / steps;
+                            best_g = cg[ci];
+                        }
+                    }
+                }
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
                 if (rc) return rc;
-                size_t bi = 0;
-                for (size_t c = 1; c < cands.size(); ++c)
-                    if (best[c] < 0.99f * best[bi]) bi = c;
-                choice = cands[bi];
+                choice = std::make_pair(best_f, best_g);
                 std::lock_guard<std::mutex> lk(g_lock_mu);
                 g_lock_cache[key] = choice;
             }
-            if (choice >= 0) {
-                fw.tm = &tms[choice];
+            if (choice.first >= 0) {
+                fw.tm = &tms[choice.first];
                 fw.tv = tmulti_shape(fw.tm);
+                fw.map = 1;
             }
-            // the timed launches left the levels dirty: start from zero again
+            if (grad && choice.second >= 0) gr = lock_grad_kernels(tms, ntm, choice.second);
+            // the timed launches left the levels (and the adjoint's) dirty: start
+            // from zero again, with the forward job of every shot
             for (int i = 0; i < n; ++i) {
-                ls[i].s = State();
+                LockShot &x = ls[i];
+                x.s = State();
+                x.adj = State();
                 for (int k = 0; k < 4; ++k) {
-                    ls[i].s.buf[k] = ls[i].L.U[k];
-                    CK(cudaMemsetAsync(ls[i].L.U[k], 0, sizeof(float) * ls[i].d.npad, stream));
+                    x.s.buf[k] = x.L.U[k];
+                    CK(cudaMemsetAsync(x.L.U[k], 0, sizeof(float) * x.d.npad, stream));
                 }
+                forward_job(x, slots[i], st, grad);
             }
         }
-        const long long total_blocks_f = set_forward(fw);
-        if (total_blocks_f > 0x7fffffffLL ||
-            lock_table_bytes(n, total_blocks, total_blocks_f, nphases) > table_bytes)
-            return WAVE_ENOSPACE;
-        tab.dev_block_map_f = (int2 *)((char *)table + map_bytes);
-        tab.dev_rows = (char *)table + map_bytes + align_up(sizeof(int2) * (size_t)total_blocks_f);
+        if (fw.tm != nullptr && (rc = set_map(fw))) return rc;
+        if (gr.rec.tm != nullptr && (rc = set_map(gr.rec))) return rc;
         tab.rows.reserve((size_t)nphases * tab.row_bytes);
-        if (fw.tm) {
-            block_map(fw.tv, true, tab.block_map_f);
-            CK(wt::allow_max_dynamic_smem(fw.tm->func));
-        }
 
         // The time loops go into one CUDA graph, captured on the library's
         // stream and launched on `stream` after the tables are uploaded.
         cudaStream_t cs;
-        int rc = capture_stream(&cs);
-        if (rc) return rc;
+        if ((rc = capture_stream(&cs))) return rc;
         std::lock_guard<std::mutex> capture_lock(g_capture_mu);  // released after `cap` ends
         Capture cap;
         if ((rc = cap.begin(cs))) return rc;
@@ -1980,7 +2125,7 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
                                       slots[i].rec_out, cs) != cudaSuccess)
                     rc = WAVE_ECUDA;
         } else {
-            rc = lock_grad(ls, slots, ckpt_every, mv, v, fw, st, tab, cs, G->dt);
+            rc = lock_grad(ls, slots, ckpt_every, mv, v, fw, gr, st, tab, cs, G->dt);
         }
         if (rc) return rc;
         if ((rc = cap.end())) return rc;
@@ -1988,13 +2133,11 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
         cudaGraphExec_t exec = nullptr;
         CK(cudaGraphInstantiate(&exec, cap.graph, 0));
         rc = WAVE_OK;
-        if (cudaMemcpyAsync(tab.dev_block_map, tab.block_map.data(), sizeof(int2) * tab.block_map.size(),
-                            cudaMemcpyHostToDevice, stream) != cudaSuccess)
-            rc = WAVE_ECUDA;
-        if (rc == WAVE_OK && !tab.block_map_f.empty() &&
-            cudaMemcpyAsync(tab.dev_block_map_f, tab.block_map_f.data(), sizeof(int2) * tab.block_map_f.size(),
-                            cudaMemcpyHostToDevice, stream) != cudaSuccess)
-            rc = WAVE_ECUDA;
+        for (int k = 0; k < kLockMaps && rc == WAVE_OK; ++k)
+            if (!tab.map[k].empty() &&
+                cudaMemcpyAsync(tab.dev_map[k], tab.map[k].data(), sizeof(int2) * tab.map[k].size(),
+                                cudaMemcpyHostToDevice, stream) != cudaSuccess)
+                rc = WAVE_ECUDA;
         if (rc == WAVE_OK && cudaMemcpyAsync(tab.dev_rows, tab.rows.data(), tab.rows.size(), cudaMemcpyHostToDevice,
                                              stream) != cudaSuccess)
             rc = WAVE_ECUDA;
@@ -2024,24 +2167,27 @@ int lockstep_describe(const wave_grid *G, int n, const wave_shot *shots, int ckp
 {
     const int R = G->space_order / 2;
     const MultiVariant *mv = multi_variant(R);
-    for (int k = 0; k < 9; ++k) out[k] = 0;
+    for (int k = 0; k < 11; ++k) out[k] = 0;
     if (!lockstep_supported(G, tuning, ckpt_every)) return WAVE_OK;  // per-shot streams
     out[8] = 1;
+    const wt::TMultiVariant *tms = nullptr;
+    const int ntm = tmulti_variants(R, &tms);
     const wt::TMultiVariant *tm = nullptr;
+    LockGrad gr;
     if (tuning->time_tile == 0) {
         LockKey key;
-        const int rc = lock_key(G, n, shots, &key);
+        const int rc = lock_key(G, n, shots, ckpt_every, &key);
         if (rc) return rc;
         std::lock_guard<std::mutex> lk(g_lock_mu);
         auto it = g_lock_cache.find(key);
         if (it == g_lock_cache.end()) return WAVE_OK;  // not timed yet: out[0] = 0
-        if (it->second >= 0) {
-            const wt::TMultiVariant *tms = nullptr;
-            tmulti_variants(R, &tms);
-            tm = &tms[it->second];
-        }
+        if (it->second.first >= 0) tm = &tms[it->second.first];
+        if (ckpt_every > 0 && it->second.second >= 0) gr = lock_grad_kernels(tms, ntm, it->second.second);
     } else if (tuning->kernel == 2) {
         tm = tmulti_named(R, tuning);
+        for (int c = 0; c < ntm && ckpt_every > 0 && tm != nullptr && gr.rec.tm == nullptr; ++c)
+            if (tms[c].mode == 1 && tms[c].T == tm->T && tmulti_fits(&tms[c], G->nt, ckpt_every))
+                gr = lock_grad_kernels(tms, ntm, c);
     }
     if (tm != nullptr) {
         const int v[8] = {tm->T, tm->BY, 0, tm->BZ, tm->V, tm->P, WAVE_KERNEL_STAGED, tm->VY};
@@ -2050,19 +2196,16 @@ int lockstep_describe(const wave_grid *G, int n, const wave_shot *shots, int ckp
         const int v[8] = {1, mv->BY, 0, mv->BZ, mv->V, mv->P, WAVE_KERNEL_SHARED, 1};
         for (int k = 0; k < 8; ++k) out[k] = v[k];
     }
+    if (ckpt_every > 0) {
+        out[9] = gr.rec.tm != nullptr ? WAVE_KERNEL_STAGED : WAVE_KERNEL_SHARED;
+        out[10] = gr.rec.T();
+    }
     return WAVE_OK;
 }
 
 size_t lockstep_table_bytes(const wave_grid *G, int n, const wave_shot *shots, int ckpt_every)
 {
-    // an upper bound on the launch's blocks, for either map: every variant
-    // has BZ >= 24, BY >= 8, and an x-chunk of at least one plane
-    long long total = 0;
-    for (int i = 0; i < n; ++i) {
-        const long long nzp = (shots[i].n[2] + 7) / 8 * 8;
-        total += ((nzp + 23) / 24) * ((shots[i].n[1] + 7) / 8) * (long long)shots[i].n[0];
-    }
-    return lock_table_bytes(n, total, total, lock_phases(G->nt, ckpt_every));
+    return lock_table_bytes(n, lock_block_bound(n, shots), lock_phases(G->nt, ckpt_every));
 }
 
 cudaError_t allow_max_dynamic_smem(const void *func)
@@ -2469,6 +2612,7 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
             aj.q_base = s0 + len - 1;
             aj.q_dir = -1;
             aj.dload = L.store;
+            aj.l_rows = store_rows;
             aj.l_base = len - 1;
             aj.l_dir = -1;
             aj.gacc = L.G;
@@ -2550,6 +2694,7 @@ int32_t wave_born(const wave_grid *g, const float *m, const float *damp, const f
         pj.corner = L.corner;
         pj.nslot = 8 * nrec;
         pj.dload = L.store;
+        pj.l_rows = 1;
         pj.l_base = 0;
         pj.l_dir = 0;
         pj.born = L.G;
@@ -2714,6 +2859,7 @@ int32_t wave_grad_revolve(const wave_grid *g, const float *m, const float *damp,
                 aj.q_base = x.a;
                 aj.q_dir = -1;
                 aj.dload = L.store;
+                aj.l_rows = 1;
                 aj.l_base = 0;
                 aj.l_dir = -1;
                 aj.gacc = L.G;
@@ -2784,6 +2930,83 @@ int32_t wave_heat(const wave_grid *g, const float *kappa, const float *u0, const
         job.order_cap = L.order_cap;
         State s;
         for (int i = 0; i < 4; ++i) s.buf[i] = L.U[i];
+        if ((rc = prof_begin(tuning, stream))) return rc;
+        if ((rc = run_steps(job, s, g->nt, plan, stream))) return rc;
+        if ((rc = prof_end(stream))) return rc;
+        if (nrec > 0 && rec_traces != nullptr)
+            CK(wt::launch_gather(L.corner, L.rec.wts, g->nt, nrec, 1, rec_traces, stream));
+        CK(wt::launch_unpad(s.buf[s.a], d.nx, d.ny, d.nz, d.nzp, 1.f, u_out, stream));
+        return WAVE_OK;
+    } catch (...) {
+        return WAVE_EINVAL;
+    }
+}
+
+int32_t wave_heat_ab2(const wave_grid *g, const float *kappa, const float *u0, const wave_points *src,
+                      const float *src_traces, const wave_points *rec, float *rec_traces, float *u_out,
+                      const wave_tuning *tuning, void *ws, size_t ws_bytes, void *stream_)
+{
+    try {
+        Dims d;
+        int rc = check_grid(g, &d);
+        if (rc) return rc;
+        if (!u0 || !u_out || !ws) return WAVE_EINVAL;
+        if (check_points(src, true, src_traces) || check_points(rec, false, nullptr)) return WAVE_EINVAL;
+        if ((uintptr_t)ws % kAlign) return WAVE_EINVAL;
+        const int nsrc = npts_of(src), nrec = npts_of(rec);
+        const int R = g->space_order / 2;
+        const Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_FWD, nsrc, nrec, g->nt, 0);
+        if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
+        HostTable ti, tr;
+        if (build_table(d, g->h, src, false, &ti) || build_table(d, g->h, rec, true, &tr)) return WAVE_EINVAL;
+        // depth: 2 where compiled and no receiver needs the intermediate level
+        // (a depth-2 launch stores the new level and rate, not the level
+        // between), else 1; tuning->time_tile 1 asks for the untiled sweep
+        const int want = tuning != nullptr && tuning->time_tile == 1 ? 1 : 2;
+        const int T = (want == 2 && nrec == 0 && ab2_variant(R, 2) != nullptr) ? 2 : 1;
+        Plan plan;
+        plan.v = ab2_variant(R, T);
+        if (plan.v == nullptr) return WAVE_EUNSUPPORTED;
+        plan.chunk_given = tuning != nullptr && tuning->tile_x > 0;
+        plan.chunk = std::min(plan.chunk_given ? std::min(tuning->tile_x, d.nx) : default_chunk(d, plan.v),
+                              max_chunk(plan.v));
+        cudaStream_t stream = (cudaStream_t)stream_;
+        const Stencil st = make_stencil(g);
+        // B = 0, C = dt kappa; the two-step scheme is stable while
+        // dt kappa |L| <= 1 (the check takes 2 dt |L| against 2)
+        const bool allow = tuning && (tuning->flags & WAVE_ALLOW_UNSTABLE);
+        double stot = 0.0;
+        for (int a = 0; a < 3; ++a) stot += symbol_at_pi(g->space_order) / ((double)g->h[a] * g->h[a]);
+        CK(cudaMemsetAsync(L.status, 0, sizeof(int) * kStatusWords, stream));
+        CK(wt::launch_heat_prep(kappa, d.nx, d.ny, d.nz, d.nzp, g->dt, allow ? 0.f : (float)(2.0 * g->dt * stot),
+                                L.cB, L.cC, L.status, stream));
+        // level 0 = u0 in U[0]; the rate F^{-1} (weight 0 in the Euler start,
+        // but read) = 0 in U[2]
+        CK(wt::launch_pad(u0, d.nx, d.ny, d.nz, d.nzp, L.U[0], stream));
+        CK(cudaMemsetAsync(L.U[2], 0, sizeof(float) * d.npad, stream));
+        if ((rc = upload_table(ti, L.inj, stream)) || (rc = upload_table(tr, L.rec, stream))) return rc;
+        Job job;
+        job.d = d;
+        job.st = st;
+        job.cB = L.cB;
+        job.cC = L.cC;
+        job.status = L.status;
+        job.cE = nullptr;
+        job.inj = L.inj.view();
+        job.q = src_traces;
+        job.nq = nsrc;
+        job.rec = L.rec.view();
+        job.corner = L.corner;
+        job.nslot = 8 * nrec;
+        job.hinj = &ti;
+        job.hrec = &tr;
+        job.order = L.order;
+        job.order_cap = L.order_cap;
+        job.ab2 = T;
+        State s;
+        for (int i = 0; i < 4; ++i) s.buf[i] = L.U[i];
+        s.a = 0;
+        s.b = 2;
         if ((rc = prof_begin(tuning, stream))) return rc;
         if ((rc = run_steps(job, s, g->nt, plan, stream))) return rc;
         if ((rc = prof_end(stream))) return rc;

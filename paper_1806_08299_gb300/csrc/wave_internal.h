@@ -57,11 +57,12 @@ int sweep_multi_variant_r6(const MultiVariant **out);
 int sweep_multi_variant_r7(const MultiVariant **out);
 int sweep_multi_variant_r8(const MultiVariant **out);
 
-// Batched variants of the stage-specialised sweep (forward and adjoint
-// sweeps of a lockstep group), per radius; each has the single-shot variant of
-// the same shape (kind 1) for its geometry.
+// Batched variants of the stage-specialised sweep (the sweeps of a lockstep
+// group: forward with mode 0, the gradient's recompute with mode 1 and its
+// imaging-condition adjoint with mode 2), per radius; each has the
+// single-shot variant of the same shape and mode (kind 1) for its geometry.
 struct TMultiVariant {
-    int R, T, V, VY, BZ, BY, P, threads;
+    int R, T, V, VY, BZ, BY, P, mode, threads;
     size_t smem;  // shared memory without the plane_start slices
     cudaError_t (*launch)(int nblocks, size_t smem, cudaStream_t stream, const ShotTSweep *shots,
                           const int2 *block_map, const Stencil &st, int parity, int step);
@@ -93,9 +94,10 @@ struct ShotSlot {
 // forward kernel is chosen by timing) on a batched kernel; ckpt_every as for
 // lockstep_group.
 bool lockstep_supported(const wave_grid *g, const wave_tuning *tuning, int ckpt_every);
-// The forward kernel of a lockstep group of the n shots (out[0..7] in the
+// The kernels of a lockstep group of the n shots: forward (out[0..7] in the
 // form of wave_describe_plan, out[8] = 1; all 0 when the group runs per shot,
-// out[0] = 0 while an autotuned choice is not made yet).
+// out[0] = 0 while an autotuned choice is not made yet) and, for the
+// gradient, the recompute and adjoint phases' family and depth (out[9, 10]).
 int lockstep_describe(const wave_grid *g, int n, const wave_shot *shots, int ckpt_every,
                       const wave_tuning *tuning, int32_t *out);
 
@@ -214,27 +216,26 @@ cudaError_t launch_tsweep(int nblocks, cudaStream_t stream, const SweepArgs &a, 
     return cudaLaunchKernelEx(&cfg, tsweep_kernel<R, T, V, VY, BZ, BY, P, MB, MODE>, a, st, m);
 }
 
-template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB>
+template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB, int MODE>
 cudaError_t launch_tsweep_multi(int nblocks, size_t smem, cudaStream_t stream, const ShotTSweep *shots,
                                 const int2 *block_map, const Stencil &st, int parity, int step)
 {
-    cudaError_t e = allow_max_dynamic_smem((const void *)tsweep_multi_kernel<R, T, V, VY, BZ, BY, P, MB>);
-    if (e == cudaSuccess)
-        e = check_regsplit<TShape<R, T, V, VY, BZ, BY, P, MB, 0>>(
-            (const void *)tsweep_multi_kernel<R, T, V, VY, BZ, BY, P, MB>);
+    const void *func = (const void *)tsweep_multi_kernel<R, T, V, VY, BZ, BY, P, MB, MODE>;
+    cudaError_t e = allow_max_dynamic_smem(func);
+    if (e == cudaSuccess) e = check_regsplit<TShape<R, T, V, VY, BZ, BY, P, MB, MODE>>(func);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)nblocks);
-    cfg.blockDim = dim3((unsigned)TShape<R, T, V, VY, BZ, BY, P, MB, 0>::NTB);
+    cfg.blockDim = dim3((unsigned)TShape<R, T, V, VY, BZ, BY, P, MB, MODE>::NTB);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, tsweep_multi_kernel<R, T, V, VY, BZ, BY, P, MB>, shots, block_map, st,
-                              parity, step);
+    return cudaLaunchKernelEx(&cfg, tsweep_multi_kernel<R, T, V, VY, BZ, BY, P, MB, MODE>, shots, block_map,
+                              st, parity, step);
 }
 
 template <int R, int T, int V, int BZ, int BY, int P, int MB>
@@ -305,17 +306,17 @@ cudaError_t launch_sweep_multi(int nblocks, size_t smem, cudaStream_t stream, co
     }                                                                                             \
     }
 
-#define WAVE_TMULTI_ENTRY(R_, T_, V_, VY_, BZ_, BY_, P_, MB_)                                     \
-    {R_, T_, V_, VY_, BZ_, BY_, P_, wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, 0>::NTB,        \
-     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, 0>::SMEM,                                      \
-     &wt::launch_tsweep_multi<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>,                                 \
-     (const void *)&wt::tsweep_multi_kernel<R_, T_, V_, VY_, BZ_, BY_, P_, MB_>},
+#define WAVE_TMULTI_ENTRY(R_, T_, V_, VY_, BZ_, BY_, P_, MB_, M_)                                 \
+    {R_, T_, V_, VY_, BZ_, BY_, P_, M_, wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, M_>::NTB,   \
+     wt::TShape<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, M_>::SMEM,                                     \
+     &wt::launch_tsweep_multi<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, M_>,                             \
+     (const void *)&wt::tsweep_multi_kernel<R_, T_, V_, VY_, BZ_, BY_, P_, MB_, M_>},
 
 // the list may be empty: a zero sentinel keeps the array non-empty
 #define WAVE_DEFINE_TMULTI(r_)                                                                    \
     namespace wt {                                                                                \
     static const TMultiVariant kTMulti_r##r_[] = {WAVE_TMULTI_VARIANTS_R##r_(WAVE_TMULTI_ENTRY)   \
-                                                  {0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr, nullptr}}; \
+                                                  {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr, nullptr}}; \
     int sweep_tmulti_variants_r##r_(const TMultiVariant **out)                                    \
     {                                                                                             \
         *out = kTMulti_r##r_;                                                                     \

@@ -35,7 +35,8 @@ EXPORTED = ["wave_version", "wave_strerror", "wave_fd_coefficients", "wave_cfl_d
             "wave_autotune_stats", "wave_plan_bound",
             "wave_fwd_noalloc", "wave_measure_peaks", "wave_batch_workspace_bytes",
             "wave_fwd_batched", "wave_grad_batched", "wave_describe_batch_plan", "wave_heat",
-            "wave_grad_revolve", "wave_revolve_forward_steps", "wave_revolve_schedule", "wave_born"]
+            "wave_grad_revolve", "wave_revolve_forward_steps", "wave_revolve_schedule", "wave_born",
+            "wave_heat_ab2"]
 
 
 class WaveError(RuntimeError):
@@ -148,6 +149,8 @@ def _lib():
         lib.wave_revolve_schedule.argtypes = [i32, i32, ctypes.POINTER(i32), i32]
         lib.wave_revolve_schedule.restype = i32
         lib.wave_heat.argtypes = [gp, vp, vp, pp, vp, pp, vp, vp, tp, vp, ctypes.c_size_t, vp]
+        lib.wave_heat_ab2.argtypes = [gp, vp, vp, pp, vp, pp, vp, vp, tp, vp, ctypes.c_size_t, vp]
+        lib.wave_heat_ab2.restype = i32
         lib.wave_heat.restype = i32
         lib.wave_status.argtypes = [vp, vp]
         lib.wave_status.restype = i32
@@ -424,11 +427,9 @@ def revolve_schedule(nt, nslots):
     return [(buf[3 * i], buf[3 * i + 1], buf[3 * i + 2]) for i in range(n)]
 
 
-def heat(grid, u0, kappa=None, src_xyz=None, src_traces=None, rec_xyz=None, *, tuning=None,
-         workspace=None, stream=None):
-    """Heat (Laplace) operator, explicit Euler for u_t = kappa (lap u + f)
-    (wave_heat).  u0: initial field; kappa: diffusivity field or None for 1.
-    Returns (u^nt, rec_traces [nt][nrec], workspace)."""
+def _heat(fn, grid, u0, kappa=None, src_xyz=None, src_traces=None, rec_xyz=None, *, tuning=None,
+          workspace=None, stream=None):
+    """Marshalling shared by wave_heat and wave_heat_ab2 (same arguments)."""
     torch = _torch()
     n = tuple(grid.n)
     sp, sa = _points(src_xyz)
@@ -439,7 +440,7 @@ def heat(grid, u0, kappa=None, src_xyz=None, src_traces=None, rec_xyz=None, *, t
     ws = _workspace(workspace_bytes(grid, WAVE_OP_FWD, sp.npts, rp.npts), dev, workspace)
     g = grid.c()
     t = tuning.c() if tuning is not None else None
-    code = _lib().wave_heat(
+    code = getattr(_lib(), fn)(
         ctypes.byref(g), _dev_ptr(kappa, "kappa", n) if kappa is not None else None,
         _dev_ptr(u0, "u0", n), ctypes.byref(sp),
         _dev_ptr(src_traces, "src_traces", (grid.nt, sp.npts)) if sp.npts else None,
@@ -447,8 +448,25 @@ def heat(grid, u0, kappa=None, src_xyz=None, src_traces=None, rec_xyz=None, *, t
         ctypes.byref(t) if t is not None else None, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
         _stream(stream))
     del sa, ra
-    _check(code, "wave_heat")
+    _check(code, fn)
     return u_out, rec, ws
+
+
+def heat(grid, u0, kappa=None, src_xyz=None, src_traces=None, rec_xyz=None, *, tuning=None,
+         workspace=None, stream=None):
+    """Heat (Laplace) operator, explicit Euler for u_t = kappa (lap u + f)
+    (wave_heat).  u0: initial field; kappa: diffusivity field or None for 1.
+    Returns (u^nt, rec_traces [nt][nrec], workspace)."""
+    return _heat("wave_heat", grid, u0, kappa, src_xyz, src_traces, rec_xyz, tuning=tuning,
+                 workspace=workspace, stream=stream)
+
+
+def heat_ab2(grid, u0, kappa=None, src_xyz=None, src_traces=None, rec_xyz=None, *, tuning=None,
+             workspace=None, stream=None):
+    """The same operator by the two-step Adams-Bashforth scheme with an Euler
+    first step (wave_heat_ab2).  Returns (u^nt, rec_traces, workspace)."""
+    return _heat("wave_heat_ab2", grid, u0, kappa, src_xyz, src_traces, rec_xyz, tuning=tuning,
+                 workspace=workspace, stream=stream)
 
 
 @dataclass
@@ -484,13 +502,14 @@ def batch_workspace_bytes(grid, shots, ckpt_every=0, concurrency=0):
 
 
 def describe_batch_plan(grid, shots, ckpt_every=0, concurrency=0, tuning=None):
-    """Forward kernel of the first group of a batched call
+    """Kernels of the first group of a batched call
     (wave_describe_batch_plan): None when the shots run one by one, else the
-    keys of describe_plan plus lockstep=True (time_tile 0 while an autotuned
-    group has not been timed yet)."""
+    forward kernel as the keys of describe_plan plus lockstep=True (time_tile
+    0 while an autotuned group has not been timed yet), and for the gradient
+    grad_kernel / grad_time_tile of its recompute and adjoint phases."""
     arr, keep = _shots(shots)
     g = grid.c()
-    out = (ctypes.c_int32 * 9)()
+    out = (ctypes.c_int32 * 11)()
     t = tuning.c() if tuning is not None else None
     _check(_lib().wave_describe_batch_plan(ctypes.byref(g), len(shots), arr, int(ckpt_every), int(concurrency),
                                            ctypes.byref(t) if t else None, out), "wave_describe_batch_plan")
@@ -498,7 +517,8 @@ def describe_batch_plan(grid, shots, ckpt_every=0, concurrency=0, tuning=None):
     if out[8] == 0:
         return None
     return dict(time_tile=out[0], tile_y=out[1], tile_x=out[2], tile_z=out[3], vec=out[4],
-                prefetch=out[5], kernel=out[6], rows=out[7], lockstep=True)
+                prefetch=out[5], kernel=out[6], rows=out[7], lockstep=True,
+                grad_kernel=out[9], grad_time_tile=out[10])
 
 
 def _traces(x, name, nt, counts):

@@ -17,7 +17,7 @@ def _declared():
     for f in sorted(os.listdir(INCLUDE)):
         if f.endswith(".h"):
             src = re.sub(r"/\*.*?\*/", "", open(os.path.join(INCLUDE, f)).read(), flags=re.S)
-            names |= set(re.findall(r"\b(wave_[a-z_]+)\s*\(", src))
+            names |= set(re.findall(r"\b(wave_[a-z0-9_]+)\s*\(", src))
     return sorted(names)
 
 

@@ -246,14 +246,16 @@ def test_lockstep_staged_fwd_equals_per_shot(wavelib, cuda, so, T):
         assert torch.equal(r, d1)
 
 
-@pytest.mark.parametrize("T", [1, 2])
-def test_lockstep_staged_grad_equals_shot_order_sum(wavelib, cuda, T):
+@pytest.mark.parametrize("so,T", [(4, 1), (4, 2), (8, 1), (8, 2)])
+def test_lockstep_staged_grad_equals_shot_order_sum(wavelib, cuda, so, T):
     """Gradient groups whose forward phases (with checkpoints every k steps,
-    k a multiple of T) run on the batched stage-specialised kernel: the
-    survey gradient equals the per-shot wave_grad gradients added in shot
-    order, bit for bit."""
+    k a multiple of T) and recompute / imaging-condition phases run on
+    batched stage-specialised kernels (at so 8 and T = 2 the gradient phases
+    have a shape of their own, 32x32, beside the forward's 64x24): the survey
+    gradient equals the per-shot wave_grad gradients added in shot order, bit
+    for bit."""
     import torch
-    so, nt, k = 4, 30, 6
+    nt, k = 30, 6
     grid, h, dt, m, damp, shots, q = _survey(wavelib, so, nt, seed=17)
     rng = np.random.default_rng(4)
     res = [rng.standard_normal((nt, len(s.rec_xyz))).astype(np.float32) for s in shots]
@@ -262,6 +264,9 @@ def test_lockstep_staged_grad_equals_shot_order_sum(wavelib, cuda, T):
     g, ws = wavelib.grad_batched(grid, shots, tm, td, [_t(x, cuda) for x in q],
                                  [_t(x, cuda) for x in res], k, concurrency=2, tuning=tune)
     assert wavelib.status(ws) == wavelib.WAVE_OK
+    p = wavelib.describe_batch_plan(grid, shots, k, 2, tune)
+    assert (p["time_tile"], p["kernel"]) == (T, wavelib.WAVE_KERNEL_STAGED)
+    assert (p["grad_kernel"], p["grad_time_tile"]) == (wavelib.WAVE_KERNEL_STAGED, T)
     want = torch.zeros(grid.n, dtype=torch.float32, device=cuda)
     for s, qq, rr in zip(shots, q, res):
         w = _win(s)
