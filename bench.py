@@ -41,9 +41,9 @@ HBM_FALLBACK_GBS = 6800.0
 # profiles/traffic_tsweep_t2_so8_512.md), valid only for the kernel sources it was
 # taken on: the SHA-256 of csrc/sweep.cuh, csrc/tsweep.cuh and the radius-4
 # variant lists must match, else the bench reports null.
-TRAFFIC_SRC_SHA256 = "089368b8f2fc9c2566b43ec08f0506407be91301a132c4cad407e58474e4138a"
+TRAFFIC_SRC_SHA256 = "a52c3aedf1c1bd9ea98bb74d77059027a683d60b1a9401c87dee124cabfab908"
 TRAFFIC_BYTES = {  # ("family R T V rows BZ BY P", chunk, n) -> bytes per launch
-    ("staged R4 T2 V4 rows2 BZ64 BY24 P1", 103, (512, 512, 512)): 2532920320 + 1047564544,
+    ("staged R4 T2 V4 rows2 BZ64 BY24 P1", 103, (512, 512, 512)): 2419667456 + 1043724032,
 }
 
 
