@@ -528,7 +528,11 @@ def run_ours(args):
 
 def _fwi_gradient(dev, inputs, wave, args):
     """Forward with checkpoints + recompute + adjoint + imaging condition for
-    one 256^3 so-8 shot of 2000 steps, k = 50 (s per shot)."""
+    one 256^3 so-8 shot of 2000 steps, k = 50 (s per shot); the same gradient
+    by binomial checkpointing with 40 and 10 stored states (wave_grad_revolve:
+    s per shot, forward steps, device bytes); Born modelling of the shot along
+    the sphere the initial model lacks (wave_born: a background sweep storing
+    D and a perturbation sweep per step, 28 + 28 B per point-update)."""
     import torch
     p = inputs.c4(nt=args.fwi_nt, true_model=False)
     grid = wave.Grid(p.n, p.h, p.dt, p.nt, p.space_order)
@@ -547,10 +551,50 @@ def _fwi_gradient(dev, inputs, wave, args):
     torch.cuda.synchronize()
     ms, _ = _timed(shot, 1, torch.cuda.current_stream())
     plan = wave.describe_plan(grid, tune)
-    return {"s_per_shot": ms / 1e3, "workload": "c4: 256^3 so8, %d steps, checkpoints every %d, "
-            "forward + recompute + adjoint + imaging condition" % (p.nt, k),
-            "time_tile": plan["time_tile"],
-            "gpts_equiv": 3 * float(np.prod(p.n)) * p.nt / (ms / 1e3) / 1e9}
+    pts = float(np.prod(p.n))
+    nrec = len(p.rec_xyz)
+    out = {"s_per_shot": ms / 1e3, "workload": "c4: 256^3 so8, %d steps, checkpoints every %d, "
+           "forward + recompute + adjoint + imaging condition" % (p.nt, k),
+           "time_tile": plan["time_tile"],
+           "gpts_equiv": 3 * pts * p.nt / (ms / 1e3) / 1e9,
+           "device_bytes": wave.ckpt_bytes(grid, k) + wave.workspace_bytes(grid, wave.WAVE_OP_GRAD, 1, nrec, k)}
+
+    # the same gradient by binomial checkpointing, no forward call first
+    d, _, _, _ = wave.fwd(grid, tm, td, p.src_xyz, tq, p.rec_xyz, tuning=tune)
+    rev = []
+    for ns in (40, 10):
+        ws_r = torch.empty(wave.workspace_bytes(grid, wave.WAVE_OP_REVOLVE, 1, nrec, ns), dtype=torch.uint8,
+                           device=dev)
+
+        def shot_rev():
+            return wave.grad_revolve(grid, tm, td, p.src_xyz, tq, p.rec_xyz, d, ns, tuning=tune, workspace=ws_r)
+
+        shot_rev()
+        torch.cuda.synchronize()
+        ms_r, _ = _timed(shot_rev, 1, torch.cuda.current_stream())
+        rev.append({"slots": ns, "s_per_shot": ms_r / 1e3, "forward_steps": wave.revolve_forward_steps(p.nt, ns),
+                    "device_bytes": ws_r.numel()})
+        del ws_r
+    out["revolve"] = rev
+    out["uniform_forward_steps"] = 2 * p.nt
+
+    # Born modelling on the same shot: dm = the sphere the initial model lacks
+    pt = inputs.c4(nt=args.fwi_nt, true_model=True)
+    tdm = torch.from_numpy((pt.m - p.m).astype(np.float32)).to(dev)
+    del pt
+
+    def born():
+        return wave.born(grid, tm, td, tdm, p.src_xyz, tq, p.rec_xyz, tuning=tune)
+
+    born()
+    torch.cuda.synchronize()
+    ms_b, _ = _timed(born, 1, torch.cuda.current_stream())
+    out["born"] = {"s_per_shot": ms_b / 1e3, "gpts": pts * p.nt / (ms_b / 1e3) / 1e9,
+                   "sweep_gpts": 2 * pts * p.nt / (ms_b / 1e3) / 1e9,
+                   "dram_bytes_per_point": 56.0,
+                   "hbm_roof_gpts": _peaks()[0] / 56.0}
+    torch.cuda.empty_cache()
+    return out
 
 
 def _fwi_survey(dev, inputs, wave, args):
