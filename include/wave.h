@@ -286,8 +286,9 @@ int32_t wave_heat(const wave_grid *g, const float *kappa, const float *u0,
  * per point (read u^n, F^{n-1}, C; write u^{n+1}, F^n) and a depth-2 tile 10
  * (the new level and rate only; level n+1 stays on chip), against 12 for a
  * depth-2 leapfrog tile.  Arguments as wave_heat; depth 2 runs when compiled
- * for the order (so 2, 4, 8), no receivers are given (a depth-2 launch does
- * not store the level between its steps) and tuning->time_tile is not 1.
+ * for the order (so 2, 4, 8) and tuning->time_tile is not 1 (a depth-2
+ * launch does not store the level between its steps: its second stage
+ * records the receivers of that level from registers).
  * Stability: dt kappa |L| <= 1, else WAVE_EUNSTABLE through the status word
  * (unless WAVE_ALLOW_UNSTABLE).  Workspace: WAVE_OP_FWD. */
 int32_t wave_heat_ab2(const wave_grid *g, const float *kappa, const float *u0,

@@ -375,6 +375,40 @@ __device__ __forceinline__ void tstage_inject(float2 (&un)[VY][V / 2], const flo
             }
 }
 
+// Receiver corners of one plane from the values `val` of a thread's VY x V
+// points at global row gy and column gz, into corner row crow (entries
+// [e0, e1) of the plane's record table; warp-cooperative like
+// tstage_inject, called by whole warps; lanes with act false own no point).
+// The depth-2 Adams-Bashforth sweep records level n+1 this way, because it
+// does not store that level.
+template <int V, int VY>
+__device__ __forceinline__ void tstage_record(const float2 (&val)[VY][V / 2], const SweepArgs &a, int e0, int e1,
+                                              int gy, int gz, bool act, long long crow, int wy0, int wy1, int wz0,
+                                              int wz1)
+{
+    const int lane = threadIdx.x & 31;
+    for (int eb = e0; eb < e1; eb += 32) {
+        const int4 mine = eb + lane < e1 ? __ldg(a.rec.pts + eb + lane) : make_int4(-1, -1, 0, 0);
+        const bool rel = mine.x >= wy0 && mine.x < wy1 && mine.y >= wz0 && mine.y < wz1;
+        unsigned m = __ballot_sync(0xffffffffu, rel);
+        while (m != 0u) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1u;
+            const int px = __shfl_sync(0xffffffffu, mine.x, l), py = __shfl_sync(0xffffffffu, mine.y, l);
+            const int pz = __shfl_sync(0xffffffffu, mine.z, l), pw = __shfl_sync(0xffffffffu, mine.w, l);
+            const int v = px - gy, jj = py - gz;
+            if (!act || v < 0 || v >= VY || jj < 0 || jj >= V) continue;
+            float x = 0.f;
+#pragma unroll
+            for (int vv = 0; vv < VY; ++vv)
+#pragma unroll
+                for (int j = 0; j < V; ++j)
+                    if (vv == v && j == jj) x = (j & 1) ? val[vv][j >> 1].y : val[vv][j >> 1].x;
+            for (int itm = pz; itm < pw; ++itm) a.corner[crow + __ldg(a.rec.item + itm)] = x;
+        }
+    }
+}
+
 // The rows [y0, y1) and columns [z0, z1) that the lanes of the calling warp
 // cover with their VY x V points at (gy, gz) (whole warp).
 template <int V, int VY>
@@ -858,6 +892,11 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                         for (int v = 0; v < VY; ++v)
                             ld2<V>(fm[v], ring1 + (size_t)sc * (S::R1SLOT / 4) + S::FBOXP / 4 + off1 + v * S::W1);
                         ab2_finish<V, VY>(un, fn, cC, fm, q[R], 1.5f, -0.5f);
+                        // level n+1 is not stored: its receivers are recorded
+                        // here, from the queue centre (this stage's own points)
+                        if (any_rec && frec[cs - pbase])
+                            tstage_record<V, VY>(q[R], a, prec[cs - pbase], prec[cs - pbase + 1], gy, gz, act,
+                                                 (long long)a.c_row0 * a.nslot, wy0, wy1, wz0, wz1);
                     } else if (any_inj && finj[cs - pbase]) {
                         tstage_inject<V, VY, DD1>(un, cC, a, pinj[cs - pbase], pinj[cs - pbase + 1], gy, gz,
                                                   a.q_row0 + a.q_dir, wy0, wy1, wz0, wz1, dd);
@@ -866,8 +905,8 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                     for (int v = 0; v < VY; ++v)
                         if (sok[v]) {
                             st2<V>(oh + (long long)v * a.nz, un[v]);
-                            // level n+1, or with AB the rate F^{n+1} (level n+1 is
-                            // not kept: no receiver reads it, see the host)
+                            // level n+1, or with AB the rate F^{n+1} (level n+1
+                            // is not kept; its receivers were recorded above)
                             if constexpr (S::AB)
                                 st2<V>(ol + (long long)v * a.nz, fn[v]);
                             else
@@ -904,9 +943,9 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
         }
     }
 
-    // Receiver corners of the stored levels (T: out_hi, T-1: out_lo), once
-    // the block's own points are written, shared out over the threads of the
-    // last stage (see sweep_block).
+    // Receiver corners of the stored levels (T: out_hi, T-1: out_lo; AB: T
+    // only), once the block's own points are written, shared out over the
+    // threads of the last stage (see sweep_block).
     constexpr int NL = T == 2 ? S::N2 : S::N1;  // threads of the last stage
     const int tl = T == 2 ? tid - S::N1 : tid;
     if (any_rec && tl >= 0 && tl < NL) {
@@ -923,7 +962,7 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
             if (pt.x < ty0 || pt.x >= ty0 + BY || pt.y < tz0 || pt.y >= tz0 + BZ) continue;
             const long long pix = (long long)(pbase + lo) * a.sx + (long long)pt.x * a.nz + pt.y;
 #pragma unroll
-            for (int sg = (T > 1 ? T - 1 : 1); sg <= T; ++sg) {
+            for (int sg = (T > 1 && !S::AB ? T - 1 : T); sg <= T; ++sg) {
                 const float v = (sg == T ? a.out_hi : a.out_lo)[pix];  // written by this block
                 const long long crow = (long long)(a.c_row0 + a.c_dir * (sg - 1)) * a.nslot;
                 for (int itm = pt.z; itm < pt.w; ++itm) a.corner[crow + __ldg(a.rec.item + itm)] = v;

@@ -2959,11 +2959,10 @@ int32_t wave_heat_ab2(const wave_grid *g, const float *kappa, const float *u0, c
         if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
         HostTable ti, tr;
         if (build_table(d, g->h, src, false, &ti) || build_table(d, g->h, rec, true, &tr)) return WAVE_EINVAL;
-        // depth: 2 where compiled and no receiver needs the intermediate level
-        // (a depth-2 launch stores the new level and rate, not the level
-        // between), else 1; tuning->time_tile 1 asks for the untiled sweep
+        // depth 2 where compiled, else 1; tuning->time_tile 1 asks for the
+        // untiled sweep
         const int want = tuning != nullptr && tuning->time_tile == 1 ? 1 : 2;
-        const int T = (want == 2 && nrec == 0 && ab2_variant(R, 2) != nullptr) ? 2 : 1;
+        const int T = (want == 2 && ab2_variant(R, 2) != nullptr) ? 2 : 1;
         Plan plan;
         plan.v = ab2_variant(R, T);
         if (plan.v == nullptr) return WAVE_EUNSUPPORTED;
