@@ -104,9 +104,12 @@ struct TShape {
     // L2 prefetch distance in iterations (0: none).  With one slot of
     // lookahead (P = 1) a ring-A load is issued about one iteration before
     // its use, which does not cover HBM latency, so its inputs are first
-    // brought into L2 four iterations ahead; with P >= 2 the ring itself
+    // brought into L2 a few iterations ahead: fewer as an iteration gets
+    // longer with the radius (measured on the 512^3 depth-2 tiles, GPts/s at
+    // distances 1 / 2 / 3 / 4: so 2 481 / 498 / 503 / 492, so 4 451 / 460 /
+    // 452 / 449, so 8 372 / 368 / 364 / 366); with P >= 2 the ring itself
     // covers the latency and the extra requests only cost.
-    static constexpr int LP = P == 1 ? 4 : 0;
+    static constexpr int LP = P == 1 ? (R == 1 ? 3 : R == 2 ? 2 : 1) : 0;
     static constexpr int DA = P + 1;                      // ring A slots
     static constexpr int DB = T == 2 ? P + 1 : 0;         // ring B slots
     static constexpr int D1 = T == 2 ? R + 3 : 0;         // ring 1 planes

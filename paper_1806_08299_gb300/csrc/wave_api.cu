@@ -304,6 +304,8 @@ struct Layout {
     DevTable inj, rec, inj2;
     float *corner = nullptr;
     int *order = nullptr;    // launch order of the sweep's blocks (order_cap entries)
+    int *order_b = nullptr;  // GRAD, REVOLVE, BORN: a second order buffer (the other jobs of the call)
+    int *order_c = nullptr;  // REVOLVE: a third
     long long order_cap = 0;
     size_t bytes = 0;
 };
@@ -353,6 +355,9 @@ Layout carve(void *ws, size_t cap, bool dry, const Dims &d, int op, int nsrc, in
         // x-chunks can make
         L.order_cap = (long long)((d.nzp + 31) / 32) * ((d.ny + 7) / 8) * d.nx;
         L.order = c.take<int>((size_t)L.order_cap);
+        if (op == WAVE_OP_GRAD || op == WAVE_OP_REVOLVE || op == WAVE_OP_BORN)
+            L.order_b = c.take<int>((size_t)L.order_cap);
+        if (op == WAVE_OP_REVOLVE) L.order_c = c.take<int>((size_t)L.order_cap);
     }
     L.bytes = c.off;
     return L;
@@ -626,6 +631,17 @@ TuneKey tune_key(const Dims &d, int so, int T)
 
 // What one run of consecutive steps injects, records and stores.  Every row
 // index is "base + dir * j" for local step j of the run (j = 0 first).
+// The heavy-first launch order a job's order buffer holds: the launch shape
+// it was computed for.  A caller that runs one job in many short run_steps
+// calls (one step each) keeps one of these per job and order buffer, so that
+// the order is computed and uploaded once, not per call (an upload from
+// pageable host memory first waits for the stream to drain).
+struct OrderCache {
+    const SweepVariant *v = nullptr;
+    int chunk = 0;
+    bool ordered = false;
+};
+
 struct Job {
     Dims d;
     Stencil st;
@@ -653,6 +669,7 @@ struct Job {
     const HostTable *hinj = nullptr, *hrec = nullptr;
     int *order = nullptr;
     long long order_cap = 0;
+    OrderCache *ocache = nullptr;  // kept across run_steps calls (the order buffer is this job's alone)
 };
 
 // Events around the sweep launches of the last timed call on this thread.
@@ -900,9 +917,8 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
 {
     const Dims &d = job.d;
     const int R = plan.v->R;
-    const SweepVariant *ov = nullptr;  // launch shape the order buffer holds
-    int ochunk = 0;
-    bool ordered = false;
+    OrderCache own;  // launch shape the order buffer holds
+    OrderCache &oc = job.ocache != nullptr ? *job.ocache : own;
     int j = 0;
     while (j <= nsteps) {
         if (ckpt != nullptr && (j0 + j) % ckpt_every == 0 && j < nsteps) {
@@ -962,17 +978,17 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         long long nblocks = 0;
         int rc = build_launch(job, s, j, v, chunk, &a, &maps, &tmaps, &nblocks);
         if (rc) return rc;
-        if (job.order != nullptr && (v != ov || chunk != ochunk)) {
-            ov = v;
-            ochunk = chunk;
+        if (job.order != nullptr && (v != oc.v || chunk != oc.chunk)) {
+            oc.v = v;
+            oc.chunk = chunk;
             std::vector<int> ord;
             heavy_first_order(d, v, chunk, job.hinj, job.hrec, &ord);
-            ordered = !ord.empty() && (long long)ord.size() == nblocks && nblocks <= job.order_cap;
-            if (ordered)
+            oc.ordered = !ord.empty() && (long long)ord.size() == nblocks && nblocks <= job.order_cap;
+            if (oc.ordered)
                 CK(cudaMemcpyAsync(job.order, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice,
                                    stream));
         }
-        a.order = ordered ? job.order : nullptr;
+        a.order = oc.ordered ? job.order : nullptr;
         if (v->kind == 1)
             CK(v->launch_t((int)nblocks, stream, a, job.st, tmaps));
         else
@@ -2563,6 +2579,9 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
         for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.V[i], 0, sizeof(float) * d.npad, stream));
         State adj;
         for (int i = 0; i < 4; ++i) adj.buf[i] = L.V[i];
+        // the recompute and adjoint jobs keep their launch orders across
+        // segments, each in its own buffer
+        OrderCache ocr, oca;
         const int nseg = (nt + ckpt_every - 1) / ckpt_every;
         if ((rc = prof_begin(tuning, stream))) return rc;
         for (int c = nseg - 1; c >= 0; --c) {
@@ -2596,6 +2615,7 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
             rj.hinj = &ts;
             rj.order = L.order;
             rj.order_cap = L.order_cap;
+            rj.ocache = &ocr;
             if ((rc = run_steps(rj, fw, len, plan, stream))) return rc;
             // 2) adjoint over the segment, newest step first: reversed step
             //    for n = s0+len-1 .. s0 produces nu^{n+1}, injects res^n and
@@ -2617,8 +2637,9 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
             aj.l_dir = -1;
             aj.gacc = L.G;
             aj.hinj = &tr;
-            aj.order = L.order;
+            aj.order = L.order_b;
             aj.order_cap = L.order_cap;
+            aj.ocache = &oca;
             if ((rc = run_steps(aj, adj, len, plan, stream))) return rc;
         }
         if ((rc = prof_end(stream))) return rc;
@@ -2699,8 +2720,11 @@ int32_t wave_born(const wave_grid *g, const float *m, const float *damp, const f
         pj.l_dir = 0;
         pj.born = L.G;
         pj.hrec = &tr;
-        pj.order = L.order;
+        pj.order = L.order_b;
         pj.order_cap = L.order_cap;
+        OrderCache ocb, ocp;  // each job's launch order, computed once for its many one-step calls
+        bj.ocache = &ocb;
+        pj.ocache = &ocp;
         if ((rc = prof_begin(tuning, stream))) return rc;
         for (int n = 0; n < nt; ++n) {
             bj.q_base = n;
@@ -2792,6 +2816,49 @@ int32_t wave_grad_revolve(const wave_grid *g, const float *m, const float *damp,
             adj.buf[i] = L.V[i];
         }
         const size_t lvl = sizeof(float) * d.npad;
+        // the three jobs of the schedule, each with its own launch-order
+        // buffer kept across its many short calls
+        Job fj;  // forward advance
+        fj.d = d;
+        fj.st = st;
+        fj.cB = L.cB;
+        fj.cC = L.cC;
+        fj.status = L.status;
+        fj.inj = L.inj.view();
+        fj.q = src_traces;
+        fj.nq = nsrc;
+        fj.q_dir = 1;
+        fj.hinj = &ts;
+        fj.order = L.order;
+        fj.order_cap = L.order_cap;
+        Job rj = fj;  // one recompute step from u^a storing D^a
+        rj.cE = L.cE;
+        rj.dstore = L.store;
+        rj.d_base = 0;
+        rj.d_dir = 1;
+        rj.order = L.order_b;
+        Job aj;  // the adjoint step of time index a: nu^{a+1}, res^a, G += nu^{a+1} D^a
+        aj.d = d;
+        aj.st = st;
+        aj.cB = L.cB;
+        aj.cC = L.cC;
+        aj.status = L.status;
+        aj.inj = L.inj2.view();
+        aj.q = rec_resid;
+        aj.nq = nrec;
+        aj.q_dir = -1;
+        aj.dload = L.store;
+        aj.l_rows = 1;
+        aj.l_base = 0;
+        aj.l_dir = -1;
+        aj.gacc = L.G;
+        aj.hinj = &tr;
+        aj.order = L.order_c;
+        aj.order_cap = L.order_cap;
+        OrderCache ocf, ocr, oca;
+        fj.ocache = &ocf;
+        rj.ocache = &ocr;
+        aj.ocache = &oca;
         if ((rc = prof_begin(tuning, stream))) return rc;
         for (const RevAction &x : sched) {
             if (x.kind == REV_RESTORE) {
@@ -2810,62 +2877,12 @@ int32_t wave_grad_revolve(const wave_grid *g, const float *m, const float *damp,
                 CK(cudaMemcpyAsync(sp, fw.buf[fw.a], lvl, cudaMemcpyDeviceToDevice, stream));
                 CK(cudaMemcpyAsync(sp + d.npad, fw.buf[fw.b], lvl, cudaMemcpyDeviceToDevice, stream));
             } else if (x.kind == REV_ADVANCE) {
-                Job fj;
-                fj.d = d;
-                fj.st = st;
-                fj.cB = L.cB;
-                fj.cC = L.cC;
-                fj.status = L.status;
-                fj.inj = L.inj.view();
-                fj.q = src_traces;
-                fj.nq = nsrc;
                 fj.q_base = x.a;
-                fj.q_dir = 1;
-                fj.hinj = &ts;
-                fj.order = L.order;
-                fj.order_cap = L.order_cap;
                 if ((rc = run_steps(fj, fw, x.b - x.a, fplan, stream))) return rc;
             } else {
-                // one recompute step from u^a storing D^a, then the adjoint
-                // step of time index a (nu^{a+1}, res^a, G += nu^{a+1} D^a)
-                Job rj;
-                rj.d = d;
-                rj.st = st;
-                rj.cB = L.cB;
-                rj.cC = L.cC;
-                rj.status = L.status;
-                rj.cE = L.cE;
-                rj.inj = L.inj.view();
-                rj.q = src_traces;
-                rj.nq = nsrc;
                 rj.q_base = x.a;
-                rj.q_dir = 1;
-                rj.dstore = L.store;
-                rj.d_base = 0;
-                rj.d_dir = 1;
-                rj.hinj = &ts;
-                rj.order = L.order;
-                rj.order_cap = L.order_cap;
                 if ((rc = run_steps(rj, fw, 1, gplan, stream))) return rc;
-                Job aj;
-                aj.d = d;
-                aj.st = st;
-                aj.cB = L.cB;
-                aj.cC = L.cC;
-                aj.status = L.status;
-                aj.inj = L.inj2.view();
-                aj.q = rec_resid;
-                aj.nq = nrec;
                 aj.q_base = x.a;
-                aj.q_dir = -1;
-                aj.dload = L.store;
-                aj.l_rows = 1;
-                aj.l_base = 0;
-                aj.l_dir = -1;
-                aj.gacc = L.G;
-                aj.hinj = &tr;
-                aj.order = L.order;
-                aj.order_cap = L.order_cap;
                 if ((rc = run_steps(aj, adj, 1, gplan, stream))) return rc;
             }
         }
