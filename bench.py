@@ -41,9 +41,9 @@ HBM_FALLBACK_GBS = 6800.0
 # profiles/traffic_tsweep_t2_so8_512.md), valid only for the kernel sources it was
 # taken on: the SHA-256 of csrc/sweep.cuh, csrc/tsweep.cuh and the radius-4
 # variant lists must match, else the bench reports null.
-TRAFFIC_SRC_SHA256 = "a52c3aedf1c1bd9ea98bb74d77059027a683d60b1a9401c87dee124cabfab908"
+TRAFFIC_SRC_SHA256 = "7728b342cdcbe7b013ea9af4e8b0bde4655463a8369301be8f890227a72a7fdb"
 TRAFFIC_BYTES = {  # ("family R T V rows BZ BY P", chunk, n) -> bytes per launch
-    ("staged R4 T2 V4 rows2 BZ64 BY24 P1", 103, (512, 512, 512)): 2419667456 + 1043724032,
+    ("staged R4 T2 V4 rows2 BZ64 BY24 P1", 103, (512, 512, 512)): 2366497280 + 1045686272,
 }
 
 
