@@ -531,8 +531,9 @@ def _fwi_gradient(dev, inputs, wave, args):
     one 256^3 so-8 shot of 2000 steps, k = 50 (s per shot); the same gradient
     by binomial checkpointing with 40 and 10 stored states (wave_grad_revolve:
     s per shot, forward steps, device bytes); Born modelling of the shot along
-    the sphere the initial model lacks (wave_born: a background sweep storing
-    D and a perturbation sweep per step, 28 + 28 B per point-update)."""
+    the sphere the initial model lacks (wave_born: both fields in one fused
+    sweep per step, 40 B per point-update; and the two-sweep form, a
+    background sweep storing D and a perturbation sweep, 28 + 28 B)."""
     import torch
     p = inputs.c4(nt=args.fwi_nt, true_model=False)
     grid = wave.Grid(p.n, p.h, p.dt, p.nt, p.space_order)
@@ -589,10 +590,21 @@ def _fwi_gradient(dev, inputs, wave, args):
     born()
     torch.cuda.synchronize()
     ms_b, _ = _timed(born, 1, torch.cuda.current_stream())
-    out["born"] = {"s_per_shot": ms_b / 1e3, "gpts": pts * p.nt / (ms_b / 1e3) / 1e9,
-                   "sweep_gpts": 2 * pts * p.nt / (ms_b / 1e3) / 1e9,
-                   "dram_bytes_per_point": 56.0,
-                   "hbm_roof_gpts": _peaks()[0] / 56.0}
+    gpts_b = pts * p.nt / (ms_b / 1e3) / 1e9
+    out["born"] = {"s_per_shot": ms_b / 1e3, "gpts": gpts_b, "kernel": "fused (one sweep per step)",
+                   "dram_bytes_per_point": 40.0, "hbm_roof_gpts": _peaks()[0] / 40.0,
+                   "frac_hbm": gpts_b * 40.0 / _peaks()[0]}
+
+    def born2():
+        return wave.born(grid, tm, td, tdm, p.src_xyz, tq, p.rec_xyz,
+                         tuning=wave.Tuning(time_tile=0, flags=wave.WAVE_BORN_TWO_SWEEPS))
+
+    born2()
+    torch.cuda.synchronize()
+    ms_b2, _ = _timed(born2, 1, torch.cuda.current_stream())
+    gpts_b2 = pts * p.nt / (ms_b2 / 1e3) / 1e9
+    out["born_two_sweeps"] = {"s_per_shot": ms_b2 / 1e3, "gpts": gpts_b2, "dram_bytes_per_point": 56.0,
+                              "frac_hbm": gpts_b2 * 56.0 / _peaks()[0]}
     torch.cuda.empty_cache()
     return out
 
@@ -780,8 +792,10 @@ def _laplace_sweep(dev, inputs, wave, args):
                 wave.heat_ab2(grid2, tu, None, None, None, None, tuning=t, workspace=ws)
                 st = wave.sweep_stats()
                 best, launches = min(best, st[0]), st[1]
-            return {"gpts": pts / (best / 1e3) / 1e9, "launches_per_call": launches,
-                    "dram_bytes_per_point": 20.0 if T == 1 else 10.0}
+            gpts = pts / (best / 1e3) / 1e9
+            bpp = 20.0 if T == 1 else 10.0
+            return {"gpts": gpts, "launches_per_call": launches, "dram_bytes_per_point": bpp,
+                    "frac_hbm": gpts * bpp / _peaks()[0]}
 
         ab1 = ab2_at(1)
         ab = {"untiled": ab1}

@@ -72,6 +72,9 @@ extern "C" {
                                  (read back with wave_sweep_stats)                       */
 #define WAVE_AUTOTUNE_SHAPE 4 /* with time_tile = T >= 1: time the compiled variants of
                                  depth T (tile, vec, x-chunk) and keep the fastest       */
+#define WAVE_BORN_TWO_SWEEPS 8 /* wave_born: the background and perturbation sweeps as two
+                                 launches per step (the form of every order) instead of
+                                 the fused sweep                                        */
 #define WAVE_TEST_WITHHOLD 256 /* test hook: the sweep's producer issues no loads, so
                                  every bounded wait of the call runs out (about 2 s per
                                  launch) and wave_status reports WAVE_ETIMEOUT; the
@@ -222,9 +225,14 @@ int32_t wave_grad_revolve(const wave_grid *g, const float *m, const float *damp,
  * background wavefield u (sources as wave_fwd) and alpha = 1 / (m + eta),
  *   du^{n+1} = alpha (2 m du^n - (m - eta) du^{n-1} + dt^2 L du^n) - alpha dm D^n,
  *   du^0 = du^-1 = 0,   rec_traces[n][r] = sum_p w_{r,p} du^{n+1}[p].
- * Its adjoint is wave_grad: <born(dm), r> = <dm, grad(r)>.  Each step runs
- * the background sweep, storing D^n, then the perturbation sweep, which
- * adds C (P D^n) with P = -dm / dt^2 (C = alpha dt^2) to its new level.
+ * Its adjoint is wave_grad: <born(dm), r> = <dm, grad(r)>.  Each step
+ * advances both fields in one fused sweep (where compiled for the order):
+ * the background with D^n kept in registers, the perturbation adding
+ * C (P D^n) with P = -dm / dt^2 (C = alpha dt^2) to its new level, reading
+ * u^n, u^{n-1}, du^n, du^{n-1}, B, C, E, P and writing two levels (40 B per
+ * point-update).  With WAVE_BORN_TWO_SWEEPS, or at an order without the
+ * fused sweep, the background sweep stores D^n and a second sweep runs the
+ * perturbation (56 B); both forms give the same bits.
  *   m, damp, dm  device [nx][ny][nz]
  *   src / src_traces, rec   as wave_fwd
  *   rec_traces   device [nt][nrec] out (linearised data)

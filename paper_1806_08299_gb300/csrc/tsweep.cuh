@@ -67,6 +67,8 @@ struct TMaps {
     //   MODE 3: T = 1: x0 = D row l_row0, x1 = P (Born source coefficient)
     //   MODE 4 (two-step Adams-Bashforth heat): um is the rate F^{n-1}; B and
     //           the stage-2 boxes u2, B2 are not loaded
+    //   MODE 5 (fused Born, T = 1): x0 = E, x1 = P; the perturbation field's
+    //           centre box y0 (WC x HC), its level n y1 and n-1 y2 (W1 x H1)
     // The D maps cover the whole store [rows][nx][ny][nzp] as one tensor of
     // rows * nx planes: row r, plane x is plane r * nx + x.  Every D box lies
     // in [X0, X1) in x, so none reaches into a neighbouring row, and one map
@@ -114,19 +116,22 @@ struct TShape {
     static constexpr int DB = T == 2 ? P + 1 : 0;         // ring B slots
     static constexpr int D1 = T == 2 ? R + 3 : 0;         // ring 1 planes
     static constexpr bool AB = MODE == 4;                 // two-step Adams-Bashforth (heat)
+    static constexpr bool FB = MODE == 5;                 // fused Born: background and perturbation
     static constexpr unsigned CBOX = WC * HC * 4, FBOX = W1 * H1 * 4, SBOX = BZ * BY * 4;
     static constexpr unsigned CBOXP = (CBOX + 127) / 128 * 128;
     static constexpr unsigned FBOXP = (FBOX + 127) / 128 * 128;
     static constexpr unsigned SBOXP = (SBOX + 127) / 128 * 128;
     // extra boxes of the gradient modes per ring-A / ring-B slot
     static constexpr int XA =
-        (MODE == 0 || MODE == 4) ? 0 : (T == 1 ? (MODE == 3 ? 2 : MODE) : (MODE == 1 ? 1 : 0));
+        (MODE == 0 || MODE == 4) ? 0 : (T == 1 ? (MODE >= 3 ? 2 : MODE) : (MODE == 1 ? 1 : 0));
     static constexpr int XBB = T == 2 ? (MODE == 1 ? 1 : (MODE == 2 ? 3 : 0)) : 0;
     // ring A slot: centre box, level n (queue feed), level n-1, B, C, [x0, x1]
     // (AB: the rate F^{n-1} in the level n-1 box, no B box)
+    // (FB: then the perturbation's centre box, level n and level n-1)
     static constexpr unsigned A_C = 0, A_F = CBOXP, A_UM = A_F + FBOXP, A_B = AB ? A_UM : A_UM + FBOXP,
                               A_CC = A_B + FBOXP, A_X0 = A_CC + FBOXP, A_X1 = A_X0 + FBOXP,
-                              ASLOT = A_X0 + XA * FBOXP;
+                              A_C2 = A_X0 + XA * FBOXP, A_F2 = A_C2 + CBOXP, A_UM2 = A_F2 + FBOXP,
+                              ASLOT = FB ? A_UM2 + FBOXP : A_X0 + XA * FBOXP;
     // ring B slot: level n, B, C over the output tile, [y0, y1, y2] (AB: C only)
     static constexpr unsigned B_UM = 0, B_B = AB ? 0 : SBOXP, B_C = AB ? 0 : 2 * SBOXP, B_Y0 = 3 * SBOXP,
                               B_Y1 = 4 * SBOXP, B_Y2 = 5 * SBOXP, BSLOT = AB ? SBOXP : (3 + XBB) * SBOXP;
@@ -138,8 +143,9 @@ struct TShape {
     static constexpr size_t OFF_P = OFF_BAR + 8 * (2 * DA + 2 * DB + 2 * D1) + 16;
     static constexpr size_t SMEM = OFF_P;                 // + per-plane sparse slices
     static size_t smem_bytes(int chunk) { return OFF_P + sweep_table_bytes(chunk, RT) + 16; }
-    static constexpr unsigned TXA = CBOX + ((AB ? 3 : 4) + XA) * FBOX;  // bytes of a ring-A slot from iteration 2R on
-    static constexpr unsigned TXF = FBOX;                    // before (queue fill only)
+    static constexpr unsigned TXA = CBOX + ((AB ? 3 : 4) + XA) * FBOX + (FB ? CBOX + 2 * FBOX : 0);  // bytes of a
+                                                             // ring-A slot from iteration 2R on
+    static constexpr unsigned TXF = (FB ? 2 : 1) * FBOX;     // before (queue fill only)
     static constexpr unsigned TXB = (AB ? 1 : 3 + XBB) * SBOX;
     static_assert(T == 1 || T == 2, "stage-specialised sweep: T = 1 or 2");
     static_assert(V == 4, "four z points per thread (two pairs)");
@@ -158,9 +164,9 @@ struct TShape {
                               (long long)CREG * (N1 + N2) + (long long)PREG * NP <= (long long)LREG * NTB &&
                               ((N1 + N2) / 128 * CREG + PREG) * 32 <= 16384),
                   "register split does not fit");
-    static_assert(MODE >= 0 && MODE <= 4 && (MODE != 3 || T == 1),
+    static_assert(MODE >= 0 && MODE <= 5 && ((MODE != 3 && MODE != 5) || T == 1),
                   "mode: 0 plain, 1 second differences, 2 imaging condition, 3 Born source (T = 1), "
-                  "4 two-step Adams-Bashforth");
+                  "4 two-step Adams-Bashforth, 5 fused Born (T = 1)");
 };
 
 // Level n+1 of a thread's VY x V points (VY rows, V/2 pairs each) from the
@@ -451,7 +457,9 @@ __device__ __forceinline__ void tstage_abort(volatile int *abort_flag, int *stat
 // u + C (3/2 F - 1/2 F_prev) (stage 1 with the launch's weights ab1, ab0,
 // which start the scheme with an Euler step), hands F to stage 2 beside its
 // level through ring 1, and the last stage stores the new level (out_hi)
-// and its rate (out_lo).
+// and its rate (out_lo).  MODE 5 (fused Born, T = 1): MODE 1 and MODE 3 in
+// one pass, the background level n+1 to out_hi (its D kept in registers)
+// and the perturbation's to out_lo; the receivers record the perturbation.
 template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB, int MODE>
 __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &st, const TMaps &mp,
                                              const int blk)
@@ -573,7 +581,7 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
         const int lane = tid - (S::N1 + S::N2);  // lanes 0 and 1 of the first producer warp work
         if (a.withhold) return;
         // plane offsets of this launch's D rows in the store tensor (MODE 2, 3)
-        const int xrow = (T == 1 && MODE >= 2) ? (int)(a.l_row0 * a.nx) : 0;
+        const int xrow = (T == 1 && (MODE == 2 || MODE == 3)) ? (int)(a.l_row0 * a.nx) : 0;
         const int yrow0 = (T == 2 && MODE == 2) ? (int)(a.l_row0 * a.nx) : 0;
         const int yrow1 = (T == 2 && MODE == 2) ? (int)((a.l_row0 + a.l_dir) * a.nx) : 0;
         if (lane == 0) {
@@ -590,6 +598,7 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                 const bool full_slot = i >= 2 * R;
                 mbar_expect_tx(fullA + s, full_slot ? S::TXA : S::TXF);
                 tma_load_3d(sl + S::A_F, &mp.uf, gz0, gy0, c0, fullA + s);
+                if constexpr (S::FB) tma_load_3d(sl + S::A_F2, &mp.y1, gz0, gy0, c0, fullA + s);
                 if (full_slot) {
                     tma_load_3d(sl + S::A_C, &mp.uc, gz0 - S::RP, gy0 - R, c0 - R, fullA + s);
                     tma_load_3d(sl + S::A_UM, &mp.um, gz0, gy0, c0 - R, fullA + s);
@@ -597,6 +606,10 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                     tma_load_3d(sl + S::A_CC, &mp.C, gz0, gy0, c0 - R, fullA + s);
                     if constexpr (S::XA >= 1) tma_load_3d(sl + S::A_X0, &mp.x0, gz0, gy0, c0 - R + xrow, fullA + s);
                     if constexpr (S::XA >= 2) tma_load_3d(sl + S::A_X1, &mp.x1, gz0, gy0, c0 - R, fullA + s);
+                    if constexpr (S::FB) {
+                        tma_load_3d(sl + S::A_C2, &mp.y0, gz0 - S::RP, gy0 - R, c0 - R, fullA + s);
+                        tma_load_3d(sl + S::A_UM2, &mp.y2, gz0, gy0, c0 - R, fullA + s);
+                    }
                 }
                 // bring the first-touch inputs of iteration i + LP into L2, so
                 // that its loads above wait for L2 rather than HBM (the centre
@@ -667,19 +680,26 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
         int wy0, wy1, wz0, wz1;  // the warp's rows and columns (injection scan)
         warp_extent<V, VY>(gy, gz, wy0, wy1, wz0, wz1);
         float2 q[QL][VY][V2];
+        float2 qb[S::FB ? QL : 1][VY][V2];  // FB: the perturbation's x-queue
 #pragma unroll
         for (int k = 0; k < QL; ++k)
 #pragma unroll
             for (int v = 0; v < VY; ++v)
 #pragma unroll
                 for (int j = 0; j < V2; ++j) q[k][v][j] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < (S::FB ? QL : 1); ++k)
+#pragma unroll
+            for (int v = 0; v < VY; ++v)
+#pragma unroll
+                for (int j = 0; j < V2; ++j) qb[k][v][j] = make_float2(0.f, 0.f);
         // T = 1: stage 1 writes level n+1 of its own points (planes [X0, X1)),
-        // and with AB the rate F^n beside it
+        // and with AB the rate F^n beside it (FB: the perturbation's level)
         float *outp = nullptr, *outf = nullptr;
         bool sok[VY];
         if constexpr (T == 1) {
             outp = a.out_hi + ((long long)X0 * a.sx + (long long)gy * a.nz + gz);
-            if constexpr (S::AB) outf = a.out_lo + ((long long)X0 * a.sx + (long long)gy * a.nz + gz);
+            if constexpr (S::AB || S::FB) outf = a.out_lo + ((long long)X0 * a.sx + (long long)gy * a.nz + gz);
 #pragma unroll
             for (int v = 0; v < VY; ++v) sok[v] = act && gy + v < a.ny && gz < a.nz;
         }
@@ -704,13 +724,23 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                     for (int j = 0; j < V2; ++j) q[k][v][j] = q[k + 1][v][j];
 #pragma unroll
             for (int v = 0; v < VY; ++v) ld2<V>(q[QL - 1][v], sl + S::A_F / 4 + offF + v * S::W1);
+            if constexpr (S::FB) {
+#pragma unroll
+                for (int k = 0; k < QL - 1; ++k)
+#pragma unroll
+                    for (int v = 0; v < VY; ++v)
+#pragma unroll
+                        for (int j = 0; j < V2; ++j) qb[k][v][j] = qb[k + 1][v][j];
+#pragma unroll
+                for (int v = 0; v < VY; ++v) ld2<V>(qb[QL - 1][v], sl + S::A_F2 / 4 + offF + v * S::W1);
+            }
             if (i >= 2 * R) {
                 float2 un[VY][V2], cC[VY][V2];
                 const int cs = c00 + i - R;  // plane of level n+1
                 // gradient modes: the points of this plane the stage owns (T = 1:
                 // the tile; T = 2: the tile inside the stage-1 region, stage 1's
                 // second differences only), their index and E or D, G
-                constexpr bool DD1 = MODE == 1;
+                constexpr bool DD1 = MODE == 1 || MODE == 5;  // FB: the background's D, in registers
                 bool own[VY];
                 long long pix = 0;
                 float2 ex[VY][V2], dd[VY][V2];
@@ -773,15 +803,33 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
                             un[v][j] = __ffma2_rn(cC[v][j], __fmul2_rn(pb[j], ex[v][j]), un[v][j]);
                     }
                 }
+                float2 vn[VY][V2];  // FB: the perturbation's new level
+                if constexpr (S::FB) {
+                    // the perturbation sweep of MODE 3 on this plane, with the
+                    // background's D from registers instead of a stored row
+                    float2 cC2[VY][V2];
+                    tstage_update<R, V, VY, S::WC, S::W1>(vn, cC2, qb, sl + S::A_C2 / 4 + offC,
+                                                          sl + S::A_UM2 / 4 + offF, sl + S::A_B / 4 + offF,
+                                                          sl + S::A_CC / 4 + offF, st);
+#pragma unroll
+                    for (int v = 0; v < VY; ++v) {
+                        float2 pb[V2];
+                        ld2<V>(pb, sl + S::A_X1 / 4 + offF + v * S::W1);
+#pragma unroll
+                        for (int j = 0; j < V2; ++j)
+                            vn[v][j] = __ffma2_rn(cC2[v][j], __fmul2_rn(pb[j], dd[v][j]), vn[v][j]);
+                    }
+                }
                 if constexpr (T == 1) {
 #pragma unroll
                     for (int v = 0; v < VY; ++v)
                         if (sok[v]) {
                             st2<V>(outp + (long long)v * a.nz, un[v]);
                             if constexpr (S::AB) st2<V>(outf + (long long)v * a.nz, fn[v]);
+                            if constexpr (S::FB) st2<V>(outf + (long long)v * a.nz, vn[v]);
                         }
                     outp += a.sx;
-                    if constexpr (S::AB) outf += a.sx;
+                    if constexpr (S::AB || S::FB) outf += a.sx;
                 } else {
                     // hand the plane to stage 2 through ring 1
                     if (r1 > 0 && !__all_sync(FULL, mbar_wait_bounded(empty1 + s1, (uint32_t)((r1 - 1) & 1)))) {
@@ -966,7 +1014,8 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
             const long long pix = (long long)(pbase + lo) * a.sx + (long long)pt.x * a.nz + pt.y;
 #pragma unroll
             for (int sg = (T > 1 && !S::AB ? T - 1 : T); sg <= T; ++sg) {
-                const float v = (sg == T ? a.out_hi : a.out_lo)[pix];  // written by this block
+                // written by this block (FB: the perturbation's level)
+                const float v = (sg == T && !S::FB ? a.out_hi : a.out_lo)[pix];
                 const long long crow = (long long)(a.c_row0 + a.c_dir * (sg - 1)) * a.nslot;
                 for (int itm = pt.z; itm < pt.w; ++itm) a.corner[crow + __ldg(a.rec.item + itm)] = v;
             }

@@ -95,22 +95,26 @@
 // TMA) has one untiled shape per radius, the only kernel that runs it.
 // MODE 4 (the two-step Adams-Bashforth heat operator: the rate F in place of
 // level n-1, handed to stage 2 beside level n+1) has untiled and depth-2
-// shapes at so 2, 4 and 8 and an untiled one at so 16.
+// shapes at so 2, 4 and 8 and an untiled one at so 16.  MODE 5 (the fused
+// Born sweep: background and perturbation fields in one pass, two x-queues
+// per thread) has one untiled shape per radius, one row per thread.
 #define WAVE_TSWEEP_MODE_VARIANTS_R1(Z)                                                            \
-    Z(1, 1, 4, 1, 64, 8, 2, 2, 3) Z(1, 1, 4, 1, 64, 8, 2, 2, 4) Z(1, 2, 4, 2, 128, 12, 1, 1, 4)
+    Z(1, 1, 4, 1, 64, 8, 2, 2, 3) Z(1, 1, 4, 1, 64, 8, 2, 2, 4) Z(1, 2, 4, 2, 128, 12, 1, 1, 4)      \
+    Z(1, 1, 4, 1, 64, 8, 2, 2, 5)
 #define WAVE_TSWEEP_MODE_VARIANTS_R2(Z)                                                            \
     Z(2, 1, 4, 1, 64, 8, 2, 2, 1) Z(2, 1, 4, 1, 64, 8, 2, 2, 2) Z(2, 2, 4, 2, 128, 12, 1, 1, 1)    \
     Z(2, 2, 4, 2, 128, 12, 1, 1, 2) Z(2, 1, 4, 1, 64, 8, 2, 2, 3) Z(2, 1, 4, 1, 64, 8, 2, 2, 4)      \
-    Z(2, 2, 4, 2, 128, 12, 1, 1, 4)
-#define WAVE_TSWEEP_MODE_VARIANTS_R3(Z) Z(3, 1, 4, 2, 64, 16, 2, 2, 3)
+    Z(2, 2, 4, 2, 128, 12, 1, 1, 4) Z(2, 1, 4, 1, 64, 8, 2, 2, 5)
+#define WAVE_TSWEEP_MODE_VARIANTS_R3(Z) Z(3, 1, 4, 2, 64, 16, 2, 2, 3) Z(3, 1, 4, 1, 64, 8, 2, 2, 5)
 #define WAVE_TSWEEP_MODE_VARIANTS_R4(Z)                                                            \
     Z(4, 1, 4, 2, 64, 16, 2, 2, 1) Z(4, 1, 4, 2, 64, 16, 2, 2, 2) Z(4, 2, 4, 2, 32, 32, 1, 1, 1)   \
     Z(4, 2, 4, 2, 32, 32, 1, 1, 2) Z(4, 1, 4, 2, 64, 16, 2, 2, 3) Z(4, 1, 4, 2, 64, 16, 2, 2, 4)    \
-    Z(4, 2, 4, 2, 56, 16, 2, 1, 4)
-#define WAVE_TSWEEP_MODE_VARIANTS_R5(Z) Z(5, 1, 4, 2, 64, 16, 2, 2, 3)
-#define WAVE_TSWEEP_MODE_VARIANTS_R6(Z) Z(6, 1, 4, 2, 64, 16, 2, 2, 3)
-#define WAVE_TSWEEP_MODE_VARIANTS_R7(Z) Z(7, 1, 4, 2, 64, 32, 2, 0, 3)
-#define WAVE_TSWEEP_MODE_VARIANTS_R8(Z) Z(8, 1, 4, 2, 64, 32, 2, 0, 3) Z(8, 1, 4, 2, 64, 32, 2, 0, 4)
+    Z(4, 2, 4, 2, 56, 16, 2, 1, 4) Z(4, 1, 4, 1, 64, 8, 2, 2, 5)
+#define WAVE_TSWEEP_MODE_VARIANTS_R5(Z) Z(5, 1, 4, 2, 64, 16, 2, 2, 3) Z(5, 1, 4, 1, 64, 8, 2, 2, 5)
+#define WAVE_TSWEEP_MODE_VARIANTS_R6(Z) Z(6, 1, 4, 2, 64, 16, 2, 2, 3) Z(6, 1, 4, 1, 64, 8, 2, 1, 5)
+#define WAVE_TSWEEP_MODE_VARIANTS_R7(Z) Z(7, 1, 4, 2, 64, 32, 2, 0, 3) Z(7, 1, 4, 1, 64, 8, 2, 1, 5)
+#define WAVE_TSWEEP_MODE_VARIANTS_R8(Z) Z(8, 1, 4, 2, 64, 32, 2, 0, 3) Z(8, 1, 4, 2, 64, 32, 2, 0, 4)  \
+    Z(8, 1, 4, 1, 64, 8, 2, 1, 5)
 
 // Batched stage-specialised variants M(R, T, V, VY, BZ, BY, P, MB, MODE): the
 // sweeps of a survey group on the stage-specialised kernel, each the batched

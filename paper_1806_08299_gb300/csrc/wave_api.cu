@@ -498,6 +498,17 @@ const SweepVariant *ab2_variant(int R, int T)
     return nullptr;
 }
 
+// The fused Born variant (mode 5: background and perturbation in one
+// sweep) of radius R, or nullptr.
+const SweepVariant *born_fused_variant(int R)
+{
+    const SweepVariant *vs = nullptr;
+    const int nv = mode_variants_for(R, &vs);
+    for (int i = 0; i < nv; ++i)
+        if (vs[i].XB == 5) return &vs[i];
+    return nullptr;
+}
+
 // The variant of the Born perturbation sweep (mode 3) of radius R.
 const SweepVariant *born_variant(int R)
 {
@@ -631,6 +642,8 @@ TuneKey tune_key(const Dims &d, int so, int T)
 
 // What one run of consecutive steps injects, records and stores.  Every row
 // index is "base + dir * j" for local step j of the run (j = 0 first).
+struct State;  // a wavefield's four buffers and which hold levels n and n-1 (below)
+
 // The heavy-first launch order a job's order buffer holds: the launch shape
 // it was computed for.  A caller that runs one job in many short run_steps
 // calls (one step each) keeps one of these per job and order buffer, so that
@@ -664,6 +677,7 @@ struct Job {
     float *gacc = nullptr;
     const float *born = nullptr;  // Born perturbation sweep: the coefficient P = -dm / dt^2 (padded)
     int ab2 = 0;                  // two-step Adams-Bashforth heat: its depth (1 or 2); 0: not that scheme
+    State *s2 = nullptr;          // fused Born (with born): the perturbation field's state, advanced with s
     // host copies of the injection / record tables and the device buffer for
     // the heavy-first launch order (nullptr: natural order)
     const HostTable *hinj = nullptr, *hrec = nullptr;
@@ -759,6 +773,16 @@ int build_launch(const Job &job, const State &s, int j, const SweepVariant *v, i
             rc = encode_rows_map(&tm->x0, job.dload, d, job.l_rows, v->W1, v->H1);
             if (!rc) rc = encode_map(&tm->x1, job.born, d, v->W1, v->H1);
         }
+        // fused Born: E and P, and the perturbation field's centre box and levels
+        if (!rc && v->XB == 5) {
+            if (job.s2 == nullptr) return WAVE_EINVAL;
+            const State &s2 = *job.s2;
+            rc = encode_map(&tm->x0, job.cE, d, v->W1, v->H1);
+            if (!rc) rc = encode_map(&tm->x1, job.born, d, v->W1, v->H1);
+            if (!rc) rc = encode_map(&tm->y0, s2.buf[s2.a], d, v->WC, v->HC);
+            if (!rc) rc = encode_map(&tm->y1, s2.buf[s2.a], d, v->W1, v->H1);
+            if (!rc) rc = encode_map(&tm->y2, s2.buf[s2.b], d, v->W1, v->H1);
+        }
         if (rc) return rc;
     } else {
         rc = encode_map(&mp->u, s.buf[s.a], d, v->PW, v->H0);
@@ -781,6 +805,7 @@ int build_launch(const Job &job, const State &s, int j, const SweepVariant *v, i
         if (i != s.a && i != s.b) spare[ns++] = i;
     if (v->T == 1 && !(v->kind == 1 && v->XB == 4)) {
         a.out_hi = s.buf[s.b];
+        if (v->kind == 1 && v->XB == 5) a.out_lo = job.s2->buf[job.s2->b];  // in place, as the background
     } else {
         // T >= 2, and the two-step Adams-Bashforth sweep at any depth: the new
         // level and the new rate (the old ones are still read by neighbours)
@@ -939,8 +964,12 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
         const int mode = job.ab2 != 0 ? 4
                          : job.gacc != nullptr ? 2
                          : job.dstore != nullptr ? 1
-                         : job.born != nullptr ? 3 : 0;
-        if (mode == 4) {
+                         : job.born != nullptr ? (job.s2 != nullptr ? 5 : 3) : 0;
+        if (mode == 5) {
+            v = born_fused_variant(R);
+            if (v == nullptr) return WAVE_EUNSUPPORTED;
+            chunk = std::min(default_chunk(d, v), max_chunk(v));
+        } else if (mode == 4) {
             // the Adams-Bashforth heat sweep: the first step (the Euler start)
             // and a last odd step run untiled
             const int Tw = (j == 0 || limit < 2) ? 1 : job.ab2;
@@ -998,6 +1027,7 @@ int run_steps(const Job &job, State &s, int nsteps, const Plan &plan, cudaStream
             g_prof.steps += v->T;
         }
         advance_state(s, mode == 4 ? 2 : v->T);  // Adams-Bashforth: new level and rate in the spares
+        if (mode == 5) advance_state(*job.s2, 1);
         j += v->T;
     }
     return WAVE_OK;
@@ -2726,11 +2756,37 @@ int32_t wave_born(const wave_grid *g, const float *m, const float *damp, const f
         bj.ocache = &ocb;
         pj.ocache = &ocp;
         if ((rc = prof_begin(tuning, stream))) return rc;
-        for (int n = 0; n < nt; ++n) {
-            bj.q_base = n;
-            if ((rc = run_steps(bj, bg, 1, plan, stream))) return rc;
-            pj.c_base = n;
-            if ((rc = run_steps(pj, pt, 1, plan, stream))) return rc;
+        const bool two = tuning != nullptr && (tuning->flags & WAVE_BORN_TWO_SWEEPS);
+        if (!two && born_fused_variant(g->space_order / 2) != nullptr) {
+            // one fused sweep per step: the background (sources, D in
+            // registers) and the perturbation (receivers) together
+            Job fj;
+            fj.d = d;
+            fj.st = st;
+            fj.cB = L.cB;
+            fj.cC = L.cC;
+            fj.cE = L.cE;
+            fj.status = L.status;
+            fj.inj = L.inj.view();
+            fj.q = src_traces;
+            fj.nq = nsrc;
+            fj.rec = L.rec.view();
+            fj.corner = L.corner;
+            fj.nslot = 8 * nrec;
+            fj.born = L.G;
+            fj.s2 = &pt;
+            fj.hinj = &ts;
+            fj.hrec = &tr;
+            fj.order = L.order;
+            fj.order_cap = L.order_cap;
+            if ((rc = run_steps(fj, bg, nt, plan, stream))) return rc;
+        } else {
+            for (int n = 0; n < nt; ++n) {
+                bj.q_base = n;
+                if ((rc = run_steps(bj, bg, 1, plan, stream))) return rc;
+                pj.c_base = n;
+                if ((rc = run_steps(pj, pt, 1, plan, stream))) return rc;
+            }
         }
         if ((rc = prof_end(stream))) return rc;
         if (nrec > 0) CK(wt::launch_gather(L.corner, L.rec.wts, nt, nrec, 1, rec_traces, stream));

@@ -25,6 +25,7 @@ WAVE_OP_FWD, WAVE_OP_ADJ, WAVE_OP_GRAD, WAVE_OP_REVOLVE, WAVE_OP_BORN = 0, 1, 2,
 WAVE_ALLOW_UNSTABLE = 1
 WAVE_TIME_SWEEPS = 2
 WAVE_AUTOTUNE_SHAPE = 4
+WAVE_BORN_TWO_SWEEPS = 8
 WAVE_TEST_WITHHOLD = 256
 WAVE_KERNEL_SHARED, WAVE_KERNEL_STAGED = 1, 2
 WAVE_NOALLOC_MAX_BYTES = 32 * 1024 * 1024

@@ -8,7 +8,9 @@
 * linearity: born(2 dm) = 2 born(dm) to 1e-6 of max |dd| (every operation
   of the perturbation sweep is linear in dm and doubling is exact, except
   where a product P D rounds in the subnormal range ahead of the wavefront);
-* the background plan (tiled or not) does not change the bits.
+* the background plan (tiled or not) does not change the bits;
+* the fused sweep (both fields in one pass) gives the bits of the two-sweep
+  form (background storing D, then the perturbation sweep) at every order.
 """
 import numpy as np
 import pytest
@@ -49,6 +51,12 @@ def test_born_vs_oracle(wavelib, cuda, oracle, so):
     h = [float(np.float32(v)) for v in grid.h]
     ddr, dur = oracle.born(_f64(m), _f64(damp), _f64(dm), h, float(np.float32(grid.dt)), nt, so, _f64(src),
                            _f64(q), _f64(rec))
+    dd2, du2, ws2 = wavelib.born(grid, _t(m, cuda), _t(damp, cuda), _t(dm, cuda), src, _t(q, cuda), rec,
+                                 want_du_last=True, tuning=wavelib.Tuning(flags=wavelib.WAVE_BORN_TWO_SWEEPS))
+    assert wavelib.status(ws2) == wavelib.WAVE_OK
+    import torch
+    torch.cuda.synchronize()
+    assert torch.equal(dd, dd2) and torch.equal(du, du2)
     dd, du = dd.cpu().numpy(), du.cpu().numpy()
     assert np.abs(ddr).max() > 0
     assert np.abs(dd - ddr).max() <= TOL * np.abs(ddr).max()
