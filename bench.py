@@ -307,13 +307,18 @@ def _spread(ms_list, pts):
             "max_gpts": pts / (ms_sorted[0] / 1e3) / 1e9, "median_gpts": pts / (med / 1e3) / 1e9}
 
 
-def run_survey_only(args):
-    """The survey section alone (one GPU), for profiling its batched kernels."""
+def run_section_only(args):
+    """One section alone (one GPU), for profiling its kernels."""
     import torch
     from paper_1806_08299_gb300 import inputs, wave
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    print(json.dumps({"fwi_survey": _fwi_survey(dev, inputs, wave, args)}))
+    if args.only_survey:
+        print(json.dumps({"fwi_survey": _fwi_survey(dev, inputs, wave, args)}))
+    if args.only_fwi:
+        print(json.dumps({"fwi_gradient": _fwi_gradient(dev, inputs, wave, args)}))
+    if args.only_laplace:
+        print(json.dumps({"laplace": _laplace_sweep(dev, inputs, wave, args)}))
 
 
 def run_ours(args):
@@ -835,11 +840,15 @@ def main():
                     help="ncu dram bytes per sweep launch, when captured for this kernel")
     ap.add_argument("--only-survey", action="store_true",
                     help="run only the batched survey (FWI gradient step over c5 shots) and print its entry")
+    ap.add_argument("--only-fwi", action="store_true",
+                    help="run only the c4 gradient, revolve and Born entry and print it")
+    ap.add_argument("--only-laplace", action="store_true",
+                    help="run only the Laplace operator entry (leapfrog-form and Adams-Bashforth sweeps)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.only_survey:
-        run_survey_only(args)
+    elif args.only_survey or args.only_fwi or args.only_laplace:
+        run_section_only(args)
     else:
         run_ours(args)
 
