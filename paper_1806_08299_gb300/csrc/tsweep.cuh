@@ -76,6 +76,31 @@ struct TMaps {
     CUtensorMap x0, x1, y0, y1, y2;
 };
 
+// Threads per row group of a stage whose rows hold lz threads: lz rounded up
+// to whole 8-lane phases of a 16-byte shared-memory access when that adds no
+// warp, else lz.  A phase that straddles two rows meets the far end of the
+// other row in the same banks (rows 64 + 8 floats wide: a two-way conflict on
+// a quarter of the phases); with whole phases per row every access of a
+// phase is 32 consecutive floats.
+constexpr int tstage_row_threads(int lz, int ly)
+{
+    return ((lz + 7) / 8 * 8 * ly + 31) / 32 == (lz * ly + 31) / 32 ? (lz + 7) / 8 * 8 : lz;
+}
+
+// Place thread t of a stage on its grid of ly row groups of lzp thread slots,
+// lz of them real: act tells whether it owns points; a slot past lz in its row
+// repeats column c - 8 of the same row (in a bank group its phase does not
+// use), a thread past the grid repeats thread 0.
+__device__ __forceinline__ void tstage_place(int t, int lz, int lzp, int ly, bool &act, int &row, int &col)
+{
+    const bool in = t < lzp * ly;
+    if (!in) t = 0;
+    row = t / lzp;
+    col = t - row * lzp;
+    act = in && col < lz;
+    if (col >= lz) col -= 8;
+}
+
 template <int R, int T, int V, int VY, int BZ, int BY, int P, int MB, int MODE = 0>
 struct TShape {
     static constexpr int RT = R * T;
@@ -85,9 +110,11 @@ struct TShape {
     static constexpr int HC = H1 + 2 * R;                 // centre box rows
     static constexpr int WC = W1 + 2 * RP;                // centre box columns (pitch)
     static constexpr int LZ1 = W1 / V, LY1 = H1 / VY;     // stage-1 thread grid
-    static constexpr int N1 = (LZ1 * LY1 + 31) / 32 * 32;
+    static constexpr int LZ1P = tstage_row_threads(LZ1, LY1);
+    static constexpr int N1 = (LZ1P * LY1 + 31) / 32 * 32;
     static constexpr int LZ2 = BZ / V, LY2 = BY / VY;     // stage-2 thread grid
-    static constexpr int N2 = T == 2 ? (LZ2 * LY2 + 31) / 32 * 32 : 0;
+    static constexpr int LZ2P = tstage_row_threads(LZ2, LY2);
+    static constexpr int N2 = T == 2 ? (LZ2P * LY2 + 31) / 32 * 32 : 0;
     // MB = 0: one block per SM whose consumer warps take over the registers
     // of a producer warpgroup (setmaxnreg).  Each quarter of an SM has its
     // own 16K registers for every fourth warp, so a block of 8 consumer
@@ -151,6 +178,7 @@ struct TShape {
     static_assert(V == 4, "four z points per thread (two pairs)");
     static_assert(VY == 1 || VY == 2, "one or two rows per thread");
     static_assert(BZ % 4 == 0 && BY % VY == 0 && H1 % VY == 0, "tile must split into thread blocks");
+    static_assert((LZ1P == LZ1 || LZ1 >= 8) && (LZ2P == LZ2 || LZ2 >= 8), "padded rows repeat column c - 8");
     static_assert(R >= 1 && R <= kMaxR, "radius out of range");
     static_assert(WC <= 256 && HC <= 256, "TMA box dimension above 256");
     static_assert(TXA < (1u << 20), "mbarrier tx count");
@@ -671,9 +699,11 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
     if constexpr (S::RSPLIT) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(S::CREG));
     if (tid < S::N1) {
         // ------------------------------ stage 1 ------------------------------
-        const bool act = tid < S::LZ1 * S::LY1;
-        const int t = act ? tid : 0;
-        const int ry = (t / S::LZ1) * VY, cz = (t % S::LZ1) * V;
+        bool act;
+        int ry, cz;
+        tstage_place(tid, S::LZ1, S::LZ1P, S::LY1, act, ry, cz);
+        ry *= VY;
+        cz *= V;
         const int offF = ry * S::W1 + cz;                 // in stage-1 boxes and ring-1 planes
         const int offC = (ry + R) * S::WC + cz + S::RP;   // in the centre box
         const int gy = gy0 + ry, gz = gz0 + cz;
@@ -858,10 +888,11 @@ __device__ __forceinline__ void tsweep_block(const SweepArgs &a, const Stencil &
     if constexpr (T == 2) {
         if (tid >= S::N1) {
             // ------------------------------ stage 2 ------------------------------
-            const int t2 = tid - S::N1;
-            const bool act = t2 < S::LZ2 * S::LY2;
-            const int t = act ? t2 : 0;
-            const int ry = (t / S::LZ2) * VY, cz = (t % S::LZ2) * V;
+            bool act;
+            int ry, cz;
+            tstage_place(tid - S::N1, S::LZ2, S::LZ2P, S::LY2, act, ry, cz);
+            ry *= VY;
+            cz *= V;
             const int off1 = (ry + R) * S::W1 + cz + S::RP;  // in ring-1 planes
             const int offS = ry * BZ + cz;                   // in ring-B boxes
             const int gy = ty0 + ry, gz = tz0 + cz;
