@@ -8,6 +8,7 @@ fixed number of steps.  For each variant it runs `--reps` forward calls and
 reports the best milliseconds per time step of the sweep launches (CUDA
 events the library records on the launch stream) and the resulting GPts/s.
 This is also the small case that the ncu summaries under profiles/ capture.
+It is a measurement driver for profiling, not part of the library's API.
 """
 import argparse
 import json

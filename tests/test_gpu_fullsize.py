@@ -93,6 +93,7 @@ def test_c4_gradient_finite_differences(wavelib, cuda):
     assert j0 > 0
     rng = np.random.default_rng(4)
     n = p0.n
+    report = []
     idx = [np.arange(v) for v in n]
     x, y, z = np.meshgrid(*idx, indexing="ij", sparse=True)
     for i in range(8):
@@ -119,4 +120,7 @@ def test_c4_gradient_finite_differences(wavelib, cuda):
         # 1e-5 parity bound on the traces), so the difference quotient is
         # uncertain by up to 2e-5 J / eps on top of 1 % for truncation.
         floor = 2e-5 * max(j0, jp, jm) / eps
+        # which bound decides this direction, and the relative error reached
+        report.append((i, fd, want, abs(fd - want) / abs(want), floor / abs(want)))
+        print("c4 FD direction %d: fd %.6e  adjoint %.6e  rel.err %.2e  floor/|adjoint| %.2e" % report[-1])
         assert abs(fd - want) <= 1e-2 * abs(want) + floor, (i, fd, want, floor)
