@@ -41,9 +41,9 @@ HBM_FALLBACK_GBS = 6800.0
 # profiles/traffic_tsweep_t2_so8_512.md), valid only for the kernel sources it was
 # taken on: the SHA-256 of csrc/sweep.cuh, csrc/tsweep.cuh and the radius-4
 # variant lists must match, else the bench reports null.
-TRAFFIC_SRC_SHA256 = "7728b342cdcbe7b013ea9af4e8b0bde4655463a8369301be8f890227a72a7fdb"
+TRAFFIC_SRC_SHA256 = "d39d15e353c637c5d984cfa5038629eef420729449ee0a69202b2f165d6ca8ac"
 TRAFFIC_BYTES = {  # ("family R T V rows BZ BY P", chunk, n) -> bytes per launch
-    ("staged R4 T2 V4 rows2 BZ64 BY24 P1", 103, (512, 512, 512)): 2366497280 + 1045686272,
+    ("staged R4 T2 V4 rows2 BZ64 BY24 P1", 103, (512, 512, 512)): 2345876480 + 1043785472,
 }
 
 

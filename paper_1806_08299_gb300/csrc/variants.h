@@ -60,11 +60,11 @@
     Z(4, 1, 4, 1, 64, 8, 2, 2) Z(4, 1, 4, 2, 64, 16, 2, 2) Z(4, 2, 4, 2, 56, 24, 1, 1)             \
     Z(4, 2, 4, 2, 64, 24, 1, 1) Z(4, 2, 4, 2, 32, 32, 2, 1) Z(4, 2, 4, 2, 56, 16, 2, 1)            \
     Z(4, 2, 4, 1, 56, 16, 2, 1)
-#define WAVE_TSWEEP_VARIANTS_R5(Z) Z(5, 1, 4, 2, 64, 16, 2, 2)
+#define WAVE_TSWEEP_VARIANTS_R5(Z) Z(5, 1, 4, 2, 64, 16, 2, 2) Z(5, 2, 4, 2, 48, 16, 1, 1)
 #define WAVE_TSWEEP_VARIANTS_R6(Z) \
     Z(6, 1, 4, 1, 64, 8, 2, 2) Z(6, 1, 4, 2, 64, 16, 2, 2) Z(6, 1, 4, 2, 64, 32, 2, 1) Z(6, 2, 4, 2, 32, 24, 1, 1)
 #define WAVE_TSWEEP_VARIANTS_R7(Z) \
-    Z(7, 1, 4, 2, 64, 16, 2, 1) Z(7, 1, 4, 2, 64, 32, 2, 0) Z(7, 1, 4, 2, 64, 32, 1, 0)
+    Z(7, 1, 4, 2, 64, 16, 2, 1) Z(7, 1, 4, 2, 64, 32, 2, 0) Z(7, 1, 4, 2, 64, 32, 1, 0) Z(7, 2, 4, 2, 32, 16, 1, 0)
 #define WAVE_TSWEEP_VARIANTS_R8(Z)                                                                 \
     Z(8, 1, 4, 1, 64, 8, 2, 2) Z(8, 1, 4, 2, 64, 16, 2, 1) Z(8, 1, 4, 2, 64, 24, 2, 1)             \
     Z(8, 2, 4, 2, 32, 8, 1, 1) Z(8, 1, 4, 2, 64, 32, 2, 0) Z(8, 1, 4, 2, 64, 32, 1, 0)             \
