@@ -191,7 +191,13 @@ int32_t wave_adj(const wave_grid *g, const float *m, const float *damp,
  * previous wave_fwd call with the same grid, m, damp, sources and ckpt_every:
  * each segment of ckpt_every steps is recomputed from its checkpoint with the
  * second difference stored per step, then the adjoint sweep of that segment
- * accumulates the imaging condition.  Workspace: WAVE_OP_GRAD. */
+ * accumulates the imaging condition.  Workspace: WAVE_OP_GRAD.
+ * The recompute and adjoint sweeps each run on the compiled shape measured
+ * fastest for that phase on this grid (a few steps of every candidate, once
+ * per grid, forward plan and point counts); every shape gives the same bits.
+ * Test hook: the environment variable WAVE_GRAD_PIN="i,j" makes this call
+ * (and wave_grad_revolve) run recompute candidate i and adjoint candidate j
+ * untimed, and return WAVE_EUNSUPPORTED when either index is past the end. */
 int32_t wave_grad(const wave_grid *g, const float *m, const float *damp,
                   const wave_points *src, const float *src_traces,
                   const wave_points *rec, const float *rec_resid,

@@ -94,6 +94,28 @@ __global__ void gather_kernel(const float *__restrict__ corner, const float *__r
     }
 }
 
+// Per-entry injection values of every trace row of a call:
+//   F[r][e] = sum over the entry's items i (ascending) of w[i] q[r][item[i]]
+// the sum the sweep forms when it reaches the entry's plane (the same fused
+// multiply-adds in the same order, so the same bits), formed once per call
+// instead, so that the sweep's plane loop reads one value per entry.
+__global__ void inj_sum_kernel(const int4 *__restrict__ pts, const int *__restrict__ item,
+                               const float *__restrict__ w, const float *__restrict__ q, int nq, int ne,
+                               int rows, long long fstride, float *__restrict__ F)
+{
+    const long long total = (long long)rows * ne;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / ne);
+        const int e = (int)(i - (long long)r * ne);
+        const int4 pt = pts[e];
+        const float *qr = q + (long long)r * nq;
+        float f = 0.f;
+        for (int k = pt.z; k < pt.w; ++k) f = __fmaf_rn(w[k], qr[item[k]], f);
+        F[(long long)r * fstride + e] = f;
+    }
+}
+
 static int grid_for(long long n)
 {
     long long b = (n + 255) / 256;
@@ -167,6 +189,14 @@ cudaError_t launch_gather(const float *corner, const float *w, int rows, int npt
     if (rows <= 0 || npts <= 0) return cudaSuccess;
     gather_kernel<<<grid_for((long long)rows * npts), 256, 0, s>>>(corner, w, rows, npts, row_dir,
                                                                    out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inj_sum(const int4 *pts, const int *item, const float *w, const float *q, int nq, int ne,
+                           int rows, long long fstride, float *F, cudaStream_t s)
+{
+    if (rows <= 0 || ne <= 0) return cudaSuccess;
+    inj_sum_kernel<<<grid_for((long long)rows * ne), 256, 0, s>>>(pts, item, w, q, nq, ne, rows, fstride, F);
     return cudaGetLastError();
 }
 

@@ -93,6 +93,11 @@ struct PointTable {
     const int4 *pts;
     const int *item;
     const float *w;
+    // injection tables: the value each entry injects at every trace row,
+    // f[row * fstride + e] = sum over its items (ascending) of w q[row][item],
+    // summed once per call; nullptr: the sweep sums the items itself
+    const float *f;
+    long long fstride;
 };
 
 struct SweepArgs {
@@ -708,12 +713,17 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
                         unsigned hits = 0u;
 #pragma unroll
                         for (int j = 0; j < V; ++j) fv[j] = 0.f;
-                        const long long qrow = (long long)(a.q_row0 + a.q_dir * (s - 1)) * a.nq;
+                        const int trow = a.q_row0 + a.q_dir * (s - 1);
+                        const long long qrow = (long long)trow * a.nq;
+                        const float *frow = a.inj.f != nullptr ? a.inj.f + (long long)trow * a.inj.fstride : nullptr;
                         for (int eb = e0; eb < e1; eb += 4) {
                             int4 pt4[4];  // four table points per round trip
+                            float f4[4];  // and their summed values, when the call has them
 #pragma unroll
-                            for (int u = 0; u < 4; ++u)
+                            for (int u = 0; u < 4; ++u) {
                                 pt4[u] = eb + u < e1 ? __ldg(a.inj.pts + eb + u) : make_int4(-1, -1, 0, 0);
+                                f4[u] = frow != nullptr && eb + u < e1 ? __ldg(frow + eb + u) : 0.f;
+                            }
 #pragma unroll
                             for (int u = 0; u < 4; ++u) {
                                 const int4 pt = pt4[u];
@@ -722,6 +732,10 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
                                 // keeps the ascending order
                                 float f = 0.f;
                                 int itm = pt.z;
+                                if (frow != nullptr) {
+                                    f = f4[u];
+                                    itm = pt.w;
+                                }
                                 for (; itm + 1 < pt.w; itm += 2) {
                                     const int i0 = __ldg(a.inj.item + itm), i1 = __ldg(a.inj.item + itm + 1);
                                     const float w0 = __ldg(a.inj.w + itm), w1 = __ldg(a.inj.w + itm + 1);

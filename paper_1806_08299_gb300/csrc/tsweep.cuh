@@ -355,6 +355,9 @@ __device__ __forceinline__ void tstage_inject(float2 (&un)[VY][V / 2], const flo
                                               float2 (*dd)[V / 2] = nullptr)
 {
     const long long qbase = (long long)qrow * a.nq;
+    // the call's summed entry values, loaded beside the entries (one round
+    // trip per 32 entries instead of the item, weight and trace chain)
+    const float *frow = a.inj.f != nullptr ? a.inj.f + (long long)qrow * a.inj.fstride : nullptr;
     const int lane = threadIdx.x & 31;
     float fv[VY][V];
     unsigned hits[VY];
@@ -366,6 +369,7 @@ __device__ __forceinline__ void tstage_inject(float2 (&un)[VY][V / 2], const flo
     }
     for (int eb = e0; eb < e1; eb += 32) {
         const int4 mine = eb + lane < e1 ? __ldg(a.inj.pts + eb + lane) : make_int4(-1, -1, 0, 0);
+        const float fmine = frow != nullptr && eb + lane < e1 ? __ldg(frow + eb + lane) : 0.f;
         const bool rel = mine.x >= wy0 && mine.x < wy1 && mine.y >= wz0 && mine.y < wz1;
         unsigned m = __ballot_sync(0xffffffffu, rel);
         while (m != 0u) {
@@ -376,10 +380,15 @@ __device__ __forceinline__ void tstage_inject(float2 (&un)[VY][V / 2], const flo
             pt.y = __shfl_sync(0xffffffffu, mine.y, l);
             pt.z = __shfl_sync(0xffffffffu, mine.z, l);
             pt.w = __shfl_sync(0xffffffffu, mine.w, l);
+            const float fl = __shfl_sync(0xffffffffu, fmine, l);
             const int v = pt.x - gy, jj = pt.y - gz;
             if (v < 0 || v >= VY || jj < 0 || jj >= V) continue;
             float f = 0.f;
             int itm = pt.z;
+            if (frow != nullptr) {
+                f = fl;
+                itm = pt.w;
+            }
             for (; itm + 1 < pt.w; itm += 2) {  // items in pairs, ascending sum
                 const int i0 = __ldg(a.inj.item + itm), i1 = __ldg(a.inj.item + itm + 1);
                 const float w0 = __ldg(a.inj.w + itm), w1 = __ldg(a.inj.w + itm + 1);

@@ -109,7 +109,8 @@
 #define WAVE_TSWEEP_MODE_VARIANTS_R4(Z)                                                            \
     Z(4, 1, 4, 2, 64, 16, 2, 2, 1) Z(4, 1, 4, 2, 64, 16, 2, 2, 2) Z(4, 2, 4, 2, 32, 32, 1, 1, 1)   \
     Z(4, 2, 4, 2, 32, 32, 1, 1, 2) Z(4, 1, 4, 2, 64, 16, 2, 2, 3) Z(4, 1, 4, 2, 64, 16, 2, 2, 4)    \
-    Z(4, 2, 4, 2, 56, 16, 2, 1, 4) Z(4, 1, 4, 1, 64, 8, 2, 2, 5)
+    Z(4, 2, 4, 2, 56, 16, 2, 1, 4) Z(4, 1, 4, 1, 64, 8, 2, 2, 5) Z(4, 2, 4, 1, 32, 24, 1, 1, 1)    \
+    Z(4, 2, 4, 1, 32, 24, 1, 1, 2) Z(4, 1, 4, 1, 64, 8, 2, 3, 1) Z(4, 1, 4, 1, 64, 8, 2, 3, 2)
 #define WAVE_TSWEEP_MODE_VARIANTS_R5(Z) Z(5, 1, 4, 2, 64, 16, 2, 2, 3) Z(5, 1, 4, 1, 64, 8, 2, 2, 5)
 #define WAVE_TSWEEP_MODE_VARIANTS_R6(Z) Z(6, 1, 4, 2, 64, 16, 2, 2, 3) Z(6, 1, 4, 1, 64, 8, 2, 1, 5)
 #define WAVE_TSWEEP_MODE_VARIANTS_R7(Z) Z(7, 1, 4, 2, 64, 32, 2, 0, 3) Z(7, 1, 4, 1, 64, 8, 2, 1, 5)

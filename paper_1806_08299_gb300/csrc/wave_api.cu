@@ -247,7 +247,13 @@ struct DevTable {
     float *w = nullptr;
     float *wts = nullptr;
     int npts = 0;
-    PointTable view() const { return PointTable{npts ? plane_start : nullptr, pts, item, w}; }
+    float *f = nullptr;      // injection tables: room for the summed entry values [rows][8 npts]
+    long long fstride = 0;
+    bool fready = false;     // f holds this call's sums (sum_table)
+    PointTable view() const
+    {
+        return PointTable{npts ? plane_start : nullptr, pts, item, w, fready ? f : nullptr, fstride};
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -269,7 +275,9 @@ struct Carver {
     }
 };
 
-void carve_table(Carver &c, const Dims &d, int np, DevTable *t)
+// rows > 0: an injection table, with room for the summed value of each
+// entry at each of `rows` trace rows
+void carve_table(Carver &c, const Dims &d, int np, DevTable *t, int rows = 0)
 {
     t->plane_start = c.take<int>(d.nx + 1);
     t->pts = c.take<int4>((size_t)8 * np);
@@ -277,6 +285,10 @@ void carve_table(Carver &c, const Dims &d, int np, DevTable *t)
     t->w = c.take<float>((size_t)8 * np);
     t->wts = c.take<float>((size_t)8 * np);
     t->npts = np;
+    if (rows > 0 && np > 0) {
+        t->fstride = 8LL * np;
+        t->f = c.take<float>((size_t)rows * 8 * np);
+    }
 }
 
 int upload_table(const HostTable &h, const DevTable &t, cudaStream_t s)
@@ -290,6 +302,18 @@ int upload_table(const HostTable &h, const DevTable &t, cudaStream_t s)
         CK(cudaMemcpyAsync(t.w, h.w.data(), sizeof(float) * h.w.size(), cudaMemcpyHostToDevice, s));
     }
     CK(cudaMemcpyAsync(t.wts, h.wts.data(), sizeof(float) * h.wts.size(), cudaMemcpyHostToDevice, s));
+    return WAVE_OK;
+}
+
+// The value each entry of injection table t injects at every trace row of
+// the call (traces q [rows][nq]), summed once here so that the sweeps read
+// one value per entry and plane instead of its items, weights and traces.
+int sum_table(const HostTable &h, DevTable &t, const float *q, int nq, int rows, cudaStream_t s)
+{
+    t.fready = false;
+    if (t.npts == 0 || t.f == nullptr || q == nullptr || rows <= 0 || h.pts.empty()) return WAVE_OK;
+    CK(wt::launch_inj_sum(t.pts, t.item, t.w, q, nq, (int)h.pts.size(), rows, t.fstride, t.f, s));
+    t.fready = true;
     return WAVE_OK;
 }
 
@@ -332,7 +356,7 @@ Layout carve(void *ws, size_t cap, bool dry, const Dims &d, int op, int nsrc, in
         for (int i = 0; i < 4; ++i) L.V[i] = c.take<float>(d.npad);
         L.G = c.take<float>(d.npad);
         L.store = c.take<float>(d.npad);
-        carve_table(c, d, nsrc, &L.inj);
+        carve_table(c, d, nsrc, &L.inj, nt);
         carve_table(c, d, nrec, &L.rec);
         L.corner = c.take<float>((size_t)nt * 8 * std::max(nrec, 0));
     } else if (grad) {
@@ -341,12 +365,12 @@ Layout carve(void *ws, size_t cap, bool dry, const Dims &d, int op, int nsrc, in
         const int rows = op == WAVE_OP_REVOLVE ? 1 : std::max(1, std::min(ckpt_every, nt));
         L.store = c.take<float>((size_t)d.npad * (size_t)rows);
         if (op == WAVE_OP_REVOLVE) L.slots = c.take<float>((size_t)d.npad * 2 * (size_t)std::max(0, ckpt_every));
-        carve_table(c, d, nsrc, &L.inj);
-        carve_table(c, d, nrec, &L.inj2);
+        carve_table(c, d, nsrc, &L.inj, nt);
+        carve_table(c, d, nrec, &L.inj2, nt);
     } else {
         const int ni = op == WAVE_OP_FWD ? nsrc : nrec;
         const int nr = op == WAVE_OP_FWD ? nrec : nsrc;
-        carve_table(c, d, ni, &L.inj);
+        carve_table(c, d, ni, &L.inj, nt);
         carve_table(c, d, nr, &L.rec);
         L.corner = c.take<float>((size_t)nt * 8 * std::max(nr, 0));
     }
@@ -1300,122 +1324,142 @@ int resolve_plan(const Dims &d, const wave_grid *g, const wave_tuning *t, bool m
     return WAVE_OK;
 }
 
-// The family that runs the gradient sweeps of wave_grad (the recompute sweep
-// storing second differences, and the adjoint sweep with the imaging
-// condition).  Which family and depth is fastest there depends on the grid --
-// the shared-warp untiled sweep streams E, D and G through TMA with three or
-// four blocks per SM, the stage-specialised sweeps save DRAM bytes but hold
-// fewer warps, and a block that injects many points waits on their table and
-// trace loads every plane -- so the candidates are timed once per (grid,
-// forward plan, source and receiver counts) on the workspace's scratch state
-// with the call's own sources and receivers, a few steps of each mode, and
-// the fastest kept.  Returns the plan run_steps is given for those sweeps; run_steps picks
-// the mode variant of its shape.  Every candidate gives the same bits.
+// The shapes that run the gradient sweeps of wave_grad: the recompute sweep
+// storing second differences (mode 1) and the adjoint sweep with the imaging
+// condition (mode 2), chosen each on its own.  Which is fastest depends on
+// the grid and on the phase -- the shared-warp untiled sweep streams E, D and
+// G through TMA with three or four blocks per SM, the stage-specialised
+// shapes save DRAM bytes but hold fewer warps, the imaging condition loads
+// and stores more per point than the recompute, and a block that injects
+// many points waits on their table and trace loads every plane -- so the
+// candidates are timed once per (grid, forward plan, source and receiver
+// counts) on the workspace's scratch state with the call's own sources and
+// receivers, a few steps of each phase, and the fastest of each phase kept.
+// The candidates: the untiled default of sweep.cuh (its own mode variants),
+// and, when the forward plan is stage-specialised, every compiled
+// stage-specialised mode variant of the plan's depth or untiled.  Every
+// candidate gives the same bits.
 struct GradKey {
-    int nx, ny, nz, so, dev, nsrc, nrec;
+    int nx, ny, nz, so, dev, nsrc, nrec, rows;
     const SweepVariant *v;
     bool operator<(const GradKey &o) const
     {
-        return std::tie(nx, ny, nz, so, dev, nsrc, nrec, v) <
-               std::tie(o.nx, o.ny, o.nz, o.so, o.dev, o.nsrc, o.nrec, o.v);
+        return std::tie(nx, ny, nz, so, dev, nsrc, nrec, rows, v) <
+               std::tie(o.nx, o.ny, o.nz, o.so, o.dev, o.nsrc, o.nrec, o.rows, o.v);
     }
 };
 std::mutex g_grad_mu;
-std::map<GradKey, Plan> g_grad_cache;
+std::map<GradKey, std::pair<Plan, Plan>> g_grad_cache;
 
 int grad_plan(const Dims &d, const wave_grid *g, const Plan &fwd, const Stencil &st, const float *cB,
               const float *cC, const float *cE, float *const U[4], float *store, int store_rows, float *G,
               int *status, const PointTable &src, const float *src_traces, int nsrc, const PointTable &rec,
-              const float *rec_resid, int nrec, cudaStream_t stream, Plan *out)
+              const float *rec_resid, int nrec, cudaStream_t stream, Plan *rout, Plan *aout)
 {
     const int R = g->space_order / 2;
     int dev = 0;
     cudaGetDevice(&dev);
-    const GradKey key{d.nx, d.ny, d.nz, g->space_order, dev, nsrc, nrec, fwd.v};
-    {
-        std::lock_guard<std::mutex> lk(g_grad_mu);
-        auto it = g_grad_cache.find(key);
-        if (it != g_grad_cache.end()) {
-            *out = it->second;
-            return WAVE_OK;
-        }
-    }
-    std::vector<Plan> cands;
     Plan p0;  // the untiled default of sweep.cuh: its own mode variants
     p0.v = find_variant(R, 1, 0, 0, 0, 1);
     if (p0.v == nullptr) return WAVE_EUNSUPPORTED;
     p0.chunk = default_chunk(d, p0.v);
-    cands.push_back(p0);
-    if (fwd.v->kind == 1) {
-        // the plan's own depth, and the untiled staged shape, where mode variants exist
-        for (int T : {fwd.v->T, 1}) {
-            const SweepVariant *base = T == fwd.v->T ? fwd.v : find_variant(R, 1, 0, 0, 0, 2);
-            if (base == nullptr || mode_variant(base, 1) == nullptr || mode_variant(base, 2) == nullptr) continue;
+    std::vector<Plan> cands[2];  // [0] recompute (mode 1), [1] adjoint (mode 2)
+    for (int k = 0; k < 2; ++k) {
+        cands[k].push_back(p0);
+        if (fwd.v->kind != 1) continue;
+        const SweepVariant *vs = nullptr;
+        const int nv = mode_variants_for(R, &vs);
+        for (int i = 0; i < nv; ++i) {
+            const SweepVariant *v = &vs[i];
+            if (v->kind != 1 || v->XB != k + 1 || (v->T != 1 && v->T != fwd.v->T)) continue;
             Plan p;
-            p.v = base;
-            p.chunk = fwd.chunk_given ? fwd.chunk : default_chunk(d, mode_variant(base, 2));
+            p.v = v;  // a mode variant runs itself in its own mode (mode_variant)
+            p.chunk = fwd.chunk_given ? fwd.chunk : default_chunk(d, v);
             p.chunk_given = fwd.chunk_given;
-            bool dup = false;
-            for (const Plan &c : cands) dup |= mode_variant(c.v, 2) == mode_variant(p.v, 2);
-            if (!dup) cands.push_back(p);
+            cands[k].push_back(p);
         }
     }
-    Plan best = cands[0];
-    if (cands.size() > 1) {
+    // test hook: WAVE_GRAD_PIN="i,j" runs recompute candidate i and adjoint
+    // candidate j of the lists above, untimed and uncached
+    if (const char *pin = std::getenv("WAVE_GRAD_PIN")) {
+        int i = -1, j = -1;
+        if (std::sscanf(pin, "%d,%d", &i, &j) != 2 || i < 0 || j < 0 || i >= (int)cands[0].size() ||
+            j >= (int)cands[1].size())
+            return WAVE_EUNSUPPORTED;
+        *rout = cands[0][i];
+        *aout = cands[1][j];
+        return WAVE_OK;
+    }
+    const GradKey key{d.nx, d.ny, d.nz, g->space_order, dev, nsrc, nrec, store_rows, fwd.v};
+    {
+        std::lock_guard<std::mutex> lk(g_grad_mu);
+        auto it = g_grad_cache.find(key);
+        if (it != g_grad_cache.end()) {
+            *rout = it->second.first;
+            *aout = it->second.second;
+            return WAVE_OK;
+        }
+    }
+    Plan best[2] = {cands[0][0], cands[1][0]};
+    if (cands[0].size() > 1 || cands[1].size() > 1) {
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        float best_ms = 1e30f;
+        float best_ms[2] = {1e30f, 1e30f};
         int rc = WAVE_OK;
-        const int steps = std::min(8, store_rows);  // rows of the second-difference store
+        const int steps = std::min(16, store_rows);  // rows of the second-difference store
         for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(U[k], 0, sizeof(float) * d.npad, stream));
+        CK(cudaMemsetAsync(store, 0, sizeof(float) * d.npad * (size_t)steps, stream));
+        // recompute (second differences into store rows 0..steps-1) and
+        // adjoint (imaging condition from those rows into G), on zero fields
+        Job rj;
+        rj.d = d;
+        rj.st = st;
+        rj.cB = cB;
+        rj.cC = cC;
+        rj.cE = cE;
+        rj.status = status;
+        rj.dstore = store;
+        rj.inj = src;
+        rj.q = src_traces;
+        rj.nq = nsrc;
+        Job aj = rj;
+        aj.dstore = nullptr;
+        aj.cE = nullptr;
+        aj.inj = rec;
+        aj.q = rec_resid;
+        aj.nq = nrec;
+        aj.q_base = steps - 1;
+        aj.q_dir = -1;
+        aj.dload = store;
+        aj.l_rows = store_rows;
+        aj.l_base = steps - 1;
+        aj.l_dir = -1;
+        aj.gacc = G;
         for (int pass = 0; pass < 2 && rc == WAVE_OK; ++pass) {
-            for (const Plan &p : cands) {
-                // recompute (second differences into store rows 0..7) then
-                // adjoint (imaging condition from those rows into G), on zero
-                // fields without sparse points
-                Job rj;
-                rj.d = d;
-                rj.st = st;
-                rj.cB = cB;
-                rj.cC = cC;
-                rj.cE = cE;
-                rj.status = status;
-                rj.dstore = store;
-                rj.inj = src;
-                rj.q = src_traces;
-                rj.nq = nsrc;
-                Job aj = rj;
-                aj.dstore = nullptr;
-                aj.cE = nullptr;
-                aj.inj = rec;
-                aj.q = rec_resid;
-                aj.nq = nrec;
-                aj.q_base = steps - 1;
-                aj.q_dir = -1;
-                aj.dload = store;
-                aj.l_rows = store_rows;
-                aj.l_base = steps - 1;
-                aj.l_dir = -1;
-                aj.gacc = G;
-                State s1, s2;
-                for (int k = 0; k < 4; ++k) s1.buf[k] = s2.buf[k] = U[k];
-                float ms = 0.f;
-                if (cudaEventRecord(e0, stream) != cudaSuccess) { rc = WAVE_ECUDA; break; }
-                if ((rc = run_steps(rj, s1, steps, p, stream))) break;
-                if ((rc = run_steps(aj, s2, steps, p, stream))) break;
-                if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                    rc = WAVE_ECUDA;
-                    break;
+            for (int k = 0; k < 2 && rc == WAVE_OK; ++k) {
+                for (const Plan &p : cands[k]) {
+                    State s;
+                    for (int i = 0; i < 4; ++i) s.buf[i] = U[i];
+                    float ms = 0.f;
+                    if (cudaEventRecord(e0, stream) != cudaSuccess) { rc = WAVE_ECUDA; break; }
+                    if ((rc = run_steps(k == 0 ? rj : aj, s, steps, p, stream))) break;
+                    if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                        rc = WAVE_ECUDA;
+                        break;
+                    }
+                    if (pass == 1 && ms < 0.99f * best_ms[k]) {  // ties keep the earlier candidate
+                        best_ms[k] = ms;
+                        best[k] = p;
+                    }
+                    if (tune_log() && pass == 1)
+                        std::fprintf(stderr,
+                                     "wave gradient %s sweeps: kernel=%d T=%d tile=%dx%d rows=%d: %.4f ms for %d "
+                                     "steps\n",
+                                     k == 0 ? "recompute" : "adjoint", p.v->kind + 1, p.v->T, p.v->BZ, p.v->BY,
+                                     rows_of(p.v), ms, steps);
                 }
-                if (pass == 1 && ms < 0.99f * best_ms) {  // ties keep the earlier candidate
-                    best_ms = ms;
-                    best = p;
-                }
-                if (tune_log() && pass == 1)
-                    std::fprintf(stderr, "wave gradient sweeps: kernel=%d T=%d tile=%dx%d: %.4f ms for %d steps\n",
-                                 p.v->kind + 1, p.v->T, p.v->BZ, p.v->BY, ms, 2 * steps);
             }
         }
         cudaEventDestroy(e0);
@@ -1423,8 +1467,9 @@ int grad_plan(const Dims &d, const wave_grid *g, const Plan &fwd, const Stencil 
         if (rc) return rc;
     }
     std::lock_guard<std::mutex> lk(g_grad_mu);
-    g_grad_cache[key] = best;
-    *out = best;
+    g_grad_cache[key] = std::make_pair(best[0], best[1]);
+    *rout = best[0];
+    *aout = best[1];
     return WAVE_OK;
 }
 
@@ -1964,6 +2009,8 @@ int lockstep_group(const wave_grid *G, int n, const ShotSlot *slots, int ckpt_ev
             for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(x.L.U[k], 0, sizeof(float) * x.d.npad, stream));
             if ((rc = upload_table(x.ti, x.L.inj, stream))) return rc;
             if ((rc = upload_table(x.tr, grad ? x.L.inj2 : x.L.rec, stream))) return rc;
+            if ((rc = sum_table(x.ti, x.L.inj, slots[i].q, ns, nt, stream))) return rc;
+            if (grad && (rc = sum_table(x.tr, x.L.inj2, slots[i].resid, nr, nt, stream))) return rc;
             for (int k = 0; k < 4; ++k) x.s.buf[k] = x.L.U[k];
             forward_job(x, slots[i], st, grad);
         }
@@ -2460,7 +2507,7 @@ int32_t wave_fwd(const wave_grid *g, const float *m, const float *damp, const wa
         if (ckpt != nullptr && ckpt_every < 1) return WAVE_EINVAL;
         if ((uintptr_t)ws % kAlign) return WAVE_EINVAL;
         const int nsrc = npts_of(src), nrec = npts_of(rec);
-        const Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_FWD, nsrc, nrec, g->nt, ckpt_every);
+        Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_FWD, nsrc, nrec, g->nt, ckpt_every);
         if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
         HostTable ti, tr;
         if (build_table(d, g->h, src, false, &ti) || build_table(d, g->h, rec, true, &tr))
@@ -2473,6 +2520,7 @@ int32_t wave_fwd(const wave_grid *g, const float *m, const float *damp, const wa
         if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, L.status, stream, &plan))) return rc;
         for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.U[i], 0, sizeof(float) * d.npad, stream));
         if ((rc = upload_table(ti, L.inj, stream)) || (rc = upload_table(tr, L.rec, stream))) return rc;
+        if ((rc = sum_table(ti, L.inj, src_traces, nsrc, g->nt, stream))) return rc;
         Job job;
         job.d = d;
         job.st = st;
@@ -2522,7 +2570,7 @@ int32_t wave_adj(const wave_grid *g, const float *m, const float *damp, const wa
         if (check_points(rec, true, rec_resid) || check_points(src, false, nullptr)) return WAVE_EINVAL;
         if ((uintptr_t)ws % kAlign) return WAVE_EINVAL;
         const int nsrc = npts_of(src), nrec = npts_of(rec);
-        const Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_ADJ, nsrc, nrec, g->nt, 0);
+        Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_ADJ, nsrc, nrec, g->nt, 0);
         if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
         HostTable ti, tr;
         if (build_table(d, g->h, rec, false, &ti) || build_table(d, g->h, src, true, &tr))
@@ -2535,6 +2583,7 @@ int32_t wave_adj(const wave_grid *g, const float *m, const float *damp, const wa
         if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, L.status, stream, &plan))) return rc;
         for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.U[i], 0, sizeof(float) * d.npad, stream));
         if ((rc = upload_table(ti, L.inj, stream)) || (rc = upload_table(tr, L.rec, stream))) return rc;
+        if ((rc = sum_table(ti, L.inj, rec_resid, nrec, g->nt, stream))) return rc;
         // reversed step j produces nu^{nt-j}: it injects res^{nt-1-j} and records
         // dJ/dq^{nt-1-j}
         Job job;
@@ -2588,7 +2637,7 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
         if ((uintptr_t)ws % kAlign) return WAVE_EINVAL;
         const int nsrc = npts_of(src), nrec = npts_of(rec);
         const int nt = g->nt;
-        const Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_GRAD, nsrc, nrec, nt, ckpt_every);
+        Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_GRAD, nsrc, nrec, nt, ckpt_every);
         if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
         HostTable ts, tr;
         if (build_table(d, g->h, src, false, &ts) || build_table(d, g->h, rec, false, &tr))
@@ -2596,14 +2645,18 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
         cudaStream_t stream = (cudaStream_t)stream_;
         const Stencil st = make_stencil(g);
         if ((rc = prep_model(d, g, tuning, m, damp, L, stream))) return rc;
-        Plan plan;
-        if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, L.status, stream, &plan))) return rc;
-        // the sweeps below run in the gradient modes: the family chosen for them
-        Plan fplan = plan;
+        Plan fplan;
+        if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, L.status, stream, &fplan))) return rc;
+        // the sweeps below run in the gradient modes, on the shapes chosen for them
         const int store_rows = std::max(1, std::min(ckpt_every, nt));
         if ((rc = upload_table(ts, L.inj, stream)) || (rc = upload_table(tr, L.inj2, stream))) return rc;
+        if ((rc = sum_table(ts, L.inj, src_traces, nsrc, nt, stream)) ||
+            (rc = sum_table(tr, L.inj2, rec_resid, nrec, nt, stream)))
+            return rc;
+        Plan rplan, aplan;
         if ((rc = grad_plan(d, g, fplan, st, L.cB, L.cC, L.cE, L.U, L.store, store_rows, L.G, L.status,
-                            L.inj.view(), src_traces, nsrc, L.inj2.view(), rec_resid, nrec, stream, &plan)))
+                            L.inj.view(), src_traces, nsrc, L.inj2.view(), rec_resid, nrec, stream, &rplan,
+                            &aplan)))
             return rc;
         CK(cudaMemsetAsync(L.G, 0, sizeof(float) * d.npad, stream));
         for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.V[i], 0, sizeof(float) * d.npad, stream));
@@ -2646,7 +2699,7 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
             rj.order = L.order;
             rj.order_cap = L.order_cap;
             rj.ocache = &ocr;
-            if ((rc = run_steps(rj, fw, len, plan, stream))) return rc;
+            if ((rc = run_steps(rj, fw, len, rplan, stream))) return rc;
             // 2) adjoint over the segment, newest step first: reversed step
             //    for n = s0+len-1 .. s0 produces nu^{n+1}, injects res^n and
             //    accumulates G += nu^{n+1} D^n
@@ -2670,7 +2723,7 @@ int32_t wave_grad(const wave_grid *g, const float *m, const float *damp, const w
             aj.order = L.order_b;
             aj.order_cap = L.order_cap;
             aj.ocache = &oca;
-            if ((rc = run_steps(aj, adj, len, plan, stream))) return rc;
+            if ((rc = run_steps(aj, adj, len, aplan, stream))) return rc;
         }
         if ((rc = prof_end(stream))) return rc;
         const float scale = (float)(-1.0 / ((double)g->dt * (double)g->dt));
@@ -2694,7 +2747,7 @@ int32_t wave_born(const wave_grid *g, const float *m, const float *damp, const f
         if ((uintptr_t)ws % kAlign) return WAVE_EINVAL;
         const int nsrc = npts_of(src), nrec = npts_of(rec);
         const int nt = g->nt;
-        const Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_BORN, nsrc, nrec, nt, 0);
+        Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_BORN, nsrc, nrec, nt, 0);
         if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
         HostTable ts, tr;
         if (build_table(d, g->h, src, false, &ts) || build_table(d, g->h, rec, true, &tr)) return WAVE_EINVAL;
@@ -2707,6 +2760,7 @@ int32_t wave_born(const wave_grid *g, const float *m, const float *damp, const f
         Plan plan;
         if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, L.status, stream, &plan))) return rc;
         if ((rc = upload_table(ts, L.inj, stream)) || (rc = upload_table(tr, L.rec, stream))) return rc;
+        if ((rc = sum_table(ts, L.inj, src_traces, nsrc, nt, stream))) return rc;
         for (int i = 0; i < 4; ++i) {
             CK(cudaMemsetAsync(L.U[i], 0, sizeof(float) * d.npad, stream));
             CK(cudaMemsetAsync(L.V[i], 0, sizeof(float) * d.npad, stream));
@@ -2846,7 +2900,7 @@ int32_t wave_grad_revolve(const wave_grid *g, const float *m, const float *damp,
         if (check_points(src, true, src_traces) || check_points(rec, true, rec_resid)) return WAVE_EINVAL;
         if ((uintptr_t)ws % kAlign) return WAVE_EINVAL;
         const int nsrc = npts_of(src), nrec = npts_of(rec);
-        const Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_REVOLVE, nsrc, nrec, nt, nslots);
+        Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_REVOLVE, nsrc, nrec, nt, nslots);
         if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
         HostTable ts, tr;
         if (build_table(d, g->h, src, false, &ts) || build_table(d, g->h, rec, false, &tr))
@@ -2857,11 +2911,14 @@ int32_t wave_grad_revolve(const wave_grid *g, const float *m, const float *damp,
         if ((rc = prep_model(d, g, tuning, m, damp, L, stream))) return rc;
         // forward advances on the forward plan, the reversed steps on the
         // family the gradient modes run fastest on (as wave_grad)
-        Plan fplan, gplan;
+        Plan fplan, rplan, aplan;
         if ((rc = resolve_plan(d, g, tuning, true, &st, L.cB, L.cC, L.U, L.status, stream, &fplan))) return rc;
         if ((rc = upload_table(ts, L.inj, stream)) || (rc = upload_table(tr, L.inj2, stream))) return rc;
+        if ((rc = sum_table(ts, L.inj, src_traces, nsrc, nt, stream)) ||
+            (rc = sum_table(tr, L.inj2, rec_resid, nrec, nt, stream)))
+            return rc;
         if ((rc = grad_plan(d, g, fplan, st, L.cB, L.cC, L.cE, L.U, L.store, 1, L.G, L.status, L.inj.view(),
-                            src_traces, nsrc, L.inj2.view(), rec_resid, nrec, stream, &gplan)))
+                            src_traces, nsrc, L.inj2.view(), rec_resid, nrec, stream, &rplan, &aplan)))
             return rc;
         CK(cudaMemsetAsync(L.G, 0, sizeof(float) * d.npad, stream));
         for (int i = 0; i < 4; ++i) CK(cudaMemsetAsync(L.V[i], 0, sizeof(float) * d.npad, stream));
@@ -2937,9 +2994,9 @@ int32_t wave_grad_revolve(const wave_grid *g, const float *m, const float *damp,
                 if ((rc = run_steps(fj, fw, x.b - x.a, fplan, stream))) return rc;
             } else {
                 rj.q_base = x.a;
-                if ((rc = run_steps(rj, fw, 1, gplan, stream))) return rc;
+                if ((rc = run_steps(rj, fw, 1, rplan, stream))) return rc;
                 aj.q_base = x.a;
-                if ((rc = run_steps(aj, adj, 1, gplan, stream))) return rc;
+                if ((rc = run_steps(aj, adj, 1, aplan, stream))) return rc;
             }
         }
         if ((rc = prof_end(stream))) return rc;
@@ -2963,7 +3020,7 @@ int32_t wave_heat(const wave_grid *g, const float *kappa, const float *u0, const
         if (check_points(src, true, src_traces) || check_points(rec, false, nullptr)) return WAVE_EINVAL;
         if ((uintptr_t)ws % kAlign) return WAVE_EINVAL;
         const int nsrc = npts_of(src), nrec = npts_of(rec);
-        const Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_FWD, nsrc, nrec, g->nt, 0);
+        Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_FWD, nsrc, nrec, g->nt, 0);
         if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
         HostTable ti, tr;
         if (build_table(d, g->h, src, false, &ti) || build_table(d, g->h, rec, true, &tr))
@@ -2984,6 +3041,7 @@ int32_t wave_heat(const wave_grid *g, const float *kappa, const float *u0, const
         CK(cudaMemsetAsync(L.U[1], 0, sizeof(float) * d.npad, stream));
         CK(wt::launch_pad(u0, d.nx, d.ny, d.nz, d.nzp, L.U[0], stream));
         if ((rc = upload_table(ti, L.inj, stream)) || (rc = upload_table(tr, L.rec, stream))) return rc;
+        if ((rc = sum_table(ti, L.inj, src_traces, nsrc, g->nt, stream))) return rc;
         Job job;
         job.d = d;
         job.st = st;
@@ -3028,7 +3086,7 @@ int32_t wave_heat_ab2(const wave_grid *g, const float *kappa, const float *u0, c
         if ((uintptr_t)ws % kAlign) return WAVE_EINVAL;
         const int nsrc = npts_of(src), nrec = npts_of(rec);
         const int R = g->space_order / 2;
-        const Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_FWD, nsrc, nrec, g->nt, 0);
+        Layout L = carve(ws, ws_bytes, false, d, WAVE_OP_FWD, nsrc, nrec, g->nt, 0);
         if (L.bytes > ws_bytes) return WAVE_ENOSPACE;
         HostTable ti, tr;
         if (build_table(d, g->h, src, false, &ti) || build_table(d, g->h, rec, true, &tr)) return WAVE_EINVAL;
@@ -3057,6 +3115,7 @@ int32_t wave_heat_ab2(const wave_grid *g, const float *kappa, const float *u0, c
         CK(wt::launch_pad(u0, d.nx, d.ny, d.nz, d.nzp, L.U[0], stream));
         CK(cudaMemsetAsync(L.U[2], 0, sizeof(float) * d.npad, stream));
         if ((rc = upload_table(ti, L.inj, stream)) || (rc = upload_table(tr, L.rec, stream))) return rc;
+        if ((rc = sum_table(ti, L.inj, src_traces, nsrc, g->nt, stream))) return rc;
         Job job;
         job.d = d;
         job.st = st;

@@ -136,6 +136,10 @@ cudaError_t launch_unpad(const float *src, int nx, int ny, int nz, int nzp, floa
                          float *dst, cudaStream_t s);
 cudaError_t launch_gather(const float *corner, const float *w, int rows, int npts, int row_dir,
                           float *out, cudaStream_t s);
+// F[r][e] (row stride fstride) = the ascending sum of w q[r][item] over the
+// items of injection entry e, for rows [0, rows) of traces q [rows][nq].
+cudaError_t launch_inj_sum(const int4 *pts, const int *item, const float *w, const float *q, int nq, int ne,
+                           int rows, long long fstride, float *F, cudaStream_t s);
 
 // Raise the dynamic shared-memory limit of kernel `func` on the current
 // device to the device's opt-in maximum, once per (device, kernel); it is

@@ -6,6 +6,8 @@
 * wave_grad (checkpoint every k steps, segment recompute, fused imaging
   condition) against the oracle gradient, rel-L2 <= 1e-5, with a ragged last
   segment, for untiled and time-tiled sweeps (bitwise equal to each other);
+* every shape wave_grad can choose for its recompute and adjoint sweeps gives
+  the same gradient bit for bit;
 * the torch.autograd.Function gives the same gradient as wave_grad.
 """
 import numpy as np
@@ -140,3 +142,50 @@ def test_staged_gradient_modes_bitwise(wavelib, cuda, oracle, so):
                 tune = wavelib.Tuning(time_tile=T, tile_y=v["tile_y"], tile_z=v["tile_z"], tile_x=tile_x,
                                       kernel=wavelib.WAVE_KERNEL_STAGED, rows=v["rows"])
                 assert np.array_equal(grad(tune), g1), (T, v, tile_x)
+
+
+@pytest.mark.parametrize("so,T", [(8, 2), (8, 1), (4, 2)])
+def test_every_gradient_shape_bitwise(wavelib, cuda, oracle, monkeypatch, so, T):
+    """wave_grad times its candidate shapes for the recompute sweep and for the
+    adjoint sweep separately.  Pinned one by one through the WAVE_GRAD_PIN
+    test hook, every recompute candidate (with the first adjoint candidate)
+    and every adjoint candidate (with the first recompute candidate) gives the
+    gradient of the first pair bit for bit, which is at parity with the
+    oracle; a ragged last segment."""
+    import torch
+    n = (37, 52, 45)
+    nt, k = 23, 9
+    grid, h, dt, m, damp, src, q, rec = _setup(wavelib, n, so, nt, seed=61 + so, nsrc=2, nrec=7)
+    res = np.random.default_rng(7).standard_normal((nt, len(rec))).astype(np.float32)
+    tm, td, tq, tr = _t(m, cuda), _t(damp, cuda), _t(q, cuda), _t(res, cuda)
+    tune = wavelib.Tuning(time_tile=T, kernel=wavelib.WAVE_KERNEL_STAGED)
+    _, _, ckpt, _ = wavelib.fwd(grid, tm, td, src, tq, rec, tuning=tune, ckpt_every=k)
+
+    def grad(i, j):
+        monkeypatch.setenv("WAVE_GRAD_PIN", "%d,%d" % (i, j))
+        try:
+            g, ws = wavelib.grad(grid, tm, td, src, tq, rec, tr, ckpt, k, tuning=tune)
+        except wavelib.WaveError as e:
+            assert e.code == wavelib.WAVE_EUNSUPPORTED
+            return None
+        assert wavelib.status(ws) == 0
+        torch.cuda.synchronize()
+        return g.cpu().numpy()
+
+    g0 = grad(0, 0)
+    gref = oracle.gradient(_f64(m), _f64(damp), h, dt, nt, so, _f64(src), _f64(q), _f64(rec), _f64(res))
+    assert _relerr(g0, gref) <= TOL
+    ran = [0, 0]
+    for side in (0, 1):
+        for c in range(1, 16):
+            g = grad(c, 0) if side == 0 else grad(0, c)
+            if g is None:
+                break
+            ran[side] += 1
+            assert np.array_equal(g, g0), (side, c)
+    # the shared-warp default and the staged shapes of depth T and 1
+    assert ran[0] >= 2 and ran[1] >= 2, ran
+    monkeypatch.delenv("WAVE_GRAD_PIN")
+    g_auto, _ = wavelib.grad(grid, tm, td, src, tq, rec, tr, ckpt, k, tuning=tune)
+    torch.cuda.synchronize()
+    assert np.array_equal(g_auto.cpu().numpy(), g0)
