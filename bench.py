@@ -564,6 +564,16 @@ def _fwi_gradient(dev, inputs, wave, args):
            "time_tile": plan["time_tile"],
            "gpts_equiv": 3 * pts * p.nt / (ms / 1e3) / 1e9,
            "device_bytes": wave.ckpt_bytes(grid, k) + wave.workspace_bytes(grid, wave.WAVE_OP_GRAD, 1, nrec, k)}
+    # HBM roof of the shot: per point and step the forward moves 24/T B (20
+    # untiled), the recompute storing D 28 B (u^n, u^{n-1}, B, C, E read;
+    # u^{n+1}, D written) and the adjoint with the imaging condition 32 B
+    # (nu^n, nu^{n-1}, B, C, D, G read; nu^{n+1}, G written), both at the
+    # untiled shapes this grid's timing picks; checkpoint copies not counted
+    tf = plan["time_tile"]
+    bps = (24.0 / tf if tf >= 2 else 20.0) + 28.0 + 32.0
+    roof_s = pts * p.nt * bps / (_peaks()[0] * 1e9)
+    out["roofline"] = {"bound": "hbm", "bytes_per_point_step": bps, "roof_s_per_shot": roof_s,
+                       "frac": roof_s / (ms / 1e3), "peak_gbs": _peaks()[0]}
 
     # the same gradient by binomial checkpointing, no forward call first
     d, _, _, _ = wave.fwd(grid, tm, td, p.src_xyz, tq, p.rec_xyz, tuning=tune)
