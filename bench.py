@@ -41,9 +41,9 @@ HBM_FALLBACK_GBS = 6800.0
 # profiles/traffic_tsweep_t2_so8_512.md), valid only for the kernel sources it was
 # taken on: the SHA-256 of csrc/sweep.cuh, csrc/tsweep.cuh and the radius-4
 # variant lists must match, else the bench reports null.
-TRAFFIC_SRC_SHA256 = "d39d15e353c637c5d984cfa5038629eef420729449ee0a69202b2f165d6ca8ac"
+TRAFFIC_SRC_SHA256 = "de67d7eb9a0fcf2381682edcccbbaf4a084634580ad2a99bc76c93eeb874d1a0"
 TRAFFIC_BYTES = {  # ("family R T V rows BZ BY P", chunk, n) -> bytes per launch
-    ("staged R4 T2 V4 rows2 BZ64 BY24 P1", 103, (512, 512, 512)): 2345876480 + 1043785472,
+    ("staged R4 T2 V4 rows2 BZ64 BY24 P1", 103, (512, 512, 512)): 2334687744 + 1043836672,
 }
 
 
@@ -564,16 +564,21 @@ def _fwi_gradient(dev, inputs, wave, args):
            "time_tile": plan["time_tile"],
            "gpts_equiv": 3 * pts * p.nt / (ms / 1e3) / 1e9,
            "device_bytes": wave.ckpt_bytes(grid, k) + wave.workspace_bytes(grid, wave.WAVE_OP_GRAD, 1, nrec, k)}
-    # HBM roof of the shot: per point and step the forward moves 24/T B (20
-    # untiled), the recompute storing D 28 B (u^n, u^{n-1}, B, C, E read;
-    # u^{n+1}, D written) and the adjoint with the imaging condition 32 B
-    # (nu^n, nu^{n-1}, B, C, D, G read; nu^{n+1}, G written), both at the
-    # untiled shapes this grid's timing picks; checkpoint copies not counted
-    tf = plan["time_tile"]
-    bps = (24.0 / tf if tf >= 2 else 20.0) + 28.0 + 32.0
+    # HBM roof of the shot at the depths its three passes ran: per point and
+    # step the forward moves 20 B untiled, 12 B at depth 2 (24 B per launch);
+    # the recompute storing D 28 B untiled (u^n, u^{n-1}, B, C, E read;
+    # u^{n+1}, D written), 18 B at depth 2 (two levels and two D rows
+    # written); the adjoint with the imaging condition 32 B untiled (nu^n,
+    # nu^{n-1}, B, C, D, G read; nu^{n+1}, G written), 20 B at depth 2;
+    # checkpoint copies not counted
+    gp = wave.describe_grad_plan(grid, len(p.src_xyz), nrec, k, tuning=tune)
+    tf, tr, ta = plan["time_tile"], gp["recompute"]["time_tile"], gp["adjoint"]["time_tile"]
+    bps = (12.0 if tf >= 2 else 20.0) + (18.0 if tr >= 2 else 28.0) + (20.0 if ta >= 2 else 32.0)
     roof_s = pts * p.nt * bps / (_peaks()[0] * 1e9)
     out["roofline"] = {"bound": "hbm", "bytes_per_point_step": bps, "roof_s_per_shot": roof_s,
-                       "frac": roof_s / (ms / 1e3), "peak_gbs": _peaks()[0]}
+                       "frac": roof_s / (ms / 1e3), "peak_gbs": _peaks()[0],
+                       "depths": {"forward": tf, "recompute": tr, "adjoint": ta}}
+    out["gradient_plans"] = gp
 
     # the same gradient by binomial checkpointing, no forward call first
     d, _, _, _ = wave.fwd(grid, tm, td, p.src_xyz, tq, p.rec_xyz, tuning=tune)

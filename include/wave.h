@@ -362,6 +362,16 @@ int32_t wave_plan_bound(const wave_grid *g, const wave_tuning *tuning, double hb
  * (WAVE_KERNEL_*), rows per thread.  Returns WAVE_OK or a WAVE_E* code. */
 int32_t wave_describe_plan(const wave_grid *g, const wave_tuning *tuning, int32_t *out);
 
+/* The shapes a wave_grad call with these arguments (grid, tuning, source and
+ * receiver counts, checkpoint interval) runs its gradient sweeps on, as
+ * timed by the first such call on this device: out[0..7] the recompute sweeps
+ * storing second differences, out[8..15] the adjoint sweeps with the imaging
+ * condition, each laid out as wave_describe_plan's out (the x-chunk is the
+ * one the sweeps run).  A host-side query; WAVE_EUNSUPPORTED when no such
+ * call has run yet, WAVE_EINVAL on bad arguments. */
+int32_t wave_describe_grad_plan(const wave_grid *g, const wave_tuning *tuning, int32_t nsrc, int32_t nrec,
+                                int32_t ckpt_every, int32_t *out);
+
 /* ------------------------------------------------------------------------
  * Batched shots.  A seismic survey runs many independent shots over one
  * model; each shot here is a window of the global grid (its own sources and

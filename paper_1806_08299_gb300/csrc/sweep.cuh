@@ -95,7 +95,8 @@ struct PointTable {
     const float *w;
     // injection tables: the value each entry injects at every trace row,
     // f[row * fstride + e] = sum over its items (ascending) of w q[row][item],
-    // summed once per call; nullptr: the sweep sums the items itself
+    // summed once per call before the sweeps (which read only f, pts and
+    // plane_start; item and w serve that sum)
     const float *f;
     long long fstride;
 };
@@ -713,38 +714,25 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, const Stencil &s
                         unsigned hits = 0u;
 #pragma unroll
                         for (int j = 0; j < V; ++j) fv[j] = 0.f;
-                        const int trow = a.q_row0 + a.q_dir * (s - 1);
-                        const long long qrow = (long long)trow * a.nq;
-                        const float *frow = a.inj.f != nullptr ? a.inj.f + (long long)trow * a.inj.fstride : nullptr;
+                        // the value each entry injects at this trace row, summed
+                        // once per call (inj.f), loaded beside the entries
+                        const float *frow = a.inj.f + (long long)(a.q_row0 + a.q_dir * (s - 1)) * a.inj.fstride;
                         for (int eb = e0; eb < e1; eb += 4) {
-                            int4 pt4[4];  // four table points per round trip
-                            float f4[4];  // and their summed values, when the call has them
+                            // four table points ((y, z), the first half of each
+                            // record) and their values per round trip
+                            int2 pt4[4];
+                            float f4[4];
 #pragma unroll
                             for (int u = 0; u < 4; ++u) {
-                                pt4[u] = eb + u < e1 ? __ldg(a.inj.pts + eb + u) : make_int4(-1, -1, 0, 0);
-                                f4[u] = frow != nullptr && eb + u < e1 ? __ldg(frow + eb + u) : 0.f;
+                                pt4[u] = eb + u < e1 ? __ldg(reinterpret_cast<const int2 *>(a.inj.pts + eb + u))
+                                                     : make_int2(-1, -1);
+                                f4[u] = eb + u < e1 ? __ldg(frow + eb + u) : 0.f;
                             }
 #pragma unroll
                             for (int u = 0; u < 4; ++u) {
-                                const int4 pt = pt4[u];
+                                const int2 pt = pt4[u];
                                 if (pt.x != gy || pt.y < gz || pt.y >= gz + V) continue;
-                                // items two at a time: their loads overlap, the sum
-                                // keeps the ascending order
-                                float f = 0.f;
-                                int itm = pt.z;
-                                if (frow != nullptr) {
-                                    f = f4[u];
-                                    itm = pt.w;
-                                }
-                                for (; itm + 1 < pt.w; itm += 2) {
-                                    const int i0 = __ldg(a.inj.item + itm), i1 = __ldg(a.inj.item + itm + 1);
-                                    const float w0 = __ldg(a.inj.w + itm), w1 = __ldg(a.inj.w + itm + 1);
-                                    const float q0 = __ldg(a.q + qrow + i0), q1 = __ldg(a.q + qrow + i1);
-                                    f = __fmaf_rn(w0, q0, f);
-                                    f = __fmaf_rn(w1, q1, f);
-                                }
-                                if (itm < pt.w)
-                                    f = __fmaf_rn(__ldg(a.inj.w + itm), __ldg(a.q + qrow + __ldg(a.inj.item + itm)), f);
+                                const float f = f4[u];
                                 const int jj = pt.y - gz;
 #pragma unroll
                                 for (int j = 0; j < V; ++j) fv[j] = jj == j ? f : fv[j];

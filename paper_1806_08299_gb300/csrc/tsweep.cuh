@@ -354,10 +354,9 @@ __device__ __forceinline__ void tstage_inject(float2 (&un)[VY][V / 2], const flo
                                               int wy0, int wy1, int wz0, int wz1,
                                               float2 (*dd)[V / 2] = nullptr)
 {
-    const long long qbase = (long long)qrow * a.nq;
-    // the call's summed entry values, loaded beside the entries (one round
-    // trip per 32 entries instead of the item, weight and trace chain)
-    const float *frow = a.inj.f != nullptr ? a.inj.f + (long long)qrow * a.inj.fstride : nullptr;
+    // the value each entry injects at this trace row, summed once per call
+    // (inj.f), loaded beside the entries: one round trip per 32 entries
+    const float *frow = a.inj.f + (long long)qrow * a.inj.fstride;
     const int lane = threadIdx.x & 31;
     float fv[VY][V];
     unsigned hits[VY];
@@ -368,36 +367,21 @@ __device__ __forceinline__ void tstage_inject(float2 (&un)[VY][V / 2], const flo
         for (int j = 0; j < V; ++j) fv[v][j] = 0.f;
     }
     for (int eb = e0; eb < e1; eb += 32) {
-        const int4 mine = eb + lane < e1 ? __ldg(a.inj.pts + eb + lane) : make_int4(-1, -1, 0, 0);
-        const float fmine = frow != nullptr && eb + lane < e1 ? __ldg(frow + eb + lane) : 0.f;
+        // the entry's (y, z) only: the first half of its table record
+        const int2 mine = eb + lane < e1 ? __ldg(reinterpret_cast<const int2 *>(a.inj.pts + eb + lane))
+                                         : make_int2(-1, -1);
+        const float fmine = eb + lane < e1 ? __ldg(frow + eb + lane) : 0.f;
         const bool rel = mine.x >= wy0 && mine.x < wy1 && mine.y >= wz0 && mine.y < wz1;
         unsigned m = __ballot_sync(0xffffffffu, rel);
         while (m != 0u) {
             const int l = __ffs(m) - 1;
             m &= m - 1u;
-            int4 pt;
+            int2 pt;
             pt.x = __shfl_sync(0xffffffffu, mine.x, l);
             pt.y = __shfl_sync(0xffffffffu, mine.y, l);
-            pt.z = __shfl_sync(0xffffffffu, mine.z, l);
-            pt.w = __shfl_sync(0xffffffffu, mine.w, l);
-            const float fl = __shfl_sync(0xffffffffu, fmine, l);
+            const float f = __shfl_sync(0xffffffffu, fmine, l);
             const int v = pt.x - gy, jj = pt.y - gz;
             if (v < 0 || v >= VY || jj < 0 || jj >= V) continue;
-            float f = 0.f;
-            int itm = pt.z;
-            if (frow != nullptr) {
-                f = fl;
-                itm = pt.w;
-            }
-            for (; itm + 1 < pt.w; itm += 2) {  // items in pairs, ascending sum
-                const int i0 = __ldg(a.inj.item + itm), i1 = __ldg(a.inj.item + itm + 1);
-                const float w0 = __ldg(a.inj.w + itm), w1 = __ldg(a.inj.w + itm + 1);
-                const float q0 = __ldg(a.q + qbase + i0), q1 = __ldg(a.q + qbase + i1);
-                f = __fmaf_rn(w0, q0, f);
-                f = __fmaf_rn(w1, q1, f);
-            }
-            if (itm < pt.w)
-                f = __fmaf_rn(__ldg(a.inj.w + itm), __ldg(a.q + qbase + __ldg(a.inj.item + itm)), f);
 #pragma unroll
             for (int vv = 0; vv < VY; ++vv)
 #pragma unroll

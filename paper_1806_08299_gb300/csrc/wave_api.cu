@@ -838,6 +838,8 @@ int build_launch(const Job &job, const State &s, int j, const SweepVariant *v, i
     }
     a.cE = job.cE;
     a.inj = job.inj;
+    // the sweeps read injection values only from the call's sums (sum_table)
+    if (a.inj.plane_start != nullptr && a.inj.f == nullptr) return WAVE_EINVAL;
     a.q = job.q;
     a.nq = job.nq;
     a.q_row0 = job.q_base + job.q_dir * j;
@@ -3241,6 +3243,43 @@ int32_t wave_plan_bound(const wave_grid *g, const wave_tuning *tuning, double hb
     }
     if (hbm <= 0.0 || lsu <= 0.0) return WAVE_ECUDA;
     *ms = plan_bound_ms(d, p.v, p.chunk, hbm, lsu, l2);
+    return WAVE_OK;
+}
+
+int32_t wave_describe_grad_plan(const wave_grid *g, const wave_tuning *tuning, int32_t nsrc, int32_t nrec,
+                                int32_t ckpt_every, int32_t *out)
+{
+    Dims d;
+    int rc = check_grid(g, &d);
+    if (rc) return rc;
+    if (out == nullptr || nsrc < 0 || nrec < 0 || ckpt_every < 1) return WAVE_EINVAL;
+    Plan fwd;
+    float *U[4] = {nullptr, nullptr, nullptr, nullptr};
+    if ((rc = resolve_plan(d, g, tuning, false, nullptr, nullptr, nullptr, U, nullptr, nullptr, &fwd))) return rc;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int rows = std::max(1, std::min((int)ckpt_every, g->nt));
+    const GradKey key{d.nx, d.ny, d.nz, g->space_order, dev, nsrc, nrec, rows, fwd.v};
+    std::pair<Plan, Plan> pp;
+    {
+        std::lock_guard<std::mutex> lk(g_grad_mu);
+        auto it = g_grad_cache.find(key);
+        if (it == g_grad_cache.end()) return WAVE_EUNSUPPORTED;
+        pp = it->second;
+    }
+    const Plan *ps[2] = {&pp.first, &pp.second};
+    for (int k = 0; k < 2; ++k) {
+        const Plan &p = *ps[k];
+        int32_t *o = out + 8 * k;
+        o[0] = p.v->T;
+        o[1] = p.v->BY;
+        o[2] = p.chunk > 0 ? p.chunk : default_chunk(d, p.v);
+        o[3] = p.v->BZ;
+        o[4] = p.v->V;
+        o[5] = p.v->P;
+        o[6] = p.v->kind + 1;
+        o[7] = rows_of(p.v);
+    }
     return WAVE_OK;
 }
 

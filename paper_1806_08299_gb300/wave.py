@@ -37,7 +37,7 @@ EXPORTED = ["wave_version", "wave_strerror", "wave_fd_coefficients", "wave_cfl_d
             "wave_fwd_noalloc", "wave_measure_peaks", "wave_batch_workspace_bytes",
             "wave_fwd_batched", "wave_grad_batched", "wave_describe_batch_plan", "wave_heat",
             "wave_grad_revolve", "wave_revolve_forward_steps", "wave_revolve_schedule", "wave_born",
-            "wave_heat_ab2"]
+            "wave_heat_ab2", "wave_describe_grad_plan"]
 
 
 class WaveError(RuntimeError):
@@ -157,6 +157,8 @@ def _lib():
         lib.wave_status.restype = i32
         lib.wave_describe_plan.argtypes = [gp, tp, ctypes.POINTER(i32)]
         lib.wave_describe_plan.restype = i32
+        lib.wave_describe_grad_plan.argtypes = [gp, tp, i32, i32, i32, ctypes.POINTER(i32)]
+        lib.wave_describe_grad_plan.restype = i32
         lib.wave_sweep_stats.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32),
                                          ctypes.POINTER(i32)]
         lib.wave_sweep_stats.restype = i32
@@ -233,6 +235,19 @@ def describe_plan(grid, tuning=None):
            "wave_describe_plan")
     return dict(time_tile=out[0], tile_y=out[1], tile_x=out[2], tile_z=out[3], vec=out[4],
                 prefetch=out[5], kernel=out[6], rows=out[7])
+
+
+def describe_grad_plan(grid, nsrc, nrec, ckpt_every, tuning=None):
+    """Shapes of the recompute and adjoint sweeps of the last wave_grad call
+    with these arguments (raises WaveError when none has run)."""
+    g = grid.c()
+    out = (ctypes.c_int32 * 16)()
+    t = tuning.c() if tuning is not None else None
+    _check(_lib().wave_describe_grad_plan(ctypes.byref(g), ctypes.byref(t) if t else None, int(nsrc), int(nrec),
+                                          int(ckpt_every), out), "wave_describe_grad_plan")
+    keys = ("time_tile", "tile_y", "tile_x", "tile_z", "vec", "prefetch", "kernel", "rows")
+    return {"recompute": {k: out[i] for i, k in enumerate(keys)},
+            "adjoint": {k: out[8 + i] for i, k in enumerate(keys)}}
 
 
 # --------------------------------------------------------------------------

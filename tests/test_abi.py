@@ -193,3 +193,15 @@ def test_batch_plan_of_named_tunings_without_gpu(wavelib):
     assert wavelib.describe_batch_plan(g, shots, 0, 2, wavelib.Tuning(time_tile=2)) is None
     odd = wavelib.Grid((48, 40, 44), (0.01,) * 3, 1e-3, 23, 4)
     assert wavelib.describe_batch_plan(odd, shots, 0, 2, wavelib.Tuning(time_tile=2, kernel=staged)) is None
+
+
+def test_grad_plan_query_before_any_gradient_call(wavelib):
+    # host-side query: no gradient call with these arguments has run in this
+    # process, so there is no timed choice to report; bad arguments are refused
+    g = wavelib.Grid((40, 36, 44), (0.01,) * 3, 1e-3, 30, 8)
+    with pytest.raises(wavelib.WaveError) as e:
+        wavelib.describe_grad_plan(g, 1, 3, 10, tuning=wavelib.Tuning(time_tile=1))
+    assert e.value.code == wavelib.WAVE_EUNSUPPORTED
+    with pytest.raises(wavelib.WaveError) as e:
+        wavelib.describe_grad_plan(g, 1, 3, 0)
+    assert e.value.code == wavelib.WAVE_EINVAL

@@ -189,3 +189,9 @@ def test_every_gradient_shape_bitwise(wavelib, cuda, oracle, monkeypatch, so, T)
     g_auto, _ = wavelib.grad(grid, tm, td, src, tq, rec, tr, ckpt, k, tuning=tune)
     torch.cuda.synchronize()
     assert np.array_equal(g_auto.cpu().numpy(), g0)
+    # the timed choice is reported per phase, among the candidates' depths
+    gp = wavelib.describe_grad_plan(grid, len(src), len(rec), k, tuning=tune)
+    for phase in ("recompute", "adjoint"):
+        assert gp[phase]["time_tile"] in (1, T), gp
+        assert gp[phase]["kernel"] in (wavelib.WAVE_KERNEL_SHARED, wavelib.WAVE_KERNEL_STAGED), gp
+        assert gp[phase]["tile_x"] >= 1
