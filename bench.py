@@ -481,6 +481,11 @@ def run_ours(args):
                 "alu": {"fp32_tflops_measured": fp32_tflops, "flops_per_point": flops_per_pt,
                         "roof_gpts": alu_roof, "frac": gpts / alu_roof},
                 "smem_tbs_measured": smem_tbs,
+                # the launch's point-updates at the untiled sweep's 20 B each: above
+                # the measured HBM bandwidth (frac > 1) a time tile delivers more
+                # updates than any untiled sweep could at that bandwidth
+                "untiled_equivalent": {"bytes_per_point": 20, "gbs": gpts * 20.0,
+                                       "frac": gpts * 20.0 / hbm},
                 "model": _model_line(p.space_order, pl)}
 
     T = plan["time_tile"]
