@@ -1164,7 +1164,7 @@ bool tune_prune()
 // points) and cache the fastest: the paper's auto-tuner extended to the time
 // tile (Sec. 4.4, Sec. 5.2.2), here over (T, tile, x-chunk).  Candidates are
 // timed in two passes over the whole list (a warm-up launch before the first)
-// and each keeps its better pass, so that no candidate's verdict rests on one
+// and each keeps its better pass, so that no candidate's result rests on one
 // run taken in one GPU state; candidates within a few percent of each other
 // are otherwise decided by noise.
 int autotune(const Dims &d, const Stencil &st, const float *cB, const float *cC, float *const U[4],
