@@ -162,6 +162,21 @@ def max_over_ranks(x, dist=None, device=None):
     return float(t.item())
 
 
+def gradient_bytes_per_point_step(t_forward, t_recompute, t_adjoint):
+    """Compulsory HBM bytes per grid point and time step of one FWI gradient
+    shot at the depths its three passes ran.  Forward: u^n, u^{n-1}, B, C read
+    and u^{n+1} written, 20 B untiled; a depth-2 launch reads the four once
+    and writes two levels, 24 B per two steps.  Recompute storing D: E read
+    and D written besides, 28 B untiled, 36 B per two steps at depth 2 (two
+    levels and two D rows written).  Adjoint with the imaging condition: D
+    and G read and G written besides, 32 B untiled, 40 B per two steps at
+    depth 2 (two D rows read, G read and written once)."""
+    fwd = 24.0 / 2 if t_forward >= 2 else 20.0
+    rec = 36.0 / 2 if t_recompute >= 2 else 28.0
+    adj = 40.0 / 2 if t_adjoint >= 2 else 32.0
+    return fwd + rec + adj
+
+
 def whole_job_rate(pts_per_rank, steps, ms, world):
     """GPts/s of `world` replicas that each update pts_per_rank points per
     step for `steps` steps, over the slowest rank's `ms` milliseconds."""
@@ -569,16 +584,11 @@ def _fwi_gradient(dev, inputs, wave, args):
            "time_tile": plan["time_tile"],
            "gpts_equiv": 3 * pts * p.nt / (ms / 1e3) / 1e9,
            "device_bytes": wave.ckpt_bytes(grid, k) + wave.workspace_bytes(grid, wave.WAVE_OP_GRAD, 1, nrec, k)}
-    # HBM roof of the shot at the depths its three passes ran: per point and
-    # step the forward moves 20 B untiled, 12 B at depth 2 (24 B per launch);
-    # the recompute storing D 28 B untiled (u^n, u^{n-1}, B, C, E read;
-    # u^{n+1}, D written), 18 B at depth 2 (two levels and two D rows
-    # written); the adjoint with the imaging condition 32 B untiled (nu^n,
-    # nu^{n-1}, B, C, D, G read; nu^{n+1}, G written), 20 B at depth 2;
-    # checkpoint copies not counted
+    # HBM roof of the shot at the depths its three passes ran (checkpoint
+    # copies not counted)
     gp = wave.describe_grad_plan(grid, len(p.src_xyz), nrec, k, tuning=tune)
     tf, tr, ta = plan["time_tile"], gp["recompute"]["time_tile"], gp["adjoint"]["time_tile"]
-    bps = (12.0 if tf >= 2 else 20.0) + (18.0 if tr >= 2 else 28.0) + (20.0 if ta >= 2 else 32.0)
+    bps = gradient_bytes_per_point_step(tf, tr, ta)
     roof_s = pts * p.nt * bps / (_peaks()[0] * 1e9)
     out["roofline"] = {"bound": "hbm", "bytes_per_point_step": bps, "roof_s_per_shot": roof_s,
                        "frac": roof_s / (ms / 1e3), "peak_gbs": _peaks()[0],

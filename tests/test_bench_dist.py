@@ -59,3 +59,12 @@ def test_reference_arm_runs_on_rank0_only():
                        capture_output=True, text=True, env=env, timeout=300, cwd=ROOT)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_gradient_byte_model():
+    # the compulsory bytes of a gradient shot per point and step: all passes
+    # untiled, all at depth 2, and the mix the c4 timing picked in one run
+    import bench
+    assert bench.gradient_bytes_per_point_step(1, 1, 1) == 20 + 28 + 32
+    assert bench.gradient_bytes_per_point_step(2, 2, 2) == 12 + 18 + 20
+    assert bench.gradient_bytes_per_point_step(2, 1, 2) == 60
